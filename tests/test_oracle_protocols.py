@@ -1,0 +1,166 @@
+"""Pins for oracle.protocols: reconstruction against plaintext, Table 1 byte counts, truncation
+error model (Sec. 4.2) and abort on inconsistent Pi_Rec messages -- no GPU."""
+import hashlib
+
+import numpy as np
+import pytest
+
+from oracle.protocols import (Abort, asr, decode_fixed, encode_fixed, matmul, mult, reconstruct,
+                              share_input, trunc_coeffs)
+from oracle.shares import OFFLINE, ONLINE, Session
+
+U64 = np.uint64
+SEED = hashlib.sha256(b"mpc3-oracle-tests").digest()
+
+
+def _rng(i=0):
+    return np.random.default_rng(1000 + i)
+
+
+def test_fixed_point_encoding_sec2():
+    # Sec. 2: x >= 0 -> floor(x 2^k); x < 0 -> 2^l + floor(x 2^k)
+    assert int(encode_fixed(1.5, 13)) == 3 * (1 << 12)
+    assert int(encode_fixed(-1.0, 13)) == (1 << 64) - (1 << 13)
+    assert int(encode_fixed(-1e-9, 13)) == (1 << 64) - 1
+    v = _rng().uniform(-4, 4, 100)
+    assert np.all(np.abs(decode_fixed(encode_fixed(v, 13), 13) - v) <= 2.0 ** -13)
+
+
+def test_share_and_reconstruct_roundtrip():
+    s = Session(SEED)
+    x = _rng(1).integers(0, 2**64, 257, dtype=U64)
+    X = share_input(s, x, 1)
+    assert np.array_equal(reconstruct(s, X), x)
+    # the masks are fresh PRG output: m differs from x
+    assert not np.array_equal(X.p1_m, x)
+
+
+def test_mult_reconstructs_product_mod_2_64():
+    s = Session(SEED)
+    rng = _rng(2)
+    x = rng.integers(0, 2**64, 300, dtype=U64)
+    y = rng.integers(0, 2**64, 300, dtype=U64)
+    Z = mult(s, share_input(s, x, 1), share_input(s, y, 2), 3)
+    z = reconstruct(s, Z)
+    ref = [(int(a) * int(b)) % (1 << 64) for a, b in zip(x, y)]
+    assert [int(v) for v in z] == ref
+
+
+def test_matmul_reconstructs_product_python_ints():
+    s = Session(SEED)
+    rng = _rng(3)
+    M, K, N = 5, 7, 3
+    A = rng.integers(0, 2**64, (M, K), dtype=U64)
+    B = rng.integers(0, 2**64, (K, N), dtype=U64)
+    res = matmul(s, share_input(s, A, 1), share_input(s, B, 2), 3)
+    z = reconstruct(s, res.out)
+    for a in range(M):
+        for b in range(N):
+            ref = sum(int(A[a, k]) * int(B[k, b]) for k in range(K)) % (1 << 64)
+            assert int(z[a, b]) == ref
+
+
+def test_trunc_coefficients_reproduce_arithmetic_shift():
+    rng = _rng(4)
+    for t in (0, 1, 13, 16, 63):
+        c, cp = trunc_coeffs(t)
+        b1 = rng.integers(0, 2**64, 50, dtype=U64)
+        b2 = rng.integers(0, 2**64, 50, dtype=U64)
+        bits = (b1[:, None] >> np.arange(64, dtype=U64)) & (b2[:, None] >> np.arange(64, dtype=U64)) & U64(1)
+        rx = b1 + b2 + np.sum(bits * c, axis=1, dtype=U64)
+        rz = asr(b1, t) + asr(b2, t) + np.sum(bits * cp, axis=1, dtype=U64)
+        assert np.array_equal(rx, b1 ^ b2)
+        assert np.array_equal(rz, asr(b1 ^ b2, t))
+
+
+def test_trunc_error_model_sec4_2():
+    """Sec. 4.2: the truncated result is off by at most one in the last bit (carry), and wrong with
+    probability about 2^(l_x - l + 1) (wrap)."""
+    s = Session(SEED)
+    rng = _rng(5)
+    M, K, N = 16, 32, 16
+    A = encode_fixed(rng.uniform(-4, 4, (M, K)), 13)
+    B = encode_fixed(rng.uniform(-4, 4, (K, N)), 13)
+    res = matmul(s, share_input(s, A, 1), share_input(s, B, 2), 3, trunc_bits=13)
+    zpre = reconstruct(s, res.z_pre)
+    assert np.array_equal(zpre, A @ B)
+    out = reconstruct(s, res.out)
+    diff = out.astype(np.int64) - asr(A @ B, 13).astype(np.int64)
+    assert set(np.unique(diff)) <= {0, 1}
+    # the pair itself: r_z = r_x >>_arith t
+    tp = res.tp
+    rx = (tp.rx1_p0 + tp.rx2_p0)
+    rz = (tp.rz1_p0 + tp.rz2_p0)
+    assert np.array_equal(rx, tp.b1 ^ tp.b2)
+    assert np.array_equal(rz, asr(rx, 13))
+
+
+def test_trunc_wrap_probability():
+    """With |x| < 2^(l_x) the wrap of m = x + r_x happens with probability about 2^(l_x - l + 1)."""
+    s = Session(SEED)
+    rng = _rng(6)
+    n = 20000
+    lx = 60
+    x = rng.integers(-(2**(lx - 1)), 2**(lx - 1), n).astype(np.int64).astype(U64)
+    X = share_input(s, x.reshape(n, 1), 1)
+    ONE = share_input(s, np.ones((1, 1), dtype=U64), 2)
+    res = matmul(s, X, ONE, 3, trunc_bits=13)
+    out = reconstruct(s, res.out).reshape(-1).astype(np.int64)
+    diff = out - asr(x, 13).astype(np.int64)
+    wrong = np.count_nonzero((diff != 0) & (diff != 1))
+    # m = x + r wraps (as a signed value) with probability |x| / 2^l for uniform r
+    p = np.abs(x.astype(np.int64)).astype(np.float64) / 2.0 ** 64
+    mean, sd = p.sum(), np.sqrt((p * (1 - p)).sum())
+    assert abs(wrong - mean) <= 5 * sd + 1
+    assert wrong <= n * 2.0 ** (lx - 64 + 1)   # Sec. 4.2 bound 2^(l_x - l + 1)
+
+
+def _per_elem(s, phase, proto, count):
+    return s.ledger_bytes(phase, proto) / (8 * count)
+
+
+def test_ledger_matches_table1(golden):
+    import os
+    rows = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_comm.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            op, off, on = line.split()
+            rows[op] = (int(off), int(on))
+    rng = _rng(7)
+    # mult
+    s = Session(SEED)
+    x = rng.integers(0, 2**64, 64, dtype=U64)
+    X, Y = share_input(s, x, 1), share_input(s, x, 2)
+    assert _per_elem(s, ONLINE, "share", 128) == rows["share"][1]
+    mult(s, X, Y, 3)
+    assert (_per_elem(s, OFFLINE, "mult", 64), _per_elem(s, ONLINE, "mult", 64)) == rows["mult"]
+    # inner product (matrix product, n = K independent)
+    for K in (1, 9):
+        s = Session(SEED)
+        A = share_input(s, rng.integers(0, 2**64, (3, K), dtype=U64), 1)
+        B = share_input(s, rng.integers(0, 2**64, (K, 4), dtype=U64), 2)
+        matmul(s, A, B, 3)
+        assert (_per_elem(s, OFFLINE, "inner", 12), _per_elem(s, ONLINE, "inner", 12)) == rows["inner"]
+        s.ledger.clear()
+        matmul(s, A, B, 4, trunc_bits=13)
+        off = _per_elem(s, OFFLINE, "inner", 12) + _per_elem(s, OFFLINE, "trunc", 12)
+        on = _per_elem(s, ONLINE, "inner", 12) + _per_elem(s, ONLINE, "trunc", 12)
+        assert (off, on) == rows["inner_trunc"]
+        assert (_per_elem(s, OFFLINE, "trunc", 12), _per_elem(s, ONLINE, "trunc", 12)) == rows["trunc"]
+
+
+def test_rec_aborts_on_inconsistent_message():
+    s = Session(SEED)
+    X = share_input(s, np.arange(10, dtype=U64), 1)
+    s.arm_fault("REC_MSG", 3, 1)
+    with pytest.raises(Abort):
+        reconstruct(s, X)
+
+
+def test_inconsistent_replica_aborts_at_reconstruction():
+    s = Session(SEED)
+    s.arm_fault("MX_COPY_P1", 2, 1 << 40)
+    X = share_input(s, np.arange(10, dtype=U64), 1)
+    with pytest.raises(Abort):
+        reconstruct(s, X)
