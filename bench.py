@@ -1,0 +1,327 @@
+"""Benchmark: one secure Z_2^64 GEMM layer per step on GB300, through libmpc3's C-ABI.
+
+Step = the whole hot path on one batch of synthetic input:
+  input sharing of X (n x n) and W (n x n)          Pi_<.>^{l,0}
+  Pi_Inner for all n^2 outputs + Pi_Trunc^13          (offline Gamma, trunc pairs, online products)
+  Pi_BIVerify of the layer (batch 0: the n^2 inner products; batch 1: the truncation pairs)
+  Pi_Rec of the n x n output
+Metric: secure ring-MAC/s = n^3 / step time (plaintext-equivalent multiply-accumulates of the
+secure product, verification included).  Inputs are resident in HBM when timing starts ("value");
+"e2e" repeats the step through the same C-ABI with the inputs in pinned host memory and the
+output read back to pinned host memory.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 4096] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("secure Z_2^64 ring-MAC/s incl. verification (limb-INT8 TC vs u64 path); "
+          "CNN images/s")
+UNIT = "ring-MAC/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--trunc", type=int, default=13)
+    ap.add_argument("--gemm-path", choices=["u64", "tc"], default="u64")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# reference arm / CPU baseline: the oracle timed on the host on a bounded slab of the workload
+# ---------------------------------------------------------------------------------------------
+def oracle_step(n: int, rows: int, cols: int, t: int, seed: bytes, call: int):
+    from oracle import protocols as OP
+    from oracle import verify as OV
+    from oracle.shares import Session
+    from paper_2411_09287_gb300 import workloads
+    X, W = workloads.gemm_square(n) if n <= 1024 else workloads.gemm_shape(rows, cols, n, "slab")
+    X, W = X[:rows, :n], W[:n, :cols]
+    s = Session(seed)
+    SX = OP.share_input(s, X, call)
+    SW = OP.share_input(s, W, call + 1)
+    res = OP.matmul(s, SX, SW, call + 2, trunc_bits=t)
+    ok = OV.matmul_verify(s, SX, SW, res, call + 3, t)
+    out = OP.reconstruct(s, res.out)
+    assert ok and out.shape == (rows, cols)
+
+
+def cpu_baseline(n: int, t: int, rows: int = 2, cols: int = 32, reps: int = 1):
+    from paper_2411_09287_gb300 import workloads
+    seed = workloads.master_seed("C3-cpu")
+    t0 = time.perf_counter()
+    for i in range(reps):
+        oracle_step(n, rows, cols, t, seed, 10 + 10 * i)
+    dt = (time.perf_counter() - t0) / reps
+    macs = rows * cols * n
+    return {"value": macs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{rows}x{cols} output slab of the {n}x{n}x{n} layer (K = {n}): share, "
+                      f"Pi_Inner + Pi_Trunc^{t}, Pi_BIVerify (both batches), Pi_Rec; "
+                      f"{dt:.1f} s per slab, numpy single-threaded"}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    rows, cols = 1, 16
+    for i in range(warm):
+        oracle_step(args.n, rows, cols, args.trunc, b"\x01" * 32, 100 + i * 10)
+    t0 = time.perf_counter()
+    for i in range(steps):
+        oracle_step(args.n, rows, cols, args.trunc, b"\x02" * 32, 1000 + i * 10)
+    dt = (time.perf_counter() - t0) / steps
+    v = rows * cols * args.n / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": steps, "warmup": warm, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"secure GEMM {args.n}x{args.n}x{args.n} + trunc + verify + rec",
+                       "sample_rows": rows, "sample_cols": cols},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{rows}x{cols} output slab of the layer per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+
+    from paper_2411_09287_gb300 import mpc, workloads
+
+    n, t = args.n, args.trunc
+    M = N = K = n
+    E = M * N
+    gemm_path = mpc.GEMM_U64 if args.gemm_path == "u64" else mpc.GEMM_LIMB_TC
+    ctx = mpc.Context(workloads.master_seed(f"C3-{n}") , device=local, gemm_path=gemm_path)
+    X, W = workloads.gemm_square(n)
+    Xd, Wd = mpc.from_u64(ctx, X.reshape(-1)), mpc.from_u64(ctx, W.reshape(-1))
+    xs, wsh = ctx.shares(M * K), ctx.shares(K * N)
+    zpre, zout, pq = ctx.shares(E), ctx.shares(E), ctx.empty(12 * E)
+    out_dev = ctx.empty(E)
+    # one workspace for every call of the step
+    wsb = max(ctx.ws_size(mpc.OP_SHARE, M * K), ctx.ws_size(mpc.OP_MATMUL, M, N, K, t),
+              ctx.ws_size(mpc.OP_VERIFY_MATMUL, M, N, K, t), ctx.ws_size(mpc.OP_RECONSTRUCT, E))
+    ws = ctx.workspace(wsb)
+    lib, h = ctx.lib, ctx.h
+    import ctypes as C
+    P = lambda tt: C.c_void_p(tt.data_ptr())
+    call = [1]
+
+    def check(rc, what):
+        if rc != mpc.MPC_OK:
+            raise mpc.MpcError(rc, f"{what}: {lib.mpc_last_error(h).decode()}")
+
+    def step(x_ptr, w_ptr, on_host, out_ptr, out_host):
+        c = call[0]
+        call[0] += 8
+        check(lib.mpc_share_input(h, c, x_ptr, on_host, M * K, P(xs), P(ws), wsb), "share X")
+        check(lib.mpc_share_input(h, c + 1, w_ptr, on_host, K * N, P(wsh), P(ws), wsb), "share W")
+        check(lib.mpc_matmul(h, c + 2, P(xs), P(wsh), M, N, K, t, P(zpre), P(zout), P(pq), P(ws),
+                             wsb), "matmul")
+        check(lib.mpc_verify_matmul(h, c + 3, P(xs), P(wsh), P(zpre), P(pq), M, N, K, t, c + 2,
+                                    -1, -1, P(ws), wsb, None), "verify")
+        check(lib.mpc_reconstruct(h, P(zout), E, out_ptr, out_host, P(ws), wsb), "reconstruct")
+
+    stream = torch.cuda.current_stream()
+    dev_args = (P(Xd), P(Wd), 0, P(out_dev), 0)
+    for _ in range(args.warmup):
+        step(*dev_args)
+    torch.cuda.synchronize()
+    ref_out = mpc.to_u64(out_dev)[:E].copy()
+
+    # ---- timed region: inputs resident in HBM ----
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ctx.profile(True)
+    l0 = ctx.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(*dev_args)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = (ctx.launch_count() - l0) // args.steps
+    phases = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    assert np.array_equal(mpc.to_u64(out_dev)[:E], ref_out), "output changed between steps"
+
+    # ---- e2e: host inputs (pinned) -> device, output -> pinned host ----
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(X.reshape(-1).view(np.int64)).pin_memory()
+        Wh = torch.from_numpy(W.reshape(-1).view(np.int64)).pin_memory()
+        Oh = torch.empty(E, dtype=torch.int64).pin_memory()
+        host_args = (P(Xh), P(Wh), 1, P(Oh), 1)
+        step(*host_args)
+        torch.cuda.synchronize()
+        e_steps = max(1, min(args.steps, 3))
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            step(*host_args)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / e_steps
+        if world > 1:
+            dtt = torch.tensor([dt], device="cuda")
+            dist.all_reduce(dtt, op=dist.ReduceOp.MAX)
+            dt = float(dtt.item())
+        assert np.array_equal(Oh.numpy().view(np.uint64), ref_out)
+        e2e = {"value": world * n ** 3 / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+               "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": n * n * 8}
+
+    if world > 1:
+        mt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(mt, op=dist.ReduceOp.MAX)
+        ms = float(mt.item())
+    value = world * n ** 3 / (ms * 1e-3)
+
+    # ---- roofline of the dominant phase ----
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else open(os.devnull) as f:
+        try:
+            peaks = json.load(f)
+        except Exception:
+            peaks = {}
+    per = {k: v[0] / args.steps for k, v in phases.items()}
+    dom = max(per, key=per.get)
+    sm_max = (clk.get("sm_max_mhz") or 2070.0)
+    alu_peak = 152 * 64 * sm_max * 1e6 / 1e12      # int32 IMAD/s, Tops (derivation in the design doc)
+    work = {   # algorithmic u64 MACs per step of the GEMM-shaped phases (3 IMAD per u64 MAC)
+        "gemm": 5 * M * N * K,
+        "trunc_s": 4096 * 64 * E,
+    }
+    if dom in work:
+        achieved = 3 * work[dom] / (per[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak,
+                "unit": "Tops/s (int32 IMAD)", "frac": achieved / alu_peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 64 IMAD/clk x max SM clock"}
+    else:
+        roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": alu_peak,
+                "unit": "Tops/s (int32 IMAD)", "frac": None, "traffic": None}
+    gemm_ach = 3 * work["gemm"] / (per["gemm"] * 1e-3) / 1e12 if per.get("gemm") else None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"secure GEMM {n}x{n}x{n} over Z_2^64 (uniform u64 shares) + "
+                               f"Pi_Trunc^{t} + Pi_BIVerify (2 batches) + Pi_Rec",
+                   "M": M, "N": N, "K": K, "trunc_bits": t, "gemm_path": args.gemm_path,
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (working set "
+                                                            f"{(wsb + 8 * 6 * (2 * n * n + 4 * E)) / 2**30:.1f} GiB)"},
+        "roofline": roof,
+        "gemm_u64_path": {"tops": gemm_ach, "frac_of_alu_peak": gemm_ach / alu_peak if gemm_ach else None},
+        "phases_ms": {k: round(v, 3) for k, v in per.items() if v > 0},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline(n, t)
+        except Exception as ex:   # reported, never silently replaced
+            line["cpu_baseline"] = {"error": str(ex)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

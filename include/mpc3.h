@@ -1,0 +1,204 @@
+/*
+ * libmpc3 -- maliciously secure three-party linear-function evaluation over Z_2^64 on one GPU.
+ *
+ * The library implements the hot path of "The Communication-Friendly Privacy-Preserving Machine
+ * Learning against Malicious Adversaries" (arXiv 2411.09287): the <.>-sharing of Sec. 2, Pi_Mult
+ * (Fig. MultP), Pi_Inner for matrix products (Fig. DPP, Sec. 4.1), Pi_Trunc (Fig. trunc), the
+ * batched verification Pi_MultVerify / Pi_BIVerify (Fig. PPEV, Fig. PBDP) built from Pi_Tran
+ * (Fig. MTP), Pi_Reduce (Fig. Reduce) and Pi_InnerVerify (Fig. DPV) over GR(2^64, 64), and
+ * Pi_Rec (Sec. 2).  All three parties P0, P1, P2 are simulated on one GPU: each holds its own
+ * device copy of every share it owns, and every protocol message is a device-to-device copy that
+ * is counted in a ledger.
+ *
+ * Conventions
+ *   - All values are uint64_t, i.e. elements of Z_2^64; arithmetic wraps mod 2^64.
+ *   - A <.>-shared tensor of n elements ("sharing") is one device buffer of 6*n words, component c
+ *     at [c*n, (c+1)*n):  0: P0.[r]_1  1: P0.[r]_2  2: P1.m  3: P1.[r]_1  4: P2.m  5: P2.[r]_2,
+ *     with m = x + [r]_1 + [r]_2 (Sec. 2 Notation).  Matrices are row-major inside a component.
+ *   - Every call enqueues work on the context's stream and returns once it is enqueued, except
+ *     mpc_verify_* and mpc_reconstruct with a host output, which synchronise to read the result.
+ *   - Buffers passed in are borrowed for the duration of the enqueued work; the caller owns them.
+ *     `workspace` is caller-owned device scratch of at least mpc_workspace_size(...) bytes,
+ *     256-byte aligned; its contents are undefined after the call.
+ *   - call_id / verify_id name the PRG streams of a call (< 2^44).  Two calls must not share an
+ *     id.  Randomness is drawn from ChaCha20 (RFC 8439) keyed per party pair from the seed.
+ *   - Return value: MPC_OK or one of the MPC_ERR_* codes below; mpc_last_error() describes the
+ *     last failure.  After MPC_ERR_ABORT or MPC_ERR_VERIFY the context is aborted (security with
+ *     abort, Sec. 2 "Security Model") and every later call returns MPC_ERR_ABORT.
+ */
+#ifndef MPC3_H
+#define MPC3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPC3_ABI_VERSION 1
+
+enum {
+  MPC_OK = 0,
+  MPC_ERR_ARG = 1,        /* invalid argument (null pointer, bad id, bad enum)              */
+  MPC_ERR_SHAPE = 2,      /* invalid sizes                                                   */
+  MPC_ERR_WORKSPACE = 3,  /* workspace smaller than mpc_workspace_size()                     */
+  MPC_ERR_CUDA = 4,       /* a CUDA call failed (message in mpc_last_error)                  */
+  MPC_ERR_TIMEOUT = 5,    /* reserved: a bounded device wait expired                         */
+  MPC_ERR_VERIFY = 6,     /* the batched check found Delta != 0 (Fig. DPV outputs 0)         */
+  MPC_ERR_ABORT = 7,      /* Pi_Rec saw inconsistent messages, or the context is aborted     */
+  MPC_ERR_PENDING = 8     /* reconstruction requested while products are unverified          */
+};
+
+/* third interpolation point of Pi_Reduce (Fig. Reduce): see DESIGN.md "readings" */
+enum { MPC_REDUCE_POINT_X = 0, MPC_REDUCE_POINT_2 = 1 };
+/* local products of Pi_Inner: exact u64 CUDA-core GEMM, or exact limb-split tensor-core GEMM */
+enum { MPC_GEMM_U64 = 0, MPC_GEMM_LIMB_TC = 1 };
+/* ledger axes */
+enum { MPC_PHASE_OFFLINE = 0, MPC_PHASE_ONLINE = 1, MPC_PHASE_VERIFY = 2, MPC_NPHASE = 3 };
+enum {
+  MPC_PROTO_SHARE = 0, MPC_PROTO_MULT = 1, MPC_PROTO_INNER = 2, MPC_PROTO_TRUNC = 3,
+  MPC_PROTO_REC = 4, MPC_PROTO_VERIFY = 5, MPC_NPROTO = 6
+};
+/* host-side fault injection sites (a cheating sender corrupts one delivered element) */
+enum {
+  MPC_SITE_GAMMA2 = 0,      /* P0 -> P2 [Gamma]_2 of Pi_Mult / Pi_Inner / trunc pairs        */
+  MPC_SITE_MZ1 = 1,         /* P1 -> P2 [m_z]_1                                              */
+  MPC_SITE_MZ2 = 2,         /* P2 -> P1 [m_z]_2                                              */
+  MPC_SITE_MX_COPY_P1 = 3,  /* P0 -> P1 m of an input sharing (inconsistent replica)         */
+  MPC_SITE_REC_MSG = 4,     /* P0 -> P1 [r]_2 of Pi_Rec                                      */
+  MPC_SITE_HIGH_BIT = 5,    /* [Gamma]_2 XOR 2^63: the ring attack of Sec. 3                 */
+  MPC_NSITE = 6
+};
+/* workspace queries */
+enum {
+  MPC_OP_SHARE = 0, MPC_OP_MULT = 1, MPC_OP_MATMUL = 2, MPC_OP_VERIFY_MULT = 3,
+  MPC_OP_VERIFY_MATMUL = 4, MPC_OP_RECONSTRUCT = 5
+};
+
+typedef struct mpc_ctx mpc_ctx;
+
+typedef struct {
+  uint8_t seed[32];   /* master seed; pair keys eta01, eta02, eta12 are derived from it        */
+  int device;         /* CUDA device ordinal                                                    */
+  int reduce_mode;    /* MPC_REDUCE_POINT_X (default) or MPC_REDUCE_POINT_2                     */
+  int gemm_path;      /* MPC_GEMM_U64 or MPC_GEMM_LIMB_TC                                       */
+  void* stream;       /* cudaStream_t to run on; NULL: the library creates its own              */
+} mpc_config;
+
+/* Create a context (keys, stream, device constants, ledger).  *out is NULL on failure. */
+int mpc_create(const mpc_config* cfg, mpc_ctx** out);
+/* Destroy a context; waits for its work.  NULL is ignored. */
+void mpc_destroy(mpc_ctx* ctx);
+/* Description of the last failure of this context ("" if none).  Owned by the context. */
+const char* mpc_last_error(const mpc_ctx* ctx);
+/* Run subsequent work on `stream` (cudaStream_t). */
+int mpc_set_stream(mpc_ctx* ctx, void* stream);
+/* Wait for all enqueued work; returns MPC_ERR_CUDA on an asynchronous CUDA error. */
+int mpc_sync(mpc_ctx* ctx);
+/* MPC_OK, or MPC_ERR_ABORT once the context has aborted. */
+int mpc_status(const mpc_ctx* ctx);
+
+/* Bytes of workspace an operation needs.  op = MPC_OP_*; (a, b, c) = (n, 0, 0) for SHARE, MULT,
+ * VERIFY_MULT and RECONSTRUCT, (M, N, K) for MATMUL and VERIFY_MATMUL; trunc_bits, R_main and
+ * R_trunc as passed to the operation (R < 0: default; VERIFY_MULT takes its R in R_main).
+ * Returns -1 for invalid arguments. */
+int64_t mpc_workspace_size(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int64_t c,
+                           int trunc_bits, int R_main, int R_trunc);
+
+/* Pi_<.>^{l,0}(x) (Sec. 2, Secret sharing, owner P0): [r_x]_1 from eta01, [r_x]_2 from eta02,
+ * and P0 sends m_x = x + [r_x]_1 + [r_x]_2 to P1 and P2 (2 l bits per element).
+ * x: n plaintext words, on the host if x_on_host (copied in, stream-ordered) else on the device.
+ * xs: device sharing (6n words) written by the call. */
+int mpc_share_input(mpc_ctx* ctx, uint64_t call_id, const uint64_t* x, int x_on_host, int64_t n,
+                    uint64_t* xs, void* workspace, size_t workspace_bytes);
+
+/* Pi_Mult (Fig. MultP), elementwise z_i = x_i y_i: preprocessing ([r_z] <- Pi_[.]; P0 shares
+ * Gamma = r_x r_y + r_z, 1 l bits) and online phase (P1, P2 exchange [m_z]_j, 2 l bits).
+ * xs, ys: device sharings of n elements; zs: device sharing written by the call.  The triples
+ * stay pending until mpc_verify_mult(..., mult_call_id = call_id, ...). */
+int mpc_mult(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_t* ys, int64_t n,
+             uint64_t* zs, void* workspace, size_t workspace_bytes);
+
+/* Pi_Inner for every output of Z = X W (Fig. DPP; Sec. 4.1 views an M x N product as M N inner
+ * products of dimension K), X: M x K, W: K x N.  With trunc_bits = t >= 0 also Pi_Trunc^t
+ * (Fig. trunc): the product wire's mask is the truncation pair's r_x, and the output
+ * zout has m = m_Z >>_arith t and mask r_z = r_x >>_arith t (communication 7 l offline, 2 l
+ * online per output, Table 1).  With trunc_bits < 0, zout may equal zpre or be NULL and pq is
+ * ignored.
+ *   xs: 6 M K words; ws_: 6 K N words; zpre, zout: 6 M N words each (written);
+ *   pq: 12 M N words (written): the sharings <p> and <q> of the trunc pair's two inner products,
+ *       kept for mpc_verify_matmul. */
+int mpc_matmul(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_t* ws_,
+               int64_t M, int64_t N, int64_t K, int trunc_bits, uint64_t* zpre, uint64_t* zout,
+               uint64_t* pq, void* workspace, size_t workspace_bytes);
+
+/* Pi_MultVerify^R (Fig. PPEV) of the n triples (x_i, y_i, z_i) produced by
+ * mpc_mult(call_id = mult_call_id): Pi_Tran with a revealed challenge r, R rounds of Pi_Reduce,
+ * then Pi_InnerVerify.  R < 0 selects max(0, ceil(log2 n) - 6).  Returns MPC_OK if the check
+ * accepts, MPC_ERR_VERIFY if Delta != 0, MPC_ERR_ABORT if a Pi_Rec inside aborted.
+ * trace (device, optional): per round k = 1..R at offset (k-1)*832 the revealed zeta' (64 words),
+ * <h(0)> (6 x 64), <h(p2)> (6 x 64); then the opened Delta (64) at R*832. */
+int mpc_verify_mult(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, const uint64_t* ys,
+                    const uint64_t* zs, int64_t n, uint64_t mult_call_id, int R,
+                    void* workspace, size_t workspace_bytes, uint64_t* trace);
+
+/* Pi_BIVerify (Fig. PBDP) of the layer produced by mpc_matmul(call_id = matmul_call_id):
+ * batch 0 = the M N inner products of Z = X W, consolidated with weights r^(aN+b) and evaluated
+ * as the K-dimensional claim sum_k Xt_k Wt_k = zt (rank-1 form); batch 1 (when
+ * trunc_bits >= 0) = the 2 M N inner products of the truncation pairs, merged per output into one
+ * 64-dimensional inner product.  R_main / R_trunc < 0 select the default
+ * max(0, ceil(log2 D) - 6).  Returns as mpc_verify_mult.  trace (device, optional): batch 0 as in
+ * mpc_verify_mult, then batch 1 at offset (R_main + 1) * 832. */
+int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, const uint64_t* ws_,
+                      const uint64_t* zpre, const uint64_t* pq, int64_t M, int64_t N, int64_t K,
+                      int trunc_bits, uint64_t matmul_call_id, int R_main, int R_trunc,
+                      void* workspace, size_t workspace_bytes, uint64_t* trace);
+
+/* Pi_Rec (Sec. 2): P0 sends [r]_1 to P2 and [r]_2 to P1, P1 sends m to P0; P1 sends H([r]_1) to
+ * P2, P2 sends H(m) to P0 and H([r]_2) to P1 (H = SHA-256 Merkle root, 64 KiB leaves).  On any
+ * mismatch the call returns MPC_ERR_ABORT; otherwise out = m - [r]_1 - [r]_2 (n words, host if
+ * out_on_host, else device).  Refused with MPC_ERR_PENDING while products are unverified. */
+int mpc_reconstruct(mpc_ctx* ctx, const uint64_t* xs, int64_t n, uint64_t* out, int out_on_host,
+                    void* workspace, size_t workspace_bytes);
+
+/* Ledger: bytes[phase * MPC_NPROTO + proto] of every message sent so far, and the message
+ * count.  Hash messages count 32 bytes. */
+int mpc_ledger(const mpc_ctx* ctx, uint64_t* bytes, uint64_t* messages);
+void mpc_ledger_reset(mpc_ctx* ctx);
+
+/* Arm a one-shot fault: the next message delivered at `site` has element (index mod length)
+ * XORed with xor_mask (MPC_SITE_HIGH_BIT ignores xor_mask and uses 2^63).  Host side only; it
+ * models a cheating party and never faults the device. */
+int mpc_inject_fault(mpc_ctx* ctx, int site, uint64_t index, uint64_t xor_mask);
+
+/* Phase timers: with profiling on, the library brackets each phase of its work with CUDA events
+ * on the context's stream (no synchronisation).  mpc_profile(ctx, 1) clears and starts,
+ * mpc_profile(ctx, 0) stops; mpc_profile_read() waits for the stream and returns, per phase, the
+ * summed milliseconds and the number of intervals recorded since the last read. */
+enum {
+  MPC_PROF_SHARE = 0,              /* input sharing                                         */
+  MPC_PROF_MULT = 1,               /* Pi_Mult                                               */
+  MPC_PROF_TRUNC_PAIRS = 2,        /* Pi_Trunc preprocessing (trunc pairs and their messages) */
+  MPC_PROF_GEMM = 3,               /* the local products of Pi_Inner (one interval / party) */
+  MPC_PROF_EXCHANGE = 4,           /* Gamma and m_Z messages, reconstruction of m_Z, m >> t  */
+  MPC_PROF_VERIFY_GEMM = 5,        /* batch 0 of Pi_BIVerify (folds, rounds, InnerVerify)   */
+  MPC_PROF_TRUNC_SETUP = 6,        /* batch 1: challenge, bits, powers r^(2e), z            */
+  MPC_PROF_TRUNC_S = 7,            /* batch 1: S_{j,j'} = sum_e r^(2e) b1_j b2_j'           */
+  MPC_PROF_TRUNC_ROUNDS = 8,       /* batch 1: the rounds that fold the 64 bits per output  */
+  MPC_PROF_TRUNC_MATERIALIZE = 9,  /* batch 1: folded vectors of the remaining rounds       */
+  MPC_PROF_TRUNC_TAIL = 10,        /* batch 1: remaining rounds and Pi_InnerVerify          */
+  MPC_PROF_REC = 11,               /* Pi_Rec of outputs                                     */
+  MPC_PROF_VERIFY_MULT = 12,       /* Pi_MultVerify                                         */
+  MPC_NPROF = 13
+};
+int mpc_profile(mpc_ctx* ctx, int enable);
+int mpc_profile_read(mpc_ctx* ctx, double* ms /* MPC_NPROF */, uint64_t* count /* MPC_NPROF */);
+
+/* Number of kernel launches the library has issued in this process (all contexts). */
+uint64_t mpc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPC3_H */

@@ -1,0 +1,1255 @@
+// libmpc3: the C-ABI and the protocol driver.  Every protocol step runs in the kernels of this
+// library; the host code here only sequences them, moves messages between the three simulated
+// parties (device-to-device copies counted in the ledger) and carves the caller's workspace.
+//
+// Paper map: mpc_share_input = Pi_<.>^{l,0} (Sec. 2); mpc_mult = Pi_Mult (Fig. MultP);
+// mpc_matmul = Pi_Inner per output (Fig. DPP, Sec. 4.1) + Pi_Trunc (Fig. trunc);
+// mpc_verify_mult = Pi_MultVerify (Fig. PPEV); mpc_verify_matmul = Pi_BIVerify (Fig. PBDP);
+// both use Pi_Tran (Fig. MTP), Pi_Reduce (Fig. Reduce), Pi_InnerVerify (Fig. DPV);
+// mpc_reconstruct = Pi_Rec (Sec. 2).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "mpc3.h"
+#include "kernels.h"
+
+using namespace mpc3;
+
+// ---- kernel launch accounting: every launcher called from this file is counted ----------------
+namespace {
+unsigned long long g_launches = 0;
+template <class F, class... A>
+inline void counted(int k, F f, A... a) {
+  g_launches += (unsigned long long)k;
+  f(a...);
+}
+}  // namespace
+#define gemm_u64(...) counted(1, mpc3::gemm_u64, __VA_ARGS__)
+#define launch_share_input(...) counted(1, mpc3::launch_share_input, __VA_ARGS__)
+#define launch_fill_masks(...) counted(1, mpc3::launch_fill_masks, __VA_ARGS__)
+#define launch_mult_offline(...) counted(1, mpc3::launch_mult_offline, __VA_ARGS__)
+#define launch_mult_online(...) counted(1, mpc3::launch_mult_online, __VA_ARGS__)
+#define launch_exchange_finish(...) counted(1, mpc3::launch_exchange_finish, __VA_ARGS__)
+#define launch_trunc_p0(...) counted(1, mpc3::launch_trunc_p0, __VA_ARGS__)
+#define launch_trunc_finish(...) counted(1, mpc3::launch_trunc_finish, __VA_ARGS__)
+#define launch_xor_one(...) counted(1, mpc3::launch_xor_one, __VA_ARGS__)
+#define launch_open_p1(...) counted(1, mpc3::launch_open_p1, __VA_ARGS__)
+#define launch_hash_u64(...) counted(2, mpc3::launch_hash_u64, __VA_ARGS__)
+#define launch_digest_check(...) counted(1, mpc3::launch_digest_check, __VA_ARGS__)
+#define launch_gr_random_shared(...) counted(1, mpc3::launch_gr_random_shared, __VA_ARGS__)
+#define launch_gr_powers(...) counted(1, mpc3::launch_gr_powers, __VA_ARGS__)
+#define launch_gr_mul1(...) counted(1, mpc3::launch_gr_mul1, __VA_ARGS__)
+#define launch_gr_lincomb(...) counted(1, mpc3::launch_gr_lincomb, __VA_ARGS__)
+#define launch_gr_mulmat2(...) counted(1, mpc3::launch_gr_mulmat2, __VA_ARGS__)
+#define launch_gr_inverses(...) counted(1, mpc3::launch_gr_inverses, __VA_ARGS__)
+#define launch_gr_lagrange(...) counted(1, mpc3::launch_gr_lagrange, __VA_ARGS__)
+#define launch_gr_fold_reduce(...) counted(1, mpc3::launch_gr_fold_reduce, __VA_ARGS__)
+#define launch_gr_combine_z(...) counted(1, mpc3::launch_gr_combine_z, __VA_ARGS__)
+#define launch_gr_scale_rows(...) counted(1, mpc3::launch_gr_scale_rows, __VA_ARGS__)
+#define launch_gr_lift(...) counted(1, mpc3::launch_gr_lift, __VA_ARGS__)
+#define launch_neg_copy(...) counted(1, mpc3::launch_neg_copy, __VA_ARGS__)
+#define launch_gr_check_zero(...) counted(1, mpc3::launch_gr_check_zero, __VA_ARGS__)
+#define launch_trunc_u(...) counted(1, mpc3::launch_trunc_u, __VA_ARGS__)
+#define launch_trunc_round_h(...) counted(1, mpc3::launch_trunc_round_h, __VA_ARGS__)
+#define launch_trunc_update_vw(...) counted(1, mpc3::launch_trunc_update_vw, __VA_ARGS__)
+#define launch_trunc_materialize(...) counted(1, mpc3::launch_trunc_materialize, __VA_ARGS__)
+#define launch_gr_rec1(...) counted(1, mpc3::launch_gr_rec1, __VA_ARGS__)
+#define launch_gr_inner_finish_all(...) counted(1, mpc3::launch_gr_inner_finish_all, __VA_ARGS__)
+#define launch_gr_quad_combine(...) counted(1, mpc3::launch_gr_quad_combine, __VA_ARGS__)
+#define launch_mode_consts(...) counted(1, mpc3::launch_mode_consts, __VA_ARGS__)
+#define launch_prf_words(...) counted(1, mpc3::launch_prf_words, __VA_ARGS__)
+
+namespace {
+
+constexpr u32 ST_ABORT = 1u;    // a Pi_Rec check failed
+constexpr u32 ST_VERIFY = 2u;   // Delta != 0
+
+// device constants block (words)
+constexpr int CST_INV = 0;      // 192: x^-1, (1-x)^-1, (x(x-1))^-1
+constexpr int CST_LAM = 192;    // 128: 1 - p2, p2
+constexpr int CST_ONE = 320;    // 64: the element 1
+constexpr int CST_MONE = 384;   // 64: the element -1
+constexpr int CST_WORDS = 448;
+
+constexpr int TRACE_ROUND = 832;  // words per round in a verification trace
+
+struct Arena {
+  char* base;
+  size_t cap;
+  size_t off = 0;
+  bool dry;
+  template <class T>
+  T* take(long long count) {
+    const size_t bytes = ((size_t)std::max<long long>(count, 1) * sizeof(T) + 255) & ~size_t(255);
+    T* p = dry ? nullptr : reinterpret_cast<T*>(base + off);
+    off += bytes;
+    return p;
+  }
+  bool ok() const { return dry || off <= cap; }
+};
+
+struct Fault {
+  bool armed = false;
+  u64 index = 0;
+  u64 mask = 0;
+};
+
+__global__ void k_derive_keys(Key master, u32* out) {
+  // eta_{0,1}, eta_{0,2}, eta_{1,2}: first 32 bytes of ChaCha20(master, counter 0,
+  // nonce (0x0059454B, pair, 0)), pair = 1, 2, 3
+  const int pair = threadIdx.x + 1;
+  if (pair > 3) return;
+  u32 o[16];
+  chacha_block(master, 0u, 0x0059454Bu, (u32)pair, 0u, o);
+  for (int i = 0; i < 8; ++i) out[(pair - 1) * 8 + i] = o[i];
+}
+
+__global__ void k_init_consts(int mode, u64* cst) {
+  const int t = threadIdx.x;
+  cst[CST_ONE + t] = (t == 0) ? 1ull : 0ull;
+  cst[CST_MONE + t] = (t == 0) ? ~0ull : 0ull;
+}
+
+inline long long ceil_log2(long long v) {
+  long long r = 0;
+  while ((1ll << r) < v) ++r;
+  return r;
+}
+inline int default_R(long long D) { return D > 1 ? (int)std::max<long long>(0, ceil_log2(D) - 6) : 0; }
+
+}  // namespace
+
+struct mpc_ctx {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  Key k01{}, k02{}, k12{};
+  int reduce_mode = MPC_REDUCE_POINT_X;
+  int gemm_path = MPC_GEMM_U64;
+  u64* cst = nullptr;
+  u32* status = nullptr;
+  u64 ledger[MPC_NPHASE][MPC_NPROTO] = {};
+  u64 nmsg = 0;
+  Fault fault[MPC_NSITE];
+  bool aborted = false;
+  std::set<u64> pending;   // (call_id << 1) | kind, kind 0 = mult, 1 = matmul
+  std::string err;
+  // phase timers (CUDA events on the context's stream), enabled by mpc_profile()
+  struct ProfRec {
+    int id;
+    cudaEvent_t a, b;
+  };
+  bool prof = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+};
+
+namespace {
+
+int fail(mpc_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_check(mpc_ctx* c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, MPC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return MPC_OK;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(ctx, MPC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+cudaEvent_t prof_event(mpc_ctx* c) {
+  if (c->pool_used == c->pool.size()) {
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    c->pool.push_back(e);
+  }
+  return c->pool[c->pool_used++];
+}
+
+// Times the enclosed stream work as phase `id` when profiling is on.
+struct Phase {
+  mpc_ctx* c;
+  int id;
+  cudaEvent_t a = nullptr;
+  Phase(mpc_ctx* c_, int id_) : c(c_), id(id_) {
+    if (c->prof) {
+      a = prof_event(c);
+      cudaEventRecord(a, c->st);
+    }
+  }
+  ~Phase() {
+    if (c->prof) {
+      cudaEvent_t b = prof_event(c);
+      cudaEventRecord(b, c->st);
+      c->recs.push_back({id, a, b});
+    }
+  }
+};
+
+int guard(mpc_ctx* ctx) {
+  if (!ctx) return MPC_ERR_ARG;
+  if (ctx->aborted) return fail(ctx, MPC_ERR_ABORT, "context aborted");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return fail(ctx, MPC_ERR_CUDA, cudaGetErrorString(e));
+  return MPC_OK;
+}
+
+bool id_ok(u64 id) { return id < (1ull << 44); }
+
+// ---- messages -----------------------------------------------------------------------------------
+void apply_fault(mpc_ctx* ctx, int site, u64* dst, long long n) {
+  if (site == MPC_SITE_GAMMA2 && ctx->fault[MPC_SITE_HIGH_BIT].armed) {
+    ctx->fault[MPC_SITE_HIGH_BIT].armed = false;
+    ctx->fault[MPC_SITE_GAMMA2] = {true, ctx->fault[MPC_SITE_HIGH_BIT].index, 1ull << 63};
+  }
+  Fault& f = ctx->fault[site];
+  if (f.armed && n > 0) {
+    launch_xor_one(ctx->st, dst + (f.index % (u64)n), f.mask);
+    f.armed = false;
+  }
+}
+
+int deliver(mpc_ctx* ctx, int phase, int proto, const u64* src, u64* dst, long long n, int site) {
+  if (n > 0) CK(cudaMemcpyAsync(dst, src, (size_t)n * 8, cudaMemcpyDeviceToDevice, ctx->st));
+  ctx->ledger[phase][proto] += (u64)n * 8;
+  ctx->nmsg += 1;
+  if (site >= 0) apply_fault(ctx, site, dst, n);
+  return MPC_OK;
+}
+
+void count_msgs(mpc_ctx* ctx, int phase, int proto, int count, u64 bytes_each) {
+  ctx->ledger[phase][proto] += (u64)count * bytes_each;
+  ctx->nmsg += (u64)count;
+}
+
+int read_status(mpc_ctx* ctx, u32* out) {
+  CK(cudaMemcpyAsync(out, ctx->status, sizeof(u32), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return MPC_OK;
+}
+
+// ---- GEMM helpers -------------------------------------------------------------------------------
+Opnd op(const u64* p0, long long ld, int trans = 0, const u64* p1 = nullptr, u64 s1 = 1,
+        u64 scale = 1) {
+  Opnd o;
+  o.p0 = p0; o.p1 = p1; o.ld = ld; o.s1 = s1; o.scale = scale; o.trans = trans;
+  return o;
+}
+
+Epi epi_store(u64* out, long long ldc) {
+  Epi e;
+  std::memset(&e, 0, sizeof(e));
+  e.atomic = 0; e.acc_sign = 1; e.out = out; e.ldc = ldc;
+  return e;
+}
+
+Epi epi_atomic(u64* out, long long ldc, u64 sign = 1) {
+  Epi e = epi_store(out, ldc);
+  e.atomic = 1;
+  e.acc_sign = sign;
+  return e;
+}
+
+int nsplit_for(long long K) { return (int)std::min<long long>(1024, std::max<long long>(1, K / 512)); }
+
+// out (atomic, 64x64) += sign * sum_i U_i (x) V_i with U = U0 + su U1, V = V0 + sv V1.
+void gram(mpc_ctx* ctx, u64* P, const u64* U0, const u64* U1, u64 su, long long ldu, const u64* V0,
+          const u64* V1, u64 sv, long long ldv, long long count, u64 sign) {
+  u64 us = 1, vs = 1;
+  if (!U0) { U0 = U1; U1 = nullptr; us = su; }
+  if (!V0) { V0 = V1; V1 = nullptr; vs = sv; }
+  if (!U0 || !V0 || count <= 0) return;
+  GemmTerm T;
+  T.A = op(U0, ldu, 1, U1, su, us);
+  T.B = op(V0, ldv, 0, V1, sv, vs);
+  gemm_u64(ctx->st, 64, 64, count, 1, &T, epi_atomic(P, 64, sign), nsplit_for(count));
+}
+
+// A view of a <.>^{l[x]}-shared vector: component pointers (null = identically zero), row stride.
+struct View {
+  const u64* c[6];
+  long long ld;
+};
+
+// Party sums of a secure GR inner product sum_i u_i v_i (Sec. 2 inner product over GR):
+//   S0 = sum r_u r_v (P0), S1 = -sum (m_u [r_v]_1 + m_v [r_u]_1) (P1),
+//   S2 = sum m_u (m_v - [r_v]_2) - m_v [r_u]_2 (P2).  Pmat: 3 x 4096 scratch; S: 3 x 64 out.
+int party_sums(mpc_ctx* ctx, const View& u, const View& v, long long count, u64* Pmat, u64* S) {
+  CK(cudaMemsetAsync(Pmat, 0, 3 * 4096 * 8, ctx->st));
+  const u64 M1 = ~0ull;  // -1
+  gram(ctx, Pmat, u.c[0], u.c[1], 1, u.ld, v.c[0], v.c[1], 1, v.ld, count, 1);
+  gram(ctx, Pmat + 4096, u.c[2], nullptr, 1, u.ld, v.c[3], nullptr, 1, v.ld, count, M1);
+  gram(ctx, Pmat + 4096, v.c[2], nullptr, 1, v.ld, u.c[3], nullptr, 1, u.ld, count, M1);
+  gram(ctx, Pmat + 8192, u.c[4], nullptr, 1, u.ld, v.c[4], v.c[5], M1, v.ld, count, 1);
+  gram(ctx, Pmat + 8192, v.c[4], nullptr, 1, v.ld, u.c[5], nullptr, 1, u.ld, count, M1);
+  launch_gr_fold_reduce(ctx->st, Pmat, 3, S);
+  return cuda_check(ctx, "party_sums");
+}
+
+// Secure GR inner-product finish (P0's Gamma, P1/P2 cross terms, one exchange); 3 messages.
+void inner_finish(mpc_ctx* ctx, const u64* S, u32 purpose, u64 obj, u64* h6) {
+  launch_gr_inner_finish_all(ctx->st, S, ctx->k01, ctx->k02, purpose, obj, h6);
+  count_msgs(ctx, MPC_PHASE_VERIFY, MPC_PROTO_VERIFY, 3, 512);
+}
+
+// Pi_Rec of one shared GR element (3 shares + 3 hashes); an armed REC_MSG fault corrupts the
+// P0 -> P1 share, as for any other Pi_Rec.
+void rec1(mpc_ctx* ctx, const u64* s6, u64* out) {
+  u64 mask = 0;
+  int idx = -1;
+  Fault& f = ctx->fault[MPC_SITE_REC_MSG];
+  if (f.armed) {
+    mask = f.mask;
+    idx = (int)(f.index % 64);
+    f.armed = false;
+  }
+  launch_gr_rec1(ctx->st, s6, mask, idx, out, ctx->status, ST_ABORT);
+  count_msgs(ctx, MPC_PHASE_VERIFY, MPC_PROTO_VERIFY, 3, 512);
+  count_msgs(ctx, MPC_PHASE_VERIFY, MPC_PROTO_VERIFY, 3, 32);
+}
+
+// <v> random GR element, revealed with Pi_Rec.
+void reveal(mpc_ctx* ctx, u32 purpose, u64 obj, u64* tmp6, u64* out) {
+  launch_gr_random_shared(ctx->st, 1, ctx->k01, ctx->k02, ctx->k12, purpose, obj, tmp6);
+  rec1(ctx, tmp6, out);
+}
+
+// ---- verification state ---------------------------------------------------------------------
+struct Small {   // per-verification small scratch (all device, from the workspace)
+  u64* Pmat;     // 4 x 3 x 4096
+  u64* S;        // 5 x 192: S00, S01, S10, S11, Sh2
+  u64* h0;       // 384
+  u64* h2;       // 384
+  u64* z[2];     // 384 each
+  u64* coef;     // 448
+  u64* zp;       // 64
+  u64* r;        // 64
+  u64* tmp6;     // 384
+  u64* MM;       // 128 x 64
+  u64* MA;       // 5 x 4096 (multiplication matrices of alpha components)
+  u64* alpha;    // 384
+  u64* aux;      // 4 x 64
+  u64* Sfull;    // 192
+  u64* zinit;    // 384: the claim entering the first round (never round scratch)
+};
+
+Small plan_small(Arena& a) {
+  Small s;
+  s.Pmat = a.take<u64>(4 * 3 * 4096);
+  s.S = a.take<u64>(5 * 192);
+  s.h0 = a.take<u64>(384);
+  s.h2 = a.take<u64>(384);
+  s.z[0] = a.take<u64>(384);
+  s.z[1] = a.take<u64>(384);
+  s.coef = a.take<u64>(448);
+  s.zp = a.take<u64>(64);
+  s.r = a.take<u64>(64);
+  s.tmp6 = a.take<u64>(384);
+  s.MM = a.take<u64>(128 * 64);
+  s.MA = a.take<u64>(5 * 4096);
+  s.alpha = a.take<u64>(384);
+  s.aux = a.take<u64>(4 * 64);
+  s.Sfull = a.take<u64>(192);
+  s.zinit = a.take<u64>(384);
+  return s;
+}
+
+// A dense claim: x, y vectors of D GR elements (components may be null), claimed z (6 x 64).
+struct Vec {
+  u64* c[6];
+};
+
+struct Dense {
+  Vec x[2], y[2];     // ping-pong buffers, capacity cap0 (index 0) and cap1 (index 1)
+  long long cap[2];
+  int cur = 0;
+};
+
+// Inner-verify buffers for a final dimension D.
+struct IVBuf {
+  u64* xp;    // 6 x (D+1) x 64
+  u64* yy;    // 6 x (D+1) x 64
+  u64* g2o;   // (D+1) x 64
+  u64* g2i;
+  u64* p1o;
+  u64* p2o;
+  u64* p1i;
+  u64* p2i;
+  u64* zero;  // D x 64 zeros
+  u64* delta; // 64
+};
+
+IVBuf plan_iv(Arena& a, long long D) {
+  IVBuf b;
+  const long long w = (D + 1) * 64;
+  b.xp = a.take<u64>(6 * w);
+  b.yy = a.take<u64>(6 * w);
+  b.g2o = a.take<u64>(w);
+  b.g2i = a.take<u64>(w);
+  b.p1o = a.take<u64>(w);
+  b.p2o = a.take<u64>(w);
+  b.p1i = a.take<u64>(w);
+  b.p2i = a.take<u64>(w);
+  b.zero = a.take<u64>(w);
+  b.delta = a.take<u64>(64);
+  return b;
+}
+
+void trace_round(mpc_ctx* ctx, u64* trace, int k, const Small& s) {
+  if (!trace) return;
+  u64* t = trace + (long long)(k - 1) * TRACE_ROUND;
+  cudaMemcpyAsync(t, s.zp, 64 * 8, cudaMemcpyDeviceToDevice, ctx->st);
+  cudaMemcpyAsync(t + 64, s.h0, 384 * 8, cudaMemcpyDeviceToDevice, ctx->st);
+  cudaMemcpyAsync(t + 448, s.h2, 384 * 8, cudaMemcpyDeviceToDevice, ctx->st);
+}
+
+// One Pi_Reduce round on a dense claim (Fig. Reduce).  x, y: current vectors (D elements, with
+// capacity for D+1), z: current claim; writes the folded vectors into xo, yo and z into zo.
+int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, const Vec& y,
+                       long long D, const u64* z, Vec& xo, Vec& yo, u64* zo, const Small& s,
+                       u64* trace) {
+  cudaStream_t st = ctx->st;
+  const long long Dh = (D + 1) / 2;
+  if (D & 1) {
+    for (int c = 0; c < 6; ++c) {
+      if (x.c[c]) CK(cudaMemsetAsync(x.c[c] + D * 64, 0, 512, st));
+      if (y.c[c]) CK(cudaMemsetAsync(y.c[c] + D * 64, 0, 512, st));
+    }
+  }
+  View f[2], g[2];
+  for (int a = 0; a < 2; ++a) {
+    for (int c = 0; c < 6; ++c) {
+      f[a].c[c] = x.c[c] ? x.c[c] + 64 * a : nullptr;
+      g[a].c[c] = y.c[c] ? y.c[c] + 64 * a : nullptr;
+    }
+    f[a].ld = 128;
+    g[a].ld = 128;
+  }
+  u64* S00 = s.S;
+  u64* S01 = s.S + 192;
+  u64* S10 = s.S + 384;
+  u64* S11 = s.S + 576;
+  u64* Sh2 = s.S + 768;
+  int rc;
+  if ((rc = party_sums(ctx, f[0], g[0], Dh, s.Pmat, S00))) return rc;
+  if ((rc = party_sums(ctx, f[0], g[1], Dh, s.Pmat + 3 * 4096, S01))) return rc;
+  if ((rc = party_sums(ctx, f[1], g[0], Dh, s.Pmat + 6 * 4096, S10))) return rc;
+  if ((rc = party_sums(ctx, f[1], g[1], Dh, s.Pmat + 9 * 4096, S11))) return rc;
+  launch_gr_quad_combine(st, ctx->cst + CST_LAM, S00, S01, S10, S11, Sh2);
+  const u64 obj = make_obj(vid, batch, (u32)k);
+  inner_finish(ctx, S00, P_VER_H0, obj, s.h0);
+  inner_finish(ctx, Sh2, P_VER_H2, obj, s.h2);
+  reveal(ctx, P_VER_ZETA, obj, s.tmp6, s.zp);
+  launch_gr_lagrange(st, s.zp, ctx->reduce_mode, ctx->cst + CST_INV, s.coef);
+  launch_gr_combine_z(st, s.coef, s.h0, s.h2, z, zo);
+  launch_gr_mulmat2(st, s.coef + 384, s.coef, s.MM);   // [M_{1-zeta}; M_zeta]
+  for (int c = 0; c < 6; ++c) {
+    for (int side = 0; side < 2; ++side) {
+      const u64* in = side ? y.c[c] : x.c[c];
+      u64* out = side ? yo.c[c] : xo.c[c];
+      if (!in) continue;
+      GemmTerm T;
+      T.A = op(in, 128);
+      T.B = op(s.MM, 64);
+      gemm_u64(st, Dh, 64, 128, 1, &T, epi_store(out, 64), 1);
+    }
+  }
+  trace_round(ctx, trace, k, s);
+  return cuda_check(ctx, "reduce_round");
+}
+
+// Pi_InnerVerify (Fig. DPV) on a dense claim of dimension D.
+int inner_verify_dense(mpc_ctx* ctx, u64 vid, u32 batch, const Vec& x, const Vec& y, long long D,
+                       const u64* z, const Small& s, const IVBuf& b, u64* trace, int R) {
+  cudaStream_t st = ctx->st;
+  const u64 obj = make_obj(vid, batch, 0);
+  const long long w = (D + 1) * 64;
+  const u64 M1 = ~0ull;
+  // alpha random, not revealed
+  launch_gr_random_shared(st, 1, ctx->k01, ctx->k02, ctx->k12, P_VER_ALPHA, obj, s.alpha);
+  const u64* a = s.alpha;
+  // multiplication matrices: r_a = a0 + a1 (P0), a3 (P1's [r]_1), a2 (P1's m),
+  // a4 - a5 (P2's m - [r]_2), a4 (P2's m)
+  u64* ra = s.aux;
+  u64* d45 = s.aux + 64;
+  launch_gr_lincomb(st, ctx->cst + CST_ONE, a, ctx->cst + CST_ONE, a + 64, ra);
+  launch_gr_lincomb(st, ctx->cst + CST_ONE, a + 256, ctx->cst + CST_MONE, a + 320, d45);
+  launch_gr_mulmat2(st, ra, a + 192, s.MA);            // MA[0] = M(r_a), MA[1] = M(a3)
+  launch_gr_mulmat2(st, a + 128, d45, s.MA + 8192);    // MA[2] = M(a2), MA[3] = M(a4 - a5)
+  launch_gr_mulmat2(st, a + 256, nullptr, s.MA + 16384);  // MA[4] = M(a4)
+  CK(cudaMemsetAsync(b.zero, 0, (size_t)w * 8, st));
+  auto comp = [&](int c) -> const u64* { return x.c[c] ? x.c[c] : b.zero; };
+  // masks of x' = x alpha (words i*64 + c of the (P_VER_XA, R1/R2) streams)
+  launch_fill_masks(st, w, ctx->k01, ctx->k02, P_VER_XA, obj, b.xp);
+  {  // P0: Gamma_i = r_{x_i} r_a + [r_{x'_i}]_1 + [r_{x'_i}]_2, message [Gamma]_2 = Gamma - [Gamma]_1
+    GemmTerm T;
+    T.A = op(comp(0), 64, 0, x.c[1], 1);
+    T.B = op(s.MA, 64);
+    Epi e = epi_store(b.g2o, 64);
+    e.add0 = b.xp;
+    e.add1 = b.xp + w;
+    e.prf_sign = M1;
+    e.key = ctx->k01;
+    e.tag = make_tag(P_VER_XA, C_G1);
+    e.obj = obj;
+    gemm_u64(st, D, 64, 64, 1, &T, e, 1);
+  }
+  int rc;
+  if ((rc = deliver(ctx, MPC_PHASE_VERIFY, MPC_PROTO_VERIFY, b.g2o, b.g2i, D * 64, -1))) return rc;
+  {  // P1: [m]_1 = -(m_x [r_a]_1 + m_a [r_x]_1) + [Gamma]_1
+    GemmTerm T[2];
+    T[0].A = op(comp(2), 64);
+    T[0].B = op(s.MA + 4096, 64);
+    T[1].A = op(comp(3), 64);
+    T[1].B = op(s.MA + 8192, 64);
+    Epi e = epi_store(b.p1o, 64);
+    e.acc_sign = M1;
+    e.prf_sign = 1;
+    e.key = ctx->k01;
+    e.tag = make_tag(P_VER_XA, C_G1);
+    e.obj = obj;
+    gemm_u64(st, D, 64, 64, 2, T, e, 1);
+  }
+  {  // P2: [m]_2 = m_x (m_a - [r_a]_2) - [r_x]_2 m_a + [Gamma]_2
+    GemmTerm T[2];
+    T[0].A = op(comp(4), 64);
+    T[0].B = op(s.MA + 12288, 64);
+    T[1].A = op(comp(5), 64, 0, nullptr, 1, M1);
+    T[1].B = op(s.MA + 16384, 64);
+    Epi e = epi_store(b.p2o, 64);
+    e.add0 = b.g2i;
+    gemm_u64(st, D, 64, 64, 2, T, e, 1);
+  }
+  if ((rc = deliver(ctx, MPC_PHASE_VERIFY, MPC_PROTO_VERIFY, b.p1o, b.p2i, D * 64, -1))) return rc;
+  if ((rc = deliver(ctx, MPC_PHASE_VERIFY, MPC_PROTO_VERIFY, b.p2o, b.p1i, D * 64, -1))) return rc;
+  launch_exchange_finish(st, w, b.p1o, b.p1i, b.p2o, b.p2i, b.xp, -1, nullptr);
+  // x'' = [x'_0 .. x'_{D-1}, alpha]; y'' = [y_0 .. y_{D-1}, -z]
+  for (int c = 0; c < 6; ++c) {
+    CK(cudaMemcpyAsync(b.xp + c * w + D * 64, a + c * 64, 512, cudaMemcpyDeviceToDevice, st));
+    if (y.c[c])
+      CK(cudaMemcpyAsync(b.yy + c * w, y.c[c], (size_t)D * 512, cudaMemcpyDeviceToDevice, st));
+    else
+      CK(cudaMemsetAsync(b.yy + c * w, 0, (size_t)D * 512, st));
+    launch_neg_copy(st, z + c * 64, 64, b.yy + c * w + D * 64);
+  }
+  View u, v;
+  for (int c = 0; c < 6; ++c) {
+    u.c[c] = b.xp + c * w;
+    v.c[c] = b.yy + c * w;
+  }
+  u.ld = 64;
+  v.ld = 64;
+  if ((rc = party_sums(ctx, u, v, D + 1, s.Pmat, s.Sfull))) return rc;
+  inner_finish(ctx, s.Sfull, P_VER_DELTA, obj, s.tmp6);
+  rec1(ctx, s.tmp6, b.delta);
+  launch_gr_check_zero(st, b.delta, ctx->status, ST_VERIFY);
+  if (trace)
+    CK(cudaMemcpyAsync(trace + (long long)R * TRACE_ROUND, b.delta, 512, cudaMemcpyDeviceToDevice, st));
+  return cuda_check(ctx, "inner_verify");
+}
+
+// Dense rounds k = k0..R followed by Pi_InnerVerify.
+int run_dense(mpc_ctx* ctx, u64 vid, u32 batch, Dense& dv, long long D, const u64* z0, int k0,
+              int R, const Small& s, const IVBuf& ivb, u64* trace) {
+  int rc;
+  const u64* z = z0;
+  int zi = 0;
+  for (int k = k0; k <= R; ++k) {
+    Vec& x = dv.x[dv.cur];
+    Vec& y = dv.y[dv.cur];
+    Vec& xo = dv.x[dv.cur ^ 1];
+    Vec& yo = dv.y[dv.cur ^ 1];
+    u64* zo = s.z[zi];
+    if ((rc = reduce_round_dense(ctx, vid, batch, k, x, y, D, z, xo, yo, zo, s, trace))) return rc;
+    z = zo;
+    zi ^= 1;
+    dv.cur ^= 1;
+    D = (D + 1) / 2;
+  }
+  return inner_verify_dense(ctx, vid, batch, dv.x[dv.cur], dv.y[dv.cur], D, z, s, ivb, trace, R);
+}
+
+long long dim_after(long long D, int R) {
+  for (int k = 0; k < R; ++k) D = (D + 1) / 2;
+  return D;
+}
+
+// Allocate ping-pong vectors for a dense claim of dimension D over the present components.
+Dense plan_dense(Arena& a, long long D, const bool xc[6], const bool yc[6]) {
+  Dense d;
+  d.cap[0] = D + 1;
+  d.cap[1] = (D + 1) / 2 + 1;
+  for (int i = 0; i < 2; ++i)
+    for (int c = 0; c < 6; ++c) {
+      d.x[i].c[c] = xc[c] ? a.take<u64>(d.cap[i] * 64) : nullptr;
+      d.y[i].c[c] = yc[c] ? a.take<u64>(d.cap[i] * 64) : nullptr;
+    }
+  return d;
+}
+
+int finish_verify(mpc_ctx* ctx, u64 pend_key) {
+  u32 stv = 0;
+  int rc = read_status(ctx, &stv);
+  if (rc) return rc;
+  ctx->pending.erase(pend_key);
+  if (stv & ST_ABORT) {
+    ctx->aborted = true;
+    return fail(ctx, MPC_ERR_ABORT, "Pi_Rec: inconsistent messages");
+  }
+  if (stv & ST_VERIFY) {
+    ctx->aborted = true;
+    return fail(ctx, MPC_ERR_VERIFY, "verification failed: Delta != 0");
+  }
+  return MPC_OK;
+}
+
+// ---- plans ----------------------------------------------------------------------------------
+struct MatmulPlan {
+  u64 *g2o, *g2i, *mz1, *mz2, *mz1i, *mz2i;
+  u64 *gp2, *gq2, *gp2i, *gq2i, *mp1, *mq1, *mpi1, *mqi1, *mpi2, *mqi2;
+};
+
+MatmulPlan plan_matmul(Arena& a, long long E, bool trunc) {
+  MatmulPlan p{};
+  p.g2o = a.take<u64>(E); p.g2i = a.take<u64>(E);
+  p.mz1 = a.take<u64>(E); p.mz2 = a.take<u64>(E);
+  p.mz1i = a.take<u64>(E); p.mz2i = a.take<u64>(E);
+  if (trunc) {
+    p.gp2 = a.take<u64>(E); p.gq2 = a.take<u64>(E);
+    p.gp2i = a.take<u64>(E); p.gq2i = a.take<u64>(E);
+    p.mp1 = a.take<u64>(E); p.mq1 = a.take<u64>(E);
+    p.mpi1 = a.take<u64>(E); p.mqi1 = a.take<u64>(E);
+    p.mpi2 = a.take<u64>(E); p.mqi2 = a.take<u64>(E);
+  }
+  return p;
+}
+
+struct RecPlan {
+  u64 *in_p2_r1, *in_p1_r2, *in_p0_m, *out_dev;
+  u32* hs[6];
+  u32* dg;   // 6 x 8
+};
+
+RecPlan plan_rec(Arena& a, long long n, bool need_out) {
+  RecPlan p{};
+  p.in_p2_r1 = a.take<u64>(n);
+  p.in_p1_r2 = a.take<u64>(n);
+  p.in_p0_m = a.take<u64>(n);
+  for (int i = 0; i < 6; ++i) p.hs[i] = a.take<u32>((long long)hash_scratch_words(n));
+  p.dg = a.take<u32>(48);
+  p.out_dev = need_out ? a.take<u64>(n) : nullptr;
+  return p;
+}
+
+struct VMultPlan {
+  Small s;
+  u64* pw;
+  Dense dv;
+  IVBuf iv;
+  int R;
+};
+
+VMultPlan plan_vmult(Arena& a, long long n, int R) {
+  VMultPlan p;
+  p.R = R < 0 ? default_R(n) : R;
+  p.s = plan_small(a);
+  p.pw = a.take<u64>(n * 64);
+  const bool all[6] = {true, true, true, true, true, true};
+  p.dv = plan_dense(a, n, all, all);
+  p.iv = plan_iv(a, dim_after(n, p.R));
+  return p;
+}
+
+struct VMatPlan {
+  Small s;
+  u64 *Q, *P, *T, *Pz;
+  Dense dv;
+  IVBuf iv;
+  int R0;
+  // truncation batch
+  bool trunc;
+  int R1, kd;
+  long long Dt;
+  u64 *b1, *b2, *Rtab, *S, *Zpq, *V, *W, *hsum, *S3, *zt;
+  Dense dt;
+  IVBuf ivt;
+};
+
+VMatPlan plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R0, int R1) {
+  VMatPlan p;
+  p.R0 = R0 < 0 ? default_R(K) : R0;
+  p.s = plan_small(a);
+  p.Q = a.take<u64>(N * 64);
+  p.P = a.take<u64>(M * 64);
+  p.T = a.take<u64>(6 * M * 64);
+  p.Pz = a.take<u64>(6 * 4096);
+  const bool all[6] = {true, true, true, true, true, true};
+  p.dv = plan_dense(a, K, all, all);
+  p.iv = plan_iv(a, dim_after(K, p.R0));
+  p.trunc = t >= 0;
+  if (p.trunc) {
+    const long long E = M * N;
+    const long long D0 = 64 * E;
+    p.R1 = R1 < 0 ? default_R(D0) : R1;
+    p.kd = std::min(p.R1, 6);
+    p.Dt = E * (64 >> p.kd);
+    p.b1 = a.take<u64>(E);
+    p.b2 = a.take<u64>(E);
+    p.Rtab = a.take<u64>(E * 64);
+    p.S = a.take<u64>(4096 * 64);
+    p.Zpq = a.take<u64>(12 * 64);
+    p.V = a.take<u64>(4096);
+    p.W = a.take<u64>(4096);
+    p.hsum = a.take<u64>(128);
+    p.S3 = a.take<u64>(2 * 192);
+    p.zt = a.take<u64>(2 * 384);
+    const bool xc[6] = {true, false, false, true, false, false};
+    const bool yc[6] = {false, true, false, false, false, true};
+    p.dt = plan_dense(a, p.Dt, xc, yc);
+    p.ivt = plan_iv(a, dim_after(p.Dt, p.R1 - p.kd));
+  }
+  return p;
+}
+
+}  // namespace
+
+// =================================================================================================
+// C-ABI
+// =================================================================================================
+extern "C" {
+
+int mpc_create(const mpc_config* cfg, mpc_ctx** out) {
+  if (!out) return MPC_ERR_ARG;
+  *out = nullptr;
+  if (!cfg) return MPC_ERR_ARG;
+  if (cfg->reduce_mode != MPC_REDUCE_POINT_X && cfg->reduce_mode != MPC_REDUCE_POINT_2)
+    return MPC_ERR_ARG;
+  if (cfg->gemm_path != MPC_GEMM_U64 && cfg->gemm_path != MPC_GEMM_LIMB_TC) return MPC_ERR_ARG;
+  mpc_ctx* ctx = new mpc_ctx();
+  ctx->device = cfg->device;
+  ctx->reduce_mode = cfg->reduce_mode;
+  ctx->gemm_path = cfg->gemm_path;
+  auto bail = [&](const char* what, cudaError_t e) {
+    std::fprintf(stderr, "mpc_create: %s: %s\n", what, cudaGetErrorString(e));
+    if (ctx->cst) cudaFree(ctx->cst);
+    if (ctx->own_stream && ctx->st) cudaStreamDestroy(ctx->st);
+    delete ctx;
+    return MPC_ERR_CUDA;
+  };
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return bail("cudaSetDevice", e);
+  if (cfg->stream) {
+    ctx->st = (cudaStream_t)cfg->stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail("cudaStreamCreate", e);
+    ctx->own_stream = true;
+  }
+  // constants block + status word + key staging
+  e = cudaMalloc(&ctx->cst, CST_WORDS * 8 + 256 + 256);
+  if (e != cudaSuccess) return bail("cudaMalloc", e);
+  ctx->status = reinterpret_cast<u32*>(reinterpret_cast<char*>(ctx->cst) + CST_WORDS * 8);
+  u32* keys_dev = reinterpret_cast<u32*>(reinterpret_cast<char*>(ctx->cst) + CST_WORDS * 8 + 256);
+  Key master;
+  std::memcpy(master.k, cfg->seed, 32);
+  k_derive_keys<<<1, 32, 0, ctx->st>>>(master, keys_dev);
+  launch_gr_inverses(ctx->st, ctx->cst + CST_INV);
+  launch_mode_consts(ctx->st, ctx->reduce_mode, ctx->cst + CST_LAM);
+  k_init_consts<<<1, 64, 0, ctx->st>>>(ctx->reduce_mode, ctx->cst);
+  e = cudaMemsetAsync(ctx->status, 0, sizeof(u32), ctx->st);
+  if (e != cudaSuccess) return bail("cudaMemset", e);
+  u32 kh[24];
+  e = cudaMemcpyAsync(kh, keys_dev, sizeof(kh), cudaMemcpyDeviceToHost, ctx->st);
+  if (e != cudaSuccess) return bail("key copy", e);
+  e = cudaStreamSynchronize(ctx->st);
+  if (e != cudaSuccess) return bail("init", e);
+  std::memcpy(ctx->k01.k, kh, 32);
+  std::memcpy(ctx->k02.k, kh + 8, 32);
+  std::memcpy(ctx->k12.k, kh + 16, 32);
+  *out = ctx;
+  return MPC_OK;
+}
+
+void mpc_destroy(mpc_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+  if (ctx->cst) cudaFree(ctx->cst);
+  if (ctx->own_stream && ctx->st) cudaStreamDestroy(ctx->st);
+  delete ctx;
+}
+
+const char* mpc_last_error(const mpc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int mpc_set_stream(mpc_ctx* ctx, void* stream) {
+  if (!ctx || !stream) return MPC_ERR_ARG;
+  if (ctx->own_stream && ctx->st) {
+    cudaStreamSynchronize(ctx->st);
+    cudaStreamDestroy(ctx->st);
+    ctx->own_stream = false;
+  }
+  ctx->st = (cudaStream_t)stream;
+  return MPC_OK;
+}
+
+int mpc_sync(mpc_ctx* ctx) {
+  if (!ctx) return MPC_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->st));
+  return MPC_OK;
+}
+
+int mpc_status(const mpc_ctx* ctx) {
+  if (!ctx) return MPC_ERR_ARG;
+  return ctx->aborted ? MPC_ERR_ABORT : MPC_OK;
+}
+
+int64_t mpc_workspace_size(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int64_t c,
+                           int trunc_bits, int R_main, int R_trunc) {
+  (void)ctx;
+  Arena ar{nullptr, 0, 0, true};
+  switch (op) {
+    case MPC_OP_SHARE:
+      if (a < 0) return -1;
+      ar.take<u64>(a);
+      ar.take<u64>(a);
+      break;
+    case MPC_OP_MULT:
+      if (a < 0) return -1;
+      for (int i = 0; i < 6; ++i) ar.take<u64>(a);
+      break;
+    case MPC_OP_MATMUL:
+      if (a <= 0 || b <= 0 || c <= 0) return -1;
+      plan_matmul(ar, a * b, trunc_bits >= 0);
+      break;
+    case MPC_OP_VERIFY_MULT:
+      if (a <= 0) return -1;
+      plan_vmult(ar, a, R_main);
+      break;
+    case MPC_OP_VERIFY_MATMUL:
+      if (a <= 0 || b <= 0 || c <= 0) return -1;
+      plan_vmat(ar, a, b, c, trunc_bits, R_main, R_trunc);
+      break;
+    case MPC_OP_RECONSTRUCT:
+      if (a < 0) return -1;
+      plan_rec(ar, a, true);
+      break;
+    default:
+      return -1;
+  }
+  return (int64_t)ar.off;
+}
+
+int mpc_share_input(mpc_ctx* ctx, uint64_t call_id, const uint64_t* x, int x_on_host, int64_t n,
+                    uint64_t* xs, void* workspace, size_t workspace_bytes) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (n < 0) return fail(ctx, MPC_ERR_SHAPE, "n < 0");
+  if (n == 0) return MPC_OK;
+  if (!x || !xs || !id_ok(call_id)) return fail(ctx, MPC_ERR_ARG, "share_input: bad argument");
+  Arena ar{(char*)workspace, workspace_bytes, 0, false};
+  u64* stage = ar.take<u64>(n);
+  u64* mout = ar.take<u64>(n);
+  if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "share_input: workspace too small");
+  Phase phase(ctx, MPC_PROF_SHARE);
+  const u64* xd = (const u64*)x;
+  if (x_on_host) {
+    CK(cudaMemcpyAsync(stage, x, (size_t)n * 8, cudaMemcpyHostToDevice, ctx->st));
+    xd = stage;
+  }
+  launch_share_input(ctx->st, xd, n, ctx->k01, ctx->k02, make_obj(call_id, 0, 0), (u64*)xs, mout);
+  if ((rc = deliver(ctx, MPC_PHASE_ONLINE, MPC_PROTO_SHARE, mout, (u64*)xs + 2 * n, n,
+                    MPC_SITE_MX_COPY_P1)))
+    return rc;
+  if ((rc = deliver(ctx, MPC_PHASE_ONLINE, MPC_PROTO_SHARE, mout, (u64*)xs + 4 * n, n, -1))) return rc;
+  return cuda_check(ctx, "share_input");
+}
+
+int mpc_mult(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_t* ys, int64_t n,
+             uint64_t* zs, void* workspace, size_t workspace_bytes) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (n <= 0) return fail(ctx, MPC_ERR_SHAPE, "mult: n <= 0");
+  if (!xs || !ys || !zs || !id_ok(call_id)) return fail(ctx, MPC_ERR_ARG, "mult: bad argument");
+  Arena ar{(char*)workspace, workspace_bytes, 0, false};
+  u64* g2o = ar.take<u64>(n);
+  u64* g2i = ar.take<u64>(n);
+  u64* p1o = ar.take<u64>(n);
+  u64* p2o = ar.take<u64>(n);
+  u64* p1i = ar.take<u64>(n);
+  u64* p2i = ar.take<u64>(n);
+  if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "mult: workspace too small");
+  Phase phase(ctx, MPC_PROF_MULT);
+  const u64 obj = make_obj(call_id, 0, 0);
+  launch_mult_offline(ctx->st, xs, ys, n, ctx->k01, ctx->k02, obj, zs, g2o);
+  if ((rc = deliver(ctx, MPC_PHASE_OFFLINE, MPC_PROTO_MULT, g2o, g2i, n, MPC_SITE_GAMMA2))) return rc;
+  launch_mult_online(ctx->st, xs, ys, n, ctx->k01, obj, g2i, p1o, p2o);
+  if ((rc = deliver(ctx, MPC_PHASE_ONLINE, MPC_PROTO_MULT, p1o, p2i, n, MPC_SITE_MZ1))) return rc;
+  if ((rc = deliver(ctx, MPC_PHASE_ONLINE, MPC_PROTO_MULT, p2o, p1i, n, MPC_SITE_MZ2))) return rc;
+  launch_exchange_finish(ctx->st, n, p1o, p1i, p2o, p2i, zs, -1, nullptr);
+  ctx->pending.insert((call_id << 1) | 0);
+  return cuda_check(ctx, "mult");
+}
+
+int mpc_matmul(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_t* ws_,
+               int64_t M, int64_t N, int64_t K, int trunc_bits, uint64_t* zpre, uint64_t* zout,
+               uint64_t* pq, void* workspace, size_t workspace_bytes) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (M <= 0 || N <= 0 || K <= 0) return fail(ctx, MPC_ERR_SHAPE, "matmul: bad shape");
+  if (trunc_bits > 63) return fail(ctx, MPC_ERR_ARG, "matmul: trunc_bits > 63");
+  const bool trunc = trunc_bits >= 0;
+  if (!xs || !ws_ || !zpre || !id_ok(call_id) || (trunc && (!zout || !pq || zout == zpre)))
+    return fail(ctx, MPC_ERR_ARG, "matmul: bad argument");
+  const long long E = M * N;
+  Arena ar{(char*)workspace, workspace_bytes, 0, false};
+  MatmulPlan p = plan_matmul(ar, E, trunc);
+  if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "matmul: workspace too small");
+  cudaStream_t st = ctx->st;
+  const u64 obj = make_obj(call_id, 0, 0);
+  const u64 M1 = ~0ull;
+  if (trunc) {   // Pi_Trunc preprocessing first: it assigns the product wire's mask
+    Phase phase(ctx, MPC_PROF_TRUNC_PAIRS);
+    launch_trunc_p0(st, E, ctx->k01, ctx->k02, obj, trunc_bits, zpre, zout, pq, p.gp2, p.gq2,
+                    p.mp1, p.mq1);
+    const int ph = MPC_PHASE_OFFLINE, pr = MPC_PROTO_TRUNC;
+    if ((rc = deliver(ctx, ph, pr, p.gp2, p.gp2i, E, MPC_SITE_GAMMA2))) return rc;
+    if ((rc = deliver(ctx, ph, pr, p.mp1, p.mpi2, E, MPC_SITE_MZ1))) return rc;
+    if ((rc = deliver(ctx, ph, pr, p.gp2i, p.mpi1, E, MPC_SITE_MZ2))) return rc;
+    if ((rc = deliver(ctx, ph, pr, p.gq2, p.gq2i, E, MPC_SITE_GAMMA2))) return rc;
+    if ((rc = deliver(ctx, ph, pr, p.mq1, p.mqi2, E, MPC_SITE_MZ1))) return rc;
+    if ((rc = deliver(ctx, ph, pr, p.gq2i, p.mqi1, E, MPC_SITE_MZ2))) return rc;
+    launch_trunc_finish(st, E, ctx->k01, ctx->k02, obj, trunc_bits, p.mpi1, p.mqi1, p.mpi2,
+                        p.mqi2, p.gp2i, p.gq2i, p.mp1, p.mq1, zpre, zout, pq);
+  } else {
+    launch_fill_masks(st, E, ctx->k01, ctx->k02, P_INNER, obj, zpre);
+  }
+  const u64* X = xs;
+  const u64* W = ws_;
+  const long long MK = M * K, KN = K * N;
+  {  // P0, offline: Gamma = (R_X1 + R_X2)(R_W1 + R_W2) + r_Z; message [Gamma]_2 = Gamma - [Gamma]_1
+    Phase phase(ctx, MPC_PROF_GEMM);
+    GemmTerm T;
+    T.A = op(X, K, 0, X + MK, 1);
+    T.B = op(W, N, 0, W + KN, 1);
+    Epi e = epi_store(p.g2o, N);
+    e.add0 = zpre;
+    e.add1 = zpre + E;
+    e.prf_sign = M1;
+    e.key = ctx->k01;
+    e.tag = make_tag(P_INNER, C_G1);
+    e.obj = obj;
+    gemm_u64(st, M, N, K, 1, &T, e, 1);
+  }
+  if ((rc = deliver(ctx, MPC_PHASE_OFFLINE, MPC_PROTO_INNER, p.g2o, p.g2i, E, MPC_SITE_GAMMA2)))
+    return rc;
+  {  // P1, online: [m_Z]_1 = -(M_X [R_W]_1 + [R_X]_1 M_W) + [Gamma]_1
+    Phase phase(ctx, MPC_PROF_GEMM);
+    GemmTerm T[2];
+    T[0].A = op(X + 2 * MK, K);
+    T[0].B = op(W + 3 * KN, N);
+    T[1].A = op(X + 3 * MK, K);
+    T[1].B = op(W + 2 * KN, N);
+    Epi e = epi_store(p.mz1, N);
+    e.acc_sign = M1;
+    e.prf_sign = 1;
+    e.key = ctx->k01;
+    e.tag = make_tag(P_INNER, C_G1);
+    e.obj = obj;
+    gemm_u64(st, M, N, K, 2, T, e, 1);
+  }
+  {  // P2, online: [m_Z]_2 = M_X (M_W - [R_W]_2) - [R_X]_2 M_W + [Gamma]_2
+    Phase phase(ctx, MPC_PROF_GEMM);
+    GemmTerm T[2];
+    T[0].A = op(X + 4 * MK, K);
+    T[0].B = op(W + 4 * KN, N, 0, W + 5 * KN, M1);
+    T[1].A = op(X + 5 * MK, K, 0, nullptr, 1, M1);
+    T[1].B = op(W + 4 * KN, N);
+    Epi e = epi_store(p.mz2, N);
+    e.add0 = p.g2i;
+    gemm_u64(st, M, N, K, 2, T, e, 1);
+  }
+  {
+    Phase phase(ctx, MPC_PROF_EXCHANGE);
+    if ((rc = deliver(ctx, MPC_PHASE_ONLINE, MPC_PROTO_INNER, p.mz1, p.mz1i, E, MPC_SITE_MZ1)))
+      return rc;
+    if ((rc = deliver(ctx, MPC_PHASE_ONLINE, MPC_PROTO_INNER, p.mz2, p.mz2i, E, MPC_SITE_MZ2)))
+      return rc;
+    launch_exchange_finish(st, E, p.mz1, p.mz2i, p.mz2, p.mz1i, zpre, trunc_bits,
+                           trunc ? zout : nullptr);
+  }
+  if (!trunc && zout && zout != zpre)
+    CK(cudaMemcpyAsync(zout, zpre, (size_t)E * 48, cudaMemcpyDeviceToDevice, st));
+  ctx->pending.insert((call_id << 1) | 1);
+  return cuda_check(ctx, "matmul");
+}
+
+int mpc_verify_mult(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, const uint64_t* ys,
+                    const uint64_t* zs, int64_t n, uint64_t mult_call_id, int R,
+                    void* workspace, size_t workspace_bytes, uint64_t* trace) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (n <= 0) return fail(ctx, MPC_ERR_SHAPE, "verify_mult: n <= 0");
+  if (!xs || !ys || !zs || !id_ok(verify_id)) return fail(ctx, MPC_ERR_ARG, "verify_mult: bad argument");
+  Arena ar{(char*)workspace, workspace_bytes, 0, false};
+  VMultPlan p = plan_vmult(ar, n, R);
+  if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "verify_mult: workspace too small");
+  Phase phase(ctx, MPC_PROF_VERIFY_MULT);
+  cudaStream_t st = ctx->st;
+  const Small& s = p.s;
+  // Pi_Tran (Fig. MTP): reveal r; x'_i = r^i x_i; y lifted; z = sum r^i z_i
+  reveal(ctx, P_VER_R, make_obj(verify_id, 0, 0), s.tmp6, s.r);
+  launch_gr_powers(st, s.r, n, p.pw);
+  Vec& x = p.dv.x[0];
+  Vec& y = p.dv.y[0];
+  for (int c = 0; c < 6; ++c) {
+    launch_gr_scale_rows(st, p.pw, xs + c * n, n, x.c[c]);
+    launch_gr_lift(st, ys + c * n, n, y.c[c]);
+  }
+  CK(cudaMemsetAsync(s.zinit, 0, 384 * 8, st));
+  {  // z_c = sum_i z_c[i] r^i for the 6 components at once: (6 x n) . (n x 64)
+    GemmTerm T;
+    T.A = op(zs, n);
+    T.B = op(p.pw, 64);
+    gemm_u64(st, 6, 64, n, 1, &T, epi_atomic(s.zinit, 64), nsplit_for(n));
+  }
+  p.dv.cur = 0;
+  rc = run_dense(ctx, verify_id, 0, p.dv, n, s.zinit, 1, p.R, s, p.iv, trace);
+  if (rc) return rc;
+  return finish_verify(ctx, (mult_call_id << 1) | 0);
+}
+
+int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, const uint64_t* ws_,
+                      const uint64_t* zpre, const uint64_t* pq, int64_t M, int64_t N, int64_t K,
+                      int trunc_bits, uint64_t matmul_call_id, int R_main, int R_trunc,
+                      void* workspace, size_t workspace_bytes, uint64_t* trace) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (M <= 0 || N <= 0 || K <= 0) return fail(ctx, MPC_ERR_SHAPE, "verify_matmul: bad shape");
+  const bool trunc = trunc_bits >= 0;
+  if (!xs || !ws_ || !zpre || (trunc && !pq) || !id_ok(verify_id) || !id_ok(matmul_call_id) ||
+      trunc_bits > 63)
+    return fail(ctx, MPC_ERR_ARG, "verify_matmul: bad argument");
+  Arena ar{(char*)workspace, workspace_bytes, 0, false};
+  VMatPlan p = plan_vmat(ar, M, N, K, trunc_bits, R_main, R_trunc);
+  if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "verify_matmul: workspace too small");
+  cudaStream_t st = ctx->st;
+  const Small& s = p.s;
+  const long long MK = M * K, KN = K * N, E = M * N;
+  // ---- batch 0: the M N inner products of Z = X W, rank-1 consolidation ----
+  Phase* phase = new Phase(ctx, MPC_PROF_VERIFY_GEMM);
+  reveal(ctx, P_VER_R, make_obj(verify_id, 0, 0), s.tmp6, s.r);
+  launch_gr_powers(st, s.r, N, p.Q);                       // r^b
+  launch_gr_mul1(st, p.Q + (N - 1) * 64, s.r, s.aux);      // rho = r^N
+  launch_gr_powers(st, s.aux, M, p.P);                     // rho^a
+  Vec& x = p.dv.x[0];
+  Vec& y = p.dv.y[0];
+  for (int c = 0; c < 6; ++c) {
+    GemmTerm T;
+    T.A = op(xs + c * MK, K, 1);        // Xt_k = sum_a rho^a X_ak  (K x M) . (M x 64)
+    T.B = op(p.P, 64);
+    gemm_u64(st, K, 64, M, 1, &T, epi_store(x.c[c], 64), 1);
+    GemmTerm U;
+    U.A = op(ws_ + c * KN, N);          // Wt_k = sum_b r^b W_kb   (K x N) . (N x 64)
+    U.B = op(p.Q, 64);
+    gemm_u64(st, K, 64, N, 1, &U, epi_store(y.c[c], 64), 1);
+  }
+  {  // zt = sum_a rho^a (sum_b r^b Z_ab): T = Z Q for all 6 components, then Gram with P
+    GemmTerm T;
+    T.A = op(zpre, N);
+    T.B = op(p.Q, 64);
+    gemm_u64(st, 6 * M, 64, N, 1, &T, epi_store(p.T, 64), 1);
+    CK(cudaMemsetAsync(p.Pz, 0, 6 * 4096 * 8, st));
+    for (int c = 0; c < 6; ++c)
+      gram(ctx, p.Pz + c * 4096, p.P, nullptr, 1, 64, p.T + c * M * 64, nullptr, 1, 64, M, 1);
+    launch_gr_fold_reduce(st, p.Pz, 6, s.zinit);
+  }
+  p.dv.cur = 0;
+  rc = run_dense(ctx, verify_id, 0, p.dv, K, s.zinit, 1, p.R0, s, p.iv, trace);
+  delete phase;
+  if (rc) return rc;
+  // ---- batch 1: the truncation pairs ----
+  if (trunc) {
+    phase = new Phase(ctx, MPC_PROF_TRUNC_SETUP);
+    u64* tr = trace ? trace + (long long)(p.R0 + 1) * TRACE_ROUND : nullptr;
+    const u64 mobj = make_obj(matmul_call_id, 0, 0);
+    reveal(ctx, P_VER_R, make_obj(verify_id, 1, 0), s.tmp6, s.r);
+    launch_trunc_u(st, s.r, trunc_bits, p.V);                         // V_j = u_j
+    for (int j = 0; j < 64; ++j)
+      CK(cudaMemcpyAsync(p.W + j * 64, ctx->cst + CST_ONE, 512, cudaMemcpyDeviceToDevice, st));
+    launch_prf_words(st, E, ctx->k01, make_tag(P_TRUNC_BITS, C_TB1), mobj, p.b1);
+    launch_prf_words(st, E, ctx->k02, make_tag(P_TRUNC_BITS, C_TB2), mobj, p.b2);
+    launch_gr_mul1(st, s.r, s.r, s.aux + 64);                          // r^2
+    launch_gr_powers(st, s.aux + 64, E, p.Rtab);                       // r^(2e)
+    CK(cudaMemsetAsync(p.Zpq, 0, 12 * 64 * 8, st));
+    {  // sum_e r^(2e) p_c[e], sum_e r^(2e) q_c[e]: (12 x E) . (E x 64)
+      GemmTerm T;
+      T.A = op(pq, E);
+      T.B = op(p.Rtab, 64);
+      gemm_u64(st, 12, 64, E, 1, &T, epi_atomic(p.Zpq, 64), nsplit_for(E));
+    }
+    u64* z0 = p.zt + 384;
+    for (int c = 0; c < 6; ++c)   // z_c = sum r^(2e) p_c + r sum r^(2e) q_c
+      launch_gr_lincomb(st, ctx->cst + CST_ONE, p.Zpq + c * 64, s.r, p.Zpq + (6 + c) * 64,
+                        z0 + c * 64);
+    delete phase;
+    phase = new Phase(ctx, MPC_PROF_TRUNC_S);
+    CK(cudaMemsetAsync(p.S, 0, 4096 * 64 * 8, st));
+    {  // S_{j,j'} = sum_e r^(2e) b1_{e,j} b2_{e,j'}  (P0; bit-product operand)
+      GemmTerm T;
+      T.A = op(p.b1, 0, 2, p.b2, 1);
+      T.B = op(p.Rtab, 64);
+      gemm_u64(st, 4096, 64, E, 1, &T, epi_atomic(p.S, 64), nsplit_for(E) > 64 ? 64 : nsplit_for(E));
+    }
+    delete phase;
+    phase = new Phase(ctx, MPC_PROF_TRUNC_ROUNDS);
+    const u64* z = z0;
+    u64* zbuf[2] = {s.z[0], s.z[1]};
+    int zi = 0;
+    for (int k = 1; k <= p.kd; ++k) {   // rounds folding the 64 bits of each output
+      const u64 obj = make_obj(verify_id, 1, (u32)k);
+      CK(cudaMemsetAsync(p.hsum, 0, 128 * 8, st));
+      launch_trunc_round_h(st, p.V, p.W, p.S, k, ctx->cst + CST_LAM, p.hsum);
+      CK(cudaMemsetAsync(p.S3, 0, 2 * 192 * 8, st));
+      CK(cudaMemcpyAsync(p.S3, p.hsum, 512, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(p.S3 + 192, p.hsum + 64, 512, cudaMemcpyDeviceToDevice, st));
+      inner_finish(ctx, p.S3, P_VER_H0, obj, s.h0);
+      inner_finish(ctx, p.S3 + 192, P_VER_H2, obj, s.h2);
+      reveal(ctx, P_VER_ZETA, obj, s.tmp6, s.zp);
+      launch_gr_lagrange(st, s.zp, ctx->reduce_mode, ctx->cst + CST_INV, s.coef);
+      launch_gr_combine_z(st, s.coef, s.h0, s.h2, z, zbuf[zi]);
+      z = zbuf[zi];
+      zi ^= 1;
+      launch_trunc_update_vw(st, p.V, p.W, k, s.coef);
+      trace_round(ctx, tr, k, s);
+    }
+    delete phase;
+    phase = new Phase(ctx, MPC_PROF_TRUNC_MATERIALIZE);
+    // materialise the folded vectors: x.[r]_1 at P0 and P1, y.[r]_2 at P0 and P2
+    Vec& tx = p.dt.x[0];
+    Vec& ty = p.dt.y[0];
+    launch_trunc_materialize(st, E, p.b1, p.V, p.Rtab, p.kd, tx.c[0]);
+    launch_trunc_materialize(st, E, p.b1, p.V, p.Rtab, p.kd, tx.c[3]);
+    launch_trunc_materialize(st, E, p.b2, p.W, nullptr, p.kd, ty.c[1]);
+    launch_trunc_materialize(st, E, p.b2, p.W, nullptr, p.kd, ty.c[5]);
+    delete phase;
+    if ((rc = cuda_check(ctx, "trunc batch"))) return rc;
+    phase = new Phase(ctx, MPC_PROF_TRUNC_TAIL);
+    // the claim entering the dense rounds must not alias their round scratch
+    CK(cudaMemcpyAsync(s.zinit, z, 384 * 8, cudaMemcpyDeviceToDevice, st));
+    p.dt.cur = 0;
+    rc = run_dense(ctx, verify_id, 1, p.dt, p.Dt, s.zinit, p.kd + 1, p.R1, s, p.ivt, tr);
+    delete phase;
+    if (rc) return rc;
+  }
+  return finish_verify(ctx, (matmul_call_id << 1) | 1);
+}
+
+int mpc_reconstruct(mpc_ctx* ctx, const uint64_t* xs, int64_t n, uint64_t* out, int out_on_host,
+                    void* workspace, size_t workspace_bytes) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (n <= 0) return fail(ctx, MPC_ERR_SHAPE, "reconstruct: n <= 0");
+  if (!xs || !out) return fail(ctx, MPC_ERR_ARG, "reconstruct: bad argument");
+  if (!ctx->pending.empty())
+    return fail(ctx, MPC_ERR_PENDING, "reconstruct: products are not verified yet");
+  Arena ar{(char*)workspace, workspace_bytes, 0, false};
+  RecPlan p = plan_rec(ar, n, out_on_host != 0);
+  if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "reconstruct: workspace too small");
+  Phase* phase = new Phase(ctx, MPC_PROF_REC);
+  cudaStream_t st = ctx->st;
+  const int ph = MPC_PHASE_ONLINE, pr = MPC_PROTO_REC;
+  if ((rc = deliver(ctx, ph, pr, xs, p.in_p2_r1, n, -1))) return rc;             // P0 -> P2 [r]_1
+  if ((rc = deliver(ctx, ph, pr, xs + n, p.in_p1_r2, n, MPC_SITE_REC_MSG))) return rc;  // P0 -> P1
+  if ((rc = deliver(ctx, ph, pr, xs + 2 * n, p.in_p0_m, n, -1))) return rc;      // P1 -> P0 m
+  u32* d = p.dg;
+  launch_hash_u64(st, xs + 3 * n, n, p.hs[0], d + 0);     // P1: H([r]_1) -> P2
+  launch_hash_u64(st, xs + 4 * n, n, p.hs[1], d + 8);     // P2: H(m) -> P0
+  launch_hash_u64(st, xs + 5 * n, n, p.hs[2], d + 16);    // P2: H([r]_2) -> P1
+  count_msgs(ctx, ph, pr, 3, 32);
+  launch_hash_u64(st, p.in_p2_r1, n, p.hs[3], d + 24);    // P2 hashes received [r]_1
+  launch_hash_u64(st, p.in_p0_m, n, p.hs[4], d + 32);     // P0 hashes received m
+  launch_hash_u64(st, p.in_p1_r2, n, p.hs[5], d + 40);    // P1 hashes received [r]_2
+  launch_digest_check(st, d + 0, d + 24, d + 8, d + 32, d + 16, d + 40, ctx->status, ST_ABORT);
+  u64* o = out_on_host ? p.out_dev : (u64*)out;
+  launch_open_p1(st, xs + 2 * n, xs + 3 * n, p.in_p1_r2, n, o);
+  if (out_on_host) CK(cudaMemcpyAsync(out, o, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+  delete phase;
+  if ((rc = cuda_check(ctx, "reconstruct"))) return rc;
+  u32 stv = 0;
+  if ((rc = read_status(ctx, &stv))) return rc;
+  if (stv & ST_ABORT) {
+    ctx->aborted = true;
+    if (out_on_host) std::memset(out, 0, (size_t)n * 8);
+    else cudaMemsetAsync(out, 0, (size_t)n * 8, st);
+    return fail(ctx, MPC_ERR_ABORT, "Pi_Rec: inconsistent messages");
+  }
+  return MPC_OK;
+}
+
+int mpc_ledger(const mpc_ctx* ctx, uint64_t* bytes, uint64_t* messages) {
+  if (!ctx || !bytes) return MPC_ERR_ARG;
+  for (int a = 0; a < MPC_NPHASE; ++a)
+    for (int b = 0; b < MPC_NPROTO; ++b) bytes[a * MPC_NPROTO + b] = ctx->ledger[a][b];
+  if (messages) *messages = ctx->nmsg;
+  return MPC_OK;
+}
+
+void mpc_ledger_reset(mpc_ctx* ctx) {
+  if (!ctx) return;
+  std::memset(ctx->ledger, 0, sizeof(ctx->ledger));
+  ctx->nmsg = 0;
+}
+
+int mpc_inject_fault(mpc_ctx* ctx, int site, uint64_t index, uint64_t xor_mask) {
+  if (!ctx || site < 0 || site >= MPC_NSITE) return MPC_ERR_ARG;
+  ctx->fault[site] = {true, index, site == MPC_SITE_HIGH_BIT ? (1ull << 63) : xor_mask};
+  return MPC_OK;
+}
+
+int mpc_profile(mpc_ctx* ctx, int enable) {
+  if (!ctx) return MPC_ERR_ARG;
+  if (enable) {
+    ctx->recs.clear();
+    ctx->pool_used = 0;
+  }
+  ctx->prof = enable != 0;
+  return MPC_OK;
+}
+
+int mpc_profile_read(mpc_ctx* ctx, double* ms, uint64_t* count) {
+  if (!ctx || !ms) return MPC_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->st));
+  for (int i = 0; i < MPC_NPROF; ++i) {
+    ms[i] = 0.0;
+    if (count) count[i] = 0;
+  }
+  for (const auto& r : ctx->recs) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, r.a, r.b));
+    if (r.id >= 0 && r.id < MPC_NPROF) {
+      ms[r.id] += t;
+      if (count) count[r.id] += 1;
+    }
+  }
+  ctx->recs.clear();
+  ctx->pool_used = 0;
+  return MPC_OK;
+}
+
+uint64_t mpc_launch_count(void) { return g_launches; }
+
+}  // extern "C"

@@ -1,0 +1,188 @@
+// Exact Z_2^64 GEMM on CUDA cores (the plain "u64 path").
+//
+// Computes C = sum_t A_t B_t mod 2^64 with operands formed on load (value = scale*(p0 + s1*p1)),
+// which lets one kernel evaluate every local product of Pi_Inner (Fig. DPP, Sec. 4.1):
+//   P0 : (R_X1 + R_X2)(R_W1 + R_W2)                       (offline Gamma)
+//   P1 : M_X [R_W]_1 + [R_X]_1 M_W                          (online, negated in the epilogue)
+//   P2 : M_X (M_W - [R_W]_2) - [R_X]_2 M_W                   (online)
+// and, with split-K and atomic accumulation, the Gram sums sum_i u_i (x) v_i and the GR folds of
+// the batched verification.  Tiles: BM x BN per CTA, BK = 8, TM x TN register micro-tiles,
+// double-buffered shared memory.  Index arithmetic is 64-bit; every global access is bounds
+// checked (out-of-range operand elements read as 0).
+#include "kernels.h"
+
+namespace mpc3 {
+
+namespace {
+
+__device__ __forceinline__ u64 ld_opnd(const Opnd& o, long long r, long long c, long long R,
+                                       long long C) {
+  if (r >= R || c >= C) return 0;
+  if (o.trans == 2) {
+    // bit-product operand of the truncation batch: row r = 64 j + j', column c = output e,
+    // value = bit j of p0[e] AND bit j' of p1[e]
+    return (o.p0[c] >> (r >> 6)) & (o.p1[c] >> (r & 63)) & 1ull;
+  }
+  const long long off = o.trans ? (c * o.ld + r) : (r * o.ld + c);
+  u64 v = o.p0[off];
+  if (o.p1) v += o.s1 * o.p1[off];
+  return o.scale * v;
+}
+
+template <int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+gemm_u64_kernel(long long M, long long N, long long K, int nterms, GemmTerm t0, GemmTerm t1,
+                Epi epi, long long k_per_split) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  constexpr int A_PER = BM * BK / NT;
+  constexpr int B_PER = BK * BN / NT;
+  static_assert(BM * BK % NT == 0 && BK * BN % NT == 0, "tile/thread mismatch");
+  __shared__ u64 As[2][BK][BM];
+  __shared__ u64 Bs[2][BK][BN];
+
+  const int tid = threadIdx.x;
+  const int tx = tid % (BN / TN);
+  const int ty = tid / (BN / TN);
+  const long long m0 = (long long)blockIdx.x * BM;
+  const long long n0 = (long long)blockIdx.y * BN;
+  const long long kbeg = (long long)blockIdx.z * k_per_split;
+  const long long kend = (kbeg + k_per_split < K) ? (kbeg + k_per_split) : K;
+
+  u64 acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0;
+
+  // virtual K loop over the terms: for term t, k runs over [kbeg, kend)
+  const long long ktiles_per_term = (kend > kbeg) ? (kend - kbeg + BK - 1) / BK : 0;
+  const long long total_tiles = ktiles_per_term * nterms;
+
+  u64 ra[A_PER], rb[B_PER];
+  auto load_tile = [&](long long tile) {
+    const GemmTerm& T = (tile < ktiles_per_term) ? t0 : t1;
+    const long long kt = kbeg + (tile % (ktiles_per_term ? ktiles_per_term : 1)) * BK;
+#pragma unroll
+    for (int q = 0; q < A_PER; ++q) {
+      const int e = tid + q * NT;
+      int mm, kk;
+      if (T.A.trans == 1) { mm = e % BM; kk = e / BM; }  // consecutive threads: consecutive m
+      else { kk = e % BK; mm = e / BK; }                  // consecutive threads: consecutive k
+      const long long gk = kt + kk;
+      ra[q] = (gk < kend) ? ld_opnd(T.A, m0 + mm, gk, M, K) : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < B_PER; ++q) {
+      const int e = tid + q * NT;
+      const int nn = e % BN, kk = e / BN;
+      const long long gk = kt + kk;
+      rb[q] = (gk < kend) ? ld_opnd(T.B, gk, n0 + nn, K, N) : 0;
+    }
+  };
+  auto store_tile = [&](int buf, long long tile) {
+    const GemmTerm& T = (tile < ktiles_per_term) ? t0 : t1;
+#pragma unroll
+    for (int q = 0; q < A_PER; ++q) {
+      const int e = tid + q * NT;
+      int mm, kk;
+      if (T.A.trans == 1) { mm = e % BM; kk = e / BM; }
+      else { kk = e % BK; mm = e / BK; }
+      As[buf][kk][mm] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < B_PER; ++q) {
+      const int e = tid + q * NT;
+      Bs[buf][e / BN][e % BN] = rb[q];
+    }
+  };
+
+  if (total_tiles > 0) {
+    load_tile(0);
+    store_tile(0, 0);
+    __syncthreads();
+    for (long long tile = 0; tile < total_tiles; ++tile) {
+      const int buf = (int)(tile & 1);
+      if (tile + 1 < total_tiles) load_tile(tile + 1);
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        u64 a[TM], b[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) a[i] = As[buf][k][ty * TM + i];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) b[j] = Bs[buf][k][tx * TN + j];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * b[j];
+      }
+      if (tile + 1 < total_tiles) store_tile(buf ^ 1, tile + 1);
+      __syncthreads();
+    }
+  }
+
+  // epilogue
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const long long r = m0 + ty * TM + i;
+    if (r >= M) continue;
+    const long long cbase = n0 + tx * TN;
+    u64 prfw[TN];
+#pragma unroll
+    for (int j = 0; j < TN; ++j) prfw[j] = 0;
+    if (!epi.atomic && epi.prf_sign) {
+      const long long ibase = r * epi.ldc + cbase;
+      if ((TN % 8 == 0) && (ibase % 8 == 0)) {
+#pragma unroll
+        for (int j8 = 0; j8 < TN; j8 += 8) {
+          u64 w[8];
+          prf_block8(epi.key, epi.tag, epi.obj, (u64)(ibase + j8) >> 3, w);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) prfw[j8 + q] = w[q];
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < TN; ++j)
+          if (cbase + j < N) prfw[j] = prf_word(epi.key, epi.tag, epi.obj, (u64)(ibase + j));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const long long c = cbase + j;
+      if (c >= N) continue;
+      const long long idx = r * epi.ldc + c;
+      const u64 v = epi.acc_sign * acc[i][j];
+      if (epi.atomic) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(epi.out + idx), v);
+      } else {
+        u64 o = v;
+        if (epi.add0) o += epi.add0[idx];
+        if (epi.add1) o += epi.add1[idx];
+        o += epi.prf_sign * prfw[j];
+        epi.out[idx] = o;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+void gemm_u64(cudaStream_t st, long long M, long long N, long long K, int nterms,
+              const GemmTerm* terms, const Epi& epi, int nsplit) {
+  if (M <= 0 || N <= 0) return;
+  if (nsplit < 1) nsplit = 1;
+  const long long kps = (K + nsplit - 1) / nsplit;
+  GemmTerm t1 = (nterms > 1) ? terms[1] : terms[0];
+  if (N <= 64) {
+    constexpr int BM = 128, BN = 64, BK = 8, TM = 8, TN = 4;
+    dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)nsplit);
+    gemm_u64_kernel<BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(
+        M, N, K, nterms, terms[0], t1, epi, kps);
+  } else {
+    constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
+    dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)nsplit);
+    gemm_u64_kernel<BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(
+        M, N, K, nterms, terms[0], t1, epi, kps);
+  }
+}
+
+}  // namespace mpc3

@@ -1,0 +1,113 @@
+// Host-side launchers of libmpc3's kernels (internal interface between the protocol driver in
+// api.cu and the kernels).  Every launcher enqueues on `st` and returns nothing; launch errors
+// are collected by the driver with cudaGetLastError().
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace mpc3 {
+
+// ---- u64 GEMM on CUDA cores ----------------------------------------------------------------
+// An operand is value(r, c) = scale * (p0[r, c] + s1 * p1[r, c]) with element (r, c) stored at
+// p[r*ld + c] (trans = 0) or p[c*ld + r] (trans = 1); p1 may be null.
+struct Opnd {
+  const u64* p0;
+  const u64* p1;
+  long long ld;
+  u64 s1;
+  u64 scale;
+  int trans;
+};
+struct GemmTerm {
+  Opnd A;   // M x K
+  Opnd B;   // K x N
+};
+// out[i] = acc_sign*acc + add0[i] + add1[i] + prf_sign*PRF(key, tag, obj, i), i = r*ldc + c,
+// or, with atomic = 1, out[r*ldc + c] += acc_sign*acc (split-K accumulation).
+struct Epi {
+  int atomic;
+  u64 acc_sign;
+  const u64* add0;
+  const u64* add1;
+  u64 prf_sign;
+  Key key;
+  u32 tag;
+  u64 obj;
+  u64* out;
+  long long ldc;
+};
+// C(M x N) = sum over terms of A_t (M x K) * B_t (K x N), then the epilogue.  nsplit > 1 splits
+// K across grid.z and requires epi.atomic = 1.
+void gemm_u64(cudaStream_t st, long long M, long long N, long long K, int nterms,
+              const GemmTerm* terms, const Epi& epi, int nsplit);
+
+// ---- elementwise protocol kernels (prf_kernels.cu) ------------------------------------------
+void launch_share_input(cudaStream_t st, const u64* x, long long n, Key k01, Key k02, u64 obj,
+                        u64* s6, u64* p0_out_m);
+void launch_fill_masks(cudaStream_t st, long long n, Key k01, Key k02, u32 purpose, u64 obj,
+                       u64* s6);
+void launch_mult_offline(cudaStream_t st, const u64* xs, const u64* ys, long long n, Key k01,
+                         Key k02, u64 obj, u64* zs, u64* p0_out_g2);
+void launch_mult_online(cudaStream_t st, const u64* xs, const u64* ys, long long n, Key k01,
+                        u64 obj, const u64* p2_in_g2, u64* p1_out, u64* p2_out);
+// m = own + received for P1 and P2; with t >= 0 also writes the truncated m (>>_arith t) into
+// out_s6 (P1.m, P2.m components) when out_s6 != null.
+void launch_exchange_finish(cudaStream_t st, long long n, const u64* p1_own, const u64* p1_in,
+                            const u64* p2_own, const u64* p2_in, u64* zs, int t, u64* outs);
+void launch_trunc_p0(cudaStream_t st, long long E, Key k01, Key k02, u64 obj, int t, u64* zpre,
+                     u64* zout, u64* pq, u64* p0_out_gp2, u64* p0_out_gq2, u64* p1_out_mp,
+                     u64* p1_out_mq);
+void launch_trunc_finish(cudaStream_t st, long long E, Key k01, Key k02, u64 obj, int t,
+                         const u64* p1_in_mp, const u64* p1_in_mq, const u64* p2_in_mp,
+                         const u64* p2_in_mq, const u64* p2_gp2, const u64* p2_gq2,
+                         const u64* p1_mp1, const u64* p1_mq1, u64* zpre, u64* zout, u64* pq);
+void launch_xor_one(cudaStream_t st, u64* p, u64 mask);
+void launch_open_p1(cudaStream_t st, const u64* p1_m, const u64* p1_r1, const u64* p1_in_r2,
+                    long long n, u64* out);
+
+// ---- SHA-256 Merkle hash (sha_kernels.cu) ---------------------------------------------------
+// digest (8 words) of the n-word array; scratch needs hash_scratch_words(n) 32-bit words.
+void launch_hash_u64(cudaStream_t st, const u64* data, long long n, u32* scratch, u32* digest);
+void launch_digest_check(cudaStream_t st, const u32* a0, const u32* b0, const u32* a1,
+                         const u32* b1, const u32* a2, const u32* b2, u32* status, u32 flag);
+size_t hash_scratch_words(long long n);
+
+// ---- GR(2^64, 64) kernels (gr_kernels.cu) ---------------------------------------------------
+void launch_gr_random_shared(cudaStream_t st, long long n, Key k01, Key k02, Key k12,
+                             u32 purpose, u64 obj, u64* s6);
+void launch_gr_powers(cudaStream_t st, const u64* a, long long n, u64* table);
+void launch_gr_mul1(cudaStream_t st, const u64* a, const u64* b, u64* out);
+void launch_gr_lincomb(cudaStream_t st, const u64* ca, const u64* a, const u64* cb, const u64* b,
+                       u64* out);
+void launch_gr_mulmat2(cudaStream_t st, const u64* a, const u64* b, u64* M);
+void launch_gr_inverses(cudaStream_t st, u64* out);
+void launch_gr_lagrange(cudaStream_t st, const u64* zeta_prime, int mode, const u64* inv,
+                        u64* coef);
+void launch_gr_fold_reduce(cudaStream_t st, const u64* P, int n, u64* out);
+void launch_gr_combine_z(cudaStream_t st, const u64* coef, const u64* h0, const u64* h2,
+                         const u64* z, u64* znew);
+void launch_gr_scale_rows(cudaStream_t st, const u64* pw, const u64* s, long long n, u64* out);
+void launch_gr_lift(cudaStream_t st, const u64* s, long long n, u64* out);
+void launch_fill(cudaStream_t st, u64* p, long long n, u64 v);
+void launch_neg_copy(cudaStream_t st, const u64* a, long long n, u64* out);
+void launch_gr_check_zero(cudaStream_t st, const u64* v, u32* status, u32 flag);
+void launch_trunc_u(cudaStream_t st, const u64* r, int t, u64* u);
+void launch_trunc_round_h(cudaStream_t st, const u64* V, const u64* W, const u64* S, int k,
+                          const u64* lam, u64* out);
+void launch_trunc_update_vw(cudaStream_t st, u64* V, u64* W, int k, const u64* coef);
+void launch_trunc_materialize(cudaStream_t st, long long E, const u64* words, const u64* VW,
+                              const u64* R, int kd, u64* out);
+void launch_gr_rec1(cudaStream_t st, const u64* s6, u64 xor_mask, int xor_idx, u64* out,
+                    u32* status, u32 flag);
+void launch_gr_inner_finish_all(cudaStream_t st, const u64* S, Key k01, Key k02, u32 purpose,
+                                u64 obj, u64* h6);
+void launch_gr_quad_combine(cudaStream_t st, const u64* lam, const u64* S00, const u64* S01,
+                            const u64* S10, const u64* S11, u64* out);
+void launch_mode_consts(cudaStream_t st, int mode, u64* cst);
+// PRF words of one stream into an array (e.g. the truncation bits b1, b2 of every output)
+void launch_prf_words(cudaStream_t st, long long n, Key key, u32 tag, u64 obj, u64* out);
+
+}  // namespace mpc3

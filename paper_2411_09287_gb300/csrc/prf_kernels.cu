@@ -1,0 +1,327 @@
+// Elementwise protocol kernels: input sharing (Pi_<.>^{l,0}), Pi_Mult offline/online (Fig. MultP),
+// the m-share exchange finish with the online truncation m >> t (Fig. trunc, online), and the
+// truncation-pair preprocessing (Fig. trunc, preprocessing).
+//
+// Sharing layout: a <.>-shared tensor of n elements is 6n words, component c at [c*n, (c+1)*n):
+//   0: P0.[r]_1   1: P0.[r]_2   2: P1.m   3: P1.[r]_1   4: P2.m   5: P2.[r]_2
+// Each thread owns 8 consecutive elements, i.e. one ChaCha20 block per PRG stream it draws.
+#include "kernels.h"
+
+namespace mpc3 {
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline unsigned grid_for(long long n8) {
+  long long g = (n8 + TPB - 1) / TPB;
+  if (g > (1ll << 20)) g = 1ll << 20;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+__device__ __forceinline__ u64 asr64(u64 v, int t) { return (u64)(((long long)v) >> t); }
+
+// Pi_<.>^{l,0}(x): [r]_1 from eta01 (P0, P1), [r]_2 from eta02 (P0, P2); P0 forms
+// m = x + [r]_1 + [r]_2 (its outgoing message to P1 and P2).
+__global__ void k_share_input(const u64* __restrict__ x, long long n, Key k01, Key k02, u32 tag1,
+                              u32 tag2, u64 obj, u64* __restrict__ s, u64* __restrict__ m_out) {
+  const long long nb = (n + 7) / 8;
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+       b += (long long)gridDim.x * blockDim.x) {
+    u64 r1[8], r2[8];
+    prf_block8(k01, tag1, obj, (u64)b, r1);
+    prf_block8(k02, tag2, obj, (u64)b, r2);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const long long i = b * 8 + j;
+      if (i < n) {
+        s[i] = r1[j];
+        s[n + i] = r2[j];
+        s[3 * n + i] = r1[j];
+        s[5 * n + i] = r2[j];
+        m_out[i] = x[i] + r1[j] + r2[j];
+      }
+    }
+  }
+}
+
+// [r] <- Pi_[.] (random) into the mask components of a sharing (output wires of Pi_Mult / Pi_Inner).
+__global__ void k_fill_masks(long long n, Key k01, Key k02, u32 tag1, u32 tag2, u64 obj,
+                             u64* __restrict__ s) {
+  const long long nb = (n + 7) / 8;
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+       b += (long long)gridDim.x * blockDim.x) {
+    u64 r1[8], r2[8];
+    prf_block8(k01, tag1, obj, (u64)b, r1);
+    prf_block8(k02, tag2, obj, (u64)b, r2);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const long long i = b * 8 + j;
+      if (i < n) {
+        s[i] = r1[j];
+        s[n + i] = r2[j];
+        s[3 * n + i] = r1[j];
+        s[5 * n + i] = r2[j];
+      }
+    }
+  }
+}
+
+// Pi_Mult preprocessing (P0): [r_z] <- Pi_[.]; Gamma = r_x r_y + r_z; [Gamma]_1 = PRG(eta01);
+// the message to P2 is [Gamma]_2 = Gamma - [Gamma]_1.
+__global__ void k_mult_offline(const u64* __restrict__ xs, const u64* __restrict__ ys,
+                               long long n, Key k01, Key k02, u32 tr1, u32 tr2, u32 tg1, u64 obj,
+                               u64* __restrict__ zs, u64* __restrict__ g2_out) {
+  const long long nb = (n + 7) / 8;
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+       b += (long long)gridDim.x * blockDim.x) {
+    u64 r1[8], r2[8], g1[8];
+    prf_block8(k01, tr1, obj, (u64)b, r1);
+    prf_block8(k02, tr2, obj, (u64)b, r2);
+    prf_block8(k01, tg1, obj, (u64)b, g1);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const long long i = b * 8 + j;
+      if (i < n) {
+        const u64 rx = xs[i] + xs[n + i];
+        const u64 ry = ys[i] + ys[n + i];
+        const u64 gamma = rx * ry + r1[j] + r2[j];
+        g2_out[i] = gamma - g1[j];
+        zs[i] = r1[j];
+        zs[n + i] = r2[j];
+        zs[3 * n + i] = r1[j];
+        zs[5 * n + i] = r2[j];
+      }
+    }
+  }
+}
+
+// Pi_Mult online: P1: [m_z]_1 = -m_x [r_y]_1 - m_y [r_x]_1 + [Gamma]_1;
+//                 P2: [m_z]_2 = m_x m_y - m_x [r_y]_2 - m_y [r_x]_2 + [Gamma]_2 (received).
+__global__ void k_mult_online(const u64* __restrict__ xs, const u64* __restrict__ ys,
+                              long long n, Key k01, u32 tg1, u64 obj,
+                              const u64* __restrict__ g2_in, u64* __restrict__ p1_out,
+                              u64* __restrict__ p2_out) {
+  const long long nb = (n + 7) / 8;
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+       b += (long long)gridDim.x * blockDim.x) {
+    u64 g1[8];
+    prf_block8(k01, tg1, obj, (u64)b, g1);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const long long i = b * 8 + j;
+      if (i < n) {
+        const u64 mx1 = xs[2 * n + i], rx1 = xs[3 * n + i];
+        const u64 my1 = ys[2 * n + i], ry1 = ys[3 * n + i];
+        p1_out[i] = g1[j] - mx1 * ry1 - my1 * rx1;
+        const u64 mx2 = xs[4 * n + i], rx2 = xs[5 * n + i];
+        const u64 my2 = ys[4 * n + i], ry2 = ys[5 * n + i];
+        p2_out[i] = mx2 * my2 - mx2 * ry2 - my2 * rx2 + g2_in[i];
+      }
+    }
+  }
+}
+
+// After the exchange: P1 holds m = own + received, P2 likewise.  With t >= 0 the truncated
+// output's m is m >>_arith t (Fig. trunc, online), written into outs (P1.m, P2.m components).
+__global__ void k_exchange_finish(long long n, const u64* __restrict__ p1_own,
+                                  const u64* __restrict__ p1_in, const u64* __restrict__ p2_own,
+                                  const u64* __restrict__ p2_in, u64* __restrict__ zs, int t,
+                                  u64* __restrict__ outs) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const u64 m1 = p1_own[i] + p1_in[i];
+    const u64 m2 = p2_in[i] + p2_own[i];
+    zs[2 * n + i] = m1;
+    zs[4 * n + i] = m2;
+    if (outs) {
+      outs[2 * n + i] = asr64(m1, t);
+      outs[4 * n + i] = asr64(m2, t);
+    }
+  }
+}
+
+// Pi_Trunc^t preprocessing, P0's part plus every party's PRG draws.  Per output e:
+//   b1 (eta01) and b2 (eta02) hold the bits b_{1,j}, b_{2,j};
+//   Pi_Inner #1 (r_x): x_j = -2^(j+1) <b1_j>, y_j = <b2_j>, z = <p>, p = -2 (b1 & b2);
+//   Pi_Inner #2 (r_z): x_j = c'_j <b1_j>, y_j = <b2_j>, z = <q>, q = -2 asr(b1 & b2, t);
+// the bit sharings have m = 0, so P1's and P2's cross terms vanish and [m]_j = [Gamma]_j.
+// P0's additive shares: [r_x]_1 = Gamma_p + b1 - [r_p]_1, [r_x]_2 = b2 - [r_p]_2 (and the same for
+// r_z with asr(b1, t), asr(b2, t), Gamma_q, r_q).
+// pq layout: <p> at pq[0..6E), <q> at pq[6E..12E).
+__global__ void k_trunc_p0(long long E, Key k01, Key k02, u64 obj, int t, u32 ttb1, u32 ttb2,
+                           u32 tp1, u32 tp2, u32 tpg, u32 tq1, u32 tq2, u32 tqg,
+                           u64* __restrict__ zpre, u64* __restrict__ zout, u64* __restrict__ pq,
+                           u64* __restrict__ gp2_out, u64* __restrict__ gq2_out,
+                           u64* __restrict__ mp1_out, u64* __restrict__ mq1_out) {
+  const long long nb = (E + 7) / 8;
+  u64* p = pq;
+  u64* q = pq + 6 * E;
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+       b += (long long)gridDim.x * blockDim.x) {
+    u64 b1[8], b2[8], rp1[8], rp2[8], gp1[8], rq1[8], rq2[8], gq1[8];
+    prf_block8(k01, ttb1, obj, (u64)b, b1);
+    prf_block8(k02, ttb2, obj, (u64)b, b2);
+    prf_block8(k01, tp1, obj, (u64)b, rp1);
+    prf_block8(k02, tp2, obj, (u64)b, rp2);
+    prf_block8(k01, tpg, obj, (u64)b, gp1);
+    prf_block8(k01, tq1, obj, (u64)b, rq1);
+    prf_block8(k02, tq2, obj, (u64)b, rq2);
+    prf_block8(k01, tqg, obj, (u64)b, gq1);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const long long e = b * 8 + j;
+      if (e >= E) continue;
+      const u64 a = b1[j] & b2[j];
+      const u64 gamma_p = (u64)0 - 2 * a + rp1[j] + rp2[j];
+      const u64 gamma_q = (u64)0 - 2 * asr64(a, t) + rq1[j] + rq2[j];
+      gp2_out[e] = gamma_p - gp1[j];
+      gq2_out[e] = gamma_q - gq1[j];
+      mp1_out[e] = gp1[j];          // P1's [m_p]_1 = [Gamma_p]_1 (its own PRG draw)
+      mq1_out[e] = gq1[j];
+      // <p>, <q> mask components (P0 copies and the pair parties' copies)
+      p[e] = rp1[j]; p[E + e] = rp2[j]; p[3 * E + e] = rp1[j]; p[5 * E + e] = rp2[j];
+      q[e] = rq1[j]; q[E + e] = rq2[j]; q[3 * E + e] = rq1[j]; q[5 * E + e] = rq2[j];
+      // P0's additive shares of r_x (mask of the product wire) and r_z (mask of the output)
+      zpre[e] = gamma_p + b1[j] - rp1[j];
+      zpre[E + e] = b2[j] - rp2[j];
+      zout[e] = gamma_q + asr64(b1[j], t) - rq1[j];
+      zout[E + e] = asr64(b2[j], t) - rq2[j];
+    }
+  }
+}
+
+// Pi_Trunc^t preprocessing, P1's and P2's part after the messages: m_p = [m_p]_1 + [m_p]_2 at each
+// of P1, P2; [r_x]_1 := m_{r_x} - [r_{r_x}]_1 at P1, [r_x]_2 := -[r_{r_x}]_2 at P2 (same for r_z).
+__global__ void k_trunc_finish(long long E, Key k01, Key k02, u64 obj, int t, u32 ttb1,
+                               u32 ttb2, const u64* __restrict__ p1_in_mp,
+                               const u64* __restrict__ p1_in_mq, const u64* __restrict__ p2_in_mp,
+                               const u64* __restrict__ p2_in_mq, const u64* __restrict__ p2_gp2,
+                               const u64* __restrict__ p2_gq2, const u64* __restrict__ p1_mp1,
+                               const u64* __restrict__ p1_mq1, u64* __restrict__ zpre,
+                               u64* __restrict__ zout, u64* __restrict__ pq) {
+  const long long nb = (E + 7) / 8;
+  u64* p = pq;
+  u64* q = pq + 6 * E;
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+       b += (long long)gridDim.x * blockDim.x) {
+    u64 b1[8], b2[8];
+    prf_block8(k01, ttb1, obj, (u64)b, b1);
+    prf_block8(k02, ttb2, obj, (u64)b, b2);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const long long e = b * 8 + j;
+      if (e >= E) continue;
+      // P1
+      const u64 mp_1 = p1_mp1[e] + p1_in_mp[e];
+      const u64 mq_1 = p1_mq1[e] + p1_in_mq[e];
+      p[2 * E + e] = mp_1;
+      q[2 * E + e] = mq_1;
+      zpre[3 * E + e] = mp_1 + b1[j] - p[3 * E + e];
+      zout[3 * E + e] = mq_1 + asr64(b1[j], t) - q[3 * E + e];
+      // P2
+      const u64 mp_2 = p2_in_mp[e] + p2_gp2[e];
+      const u64 mq_2 = p2_in_mq[e] + p2_gq2[e];
+      p[4 * E + e] = mp_2;
+      q[4 * E + e] = mq_2;
+      zpre[5 * E + e] = b2[j] - p[5 * E + e];
+      zout[5 * E + e] = asr64(b2[j], t) - q[5 * E + e];
+    }
+  }
+}
+
+__global__ void k_xor_one(u64* p, u64 mask) { *p ^= mask; }
+
+__global__ void k_prf_words(long long n, Key key, u32 tag, u64 obj, u64* __restrict__ out) {
+  const long long nb = (n + 7) / 8;
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+       b += (long long)gridDim.x * blockDim.x) {
+    u64 w[8];
+    prf_block8(key, tag, obj, (u64)b, w);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (b * 8 + j < n) out[b * 8 + j] = w[j];
+  }
+}
+
+// x = m - [r]_1 - [r]_2 from P1's view (own m, own [r]_1, received [r]_2).
+__global__ void k_open_p1(const u64* __restrict__ m, const u64* __restrict__ r1,
+                          const u64* __restrict__ r2, long long n, u64* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = m[i] - r1[i] - r2[i];
+}
+
+}  // namespace
+
+void launch_share_input(cudaStream_t st, const u64* x, long long n, Key k01, Key k02, u64 obj,
+                        u64* s6, u64* p0_out_m) {
+  if (n <= 0) return;
+  k_share_input<<<grid_for((n + 7) / 8), TPB, 0, st>>>(x, n, k01, k02, make_tag(P_SHARE, C_R1),
+                                                       make_tag(P_SHARE, C_R2), obj, s6, p0_out_m);
+}
+
+void launch_fill_masks(cudaStream_t st, long long n, Key k01, Key k02, u32 purpose, u64 obj,
+                       u64* s6) {
+  if (n <= 0) return;
+  k_fill_masks<<<grid_for((n + 7) / 8), TPB, 0, st>>>(n, k01, k02, make_tag(purpose, C_R1),
+                                                      make_tag(purpose, C_R2), obj, s6);
+}
+
+void launch_mult_offline(cudaStream_t st, const u64* xs, const u64* ys, long long n, Key k01,
+                         Key k02, u64 obj, u64* zs, u64* p0_out_g2) {
+  if (n <= 0) return;
+  k_mult_offline<<<grid_for((n + 7) / 8), TPB, 0, st>>>(
+      xs, ys, n, k01, k02, make_tag(P_MULT, C_R1), make_tag(P_MULT, C_R2),
+      make_tag(P_MULT, C_G1), obj, zs, p0_out_g2);
+}
+
+void launch_mult_online(cudaStream_t st, const u64* xs, const u64* ys, long long n, Key k01,
+                        u64 obj, const u64* p2_in_g2, u64* p1_out, u64* p2_out) {
+  if (n <= 0) return;
+  k_mult_online<<<grid_for((n + 7) / 8), TPB, 0, st>>>(xs, ys, n, k01, make_tag(P_MULT, C_G1),
+                                                       obj, p2_in_g2, p1_out, p2_out);
+}
+
+void launch_exchange_finish(cudaStream_t st, long long n, const u64* p1_own, const u64* p1_in,
+                            const u64* p2_own, const u64* p2_in, u64* zs, int t, u64* outs) {
+  if (n <= 0) return;
+  k_exchange_finish<<<grid_for(n), TPB, 0, st>>>(n, p1_own, p1_in, p2_own, p2_in, zs, t, outs);
+}
+
+void launch_trunc_p0(cudaStream_t st, long long E, Key k01, Key k02, u64 obj, int t, u64* zpre,
+                     u64* zout, u64* pq, u64* p0_out_gp2, u64* p0_out_gq2, u64* p1_out_mp,
+                     u64* p1_out_mq) {
+  if (E <= 0) return;
+  k_trunc_p0<<<grid_for((E + 7) / 8), TPB, 0, st>>>(
+      E, k01, k02, obj, t, make_tag(P_TRUNC_BITS, C_TB1), make_tag(P_TRUNC_BITS, C_TB2),
+      make_tag(P_TRUNC_P, C_R1), make_tag(P_TRUNC_P, C_R2), make_tag(P_TRUNC_P, C_G1),
+      make_tag(P_TRUNC_Q, C_R1), make_tag(P_TRUNC_Q, C_R2), make_tag(P_TRUNC_Q, C_G1), zpre, zout,
+      pq, p0_out_gp2, p0_out_gq2, p1_out_mp, p1_out_mq);
+}
+
+void launch_trunc_finish(cudaStream_t st, long long E, Key k01, Key k02, u64 obj, int t,
+                         const u64* p1_in_mp, const u64* p1_in_mq, const u64* p2_in_mp,
+                         const u64* p2_in_mq, const u64* p2_gp2, const u64* p2_gq2,
+                         const u64* p1_mp1, const u64* p1_mq1, u64* zpre, u64* zout, u64* pq) {
+  if (E <= 0) return;
+  k_trunc_finish<<<grid_for((E + 7) / 8), TPB, 0, st>>>(
+      E, k01, k02, obj, t, make_tag(P_TRUNC_BITS, C_TB1), make_tag(P_TRUNC_BITS, C_TB2), p1_in_mp,
+      p1_in_mq, p2_in_mp, p2_in_mq, p2_gp2, p2_gq2, p1_mp1, p1_mq1, zpre, zout, pq);
+}
+
+void launch_xor_one(cudaStream_t st, u64* p, u64 mask) { k_xor_one<<<1, 1, 0, st>>>(p, mask); }
+
+void launch_prf_words(cudaStream_t st, long long n, Key key, u32 tag, u64 obj, u64* out) {
+  if (n <= 0) return;
+  k_prf_words<<<grid_for((n + 7) / 8), TPB, 0, st>>>(n, key, tag, obj, out);
+}
+
+void launch_open_p1(cudaStream_t st, const u64* m, const u64* r1, const u64* r2, long long n,
+                    u64* out) {
+  if (n <= 0) return;
+  k_open_p1<<<grid_for(n), TPB, 0, st>>>(m, r1, r2, n, out);
+}
+
+}  // namespace mpc3

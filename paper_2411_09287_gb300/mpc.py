@@ -1,0 +1,260 @@
+"""Thin Python binding of libmpc3 (include/mpc3.h).
+
+Every method marshals arguments and calls the C-ABI of the same name; all protocol work runs in
+the library's CUDA kernels.  PyTorch is used only to allocate device memory (sharings, workspace,
+traces) and to supply the CUDA stream.  There is no CPU fallback: constructing a ``Context``
+without a CUDA device or without the built library raises.
+
+Sharings are int64 CUDA tensors holding u64 bit patterns, 6*n words each, component order
+(P0.[r]_1, P0.[r]_2, P1.m, P1.[r]_1, P2.m, P2.[r]_2).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+
+MPC_OK, MPC_ERR_ARG, MPC_ERR_SHAPE, MPC_ERR_WORKSPACE, MPC_ERR_CUDA = 0, 1, 2, 3, 4
+MPC_ERR_TIMEOUT, MPC_ERR_VERIFY, MPC_ERR_ABORT, MPC_ERR_PENDING = 5, 6, 7, 8
+REDUCE_POINT_X, REDUCE_POINT_2 = 0, 1
+GEMM_U64, GEMM_LIMB_TC = 0, 1
+OP_SHARE, OP_MULT, OP_MATMUL, OP_VERIFY_MULT, OP_VERIFY_MATMUL, OP_RECONSTRUCT = range(6)
+SITES = {"GAMMA2": 0, "MZ1": 1, "MZ2": 2, "MX_COPY_P1": 3, "REC_MSG": 4, "HIGH_BIT": 5}
+PHASES = ("offline", "online", "verify")
+PROTOS = ("share", "mult", "inner", "trunc", "rec", "verify")
+TRACE_ROUND = 832
+PROF_PHASES = ("share", "mult", "trunc_pairs", "gemm", "exchange", "verify_gemm", "trunc_setup",
+               "trunc_s", "trunc_rounds", "trunc_materialize", "trunc_tail", "rec", "verify_mult")
+ERR_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_WORKSPACE", 4: "ERR_CUDA",
+             5: "ERR_TIMEOUT", 6: "ERR_VERIFY", 7: "ERR_ABORT", 8: "ERR_PENDING"}
+
+
+class MpcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libmpc3 needs a CUDA device (no CPU fallback)")
+    return torch
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def default_R(D: int) -> int:
+    if D <= 1:
+        return 0
+    return max(0, int(np.ceil(np.log2(D))) - 6)
+
+
+class Context:
+    """One three-party run: keys from `seed`, ledger, abort state; work on the current stream."""
+
+    def __init__(self, seed: bytes, device: int = 0, reduce_mode: int = REDUCE_POINT_X,
+                 gemm_path: int = GEMM_U64, stream=None):
+        torch = _torch()
+        self.torch = torch
+        self.lib = _lib.load()
+        assert len(seed) == 32
+        self.device = torch.device("cuda", device)
+        cfg = _lib.MpcConfig()
+        for i, b in enumerate(seed):
+            cfg.seed[i] = b
+        cfg.device = device
+        cfg.reduce_mode = reduce_mode
+        cfg.gemm_path = gemm_path
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        cfg.stream = C.c_void_p(stream.cuda_stream)
+        h = C.c_void_p()
+        rc = self.lib.mpc_create(C.byref(cfg), C.byref(h))
+        if rc != MPC_OK:
+            raise MpcError(rc, "mpc_create failed")
+        self.h = h
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mpc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- helpers -------------------------------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != MPC_OK:
+            raise MpcError(rc, self.lib.mpc_last_error(self.h).decode())
+        return rc
+
+    def empty(self, nwords: int):
+        return self.torch.empty(max(int(nwords), 1), dtype=self.torch.int64, device=self.device)
+
+    def shares(self, n: int):
+        return self.empty(6 * n)
+
+    def workspace(self, nbytes: int):
+        """Grow-only workspace tensor (256-byte aligned by the caching allocator)."""
+        nwords = (int(nbytes) + 7) // 8 + 32
+        if self._ws is None or self._ws.numel() < nwords:
+            self._ws = None
+            self._ws = self.torch.empty(nwords, dtype=self.torch.int64, device=self.device)
+        return self._ws
+
+    def ws_size(self, op: int, a: int, b: int = 0, c: int = 0, trunc_bits: int = -1,
+                R_main: int = -1, R_trunc: int = -1) -> int:
+        v = self.lib.mpc_workspace_size(self.h, op, a, b, c, trunc_bits, R_main, R_trunc)
+        if v < 0:
+            raise MpcError(MPC_ERR_ARG, "bad workspace query")
+        return int(v)
+
+    # ---- protocols -------------------------------------------------------------------------------
+    def share_input(self, call_id: int, x, out=None):
+        """Pi_<.>^{l,0}(x).  x: CUDA int64 tensor (device input) or numpy uint64 array (host)."""
+        if isinstance(x, np.ndarray):
+            xh = np.ascontiguousarray(x, dtype=np.uint64)
+            n = xh.size
+            ptr, on_host = xh.ctypes.data, 1
+        else:
+            n = x.numel()
+            ptr, on_host = _ptr(x), 0
+        out = self.shares(n) if out is None else out
+        wsb = self.ws_size(OP_SHARE, n)
+        ws = self.workspace(wsb)
+        self._check(self.lib.mpc_share_input(self.h, call_id, C.c_void_p(ptr), on_host, n,
+                                             C.c_void_p(_ptr(out)), C.c_void_p(_ptr(ws)), wsb))
+        if on_host:   # the host buffer must stay alive until the copy ran
+            self.sync()
+        return out
+
+    def mult(self, call_id: int, xs, ys, n: int, out=None):
+        out = self.shares(n) if out is None else out
+        wsb = self.ws_size(OP_MULT, n)
+        ws = self.workspace(wsb)
+        self._check(self.lib.mpc_mult(self.h, call_id, C.c_void_p(_ptr(xs)), C.c_void_p(_ptr(ys)),
+                                      n, C.c_void_p(_ptr(out)), C.c_void_p(_ptr(ws)), wsb))
+        return out
+
+    def matmul(self, call_id: int, xs, ws_, M: int, N: int, K: int, trunc_bits: int = -1,
+               zpre=None, zout=None, pq=None):
+        E = M * N
+        zpre = self.shares(E) if zpre is None else zpre
+        if trunc_bits >= 0:
+            zout = self.shares(E) if zout is None else zout
+            pq = self.empty(12 * E) if pq is None else pq
+        wsb = self.ws_size(OP_MATMUL, M, N, K, trunc_bits)
+        ws = self.workspace(wsb)
+        self._check(self.lib.mpc_matmul(self.h, call_id, C.c_void_p(_ptr(xs)), C.c_void_p(_ptr(ws_)),
+                                        M, N, K, trunc_bits, C.c_void_p(_ptr(zpre)),
+                                        C.c_void_p(_ptr(zout)), C.c_void_p(_ptr(pq)),
+                                        C.c_void_p(_ptr(ws)), wsb))
+        return zpre, (zout if trunc_bits >= 0 else zpre), pq
+
+    def verify_mult(self, verify_id: int, xs, ys, zs, n: int, mult_call_id: int, R: int = -1,
+                    trace: bool = False):
+        """Returns (code, trace): code MPC_OK (accept), MPC_ERR_VERIFY or MPC_ERR_ABORT."""
+        Rr = default_R(n) if R < 0 else R
+        tr = self.empty((Rr + 1) * TRACE_ROUND) if trace else None
+        wsb = self.ws_size(OP_VERIFY_MULT, n, R_main=R)
+        ws = self.workspace(wsb)
+        rc = self.lib.mpc_verify_mult(self.h, verify_id, C.c_void_p(_ptr(xs)), C.c_void_p(_ptr(ys)),
+                                      C.c_void_p(_ptr(zs)), n, mult_call_id, R,
+                                      C.c_void_p(_ptr(ws)), wsb, C.c_void_p(_ptr(tr)))
+        if rc not in (MPC_OK, MPC_ERR_VERIFY, MPC_ERR_ABORT):
+            self._check(rc)
+        return rc, tr
+
+    def verify_matmul(self, verify_id: int, xs, ws_, zpre, pq, M: int, N: int, K: int,
+                      trunc_bits: int, matmul_call_id: int, R_main: int = -1, R_trunc: int = -1,
+                      trace: bool = False):
+        R0 = default_R(K) if R_main < 0 else R_main
+        R1 = default_R(64 * M * N) if R_trunc < 0 else R_trunc
+        ntr = (R0 + 1) * TRACE_ROUND + ((R1 + 1) * TRACE_ROUND if trunc_bits >= 0 else 0)
+        tr = self.empty(ntr) if trace else None
+        wsb = self.ws_size(OP_VERIFY_MATMUL, M, N, K, trunc_bits, R_main, R_trunc)
+        ws = self.workspace(wsb)
+        rc = self.lib.mpc_verify_matmul(self.h, verify_id, C.c_void_p(_ptr(xs)), C.c_void_p(_ptr(ws_)),
+                                        C.c_void_p(_ptr(zpre)), C.c_void_p(_ptr(pq)), M, N, K,
+                                        trunc_bits, matmul_call_id, R_main, R_trunc,
+                                        C.c_void_p(_ptr(ws)), wsb, C.c_void_p(_ptr(tr)))
+        if rc not in (MPC_OK, MPC_ERR_VERIFY, MPC_ERR_ABORT):
+            self._check(rc)
+        return rc, tr
+
+    def reconstruct(self, xs, n: int, to_host: bool = True):
+        """Pi_Rec; returns a numpy uint64 array (host) or an int64 CUDA tensor."""
+        wsb = self.ws_size(OP_RECONSTRUCT, n)
+        ws = self.workspace(wsb)
+        if to_host:
+            out = np.empty(n, dtype=np.uint64)
+            rc = self.lib.mpc_reconstruct(self.h, C.c_void_p(_ptr(xs)), n,
+                                          C.c_void_p(out.ctypes.data), 1, C.c_void_p(_ptr(ws)), wsb)
+        else:
+            out = self.empty(n)
+            rc = self.lib.mpc_reconstruct(self.h, C.c_void_p(_ptr(xs)), n, C.c_void_p(_ptr(out)),
+                                          0, C.c_void_p(_ptr(ws)), wsb)
+        self._check(rc)
+        return out
+
+    def ledger(self):
+        b = (C.c_uint64 * 18)()
+        m = C.c_uint64()
+        self._check(self.lib.mpc_ledger(self.h, b, C.byref(m)))
+        out = {(PHASES[i // 6], PROTOS[i % 6]): int(b[i]) for i in range(18)}
+        return out, int(m.value)
+
+    def ledger_reset(self):
+        self.lib.mpc_ledger_reset(self.h)
+
+    def inject_fault(self, site: str, index: int, xor_mask: int = 1):
+        self._check(self.lib.mpc_inject_fault(self.h, SITES[site], index, xor_mask))
+
+    def status(self) -> int:
+        return self.lib.mpc_status(self.h)
+
+    def profile(self, enable: bool):
+        self._check(self.lib.mpc_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{phase name: (milliseconds, intervals)} since the last read (waits for the stream)."""
+        ms = (C.c_double * len(PROF_PHASES))()
+        cnt = (C.c_uint64 * len(PROF_PHASES))()
+        self._check(self.lib.mpc_profile_read(self.h, ms, cnt))
+        return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(PROF_PHASES)}
+
+    def launch_count(self) -> int:
+        return int(self.lib.mpc_launch_count())
+
+    def sync(self):
+        self._check(self.lib.mpc_sync(self.h))
+
+
+def to_u64(t) -> np.ndarray:
+    """Device int64 tensor -> host numpy uint64 (bit pattern)."""
+    return t.detach().cpu().numpy().view(np.uint64)
+
+
+def from_u64(ctx: Context, a: np.ndarray):
+    """Host numpy uint64 -> device int64 tensor (bit pattern)."""
+    t = ctx.torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64))
+    return t.to(ctx.device)
+
+
+def encode_fixed(x, k: int) -> np.ndarray:
+    """Sec. 2 fixed-point encoding: floor(x 2^k) mod 2^64 (two's complement for x < 0)."""
+    return np.floor(np.asarray(x, dtype=np.float64) * float(1 << k)).astype(np.int64).astype(np.uint64)
+
+
+def decode_fixed(v, k: int) -> np.ndarray:
+    return np.asarray(v, dtype=np.uint64).astype(np.int64).astype(np.float64) / float(1 << k)
