@@ -175,7 +175,7 @@ def test_matmul_verify_transcript_matches_oracle(mpc, M, N, K, t, mode):
     check_trace(mpc, tr, otr, Rs)
     assert_ledger(mpc, ctx, sess)
     out = ctx.reconstruct(zout, M * N)
-    assert np.array_equal(out, OP.reconstruct(sess, res.out))
+    assert np.array_equal(out, OP.reconstruct(sess, res.out).reshape(-1))
 
 
 @pytest.mark.parametrize("R_main,R_trunc", [(0, 0), (2, 3), (7, 9)])
