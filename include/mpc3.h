@@ -162,6 +162,22 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
 int mpc_reconstruct(mpc_ctx* ctx, const uint64_t* xs, int64_t n, uint64_t* out, int out_on_host,
                     void* workspace, size_t workspace_bytes);
 
+/* Pi_Rec without any device allocation: the same protocol, messages, checks and result as
+ * mpc_reconstruct with a device output, but the received shares and the hash scratch live in
+ * one fixed device array compiled into the library instead of a caller-provided workspace.  The
+ * paper has no counterpart; this serves callers that cannot allocate device memory when they
+ * reconstruct (a process whose free device memory is all held by its own pool, or a loop that
+ * must not call cudaMalloc/cudaFree because they may synchronise the device).
+ *   n: 1 .. MPC_NOALLOC_MAX_N elements, else MPC_ERR_SHAPE; out: n device words (written).
+ *   The array costs about 6 MiB on every GPU that loads the library, for the life of the
+ *   process.  The first call on a device resolves the array's address there; make that first
+ *   call before any stream capture.  All calls share the array, so calls that can overlap on the
+ *   GPU (other streams or contexts on the same device) race and must be serialised.
+ *   Returns MPC_ERR_ABORT on inconsistent messages, MPC_ERR_PENDING while products are
+ *   unverified. */
+#define MPC_NOALLOC_MAX_N 262144
+int mpc_reconstruct_noalloc(mpc_ctx* ctx, const uint64_t* xs, int64_t n, uint64_t* out);
+
 /* Ledger: bytes[phase * MPC_NPROTO + proto] of every message sent so far, and the message
  * count.  Hash messages count 32 bytes. */
 int mpc_ledger(const mpc_ctx* ctx, uint64_t* bytes, uint64_t* messages);

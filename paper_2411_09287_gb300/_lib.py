@@ -44,6 +44,7 @@ _SIGS = {
     "mpc_ledger": (C.c_int, [C.c_void_p, c_u64p, c_u64p]),
     "mpc_ledger_reset": (None, [C.c_void_p]),
     "mpc_inject_fault": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_uint64]),
+    "mpc_reconstruct_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "mpc_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "mpc_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), c_u64p]),
     "mpc_launch_count": (C.c_uint64, []),

@@ -1253,3 +1253,22 @@ int mpc_profile_read(mpc_ctx* ctx, double* ms, uint64_t* count) {
 uint64_t mpc_launch_count(void) { return g_launches; }
 
 }  // extern "C"
+
+// ---- accessors for other translation units of the library (not part of the C-ABI) ----------
+namespace mpc3 {
+namespace internal {
+int ctx_guard(mpc_ctx* c) { return guard(c); }
+int ctx_fail(mpc_ctx* c, int code, const char* msg) { return fail(c, code, msg); }
+int ctx_deliver(mpc_ctx* c, int phase, int proto, const u64* src, u64* dst, long long n, int site) {
+  return deliver(c, phase, proto, src, dst, n, site);
+}
+void ctx_count(mpc_ctx* c, int phase, int proto, int count, u64 bytes_each) {
+  count_msgs(c, phase, proto, count, bytes_each);
+}
+int ctx_read_status(mpc_ctx* c, u32* out) { return read_status(c, out); }
+bool ctx_has_pending(const mpc_ctx* c) { return !c->pending.empty(); }
+cudaStream_t ctx_stream(const mpc_ctx* c) { return c->st; }
+u32* ctx_status_word(const mpc_ctx* c) { return c->status; }
+void ctx_set_aborted(mpc_ctx* c) { c->aborted = true; }
+}  // namespace internal
+}  // namespace mpc3

@@ -25,6 +25,7 @@ SITES = {"GAMMA2": 0, "MZ1": 1, "MZ2": 2, "MX_COPY_P1": 3, "REC_MSG": 4, "HIGH_B
 PHASES = ("offline", "online", "verify")
 PROTOS = ("share", "mult", "inner", "trunc", "rec", "verify")
 TRACE_ROUND = 832
+NOALLOC_MAX_N = 262144
 PROF_PHASES = ("share", "mult", "trunc_pairs", "gemm", "exchange", "verify_gemm", "trunc_setup",
                "trunc_s", "trunc_rounds", "trunc_materialize", "trunc_tail", "rec", "verify_mult")
 ERR_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_WORKSPACE", 4: "ERR_CUDA",
@@ -205,6 +206,15 @@ class Context:
             rc = self.lib.mpc_reconstruct(self.h, C.c_void_p(_ptr(xs)), n, C.c_void_p(_ptr(out)),
                                           0, C.c_void_p(_ptr(ws)), wsb)
         self._check(rc)
+        return out
+
+    def reconstruct_noalloc(self, xs, n: int, out=None):
+        """Pi_Rec through mpc_reconstruct_noalloc: the library uses its fixed device array as
+        scratch and allocates nothing (for callers that cannot allocate at this point); n must
+        not exceed NOALLOC_MAX_N.  Returns the int64 CUDA tensor it wrote."""
+        out = self.empty(n) if out is None else out
+        self._check(self.lib.mpc_reconstruct_noalloc(self.h, C.c_void_p(_ptr(xs)), n,
+                                                     C.c_void_p(_ptr(out))))
         return out
 
     def ledger(self):
