@@ -63,6 +63,10 @@ inline void counted(int k, F f, A... a) {
 #define launch_gr_quad_combine(...) counted(1, mpc3::launch_gr_quad_combine, __VA_ARGS__)
 #define launch_mode_consts(...) counted(1, mpc3::launch_mode_consts, __VA_ARGS__)
 #define launch_prf_words(...) counted(1, mpc3::launch_prf_words, __VA_ARGS__)
+#define launch_trunc_limb_table(...) counted(1, mpc3::launch_trunc_limb_table, __VA_ARGS__)
+#define launch_trunc_s_mma(...) counted(1, mpc3::launch_trunc_s_mma, __VA_ARGS__)
+#define launch_trunc_bit_bytes(...) counted(1, mpc3::launch_trunc_bit_bytes, __VA_ARGS__)
+#define launch_fold_reduce_strided(...) counted(1, mpc3::launch_fold_reduce_strided, __VA_ARGS__)
 
 namespace {
 
@@ -444,10 +448,28 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
   u64* S11 = s.S + 576;
   u64* Sh2 = s.S + 768;
   int rc;
-  if ((rc = party_sums(ctx, f[0], g[0], Dh, s.Pmat, S00))) return rc;
-  if ((rc = party_sums(ctx, f[0], g[1], Dh, s.Pmat + 3 * 4096, S01))) return rc;
-  if ((rc = party_sums(ctx, f[1], g[0], Dh, s.Pmat + 6 * 4096, S10))) return rc;
-  if ((rc = party_sums(ctx, f[1], g[1], Dh, s.Pmat + 9 * 4096, S11))) return rc;
+  // Shape of the truncation batch's dense rounds: x holds only [r]_1 (P0, P1 copies), y only
+  // [r]_2 (P0, P2 copies), so P1's and P2's cross terms vanish and P0's sums are single Grams.
+  const bool bit_form = x.c[0] && !x.c[1] && !x.c[2] && x.c[3] && !x.c[4] && !x.c[5] &&
+                        !y.c[0] && y.c[1] && !y.c[2] && !y.c[3] && !y.c[4] && y.c[5];
+  if (bit_form) {
+    // G00, G11 and G(x0 + x1, y0 + y1); G01 + G10 = G(x0 + x1, y0 + y1) - G00 - G11
+    CK(cudaMemsetAsync(s.Pmat, 0, 3 * 4096 * 8, st));
+    CK(cudaMemsetAsync(s.S, 0, 4 * 192 * 8, st));
+    gram(ctx, s.Pmat, x.c[0], nullptr, 1, 128, y.c[1], nullptr, 1, 128, Dh, 1);
+    gram(ctx, s.Pmat + 4096, x.c[0] + 64, nullptr, 1, 128, y.c[1] + 64, nullptr, 1, 128, Dh, 1);
+    gram(ctx, s.Pmat + 8192, x.c[0], x.c[0] + 64, 1, 128, y.c[1], y.c[1] + 64, 1, 128, Dh, 1);
+    launch_gr_fold_reduce(st, s.Pmat, 3, s.aux);            // aux: G00, G11, Gsum (64 each)
+    CK(cudaMemcpyAsync(S00, s.aux, 512, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(S11, s.aux + 64, 512, cudaMemcpyDeviceToDevice, st));
+    launch_gr_lincomb(st, ctx->cst + CST_ONE, s.aux + 128, ctx->cst + CST_MONE, s.aux, s.aux + 192);
+    launch_gr_lincomb(st, ctx->cst + CST_ONE, s.aux + 192, ctx->cst + CST_MONE, s.aux + 64, S01);
+  } else {
+    if ((rc = party_sums(ctx, f[0], g[0], Dh, s.Pmat, S00))) return rc;
+    if ((rc = party_sums(ctx, f[0], g[1], Dh, s.Pmat + 3 * 4096, S01))) return rc;
+    if ((rc = party_sums(ctx, f[1], g[0], Dh, s.Pmat + 6 * 4096, S10))) return rc;
+    if ((rc = party_sums(ctx, f[1], g[1], Dh, s.Pmat + 9 * 4096, S11))) return rc;
+  }
   launch_gr_quad_combine(st, ctx->cst + CST_LAM, S00, S01, S10, S11, Sh2);
   const u64 obj = make_obj(vid, batch, (u32)k);
   inner_finish(ctx, S00, P_VER_H0, obj, s.h0);
@@ -455,16 +477,20 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
   reveal(ctx, P_VER_ZETA, obj, s.tmp6, s.zp);
   launch_gr_lagrange(st, s.zp, ctx->reduce_mode, ctx->cst + CST_INV, s.coef);
   launch_gr_combine_z(st, s.coef, s.h0, s.h2, z, zo);
-  launch_gr_mulmat2(st, s.coef + 384, s.coef, s.MM);   // [M_{1-zeta}; M_zeta]
+  launch_gr_mulmat2(st, s.coef, nullptr, s.MM);   // M_zeta
   for (int c = 0; c < 6; ++c) {
     for (int side = 0; side < 2; ++side) {
       const u64* in = side ? y.c[c] : x.c[c];
       u64* out = side ? yo.c[c] : xo.c[c];
       if (!in) continue;
+      // f(zeta) = f(0) + zeta (f(1) - f(0)): rows [x_{2i+1} - x_{2i}] times M_zeta, plus x_{2i}
       GemmTerm T;
-      T.A = op(in, 128);
+      T.A = op(in + 64, 128, 0, in, ~0ull);
       T.B = op(s.MM, 64);
-      gemm_u64(st, Dh, 64, 128, 1, &T, epi_store(out, 64), 1);
+      Epi e = epi_store(out, 64);
+      e.add0 = in;
+      e.ld_add0 = 128;
+      gemm_u64(st, Dh, 64, 64, 1, &T, e, 1);
     }
   }
   trace_round(ctx, trace, k, s);
@@ -683,7 +709,9 @@ struct VMatPlan {
   bool trunc;
   int R1, kd;
   long long Dt;
-  u64 *b1, *b2, *Rtab, *S, *Zpq, *V, *W, *hsum, *S3, *zt;
+  long long L, Epad, nhi;    // S = sum over e_hi < nhi of T_hi (x) (sum over e_lo < L ...)
+  u64 *b1, *b2, *Rtab, *S, *Zpq, *V, *W, *hsum, *S3, *zt, *S_hi, *Pst, *Thi, *Mhi;
+  unsigned char *TL8, *BB1, *BB2;
   Dense dt;
   IVBuf ivt;
 };
@@ -706,10 +734,20 @@ VMatPlan plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R
     p.R1 = R1 < 0 ? default_R(D0) : R1;
     p.kd = std::min(p.R1, 6);
     p.Dt = E * (64 >> p.kd);
-    p.b1 = a.take<u64>(E);
-    p.b2 = a.take<u64>(E);
-    p.Rtab = a.take<u64>(E * 64);
+    p.L = E >= 65536 ? 65536 : ((E + 127) / 128) * 128;
+    p.Epad = ((E + p.L - 1) / p.L) * p.L;
+    p.nhi = p.Epad / p.L;
+    p.b1 = a.take<u64>(p.Epad);
+    p.b2 = a.take<u64>(p.Epad);
+    p.Rtab = a.take<u64>(p.Epad * 64);
     p.S = a.take<u64>(4096 * 64);
+    p.TL8 = a.take<unsigned char>(1024 * p.L);
+    p.BB1 = a.take<unsigned char>(64 * p.Epad);
+    p.BB2 = a.take<unsigned char>(64 * p.Epad);
+    p.S_hi = a.take<u64>(p.nhi * 4096 * 64);
+    p.Pst = a.take<u64>(64ll * 262144);
+    p.Thi = a.take<u64>(p.nhi * 64);
+    p.Mhi = a.take<u64>(4096);
     p.Zpq = a.take<u64>(12 * 64);
     p.V = a.take<u64>(4096);
     p.W = a.take<u64>(4096);
@@ -1090,10 +1128,27 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
     launch_trunc_u(st, s.r, trunc_bits, p.V);                         // V_j = u_j
     for (int j = 0; j < 64; ++j)
       CK(cudaMemcpyAsync(p.W + j * 64, ctx->cst + CST_ONE, 512, cudaMemcpyDeviceToDevice, st));
+    if (p.Epad > E) {
+      CK(cudaMemsetAsync(p.b1 + E, 0, (size_t)(p.Epad - E) * 8, st));
+      CK(cudaMemsetAsync(p.b2 + E, 0, (size_t)(p.Epad - E) * 8, st));
+    }
     launch_prf_words(st, E, ctx->k01, make_tag(P_TRUNC_BITS, C_TB1), mobj, p.b1);
     launch_prf_words(st, E, ctx->k02, make_tag(P_TRUNC_BITS, C_TB2), mobj, p.b2);
     launch_gr_mul1(st, s.r, s.r, s.aux + 64);                          // r^2
-    launch_gr_powers(st, s.aux + 64, E, p.Rtab);                       // r^(2e)
+    // r^(2e) for e < Epad: r^(2 e_lo) for e_lo < L by repeated multiplication, then every further
+    // block of L rows is that block times the constant r^(2 L e_hi) (a 64 x 64 matrix product)
+    launch_gr_powers(st, s.aux + 64, p.L, p.Rtab);
+    if (p.nhi > 1) {
+      launch_gr_mul1(st, p.Rtab + (p.L - 1) * 64, s.aux + 64, s.aux + 128);   // r^(2L)
+      launch_gr_powers(st, s.aux + 128, p.nhi, p.Thi);
+      for (long long h = 1; h < p.nhi; ++h) {
+        launch_gr_mulmat2(st, p.Thi + h * 64, nullptr, p.Mhi);
+        GemmTerm T;
+        T.A = op(p.Rtab, 64);
+        T.B = op(p.Mhi, 64);
+        gemm_u64(st, p.L, 64, 64, 1, &T, epi_store(p.Rtab + h * p.L * 64, 64), 1);
+      }
+    }
     CK(cudaMemsetAsync(p.Zpq, 0, 12 * 64 * 8, st));
     {  // sum_e r^(2e) p_c[e], sum_e r^(2e) q_c[e]: (12 x E) . (E x 64)
       GemmTerm T;
@@ -1107,12 +1162,17 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
                         z0 + c * 64);
     delete phase;
     phase = new Phase(ctx, MPC_PROF_TRUNC_S);
-    CK(cudaMemsetAsync(p.S, 0, 4096 * 64 * 8, st));
-    {  // S_{j,j'} = sum_e r^(2e) b1_{e,j} b2_{e,j'}  (P0; bit-product operand)
+    {  // S_{j,j'} = sum_e r^(2e) b1_{e,j} b2_{e,j'} (P0), with r^(2e) = r^(2 L e_hi) r^(2 e_lo):
+       // tensor cores for the inner sums over e_lo, then sum_{e_hi} T_hi (x) S_hi as a GEMM + fold
+      launch_trunc_limb_table(st, p.Rtab, p.L, p.TL8);
+      launch_trunc_bit_bytes(st, p.b1, p.Epad, p.BB1);
+      launch_trunc_bit_bytes(st, p.b2, p.Epad, p.BB2);
+      launch_trunc_s_mma(st, p.BB1, p.BB2, p.Epad, p.TL8, p.L, p.nhi, p.S_hi);
       GemmTerm T;
-      T.A = op(p.b1, 0, 2, p.b2, 1);
-      T.B = op(p.Rtab, 64);
-      gemm_u64(st, 4096, 64, E, 1, &T, epi_atomic(p.S, 64), nsplit_for(E) > 64 ? 64 : nsplit_for(E));
+      T.A = op(p.Rtab, p.L * 64, 1);       // A[a][e_hi] = coefficient a of r^(2 L e_hi)
+      T.B = op(p.S_hi, 262144);            // B[e_hi][(p, b)]
+      gemm_u64(st, 64, 262144, p.nhi, 1, &T, epi_store(p.Pst, 262144), 1);
+      launch_fold_reduce_strided(st, p.Pst, 262144, 4096, p.S);
     }
     delete phase;
     phase = new Phase(ctx, MPC_PROF_TRUNC_ROUNDS);

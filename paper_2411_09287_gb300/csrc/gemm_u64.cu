@@ -25,8 +25,12 @@ __device__ __forceinline__ u64 ld_opnd(const Opnd& o, long long r, long long c, 
   }
   const long long off = o.trans ? (c * o.ld + r) : (r * o.ld + c);
   u64 v = o.p0[off];
-  if (o.p1) v += o.s1 * o.p1[off];
-  return o.scale * v;
+  if (o.p1) {   // the coefficients used are +-1: avoid the 3-IMAD u64 multiply for them
+    const u64 w = o.p1[off];
+    v = (o.s1 == 1ull) ? v + w : ((o.s1 == ~0ull) ? v - w : v + o.s1 * w);
+  }
+  if (o.scale != 1ull) v = (o.scale == ~0ull) ? (0ull - v) : o.scale * v;
+  return v;
 }
 
 template <int BM, int BN, int BK, int TM, int TN>
@@ -150,12 +154,13 @@ gemm_u64_kernel(long long M, long long N, long long K, int nterms, GemmTerm t0, 
       const long long c = cbase + j;
       if (c >= N) continue;
       const long long idx = r * epi.ldc + c;
-      const u64 v = epi.acc_sign * acc[i][j];
+      const u64 v = (epi.acc_sign == 1ull) ? acc[i][j]
+                  : ((epi.acc_sign == ~0ull) ? 0ull - acc[i][j] : epi.acc_sign * acc[i][j]);
       if (epi.atomic) {
         atomicAdd(reinterpret_cast<unsigned long long*>(epi.out + idx), v);
       } else {
         u64 o = v;
-        if (epi.add0) o += epi.add0[idx];
+        if (epi.add0) o += epi.add0[epi.ld_add0 ? r * epi.ld_add0 + c : idx];
         if (epi.add1) o += epi.add1[idx];
         o += epi.prf_sign * prfw[j];
         epi.out[idx] = o;
@@ -172,7 +177,12 @@ void gemm_u64(cudaStream_t st, long long M, long long N, long long K, int nterms
   if (nsplit < 1) nsplit = 1;
   const long long kps = (K + nsplit - 1) / nsplit;
   GemmTerm t1 = (nterms > 1) ? terms[1] : terms[0];
-  if (N <= 64) {
+  if (M <= 64 && N <= 64) {   // Gram sums (64 x 64 outputs, long K)
+    constexpr int BM = 64, BN = 64, BK = 8, TM = 4, TN = 4;
+    dim3 grid(1, 1, (unsigned)nsplit);
+    gemm_u64_kernel<BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(
+        M, N, K, nterms, terms[0], t1, epi, kps);
+  } else if (N <= 64) {
     constexpr int BM = 128, BN = 64, BK = 8, TM = 8, TN = 4;
     dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)nsplit);
     gemm_u64_kernel<BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(

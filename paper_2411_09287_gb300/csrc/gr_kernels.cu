@@ -402,36 +402,61 @@ __global__ void k_trunc_update_vw(u64* __restrict__ V, u64* __restrict__ W, int 
 
 // Materialise a folded truncation-batch vector after kd rounds:
 // out[e * (64 >> kd) + jp] = [R_e *] sum_{j >> kd == jp} VW_j * (-bit_j(words[e])).
-// 64 threads per block; VW in shared memory; R (optional) holds r^(2e).
-__global__ void k_trunc_materialize(long long E, const u64* __restrict__ words,
-                                    const u64* __restrict__ VW, const u64* __restrict__ R, int kd,
-                                    u64* __restrict__ out) {
+// 256 threads = 4 groups of 64; group g handles every 4th output, thread t of a group computes
+// coefficient t.  The product R_e * X uses one uniform 64-step loop per thread: step i adds
+// R_i X_{(t-i) mod 64} to the low coefficient t (i <= t) or to the high coefficient 64 + t
+// (i > t), followed by the reduction mod f.  VW in shared memory; R (optional) holds r^(2e).
+__global__ void __launch_bounds__(256)
+k_trunc_materialize(long long E, const u64* __restrict__ words, const u64* __restrict__ VW,
+                    const u64* __restrict__ R, int kd, u64* __restrict__ out) {
   __shared__ u64 vw[64 * 64];
-  __shared__ u64 acc[64], rr[64], scr[128];
-  const int t = threadIdx.x;
-  for (int i = t; i < 4096; i += blockDim.x) vw[i] = VW[i];
+  __shared__ u64 xs[4][64], rr[4][64], hp[4][64];
+  const int tid = threadIdx.x;
+  const int g = tid >> 6, t = tid & 63;
+  for (int i = tid; i < 4096; i += blockDim.x) vw[i] = VW[i];
   __syncthreads();
   const int per = 64 >> kd;
   const int bs = 1 << kd;
   const long long nout = E * per;
-  for (long long o = blockIdx.x; o < nout; o += gridDim.x) {
-    const long long e = o / per;
-    const int jp = (int)(o % per);
-    const u64 w = words[e];
+  for (long long ob = (long long)blockIdx.x * 4; ob < nout; ob += (long long)gridDim.x * 4) {
+    const long long o = ob + g;
+    const bool live = o < nout;
     u64 s = 0;
-    for (int q = 0; q < bs; ++q) {
-      const int j = jp * bs + q;
-      if ((w >> j) & 1ull) s -= vw[j * 64 + t];
+    long long e = 0;
+    if (live) {
+      e = o / per;
+      const int jp = (int)(o % per);
+      const u64 w = words[e] >> (jp * bs);
+      for (int q = 0; q < bs; ++q)
+        if ((w >> q) & 1ull) s -= vw[(jp * bs + q) * 64 + t];
     }
     if (R) {
-      acc[t] = s;
-      rr[t] = R[e * 64 + t];
+      xs[g][t] = s;
+      rr[g][t] = live ? R[e * 64 + t] : 0ull;
       __syncthreads();
-      gr_mul_block(rr, acc, acc, scr);
-      s = acc[t];
+      u64 lo = 0, hi = 0;
+#pragma unroll 8
+      for (int i = 0; i < 64; ++i) {
+        const u64 pr = rr[g][i] * xs[g][(t - i) & 63];
+        if (i <= t) lo += pr; else hi += pr;
+      }
+      hp[g][t] = (t < 63) ? hi : 0ull;   // coefficient 64 + t of the product (t = 63: none)
+      __syncthreads();
+      const u64* h = hp[g];
+      s = lo - gr_hg(h, t);
+      if (t < 7) {
+        u64 h2[3];
+        for (int m = 0; m < 3; ++m) h2[m] = gr_hg(h, 64 + m);
+        u64 gg = 0;
+        if (t < 3) gg += h2[t];
+        if (t - 1 >= 0 && t - 1 < 3) gg += h2[t - 1];
+        if (t - 3 >= 0 && t - 3 < 3) gg += h2[t - 3];
+        if (t - 4 >= 0 && t - 4 < 3) gg += h2[t - 4];
+        s += gg;
+      }
     }
-    out[o * 64 + t] = s;
-    __syncthreads();
+    if (live) out[o * 64 + t] = s;
+    if (R) __syncthreads();   // xs/rr/hp are rewritten by the next iteration
   }
 }
 
@@ -640,8 +665,9 @@ void launch_trunc_materialize(cudaStream_t st, long long E, const u64* words, co
                               const u64* R, int kd, u64* out) {
   if (E <= 0) return;
   long long nout = E * (64 >> kd);
-  long long g = nout < (1ll << 16) ? nout : (1ll << 16);
-  k_trunc_materialize<<<(unsigned)g, 64, 0, st>>>(E, words, VW, R, kd, out);
+  long long g = (nout + 3) / 4;
+  if (g > 152 * 16) g = 152 * 16;
+  k_trunc_materialize<<<(unsigned)g, 256, 0, st>>>(E, words, VW, R, kd, out);
 }
 
 void launch_gr_rec1(cudaStream_t st, const u64* s6, u64 xor_mask, int xor_idx, u64* out,

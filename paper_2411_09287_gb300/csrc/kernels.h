@@ -31,6 +31,7 @@ struct Epi {
   int atomic;
   u64 acc_sign;
   const u64* add0;
+  long long ld_add0;   // row stride of add0 (0: same index as out)
   const u64* add1;
   u64 prf_sign;
   Key key;
@@ -109,5 +110,14 @@ void launch_gr_quad_combine(cudaStream_t st, const u64* lam, const u64* S00, con
 void launch_mode_consts(cudaStream_t st, int mode, u64* cst);
 // PRF words of one stream into an array (e.g. the truncation bits b1, b2 of every output)
 void launch_prf_words(cudaStream_t st, long long n, Key key, u32 tag, u64 obj, u64* out);
+
+// ---- trunc-batch S matrix on the tensor cores (trunc_s.cu) ----------------------------------
+size_t trunc_s_smem_bytes();
+void launch_trunc_limb_table(cudaStream_t st, const u64* Tlo, long long L, unsigned char* TL8);
+void launch_trunc_bit_bytes(cudaStream_t st, const u64* words, long long Epad, unsigned char* BB);
+void launch_trunc_s_mma(cudaStream_t st, const unsigned char* BB1, const unsigned char* BB2,
+                        long long Epad, const unsigned char* TL8, long long L, long long nhi,
+                        u64* S_hi);
+void launch_fold_reduce_strided(cudaStream_t st, const u64* P, long long ld, int npairs, u64* out);
 
 }  // namespace mpc3
