@@ -72,6 +72,7 @@ namespace {
 
 constexpr u32 ST_ABORT = 1u;    // a Pi_Rec check failed
 constexpr u32 ST_VERIFY = 2u;   // Delta != 0
+constexpr u32 ST_TIMEOUT = 4u;  // a bounded device wait expired
 
 // device constants block (words)
 constexpr int CST_INV = 0;      // 192: x^-1, (1-x)^-1, (x(x-1))^-1
@@ -242,6 +243,10 @@ void count_msgs(mpc_ctx* ctx, int phase, int proto, int count, u64 bytes_each) {
 int read_status(mpc_ctx* ctx, u32* out) {
   CK(cudaMemcpyAsync(out, ctx->status, sizeof(u32), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
+  if (*out & ST_TIMEOUT) {
+    ctx->aborted = true;
+    return fail(ctx, MPC_ERR_TIMEOUT, "a bounded device wait expired");
+  }
   return MPC_OK;
 }
 
@@ -646,10 +651,13 @@ int finish_verify(mpc_ctx* ctx, u64 pend_key) {
 struct MatmulPlan {
   u64 *g2o, *g2i, *mz1, *mz2, *mz1i, *mz2i;
   u64 *gp2, *gq2, *gp2i, *gq2i, *mp1, *mq1, *mpi1, *mqi1, *mpi2, *mqi2;
+  void* tc;   // digit planes of the tensor-core path (null on the u64 path)
 };
 
-MatmulPlan plan_matmul(Arena& a, long long E, bool trunc) {
+MatmulPlan plan_matmul(Arena& a, long long M, long long N, long long K, bool trunc, bool tc) {
+  const long long E = M * N;
   MatmulPlan p{};
+  p.tc = tc ? (void*)a.take<unsigned char>((long long)limb_tc_scratch_bytes(M, N, K, 2)) : nullptr;
   p.g2o = a.take<u64>(E); p.g2i = a.take<u64>(E);
   p.mz1 = a.take<u64>(E); p.mz2 = a.take<u64>(E);
   p.mz1i = a.take<u64>(E); p.mz2i = a.take<u64>(E);
@@ -847,7 +855,8 @@ int mpc_set_stream(mpc_ctx* ctx, void* stream) {
 int mpc_sync(mpc_ctx* ctx) {
   if (!ctx) return MPC_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->st));
-  return MPC_OK;
+  u32 stv = 0;
+  return read_status(ctx, &stv);
 }
 
 int mpc_status(const mpc_ctx* ctx) {
@@ -871,7 +880,7 @@ int64_t mpc_workspace_size(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int
       break;
     case MPC_OP_MATMUL:
       if (a <= 0 || b <= 0 || c <= 0) return -1;
-      plan_matmul(ar, a * b, trunc_bits >= 0);
+      plan_matmul(ar, a, b, c, trunc_bits >= 0, ctx && ctx->gemm_path == MPC_GEMM_LIMB_TC);
       break;
     case MPC_OP_VERIFY_MULT:
       if (a <= 0) return -1;
@@ -954,7 +963,18 @@ int mpc_matmul(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_
     return fail(ctx, MPC_ERR_ARG, "matmul: bad argument");
   const long long E = M * N;
   Arena ar{(char*)workspace, workspace_bytes, 0, false};
-  MatmulPlan p = plan_matmul(ar, E, trunc);
+  const bool tc = ctx->gemm_path == MPC_GEMM_LIMB_TC;
+  MatmulPlan p = plan_matmul(ar, M, N, K, trunc, tc);
+  // the parties' local products: CUDA-core u64 GEMM or the limb-split tensor-core GEMM
+  auto party_gemm = [&](int nterms, const GemmTerm* T, const Epi& e) -> int {
+    if (!tc) {
+      gemm_u64(ctx->st, M, N, K, nterms, T, e, 1);
+      return MPC_OK;
+    }
+    g_launches += 4;
+    const int r = limb_gemm_tc(ctx->st, M, N, K, nterms, T, e, p.tc, ctx->status, ST_TIMEOUT);
+    return r ? fail(ctx, MPC_ERR_CUDA, "matmul: tensor-core GEMM setup failed") : MPC_OK;
+  };
   if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "matmul: workspace too small");
   cudaStream_t st = ctx->st;
   const u64 obj = make_obj(call_id, 0, 0);
@@ -990,7 +1010,7 @@ int mpc_matmul(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_
     e.key = ctx->k01;
     e.tag = make_tag(P_INNER, C_G1);
     e.obj = obj;
-    gemm_u64(st, M, N, K, 1, &T, e, 1);
+    if ((rc = party_gemm(1, &T, e))) return rc;
   }
   if ((rc = deliver(ctx, MPC_PHASE_OFFLINE, MPC_PROTO_INNER, p.g2o, p.g2i, E, MPC_SITE_GAMMA2)))
     return rc;
@@ -1007,7 +1027,7 @@ int mpc_matmul(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_
     e.key = ctx->k01;
     e.tag = make_tag(P_INNER, C_G1);
     e.obj = obj;
-    gemm_u64(st, M, N, K, 2, T, e, 1);
+    if ((rc = party_gemm(2, T, e))) return rc;
   }
   {  // P2, online: [m_Z]_2 = M_X (M_W - [R_W]_2) - [R_X]_2 M_W + [Gamma]_2
     Phase phase(ctx, MPC_PROF_GEMM);
@@ -1018,7 +1038,7 @@ int mpc_matmul(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_
     T[1].B = op(W + 4 * KN, N);
     Epi e = epi_store(p.mz2, N);
     e.add0 = p.g2i;
-    gemm_u64(st, M, N, K, 2, T, e, 1);
+    if ((rc = party_gemm(2, T, e))) return rc;
   }
   {
     Phase phase(ctx, MPC_PROF_EXCHANGE);

@@ -45,6 +45,16 @@ struct Epi {
 void gemm_u64(cudaStream_t st, long long M, long long N, long long K, int nterms,
               const GemmTerm* terms, const Epi& epi, int nsplit);
 
+// ---- exact u64 GEMM on the tcgen05 tensor cores (limb_gemm_tc.cu) ---------------------------
+// Same contract as gemm_u64 without split-K (epi.atomic must be 0; returns -1 otherwise, -2 if
+// the tensor maps cannot be encoded).  scratch: limb_tc_scratch_bytes(M, N, K, nterms) bytes,
+// 256-byte aligned (the bf16 digit planes of both operands).  A bounded wait that expires
+// sets err_flag in *err and leaves the output undefined.
+size_t limb_tc_scratch_bytes(long long M, long long N, long long K, int nterms);
+int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nterms,
+                 const GemmTerm* terms, const Epi& epi, void* scratch, unsigned* err,
+                 unsigned err_flag);
+
 // ---- elementwise protocol kernels (prf_kernels.cu) ------------------------------------------
 void launch_share_input(cudaStream_t st, const u64* x, long long n, Key k01, Key k02, u64 obj,
                         u64* s6, u64* p0_out_m);

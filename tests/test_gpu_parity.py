@@ -129,19 +129,21 @@ def test_plain_small_mult_and_verify(mpc, mode):
     assert np.array_equal(z, xa * xb)
 
 
+@pytest.mark.parametrize("path", [0, 1])
 @pytest.mark.parametrize("M,N,K,t", [(64, 64, 128, 13), (37, 53, 29, 13), (129, 7, 300, 16),
-                                     (5, 130, 9, -1)])
-def test_matmul_matches_oracle(mpc, M, N, K, t):
+                                     (5, 130, 9, -1), (300, 200, 333, 13)])
+def test_matmul_matches_oracle(mpc, M, N, K, t, path):
     seed = seed_of(f"matmul-{M}-{N}-{K}")
     X, W = workloads.gemm_shape(M, N, K)
     if t >= 0:
         g = workloads.rng(f"fx-{M}-{N}-{K}")
         X = mpc.encode_fixed(g.uniform(-4, 4, (M, K)), 13)
         W = mpc.encode_fixed(g.uniform(-4, 4, (K, N)), 13)
-    ctx = mpc.Context(seed)
+    ctx = mpc.Context(seed, gemm_path=path)
     sess = Session(seed)
     gx, gw = ctx.share_input(1, X), ctx.share_input(2, W)
     zpre, zout, pq = ctx.matmul(3, gx, gw, M, N, K, t)
+    ctx.sync()
     ox, ow = OP.share_input(sess, X, 1), OP.share_input(sess, W, 2)
     res = OP.matmul(sess, ox, ow, 3, trunc_bits=t if t >= 0 else None)
     assert_shared_equal(gpu_shared(mpc, zpre, (M, N)), res.z_pre, "zpre")
@@ -154,14 +156,15 @@ def test_matmul_matches_oracle(mpc, M, N, K, t):
     assert_ledger(mpc, ctx, sess)
 
 
-@pytest.mark.parametrize("M,N,K,t,mode", [(8, 8, 16, 13, 0), (12, 10, 37, 13, 0),
-                                          (3, 5, 70, 13, 1), (16, 16, 64, -1, 0)])
-def test_matmul_verify_transcript_matches_oracle(mpc, M, N, K, t, mode):
+@pytest.mark.parametrize("M,N,K,t,mode,path", [(8, 8, 16, 13, 0, 0), (12, 10, 37, 13, 0, 0),
+                                               (3, 5, 70, 13, 1, 0), (16, 16, 64, -1, 0, 0),
+                                               (12, 10, 37, 13, 0, 1), (70, 9, 130, 13, 0, 1)])
+def test_matmul_verify_transcript_matches_oracle(mpc, M, N, K, t, mode, path):
     seed = seed_of(f"vmat-{M}-{N}-{K}-{t}-{mode}")
     g = workloads.rng(f"vmat-{M}-{N}-{K}")
     X = mpc.encode_fixed(g.uniform(-4, 4, (M, K)), 13)
     W = mpc.encode_fixed(g.uniform(-4, 4, (K, N)), 13)
-    ctx = mpc.Context(seed, reduce_mode=mode)
+    ctx = mpc.Context(seed, reduce_mode=mode, gemm_path=path)
     sess = Session(seed, reduce_mode="x" if mode == 0 else "zeta2")
     gx, gw = ctx.share_input(1, X), ctx.share_input(2, W)
     zpre, zout, pq = ctx.matmul(3, gx, gw, M, N, K, t)
@@ -176,6 +179,27 @@ def test_matmul_verify_transcript_matches_oracle(mpc, M, N, K, t, mode):
     assert_ledger(mpc, ctx, sess)
     out = ctx.reconstruct(zout, M * N)
     assert np.array_equal(out, OP.reconstruct(sess, res.out).reshape(-1))
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 192, 1000), (1, 1, 1), (130, 65, 64)])
+def test_tc_gemm_full_range_words(mpc, M, N, K):
+    """Limb-split tensor-core products on shares of full 64-bit range (every digit plane busy,
+    carries through all eight balanced digits) agree with the u64 path and with the oracle."""
+    seed = seed_of(f"tcw-{M}-{N}-{K}")
+    X = workloads.uniform_words((M, K), f"tcw-x-{M}-{N}-{K}")
+    W = workloads.uniform_words((K, N), f"tcw-w-{M}-{N}-{K}")
+    outs = []
+    for path in (0, 1):
+        ctx = mpc.Context(seed, gemm_path=path)
+        gx, gw = ctx.share_input(1, X), ctx.share_input(2, W)
+        zpre, _, _ = ctx.matmul(3, gx, gw, M, N, K, -1)
+        ctx.sync()
+        outs.append(mpc.to_u64(zpre).copy())
+    assert np.array_equal(outs[0], outs[1])
+    sess = Session(seed)
+    ox, ow = OP.share_input(sess, X, 1), OP.share_input(sess, W, 2)
+    res = OP.matmul(sess, ox, ow, 3, trunc_bits=None)
+    assert_shared_equal(gpu_shared(mpc, zpre, (M, N)), res.z_pre, "zpre")
 
 
 @pytest.mark.parametrize("R_main,R_trunc", [(0, 0), (2, 3), (7, 9)])
