@@ -5,19 +5,26 @@
 // Each u64 operand value is split into 8 balanced signed digits d_0..d_7 in [-128, 127] with
 // v = sum_i 2^(8i) d_i mod 2^64 (carry-propagating split; the carry out of d_7 vanishes mod 2^64).
 // bf16 holds every such digit exactly.  Only digit pairs with i + j < 8 contribute mod 2^64:
-//   C = sum_{s<8} 2^(8s) C_s,   C_s = sum_{i+j=s} A_i B_j.
-// C_s lives in its own TMEM accumulator (8 x 64 columns = all 512).  Within one K chunk of 64,
-// |C_s| <= 8 * 64 * 2^14 = 2^23 < 2^24, so every f32 partial sum is an exact integer; after each
-// chunk the accumulators are read back (tcgen05.ld), converted to integers and added, shifted by
-// 8s, into 64-bit registers, which wrap mod 2^64 as required.
+//   C = sum_{s<8} 2^(8s) C_s,   C_s = sum_{i+j=s} A_i B_j      (36 digit-plane products).
+// Each C_s has its own TMEM accumulator (8 x 64 columns = all 512).  One K chunk is 32 deep, so
+// |C_s| <= 8 * 32 * 2^14 = 2^22 within a chunk: every f32 partial sum is an exact integer, and
+// adding 1.5 * 2^23 turns it into an integer-valued float whose bit pattern minus 0x4B400000 is
+// that integer (exact on [-2^22, 2^22]).  After each chunk the accumulators are drained into
+// 64-bit registers, which wrap mod 2^64 as required:
+//   acc += (v0 + 2^8 v1) + 2^16 (v2 + 2^8 v3) + 2^32 (v4 + 2^8 v5) + 2^48 (v6 + 2^8 v7),
+// each bracket computed in 32-bit arithmetic (|v_s + 2^8 v_(s+1)| < 2^31).
 //
-// Data flow per CTA (128 x 64 output tile, 128 threads):
-//   - thread 0 loads the 8 + 8 digit-plane tiles of a K chunk with TMA (128B swizzle) and
-//     issues the 36 x 4 MMAs (M = 128, N = 64, K = 16) in s-major order, then commits to an
-//     mbarrier;
-//   - all 4 warps wait on that mbarrier, drain their 32 TMEM lanes (= rows) and accumulate.
-// Every mbarrier wait is bounded (clock64); on a timeout the CTA records an error in *err, waits
-// (bounded) for its TMA copies, frees its tensor memory and returns.
+// CTA = one 128 x 64 output tile, 10 warps with fixed roles:
+//   warps 0..7  drain: warp w reads TMEM lanes 32 (w % 4) .. +31 (= tile rows) and columns
+//               32 (w / 4) .. +31 of every accumulator;
+//   warp 8      TMA producer: 8 + 8 digit-plane tiles per K chunk into a 2-stage ring (64-byte
+//               swizzle, 96 KB per stage);
+//   warp 9      MMA issuer (one thread): accumulator group GA = {0, 1, 6, 7} then GB = {2, 3, 4, 5}
+//               (18 digit pairs each), each committed to its own mbarrier, so that the drain of
+//               one group overlaps the MMAs of the other.
+// Every mbarrier wait is bounded (clock64, about one second) and also gives up once another
+// warp has recorded a failure; a failure sets err_flag in *err, the CTA lets its TMA copies and
+// MMAs finish (bounded), frees its tensor memory and returns without writing its tile.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -27,10 +34,13 @@ namespace mpc3 {
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 64, TC_BK = 64;
-constexpr int A_TILE = TC_BM * TC_BK * 2;   // 16 KB per digit plane
-constexpr int B_TILE = TC_BN * TC_BK * 2;   // 8 KB per digit plane
-constexpr unsigned TX_BYTES = 8 * (A_TILE + B_TILE);
+constexpr int TC_BM = 128, TC_BN = 64, TC_BK = 32;
+constexpr int A_TILE = TC_BM * TC_BK * 2;   // 8 KB per digit plane
+constexpr int B_TILE = TC_BN * TC_BK * 2;   // 4 KB per digit plane
+constexpr int STAGE = 8 * (A_TILE + B_TILE);   // 96 KB
+constexpr int NSTAGE = 2;
+constexpr int NDRAIN = 8;
+constexpr int TC_THREADS = (NDRAIN + 2) * 32;
 constexpr long long WAIT_CYCLES = 2000000000ll;   // about one second at 2 GHz
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -45,6 +55,9 @@ __device__ __forceinline__ void mbar_expect_tx(u64* bar, unsigned bytes) {
                "r"(bytes)
                : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(u64* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(u64* bar, unsigned parity) {
   unsigned ok;
   asm volatile(
@@ -55,7 +68,15 @@ __device__ __forceinline__ bool mbar_try_wait(u64* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(u64* bar, unsigned parity) {
+// Bounded wait; gives up (returns false) after about a second or once *abort is set.
+__device__ __forceinline__ bool mbar_wait(u64* bar, unsigned parity, volatile int* abort) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort || clock64() - t0 > WAIT_CYCLES) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ bool mbar_wait_plain(u64* bar, unsigned parity) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (clock64() - t0 > WAIT_CYCLES) return false;
@@ -72,16 +93,16 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 bytes
-// apart (the layout TMA writes for a box whose inner extent is 128 bytes).
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row groups 512 bytes
+// apart (the layout TMA writes for a box whose inner extent is 64 bytes).
 __device__ __forceinline__ u64 smem_desc(const void* p) {
   const u64 addr = smem_u32(p);
   u64 d = 0;
   d |= (addr & 0x3FFFFull) >> 4;            // start address
   d |= (u64)(16 >> 4) << 16;                // leading byte offset (unused with swizzle)
-  d |= (u64)(1024 >> 4) << 32;              // stride byte offset
+  d |= (u64)(512 >> 4) << 32;               // stride byte offset
   d |= (u64)1 << 46;                        // descriptor version
-  d |= (u64)2 << 61;                        // 128-byte swizzle
+  d |= (u64)4 << 61;                        // 64-byte swizzle
   return d;
 }
 
@@ -89,15 +110,21 @@ __device__ __forceinline__ u64 smem_desc(const void* p) {
 constexpr unsigned IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TC_BN >> 3) << 17) |
                            ((unsigned)(TC_BM >> 4) << 24);
 
-__device__ __forceinline__ void mma_f16(unsigned d_tmem, u64 adesc, u64 bdesc, unsigned accumulate) {
+template <int ACC>
+__device__ __forceinline__ void mma_f16(unsigned d_tmem, u64 adesc, u64 bdesc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate));
+      "l"(adesc), "l"(bdesc), "r"(IDESC), "n"(ACC));
+}
+__device__ __forceinline__ void mma_commit(u64* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_u32(bar))
+      : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(unsigned taddr, float v[16]) {
-  unsigned r[16];
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, unsigned r[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
       " [%16];\n"
@@ -105,31 +132,77 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float v[16]) {
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
         "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(128, 1)
+// Bit pattern of (v + 1.5 * 2^23) for an integer-valued f32 v in [-2^22, 2^22]: equals
+// v + MAGIC_I exactly (the sum lies in [2^23, 2^24], where every integer is a float).
+constexpr unsigned MAGIC_I = 0x4B400000u;
+constexpr unsigned PAIR_BIAS = MAGIC_I + 256u * MAGIC_I;   // bias of v_s + 2^8 v_(s+1), mod 2^32
+// per chunk, group GA adds PAIR_BIAS << 16 and group GB adds PAIR_BIAS to the high word
+constexpr unsigned CHUNK_HI_BIAS = (PAIR_BIAS << 16) + PAIR_BIAS;
+__device__ __forceinline__ int f2i_biased(unsigned bits) {
+  return __float_as_int(__uint_as_float(bits) + 12582912.0f);
+}
+
+// TMEM column of accumulator s: group GA = {0, 1, 6, 7} in columns 0..255, GB = {2..5} above
+__host__ __device__ constexpr int acc_col(int s) {
+  return s == 0 ? 0 : s == 1 ? 64 : s == 6 ? 128 : s == 7 ? 192 : 256 + (s - 2) * 64;
+}
+// digit weight of the g-th accumulator of group G (GA = {0, 1, 6, 7}, GB = {2, 3, 4, 5})
+__host__ __device__ constexpr int group_s(int G, int g) { return G == 0 ? (g < 2 ? g : g + 4) : g + 2; }
+
+// All MMAs of one accumulator group for one K chunk, fully unrolled: a_desc / b_desc are the
+// descriptors of digit plane 0 of the stage; plane i is A_TILE (B_TILE) bytes further on, and
+// each k16 step advances 32 bytes inside the swizzled rows.
+template <int G>
+__device__ __forceinline__ void issue_group(unsigned tmem, u64 a_desc, u64 b_desc) {
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const int s = group_s(G, g);
+#pragma unroll
+    for (int kk = 0; kk < TC_BK / 16; ++kk) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (i <= s) {
+          const u64 ad = a_desc + (u64)((i * A_TILE) >> 4) + (u64)(kk * 2);
+          const u64 bd = b_desc + (u64)(((s - i) * B_TILE) >> 4) + (u64)(kk * 2);
+          if (kk == 0 && i == 0) mma_f16<0>(tmem + (unsigned)acc_col(s), ad, bd);
+          else mma_f16<1>(tmem + (unsigned)acc_col(s), ad, bd);
+        }
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
 k_limb_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                long long M, long long N, long long Kp, u64* __restrict__ C, long long ldc,
                unsigned* __restrict__ err, unsigned err_flag) {
   extern __shared__ unsigned char dsm[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
-  unsigned char* As = base;                       // 8 x 16 KB
-  unsigned char* Bs = base + 8 * A_TILE;          // 8 x 8 KB
-  __shared__ __align__(8) u64 full_bar, mma_bar;
+  __shared__ __align__(8) u64 full_bar[NSTAGE], empty_bar[NSTAGE];
+  __shared__ __align__(8) u64 accf_bar[2], acce_bar[2], done_bar;
   __shared__ unsigned tmem_slot;
   __shared__ int abort_flag;
+  volatile int* abort = &abort_flag;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const long long m0 = (long long)blockIdx.x * TC_BM;
   const long long n0 = (long long)blockIdx.y * TC_BN;
+  const int nchunks = (int)(Kp / TC_BK);
 
   if (tid == 0) {
-    mbar_init(&full_bar, 1);
-    mbar_init(&mma_bar, 1);
+    for (int i = 0; i < NSTAGE; ++i) {
+      mbar_init(&full_bar[i], 1);
+      mbar_init(&empty_bar[i], 1);
+    }
+    for (int g = 0; g < 2; ++g) {
+      mbar_init(&accf_bar[g], 1);
+      mbar_init(&acce_bar[g], NDRAIN);
+    }
+    mbar_init(&done_bar, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -144,95 +217,124 @@ k_limb_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const unsigned tmem = tmem_slot;
 
-  u64 acc[TC_BN];
-#pragma unroll
-  for (int c = 0; c < TC_BN; ++c) acc[c] = 0;
+  auto fail = [&]() {
+    *abort = 1;
+    atomicOr(err, err_flag);
+  };
 
-  const int nchunks = (int)(Kp / TC_BK);
-  int stuck = 0;   // thread 0: 1 = TMA copies of the current chunk may be in flight, 2 = MMAs
-  unsigned stuck_parity = 0;
-  for (int ch = 0; ch < nchunks; ++ch) {
-    const unsigned parity = (unsigned)(ch & 1);
-    if (tid == 0) {
-      mbar_expect_tx(&full_bar, TX_BYTES);
-      const int kx = ch * TC_BK;
+  if (warp == NDRAIN) {
+    // ---- TMA producer ----
+    if (lane == 0) {
+      int last = -1;
+      for (int c = 0; c < nchunks; ++c) {
+        const int st = c % NSTAGE;
+        if (c >= NSTAGE && !mbar_wait(&empty_bar[st], (unsigned)(((c / NSTAGE) + 1) & 1), abort)) {
+          fail();
+          break;
+        }
+        unsigned char* As = base + st * STAGE;
+        unsigned char* Bs = As + 8 * A_TILE;
+        mbar_expect_tx(&full_bar[st], (unsigned)STAGE);
+        const int kx = c * TC_BK;
 #pragma unroll 1
-      for (int i = 0; i < 8; ++i) {
-        tma_load_3d(As + i * A_TILE, &tmA, &full_bar, kx, (int)m0, i);
-        tma_load_3d(Bs + i * B_TILE, &tmB, &full_bar, kx, (int)n0, i);
+        for (int i = 0; i < 8; ++i) {
+          tma_load_3d(As + i * A_TILE, &tmA, &full_bar[st], kx, (int)m0, i);
+          tma_load_3d(Bs + i * B_TILE, &tmB, &full_bar[st], kx, (int)n0, i);
+        }
+        last = c;
       }
-      if (!mbar_wait_bounded(&full_bar, parity)) {
-        abort_flag = 1;
-        stuck = 1;
-        stuck_parity = parity;
-      } else {
+      // the copies of the last chunk issued into each stage must land before the CTA exits
+      for (int c = last; c >= 0 && c > last - NSTAGE; --c)
+        mbar_wait_plain(&full_bar[c % NSTAGE], (unsigned)((c / NSTAGE) & 1));
+    }
+  } else if (warp == NDRAIN + 1) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      const u64 d0 = smem_desc(base);
+      for (int c = 0; c < nchunks; ++c) {
+        const int st = c % NSTAGE;
+        if (!mbar_wait(&full_bar[st], (unsigned)((c / NSTAGE) & 1), abort)) { fail(); break; }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        // s-major: accumulator s collects the digit pairs i + j = s; the first MMA of each
-        // accumulator in a chunk overwrites it
-#pragma unroll 1
-        for (int s = 0; s < 8; ++s) {
-#pragma unroll 1
-          for (int kk = 0; kk < TC_BK / 16; ++kk) {
-#pragma unroll 1
-            for (int i = 0; i <= s; ++i) {
-              const int j = s - i;
-              const u64 ad = smem_desc(As + i * A_TILE) + (u64)(kk * 2);   // +32 bytes per k16
-              const u64 bd = smem_desc(Bs + j * B_TILE) + (u64)(kk * 2);
-              mma_f16(tmem + (unsigned)(s * TC_BN), ad, bd, (kk > 0 || i > 0) ? 1u : 0u);
-            }
-          }
-        }
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                smem_u32(&mma_bar))
-            : "memory");
+        const u64 ad = d0 + (u64)((st * STAGE) >> 4);
+        const u64 bd = ad + (u64)((8 * A_TILE) >> 4);
+        if (c > 0 && !mbar_wait(&acce_bar[0], (unsigned)((c - 1) & 1), abort)) { fail(); break; }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        issue_group<0>(tmem, ad, bd);
+        mma_commit(&accf_bar[0]);
+        if (c > 0 && !mbar_wait(&acce_bar[1], (unsigned)((c - 1) & 1), abort)) { fail(); break; }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        issue_group<1>(tmem, ad, bd);
+        mma_commit(&accf_bar[1]);
+        mma_commit(&empty_bar[st]);   // the stage is free once these MMAs have read it
       }
-    }
-    __syncthreads();
-    if (abort_flag) break;
-    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&mma_bar, parity));
-    if (!ok) {
-      abort_flag = 1;
-      if (tid == 0) { stuck = 2; stuck_parity = parity; }
-    } else {
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const unsigned lane_base = (unsigned)(warp * 32) << 16;
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-#pragma unroll
-        for (int c16 = 0; c16 < TC_BN / 16; ++c16) {
-          float v[16];
-          tmem_ld16(tmem + lane_base + (unsigned)(s * TC_BN + c16 * 16), v);
-          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-          for (int q = 0; q < 16; ++q)
-            acc[c16 * 16 + q] += (u64)__float2ll_rn(v[q]) << (8 * s);
-        }
-      }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (abort_flag) break;
-  }
-
-  if (abort_flag) {
-    if (tid == 0) {
-      atomicOr(err, err_flag);
-      // let the copies or MMAs of the failed chunk finish before the memory is released
-      if (stuck == 1) mbar_wait_bounded(&full_bar, stuck_parity);
-      if (stuck == 2) mbar_wait_bounded(&mma_bar, stuck_parity);
+      // every MMA issued must complete before the tensor memory is released
+      mma_commit(&done_bar);
+      mbar_wait_plain(&done_bar, 0u);
     }
   } else {
-    const long long r = m0 + warp * 32 + lane;
-    if (r < M) {
+    // ---- drain warps ----
+    const int q = warp & 3, h = warp >> 2;
+    const unsigned tl = tmem + ((unsigned)(q * 32) << 16) + (unsigned)(h * 32);
+    u64 acc[32];
 #pragma unroll
-      for (int c = 0; c < TC_BN; ++c)
-        if (n0 + c < N) C[r * ldc + n0 + c] = acc[c];
+    for (int c = 0; c < 32; ++c) acc[c] = 0;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const unsigned par = (unsigned)(c & 1);
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        ok = __all_sync(0xffffffffu, mbar_wait(&accf_bar[g], par, abort));
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const int s0 = g == 0 ? 0 : 2;   // the group's digit-weight pairs (s0, s0+1), (s1, s1+1)
+        const int s1 = g == 0 ? 6 : 4;
+#pragma unroll
+        for (int c16 = 0; c16 < 2; ++c16) {
+          unsigned a0[16], a1[16], b0[16], b1[16];
+          tmem_ld16(tl + (unsigned)(acc_col(s0) + c16 * 16), a0);
+          tmem_ld16(tl + (unsigned)(acc_col(s0 + 1) + c16 * 16), a1);
+          tmem_ld16(tl + (unsigned)(acc_col(s1) + c16 * 16), b0);
+          tmem_ld16(tl + (unsigned)(acc_col(s1 + 1) + c16 * 16), b1);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            // biased pair sums: w = C_s + 2^8 C_(s+1) + PAIR_BIAS (mod 2^32)
+            const unsigned wlo = (unsigned)f2i_biased(a0[j]) + (unsigned)f2i_biased(a1[j]) * 256u;
+            const unsigned whi = (unsigned)f2i_biased(b0[j]) + (unsigned)f2i_biased(b1[j]) * 256u;
+            const unsigned ws = wlo - PAIR_BIAS;   // exact, |ws| < 2^31: its sign extends it
+            unsigned add_lo, add_hi;
+            if (g == 0) {   // + ws + 2^48 whi; the bias of whi is removed once per tile
+              add_lo = ws;
+              add_hi = (unsigned)((int)ws >> 31) + (whi << 16);
+            } else {        // + 2^16 ws + 2^32 whi
+              add_lo = ws << 16;
+              add_hi = (unsigned)((int)ws >> 16) + whi;
+            }
+            acc[c16 * 16 + j] += ((u64)add_hi << 32) | add_lo;
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce_bar[g]);
+      }
+    }
+    if (ok && !*abort) {
+      const long long r = m0 + q * 32 + lane;
+      const long long cb = n0 + h * 32;
+      // remove the biases of whi that every chunk added to the high word
+      const u64 corr = (u64)((unsigned)nchunks * CHUNK_HI_BIAS) << 32;
+      if (r < M) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (cb + c < N) C[r * ldc + cb + c] = acc[c] - corr;
+      }
+    } else if (!ok) {
+      if (lane == 0) fail();
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
 }
@@ -355,10 +457,10 @@ bool make_map(CUtensorMap* map, void* planes, long long rows, long long Kp, int 
   if (!enc) return false;
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, 8};
   cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2)};
-  cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};   // 64-byte rows
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, planes, dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -389,10 +491,10 @@ int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nte
   k_split_digits<<<(unsigned)gb, tpb, 0, st>>>(terms[0], t1, nterms, 1, N, K, Kp, Bp);
   CUtensorMap ma, mb;
   if (!make_map(&ma, Ap, M, Kp, TC_BM) || !make_map(&mb, Bp, N, Kp, TC_BN)) return -2;
-  const size_t smem = 8 * (A_TILE + B_TILE) + 1024;
+  const size_t smem = (size_t)NSTAGE * STAGE + 1024;
   cudaFuncSetAttribute(k_limb_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid((unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)((N + TC_BN - 1) / TC_BN));
-  k_limb_gemm_tc<<<grid, 128, smem, st>>>(ma, mb, M, N, Kp, epi.out, epi.ldc, err, err_flag);
+  k_limb_gemm_tc<<<grid, TC_THREADS, smem, st>>>(ma, mb, M, N, Kp, epi.out, epi.ldc, err, err_flag);
   long long ge = ((M * N + 7) / 8 + 255) / 256;
   if (ge > (1 << 20)) ge = 1 << 20;
   if (ge < 1) ge = 1;
