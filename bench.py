@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--trunc", type=int, default=13)
-    ap.add_argument("--gemm-path", choices=["u64", "tc"], default="u64")
+    ap.add_argument("--gemm-path", choices=["u64", "tc"], default="tc")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -157,6 +157,51 @@ def run_reference(args, rank: int, world: int):
 # ---------------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------------
+# DRAM bytes per launch from one ncu capture of each kernel on the n = 1024 layer (E = 2^20),
+# scaled by the units a launch processes (both kernels stream their inputs once per unit of work,
+# so traffic grows in proportion).  Summaries with the commands that produced them: profiles/.
+NCU_TRAFFIC = {
+    # kernel: (DRAM bytes per launch at the captured size, units at that size, summary)
+    "k_trunc_s": (None, 2 ** 20, "profiles/trunc_s_mma_e4m3_n1024.md"),
+    "k_limb_gemm": (None, 1024 ** 3, "profiles/limb_gemm_tc_n1024.md"),
+}
+
+
+def rooflines(per, peaks, clk, M, N, K, E, gemm_path):
+    """Roofline records of the dominant kernels, from their CUDA-event times inside the step.
+    Tensor peaks are the measured cuBLAS bf16 rate (sustained: these kernels run inside a long
+    step); e4m3 work takes twice that (the nominal fp8 : bf16 ratio)."""
+    bf16 = peaks.get("bf16_tflops_sustained")
+    src = "of measured" if bf16 else "of fallback"
+    bf16 = bf16 or 1700.0
+    sm_max = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    out = {}
+
+    def rec(name, ms, work, peak, unit, bound, units, note):
+        if not ms:
+            return
+        tr = NCU_TRAFFIC.get(name)
+        traffic = tr[0] * units / tr[1] if tr and tr[0] is not None else None
+        ach = work / (ms * 1e-3) / 1e12
+        out[name] = {"bound": bound, "kernel": name, "achieved": ach, "peak": peak, "unit": unit,
+                     "frac": ach / peak, "traffic": traffic, "ms_per_step": ms,
+                     "work_per_step": work, "peak_source": src, "note": note}
+
+    # S matrix of the trunc batch: 4096 bit pairs x 64 coefficients x E outputs, 16 four-bit
+    # limbs, one e4m3 MAC (2 FLOP) per limb
+    rec("k_trunc_s", per.get("k_trunc_s"), 2.0 * 16 * 4096 * 64 * E, 2 * bf16, "TFLOP/s",
+        "tensor", E, "tcgen05 kind::f8f6f4 e4m3, 16 limbs; peak = 2 x measured bf16 (sustained)")
+    if gemm_path == "tc":
+        # three party products, 5 M N K u64 MACs, 36 digit-pair products each, 2 FLOP per MAC
+        rec("k_limb_gemm", per.get("k_limb_gemm"), 36.0 * 2 * 5 * M * N * K, bf16, "TFLOP/s",
+            "tensor", M * N * K, "tcgen05 kind::f16, bf16 digits; peak = measured bf16 (sustained)")
+    else:
+        alu = 152 * 64 * sm_max * 1e6 / 1e12   # int32 IMAD/s in T; a u64 MAC is 3 IMAD
+        rec("gemm", per.get("gemm"), 3.0 * 5 * M * N * K, alu, "Tops/s (int32 IMAD)", "alu",
+            M * N * K, "u64 CUDA-core GEMM; peak derived: 152 SMs x 64 IMAD/clk x max SM clock")
+    return out
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -293,22 +338,8 @@ def main():
         except Exception:
             peaks = {}
     per = {k: v[0] / args.steps for k, v in phases.items()}
-    dom = max(per, key=per.get)
-    sm_max = (clk.get("sm_max_mhz") or 2070.0)
-    alu_peak = 152 * 64 * sm_max * 1e6 / 1e12      # int32 IMAD/s, Tops (derivation in the design doc)
-    work = {   # algorithmic u64 MACs per step of the GEMM-shaped phases (3 IMAD per u64 MAC)
-        "gemm": 5 * M * N * K,
-        "trunc_s": 4096 * 64 * E,
-    }
-    if dom in work:
-        achieved = 3 * work[dom] / (per[dom] * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak,
-                "unit": "Tops/s (int32 IMAD)", "frac": achieved / alu_peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x 64 IMAD/clk x max SM clock"}
-    else:
-        roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": alu_peak,
-                "unit": "Tops/s (int32 IMAD)", "frac": None, "traffic": None}
-    gemm_ach = 3 * work["gemm"] / (per["gemm"] * 1e-3) / 1e12 if per.get("gemm") else None
+    roofs = rooflines(per, peaks, clk, M, N, K, E, args.gemm_path)
+    roof = max(roofs.values(), key=lambda r: r["ms_per_step"]) if roofs else None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -320,7 +351,7 @@ def main():
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (working set "
                                                             f"{(wsb + 8 * 6 * (2 * n * n + 4 * E)) / 2**30:.1f} GiB)"},
         "roofline": roof,
-        "gemm_u64_path": {"tops": gemm_ach, "frac_of_alu_peak": gemm_ach / alu_peak if gemm_ach else None},
+        "rooflines": roofs,
         "phases_ms": {k: round(v, 3) for k, v in per.items() if v > 0},
         "gpu_launches": launches,
         "clocks": clk,

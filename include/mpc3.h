@@ -206,7 +206,10 @@ enum {
   MPC_PROF_TRUNC_TAIL = 10,        /* batch 1: remaining rounds and Pi_InnerVerify          */
   MPC_PROF_REC = 11,               /* Pi_Rec of outputs                                     */
   MPC_PROF_VERIFY_MULT = 12,       /* Pi_MultVerify                                         */
-  MPC_NPROF = 13
+  /* kernel-level intervals, nested inside the phases above (not added to them):           */
+  MPC_PROF_K_LIMB_GEMM = 13,       /* the tensor-core kernel of each limb-split product     */
+  MPC_PROF_K_TRUNC_S = 14,         /* the tensor-core kernel of the trunc-batch S matrix     */
+  MPC_NPROF = 15
 };
 int mpc_profile(mpc_ctx* ctx, int enable);
 int mpc_profile_read(mpc_ctx* ctx, double* ms /* MPC_NPROF */, uint64_t* count /* MPC_NPROF */);

@@ -64,8 +64,7 @@ inline void counted(int k, F f, A... a) {
 #define launch_mode_consts(...) counted(1, mpc3::launch_mode_consts, __VA_ARGS__)
 #define launch_prf_words(...) counted(1, mpc3::launch_prf_words, __VA_ARGS__)
 #define launch_trunc_limb_table(...) counted(1, mpc3::launch_trunc_limb_table, __VA_ARGS__)
-#define launch_trunc_s_mma(...) counted(1, mpc3::launch_trunc_s_mma, __VA_ARGS__)
-#define launch_trunc_bit_bytes(...) counted(1, mpc3::launch_trunc_bit_bytes, __VA_ARGS__)
+#define launch_trunc_bit_transpose(...) counted(1, mpc3::launch_trunc_bit_transpose, __VA_ARGS__)
 #define launch_fold_reduce_strided(...) counted(1, mpc3::launch_fold_reduce_strided, __VA_ARGS__)
 
 namespace {
@@ -719,7 +718,8 @@ struct VMatPlan {
   long long Dt;
   long long L, Epad, nhi;    // S = sum over e_hi < nhi of T_hi (x) (sum over e_lo < L ...)
   u64 *b1, *b2, *Rtab, *S, *Zpq, *V, *W, *hsum, *S3, *zt, *S_hi, *Pst, *Thi, *Mhi;
-  unsigned char *TL8, *BB1, *BB2;
+  u64 *B1T, *B2T;   // bit-transposed b1, b2: [j][e / 64]
+  unsigned char* TL8;
   Dense dt;
   IVBuf ivt;
 };
@@ -750,8 +750,8 @@ VMatPlan plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R
     p.Rtab = a.take<u64>(p.Epad * 64);
     p.S = a.take<u64>(4096 * 64);
     p.TL8 = a.take<unsigned char>(1024 * p.L);
-    p.BB1 = a.take<unsigned char>(64 * p.Epad);
-    p.BB2 = a.take<unsigned char>(64 * p.Epad);
+    p.B1T = a.take<u64>(p.Epad);
+    p.B2T = a.take<u64>(p.Epad);
     p.S_hi = a.take<u64>(p.nhi * 4096 * 64);
     p.Pst = a.take<u64>(64ll * 262144);
     p.Thi = a.take<u64>(p.nhi * 64);
@@ -972,7 +972,13 @@ int mpc_matmul(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_
       return MPC_OK;
     }
     g_launches += 4;
-    const int r = limb_gemm_tc(ctx->st, M, N, K, nterms, T, e, p.tc, ctx->status, ST_TIMEOUT);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ctx->prof) {
+      e0 = prof_event(ctx);
+      e1 = prof_event(ctx);
+      ctx->recs.push_back({MPC_PROF_K_LIMB_GEMM, e0, e1});
+    }
+    const int r = limb_gemm_tc(ctx->st, M, N, K, nterms, T, e, p.tc, ctx->status, ST_TIMEOUT, e0, e1);
     return r ? fail(ctx, MPC_ERR_CUDA, "matmul: tensor-core GEMM setup failed") : MPC_OK;
   };
   if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "matmul: workspace too small");
@@ -1185,9 +1191,15 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
     {  // S_{j,j'} = sum_e r^(2e) b1_{e,j} b2_{e,j'} (P0), with r^(2e) = r^(2 L e_hi) r^(2 e_lo):
        // tensor cores for the inner sums over e_lo, then sum_{e_hi} T_hi (x) S_hi as a GEMM + fold
       launch_trunc_limb_table(st, p.Rtab, p.L, p.TL8);
-      launch_trunc_bit_bytes(st, p.b1, p.Epad, p.BB1);
-      launch_trunc_bit_bytes(st, p.b2, p.Epad, p.BB2);
-      launch_trunc_s_mma(st, p.BB1, p.BB2, p.Epad, p.TL8, p.L, p.nhi, p.S_hi);
+      launch_trunc_bit_transpose(st, p.b1, p.Epad, p.B1T);
+      launch_trunc_bit_transpose(st, p.b2, p.Epad, p.B2T);
+      {
+        Phase kphase(ctx, MPC_PROF_K_TRUNC_S);
+        g_launches += 1;
+        if (launch_trunc_s_tc(st, p.B1T, p.B2T, p.Epad, p.TL8, p.L, p.nhi, p.S_hi, ctx->status,
+                              ST_TIMEOUT))
+          return fail(ctx, MPC_ERR_CUDA, "verify_matmul: tensor map of the limb table");
+      }
       GemmTerm T;
       T.A = op(p.Rtab, p.L * 64, 1);       // A[a][e_hi] = coefficient a of r^(2 L e_hi)
       T.B = op(p.S_hi, 262144);            // B[e_hi][(p, b)]

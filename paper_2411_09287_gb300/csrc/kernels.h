@@ -51,9 +51,10 @@ void gemm_u64(cudaStream_t st, long long M, long long N, long long K, int nterms
 // 256-byte aligned (the bf16 digit planes of both operands).  A bounded wait that expires
 // sets err_flag in *err and leaves the output undefined.
 size_t limb_tc_scratch_bytes(long long M, long long N, long long K, int nterms);
+// ev0 / ev1 (may be null) are recorded on st around the tensor-core kernel alone.
 int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nterms,
                  const GemmTerm* terms, const Epi& epi, void* scratch, unsigned* err,
-                 unsigned err_flag);
+                 unsigned err_flag, cudaEvent_t ev0, cudaEvent_t ev1);
 
 // ---- elementwise protocol kernels (prf_kernels.cu) ------------------------------------------
 void launch_share_input(cudaStream_t st, const u64* x, long long n, Key k01, Key k02, u64 obj,
@@ -122,12 +123,14 @@ void launch_mode_consts(cudaStream_t st, int mode, u64* cst);
 void launch_prf_words(cudaStream_t st, long long n, Key key, u32 tag, u64 obj, u64* out);
 
 // ---- trunc-batch S matrix on the tensor cores (trunc_s.cu) ----------------------------------
-size_t trunc_s_smem_bytes();
 void launch_trunc_limb_table(cudaStream_t st, const u64* Tlo, long long L, unsigned char* TL8);
-void launch_trunc_bit_bytes(cudaStream_t st, const u64* words, long long Epad, unsigned char* BB);
-void launch_trunc_s_mma(cudaStream_t st, const unsigned char* BB1, const unsigned char* BB2,
-                        long long Epad, const unsigned char* TL8, long long L, long long nhi,
-                        u64* S_hi);
+// BT[j][w] = bit j of words[64 w + i] at bit i, for w < Epad / 64
+void launch_trunc_bit_transpose(cudaStream_t st, const u64* words, long long Epad, u64* BT);
+// S_hi[e_hi][64 j + j'][coeff] for e_hi < nhi; returns -2 if the tensor map cannot be encoded.
+// A bounded wait that expires sets err_flag in *err (the output is then undefined).
+int launch_trunc_s_tc(cudaStream_t st, const u64* B1T, const u64* B2T, long long Epad,
+                      const unsigned char* TL8, long long L, long long nhi, u64* S_hi,
+                      unsigned* err, unsigned err_flag);
 void launch_fold_reduce_strided(cudaStream_t st, const u64* P, long long ld, int npairs, u64* out);
 
 }  // namespace mpc3

@@ -25,14 +25,14 @@
 // Every mbarrier wait is bounded (clock64, about one second) and also gives up once another
 // warp has recorded a failure; a failure sets err_flag in *err, the CTA lets its TMA copies and
 // MMAs finish (bounded), frees its tensor memory and returns without writing its tile.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include "kernels.h"
+#include "tcgen05.cuh"
 
 namespace mpc3 {
 
 namespace {
+
+using namespace tc;
 
 constexpr int TC_BM = 128, TC_BN = 64, TC_BK = 32;
 constexpr int A_TILE = TC_BM * TC_BK * 2;   // 8 KB per digit plane
@@ -41,70 +41,6 @@ constexpr int STAGE = 8 * (A_TILE + B_TILE);   // 96 KB
 constexpr int NSTAGE = 2;
 constexpr int NDRAIN = 8;
 constexpr int TC_THREADS = (NDRAIN + 2) * 32;
-constexpr long long WAIT_CYCLES = 2000000000ll;   // about one second at 2 GHz
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(u64* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(u64* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(u64* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(u64* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait; gives up (returns false) after about a second or once *abort is set.
-__device__ __forceinline__ bool mbar_wait(u64* bar, unsigned parity, volatile int* abort) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort || clock64() - t0 > WAIT_CYCLES) return false;
-  }
-  return true;
-}
-__device__ __forceinline__ bool mbar_wait_plain(u64* bar, unsigned parity) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > WAIT_CYCLES) return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u64* bar, int x,
-                                            int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5}], [%2];\n" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<u64>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row groups 512 bytes
-// apart (the layout TMA writes for a box whose inner extent is 64 bytes).
-__device__ __forceinline__ u64 smem_desc(const void* p) {
-  const u64 addr = smem_u32(p);
-  u64 d = 0;
-  d |= (addr & 0x3FFFFull) >> 4;            // start address
-  d |= (u64)(16 >> 4) << 16;                // leading byte offset (unused with swizzle)
-  d |= (u64)(512 >> 4) << 32;               // stride byte offset
-  d |= (u64)1 << 46;                        // descriptor version
-  d |= (u64)4 << 61;                        // 64-byte swizzle
-  return d;
-}
 
 // Instruction descriptor, kind::f16: f32 accumulator, bf16 A and B, both K-major, M = 128, N = 64.
 constexpr unsigned IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TC_BN >> 3) << 17) |
@@ -117,23 +53,6 @@ __device__ __forceinline__ void mma_f16(unsigned d_tmem, u64 adesc, u64 bdesc) {
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(IDESC), "n"(ACC));
 }
-__device__ __forceinline__ void mma_commit(u64* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(unsigned taddr, unsigned r[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15},"
-      " [%16];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
-
 // Bit pattern of (v + 1.5 * 2^23) for an integer-valued f32 v in [-2^22, 2^22]: equals
 // v + MAGIC_I exactly (the sum lies in [2^23, 2^24], where every integer is a float).
 constexpr unsigned MAGIC_I = 0x4B400000u;
@@ -250,7 +169,7 @@ k_limb_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   } else if (warp == NDRAIN + 1) {
     // ---- MMA issuer ----
     if (lane == 0) {
-      const u64 d0 = smem_desc(base);
+      const u64 d0 = smem_desc(base, 64);
       for (int c = 0; c < nchunks; ++c) {
         const int st = c % NSTAGE;
         if (!mbar_wait(&full_bar[st], (unsigned)((c / NSTAGE) & 1), abort)) { fail(); break; }
@@ -439,21 +358,8 @@ __global__ void k_apply_epilogue(long long M, long long N, Epi epi) {
   }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
 bool make_map(CUtensorMap* map, void* planes, long long rows, long long Kp, int box_rows) {
-  auto enc = get_encode();
+  auto enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, 8};
   cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2)};
@@ -475,7 +381,7 @@ size_t limb_tc_scratch_bytes(long long M, long long N, long long K, int nterms) 
 
 int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nterms,
                  const GemmTerm* terms, const Epi& epi, void* scratch, unsigned* err,
-                 unsigned err_flag) {
+                 unsigned err_flag, cudaEvent_t ev0, cudaEvent_t ev1) {
   if (M <= 0 || N <= 0) return 0;
   if (epi.atomic) return -1;
   const long long Kp = ((nterms * K + TC_BK - 1) / TC_BK) * TC_BK;
@@ -494,7 +400,9 @@ int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nte
   const size_t smem = (size_t)NSTAGE * STAGE + 1024;
   cudaFuncSetAttribute(k_limb_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid((unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)((N + TC_BN - 1) / TC_BN));
+  if (ev0) cudaEventRecord(ev0, st);
   k_limb_gemm_tc<<<grid, TC_THREADS, smem, st>>>(ma, mb, M, N, Kp, epi.out, epi.ldc, err, err_flag);
+  if (ev1) cudaEventRecord(ev1, st);
   long long ge = ((M * N + 7) / 8 + 255) / 256;
   if (ge > (1 << 20)) ge = 1 << 20;
   if (ge < 1) ge = 1;

@@ -1,54 +1,61 @@
-// The matrix S_{j,j'} = sum_e r^(2e) b1_{e,j} b2_{e,j'} of the truncation-pair batch on the tensor
-// cores (legacy mma.sync, e4m3 inputs, f32 accumulation), exactly.
+// The matrix S_{j,j'} = sum_e r^(2e) b1_{e,j} b2_{e,j'} of the truncation-pair batch on the
+// 5th-generation tensor cores (tcgen05.mma kind::f8f6f4, e4m3 operands, f32 accumulators in
+// tensor memory), exactly.
 //
 // Why: in the consolidated trunc-pair claim (index i = 64 e + j), P0's cross-term sums of the first
 // six Pi_Reduce rounds (Fig. Reduce) are all linear combinations of S with public GR weights, so
 // S is computed once per layer.  Writing r^(2e) = T_hi[e_hi] T_lo[e_lo] with e = e_hi L + e_lo:
 //   S_hi[e_hi][(j,j')] = sum_{e_lo} T_lo[e_lo] b1_{e,j} b2_{e,j'}     (this file, tensor cores)
 //   S[(j,j')]          = sum_{e_hi} T_hi[e_hi] (x) S_hi[e_hi][(j,j')]  (a u64 GEMM + fold)
-// Exactness: each u64 coefficient of T_lo is split into 16 unsigned 4-bit limbs, every limb value
-// 0..15 and every bit 0/1 is exact in e4m3, and each f32 accumulator sums at most L <= 2^20 terms
-// of at most 15 < 2^24 / 2^20, so every partial sum is an exact integer; the limbs are recombined
-// mod 2^64 after the loop.
+// Exactness: each u64 coefficient of T_lo is split into 16 unsigned 4-bit limbs; every limb value
+// 0..15 and every bit 0/1 is exact in e4m3, and an accumulator sums at most L <= 2^16 terms of at
+// most 15, so every f32 partial sum is an exact integer below 2^20; the limbs are recombined
+// mod 2^64 when the e_lo loop ends.
 //
-// Operand tables (built once per layer, e-contiguous so that a 4-byte word covers 4 consecutive e):
-//   BB1[j][e], BB2[j'][e] = e4m3(bit j of b1[e]) / e4m3(bit j' of b2[e])   (64 x Epad bytes each)
-//   TL8[c][e_lo]           = e4m3(limb c % 16 of coefficient c / 16 of T_lo[e_lo]) (1024 x L)
-// The A fragment of pair rows (j, j') is the BB2 tile of the 64 rows j' loaded with ldmatrix and
-// ANDed with the BB1 bytes of the CTA's row j (0x38 & 0x38 = 0x38 = 1.0, anything & 0 = 0).
+// Operands, both K-major (K = e):
+//   A (M = 128 pairs per accumulator): byte (p, e) = e4m3(b1_{e,j} AND b2_{e,j'}), generated in
+//     shared memory by four warps from bit-transposed words BT[j][e / 64] (bit e % 64);
+//   B (N = 256 limb columns): TL8[c][e_lo] = e4m3(limb c % 16 of coefficient c / 16 of T_lo[e_lo]),
+//     loaded by TMA (128-byte swizzle).
+// CTA = 256 pairs (j = 4 blockIdx.x .. +3, all j') x 256 limb columns (16 coefficients) x one e_hi
+// block; two accumulators (pairs 0..127 and 128..255 of the tile) fill the 512 TMEM columns.
+// Warps 0-3 generate A and drain TMEM at the end, warp 4 issues the TMA loads, warp 5 the MMAs;
+// a 3-stage ring of 64 KB (two A tiles + one B tile per stage) keeps the three roles apart.
+// Every mbarrier wait is bounded; a failure sets err_flag in *err and the CTA lets its copies and
+// MMAs finish (bounded), frees its tensor memory and returns without writing.
 #include "kernels.h"
+#include "tcgen05.cuh"
 
 namespace mpc3 {
 
 namespace {
 
-constexpr int S_PAIRS = 128;       // pairs (rows) per CTA: two values of j x 64 values of j'
-constexpr int S_COLS = 256;        // limb columns per CTA = 16 coefficients x 16 limbs
-constexpr int S_KB = 128;          // e per pipeline stage
-constexpr int S_ROWB = S_KB + 16;  // padded bytes per row of a staged tile
+using namespace tc;
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+constexpr int S_KC = 128;                  // e per chunk (one 128-byte swizzled row)
+constexpr int S_TPAIRS = 256;              // pairs per CTA (two accumulators of 128)
+constexpr int S_TCOLS = 256;               // limb columns per CTA (16 coefficients x 16 limbs)
+constexpr int S_ATILE = 128 * S_KC;        // 16 KB
+constexpr int S_BTILE = S_TCOLS * S_KC;    // 32 KB
+constexpr int S_STAGE = 2 * S_ATILE + S_BTILE;
+constexpr int S_NST = 3;
+constexpr int S_THREADS = 6 * 32;
+constexpr size_t S_SMEM = (size_t)S_NST * S_STAGE + 1024;
 
-__device__ __forceinline__ void ldsm_x4(const void* p, unsigned& r0, unsigned& r1, unsigned& r2,
-                                        unsigned& r3) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(s));
-}
+// kind::f8f6f4: f32 accumulator, e4m3 A and B (format 0), both K-major, M = 128, N = 256
+constexpr unsigned S_IDESC = (1u << 4) | ((unsigned)(S_TCOLS >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
 
-__device__ __forceinline__ void mma_e4m3(float c[4], unsigned a0, unsigned a1, unsigned a2,
-                                         unsigned a3, unsigned b0, unsigned b1) {
+template <int ACC>
+__device__ __forceinline__ void mma_f8(unsigned d_tmem, u64 adesc, u64 bdesc) {
   asm volatile(
-      "mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(S_IDESC), "n"(ACC));
+}
+
+// 4 bits -> 4 bytes of e4m3 1.0 (0x38) or 0: the multiply spreads bit b to byte b (no carries)
+__device__ __forceinline__ unsigned nibble_bytes(unsigned nib) {
+  return ((nib * 0x00204081u) & 0x01010101u) * 0x38u;
 }
 
 // e4m3 encodings of the integers 0..15
@@ -77,147 +84,172 @@ __global__ void k_limb_table(const u64* __restrict__ Tlo, long long L, unsigned 
   }
 }
 
-// BB[j * Epad + e] = 0x38 if bit j of words[e] else 0 (for 16 consecutive e per thread).
-__global__ void k_bit_bytes(const u64* __restrict__ words, long long Epad, unsigned char* __restrict__ BB) {
-  const long long chunks = Epad / 16;
-  const long long total = 64 * chunks;
-  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total;
-       w += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(w / chunks);
-    const long long e0 = (w % chunks) * 16;
-    unsigned v[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-      if ((words[e0 + i] >> j) & 1ull) v[i >> 2] |= 0x38u << (8 * (i & 3));
-    uint4 out;
-    out.x = v[0]; out.y = v[1]; out.z = v[2]; out.w = v[3];
-    *reinterpret_cast<uint4*>(BB + (long long)j * Epad + e0) = out;
+// BT[j * (Epad / 64) + w] = bits j of words[64 w .. 64 w + 63] (bit i = word 64 w + i).
+// One 64-thread block per word group w: thread j gathers its bit of the 64 words.
+__global__ void k_bit_transpose(const u64* __restrict__ words, long long nw, u64* __restrict__ BT) {
+  __shared__ u64 wsh[64];
+  for (long long w = blockIdx.x; w < nw; w += gridDim.x) {
+    wsh[threadIdx.x] = words[w * 64 + threadIdx.x];
+    __syncthreads();
+    const int j = threadIdx.x;
+    u64 v = 0;
+#pragma unroll 8
+    for (int i = 0; i < 64; ++i) v |= ((wsh[i] >> j) & 1ull) << i;
+    BT[(long long)j * nw + w] = v;
+    __syncthreads();
   }
 }
 
-// S_hi[e_hi][p][coeff] for pairs p = 64 j + j'.  Grid (32 pair tiles, 4 coefficient tiles, n_hi),
-// 256 threads: warp (wm, wn) owns pairs wm*64 .. +63 of the tile (j = 2 blockIdx.x + wm, all j')
-// and limb columns wn*64 .. +63 (4 coefficients).
-__global__ void __launch_bounds__(256, 1)
-k_trunc_s_mma(const unsigned char* __restrict__ BB1, const unsigned char* __restrict__ BB2,
-              long long Epad, const unsigned char* __restrict__ TL8, long long L,
-              u64* __restrict__ S_hi) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  unsigned char* Ls = smem;                               // [2][S_COLS][S_ROWB] limb tile
-  unsigned char* Ps = Ls + 2 * S_COLS * S_ROWB;           // [2][64][S_ROWB]     b2 bytes, rows j'
-  unsigned char* Qs = Ps + 2 * 64 * S_ROWB;               // [2][2][S_ROWB]      b1 bytes, rows j
+__global__ void __launch_bounds__(S_THREADS, 1)
+k_trunc_s_tc(const __grid_constant__ CUtensorMap tmB, const u64* __restrict__ B1T,
+             const u64* __restrict__ B2T, long long nw, long long L, u64* __restrict__ S_hi,
+             unsigned* __restrict__ err, unsigned err_flag) {
+  extern __shared__ unsigned char dsm[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) u64 fullb[S_NST], fulla[S_NST], empty[S_NST], done_bar;
+  __shared__ unsigned tmem_slot;
+  __shared__ int abort_flag;
+  volatile int* abort = &abort_flag;
 
   const int tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  const int wm = warp & 1, wn = warp >> 1;
-  const int pt = blockIdx.x;
-  const int ct = blockIdx.y;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int pt = blockIdx.x, ct = blockIdx.y;
   const long long ehi = blockIdx.z;
-  const int grp = lane >> 2, q = lane & 3;
+  const int nchunks = (int)(L / S_KC);
 
-  const unsigned char* Lsrc = TL8 + (long long)(ct * S_COLS) * L;
-  const long long ebase = ehi * L;
-  const int nkb = (int)(L / S_KB);
+  if (tid == 0) {
+    for (int i = 0; i < S_NST; ++i) {
+      mbar_init(&fullb[i], 1);
+      mbar_init(&fulla[i], 4);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = tmem_slot;
 
-  auto issue = [&](int kb, int stage) {
-    const long long e0 = (long long)kb * S_KB;
-    unsigned char* ld = Ls + stage * S_COLS * S_ROWB;
-#pragma unroll
-    for (int it = 0; it < 8; ++it) {                 // 256 columns x 8 chunks of 16 bytes
-      const int chunk = tid + it * 256;
-      const int col = chunk >> 3, part = chunk & 7;
-      cp_async16(ld + col * S_ROWB + part * 16, Lsrc + (long long)col * L + e0 + part * 16);
-    }
-    unsigned char* pd = Ps + stage * 64 * S_ROWB;
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {                 // 64 rows j' x 8 chunks
-      const int chunk = tid + it * 256;
-      const int row = chunk >> 3, part = chunk & 7;
-      cp_async16(pd + row * S_ROWB + part * 16, BB2 + (long long)row * Epad + ebase + e0 + part * 16);
-    }
-    if (tid < 16) {                                  // 2 rows j x 8 chunks
-      const int row = tid >> 3, part = tid & 7;
-      cp_async16(Qs + (stage * 2 + row) * S_ROWB + part * 16,
-                 BB1 + (long long)(2 * pt + row) * Epad + ebase + e0 + part * 16);
-    }
-    cp_async_commit();
+  auto fail = [&]() {
+    *abort = 1;
+    atomicOr(err, err_flag);
   };
 
-  float acc[4][8][4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t)
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) acc[t][u][i] = 0.f;
-
-  // ldmatrix row addresses: lanes 0-7 rows 0-7 (bytes 0-15), 8-15 rows 8-15, 16-23 rows 0-7
-  // (bytes 16-31), 24-31 rows 8-15 (bytes 16-31)
-  const int lrow = (lane & 7) + ((lane >> 3) & 1) * 8;
-  const int lcol = (lane >> 4) * 16;
-
-  issue(0, 0);
-  for (int kb = 0; kb < nkb; ++kb) {
-    const int stage = kb & 1;
-    cp_async_wait0();
-    __syncthreads();
-    if (kb + 1 < nkb) issue(kb + 1, stage ^ 1);
-    const unsigned char* Lt = Ls + stage * S_COLS * S_ROWB;
-    const unsigned char* Pt = Ps + stage * 64 * S_ROWB;
-    const unsigned char* Qt = Qs + (stage * 2 + wm) * S_ROWB;
-#pragma unroll 1
-    for (int g = 0; g < 4; ++g) {                    // k32 steps of this stage
-      const unsigned mlo = *reinterpret_cast<const unsigned*>(Qt + g * 32 + 4 * q);
-      const unsigned mhi = *reinterpret_cast<const unsigned*>(Qt + g * 32 + 16 + 4 * q);
-      unsigned a[4][4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        ldsm_x4(Pt + (16 * t + lrow) * S_ROWB + g * 32 + lcol, a[t][0], a[t][1], a[t][2], a[t][3]);
-        a[t][0] &= mlo; a[t][1] &= mlo; a[t][2] &= mhi; a[t][3] &= mhi;
+  if (warp == 4) {
+    // ---- TMA producer: limb-table tile (256 columns x 128 e) per chunk ----
+    if (lane == 0) {
+      int last = -1;
+      for (int c = 0; c < nchunks; ++c) {
+        const int st = c % S_NST;
+        if (c >= S_NST && !mbar_wait(&empty[st], (unsigned)(((c / S_NST) + 1) & 1), abort)) {
+          fail();
+          break;
+        }
+        mbar_expect_tx(&fullb[st], (unsigned)S_BTILE);
+        tma_load_2d(base + st * S_STAGE + 2 * S_ATILE, &tmB, &fullb[st], c * S_KC, ct * S_TCOLS);
+        last = c;
       }
+      for (int c = last; c >= 0 && c > last - S_NST; --c)
+        mbar_wait_plain(&fullb[c % S_NST], (unsigned)((c / S_NST) & 1));
+    }
+  } else if (warp == 5) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      const u64 d0 = smem_desc(base, 128);
+      for (int c = 0; c < nchunks; ++c) {
+        const int st = c % S_NST;
+        const unsigned par = (unsigned)((c / S_NST) & 1);
+        if (!mbar_wait(&fullb[st], par, abort) || !mbar_wait(&fulla[st], par, abort)) {
+          fail();
+          break;
+        }
+        tc_fence_after();
+        const u64 ds = d0 + (u64)((st * S_STAGE) >> 4);
+        const u64 db = ds + (u64)((2 * S_ATILE) >> 4);
 #pragma unroll
-      for (int u2 = 0; u2 < 4; ++u2) {               // two n8 tiles per ldmatrix.x4
-        unsigned b00, b01, b10, b11;
-        // rows: n = wn*64 + 16 u2 + (lane & 7) + 8 ((lane >> 4) & 1); bytes (lane >> 3 & 1) * 16
-        const int nrow = wn * 64 + 16 * u2 + (lane & 7) + ((lane >> 4) & 1) * 8;
-        const int ncol = ((lane >> 3) & 1) * 16;
-        ldsm_x4(Lt + nrow * S_ROWB + g * 32 + ncol, b00, b01, b10, b11);
+        for (int a = 0; a < 2; ++a) {
+          const u64 da = ds + (u64)((a * S_ATILE) >> 4);
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          mma_e4m3(acc[t][2 * u2], a[t][0], a[t][1], a[t][2], a[t][3], b00, b01);
-          mma_e4m3(acc[t][2 * u2 + 1], a[t][0], a[t][1], a[t][2], a[t][3], b10, b11);
+          for (int k = 0; k < S_KC / 32; ++k) {
+            if (c == 0 && k == 0) mma_f8<0>(tmem + (unsigned)(a * 256), da + 2 * k, db + 2 * k);
+            else mma_f8<1>(tmem + (unsigned)(a * 256), da + 2 * k, db + 2 * k);
+          }
+        }
+        mma_commit(&empty[st]);
+      }
+      mma_commit(&done_bar);
+      mbar_wait_plain(&done_bar, 0u);
+    }
+  } else {
+    // ---- A generators (warps 0-3), then the drain ----
+    const int jp = tid & 63, jj = tid >> 6;          // row tid of both tiles: j' and j offset
+    const u64* b2row = B2T + (long long)jp * nw;
+    const u64* b1row0 = B1T + (long long)(4 * pt + jj) * nw;
+    const u64* b1row1 = B1T + (long long)(4 * pt + 2 + jj) * nw;
+    const int r7 = tid & 7;
+    const int roff = (tid >> 3) * 1024 + r7 * 128;
+    const long long w0 = ehi * (L / 64);
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+      const int st = c % S_NST;
+      if (c >= S_NST) {
+        ok = __all_sync(0xffffffffu, mbar_wait(&empty[st], (unsigned)(((c / S_NST) + 1) & 1), abort));
+        if (!ok) break;
+      }
+      const long long w = w0 + 2 * c;
+      const u64 m2lo = b2row[w], m2hi = b2row[w + 1];
+      const u64 m[2][2] = {{b1row0[w] & m2lo, b1row0[w + 1] & m2hi},
+                           {b1row1[w] & m2lo, b1row1[w + 1] & m2hi}};
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        unsigned char* row = base + st * S_STAGE + a * S_ATILE + roff;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {             // 16 e per 16-byte chunk, swizzled position
+          const unsigned bits = (unsigned)(m[a][q >> 2] >> (16 * (q & 3))) & 0xFFFFu;
+          uint4 v;
+          v.x = nibble_bytes(bits & 15u);
+          v.y = nibble_bytes((bits >> 4) & 15u);
+          v.z = nibble_bytes((bits >> 8) & 15u);
+          v.w = nibble_bytes(bits >> 12);
+          *reinterpret_cast<uint4*>(row + ((q ^ r7) << 4)) = v;
         }
       }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&fulla[st]);
+    }
+    if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&done_bar, 0u, abort));
+    if (ok && !*abort) {
+      tc_fence_after();
+      const unsigned tl = tmem + ((unsigned)(warp * 32) << 16);
+#pragma unroll 1
+      for (int a = 0; a < 2; ++a) {
+        const long long pair = (long long)pt * S_TPAIRS + a * 128 + warp * 32 + lane;
+        u64* out = S_hi + (ehi * 4096 + pair) * 64 + ct * 16;
+#pragma unroll 1
+        for (int cc = 0; cc < 16; ++cc) {
+          unsigned v[16];
+          tmem_ld16(tl + (unsigned)(a * 256 + cc * 16), v);
+          tmem_ld_wait();
+          u64 sum = 0;
+#pragma unroll
+          for (int l = 0; l < 16; ++l)   // exact: 0 <= limb sum < 2^23, + 2^23 keeps it integral
+            sum += (u64)(__float_as_uint(__uint_as_float(v[l]) + 8388608.0f) - 0x4B000000u) << (4 * l);
+          out[cc] = sum;
+        }
+      }
+    } else if (!ok && lane == 0) {
+      fail();
     }
   }
-
-  // recombine limbs: coefficient v (0..3) of this warp = tiles u = 2v (limbs 0..7), 2v+1 (8..15)
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      u64 lo = 0, hi = 0;   // rows grp and grp + 8
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int u = 2 * v + h;
-        const int l0 = 8 * h + 2 * q;
-        lo += ((u64)__float2uint_rn(acc[t][u][0]) << (4 * l0)) +
-              ((u64)__float2uint_rn(acc[t][u][1]) << (4 * (l0 + 1)));
-        hi += ((u64)__float2uint_rn(acc[t][u][2]) << (4 * l0)) +
-              ((u64)__float2uint_rn(acc[t][u][3]) << (4 * (l0 + 1)));
-      }
-      lo += __shfl_xor_sync(0xffffffffu, lo, 1);
-      lo += __shfl_xor_sync(0xffffffffu, lo, 2);
-      hi += __shfl_xor_sync(0xffffffffu, hi, 1);
-      hi += __shfl_xor_sync(0xffffffffu, hi, 2);
-      if (q == v) {
-        const int pr = pt * S_PAIRS + wm * 64 + 16 * t + grp;
-        const int coeff = ct * 16 + wn * 4 + v;
-        S_hi[(ehi * 4096 + pr) * 64 + coeff] = lo;
-        S_hi[(ehi * 4096 + pr + 8) * 64 + coeff] = hi;
-      }
-    }
-  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 // out[p][c] = reduce(sum_{a+b=s} P[a*ld + p*64 + b]) for n pairs.
@@ -252,8 +284,6 @@ __global__ void k_fold_reduce_strided(const u64* __restrict__ P, long long ld, u
 
 }  // namespace
 
-size_t trunc_s_smem_bytes() { return (size_t)(2 * S_COLS + 2 * 64 + 2 * 2) * S_ROWB; }
-
 void launch_trunc_limb_table(cudaStream_t st, const u64* Tlo, long long L, unsigned char* TL8) {
   const long long total = 1024 * (L / 16);
   long long g = (total + 255) / 256;
@@ -261,20 +291,30 @@ void launch_trunc_limb_table(cudaStream_t st, const u64* Tlo, long long L, unsig
   k_limb_table<<<(unsigned)g, 256, 0, st>>>(Tlo, L, TL8);
 }
 
-void launch_trunc_bit_bytes(cudaStream_t st, const u64* words, long long Epad, unsigned char* BB) {
-  const long long total = 64 * (Epad / 16);
-  long long g = (total + 255) / 256;
-  if (g > (1ll << 20)) g = 1ll << 20;
-  k_bit_bytes<<<(unsigned)g, 256, 0, st>>>(words, Epad, BB);
+void launch_trunc_bit_transpose(cudaStream_t st, const u64* words, long long Epad, u64* BT) {
+  const long long nw = Epad / 64;
+  const long long g = nw < (1ll << 20) ? nw : (1ll << 20);
+  k_bit_transpose<<<(unsigned)g, 64, 0, st>>>(words, nw, BT);
 }
 
-void launch_trunc_s_mma(cudaStream_t st, const unsigned char* BB1, const unsigned char* BB2,
-                        long long Epad, const unsigned char* TL8, long long L, long long nhi,
-                        u64* S_hi) {
-  const size_t smem = trunc_s_smem_bytes();
-  cudaFuncSetAttribute(k_trunc_s_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  dim3 grid(4096 / S_PAIRS, 64 / 16, (unsigned)nhi);
-  k_trunc_s_mma<<<grid, 256, smem, st>>>(BB1, BB2, Epad, TL8, L, S_hi);
+int launch_trunc_s_tc(cudaStream_t st, const u64* B1T, const u64* B2T, long long Epad,
+                      const unsigned char* TL8, long long L, long long nhi, u64* S_hi,
+                      unsigned* err, unsigned err_flag) {
+  auto enc = encode_fn();
+  if (!enc || L % S_KC != 0) return -2;
+  CUtensorMap mb;
+  cuuint64_t dims[2] = {(cuuint64_t)L, 1024};
+  cuuint64_t strides[1] = {(cuuint64_t)L};
+  cuuint32_t box[2] = {(cuuint32_t)S_KC, (cuuint32_t)S_TCOLS};
+  cuuint32_t es[2] = {1, 1};
+  if (enc(&mb, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<unsigned char*>(TL8), dims, strides,
+          box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return -2;
+  cudaFuncSetAttribute(k_trunc_s_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S_SMEM);
+  dim3 grid(4096 / S_TPAIRS, 1024 / S_TCOLS, (unsigned)nhi);
+  k_trunc_s_tc<<<grid, S_THREADS, S_SMEM, st>>>(mb, B1T, B2T, Epad / 64, L, S_hi, err, err_flag);
+  return 0;
 }
 
 void launch_fold_reduce_strided(cudaStream_t st, const u64* P, long long ld, int npairs, u64* out) {

@@ -27,7 +27,8 @@ PROTOS = ("share", "mult", "inner", "trunc", "rec", "verify")
 TRACE_ROUND = 832
 NOALLOC_MAX_N = 262144
 PROF_PHASES = ("share", "mult", "trunc_pairs", "gemm", "exchange", "verify_gemm", "trunc_setup",
-               "trunc_s", "trunc_rounds", "trunc_materialize", "trunc_tail", "rec", "verify_mult")
+               "trunc_s", "trunc_rounds", "trunc_materialize", "trunc_tail", "rec", "verify_mult",
+               "k_limb_gemm", "k_trunc_s")
 ERR_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_WORKSPACE", 4: "ERR_CUDA",
              5: "ERR_TIMEOUT", 6: "ERR_VERIFY", 7: "ERR_ABORT", 8: "ERR_PENDING"}
 
