@@ -286,6 +286,29 @@ void gram(mpc_ctx* ctx, u64* P, const u64* U0, const u64* U1, u64 su, long long 
   gemm_u64(ctx->st, 64, 64, count, 1, &T, epi_atomic(P, 64, sign), nsplit_for(count));
 }
 
+// out[i] = add0[i] + (p0[i] + s1 p1[i]) . M for i < R (rows of 64 words, M a 64 x 64 GR
+// multiplication matrix): the folds of Pi_Reduce and the products by a fixed GR element.  Tensor
+// cores on the limb path, the u64 CUDA-core GEMM otherwise.
+int gr_matmul(mpc_ctx* ctx, long long R, const u64* p0, const u64* p1, u64 s1, long long lda,
+              const u64* Mmat, const u64* add0, long long ld_add0, u64* out, long long ldc) {
+  if (R <= 0) return MPC_OK;
+  if (ctx->gemm_path == MPC_GEMM_LIMB_TC) {
+    g_launches += 1;
+    if (gr_matmul_tc(ctx->st, R, p0, p1, s1, lda, Mmat, add0, ld_add0, out, ldc, ctx->status,
+                     ST_TIMEOUT) == 0)
+      return MPC_OK;
+    g_launches -= 1;   // misaligned view: fall through to the CUDA-core GEMM
+  }
+  GemmTerm T;
+  T.A = p1 ? op(p0, lda, 0, p1, s1) : op(p0, lda);
+  T.B = op(Mmat, 64);
+  Epi e = epi_store(out, ldc);
+  e.add0 = add0;
+  e.ld_add0 = add0 ? ld_add0 : 0;
+  gemm_u64(ctx->st, R, 64, 64, 1, &T, e, 1);
+  return MPC_OK;
+}
+
 // A view of a <.>^{l[x]}-shared vector: component pointers (null = identically zero), row stride.
 struct View {
   const u64* c[6];
@@ -488,13 +511,7 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
       u64* out = side ? yo.c[c] : xo.c[c];
       if (!in) continue;
       // f(zeta) = f(0) + zeta (f(1) - f(0)): rows [x_{2i+1} - x_{2i}] times M_zeta, plus x_{2i}
-      GemmTerm T;
-      T.A = op(in + 64, 128, 0, in, ~0ull);
-      T.B = op(s.MM, 64);
-      Epi e = epi_store(out, 64);
-      e.add0 = in;
-      e.ld_add0 = 128;
-      gemm_u64(st, Dh, 64, 64, 1, &T, e, 1);
+      if ((rc = gr_matmul(ctx, Dh, in + 64, in, ~0ull, 128, s.MM, in, 128, out, 64))) return rc;
     }
   }
   trace_round(ctx, trace, k, s);
@@ -1169,10 +1186,9 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
       launch_gr_powers(st, s.aux + 128, p.nhi, p.Thi);
       for (long long h = 1; h < p.nhi; ++h) {
         launch_gr_mulmat2(st, p.Thi + h * 64, nullptr, p.Mhi);
-        GemmTerm T;
-        T.A = op(p.Rtab, 64);
-        T.B = op(p.Mhi, 64);
-        gemm_u64(st, p.L, 64, 64, 1, &T, epi_store(p.Rtab + h * p.L * 64, 64), 1);
+        if ((rc = gr_matmul(ctx, p.L, p.Rtab, nullptr, 1, 64, p.Mhi, nullptr, 0,
+                            p.Rtab + h * p.L * 64, 64)))
+          return rc;
       }
     }
     CK(cudaMemsetAsync(p.Zpq, 0, 12 * 64 * 8, st));

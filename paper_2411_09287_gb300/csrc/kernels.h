@@ -56,6 +56,13 @@ int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nte
                  const GemmTerm* terms, const Epi& epi, void* scratch, unsigned* err,
                  unsigned err_flag, cudaEvent_t ev0, cudaEvent_t ev1);
 
+// out[i][c] = add0[i][c] + sum_k (p0[i][k] + s1 p1[i][k]) M[k][c], i < R, k, c < 64 (M row-major
+// 64 x 64, p1 and add0 may be null; ld_add0 = 0 means ldc).  Exact, on the tensor cores.  Needs
+// 16-byte aligned bases and even row strides (returns -1 otherwise).
+int gr_matmul_tc(cudaStream_t st, long long R, const u64* p0, const u64* p1, u64 s1, long long lda,
+                 const u64* Mmat, const u64* add0, long long ld_add0, u64* out, long long ldc,
+                 unsigned* err, unsigned err_flag);
+
 // ---- elementwise protocol kernels (prf_kernels.cu) ------------------------------------------
 void launch_share_input(cudaStream_t st, const u64* x, long long n, Key k01, Key k02, u64 obj,
                         u64* s6, u64* p0_out_m);

@@ -371,6 +371,248 @@ bool make_map(CUtensorMap* map, void* planes, long long rows, long long Kp, int 
   return r == CUDA_SUCCESS;
 }
 
+// ---- GR-matrix products out = add0 + A . M with K = N = 64 (folds, powers tables) -------------
+// out[i][c] = add0[i][c] + sum_k A[i][k] M[k][c] for rows i < R, with A[i][k] = p0[i][k] + s1 p1[i][k]
+// (row stride lda) and M a 64 x 64 u64 matrix (the multiplication matrix of a GR element).
+// Same digit scheme and accumulator groups as k_limb_gemm_tc; the differences:
+//   - persistent CTAs loop over 128-row tiles; K = 64 is two chunks of 32;
+//   - B = M^T is split into digit planes once per CTA and stays in shared memory (64 KB);
+//   - three producer warps load the A rows from global memory and split them into the swizzled
+//     digit planes directly (no digit-plane copy in HBM); the MMA issuer and the 8 drain warps
+//     are as before, the drain warps add add0 and store the tile.
+constexpr int GM_PROD = 3;
+constexpr int GM_THREADS = (NDRAIN + GM_PROD + 1) * 32;   // 416
+constexpr int GM_BCHUNK = 8 * B_TILE;                     // 32 KB: B planes of one K chunk
+constexpr size_t GM_SMEM = (size_t)2 * GM_BCHUNK + (size_t)NSTAGE * 8 * A_TILE + 1024;
+
+// byte offset of 16-byte unit u (8 bf16 along K) of row r inside a K-major 64-byte-swizzled tile
+__device__ __forceinline__ int sw64_off(int r, int u) {
+  return (r >> 3) * 512 + (r & 7) * 64 + ((u ^ ((r >> 1) & 3)) << 4);
+}
+
+// 8 consecutive u64 values -> 8 digit planes of 8 bf16 each (one 16-byte unit per plane)
+__device__ __forceinline__ void split8_store(const u64 v[8], unsigned char* plane0, int plane_stride,
+                                             int off) {
+  unsigned packed[8][4];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    int d[8];
+    balanced_digits(v[q], d);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const unsigned b = bf16_bits(d[i]);
+      if (q & 1) packed[i][q >> 1] |= b << 16;
+      else packed[i][q >> 1] = b;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    *reinterpret_cast<uint4*>(plane0 + i * plane_stride + off) =
+        make_uint4(packed[i][0], packed[i][1], packed[i][2], packed[i][3]);
+}
+
+__global__ void __launch_bounds__(GM_THREADS, 1)
+k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ p1, u64 s1,
+               long long lda, const u64* __restrict__ Mmat, const u64* __restrict__ add0,
+               long long ld_add0, u64* __restrict__ out, long long ldc,
+               unsigned* __restrict__ err, unsigned err_flag) {
+  extern __shared__ unsigned char dsm[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
+  unsigned char* Bsm = base;                       // [2 chunks][8 planes][64 rows][64 B]
+  unsigned char* Asm = base + 2 * GM_BCHUNK;       // [NSTAGE][8 planes][128 rows][64 B]
+  __shared__ __align__(8) u64 full_bar[NSTAGE], empty_bar[NSTAGE];
+  __shared__ __align__(8) u64 accf_bar[2], acce_bar[2], done_bar;
+  __shared__ unsigned tmem_slot;
+  __shared__ int abort_flag;
+  volatile int* abort = &abort_flag;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const long long ntiles = (R + TC_BM - 1) / TC_BM;
+  const long long my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const long long nunits = 2 * my_tiles;
+
+  if (tid == 0) {
+    for (int i = 0; i < NSTAGE; ++i) {
+      mbar_init(&full_bar[i], GM_PROD);
+      mbar_init(&empty_bar[i], 1);
+    }
+    for (int g = 0; g < 2; ++g) {
+      mbar_init(&accf_bar[g], 1);
+      mbar_init(&acce_bar[g], NDRAIN);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = tmem_slot;
+
+  auto fail = [&]() {
+    *abort = 1;
+    atomicOr(err, err_flag);
+  };
+
+  if (warp >= NDRAIN && warp < NDRAIN + GM_PROD) {
+    // ---- producers: B planes once, then the A planes of every (tile, chunk) ----
+    const int pt = tid - NDRAIN * 32;   // 0 .. 32 GM_PROD - 1
+    for (int it = pt; it < 64 * 8; it += GM_PROD * 32) {   // (row c of M^T, unit of 8 k)
+      const int c = it >> 3, k8 = it & 7;
+      u64 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = Mmat[(k8 * 8 + q) * 64 + c];
+      split8_store(v, Bsm + (k8 >> 2) * GM_BCHUNK, B_TILE, sw64_off(c, k8 & 3));
+    }
+    bool ok = true;
+    for (long long u = 0; u < nunits && ok; ++u) {
+      const int st = (int)(u % NSTAGE);
+      if (u >= NSTAGE) {
+        ok = __all_sync(0xffffffffu,
+                        mbar_wait(&empty_bar[st], (unsigned)(((u / NSTAGE) + 1) & 1), abort));
+        if (!ok) break;
+      }
+      const long long tile = blockIdx.x + (u >> 1) * gridDim.x;
+      const int kc = (int)(u & 1);
+      unsigned char* As = Asm + st * 8 * A_TILE;
+      constexpr int NIT = (512 + GM_PROD * 32 - 1) / (GM_PROD * 32);   // items per thread
+#pragma unroll
+      for (int q0 = 0; q0 < NIT; q0 += 2) {         // two items in flight per thread
+        u64 v[2][8];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int item = pt + (q0 + q) * GM_PROD * 32;   // 512 items: (row, unit of 8 k)
+          const int r = item >> 2, k8 = item & 3;
+          const long long row = tile * TC_BM + r;
+          const long long off = row * lda + kc * 32 + k8 * 8;
+#pragma unroll
+          for (int j = 0; j < 8; j += 2) {
+            if (item < 512 && row < R) {
+              const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(p0 + off + j);
+              v[q][j] = a.x;
+              v[q][j + 1] = a.y;
+              if (p1) {
+                const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(p1 + off + j);
+                v[q][j] += s1 * b.x;
+                v[q][j + 1] += s1 * b.y;
+              }
+            } else {
+              v[q][j] = v[q][j + 1] = 0;
+            }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int item = pt + (q0 + q) * GM_PROD * 32;
+          if (item < 512) split8_store(v[q], As, A_TILE, sw64_off(item >> 2, item & 3));
+        }
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full_bar[st]);
+    }
+    if (!ok && lane == 0) fail();
+  } else if (warp == NDRAIN + GM_PROD) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      const u64 da0 = smem_desc(Asm, 64);
+      const u64 db0 = smem_desc(Bsm, 64);
+      for (long long u = 0; u < nunits; ++u) {
+        const int st = (int)(u % NSTAGE);
+        if (!mbar_wait(&full_bar[st], (unsigned)((u / NSTAGE) & 1), abort)) { fail(); break; }
+        tc_fence_after();
+        const u64 ad = da0 + (u64)((st * 8 * A_TILE) >> 4);
+        const u64 bd = db0 + (u64)(((int)(u & 1) * GM_BCHUNK) >> 4);
+        if (u > 0 && !mbar_wait(&acce_bar[0], (unsigned)((u - 1) & 1), abort)) { fail(); break; }
+        tc_fence_after();
+        issue_group<0>(tmem, ad, bd);
+        mma_commit(&accf_bar[0]);
+        if (u > 0 && !mbar_wait(&acce_bar[1], (unsigned)((u - 1) & 1), abort)) { fail(); break; }
+        tc_fence_after();
+        issue_group<1>(tmem, ad, bd);
+        mma_commit(&accf_bar[1]);
+        mma_commit(&empty_bar[st]);
+      }
+      mma_commit(&done_bar);
+      mbar_wait_plain(&done_bar, 0u);
+    }
+  } else if (warp < NDRAIN) {
+    // ---- drain warps: rows 32 (w % 4) + lane, columns 32 (w / 4) .. +31 ----
+    const int q4 = warp & 3, h = warp >> 2;
+    const unsigned tl = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)(h * 32);
+    u64 acc[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = 0;
+    bool ok = true;
+    for (long long u = 0; u < nunits && ok; ++u) {
+      const unsigned par = (unsigned)(u & 1);
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        ok = __all_sync(0xffffffffu, mbar_wait(&accf_bar[g], par, abort));
+        if (!ok) break;
+        tc_fence_after();
+        const int s0 = g == 0 ? 0 : 2;
+        const int s1d = g == 0 ? 6 : 4;
+#pragma unroll
+        for (int c16 = 0; c16 < 2; ++c16) {
+          unsigned x0[16], x1[16];
+          // pair (s0, s0 + 1): + ws (g = 0) or 2^16 ws (g = 1), ws sign-extended
+          tmem_ld16(tl + (unsigned)(acc_col(s0) + c16 * 16), x0);
+          tmem_ld16(tl + (unsigned)(acc_col(s0 + 1) + c16 * 16), x1);
+          tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const unsigned ws =
+                (unsigned)f2i_biased(x0[j]) + (unsigned)f2i_biased(x1[j]) * 256u - PAIR_BIAS;
+            acc[c16 * 16 + j] += g == 0 ? (u64)(long long)(int)ws : (u64)(long long)(int)ws << 16;
+          }
+          // pair (s1, s1 + 1): + 2^48 whi (g = 0) or 2^32 whi (g = 1); its bias is removed per tile
+          tmem_ld16(tl + (unsigned)(acc_col(s1d) + c16 * 16), x0);
+          tmem_ld16(tl + (unsigned)(acc_col(s1d + 1) + c16 * 16), x1);
+          tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const unsigned whi = (unsigned)f2i_biased(x0[j]) + (unsigned)f2i_biased(x1[j]) * 256u;
+            acc[c16 * 16 + j] += (u64)(g == 0 ? (whi << 16) : whi) << 32;
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce_bar[g]);
+      }
+      if (ok && (u & 1)) {   // tile complete: remove the biases of its two chunks, add, store
+        const long long tile = blockIdx.x + (u >> 1) * gridDim.x;
+        const long long r = tile * TC_BM + q4 * 32 + lane;
+        const u64 corr = (u64)(2u * CHUNK_HI_BIAS) << 32;
+        if (r < R) {
+          const u64* a0p = add0 ? add0 + r * ld_add0 + h * 32 : nullptr;
+          u64* o = out + r * ldc + h * 32;
+#pragma unroll
+          for (int c = 0; c < 32; c += 2) {
+            u64 x0 = acc[c] - corr, x1 = acc[c + 1] - corr;
+            if (a0p) {
+              const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(a0p + c);
+              x0 += a.x;
+              x1 += a.y;
+            }
+            *reinterpret_cast<ulonglong2*>(o + c) = make_ulonglong2(x0, x1);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc[c] = 0;
+      }
+    }
+    if (!ok && lane == 0) fail();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
 }  // namespace
 
 size_t limb_tc_scratch_bytes(long long M, long long N, long long K, int nterms) {
@@ -407,6 +649,30 @@ int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nte
   if (ge > (1 << 20)) ge = 1 << 20;
   if (ge < 1) ge = 1;
   k_apply_epilogue<<<(unsigned)ge, 256, 0, st>>>(M, N, epi);
+  return 0;
+}
+
+int gr_matmul_tc(cudaStream_t st, long long R, const u64* p0, const u64* p1, u64 s1, long long lda,
+                 const u64* Mmat, const u64* add0, long long ld_add0, u64* out, long long ldc,
+                 unsigned* err, unsigned err_flag) {
+  if (R <= 0) return 0;
+  // 16-byte vector accesses: row strides and bases must keep 2-word alignment
+  if ((lda & 1) || (ldc & 1) || (add0 && (ld_add0 & 1)) ||
+      ((reinterpret_cast<uintptr_t>(p0) | reinterpret_cast<uintptr_t>(p1) |
+        reinterpret_cast<uintptr_t>(add0) | reinterpret_cast<uintptr_t>(out)) & 15))
+    return -1;
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 148;
+  }
+  const long long ntiles = (R + TC_BM - 1) / TC_BM;
+  const unsigned grid = (unsigned)(ntiles < nsm ? ntiles : nsm);
+  cudaFuncSetAttribute(k_gr_matmul_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GM_SMEM);
+  k_gr_matmul_tc<<<grid, GM_THREADS, GM_SMEM, st>>>(R, p0, p1, s1, lda, Mmat, add0,
+                                                     ld_add0 ? ld_add0 : ldc, out, ldc, err, err_flag);
   return 0;
 }
 

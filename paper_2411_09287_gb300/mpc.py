@@ -103,6 +103,9 @@ class Context:
     def empty(self, nwords: int):
         return self.torch.empty(max(int(nwords), 1), dtype=self.torch.int64, device=self.device)
 
+    def zeros(self, nwords: int):
+        return self.torch.zeros(max(int(nwords), 1), dtype=self.torch.int64, device=self.device)
+
     def shares(self, n: int):
         return self.empty(6 * n)
 
@@ -167,7 +170,7 @@ class Context:
                     trace: bool = False):
         """Returns (code, trace): code MPC_OK (accept), MPC_ERR_VERIFY or MPC_ERR_ABORT."""
         Rr = default_R(n) if R < 0 else R
-        tr = self.empty((Rr + 1) * TRACE_ROUND) if trace else None
+        tr = self.zeros((Rr + 1) * TRACE_ROUND) if trace else None
         wsb = self.ws_size(OP_VERIFY_MULT, n, R_main=R)
         ws = self.workspace(wsb)
         rc = self.lib.mpc_verify_mult(self.h, verify_id, C.c_void_p(_ptr(xs)), C.c_void_p(_ptr(ys)),
@@ -183,7 +186,7 @@ class Context:
         R0 = default_R(K) if R_main < 0 else R_main
         R1 = default_R(64 * M * N) if R_trunc < 0 else R_trunc
         ntr = (R0 + 1) * TRACE_ROUND + ((R1 + 1) * TRACE_ROUND if trunc_bits >= 0 else 0)
-        tr = self.empty(ntr) if trace else None
+        tr = self.zeros(ntr) if trace else None
         wsb = self.ws_size(OP_VERIFY_MATMUL, M, N, K, trunc_bits, R_main, R_trunc)
         ws = self.workspace(wsb)
         rc = self.lib.mpc_verify_matmul(self.h, verify_id, C.c_void_p(_ptr(xs)), C.c_void_p(_ptr(ws_)),

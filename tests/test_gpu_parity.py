@@ -202,6 +202,36 @@ def test_tc_gemm_full_range_words(mpc, M, N, K):
     assert_shared_equal(gpu_shared(mpc, zpre, (M, N)), res.z_pre, "zpre")
 
 
+@pytest.mark.parametrize("M,N,K", [(300, 300, 16), (64, 1100, 8)])
+def test_tc_and_u64_paths_give_identical_verification(mpc, M, N, K):
+    """At sizes whose trunc batch spans several e_hi blocks (E > 65536) and many row tiles, the
+    tensor-core path (limb GEMMs, tensor-core folds and table products) and the u64 CUDA-core
+    path give the same products, the same verification transcript and the same opened output;
+    both paths are pinned to the oracle on the smaller shapes above."""
+    seed = seed_of(f"paths-{M}-{N}-{K}")
+    g = workloads.rng(f"paths-{M}-{N}-{K}")
+    X = mpc.encode_fixed(g.uniform(-4, 4, (M, K)), 13)
+    W = mpc.encode_fixed(g.uniform(-4, 4, (K, N)), 13)
+    res = []
+    for path in (0, 1):
+        ctx = mpc.Context(seed, gemm_path=path)
+        gx, gw = ctx.share_input(1, X), ctx.share_input(2, W)
+        zpre, zout, pq = ctx.matmul(3, gx, gw, M, N, K, 13)
+        rc, tr = ctx.verify_matmul(4, gx, gw, zpre, pq, M, N, K, 13, 3, trace=True)
+        assert rc == mpc.MPC_OK
+        out = ctx.reconstruct(zout, M * N)
+        res.append((mpc.to_u64(zpre).copy(), mpc.to_u64(tr).copy(), out))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])
+    assert np.array_equal(res[0][2], res[1][2])
+    # the opened product is the plaintext product, truncated (one-LSB carry allowed)
+    Z = (X.astype(object) @ W.astype(object))
+    ref = np.array([[(int(v) % 2**64) for v in row] for row in Z], dtype=np.uint64)
+    sref = ref.view(np.int64) >> 13
+    got = res[1][2].reshape(M, N).view(np.int64)
+    assert np.all(np.abs(got - sref) <= 1)
+
+
 @pytest.mark.parametrize("R_main,R_trunc", [(0, 0), (2, 3), (7, 9)])
 def test_matmul_verify_explicit_R(mpc, R_main, R_trunc):
     M, N, K, t = 6, 4, 20, 13
