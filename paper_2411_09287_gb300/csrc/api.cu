@@ -58,6 +58,7 @@ inline void counted(int k, F f, A... a) {
 #define launch_trunc_round_h(...) counted(1, mpc3::launch_trunc_round_h, __VA_ARGS__)
 #define launch_trunc_update_vw(...) counted(1, mpc3::launch_trunc_update_vw, __VA_ARGS__)
 #define launch_trunc_materialize(...) counted(1, mpc3::launch_trunc_materialize, __VA_ARGS__)
+#define launch_gr_mul_rows(...) counted(1, mpc3::launch_gr_mul_rows, __VA_ARGS__)
 #define launch_gr_rec1(...) counted(1, mpc3::launch_gr_rec1, __VA_ARGS__)
 #define launch_gr_inner_finish_all(...) counted(1, mpc3::launch_gr_inner_finish_all, __VA_ARGS__)
 #define launch_gr_quad_combine(...) counted(1, mpc3::launch_gr_quad_combine, __VA_ARGS__)
@@ -294,7 +295,7 @@ int gr_matmul(mpc_ctx* ctx, long long R, const u64* p0, const u64* p1, u64 s1, l
   if (R <= 0) return MPC_OK;
   if (ctx->gemm_path == MPC_GEMM_LIMB_TC) {
     g_launches += 1;
-    if (gr_matmul_tc(ctx->st, R, p0, p1, s1, lda, Mmat, add0, ld_add0, out, ldc, ctx->status,
+    if (gr_matmul_tc(ctx->st, R, p0, p1, s1, lda, 0, Mmat, add0, ld_add0, out, ldc, ctx->status,
                      ST_TIMEOUT) == 0)
       return MPC_OK;
     g_launches -= 1;   // misaligned view: fall through to the CUDA-core GEMM
@@ -483,14 +484,30 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
     // G00, G11 and G(x0 + x1, y0 + y1); G01 + G10 = G(x0 + x1, y0 + y1) - G00 - G11
     CK(cudaMemsetAsync(s.Pmat, 0, 3 * 4096 * 8, st));
     CK(cudaMemsetAsync(s.S, 0, 4 * 192 * 8, st));
-    gram(ctx, s.Pmat, x.c[0], nullptr, 1, 128, y.c[1], nullptr, 1, 128, Dh, 1);
-    gram(ctx, s.Pmat + 4096, x.c[0] + 64, nullptr, 1, 128, y.c[1] + 64, nullptr, 1, 128, Dh, 1);
-    gram(ctx, s.Pmat + 8192, x.c[0], x.c[0] + 64, 1, 128, y.c[1], y.c[1] + 64, 1, 128, Dh, 1);
-    launch_gr_fold_reduce(st, s.Pmat, 3, s.aux);            // aux: G00, G11, Gsum (64 each)
-    CK(cudaMemcpyAsync(S00, s.aux, 512, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(S11, s.aux + 64, 512, cudaMemcpyDeviceToDevice, st));
-    launch_gr_lincomb(st, ctx->cst + CST_ONE, s.aux + 128, ctx->cst + CST_MONE, s.aux, s.aux + 192);
-    launch_gr_lincomb(st, ctx->cst + CST_ONE, s.aux + 192, ctx->cst + CST_MONE, s.aux + 64, S01);
+    bool done = false;
+    if (ctx->gemm_path == MPC_GEMM_LIMB_TC) {
+      // tensor cores: G00, G11 and the cross sum G01 + G10 directly
+      g_launches += 1;
+      done = gram3_tc(st, Dh, x.c[0], y.c[1], s.Pmat, ctx->status, ST_TIMEOUT) == 0;
+      if (done) {
+        launch_gr_fold_reduce(st, s.Pmat, 3, s.aux);
+        CK(cudaMemcpyAsync(S00, s.aux, 512, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(S11, s.aux + 64, 512, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(S01, s.aux + 128, 512, cudaMemcpyDeviceToDevice, st));
+      } else {
+        g_launches -= 1;
+      }
+    }
+    if (!done) {
+      gram(ctx, s.Pmat, x.c[0], nullptr, 1, 128, y.c[1], nullptr, 1, 128, Dh, 1);
+      gram(ctx, s.Pmat + 4096, x.c[0] + 64, nullptr, 1, 128, y.c[1] + 64, nullptr, 1, 128, Dh, 1);
+      gram(ctx, s.Pmat + 8192, x.c[0], x.c[0] + 64, 1, 128, y.c[1], y.c[1] + 64, 1, 128, Dh, 1);
+      launch_gr_fold_reduce(st, s.Pmat, 3, s.aux);            // aux: G00, G11, Gsum (64 each)
+      CK(cudaMemcpyAsync(S00, s.aux, 512, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(S11, s.aux + 64, 512, cudaMemcpyDeviceToDevice, st));
+      launch_gr_lincomb(st, ctx->cst + CST_ONE, s.aux + 128, ctx->cst + CST_MONE, s.aux, s.aux + 192);
+      launch_gr_lincomb(st, ctx->cst + CST_ONE, s.aux + 192, ctx->cst + CST_MONE, s.aux + 64, S01);
+    }
   } else {
     if ((rc = party_sums(ctx, f[0], g[0], Dh, s.Pmat, S00))) return rc;
     if ((rc = party_sums(ctx, f[0], g[1], Dh, s.Pmat + 3 * 4096, S01))) return rc;
@@ -1249,10 +1266,29 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
     // materialise the folded vectors: x.[r]_1 at P0 and P1, y.[r]_2 at P0 and P2
     Vec& tx = p.dt.x[0];
     Vec& ty = p.dt.y[0];
-    launch_trunc_materialize(st, E, p.b1, p.V, p.Rtab, p.kd, tx.c[0]);
-    launch_trunc_materialize(st, E, p.b1, p.V, p.Rtab, p.kd, tx.c[3]);
-    launch_trunc_materialize(st, E, p.b2, p.W, nullptr, p.kd, ty.c[1]);
-    launch_trunc_materialize(st, E, p.b2, p.W, nullptr, p.kd, ty.c[5]);
+    if (ctx->gemm_path == MPC_GEMM_LIMB_TC && p.kd == 6) {
+      // one folded element per output e: -sum_j V_j b_{e,j} as a product of the bit matrix with
+      // -V on the tensor cores, then (x only) the GR product with r^(2e), for each party's copy
+      u64* nV = s.MM;
+      u64* nW = s.MM + 4096;
+      launch_neg_copy(st, p.V, 4096, nV);
+      launch_neg_copy(st, p.W, 4096, nW);
+      const u64* bits[4] = {p.b1, p.b1, p.b2, p.b2};
+      const u64* mats[4] = {nV, nV, nW, nW};
+      u64* outs[4] = {tx.c[0], tx.c[3], ty.c[1], ty.c[5]};
+      for (int v = 0; v < 4; ++v) {
+        g_launches += 1;
+        if (gr_matmul_tc(st, E, bits[v], nullptr, 1, 1, 1, mats[v], nullptr, 0, outs[v], 64,
+                         ctx->status, ST_TIMEOUT))
+          return fail(ctx, MPC_ERR_CUDA, "verify_matmul: folded-vector product");
+        if (v < 2) launch_gr_mul_rows(st, E, outs[v], p.Rtab, outs[v]);
+      }
+    } else {
+      launch_trunc_materialize(st, E, p.b1, p.V, p.Rtab, p.kd, tx.c[0]);
+      launch_trunc_materialize(st, E, p.b1, p.V, p.Rtab, p.kd, tx.c[3]);
+      launch_trunc_materialize(st, E, p.b2, p.W, nullptr, p.kd, ty.c[1]);
+      launch_trunc_materialize(st, E, p.b2, p.W, nullptr, p.kd, ty.c[5]);
+    }
     delete phase;
     if ((rc = cuda_check(ctx, "trunc batch"))) return rc;
     phase = new Phase(ctx, MPC_PROF_TRUNC_TAIL);

@@ -461,6 +461,69 @@ k_trunc_materialize(long long E, const u64* __restrict__ words, const u64* __res
 }
 
 
+// out[e] = a[e] * b[e] in GR(2^64, 64) for e < n (rows of 64 words; out may alias a or b).
+// One warp per element: lane l forms the product coefficients 4l .. 4l + 3 with a sliding window
+// over b (zero-padded in shared memory, so no bounds tests), then the warp reduces mod f.  Word j
+// of the padded b sits at j + j / 8, which makes the lanes' window loads (4 words apart)
+// conflict-free.
+__device__ __forceinline__ int padj(int j) { return j + (j >> 3); }
+
+__global__ void __launch_bounds__(256)
+k_gr_mul_rows(long long n, const u64* __restrict__ a, const u64* __restrict__ b, u64* out) {
+  __shared__ u64 sa[8][64], sbp[8][216], sc[8][128];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int i = l; i < 216; i += 32) sbp[w][i] = 0;
+  __syncwarp();
+  const long long stride = (long long)gridDim.x * 8;
+  for (long long e = (long long)blockIdx.x * 8 + w; e < n; e += stride) {
+    sa[w][l] = a[e * 64 + l];
+    sa[w][l + 32] = a[e * 64 + l + 32];
+    sbp[w][padj(64 + l)] = b[e * 64 + l];
+    sbp[w][padj(96 + l)] = b[e * 64 + l + 32];
+    __syncwarp();
+    const int k0 = 4 * l;
+    // window w_m = b[k0 + m - i] = padded word 64 + k0 + m - i
+    u64 w0 = sbp[w][padj(64 + k0)], w1 = sbp[w][padj(65 + k0)], w2 = sbp[w][padj(66 + k0)],
+        w3 = sbp[w][padj(67 + k0)];
+    u64 c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+#pragma unroll
+    for (int i = 0; i < 64; ++i) {
+      const u64 ai = sa[w][i];
+      c0 += ai * w0;
+      c1 += ai * w1;
+      c2 += ai * w2;
+      c3 += ai * w3;
+      w3 = w2;
+      w2 = w1;
+      w1 = w0;
+      w0 = sbp[w][padj(63 + k0 - i)];
+    }
+    sc[w][k0] = c0;
+    sc[w][k0 + 1] = c1;
+    sc[w][k0 + 2] = c2;
+    sc[w][k0 + 3] = c3;
+    __syncwarp();
+    const u64* h = sc[w] + 64;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int t = l + 32 * half;
+      u64 v = sc[w][t] - gr_hg(h, t);
+      if (t < 7) {
+        u64 h2[3];
+        for (int m = 0; m < 3; ++m) h2[m] = gr_hg(h, 64 + m);
+        u64 g = 0;
+        if (t < 3) g += h2[t];
+        if (t - 1 >= 0 && t - 1 < 3) g += h2[t - 1];
+        if (t - 3 >= 0 && t - 3 < 3) g += h2[t - 3];
+        if (t - 4 >= 0 && t - 4 < 3) g += h2[t - 4];
+        v += g;
+      }
+      out[e * 64 + t] = v;
+    }
+    __syncwarp();
+  }
+}
+
 // ---- fused small steps (single GR elements) -----------------------------------------------
 // Pi_Rec of one shared GR element s6 (6 x 64 words): P0 sends [r]_1 to P2 and [r]_2 to P1, P1
 // sends m to P0; P1 sends H([r]_1) to P2, P2 sends H(m) to P0 and H([r]_2) to P1.  Each receiver
@@ -689,6 +752,13 @@ void launch_gr_quad_combine(cudaStream_t st, const u64* lam, const u64* S00, con
 
 void launch_mode_consts(cudaStream_t st, int mode, u64* cst) {
   k_mode_consts<<<1, 64, 0, st>>>(mode, cst);
+}
+
+void launch_gr_mul_rows(cudaStream_t st, long long n, const u64* a, const u64* b, u64* out) {
+  if (n <= 0) return;
+  long long g = (n + 7) / 8;
+  if (g > 152 * 8) g = 152 * 8;
+  k_gr_mul_rows<<<(unsigned)g, 256, 0, st>>>(n, a, b, out);
 }
 
 }  // namespace mpc3

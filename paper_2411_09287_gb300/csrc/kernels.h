@@ -56,12 +56,19 @@ int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nte
                  const GemmTerm* terms, const Epi& epi, void* scratch, unsigned* err,
                  unsigned err_flag, cudaEvent_t ev0, cudaEvent_t ev1);
 
-// out[i][c] = add0[i][c] + sum_k (p0[i][k] + s1 p1[i][k]) M[k][c], i < R, k, c < 64 (M row-major
-// 64 x 64, p1 and add0 may be null; ld_add0 = 0 means ldc).  Exact, on the tensor cores.  Needs
-// 16-byte aligned bases and even row strides (returns -1 otherwise).
+// out[i][c] = add0[i][c] + sum_k A[i][k] M[k][c], i < R, k, c < 64 (M row-major 64 x 64) with
+// A[i][k] = p0[i][k] + s1 p1[i][k] (p1 may be null), or, with a_bits, A[i][k] = bit k of the word
+// p0[i].  add0 may be null; ld_add0 = 0 means ldc.  Exact, on the tensor cores.  Needs 16-byte
+// aligned bases and even row strides (returns -1 otherwise).
 int gr_matmul_tc(cudaStream_t st, long long R, const u64* p0, const u64* p1, u64 s1, long long lda,
-                 const u64* Mmat, const u64* add0, long long ld_add0, u64* out, long long ldc,
-                 unsigned* err, unsigned err_flag);
+                 int a_bits, const u64* Mmat, const u64* add0, long long ld_add0, u64* out,
+                 long long ldc, unsigned* err, unsigned err_flag);
+
+// P[0..2] (3 x 4096 words, accumulated mod 2^64) += the Gram sums G(x_e, y_e), G(x_o, y_o),
+// G(x_e, y_o) + G(x_o, y_e) over the Dh element pairs (x_{2i}, x_{2i+1}) of x and y (rows of 64
+// words, contiguous).  Exact, on the tensor cores; returns -1 for misaligned inputs.
+int gram3_tc(cudaStream_t st, long long Dh, const u64* x, const u64* y, u64* P, unsigned* err,
+             unsigned err_flag);
 
 // ---- elementwise protocol kernels (prf_kernels.cu) ------------------------------------------
 void launch_share_input(cudaStream_t st, const u64* x, long long n, Key k01, Key k02, u64 obj,
@@ -117,6 +124,8 @@ void launch_trunc_u(cudaStream_t st, const u64* r, int t, u64* u);
 void launch_trunc_round_h(cudaStream_t st, const u64* V, const u64* W, const u64* S, int k,
                           const u64* lam, u64* out);
 void launch_trunc_update_vw(cudaStream_t st, u64* V, u64* W, int k, const u64* coef);
+// out[e] = a[e] * b[e] (GR products of n row pairs; out may alias a or b)
+void launch_gr_mul_rows(cudaStream_t st, long long n, const u64* a, const u64* b, u64* out);
 void launch_trunc_materialize(cudaStream_t st, long long E, const u64* words, const u64* VW,
                               const u64* R, int kd, u64* out);
 void launch_gr_rec1(cudaStream_t st, const u64* s6, u64 xor_mask, int xor_idx, u64* out,

@@ -272,21 +272,29 @@ __device__ __forceinline__ u64 load_opnd(const Opnd& o, long long r, long long c
   return v;
 }
 
-__device__ __forceinline__ void balanced_digits(u64 v, int d[8]) {
+// 8 consecutive u64 values -> 8 digit planes of 8 bf16 each (one 16-byte unit per plane).
+// The balanced digits of v are the bytes of v + 0x8080808080808080 minus 128 (the digit set
+// [-128, 127] is a complete residue system, so this is the carry-propagating split); the bf16
+// of an integer d in [-128, 127] is the high half of the f32 (2^23 + 2^22 + d) - (2^23 + 2^22).
+__device__ __forceinline__ unsigned bf16_of_byte(unsigned byte) {   // bf16(byte - 128)
+  return __float_as_uint(__uint_as_float(0x4B400000u - 128u + byte) - 12582912.0f);
+}
+__device__ __forceinline__ void split8_store(const u64 v[8], unsigned char* plane0,
+                                             long long plane_stride, int off) {
+  u64 w[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) w[q] = v[q] + 0x8080808080808080ull;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    int b = (int)(v & 0xFFull);
-    v >>= 8;
-    if (b >= 128) {
-      b -= 256;
-      v += 1;
+    unsigned pk[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const unsigned lo = bf16_of_byte((unsigned)(w[2 * m] >> (8 * i)) & 0xFFu);
+      const unsigned hi = bf16_of_byte((unsigned)(w[2 * m + 1] >> (8 * i)) & 0xFFu);
+      pk[m] = __byte_perm(lo, hi, 0x7632);   // high halves: bf16(lo) | bf16(hi) << 16
     }
-    d[i] = b;
+    *reinterpret_cast<uint4*>(plane0 + i * plane_stride + off) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
-}
-
-__device__ __forceinline__ unsigned bf16_bits(int d) {   // exact for |d| <= 256
-  return __float_as_uint((float)d) >> 16;
 }
 
 // planes[i][row][k'] (bf16), row-major with pitch Kp; element (row, k') of the concatenated
@@ -302,31 +310,18 @@ __global__ void k_split_digits(GemmTerm t0, GemmTerm t1, int nterms, int which /
     // K x N operand) and consecutive k chunks for A
     long long row, kc;
     if (which) { row = w % R; kc = w / R; } else { row = w / chunks; kc = w % chunks; }
-    unsigned packed[8][4];
+    u64 v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const long long kk = kc * 8 + q;
-      u64 v = 0;
+      v[q] = 0;
       if (kk < (long long)nterms * K) {
         const GemmTerm& T = (kk < K) ? t0 : t1;
         const long long k = kk < K ? kk : kk - K;
-        v = which ? load_opnd(T.B, k, row, K, R) : load_opnd(T.A, row, k, R, K);
-      }
-      int d[8];
-      balanced_digits(v, d);
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const unsigned b = bf16_bits(d[i]);
-        if (q & 1) packed[i][q >> 1] |= b << 16;
-        else packed[i][q >> 1] = b;
+        v[q] = which ? load_opnd(T.B, k, row, K, R) : load_opnd(T.A, row, k, R, K);
       }
     }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      uint4 o;
-      o.x = packed[i][0]; o.y = packed[i][1]; o.z = packed[i][2]; o.w = packed[i][3];
-      *reinterpret_cast<uint4*>(planes + ((long long)i * R + row) * Kp + kc * 8) = o;
-    }
+    split8_store(v, reinterpret_cast<unsigned char*>(planes + row * Kp + kc * 8), R * Kp * 2, 0);
   }
 }
 
@@ -390,32 +385,15 @@ __device__ __forceinline__ int sw64_off(int r, int u) {
   return (r >> 3) * 512 + (r & 7) * 64 + ((u ^ ((r >> 1) & 3)) << 4);
 }
 
-// 8 consecutive u64 values -> 8 digit planes of 8 bf16 each (one 16-byte unit per plane)
-__device__ __forceinline__ void split8_store(const u64 v[8], unsigned char* plane0, int plane_stride,
-                                             int off) {
-  unsigned packed[8][4];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    int d[8];
-    balanced_digits(v[q], d);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const unsigned b = bf16_bits(d[i]);
-      if (q & 1) packed[i][q >> 1] |= b << 16;
-      else packed[i][q >> 1] = b;
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-    *reinterpret_cast<uint4*>(plane0 + i * plane_stride + off) =
-        make_uint4(packed[i][0], packed[i][1], packed[i][2], packed[i][3]);
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
 
 __global__ void __launch_bounds__(GM_THREADS, 1)
 k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ p1, u64 s1,
-               long long lda, const u64* __restrict__ Mmat, const u64* __restrict__ add0,
-               long long ld_add0, u64* __restrict__ out, long long ldc,
-               unsigned* __restrict__ err, unsigned err_flag) {
+               long long lda, int a_bits, const u64* __restrict__ Mmat,
+               const u64* __restrict__ add0, long long ld_add0, u64* __restrict__ out,
+               long long ldc, unsigned* __restrict__ err, unsigned err_flag) {
   extern __shared__ unsigned char dsm[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
@@ -478,7 +456,53 @@ k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ 
       const long long tile = blockIdx.x + (u >> 1) * gridDim.x;
       const int kc = (int)(u & 1);
       unsigned char* As = Asm + st * 8 * A_TILE;
+      if (kc == 0 && pt == 0) {   // bring the next tile's rows into L2 while this one runs
+        const long long nt = tile + gridDim.x;
+        if (nt < (R + TC_BM - 1) / TC_BM) {
+          const long long r0 = nt * TC_BM;
+          const long long nr = (R - r0 < TC_BM) ? R - r0 : TC_BM;
+          if (a_bits) {   // whole 16-byte units inside the word array only
+            const unsigned bytes = (unsigned)((nr * 8) & ~15ll);
+            if (bytes) prefetch_l2(p0 + r0, bytes);
+          } else {
+            // rows r0 .. r0 + nr - 1 of p0 and p1 (and add0): spans of lda words per row
+            const u64* lo = p0 + r0 * lda;
+            const u64* hi = p0 + (r0 + nr - 1) * lda + 64;
+            if (p1) {
+              const u64* l1 = p1 + r0 * lda;
+              const u64* h1 = p1 + (r0 + nr - 1) * lda + 64;
+              lo = l1 < lo ? l1 : lo;
+              hi = h1 > hi ? h1 : hi;
+            }
+            const long long bytes = (long long)(hi - lo) * 8;
+            for (long long o = 0; o < bytes; o += 65536)
+              prefetch_l2(reinterpret_cast<const char*>(lo) + o,
+                          (unsigned)((bytes - o < 65536 ? bytes - o : 65536) & ~15ll));
+          }
+        }
+      }
       constexpr int NIT = (512 + GM_PROD * 32 - 1) / (GM_PROD * 32);   // items per thread
+      if (a_bits) {
+        // one word per item row: load all of this thread's words first (one latency per chunk)
+        u64 wd[NIT];
+#pragma unroll
+        for (int q = 0; q < NIT; ++q) {
+          const int item = pt + q * GM_PROD * 32;
+          const long long row = tile * TC_BM + (item >> 2);
+          wd[q] = (item < 512 && row < R) ? p0[row] : 0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < NIT; ++q) {
+          const int item = pt + q * GM_PROD * 32;
+          if (item < 512) {
+            const u64 sh = wd[q] >> (kc * 32 + (item & 3) * 8);
+            u64 v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = (sh >> j) & 1ull;
+            split8_store(v, As, A_TILE, sw64_off(item >> 2, item & 3));
+          }
+        }
+      } else {
 #pragma unroll
       for (int q0 = 0; q0 < NIT; q0 += 2) {         // two items in flight per thread
         u64 v[2][8];
@@ -509,6 +533,7 @@ k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ 
           const int item = pt + (q0 + q) * GM_PROD * 32;
           if (item < 512) split8_store(v[q], As, A_TILE, sw64_off(item >> 2, item & 3));
         }
+      }
       }
       fence_proxy_async_smem();
       __syncwarp();
@@ -613,6 +638,201 @@ k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ 
   if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
+// ---- Gram sums of the dense Pi_Reduce rounds -------------------------------------------------
+// For vectors x, y of n = 2 Dh GR elements (rows of 64 words, element i at row i), the three P0
+// sums of a round in the truncation batch's form:
+//   P[0] += G(x_even, y_even), P[1] += G(x_odd, y_odd), P[2] += G(x_even, y_odd) + G(x_odd, y_even)
+// with G(u, v)[a][b] = sum_i u_i[a] v_i[b] (each P[g] a 64 x 64 matrix, mod 2^64).  The MMA tile
+// is M = 128 (rows a: x_even coefficients, then x_odd) x N = 64 (y of one parity, blockIdx.y) with
+// K = the element pairs i, split across blockIdx.x; each CTA adds its partial tile atomically.
+// Producers split x and y rows into digit planes transposed to K-major; MMA issue and drains as in
+// k_limb_gemm_tc; the drain warps accumulate over all of the CTA's chunks.
+constexpr size_t GR_SMEM = (size_t)NSTAGE * STAGE + 1024;   // 2 x (64 KB A + 32 KB B)
+
+__global__ void __launch_bounds__(GM_THREADS, 1)
+k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u64* __restrict__ P,
+          unsigned* __restrict__ err, unsigned err_flag) {
+  extern __shared__ unsigned char dsm[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) u64 full_bar[NSTAGE], empty_bar[NSTAGE];
+  __shared__ __align__(8) u64 accf_bar[2], acce_bar[2], done_bar;
+  __shared__ unsigned tmem_slot;
+  __shared__ int abort_flag;
+  volatile int* abort = &abort_flag;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int par = blockIdx.y;                      // parity of y in this CTA's tile
+  const long long nch = (Dh + TC_BK - 1) / TC_BK;  // chunks of 32 element pairs
+  const long long c0 = nch * blockIdx.x / gridDim.x;
+  const long long c1 = nch * (blockIdx.x + 1) / gridDim.x;
+  const long long nunits = c1 - c0;
+
+  if (tid == 0) {
+    for (int i = 0; i < NSTAGE; ++i) {
+      mbar_init(&full_bar[i], GM_PROD);
+      mbar_init(&empty_bar[i], 1);
+    }
+    for (int g = 0; g < 2; ++g) {
+      mbar_init(&accf_bar[g], 1);
+      mbar_init(&acce_bar[g], NDRAIN);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = tmem_slot;
+
+  auto fail = [&]() {
+    *abort = 1;
+    atomicOr(err, err_flag);
+  };
+
+  if (warp >= NDRAIN && warp < NDRAIN + GM_PROD) {
+    // ---- producers: 512 A items (x rows a = item % 128, 8 pairs k8 = item / 128) and 256 B
+    // items (y rows b = item % 64, k8 = item / 64), lanes on consecutive coefficients ----
+    const int pt = tid - NDRAIN * 32;
+    constexpr int NITEM = 768;
+    constexpr int NIT = (NITEM + GM_PROD * 32 - 1) / (GM_PROD * 32);
+    bool ok = true;
+    for (long long u = 0; u < nunits && ok; ++u) {
+      const int st = (int)(u % NSTAGE);
+      if (u >= NSTAGE) {
+        ok = __all_sync(0xffffffffu,
+                        mbar_wait(&empty_bar[st], (unsigned)(((u / NSTAGE) + 1) & 1), abort));
+        if (!ok) break;
+      }
+      const long long i0 = (c0 + u) * TC_BK;       // first element pair of the chunk
+      if (pt == 0 && u + 1 < nunits) {             // next chunk's 32 pairs (64 rows) of x and y
+        const long long i1 = i0 + TC_BK;
+        const long long np = (Dh - i1 < TC_BK) ? Dh - i1 : TC_BK;
+        if (np > 0) {
+          prefetch_l2(x + i1 * 128, (unsigned)(np * 1024));
+          prefetch_l2(y + i1 * 128, (unsigned)(np * 1024));
+        }
+      }
+      unsigned char* As = base + st * STAGE;
+      unsigned char* Bs = As + 8 * A_TILE;
+#pragma unroll
+      for (int q0 = 0; q0 < NIT; q0 += 2) {
+        u64 v[2][8];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int item = pt + (q0 + q) * GM_PROD * 32;
+          const bool isA = item < 512;
+          const int it = isA ? item : item - 512;
+          const int row = isA ? (it & 127) : (it & 63);
+          const int k8 = isA ? (it >> 7) : (it >> 6);
+          // A row a: coefficient a % 64 of x_{2i + a / 64}; B row b: coefficient b of y_{2i + par}
+          const u64* src = isA ? x + (row >> 6) * 64 + (row & 63) : y + par * 64 + row;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const long long i = i0 + k8 * 8 + j;
+            v[q][j] = (item < NITEM && i < Dh) ? src[i * 128] : 0ull;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int item = pt + (q0 + q) * GM_PROD * 32;
+          if (item < 512) split8_store(v[q], As, A_TILE, sw64_off(item & 127, item >> 7));
+          else if (item < NITEM) split8_store(v[q], Bs, B_TILE, sw64_off((item - 512) & 63, (item - 512) >> 6));
+        }
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full_bar[st]);
+    }
+    if (!ok && lane == 0) fail();
+  } else if (warp == NDRAIN + GM_PROD) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      const u64 d0 = smem_desc(base, 64);
+      for (long long u = 0; u < nunits; ++u) {
+        const int st = (int)(u % NSTAGE);
+        if (!mbar_wait(&full_bar[st], (unsigned)((u / NSTAGE) & 1), abort)) { fail(); break; }
+        tc_fence_after();
+        const u64 ad = d0 + (u64)((st * STAGE) >> 4);
+        const u64 bd = ad + (u64)((8 * A_TILE) >> 4);
+        if (u > 0 && !mbar_wait(&acce_bar[0], (unsigned)((u - 1) & 1), abort)) { fail(); break; }
+        tc_fence_after();
+        issue_group<0>(tmem, ad, bd);
+        mma_commit(&accf_bar[0]);
+        if (u > 0 && !mbar_wait(&acce_bar[1], (unsigned)((u - 1) & 1), abort)) { fail(); break; }
+        tc_fence_after();
+        issue_group<1>(tmem, ad, bd);
+        mma_commit(&accf_bar[1]);
+        mma_commit(&empty_bar[st]);
+      }
+      mma_commit(&done_bar);
+      mbar_wait_plain(&done_bar, 0u);
+    }
+  } else if (warp < NDRAIN) {
+    // ---- drain warps: tile rows 32 (w % 4) + lane, columns 32 (w / 4) .. +31 ----
+    const int q4 = warp & 3, h = warp >> 2;
+    const unsigned tl = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)(h * 32);
+    u64 acc[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = 0;
+    bool ok = true;
+    for (long long u = 0; u < nunits && ok; ++u) {
+      const unsigned pu = (unsigned)(u & 1);
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        ok = __all_sync(0xffffffffu, mbar_wait(&accf_bar[g], pu, abort));
+        if (!ok) break;
+        tc_fence_after();
+        const int s0 = g == 0 ? 0 : 2;
+        const int s1d = g == 0 ? 6 : 4;
+#pragma unroll
+        for (int c16 = 0; c16 < 2; ++c16) {
+          unsigned x0[16], x1[16];
+          tmem_ld16(tl + (unsigned)(acc_col(s0) + c16 * 16), x0);
+          tmem_ld16(tl + (unsigned)(acc_col(s0 + 1) + c16 * 16), x1);
+          tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const unsigned ws =
+                (unsigned)f2i_biased(x0[j]) + (unsigned)f2i_biased(x1[j]) * 256u - PAIR_BIAS;
+            acc[c16 * 16 + j] += g == 0 ? (u64)(long long)(int)ws : (u64)(long long)(int)ws << 16;
+          }
+          tmem_ld16(tl + (unsigned)(acc_col(s1d) + c16 * 16), x0);
+          tmem_ld16(tl + (unsigned)(acc_col(s1d + 1) + c16 * 16), x1);
+          tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const unsigned whi = (unsigned)f2i_biased(x0[j]) + (unsigned)f2i_biased(x1[j]) * 256u;
+            acc[c16 * 16 + j] += (u64)(g == 0 ? (whi << 16) : whi) << 32;
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce_bar[g]);
+      }
+    }
+    if (ok && !*abort && nunits > 0) {
+      const u64 corr = (u64)((unsigned)nunits * CHUNK_HI_BIAS) << 32;
+      const int a = q4 * 32 + lane;                // tile row: x parity a / 64, coefficient a % 64
+      const int xpar = a >> 6;
+      // (x parity, y parity) -> P block: (0,0) -> 0, (1,1) -> 1, mixed -> 2
+      u64* dst = P + (xpar == par ? xpar : 2) * 4096 + (a & 63) * 64 + h * 32;
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        atomicAdd(reinterpret_cast<unsigned long long*>(dst + c), (unsigned long long)(acc[c] - corr));
+    } else if (!ok && lane == 0) {
+      fail();
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
 }  // namespace
 
 size_t limb_tc_scratch_bytes(long long M, long long N, long long K, int nterms) {
@@ -653,9 +873,10 @@ int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nte
 }
 
 int gr_matmul_tc(cudaStream_t st, long long R, const u64* p0, const u64* p1, u64 s1, long long lda,
-                 const u64* Mmat, const u64* add0, long long ld_add0, u64* out, long long ldc,
-                 unsigned* err, unsigned err_flag) {
+                 int a_bits, const u64* Mmat, const u64* add0, long long ld_add0, u64* out,
+                 long long ldc, unsigned* err, unsigned err_flag) {
   if (R <= 0) return 0;
+  if (a_bits) lda = 0;
   // 16-byte vector accesses: row strides and bases must keep 2-word alignment
   if ((lda & 1) || (ldc & 1) || (add0 && (ld_add0 & 1)) ||
       ((reinterpret_cast<uintptr_t>(p0) | reinterpret_cast<uintptr_t>(p1) |
@@ -671,8 +892,28 @@ int gr_matmul_tc(cudaStream_t st, long long R, const u64* p0, const u64* p1, u64
   const long long ntiles = (R + TC_BM - 1) / TC_BM;
   const unsigned grid = (unsigned)(ntiles < nsm ? ntiles : nsm);
   cudaFuncSetAttribute(k_gr_matmul_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GM_SMEM);
-  k_gr_matmul_tc<<<grid, GM_THREADS, GM_SMEM, st>>>(R, p0, p1, s1, lda, Mmat, add0,
+  k_gr_matmul_tc<<<grid, GM_THREADS, GM_SMEM, st>>>(R, p0, p1, s1, lda, a_bits, Mmat, add0,
                                                      ld_add0 ? ld_add0 : ldc, out, ldc, err, err_flag);
+  return 0;
+}
+
+int gram3_tc(cudaStream_t st, long long Dh, const u64* x, const u64* y, u64* P, unsigned* err,
+             unsigned err_flag) {
+  if (Dh <= 0) return 0;
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) return -1;
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 148;
+  }
+  const long long nch = (Dh + TC_BK - 1) / TC_BK;
+  long long split = nsm / 2;
+  if (split > nch) split = nch;
+  if (split < 1) split = 1;
+  cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GR_SMEM);
+  k_gram_tc<<<dim3((unsigned)split, 2), GM_THREADS, GR_SMEM, st>>>(Dh, x, y, P, err, err_flag);
   return 0;
 }
 
