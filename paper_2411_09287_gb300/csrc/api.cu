@@ -59,6 +59,7 @@ inline void counted(int k, F f, A... a) {
 #define launch_trunc_update_vw(...) counted(1, mpc3::launch_trunc_update_vw, __VA_ARGS__)
 #define launch_trunc_materialize(...) counted(1, mpc3::launch_trunc_materialize, __VA_ARGS__)
 #define launch_gr_mul_rows(...) counted(1, mpc3::launch_gr_mul_rows, __VA_ARGS__)
+#define launch_scalar_gr_sum(...) counted(1, mpc3::launch_scalar_gr_sum, __VA_ARGS__)
 #define launch_gr_rec1(...) counted(1, mpc3::launch_gr_rec1, __VA_ARGS__)
 #define launch_gr_inner_finish_all(...) counted(1, mpc3::launch_gr_inner_finish_all, __VA_ARGS__)
 #define launch_gr_quad_combine(...) counted(1, mpc3::launch_gr_quad_combine, __VA_ARGS__)
@@ -307,6 +308,21 @@ int gr_matmul(mpc_ctx* ctx, long long R, const u64* p0, const u64* p1, u64 s1, l
   e.add0 = add0;
   e.ld_add0 = add0 ? ld_add0 : 0;
   gemm_u64(ctx->st, R, 64, 64, 1, &T, e, 1);
+  return MPC_OK;
+}
+
+// C = A B (+ epilogue) for a one-term product that the limb path runs on the tensor cores
+// (scratch: limb_tc_scratch_bytes(M, N, K, 1) bytes) and the u64 path on the CUDA cores.
+int dense_gemm(mpc_ctx* ctx, long long M, long long N, long long K, const GemmTerm& T,
+               const Epi& e, void* scratch) {
+  if (scratch && !e.atomic) {
+    g_launches += 4;
+    if (limb_gemm_tc(ctx->st, M, N, K, 1, &T, e, scratch, ctx->status, ST_TIMEOUT, nullptr,
+                     nullptr))
+      return fail(ctx, MPC_ERR_CUDA, "tensor-core GEMM setup failed");
+    return MPC_OK;
+  }
+  gemm_u64(ctx->st, M, N, K, 1, &T, e, 1);
   return MPC_OK;
 }
 
@@ -756,12 +772,19 @@ struct VMatPlan {
   unsigned char* TL8;
   Dense dt;
   IVBuf ivt;
+  void* tcs = nullptr;   // tensor-core digit planes (limb path only)
 };
 
-VMatPlan plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R0, int R1) {
+VMatPlan plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R0, int R1,
+                   bool tc) {
   VMatPlan p;
   p.R0 = R0 < 0 ? default_R(K) : R0;
   p.s = plan_small(a);
+  // digit planes of the batch-0 products (X^T P, W Q, Z Q) on the tensor-core path
+  p.tcs = tc ? (void*)a.take<unsigned char>((long long)std::max(
+                   {limb_tc_scratch_bytes(K, 64, M, 1), limb_tc_scratch_bytes(K, 64, N, 1),
+                    limb_tc_scratch_bytes(6 * M, 64, N, 1)}))
+             : nullptr;
   p.Q = a.take<u64>(N * 64);
   p.P = a.take<u64>(M * 64);
   p.T = a.take<u64>(6 * M * 64);
@@ -922,7 +945,7 @@ int64_t mpc_workspace_size(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int
       break;
     case MPC_OP_VERIFY_MATMUL:
       if (a <= 0 || b <= 0 || c <= 0) return -1;
-      plan_vmat(ar, a, b, c, trunc_bits, R_main, R_trunc);
+      plan_vmat(ar, a, b, c, trunc_bits, R_main, R_trunc, ctx && ctx->gemm_path == MPC_GEMM_LIMB_TC);
       break;
     case MPC_OP_RECONSTRUCT:
       if (a < 0) return -1;
@@ -1142,7 +1165,8 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
       trunc_bits > 63)
     return fail(ctx, MPC_ERR_ARG, "verify_matmul: bad argument");
   Arena ar{(char*)workspace, workspace_bytes, 0, false};
-  VMatPlan p = plan_vmat(ar, M, N, K, trunc_bits, R_main, R_trunc);
+  VMatPlan p = plan_vmat(ar, M, N, K, trunc_bits, R_main, R_trunc,
+                         ctx->gemm_path == MPC_GEMM_LIMB_TC);
   if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "verify_matmul: workspace too small");
   cudaStream_t st = ctx->st;
   const Small& s = p.s;
@@ -1159,17 +1183,17 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
     GemmTerm T;
     T.A = op(xs + c * MK, K, 1);        // Xt_k = sum_a rho^a X_ak  (K x M) . (M x 64)
     T.B = op(p.P, 64);
-    gemm_u64(st, K, 64, M, 1, &T, epi_store(x.c[c], 64), 1);
+    if ((rc = dense_gemm(ctx, K, 64, M, T, epi_store(x.c[c], 64), p.tcs))) return rc;
     GemmTerm U;
     U.A = op(ws_ + c * KN, N);          // Wt_k = sum_b r^b W_kb   (K x N) . (N x 64)
     U.B = op(p.Q, 64);
-    gemm_u64(st, K, 64, N, 1, &U, epi_store(y.c[c], 64), 1);
+    if ((rc = dense_gemm(ctx, K, 64, N, U, epi_store(y.c[c], 64), p.tcs))) return rc;
   }
   {  // zt = sum_a rho^a (sum_b r^b Z_ab): T = Z Q for all 6 components, then Gram with P
     GemmTerm T;
     T.A = op(zpre, N);
     T.B = op(p.Q, 64);
-    gemm_u64(st, 6 * M, 64, N, 1, &T, epi_store(p.T, 64), 1);
+    if ((rc = dense_gemm(ctx, 6 * M, 64, N, T, epi_store(p.T, 64), p.tcs))) return rc;
     CK(cudaMemsetAsync(p.Pz, 0, 6 * 4096 * 8, st));
     for (int c = 0; c < 6; ++c)
       gram(ctx, p.Pz + c * 4096, p.P, nullptr, 1, 64, p.T + c * M * 64, nullptr, 1, 64, M, 1);
@@ -1209,12 +1233,8 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
       }
     }
     CK(cudaMemsetAsync(p.Zpq, 0, 12 * 64 * 8, st));
-    {  // sum_e r^(2e) p_c[e], sum_e r^(2e) q_c[e]: (12 x E) . (E x 64)
-      GemmTerm T;
-      T.A = op(pq, E);
-      T.B = op(p.Rtab, 64);
-      gemm_u64(st, 12, 64, E, 1, &T, epi_atomic(p.Zpq, 64), nsplit_for(E));
-    }
+    // sum_e r^(2e) p_c[e], sum_e r^(2e) q_c[e]: (12 x E) . (E x 64)
+    launch_scalar_gr_sum(st, E, pq, E, 12, p.Rtab, p.Zpq);
     u64* z0 = p.zt + 384;
     for (int c = 0; c < 6; ++c)   // z_c = sum r^(2e) p_c + r sum r^(2e) q_c
       launch_gr_lincomb(st, ctx->cst + CST_ONE, p.Zpq + c * 64, s.r, p.Zpq + (6 + c) * 64,

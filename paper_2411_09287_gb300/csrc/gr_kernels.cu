@@ -524,6 +524,43 @@ k_gr_mul_rows(long long n, const u64* __restrict__ a, const u64* __restrict__ b,
   }
 }
 
+// out[c] += sum_{e < n} A[c][e] * R[e] for c < nrows <= 16: GR elements R[e] (rows of 64 words)
+// scaled by ring scalars and summed (e.g. sum_e r^(2e) p_c[e] for the truncation batch).  Each
+// block takes a contiguous slice of e; thread (t, cg) owns coefficient t of rows c = cg, cg + 4, ..;
+// the block's slice of A is staged in shared memory 64 e at a time; partial sums are added
+// atomically at the end.
+__global__ void __launch_bounds__(256)
+k_scalar_gr_sum(long long n, const u64* __restrict__ A, long long lda, int nrows,
+                const u64* __restrict__ R, u64* __restrict__ out) {
+  __shared__ u64 as[16][64];
+  const int t = threadIdx.x & 63, cg = threadIdx.x >> 6;
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long e0 = per * blockIdx.x;
+  const long long e1 = (e0 + per < n) ? e0 + per : n;
+  u64 acc[4] = {0, 0, 0, 0};
+  for (long long eb = e0; eb < e1; eb += 64) {
+    const int cnt = (int)((e1 - eb < 64) ? e1 - eb : 64);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nrows * 64; i += blockDim.x) {
+      const int c = i >> 6, k = i & 63;
+      as[c][k] = (k < cnt) ? A[c * lda + eb + k] : 0ull;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < cnt; ++k) {
+      const u64 r = R[(eb + k) * 64 + t];
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        if (cg + 4 * m < nrows) acc[m] += as[cg + 4 * m][k] * r;
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+    if (cg + 4 * m < nrows)
+      atomicAdd(reinterpret_cast<unsigned long long*>(out + (cg + 4 * m) * 64 + t),
+                (unsigned long long)acc[m]);
+}
+
 // ---- fused small steps (single GR elements) -----------------------------------------------
 // Pi_Rec of one shared GR element s6 (6 x 64 words): P0 sends [r]_1 to P2 and [r]_2 to P1, P1
 // sends m to P0; P1 sends H([r]_1) to P2, P2 sends H(m) to P0 and H([r]_2) to P1.  Each receiver
@@ -759,6 +796,14 @@ void launch_gr_mul_rows(cudaStream_t st, long long n, const u64* a, const u64* b
   long long g = (n + 7) / 8;
   if (g > 152 * 8) g = 152 * 8;
   k_gr_mul_rows<<<(unsigned)g, 256, 0, st>>>(n, a, b, out);
+}
+
+void launch_scalar_gr_sum(cudaStream_t st, long long n, const u64* A, long long lda, int nrows,
+                          const u64* R, u64* out) {
+  if (n <= 0 || nrows <= 0) return;
+  long long g = (n + 4095) / 4096;
+  if (g > 152 * 8) g = 152 * 8;
+  k_scalar_gr_sum<<<(unsigned)g, 256, 0, st>>>(n, A, lda, nrows, R, out);
 }
 
 }  // namespace mpc3

@@ -124,6 +124,9 @@ void launch_trunc_u(cudaStream_t st, const u64* r, int t, u64* u);
 void launch_trunc_round_h(cudaStream_t st, const u64* V, const u64* W, const u64* S, int k,
                           const u64* lam, u64* out);
 void launch_trunc_update_vw(cudaStream_t st, u64* V, u64* W, int k, const u64* coef);
+// out[c] += sum_{e < n} A[c * lda + e] * R[e] (R: n GR elements), c < nrows <= 16, atomically
+void launch_scalar_gr_sum(cudaStream_t st, long long n, const u64* A, long long lda, int nrows,
+                          const u64* R, u64* out);
 // out[e] = a[e] * b[e] (GR products of n row pairs; out may alias a or b)
 void launch_gr_mul_rows(cudaStream_t st, long long n, const u64* a, const u64* b, u64* out);
 void launch_trunc_materialize(cudaStream_t st, long long E, const u64* words, const u64* VW,
