@@ -157,48 +157,58 @@ def run_reference(args, rank: int, world: int):
 # ---------------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------------
-# DRAM bytes per launch from one ncu capture of each kernel on the n = 1024 layer (E = 2^20),
-# scaled by the units a launch processes (both kernels stream their inputs once per unit of work,
-# so traffic grows in proportion).  Summaries with the commands that produced them: profiles/.
-NCU_TRAFFIC = {
-    # kernel: (DRAM bytes per launch at the captured size, units at that size, summary)
-    "k_trunc_s": (None, 2 ** 20, "profiles/trunc_s_mma_e4m3_n1024.md"),
-    "k_limb_gemm": (None, 1024 ** 3, "profiles/limb_gemm_tc_n1024.md"),
+# DRAM bytes (read + write) per step of each kernel, summed over its launches, from one ncu
+# capture of the n = 1024 layer (E = 2^20 outputs); every one of these kernels streams data in
+# proportion to E (operand digit planes, folded vectors, bit words, tables), so the bench scales
+# the figure by E / 2^20.  The summaries, with the commands that produced them: profiles/.
+NCU_TRAFFIC_E = 2 ** 20
+NCU_TRAFFIC = {   # bytes per step at E = 2^20 (profiles/traffic_verify_kernels_n1024.md)
+    "k_trunc_s": 0.419e9,
+    "k_limb_gemm": 0.485e9,
+    "k_gr_matmul": 8.257e9,
+    "k_gram": 2.308e9,
+    "k_gr_mul_rows": 3.138e9,
 }
+ALU_NOTE = "peak derived: 152 SMs x 64 IMAD/clk x max SM clock; a u64 MAC is 3 IMAD"
 
 
-def rooflines(per, peaks, clk, M, N, K, E, gemm_path):
-    """Roofline records of the dominant kernels, from their CUDA-event times inside the step.
-    Tensor peaks are the measured cuBLAS bf16 rate (sustained: these kernels run inside a long
-    step); e4m3 work takes twice that (the nominal fp8 : bf16 ratio)."""
+def rooflines(phases, steps, peaks, clk, M, N, K, E, gemm_path):
+    """Roofline records of the dominant kernels: CUDA-event time of each kernel inside the step
+    and the algorithmic u64 multiply-accumulates the library attributes to it.  Tensor kernels
+    count the digit products they must form (36 bf16 digit pairs per u64 MAC for the 8-bit
+    balanced digits, 16 e4m3 limbs per bit-times-u64 MAC for the S matrix), 2 FLOP each, against
+    the measured cuBLAS bf16 rate (sustained: they run inside a long step) or twice it for e4m3
+    (the nominal fp8 : bf16 ratio).  CUDA-core kernels count 3 IMAD per u64 MAC."""
     bf16 = peaks.get("bf16_tflops_sustained")
     src = "of measured" if bf16 else "of fallback"
     bf16 = bf16 or 1700.0
     sm_max = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    alu = 152 * 64 * sm_max * 1e6 / 1e12   # T IMAD/s
     out = {}
 
-    def rec(name, ms, work, peak, unit, bound, units, note):
-        if not ms:
+    def rec(name, ops_per_mac, peak, unit, bound, note, work=None):
+        ms, _, w = phases.get(name, (0.0, 0, 0.0))
+        ms /= steps
+        w = (w / steps) if work is None else work
+        if not ms or not w:
             return
+        ach = ops_per_mac * w / (ms * 1e-3) / 1e12
         tr = NCU_TRAFFIC.get(name)
-        traffic = tr[0] * units / tr[1] if tr and tr[0] is not None else None
-        ach = work / (ms * 1e-3) / 1e12
         out[name] = {"bound": bound, "kernel": name, "achieved": ach, "peak": peak, "unit": unit,
-                     "frac": ach / peak, "traffic": traffic, "ms_per_step": ms,
-                     "work_per_step": work, "peak_source": src, "note": note}
+                     "frac": ach / peak, "traffic": tr * E / NCU_TRAFFIC_E if tr else None,
+                     "ms_per_step": ms, "u64_macs_per_step": w, "peak_source": src, "note": note}
 
-    # S matrix of the trunc batch: 4096 bit pairs x 64 coefficients x E outputs, 16 four-bit
-    # limbs, one e4m3 MAC (2 FLOP) per limb
-    rec("k_trunc_s", per.get("k_trunc_s"), 2.0 * 16 * 4096 * 64 * E, 2 * bf16, "TFLOP/s",
-        "tensor", E, "tcgen05 kind::f8f6f4 e4m3, 16 limbs; peak = 2 x measured bf16 (sustained)")
+    rec("k_trunc_s", 2 * 16, 2 * bf16, "TFLOP/s", "tensor",
+        "tcgen05 kind::f8f6f4, 16 e4m3 limbs per MAC; peak = 2 x measured bf16 (sustained)")
     if gemm_path == "tc":
-        # three party products, 5 M N K u64 MACs, 36 digit-pair products each, 2 FLOP per MAC
-        rec("k_limb_gemm", per.get("k_limb_gemm"), 36.0 * 2 * 5 * M * N * K, bf16, "TFLOP/s",
-            "tensor", M * N * K, "tcgen05 kind::f16, bf16 digits; peak = measured bf16 (sustained)")
+        for k, what in (("k_limb_gemm", "limb-split products"), ("k_gr_matmul", "GR-matrix products"),
+                        ("k_gram", "Gram sums")):
+            rec(k, 2 * 36, bf16, "TFLOP/s", "tensor",
+                f"tcgen05 kind::f16 {what}, 36 bf16 digit pairs per MAC; peak = measured bf16 (sustained)")
+        rec("k_gr_mul_rows", 3, alu, "Tops/s (int32 IMAD)", "alu", ALU_NOTE)
     else:
-        alu = 152 * 64 * sm_max * 1e6 / 1e12   # int32 IMAD/s in T; a u64 MAC is 3 IMAD
-        rec("gemm", per.get("gemm"), 3.0 * 5 * M * N * K, alu, "Tops/s (int32 IMAD)", "alu",
-            M * N * K, "u64 CUDA-core GEMM; peak derived: 152 SMs x 64 IMAD/clk x max SM clock")
+        rec("gemm", 3, alu, "Tops/s (int32 IMAD)", "alu", "u64 CUDA-core GEMM; " + ALU_NOTE,
+            work=5.0 * M * N * K)
     return out
 
 
@@ -271,10 +281,11 @@ def main():
         for _ in range(16):
             a, b = int(g.integers(0, M)), int(g.integers(0, N))
             ref = sum(int(X[a, k]) * int(W[k, b]) for k in range(K)) % (1 << 64)
-            assert int(zp[a * N + b]) == ref, "secure product differs from X W"
+            assert int(zp[a * N + b]) == ref, f"secure product differs from X W at ({a}, {b})"
         return o
 
-    sampled_check()
+    if args.warmup > 0:   # (with no warm-up step there is no product to check yet)
+        sampled_check()
 
     # ---- timed region: inputs resident in HBM ----
     clocks = ClockSampler(torch.cuda.current_device())
@@ -338,7 +349,7 @@ def main():
         except Exception:
             peaks = {}
     per = {k: v[0] / args.steps for k, v in phases.items()}
-    roofs = rooflines(per, peaks, clk, M, N, K, E, args.gemm_path)
+    roofs = rooflines(phases, args.steps, peaks, clk, M, N, K, E, args.gemm_path)
     roof = max(roofs.values(), key=lambda r: r["ms_per_step"]) if roofs else None
 
     line = {
