@@ -32,7 +32,23 @@ METRIC = ("secure Z_2^64 ring-MAC/s incl. verification (limb-INT8 TC vs u64 path
 UNIT = "ring-MAC/s"
 
 
-def parse():
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The job's time: the maximum of a per-rank time over all ranks (replicas)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n: int, world: int, seconds_per_step: float) -> float:
+    """Whole-job secure ring-MAC/s: every rank runs one n x n x n layer per step."""
+    return world * float(n) ** 3 / seconds_per_step
+
+
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -43,7 +59,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -326,20 +342,13 @@ def main():
         for _ in range(e_steps):
             step(*host_args)
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / e_steps
-        if world > 1:
-            dtt = torch.tensor([dt], device="cuda")
-            dist.all_reduce(dtt, op=dist.ReduceOp.MAX)
-            dt = float(dtt.item())
+        dt = max_over_ranks((time.perf_counter() - t0) / e_steps, world)
         sampled_check()
-        e2e = {"value": world * n ** 3 / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+        e2e = {"value": job_value(n, world, dt), "unit": UNIT, "ms_per_step": dt * 1e3,
                "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": n * n * 8}
 
-    if world > 1:
-        mt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(mt, op=dist.ReduceOp.MAX)
-        ms = float(mt.item())
-    value = world * n ** 3 / (ms * 1e-3)
+    ms = max_over_ranks(ms, world)
+    value = job_value(n, world, ms * 1e-3)
 
     # ---- roofline of the dominant phase ----
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) if os.path.exists(
