@@ -167,12 +167,19 @@ class GR:
         return r
 
     def powers(self, a, n: int) -> np.ndarray:
-        """[a^0, a^1, ..., a^(n-1)] by repeated multiplication (shape (n, d))."""
+        """[a^0, a^1, ..., a^(n-1)] (shape (n, d)), by doubling blocks: once a^0 .. a^(k-1) are
+        known, a^(k+i) = a^i a^k for i < k."""
         out = self.zeros((n,))
-        cur = self.const(1)
-        for i in range(n):
-            out[i] = cur
-            cur = self.mul(cur, a)
+        if n == 0:
+            return out
+        out[0] = self.const(1)
+        k = 1
+        ak = np.asarray(a, dtype=np.uint64) & self.mask        # a^k
+        while k < n:
+            m = min(k, n - k)
+            out[k:k + m] = self.mul(out[:m], ak)
+            ak = self.mul(ak, ak)
+            k += m
         return out
 
     def is_unit(self, a) -> bool:

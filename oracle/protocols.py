@@ -82,14 +82,15 @@ def reconstruct(sess: Session, x: Shared, phase: str = ONLINE, proto: str = "rec
     r1_at_p2 = sess.send(0, 2, phase, proto, x.p0_r1)
     r2_at_p1 = sess.send(0, 1, phase, proto, x.p0_r2, site="REC_MSG")
     m_at_p0 = sess.send(1, 0, phase, proto, x.p1_m)
-    h_r1_at_p2 = sess.send_hash(1, 2, phase, proto, hash_u64(x.p1_r1))
-    h_m_at_p0 = sess.send_hash(2, 0, phase, proto, hash_u64(x.p2_m))
-    h_r2_at_p1 = sess.send_hash(2, 1, phase, proto, hash_u64(x.p2_r2))
-    if hash_u64(m_at_p0) != h_m_at_p0:
+    w = sess.wire
+    h_r1_at_p2 = sess.send_hash(1, 2, phase, proto, hash_u64(w(x.p1_r1)))
+    h_m_at_p0 = sess.send_hash(2, 0, phase, proto, hash_u64(w(x.p2_m)))
+    h_r2_at_p1 = sess.send_hash(2, 1, phase, proto, hash_u64(w(x.p2_r2)))
+    if hash_u64(w(m_at_p0)) != h_m_at_p0:
         raise Abort("P0: m from P1 disagrees with H(m) from P2")
-    if hash_u64(r2_at_p1) != h_r2_at_p1:
+    if hash_u64(w(r2_at_p1)) != h_r2_at_p1:
         raise Abort("P1: [r]_2 from P0 disagrees with H([r]_2) from P2")
-    if hash_u64(r1_at_p2) != h_r1_at_p2:
+    if hash_u64(w(r1_at_p2)) != h_r1_at_p2:
         raise Abort("P2: [r]_1 from P0 disagrees with H([r]_1) from P1")
     mask = sess.mask
     out0 = (m_at_p0 - x.p0_r1 - x.p0_r2) & mask
@@ -119,21 +120,24 @@ def _exchange_mz(sess: Session, mz1, mz2, proto: str, phase: str):
     return (mz1 + mz2_at_p1) & mask, (mz1_at_p2 + mz2) & mask
 
 
-def mult(sess: Session, x: Shared, y: Shared, call_id: int) -> Shared:
+def mult(sess: Session, x: Shared, y: Shared, call_id: int, purpose: int = P_MULT,
+         batch: int = 0, sub: int = 0) -> Shared:
     """Fig. MultP.  Offline: [r_z] <- Pi_[.]; P0 computes Gamma = r_x r_y + r_z and shares it with
     Pi_[.](Gamma).  Online: P_j computes [m_z]_j = (j-1) m_x m_y - m_x [r_y]_j - m_y [r_x]_j +
-    [Gamma]_j, and P1, P2 exchange their shares to reconstruct m_z."""
+    [Gamma]_j, and P1, P2 exchange their shares to reconstruct m_z.  Element i's mask and [Gamma]_1
+    are words i of the (purpose, obj_id(call_id, batch, sub)) streams; over Z_2 (a Boolean
+    session) the same formulas are the AND gate, with + and - both XOR."""
     mask = sess.mask
-    obj = obj_id(call_id)
+    obj = obj_id(call_id, batch, sub)
     n = x.p1_m.size
     shape = x.p1_m.shape
-    rz1 = sess.prf(C_R1, P_MULT, obj, n).reshape(shape)
-    rz2 = sess.prf(C_R2, P_MULT, obj, n).reshape(shape)
+    rz1 = sess.prf(C_R1, purpose, obj, n).reshape(shape)
+    rz2 = sess.prf(C_R2, purpose, obj, n).reshape(shape)
     # offline, P0
     rx = (x.p0_r1 + x.p0_r2) & mask
     ry = (y.p0_r1 + y.p0_r2) & mask
     gamma = (rx * ry + rz1 + rz2) & mask
-    g1 = sess.prf(C_G1, P_MULT, obj, n).reshape(shape)
+    g1 = sess.prf(C_G1, purpose, obj, n).reshape(shape)
     g2_at_p2 = _gamma_message(sess, gamma, g1, "mult", OFFLINE)
     # online, P1 (j = 1) and P2 (j = 2)
     mz1 = (U64(0) - x.p1_m * y.p1_r1 - y.p1_m * x.p1_r1 + g1) & mask

@@ -26,6 +26,10 @@ _COMP_PAIR = {C_R1: PAIR_01, C_R2: PAIR_02, C_M12: PAIR_12, C_G1: PAIR_01,
 
 # Stream purposes (tag = purpose << 4 | component).
 P_SHARE, P_MULT, P_INNER, P_TRUNC_BITS, P_TRUNC_P, P_TRUNC_Q = 0x01, 0x02, 0x03, 0x04, 0x05, 0x06
+# non-linear layers (Sec. 4.3): daBits, edaBits, AND gates, their arithmetic products, the final
+# product of ReLU / compare-select
+P_DABIT, P_EDABIT, P_AND, P_EDA_MULT, P_EDA_INNER, P_DA_MULT1, P_DA_MULT2, P_NL_MULT = (
+    0x07, 0x08, 0x09, 0x0A, 0x0B, 0x0C, 0x0D, 0x0E)
 P_VER_R, P_VER_ZETA, P_VER_H0, P_VER_H2, P_VER_ALPHA, P_VER_XA, P_VER_DELTA = (
     0x10, 0x11, 0x12, 0x13, 0x14, 0x15, 0x16)
 
@@ -122,6 +126,10 @@ class Session:
         if n is None:
             return self.prf(comp, purpose, obj, d)
         return self.prf(comp, purpose, obj, n * d).reshape(n, d)
+
+    def wire(self, arr) -> np.ndarray:
+        """The words a party puts on the wire for `arr` (what Pi_Rec hashes)."""
+        return np.asarray(arr, dtype=np.uint64)
 
     # ---- messages ----------------------------------------------------------------------------
     def arm_fault(self, site: str, index: int, xor_mask: int):
