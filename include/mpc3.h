@@ -68,12 +68,14 @@ enum {
   MPC_SITE_MX_COPY_P1 = 3,  /* P0 -> P1 m of an input sharing (inconsistent replica)         */
   MPC_SITE_REC_MSG = 4,     /* P0 -> P1 [r]_2 of Pi_Rec                                      */
   MPC_SITE_HIGH_BIT = 5,    /* [Gamma]_2 XOR 2^63: the ring attack of Sec. 3                 */
-  MPC_NSITE = 6
+  MPC_SITE_AND_GAMMA2 = 6,  /* P0 -> P2 [Gamma]_2 of a Boolean AND gate (non-linear layers):
+                               flips bit `index` of the packed message when mask & 1            */
+  MPC_NSITE = 7
 };
 /* workspace queries */
 enum {
   MPC_OP_SHARE = 0, MPC_OP_MULT = 1, MPC_OP_MATMUL = 2, MPC_OP_VERIFY_MULT = 3,
-  MPC_OP_VERIFY_MATMUL = 4, MPC_OP_RECONSTRUCT = 5
+  MPC_OP_VERIFY_MATMUL = 4, MPC_OP_RECONSTRUCT = 5, MPC_OP_RELU = 6, MPC_OP_MAXPOOL2 = 7
 };
 
 typedef struct mpc_ctx mpc_ctx;
@@ -100,7 +102,8 @@ int mpc_sync(mpc_ctx* ctx);
 int mpc_status(const mpc_ctx* ctx);
 
 /* Bytes of workspace an operation needs.  op = MPC_OP_*; (a, b, c) = (n, 0, 0) for SHARE, MULT,
- * VERIFY_MULT and RECONSTRUCT, (M, N, K) for MATMUL and VERIFY_MATMUL; trunc_bits, R_main and
+ * VERIFY_MULT, RECONSTRUCT and RELU, (M, N, K) for MATMUL and VERIFY_MATMUL, (B C, H, W) for
+ * MAXPOOL2; trunc_bits, R_main and
  * R_trunc as passed to the operation (R < 0: default; VERIFY_MULT takes its R in R_main).
  * Returns -1 for invalid arguments. */
 int64_t mpc_workspace_size(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int64_t c,
@@ -178,6 +181,33 @@ int mpc_reconstruct(mpc_ctx* ctx, const uint64_t* xs, int64_t n, uint64_t* out, 
 #define MPC_NOALLOC_MAX_N 262144
 int mpc_reconstruct_noalloc(mpc_ctx* ctx, const uint64_t* xs, int64_t n, uint64_t* out);
 
+/* ---- non-linear layers (Sec. 4.3) -------------------------------------------------------------
+ * ReLU(x) = x [x >= 0] and 2x2 max-pool, each one layer with its own verification (reading A14):
+ *   - per compare-select stage: edaBits (Fig. edabits: 64 Pi_Mult + one dimension-64 Pi_Inner per
+ *     element), Delta = x - r opened with Pi_Rec, msb(x) from a depth-6 parallel-prefix carry
+ *     circuit of AND gates (Boolean Pi_Mult over Z_2, 125 per element), B2A of NOT msb with a
+ *     daBit (two Pi_Mult), and one Pi_Mult (x - y) [x >= y];
+ *   - then Pi_MultVerify of every arithmetic product (batch 0) and Pi_BIVerify of the edaBit
+ *     inner products (batch 1) over GR(2^64, 64), and Pi_MultVerify of every AND gate over
+ *     GF(2^64) = GR(2, 64) (batch 2).
+ * Elements are processed in groups padded to n_pad = 64 ceil(n / 64); Boolean values are
+ * bit-sliced.  Returns MPC_OK (verified), MPC_ERR_VERIFY, MPC_ERR_ABORT (a Pi_Rec mismatch).
+ *   xs: device sharing of n elements (6 n words, read); out: 6 n words (written);
+ *   call_id: streams of the layer; verify_id: streams of its verification;
+ *   trace (optional, device, zero-filled by the caller): per batch, R + 1 blocks as for
+ *     mpc_verify_mult for batches 0 and 1 (R = max(0, ceil(log2 D) - 6), D = products / entries),
+ *     then (R2 + 1) blocks of MPC_TRACE_GF_ROUND words for batch 2: zeta', h0 (6), h2 (6) per
+ *     round and Delta. */
+#define MPC_TRACE_GF_ROUND 13
+int mpc_relu(mpc_ctx* ctx, uint64_t call_id, uint64_t verify_id, const uint64_t* xs, int64_t n,
+             uint64_t* out, void* workspace, size_t workspace_bytes, uint64_t* trace);
+/* 2x2 / stride-2 max-pool of a (B, C, H, W) tensor, H and W even; out has B C (H/2) (W/2)
+ * elements.  Stage 0 compares the window pairs ([2i][2j], [2i][2j+1]) and ([2i+1][2j],
+ * [2i+1][2j+1]) in one batch, stage 1 the two winners. */
+int mpc_maxpool2(mpc_ctx* ctx, uint64_t call_id, uint64_t verify_id, const uint64_t* xs, int64_t B,
+                 int64_t C, int64_t H, int64_t W, uint64_t* out, void* workspace,
+                 size_t workspace_bytes, uint64_t* trace);
+
 /* Ledger: bytes[phase * MPC_NPROTO + proto] of every message sent so far, and the message
  * count.  Hash messages count 32 bytes. */
 int mpc_ledger(const mpc_ctx* ctx, uint64_t* bytes, uint64_t* messages);
@@ -209,10 +239,19 @@ enum {
   /* kernel-level intervals, nested inside the phases above (not added to them):           */
   MPC_PROF_K_LIMB_GEMM = 13,       /* the tensor-core kernel of each limb-split product     */
   MPC_PROF_K_TRUNC_S = 14,         /* the tensor-core kernel of the trunc-batch S matrix     */
-  MPC_NPROF = 15
+  MPC_PROF_K_GR_MATMUL = 15,       /* tensor-core GR-matrix products (folds, tables)        */
+  MPC_PROF_K_GRAM = 16,            /* tensor-core Gram sums of the dense rounds              */
+  MPC_PROF_K_GR_MUL_ROWS = 17,     /* elementwise GR products (CUDA cores)                   */
+  MPC_PROF_NONLINEAR = 18,         /* a non-linear layer (ReLU / max-pool), its verification */
+  MPC_NPROF = 19
 };
 int mpc_profile(mpc_ctx* ctx, int enable);
-int mpc_profile_read(mpc_ctx* ctx, double* ms /* MPC_NPROF */, uint64_t* count /* MPC_NPROF */);
+/* work (may be NULL): per interval id, the algorithmic u64 multiply-accumulates of the kernels
+ * timed under that id (M N K per limb-split product, 4096 per bit pair, coefficient and output
+ * of the S matrix, R 64 64 per GR-matrix product, 4 Dh 4096 per Gram call, 4096 per elementwise
+ * GR product); 0 for the phases. */
+int mpc_profile_read(mpc_ctx* ctx, double* ms /* MPC_NPROF */, uint64_t* count /* MPC_NPROF */,
+                     double* work /* MPC_NPROF */);
 
 /* Number of kernel launches the library has issued in this process (all contexts). */
 uint64_t mpc_launch_count(void);

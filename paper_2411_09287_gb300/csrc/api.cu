@@ -149,6 +149,7 @@ struct mpc_ctx {
   struct ProfRec {
     int id;
     cudaEvent_t a, b;
+    double work;   // algorithmic u64 multiply-accumulates of a kernel interval
   };
   bool prof = false;
   std::vector<ProfRec> recs;
@@ -189,8 +190,9 @@ cudaEvent_t prof_event(mpc_ctx* c) {
 struct Phase {
   mpc_ctx* c;
   int id;
+  double work;
   cudaEvent_t a = nullptr;
-  Phase(mpc_ctx* c_, int id_) : c(c_), id(id_) {
+  Phase(mpc_ctx* c_, int id_, double work_ = 0.0) : c(c_), id(id_), work(work_) {
     if (c->prof) {
       a = prof_event(c);
       cudaEventRecord(a, c->st);
@@ -200,7 +202,7 @@ struct Phase {
     if (c->prof) {
       cudaEvent_t b = prof_event(c);
       cudaEventRecord(b, c->st);
-      c->recs.push_back({id, a, b});
+      c->recs.push_back({id, a, b, work});
     }
   }
 };
@@ -296,6 +298,7 @@ int gr_matmul(mpc_ctx* ctx, long long R, const u64* p0, const u64* p1, u64 s1, l
   if (R <= 0) return MPC_OK;
   if (ctx->gemm_path == MPC_GEMM_LIMB_TC) {
     g_launches += 1;
+    Phase kp(ctx, MPC_PROF_K_GR_MATMUL, (double)R * 4096);
     if (gr_matmul_tc(ctx->st, R, p0, p1, s1, lda, 0, Mmat, add0, ld_add0, out, ldc, ctx->status,
                      ST_TIMEOUT) == 0)
       return MPC_OK;
@@ -317,8 +320,13 @@ int dense_gemm(mpc_ctx* ctx, long long M, long long N, long long K, const GemmTe
                const Epi& e, void* scratch) {
   if (scratch && !e.atomic) {
     g_launches += 4;
-    if (limb_gemm_tc(ctx->st, M, N, K, 1, &T, e, scratch, ctx->status, ST_TIMEOUT, nullptr,
-                     nullptr))
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ctx->prof) {
+      e0 = prof_event(ctx);
+      e1 = prof_event(ctx);
+      ctx->recs.push_back({MPC_PROF_K_LIMB_GEMM, e0, e1, (double)M * N * K});
+    }
+    if (limb_gemm_tc(ctx->st, M, N, K, 1, &T, e, scratch, ctx->status, ST_TIMEOUT, e0, e1))
       return fail(ctx, MPC_ERR_CUDA, "tensor-core GEMM setup failed");
     return MPC_OK;
   }
@@ -504,7 +512,10 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
     if (ctx->gemm_path == MPC_GEMM_LIMB_TC) {
       // tensor cores: G00, G11 and the cross sum G01 + G10 directly
       g_launches += 1;
-      done = gram3_tc(st, Dh, x.c[0], y.c[1], s.Pmat, ctx->status, ST_TIMEOUT) == 0;
+      {
+        Phase kp(ctx, MPC_PROF_K_GRAM, 4.0 * Dh * 4096);
+        done = gram3_tc(st, Dh, x.c[0], y.c[1], s.Pmat, ctx->status, ST_TIMEOUT) == 0;
+      }
       if (done) {
         launch_gr_fold_reduce(st, s.Pmat, 3, s.aux);
         CK(cudaMemcpyAsync(S00, s.aux, 512, cudaMemcpyDeviceToDevice, st));
@@ -921,6 +932,10 @@ int mpc_status(const mpc_ctx* ctx) {
   return ctx->aborted ? MPC_ERR_ABORT : MPC_OK;
 }
 
+namespace {
+void nl_plan_take(Arena& a, int nst, const long long np[2]);   // workspace of a non-linear layer
+}
+
 int64_t mpc_workspace_size(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int64_t c,
                            int trunc_bits, int R_main, int R_trunc) {
   (void)ctx;
@@ -947,6 +962,19 @@ int64_t mpc_workspace_size(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int
       if (a <= 0 || b <= 0 || c <= 0) return -1;
       plan_vmat(ar, a, b, c, trunc_bits, R_main, R_trunc, ctx && ctx->gemm_path == MPC_GEMM_LIMB_TC);
       break;
+    case MPC_OP_RELU: {
+      if (a <= 0) return -1;
+      const long long np[2] = {64 * ((a + 63) / 64), 0};
+      nl_plan_take(ar, 1, np);
+      break;
+    }
+    case MPC_OP_MAXPOOL2: {
+      if (a <= 0 || b <= 0 || c <= 0 || (b & 1) || (c & 1)) return -1;
+      const long long nw = a * (b / 2) * (c / 2);
+      const long long np[2] = {64 * ((2 * nw + 63) / 64), 64 * ((nw + 63) / 64)};
+      nl_plan_take(ar, 2, np);
+      break;
+    }
     case MPC_OP_RECONSTRUCT:
       if (a < 0) return -1;
       plan_rec(ar, a, true);
@@ -1033,7 +1061,7 @@ int mpc_matmul(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_
     if (ctx->prof) {
       e0 = prof_event(ctx);
       e1 = prof_event(ctx);
-      ctx->recs.push_back({MPC_PROF_K_LIMB_GEMM, e0, e1});
+      ctx->recs.push_back({MPC_PROF_K_LIMB_GEMM, e0, e1, (double)M * N * K * nterms});
     }
     const int r = limb_gemm_tc(ctx->st, M, N, K, nterms, T, e, p.tc, ctx->status, ST_TIMEOUT, e0, e1);
     return r ? fail(ctx, MPC_ERR_CUDA, "matmul: tensor-core GEMM setup failed") : MPC_OK;
@@ -1247,7 +1275,7 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
       launch_trunc_bit_transpose(st, p.b1, p.Epad, p.B1T);
       launch_trunc_bit_transpose(st, p.b2, p.Epad, p.B2T);
       {
-        Phase kphase(ctx, MPC_PROF_K_TRUNC_S);
+        Phase kphase(ctx, MPC_PROF_K_TRUNC_S, 4096.0 * 64 * E);
         g_launches += 1;
         if (launch_trunc_s_tc(st, p.B1T, p.B2T, p.Epad, p.TL8, p.L, p.nhi, p.S_hi, ctx->status,
                               ST_TIMEOUT))
@@ -1298,10 +1326,16 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
       u64* outs[4] = {tx.c[0], tx.c[3], ty.c[1], ty.c[5]};
       for (int v = 0; v < 4; ++v) {
         g_launches += 1;
-        if (gr_matmul_tc(st, E, bits[v], nullptr, 1, 1, 1, mats[v], nullptr, 0, outs[v], 64,
-                         ctx->status, ST_TIMEOUT))
-          return fail(ctx, MPC_ERR_CUDA, "verify_matmul: folded-vector product");
-        if (v < 2) launch_gr_mul_rows(st, E, outs[v], p.Rtab, outs[v]);
+        {
+          Phase kp(ctx, MPC_PROF_K_GR_MATMUL, (double)E * 4096);
+          if (gr_matmul_tc(st, E, bits[v], nullptr, 1, 1, 1, mats[v], nullptr, 0, outs[v], 64,
+                           ctx->status, ST_TIMEOUT))
+            return fail(ctx, MPC_ERR_CUDA, "verify_matmul: folded-vector product");
+        }
+        if (v < 2) {
+          Phase kp(ctx, MPC_PROF_K_GR_MUL_ROWS, (double)E * 4096);
+          launch_gr_mul_rows(st, E, outs[v], p.Rtab, outs[v]);
+        }
       }
     } else {
       launch_trunc_materialize(st, E, p.b1, p.V, p.Rtab, p.kd, tx.c[0]);
@@ -1394,12 +1428,13 @@ int mpc_profile(mpc_ctx* ctx, int enable) {
   return MPC_OK;
 }
 
-int mpc_profile_read(mpc_ctx* ctx, double* ms, uint64_t* count) {
+int mpc_profile_read(mpc_ctx* ctx, double* ms, uint64_t* count, double* work) {
   if (!ctx || !ms) return MPC_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->st));
   for (int i = 0; i < MPC_NPROF; ++i) {
     ms[i] = 0.0;
     if (count) count[i] = 0;
+    if (work) work[i] = 0.0;
   }
   for (const auto& r : ctx->recs) {
     float t = 0.f;
@@ -1407,6 +1442,7 @@ int mpc_profile_read(mpc_ctx* ctx, double* ms, uint64_t* count) {
     if (r.id >= 0 && r.id < MPC_NPROF) {
       ms[r.id] += t;
       if (count) count[r.id] += 1;
+      if (work) work[r.id] += r.work;
     }
   }
   ctx->recs.clear();
@@ -1436,3 +1472,605 @@ u32* ctx_status_word(const mpc_ctx* c) { return c->status; }
 void ctx_set_aborted(mpc_ctx* c) { c->aborted = true; }
 }  // namespace internal
 }  // namespace mpc3
+
+// ---- non-linear layers (Sec. 4.3) -------------------------------------------------------------
+namespace {
+
+// messages of one Pi_Mult / AND batch of up to n words
+struct MsgBuf {
+  u64 *g2o, *g2i, *p1o, *p2o, *p1i, *p2i;
+};
+MsgBuf plan_msg(Arena& a, long long n) {
+  MsgBuf m;
+  m.g2o = a.take<u64>(n); m.g2i = a.take<u64>(n);
+  m.p1o = a.take<u64>(n); m.p2o = a.take<u64>(n);
+  m.p1i = a.take<u64>(n); m.p2i = a.take<u64>(n);
+  return m;
+}
+
+// A Boolean message of nw words; the AND_GAMMA2 site flips bit `index` of it (when mask & 1), the
+// Boolean counterpart of an element fault; HIGH_BIT at l = 1 is the same bit flip.
+int deliver_bits(mpc_ctx* ctx, int phase, int proto, const u64* src, u64* dst, long long nw, int site) {
+  if (nw > 0) CK(cudaMemcpyAsync(dst, src, (size_t)nw * 8, cudaMemcpyDeviceToDevice, ctx->st));
+  ctx->ledger[phase][proto] += (u64)nw * 8;
+  ctx->nmsg += 1;
+  if (site >= 0 && nw > 0) {
+    Fault& f = ctx->fault[site];
+    if (f.armed) {
+      const u64 bit = f.index % (u64)(64 * nw);
+      if (f.mask & 1ull) launch_xor_one(ctx->st, dst + bit / 64, 1ull << (bit % 64));
+      f.armed = false;
+    }
+  }
+  return MPC_OK;
+}
+
+// arithmetic Pi_Mult (Fig. MultP) with the streams of (purpose, obj)
+int mult_p(mpc_ctx* ctx, const u64* xs, const u64* ys, long long n, u32 purpose, u64 obj, u64* zs,
+           const MsgBuf& m) {
+  int rc;
+  launch_mult_offline_p(ctx->st, xs, ys, n, ctx->k01, ctx->k02, purpose, obj, zs, m.g2o);
+  g_launches += 1;
+  if ((rc = deliver(ctx, MPC_PHASE_OFFLINE, MPC_PROTO_MULT, m.g2o, m.g2i, n, MPC_SITE_GAMMA2))) return rc;
+  launch_mult_online_p(ctx->st, xs, ys, n, ctx->k01, purpose, obj, m.g2i, m.p1o, m.p2o);
+  g_launches += 1;
+  if ((rc = deliver(ctx, MPC_PHASE_ONLINE, MPC_PROTO_MULT, m.p1o, m.p2i, n, MPC_SITE_MZ1))) return rc;
+  if ((rc = deliver(ctx, MPC_PHASE_ONLINE, MPC_PROTO_MULT, m.p2o, m.p1i, n, MPC_SITE_MZ2))) return rc;
+  launch_exchange_finish(ctx->st, n, m.p1o, m.p1i, m.p2o, m.p2i, zs, -1, nullptr);
+  return MPC_OK;
+}
+
+// Boolean AND gates (Fig. MultP over Z_2) on nw bit-sliced words
+int and_p(mpc_ctx* ctx, const u64* xs, const u64* ys, long long nw, u32 purpose, u64 obj, u64* zs,
+          const MsgBuf& m) {
+  int rc;
+  launch_and_offline(ctx->st, xs, ys, nw, ctx->k01, ctx->k02, purpose, obj, zs, m.g2o);
+  g_launches += 1;
+  if ((rc = deliver_bits(ctx, MPC_PHASE_OFFLINE, MPC_PROTO_MULT, m.g2o, m.g2i, nw, MPC_SITE_AND_GAMMA2)))
+    return rc;
+  launch_and_online(ctx->st, xs, ys, nw, ctx->k01, purpose, obj, m.g2i, m.p1o, m.p2o);
+  g_launches += 1;
+  if ((rc = deliver_bits(ctx, MPC_PHASE_ONLINE, MPC_PROTO_MULT, m.p1o, m.p2i, nw, -1))) return rc;
+  if ((rc = deliver_bits(ctx, MPC_PHASE_ONLINE, MPC_PROTO_MULT, m.p2o, m.p1i, nw, -1))) return rc;
+  launch_xor_finish(ctx->st, nw, m.p1o, m.p1i, m.p2o, m.p2i, zs);
+  g_launches += 1;
+  return MPC_OK;
+}
+
+// Pi_Rec of n words inside a layer (messages, hashes, consistency check into the status word);
+// P1's opening into out: m - [r]_1 - [r]_2, or m XOR [r]_1 XOR [r]_2 for a Boolean sharing.
+int rec_open(mpc_ctx* ctx, const u64* xs, long long n, const RecPlan& p, u64* out, bool boolean) {
+  int rc;
+  cudaStream_t st = ctx->st;
+  const int ph = MPC_PHASE_ONLINE, pr = MPC_PROTO_REC;
+  if ((rc = deliver(ctx, ph, pr, xs, p.in_p2_r1, n, -1))) return rc;
+  if ((rc = deliver(ctx, ph, pr, xs + n, p.in_p1_r2, n, boolean ? -1 : MPC_SITE_REC_MSG))) return rc;
+  if ((rc = deliver(ctx, ph, pr, xs + 2 * n, p.in_p0_m, n, -1))) return rc;
+  u32* d = p.dg;
+  launch_hash_u64(st, xs + 3 * n, n, p.hs[0], d + 0);
+  launch_hash_u64(st, xs + 4 * n, n, p.hs[1], d + 8);
+  launch_hash_u64(st, xs + 5 * n, n, p.hs[2], d + 16);
+  count_msgs(ctx, ph, pr, 3, 32);
+  launch_hash_u64(st, p.in_p2_r1, n, p.hs[3], d + 24);
+  launch_hash_u64(st, p.in_p0_m, n, p.hs[4], d + 32);
+  launch_hash_u64(st, p.in_p1_r2, n, p.hs[5], d + 40);
+  launch_digest_check(st, d + 0, d + 24, d + 8, d + 32, d + 16, d + 40, ctx->status, ST_ABORT);
+  if (boolean) {
+    launch_open_xor(st, xs + 2 * n, xs + 3 * n, p.in_p1_r2, n, out);
+    g_launches += 1;
+  } else {
+    launch_open_p1(st, xs + 2 * n, xs + 3 * n, p.in_p1_r2, n, out);
+  }
+  return MPC_OK;
+}
+
+constexpr int NL_LEVELS = 6;
+inline int level_planes(int l) { return l == NL_LEVELS ? 1 : 2 * (32 >> (l - 1)); }   // 64,32,..,4,1
+
+// Buffers of one compare-select stage of np (padded) elements, W = np / 64 words per plane.
+struct CSPlan {
+  long long np, W;
+  MsgBuf ma, mb;                 // arithmetic (64 np) and Boolean (64 W) message buffers
+  u64 *b1w, *b2w, *mbw, *rbits;  // edaBit bit planes (64 W each), Boolean sharing (6 x 64 W)
+  u64 *B1, *B2, *eprod, *rp;     // 6 x 64 np each
+  u64 *ez, *ra, *dd;             // 6 x np: edaBit inner products, <r>, <x - r>
+  u64 *delta, *dpl;              // np public words, 64 W bit planes
+  u64 *G, *P, *G2, *P2;          // 6 x 64 W each
+  u64 *X[NL_LEVELS + 1], *Y[NL_LEVELS + 1], *Z[NL_LEVELS + 1];   // AND triples per level
+  u64 *ge, *r1w, *r2w, *r3w, *rb, *e, *dbits;                    // Boolean, W-sized
+  u64 *A1, *A2, *A3, *t, *rpd, *u, *rad, *gea, *d, *prod;        // 6 x np
+  RecPlan reca, recb;
+  long long and_words;           // words of all AND triples (per component)
+};
+
+CSPlan plan_cs(Arena& a, long long np) {
+  CSPlan p;
+  p.np = np;
+  p.W = np / 64;
+  const long long W = p.W, N = 64 * np;
+  p.ma = plan_msg(a, N);
+  p.mb = plan_msg(a, 64 * W);
+  p.b1w = a.take<u64>(64 * W); p.b2w = a.take<u64>(64 * W); p.mbw = a.take<u64>(64 * W);
+  p.rbits = a.take<u64>(6 * 64 * W);
+  p.B1 = a.take<u64>(6 * N); p.B2 = a.take<u64>(6 * N);
+  p.eprod = a.take<u64>(6 * N); p.rp = a.take<u64>(6 * N);
+  p.ez = a.take<u64>(6 * np); p.ra = a.take<u64>(6 * np); p.dd = a.take<u64>(6 * np);
+  p.delta = a.take<u64>(np); p.dpl = a.take<u64>(64 * W);
+  p.G = a.take<u64>(6 * 64 * W); p.P = a.take<u64>(6 * 64 * W);
+  p.G2 = a.take<u64>(6 * 64 * W); p.P2 = a.take<u64>(6 * 64 * W);
+  p.and_words = 0;
+  for (int l = 1; l <= NL_LEVELS; ++l) {
+    const long long nw = (long long)level_planes(l) * W;
+    p.X[l] = a.take<u64>(6 * nw); p.Y[l] = a.take<u64>(6 * nw); p.Z[l] = a.take<u64>(6 * nw);
+    p.and_words += nw;
+  }
+  p.ge = a.take<u64>(6 * W);
+  p.r1w = a.take<u64>(W); p.r2w = a.take<u64>(W); p.r3w = a.take<u64>(W);
+  p.rb = a.take<u64>(6 * W); p.e = a.take<u64>(6 * W); p.dbits = a.take<u64>(W);
+  p.A1 = a.take<u64>(6 * np); p.A2 = a.take<u64>(6 * np); p.A3 = a.take<u64>(6 * np);
+  p.t = a.take<u64>(6 * np); p.rpd = a.take<u64>(6 * np); p.u = a.take<u64>(6 * np);
+  p.rad = a.take<u64>(6 * np); p.gea = a.take<u64>(6 * np); p.d = a.take<u64>(6 * np);
+  p.prod = a.take<u64>(6 * np);
+  p.reca = plan_rec(a, np, false);
+  p.recb = plan_rec(a, W, false);
+  return p;
+}
+
+// Boolean sharing (6 x nw words) whose components are the pair-known bit planes (r1, r2, m):
+// P0 (r1, r2), P1 (m, r1), P2 (m, r2)
+int bool_from_planes(mpc_ctx* ctx, const u64* r1, const u64* r2, const u64* m, long long nw, u64* s) {
+  const u64* src[6] = {r1, r2, m, r1, m, r2};
+  for (int c = 0; c < 6; ++c)
+    CK(cudaMemcpyAsync(s + c * nw, src[c], (size_t)nw * 8, cudaMemcpyDeviceToDevice, ctx->st));
+  return MPC_OK;
+}
+
+// <max(a, b)> into out (6 np each; out may alias neither a nor b): Sec. 4.3 compare-select
+int compare_select(mpc_ctx* ctx, u64 call_id, int stage, const u64* a, const u64* b, CSPlan& p,
+                   u64* out) {
+  int rc;
+  cudaStream_t st = ctx->st;
+  const long long np = p.np, W = p.W, N = 64 * np;
+  const u64 obj = make_obj(call_id, (u32)stage, 0);
+  launch_addsub(st, 6 * np, a, b, 1, p.d);                                  // d = a - b
+  g_launches += 1;
+  // edaBits (Fig. edabits)
+  launch_prf_words(st, 64 * W, ctx->k01, make_tag(P_EDABIT, C_R1), obj, p.b1w);
+  launch_prf_words(st, 64 * W, ctx->k02, make_tag(P_EDABIT, C_R2), obj, p.b2w);
+  launch_prf_words(st, 64 * W, ctx->k12, make_tag(P_EDABIT, C_M12), obj, p.mbw);
+  if ((rc = bool_from_planes(ctx, p.b1w, p.b2w, p.mbw, 64 * W, p.rbits))) return rc;
+  launch_bits_to_arith(st, p.b1w, N, 0, p.B1);
+  launch_bits_to_arith(st, p.b2w, N, 1, p.B2);
+  g_launches += 2;
+  if ((rc = mult_p(ctx, p.B1, p.B2, N, P_EDA_MULT, obj, p.eprod, p.ma))) return rc;
+  launch_lin_apb_m2c(st, 6 * N, p.B1, p.B2, p.eprod, p.rp);                 // r' = b1 + b2 - 2 b1 b2
+  launch_eda_inner_offline(st, np, ctx->k01, ctx->k02, obj, p.ez, p.ma.g2o);
+  g_launches += 2;
+  if ((rc = deliver(ctx, MPC_PHASE_OFFLINE, MPC_PROTO_INNER, p.ma.g2o, p.ma.g2i, np, MPC_SITE_GAMMA2)))
+    return rc;
+  launch_eda_inner_online(st, p.mbw, p.rp, np, ctx->k01, obj, p.ma.g2i, p.ma.p1o, p.ma.p2o);
+  g_launches += 1;
+  if ((rc = deliver(ctx, MPC_PHASE_OFFLINE, MPC_PROTO_INNER, p.ma.p1o, p.ma.p2i, np, MPC_SITE_MZ1))) return rc;
+  if ((rc = deliver(ctx, MPC_PHASE_OFFLINE, MPC_PROTO_INNER, p.ma.p2o, p.ma.p1i, np, MPC_SITE_MZ2))) return rc;
+  launch_exchange_finish(st, np, p.ma.p1o, p.ma.p1i, p.ma.p2o, p.ma.p2i, p.ez, -1, nullptr);
+  launch_eda_compose(st, p.mbw, p.rp, p.ez, np, p.ra);
+  g_launches += 2;
+  // msb(d): open Delta = d - r, carry circuit over the bits of Delta + r
+  launch_addsub(st, 6 * np, p.d, p.ra, 1, p.dd);
+  g_launches += 1;
+  if ((rc = rec_open(ctx, p.dd, np, p.reca, p.delta, false))) return rc;
+  launch_trunc_bit_transpose(st, p.delta, np, p.dpl);
+  launch_msb_leaves(st, p.rbits, p.dpl, W, p.G, p.P);
+  g_launches += 2;
+  u64 *G = p.G, *P = p.P, *G2 = p.G2, *P2 = p.P2;
+  for (int l = 1; l <= NL_LEVELS; ++l) {
+    const int C = 32 >> (l - 1);
+    const int root = l == NL_LEVELS;
+    const long long nw = (long long)level_planes(l) * W;
+    launch_msb_gather(st, G, P, C, root, W, p.X[l], p.Y[l]);
+    g_launches += 1;
+    if ((rc = and_p(ctx, p.X[l], p.Y[l], nw, P_AND, make_obj(call_id, (u32)stage, (u32)l), p.Z[l], p.mb)))
+      return rc;
+    launch_msb_combine(st, G, p.Z[l], C, root, W, G2, P2);
+    g_launches += 1;
+    std::swap(G, G2);
+    std::swap(P, P2);
+  }
+  launch_msb_out(st, p.rbits, G, p.dpl + 63 * W, W, 1, p.ge);               // [d >= 0] = NOT msb
+  g_launches += 1;
+  // daBit and B2A
+  launch_prf_words(st, W, ctx->k01, make_tag(P_DABIT, C_R1), obj, p.r1w);
+  launch_prf_words(st, W, ctx->k02, make_tag(P_DABIT, C_R2), obj, p.r2w);
+  launch_prf_words(st, W, ctx->k12, make_tag(P_DABIT, C_M12), obj, p.r3w);
+  if ((rc = bool_from_planes(ctx, p.r1w, p.r2w, p.r3w, W, p.rb))) return rc;
+  launch_bits_to_arith(st, p.r1w, np, 0, p.A1);
+  launch_bits_to_arith(st, p.r2w, np, 1, p.A2);
+  launch_bits_to_arith(st, p.r3w, np, 2, p.A3);
+  g_launches += 3;
+  if ((rc = mult_p(ctx, p.A1, p.A2, np, P_DA_MULT1, obj, p.t, p.ma))) return rc;
+  launch_lin_apb_m2c(st, 6 * np, p.A1, p.A2, p.t, p.rpd);
+  g_launches += 1;
+  if ((rc = mult_p(ctx, p.rpd, p.A3, np, P_DA_MULT2, obj, p.u, p.ma))) return rc;
+  launch_lin_apb_m2c(st, 6 * np, p.rpd, p.A3, p.u, p.rad);
+  launch_bxor(st, 6 * W, p.ge, p.rb, p.e);
+  g_launches += 2;
+  if ((rc = rec_open(ctx, p.e, W, p.recb, p.dbits, true))) return rc;
+  launch_b2a_apply(st, p.dbits, p.rad, np, p.gea);
+  g_launches += 1;
+  // out = b + (a - b) [a >= b]
+  if ((rc = mult_p(ctx, p.d, p.gea, np, P_NL_MULT, obj, p.prod, p.ma))) return rc;
+  launch_addsub(st, 6 * np, b, p.prod, 0, out);
+  g_launches += 1;
+  return cuda_check(ctx, "compare_select");
+}
+
+// ---- verification of a non-linear layer -------------------------------------------------------
+struct GfPlan {   // GF(2^64) Pi_MultVerify of D AND gates
+  long long D;
+  int R;
+  u64 *XA, *YA, *ZA;        // concatenated triples, 6 x nw words each
+  u64 *pw;                  // D
+  u64 *x[2], *y[2];         // ping-pong GF vectors, 6 x (D + 1) and 6 x ((D + 1) / 2 + 1)
+  u64 *small;               // 64 words: z, h0, h2, S, coef, r, zeta', tmp6, alpha, delta
+  u64 *lhs, *rhs;           // 6 x (Dfinal + 1)
+};
+
+GfPlan plan_gf(Arena& a, long long nw, int R) {
+  GfPlan g;
+  g.D = 64 * nw;
+  g.R = R < 0 ? default_R(g.D) : R;
+  g.XA = a.take<u64>(6 * nw); g.YA = a.take<u64>(6 * nw); g.ZA = a.take<u64>(6 * nw);
+  g.pw = a.take<u64>(g.D);
+  g.x[0] = a.take<u64>(6 * (g.D + 1)); g.y[0] = a.take<u64>(6 * (g.D + 1));
+  g.x[1] = a.take<u64>(6 * ((g.D + 1) / 2 + 1)); g.y[1] = a.take<u64>(6 * ((g.D + 1) / 2 + 1));
+  g.small = a.take<u64>(128);
+  const long long Df = dim_after(g.D, g.R);
+  g.lhs = a.take<u64>(6 * (Df + 1)); g.rhs = a.take<u64>(6 * (Df + 1));
+  return g;
+}
+
+// random shared GF element revealed with Pi_Rec (3 one-word messages, 3 hashes)
+void gf_reveal(mpc_ctx* ctx, u32 purpose, u64 obj, u64* tmp6, u64* out) {
+  launch_gf_random_shared(ctx->st, ctx->k01, ctx->k02, ctx->k12, purpose, obj, tmp6);
+  launch_gf_rec1(ctx->st, tmp6, 0ull, out, ctx->status, ST_ABORT);
+  g_launches += 2;
+  count_msgs(ctx, MPC_PHASE_VERIFY, MPC_PROTO_VERIFY, 3, 8);
+  count_msgs(ctx, MPC_PHASE_VERIFY, MPC_PROTO_VERIFY, 3, 32);
+}
+
+// secure GF inner product of (u, v) from their party sums (S must be zeroed by the caller, then
+// filled by launch_gf_party_sums): finish + 3 one-word messages
+void gf_inner_finish(mpc_ctx* ctx, const u64* S, u32 purpose, u64 obj, u64* h6) {
+  launch_gf_inner_finish(ctx->st, S, ctx->k01, ctx->k02, purpose, obj, h6);
+  g_launches += 1;
+  count_msgs(ctx, MPC_PHASE_VERIFY, MPC_PROTO_VERIFY, 3, 8);
+}
+
+// Pi_MultVerify (Fig. PPEV) over GF(2^64) of the AND triples in g.XA/YA/ZA (batch 2)
+int gf_verify(mpc_ctx* ctx, u64 vid, GfPlan& g, u64* trace) {
+  cudaStream_t st = ctx->st;
+  u64* z = g.small;          // 6
+  u64* h0 = g.small + 8;     // 6
+  u64* h2 = g.small + 16;    // 6
+  u64* S = g.small + 24;     // 3
+  u64* coef = g.small + 32;  // 5
+  u64* r = g.small + 40;     // 1
+  u64* zp = g.small + 41;    // 1
+  u64* tmp6 = g.small + 48;  // 6
+  u64* alpha = g.small + 56; // 6
+  u64* dl = g.small + 64;    // 1
+  u64* zn = g.small + 72;    // 6
+  const long long nw = g.D / 64;
+  CK(cudaMemsetAsync(g.small, 0, 128 * 8, st));
+  gf_reveal(ctx, P_VER_R, make_obj(vid, 2, 0), tmp6, r);
+  launch_gf_powers(st, r, g.D, g.pw);
+  launch_gf_tran(st, g.XA, g.YA, g.ZA, nw, g.pw, g.D + 1, g.x[0], g.y[0], z);
+  g_launches += 2;
+  long long D = g.D;
+  int cur = 0;
+  const u64 X1 = 3ull, XX = 2ull;   // 1 + x and x: the fold weights at the third point x
+  for (int k = 1; k <= g.R; ++k) {
+    const long long cap = cur == 0 ? g.D + 1 : (g.D + 1) / 2 + 1;
+    u64* xv = g.x[cur];
+    u64* yv = g.y[cur];
+    if (D & 1)
+      for (int c = 0; c < 6; ++c) {
+        CK(cudaMemsetAsync(xv + c * cap + D, 0, 8, st));
+        CK(cudaMemsetAsync(yv + c * cap + D, 0, 8, st));
+      }
+    const long long Dh = (D + 1) / 2;
+    const u64 obj = make_obj(vid, 2, (u32)k);
+    const u64* uc[6];
+    const u64* vc[6];
+    for (int c = 0; c < 6; ++c) {
+      uc[c] = xv + c * cap;
+      vc[c] = yv + c * cap;
+    }
+    CK(cudaMemsetAsync(S, 0, 3 * 8, st));
+    launch_gf_party_sums(st, uc, vc, Dh, 2, 0, 0, 0, 0, S);           // even entries
+    g_launches += 1;
+    gf_inner_finish(ctx, S, P_VER_H0, obj, h0);
+    CK(cudaMemsetAsync(S, 0, 3 * 8, st));
+    launch_gf_party_sums(st, uc, vc, Dh, 1, 0, 1, X1, XX, S);         // f(x) = (1+x) f(0) + x f(1)
+    g_launches += 1;
+    gf_inner_finish(ctx, S, P_VER_H2, obj, h2);
+    gf_reveal(ctx, P_VER_ZETA, obj, tmp6, zp);
+    launch_gf_lagrange(st, zp, coef);
+    launch_gf_combine_z(st, coef, h0, h2, z, zn);
+    g_launches += 2;
+    CK(cudaMemcpyAsync(z, zn, 6 * 8, cudaMemcpyDeviceToDevice, st));
+    const long long ocap = (g.D + 1) / 2 + 1;
+    u64* xo = g.x[1];
+    u64* yo = g.y[1];
+    if (cur == 1) {   // fold in place is not allowed: fold into slot 0's storage
+      xo = g.x[0];
+      yo = g.y[0];
+    }
+    const long long ocap2 = cur == 1 ? g.D + 1 : ocap;
+    for (int c = 0; c < 6; ++c) {
+      launch_gf_fold(st, xv + c * cap, D, coef, xo + c * ocap2);
+      launch_gf_fold(st, yv + c * cap, D, coef, yo + c * ocap2);
+    }
+    g_launches += 12;
+    if (trace) {
+      u64* t = trace + (long long)(k - 1) * MPC_TRACE_GF_ROUND;
+      CK(cudaMemcpyAsync(t, zp, 8, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(t + 1, h0, 48, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(t + 7, h2, 48, cudaMemcpyDeviceToDevice, st));
+    }
+    cur ^= 1;
+    D = Dh;
+  }
+  // Pi_InnerVerify (Fig. DPV): alpha random (kept shared), x' = x alpha, Delta = <[x'; alpha],
+  // [y; -z]> opened, accept iff 0
+  const long long cap = cur == 0 ? g.D + 1 : (g.D + 1) / 2 + 1;
+  u64* xv = g.x[cur];
+  u64* yv = g.y[cur];
+  const u64 obj = make_obj(vid, 2, 0);
+  launch_gf_random_shared(st, ctx->k01, ctx->k02, ctx->k12, P_VER_ALPHA, obj, alpha);
+  g_launches += 1;
+  const u64* xc[6];
+  for (int c = 0; c < 6; ++c) xc[c] = xv + c * cap;
+  const long long Df = D;
+  launch_gf_mult_alpha(st, xc, alpha, Df, Df + 1, ctx->k01, ctx->k02, obj, g.lhs);
+  g_launches += 1;
+  count_msgs(ctx, MPC_PHASE_VERIFY, MPC_PROTO_VERIFY, 3, (u64)8 * Df);
+  // lhs = [x alpha ; alpha], rhs = [y ; -z] (-z = z in characteristic 2), Df + 1 entries each
+  for (int c = 0; c < 6; ++c) {
+    CK(cudaMemcpyAsync(g.lhs + c * (Df + 1) + Df, alpha + c, 8, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(g.rhs + c * (Df + 1), yv + c * cap, (size_t)Df * 8, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(g.rhs + c * (Df + 1) + Df, z + c, 8, cudaMemcpyDeviceToDevice, st));
+  }
+  const u64* uc[6];
+  const u64* vc[6];
+  for (int c = 0; c < 6; ++c) {
+    uc[c] = g.lhs + c * (Df + 1);
+    vc[c] = g.rhs + c * (Df + 1);
+  }
+  CK(cudaMemsetAsync(S, 0, 3 * 8, st));
+  launch_gf_party_sums(st, uc, vc, Df + 1, 1, 0, 0, 0, 0, S);
+  g_launches += 1;
+  gf_inner_finish(ctx, S, P_VER_DELTA, obj, tmp6);
+  launch_gf_rec1(st, tmp6, 0ull, dl, ctx->status, ST_ABORT);
+  launch_gf_check_zero(st, dl, ctx->status, ST_VERIFY);
+  g_launches += 2;
+  count_msgs(ctx, MPC_PHASE_VERIFY, MPC_PROTO_VERIFY, 3, 8);
+  count_msgs(ctx, MPC_PHASE_VERIFY, MPC_PROTO_VERIFY, 3, 32);
+  if (trace) CK(cudaMemcpyAsync(trace + (long long)g.R * MPC_TRACE_GF_ROUND, dl, 8, cudaMemcpyDeviceToDevice, st));
+  return cuda_check(ctx, "gf_verify");
+}
+
+struct NLPlan {
+  int nst;
+  CSPlan cs[2];
+  u64 *a[2], *b[2], *o[2];       // stage operands (6 x np each)
+  // batch 0: arithmetic products
+  long long nm;
+  u64 *MX, *MY, *MZ;
+  VMultPlan vm;
+  // batch 1: edaBit inner products (D1 = 64 sum np rows)
+  long long ne, D1;
+  int R1;
+  Small s1;
+  u64* pw1;
+  Dense d1;
+  IVBuf iv1;
+  u64** ydev;                    // 6 device pointers (kernel argument)
+  // batch 2: AND gates
+  GfPlan gf;
+};
+
+NLPlan plan_nl(Arena& a, int nst, const long long np[2]) {
+  NLPlan p;
+  p.nst = nst;
+  p.nm = 0;
+  p.ne = 0;
+  long long andw = 0;
+  for (int s = 0; s < nst; ++s) {
+    p.a[s] = a.take<u64>(6 * np[s]);
+    p.b[s] = a.take<u64>(6 * np[s]);
+    p.o[s] = a.take<u64>(6 * np[s]);
+    p.cs[s] = plan_cs(a, np[s]);
+    p.nm += 67 * np[s];
+    p.ne += np[s];
+    andw += p.cs[s].and_words;
+  }
+  p.MX = a.take<u64>(6 * p.nm); p.MY = a.take<u64>(6 * p.nm); p.MZ = a.take<u64>(6 * p.nm);
+  p.vm = plan_vmult(a, p.nm, -1);
+  p.D1 = 64 * p.ne;
+  p.R1 = default_R(p.D1);
+  p.s1 = plan_small(a);
+  p.pw1 = a.take<u64>(p.ne * 64);
+  const bool xc[6] = {false, false, true, false, true, false};
+  const bool yc[6] = {true, true, true, true, true, true};
+  p.d1 = plan_dense(a, p.D1, xc, yc);
+  p.iv1 = plan_iv(a, dim_after(p.D1, p.R1));
+  p.ydev = a.take<u64*>(6);
+  p.gf = plan_gf(a, andw, -1);
+  return p;
+}
+
+// copy component c of an n-element sharing into a concatenated sharing of total length tot at
+// offset off
+int append_sharing(mpc_ctx* ctx, const u64* src, long long n, u64* dst, long long tot, long long off) {
+  for (int c = 0; c < 6; ++c)
+    CK(cudaMemcpyAsync(dst + c * tot + off, src + c * n, (size_t)n * 8, cudaMemcpyDeviceToDevice, ctx->st));
+  return MPC_OK;
+}
+
+int verify_nl(mpc_ctx* ctx, u64 vid, NLPlan& p, u64* trace) {
+  int rc;
+  cudaStream_t st = ctx->st;
+  // ---- batch 0: every arithmetic Pi_Mult, in the order edaBit products, daBit products (two),
+  // final product, stage by stage
+  long long off = 0;
+  for (int s = 0; s < p.nst; ++s) {
+    CSPlan& c = p.cs[s];
+    const long long N = 64 * c.np;
+    const u64* trip[4][3] = {{c.B1, c.B2, c.eprod}, {c.A1, c.A2, c.t}, {c.rpd, c.A3, c.u},
+                             {c.d, c.gea, c.prod}};
+    const long long len[4] = {N, c.np, c.np, c.np};
+    for (int q = 0; q < 4; ++q) {
+      if ((rc = append_sharing(ctx, trip[q][0], len[q], p.MX, p.nm, off))) return rc;
+      if ((rc = append_sharing(ctx, trip[q][1], len[q], p.MY, p.nm, off))) return rc;
+      if ((rc = append_sharing(ctx, trip[q][2], len[q], p.MZ, p.nm, off))) return rc;
+      off += len[q];
+    }
+  }
+  {
+    VMultPlan& v = p.vm;
+    const Small& s = v.s;
+    const long long n = p.nm;
+    reveal(ctx, P_VER_R, make_obj(vid, 0, 0), s.tmp6, s.r);
+    launch_gr_powers(st, s.r, n, v.pw);
+    Vec& x = v.dv.x[0];
+    Vec& y = v.dv.y[0];
+    for (int c = 0; c < 6; ++c) {
+      launch_gr_scale_rows(st, v.pw, p.MX + c * n, n, x.c[c]);
+      launch_gr_lift(st, p.MY + c * n, n, y.c[c]);
+    }
+    CK(cudaMemsetAsync(s.zinit, 0, 384 * 8, st));
+    launch_scalar_gr_sum(st, n, p.MZ, n, 6, v.pw, s.zinit);
+    v.dv.cur = 0;
+    if ((rc = run_dense(ctx, vid, 0, v.dv, n, s.zinit, 1, v.R, s, v.iv, trace))) return rc;
+  }
+  u64* tr1 = trace ? trace + (long long)(p.vm.R + 1) * TRACE_ROUND : nullptr;
+  // ---- batch 1: the edaBit inner products, weight r^e on row e (e over all stages)
+  {
+    const Small& s = p.s1;
+    reveal(ctx, P_VER_R, make_obj(vid, 1, 0), s.tmp6, s.r);
+    launch_gr_powers(st, s.r, p.ne, p.pw1);
+    Vec& x = p.d1.x[0];
+    Vec& y = p.d1.y[0];
+    CK(cudaMemcpyAsync(p.ydev, y.c, 6 * sizeof(u64*), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(s.zinit, 0, 384 * 8, st));
+    long long e0 = 0;
+    for (int q = 0; q < p.nst; ++q) {
+      CSPlan& c = p.cs[q];
+      launch_eda_tran(st, c.mbw, c.rp, c.np, p.pw1, e0, x.c[2], x.c[4], p.ydev);
+      launch_scalar_gr_sum(st, c.np, c.ez, c.np, 6, p.pw1 + e0 * 64, s.zinit);
+      g_launches += 1;
+      e0 += c.np;
+    }
+    p.d1.cur = 0;
+    if ((rc = run_dense(ctx, vid, 1, p.d1, p.D1, s.zinit, 1, p.R1, s, p.iv1, tr1))) return rc;
+  }
+  u64* tr2 = tr1 ? tr1 + (long long)(p.R1 + 1) * TRACE_ROUND : nullptr;
+  // ---- batch 2: every AND gate over GF(2^64), stage by stage, level by level
+  {
+    GfPlan& g = p.gf;
+    const long long nw = g.D / 64;
+    long long woff = 0;
+    for (int s = 0; s < p.nst; ++s) {
+      CSPlan& c = p.cs[s];
+      for (int l = 1; l <= NL_LEVELS; ++l) {
+        const long long lw = (long long)level_planes(l) * c.W;
+        if ((rc = append_sharing(ctx, c.X[l], lw, g.XA, nw, woff))) return rc;
+        if ((rc = append_sharing(ctx, c.Y[l], lw, g.YA, nw, woff))) return rc;
+        if ((rc = append_sharing(ctx, c.Z[l], lw, g.ZA, nw, woff))) return rc;
+        woff += lw;
+      }
+    }
+    if ((rc = gf_verify(ctx, vid, g, tr2))) return rc;
+  }
+  return MPC_OK;
+}
+
+int nl_finish(mpc_ctx* ctx) {
+  u32 stv = 0;
+  int rc = read_status(ctx, &stv);
+  if (rc) return rc;
+  if (stv & ST_ABORT) {
+    ctx->aborted = true;
+    return fail(ctx, MPC_ERR_ABORT, "Pi_Rec: inconsistent messages");
+  }
+  if (stv & ST_VERIFY) {
+    ctx->aborted = true;
+    return fail(ctx, MPC_ERR_VERIFY, "non-linear layer: verification failed");
+  }
+  return MPC_OK;
+}
+
+long long npad64(long long n) { return 64 * ((n + 63) / 64); }
+
+void nl_plan_take(Arena& a, int nst, const long long np[2]) { plan_nl(a, nst, np); }
+
+}  // namespace
+
+int mpc_relu(mpc_ctx* ctx, uint64_t call_id, uint64_t verify_id, const uint64_t* xs, int64_t n,
+             uint64_t* out, void* workspace, size_t workspace_bytes, uint64_t* trace) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (n <= 0) return fail(ctx, MPC_ERR_SHAPE, "relu: n <= 0");
+  if (!xs || !out || !id_ok(call_id) || !id_ok(verify_id)) return fail(ctx, MPC_ERR_ARG, "relu: bad argument");
+  Arena ar{(char*)workspace, workspace_bytes, 0, false};
+  const long long np[2] = {npad64(n), 0};
+  NLPlan p = plan_nl(ar, 1, np);
+  if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "relu: workspace too small");
+  Phase phase(ctx, MPC_PROF_NONLINEAR);
+  cudaStream_t st = ctx->st;
+  CK(cudaMemsetAsync(p.a[0], 0, (size_t)6 * np[0] * 8, st));
+  CK(cudaMemsetAsync(p.b[0], 0, (size_t)6 * np[0] * 8, st));
+  if ((rc = append_sharing(ctx, xs, n, p.a[0], np[0], 0))) return rc;      // zero-padded x, b = 0
+  if ((rc = compare_select(ctx, call_id, 0, p.a[0], p.b[0], p.cs[0], p.o[0]))) return rc;
+  if ((rc = verify_nl(ctx, verify_id, p, trace))) return rc;
+  for (int c = 0; c < 6; ++c)
+    CK(cudaMemcpyAsync(out + c * n, p.o[0] + c * np[0], (size_t)n * 8, cudaMemcpyDeviceToDevice, st));
+  if ((rc = cuda_check(ctx, "relu"))) return rc;
+  return nl_finish(ctx);
+}
+
+int mpc_maxpool2(mpc_ctx* ctx, uint64_t call_id, uint64_t verify_id, const uint64_t* xs, int64_t B,
+                 int64_t C, int64_t H, int64_t W, uint64_t* out, void* workspace,
+                 size_t workspace_bytes, uint64_t* trace) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (B <= 0 || C <= 0 || H <= 0 || W <= 0 || (H & 1) || (W & 1))
+    return fail(ctx, MPC_ERR_SHAPE, "maxpool2: bad shape");
+  if (!xs || !out || !id_ok(call_id) || !id_ok(verify_id)) return fail(ctx, MPC_ERR_ARG, "maxpool2: bad argument");
+  const long long nw = B * C * (H / 2) * (W / 2);
+  Arena ar{(char*)workspace, workspace_bytes, 0, false};
+  const long long np[2] = {npad64(2 * nw), npad64(nw)};
+  NLPlan p = plan_nl(ar, 2, np);
+  if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "maxpool2: workspace too small");
+  Phase phase(ctx, MPC_PROF_NONLINEAR);
+  cudaStream_t st = ctx->st;
+  for (int s = 0; s < 2; ++s) {
+    CK(cudaMemsetAsync(p.a[s], 0, (size_t)6 * np[s] * 8, st));
+    CK(cudaMemsetAsync(p.b[s], 0, (size_t)6 * np[s] * 8, st));
+  }
+  // stage 0 operands: left = [a ; c], right = [b ; d] of every window
+  launch_window_gather(st, xs, B * C, H, W, np[0], p.a[0], p.b[0]);
+  g_launches += 1;
+  if ((rc = compare_select(ctx, call_id, 0, p.a[0], p.b[0], p.cs[0], p.o[0]))) return rc;
+  for (int c = 0; c < 6; ++c) {
+    CK(cudaMemcpyAsync(p.a[1] + c * np[1], p.o[0] + c * np[0], (size_t)nw * 8, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(p.b[1] + c * np[1], p.o[0] + c * np[0] + nw, (size_t)nw * 8, cudaMemcpyDeviceToDevice, st));
+  }
+  if ((rc = compare_select(ctx, call_id, 1, p.a[1], p.b[1], p.cs[1], p.o[1]))) return rc;
+  if ((rc = verify_nl(ctx, verify_id, p, trace))) return rc;
+  for (int c = 0; c < 6; ++c)
+    CK(cudaMemcpyAsync(out + c * nw, p.o[1] + c * np[1], (size_t)nw * 8, cudaMemcpyDeviceToDevice, st));
+  if ((rc = cuda_check(ctx, "maxpool2"))) return rc;
+  return nl_finish(ctx);
+}

@@ -30,7 +30,8 @@ enum Comp : u32 { C_R1 = 1, C_R2 = 2, C_M12 = 3, C_G1 = 4, C_TB1 = 5, C_TB2 = 6 
 // stream purposes
 enum Purpose : u32 {
   P_SHARE = 0x01, P_MULT = 0x02, P_INNER = 0x03, P_TRUNC_BITS = 0x04, P_TRUNC_P = 0x05,
-  P_TRUNC_Q = 0x06, P_VER_R = 0x10, P_VER_ZETA = 0x11, P_VER_H0 = 0x12, P_VER_H2 = 0x13,
+  P_TRUNC_Q = 0x06, P_DABIT = 0x07, P_EDABIT = 0x08, P_AND = 0x09, P_EDA_MULT = 0x0A,
+  P_EDA_INNER = 0x0B, P_DA_MULT1 = 0x0C, P_DA_MULT2 = 0x0D, P_NL_MULT = 0x0E, P_VER_R = 0x10, P_VER_ZETA = 0x11, P_VER_H0 = 0x12, P_VER_H2 = 0x13,
   P_VER_ALPHA = 0x14, P_VER_XA = 0x15, P_VER_DELTA = 0x16
 };
 __host__ __device__ inline u32 make_tag(u32 purpose, u32 comp) { return (purpose << 4) | comp; }

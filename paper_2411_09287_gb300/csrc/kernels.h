@@ -152,4 +152,59 @@ int launch_trunc_s_tc(cudaStream_t st, const u64* B1T, const u64* B2T, long long
                       unsigned* err, unsigned err_flag);
 void launch_fold_reduce_strided(cudaStream_t st, const u64* P, long long ld, int npairs, u64* out);
 
+// ---- non-linear layers: Boolean sharings, AND gates, GF(2^64) (nonlinear.cu) ------------------
+void launch_and_offline(cudaStream_t st, const u64* xs, const u64* ys, long long nw, Key k01, Key k02,
+                        u32 purpose, u64 obj, u64* zs, u64* g2_out);
+void launch_and_online(cudaStream_t st, const u64* xs, const u64* ys, long long nw, Key k01,
+                       u32 purpose, u64 obj, const u64* g2_in, u64* p1_out, u64* p2_out);
+void launch_xor_finish(cudaStream_t st, long long nw, const u64* p1_own, const u64* p1_in,
+                       const u64* p2_own, const u64* p2_in, u64* zs);
+void launch_bits_to_arith(cudaStream_t st, const u64* bits, long long n, int kind, u64* out);
+void launch_lin_apb_m2c(cudaStream_t st, long long n, const u64* a, const u64* b, const u64* c, u64* out);
+void launch_eda_inner_offline(cudaStream_t st, long long np, Key k01, Key k02, u64 obj, u64* zs,
+                              u64* g2_out);
+void launch_eda_inner_online(cudaStream_t st, const u64* mbits, const u64* rp, long long np, Key k01,
+                             u64 obj, const u64* g2_in, u64* p1_out, u64* p2_out);
+void launch_eda_compose(cudaStream_t st, const u64* mbits, const u64* rp, const u64* z, long long np,
+                        u64* ra);
+void launch_msb_leaves(cudaStream_t st, const u64* rbits, const u64* dplanes, long long W, u64* G,
+                       u64* P);
+void launch_msb_gather(cudaStream_t st, const u64* G, const u64* P, int C, int root, long long W,
+                       u64* X, u64* Y);
+void launch_msb_combine(cudaStream_t st, const u64* G, const u64* Z, int C, int root, long long W,
+                        u64* Gout, u64* Pout);
+void launch_msb_out(cudaStream_t st, const u64* rbits, const u64* Groot, const u64* d63, long long W,
+                    int negate, u64* out);
+void launch_bxor(cudaStream_t st, long long n6, const u64* a, const u64* b, u64* out);
+void launch_b2a_apply(cudaStream_t st, const u64* dbits, const u64* ra, long long n, u64* out);
+void launch_addsub(cudaStream_t st, long long n, const u64* a, const u64* b, int sub, u64* out);
+void launch_open_xor(cudaStream_t st, const u64* m, const u64* r1, const u64* r2_in, long long n,
+                     u64* out);
+void launch_eda_tran(cudaStream_t st, const u64* mbits, const u64* rp, long long np, const u64* pw,
+                     long long e0, u64* x2, u64* x4, u64* const* y_dev);
+void launch_gf_powers(cudaStream_t st, const u64* r, long long n, u64* out);
+void launch_gf_tran(cudaStream_t st, const u64* X, const u64* Y, const u64* Z, long long nw,
+                    const u64* pw, long long ld, u64* xo, u64* yo, u64* zsum);
+void launch_gf_party_sums(cudaStream_t st, const u64* const u[6], const u64* const v[6], long long D,
+                          long long stride, long long off, int fold, u64 fa, u64 fb, u64* S);
+void launch_gf_fold(cudaStream_t st, const u64* v, long long D, const u64* zeta, u64* out);
+void launch_gf_inner_finish(cudaStream_t st, const u64* S, Key k01, Key k02, u32 purpose, u64 obj,
+                            u64* h6);
+void launch_gf_random_shared(cudaStream_t st, Key k01, Key k02, Key k12, u32 purpose, u64 obj,
+                             u64* s6);
+void launch_gf_rec1(cudaStream_t st, const u64* s6, u64 xor_mask, u64* out, u32* status, u32 flag);
+void launch_gf_lagrange(cudaStream_t st, const u64* zeta, u64* coef);
+void launch_gf_combine_z(cudaStream_t st, const u64* coef, const u64* h0, const u64* h2, const u64* z,
+                         u64* zo);
+void launch_gf_mult_alpha(cudaStream_t st, const u64* const x[6], const u64* a6, long long D,
+                          long long ld, Key k01, Key k02, u64 obj, u64* xa);
+void launch_window_gather(cudaStream_t st, const u64* x, long long BC, long long H, long long W,
+                          long long np, u64* left, u64* right);
+void launch_gf_check_zero(cudaStream_t st, const u64* d, u32* status, u32 flag);
+// arithmetic Pi_Mult with the streams of `purpose` (prf_kernels.cu)
+void launch_mult_offline_p(cudaStream_t st, const u64* xs, const u64* ys, long long n, Key k01,
+                           Key k02, u32 purpose, u64 obj, u64* zs, u64* p0_out_g2);
+void launch_mult_online_p(cudaStream_t st, const u64* xs, const u64* ys, long long n, Key k01,
+                          u32 purpose, u64 obj, const u64* p2_in_g2, u64* p1_out, u64* p2_out);
+
 }  // namespace mpc3

@@ -277,6 +277,21 @@ void launch_mult_offline(cudaStream_t st, const u64* xs, const u64* ys, long lon
       make_tag(P_MULT, C_G1), obj, zs, p0_out_g2);
 }
 
+void launch_mult_offline_p(cudaStream_t st, const u64* xs, const u64* ys, long long n, Key k01,
+                           Key k02, u32 purpose, u64 obj, u64* zs, u64* p0_out_g2) {
+  if (n <= 0) return;
+  k_mult_offline<<<grid_for((n + 7) / 8), TPB, 0, st>>>(
+      xs, ys, n, k01, k02, make_tag(purpose, C_R1), make_tag(purpose, C_R2),
+      make_tag(purpose, C_G1), obj, zs, p0_out_g2);
+}
+
+void launch_mult_online_p(cudaStream_t st, const u64* xs, const u64* ys, long long n, Key k01,
+                          u32 purpose, u64 obj, const u64* p2_in_g2, u64* p1_out, u64* p2_out) {
+  if (n <= 0) return;
+  k_mult_online<<<grid_for((n + 7) / 8), TPB, 0, st>>>(xs, ys, n, k01, make_tag(purpose, C_G1),
+                                                       obj, p2_in_g2, p1_out, p2_out);
+}
+
 void launch_mult_online(cudaStream_t st, const u64* xs, const u64* ys, long long n, Key k01,
                         u64 obj, const u64* p2_in_g2, u64* p1_out, u64* p2_out) {
   if (n <= 0) return;

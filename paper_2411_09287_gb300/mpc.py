@@ -20,15 +20,18 @@ MPC_OK, MPC_ERR_ARG, MPC_ERR_SHAPE, MPC_ERR_WORKSPACE, MPC_ERR_CUDA = 0, 1, 2, 3
 MPC_ERR_TIMEOUT, MPC_ERR_VERIFY, MPC_ERR_ABORT, MPC_ERR_PENDING = 5, 6, 7, 8
 REDUCE_POINT_X, REDUCE_POINT_2 = 0, 1
 GEMM_U64, GEMM_LIMB_TC = 0, 1
-OP_SHARE, OP_MULT, OP_MATMUL, OP_VERIFY_MULT, OP_VERIFY_MATMUL, OP_RECONSTRUCT = range(6)
-SITES = {"GAMMA2": 0, "MZ1": 1, "MZ2": 2, "MX_COPY_P1": 3, "REC_MSG": 4, "HIGH_BIT": 5}
+(OP_SHARE, OP_MULT, OP_MATMUL, OP_VERIFY_MULT, OP_VERIFY_MATMUL, OP_RECONSTRUCT, OP_RELU,
+ OP_MAXPOOL2) = range(8)
+SITES = {"GAMMA2": 0, "MZ1": 1, "MZ2": 2, "MX_COPY_P1": 3, "REC_MSG": 4, "HIGH_BIT": 5,
+         "AND_GAMMA2": 6}
+TRACE_GF_ROUND = 13
 PHASES = ("offline", "online", "verify")
 PROTOS = ("share", "mult", "inner", "trunc", "rec", "verify")
 TRACE_ROUND = 832
 NOALLOC_MAX_N = 262144
 PROF_PHASES = ("share", "mult", "trunc_pairs", "gemm", "exchange", "verify_gemm", "trunc_setup",
                "trunc_s", "trunc_rounds", "trunc_materialize", "trunc_tail", "rec", "verify_mult",
-               "k_limb_gemm", "k_trunc_s")
+               "k_limb_gemm", "k_trunc_s", "k_gr_matmul", "k_gram", "k_gr_mul_rows", "nonlinear")
 ERR_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_WORKSPACE", 4: "ERR_CUDA",
              5: "ERR_TIMEOUT", 6: "ERR_VERIFY", 7: "ERR_ABORT", 8: "ERR_PENDING"}
 
@@ -180,6 +183,50 @@ class Context:
             self._check(rc)
         return rc, tr
 
+    @staticmethod
+    def nonlinear_R(np_list):
+        """Default rounds (R0, R1, R2) of a non-linear layer's three verification batches for
+        stage widths np_list (padded): arithmetic products, edaBit inner products, AND gates."""
+        nm = sum(67 * n for n in np_list)
+        ne = sum(np_list)
+        nand = sum(125 * n for n in np_list)
+        return default_R(nm), default_R(64 * ne), default_R(nand)
+
+    def _nl_trace(self, np_list, trace):
+        if not trace:
+            return None
+        R0, R1, R2 = self.nonlinear_R(np_list)
+        return self.zeros((R0 + 1) * TRACE_ROUND + (R1 + 1) * TRACE_ROUND + (R2 + 1) * TRACE_GF_ROUND)
+
+    def relu(self, call_id: int, verify_id: int, xs, n: int, trace: bool = False):
+        """ReLU layer with its verification (Sec. 4.3).  Returns (code, out sharing, trace)."""
+        out = self.shares(n)
+        np_ = 64 * ((n + 63) // 64)
+        tr = self._nl_trace([np_], trace)
+        wsb = self.ws_size(OP_RELU, n)
+        ws = self.workspace(wsb)
+        rc = self.lib.mpc_relu(self.h, call_id, verify_id, C.c_void_p(_ptr(xs)), n,
+                               C.c_void_p(_ptr(out)), C.c_void_p(_ptr(ws)), wsb, C.c_void_p(_ptr(tr)))
+        if rc not in (MPC_OK, MPC_ERR_VERIFY, MPC_ERR_ABORT):
+            self._check(rc)
+        return rc, out, tr
+
+    def maxpool2(self, call_id: int, verify_id: int, xs, shape, trace: bool = False):
+        """2x2 / stride-2 max-pool of a (B, C, H, W) sharing with its verification."""
+        B, Cc, H, W = shape
+        nw = B * Cc * (H // 2) * (W // 2)
+        out = self.shares(nw)
+        nps = [64 * ((2 * nw + 63) // 64), 64 * ((nw + 63) // 64)]
+        tr = self._nl_trace(nps, trace)
+        wsb = self.ws_size(OP_MAXPOOL2, B * Cc, H, W)
+        ws = self.workspace(wsb)
+        rc = self.lib.mpc_maxpool2(self.h, call_id, verify_id, C.c_void_p(_ptr(xs)), B, Cc, H, W,
+                                   C.c_void_p(_ptr(out)), C.c_void_p(_ptr(ws)), wsb,
+                                   C.c_void_p(_ptr(tr)))
+        if rc not in (MPC_OK, MPC_ERR_VERIFY, MPC_ERR_ABORT):
+            self._check(rc)
+        return rc, out, tr
+
     def verify_matmul(self, verify_id: int, xs, ws_, zpre, pq, M: int, N: int, K: int,
                       trunc_bits: int, matmul_call_id: int, R_main: int = -1, R_trunc: int = -1,
                       trace: bool = False):
@@ -241,11 +288,14 @@ class Context:
         self._check(self.lib.mpc_profile(self.h, 1 if enable else 0))
 
     def profile_read(self):
-        """{phase name: (milliseconds, intervals)} since the last read (waits for the stream)."""
+        """{phase name: (milliseconds, intervals, algorithmic u64 MACs)} since the last read
+        (waits for the stream)."""
         ms = (C.c_double * len(PROF_PHASES))()
         cnt = (C.c_uint64 * len(PROF_PHASES))()
-        self._check(self.lib.mpc_profile_read(self.h, ms, cnt))
-        return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(PROF_PHASES)}
+        work = (C.c_double * len(PROF_PHASES))()
+        self._check(self.lib.mpc_profile_read(self.h, ms, cnt, work))
+        return {name: (float(ms[i]), int(cnt[i]), float(work[i]))
+                for i, name in enumerate(PROF_PHASES)}
 
     def launch_count(self) -> int:
         return int(self.lib.mpc_launch_count())
