@@ -1,0 +1,57 @@
+"""Secure inference of a fully connected ReLU network through libmpc3 (config C2 shape:
+784-128-128-10 at 13 fractional bits).
+
+P0 owns the inputs and the weights (reading A13) and shares them (Pi_<.>).  Each layer is one
+Pi_Inner matrix product with Pi_Trunc^13 (Sec. 4.1-4.2) followed, except after the last layer, by
+a ReLU (Sec. 4.3); every layer is verified before the next one uses its output (reading A14), and
+only the logits are opened (Pi_Rec).  All protocol work runs in libmpc3's kernels; this module
+only sequences the calls.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import mpc as M
+
+
+def mlp_weights(sizes, seed_name: str, std: float = 0.05):
+    """Synthetic weights N(0, std^2) (numpy PCG64 from the named seed), one matrix per layer."""
+    from .workloads import rng
+    g = rng(seed_name)
+    return [g.normal(0.0, std, (sizes[i], sizes[i + 1])) for i in range(len(sizes) - 1)]
+
+
+def fp64_forward(x, weights):
+    """The plaintext model in float64 (ReLU after every layer but the last)."""
+    h = np.asarray(x, dtype=np.float64)
+    for i, w in enumerate(weights):
+        h = h @ w
+        if i + 1 < len(weights):
+            h = np.maximum(h, 0.0)
+    return h
+
+
+def secure_forward(ctx: "M.Context", x_fixed, w_fixed, k: int = 13, call_base: int = 1000,
+                   profile_phases=None):
+    """Secure forward pass.  x_fixed: (B, n0) u64 fixed-point; w_fixed: list of (n_i, n_{i+1}) u64
+    fixed-point matrices.  Returns the opened logits (u64, fixed-point with k bits)."""
+    B = x_fixed.shape[0]
+    cid = call_base
+    h = ctx.share_input(cid, np.ascontiguousarray(x_fixed).reshape(-1))
+    cid += 1
+    for i, w in enumerate(w_fixed):
+        n_in, n_out = w.shape
+        gw = ctx.share_input(cid, np.ascontiguousarray(w).reshape(-1))
+        zpre, zout, pq = ctx.matmul(cid + 1, h, gw, B, n_out, n_in, k)
+        rc, _ = ctx.verify_matmul(cid + 2, h, gw, zpre, pq, B, n_out, n_in, k, cid + 1)
+        if rc != M.MPC_OK:
+            raise M.MpcError(rc, f"layer {i}: verification rejected")
+        h = zout
+        cid += 3
+        if i + 1 < len(w_fixed):
+            rc, h, _ = ctx.relu(cid, cid + 1, h, B * n_out)
+            if rc != M.MPC_OK:
+                raise M.MpcError(rc, f"layer {i}: ReLU verification rejected")
+            cid += 2
+    n_last = w_fixed[-1].shape[1]
+    return ctx.reconstruct(h, B * n_last).reshape(B, n_last)

@@ -1,0 +1,39 @@
+"""Config C2 on the GPU: secure 784-128-128-10 MLP inference, batch 128, 13 fractional bits,
+weights N(0, 0.05^2), inputs U[0, 1).  Every layer's products, truncation pairs and ReLU are
+verified; the opened logits stay within 2^-8 of a float64 model evaluated on the decoded
+fixed-point inputs and weights (the protocol's error bound; reading A10)."""
+import hashlib
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mpc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2411_09287_gb300 import mpc as M
+    return M
+
+
+@pytest.mark.parametrize("path", [1, 0])
+def test_secure_mlp_logits_within_bound(mpc, path):
+    from paper_2411_09287_gb300 import secure_mlp as SM
+    from paper_2411_09287_gb300 import workloads
+    k = 13
+    sizes = [784, 128, 128, 10]
+    weights = SM.mlp_weights(sizes, "C2-weights")
+    x = workloads.rng("C2-inputs").uniform(0.0, 1.0, (128, 784))
+    xf = mpc.encode_fixed(x, k)
+    wf = [mpc.encode_fixed(w, k) for w in weights]
+    ctx = mpc.Context(hashlib.sha256(b"mpc3-config-C2").digest(), gemm_path=path)
+    logits = SM.secure_forward(ctx, xf, wf, k)
+    got = mpc.decode_fixed(logits, k)
+    ref = SM.fp64_forward(mpc.decode_fixed(xf, k), [mpc.decode_fixed(w, k) for w in wf])
+    err = np.abs(got - ref)
+    assert err.max() <= 2.0 ** -8, err.max()
+    # the secure network computes the same classification as the float64 model
+    assert np.mean(np.argmax(got, axis=1) == np.argmax(ref, axis=1)) > 0.95
