@@ -181,6 +181,14 @@ int mpc_reconstruct(mpc_ctx* ctx, const uint64_t* xs, int64_t n, uint64_t* out, 
 #define MPC_NOALLOC_MAX_N 262144
 int mpc_reconstruct_noalloc(mpc_ctx* ctx, const uint64_t* xs, int64_t n, uint64_t* out);
 
+/* Local rearrangement of a sharing (Sec. 2, linear homomorphic property: every party applies the
+ * same public map to each component it holds; no communication): out[k] = x[idx[k]], or 0 when
+ * idx[k] < 0 (zero padding).  Used for im2col views of convolutions and layout changes.
+ *   xs: 6 n_in words; idx: n_out device int64 indices (borrowed); out: 6 n_out words (written).
+ *   Indices >= n_in read as 0 (an out-of-range index is never dereferenced). */
+int mpc_gather(mpc_ctx* ctx, const uint64_t* xs, int64_t n_in, const int64_t* idx, int64_t n_out,
+               uint64_t* out);
+
 /* ---- non-linear layers (Sec. 4.3) -------------------------------------------------------------
  * ReLU(x) = x [x >= 0] and 2x2 max-pool, each one layer with its own verification (reading A14):
  *   - per compare-select stage: edaBits (Fig. edabits: 64 Pi_Mult + one dimension-64 Pi_Inner per

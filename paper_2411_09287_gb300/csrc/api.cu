@@ -2074,3 +2074,14 @@ int mpc_maxpool2(mpc_ctx* ctx, uint64_t call_id, uint64_t verify_id, const uint6
   if ((rc = cuda_check(ctx, "maxpool2"))) return rc;
   return nl_finish(ctx);
 }
+
+int mpc_gather(mpc_ctx* ctx, const uint64_t* xs, int64_t n_in, const int64_t* idx, int64_t n_out,
+               uint64_t* out) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (n_in <= 0 || n_out <= 0) return fail(ctx, MPC_ERR_SHAPE, "gather: bad size");
+  if (!xs || !idx || !out) return fail(ctx, MPC_ERR_ARG, "gather: bad argument");
+  launch_gather(ctx->st, xs, n_in, reinterpret_cast<const long long*>(idx), n_out, out);
+  g_launches += 1;
+  return cuda_check(ctx, "gather");
+}

@@ -198,6 +198,8 @@ void launch_gf_combine_z(cudaStream_t st, const u64* coef, const u64* h0, const 
                          u64* zo);
 void launch_gf_mult_alpha(cudaStream_t st, const u64* const x[6], const u64* a6, long long D,
                           long long ld, Key k01, Key k02, u64 obj, u64* xa);
+void launch_gather(cudaStream_t st, const u64* xs, long long n_in, const long long* idx,
+                   long long n_out, u64* out);
 void launch_window_gather(cudaStream_t st, const u64* x, long long BC, long long H, long long W,
                           long long np, u64* left, u64* right);
 void launch_gf_check_zero(cudaStream_t st, const u64* d, u32* status, u32 flag);

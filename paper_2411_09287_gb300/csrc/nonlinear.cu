@@ -519,6 +519,17 @@ __global__ void k_window_gather(const u64* __restrict__ x, long long BC, long lo
   }
 }
 
+// out[c][k] = idx[k] >= 0 ? xs[c][idx[k]] : 0 for the six components (a local linear map)
+__global__ void k_gather(const u64* __restrict__ xs, long long n_in, const long long* __restrict__ idx,
+                         long long n_out, u64* __restrict__ out) {
+  GRID_STRIDE(t, 6 * n_out) {
+    const int c = (int)(t / n_out);
+    const long long k = t % n_out;
+    const long long j = idx[k];
+    out[t] = (j >= 0 && j < n_in) ? xs[c * n_in + j] : 0ull;
+  }
+}
+
 }  // namespace
 
 // ---- launchers ------------------------------------------------------------------------------
@@ -658,6 +669,12 @@ void launch_eda_tran(cudaStream_t st, const u64* mbits, const u64* rp, long long
 void launch_window_gather(cudaStream_t st, const u64* x, long long BC, long long H, long long W,
                           long long np, u64* left, u64* right) {
   k_window_gather<<<grid_for(6 * BC * (H / 2) * (W / 2)), TPB, 0, st>>>(x, BC, H, W, np, left, right);
+}
+
+void launch_gather(cudaStream_t st, const u64* xs, long long n_in, const long long* idx,
+                   long long n_out, u64* out) {
+  if (n_out <= 0) return;
+  k_gather<<<grid_for(6 * n_out), TPB, 0, st>>>(xs, n_in, idx, n_out, out);
 }
 
 }  // namespace mpc3

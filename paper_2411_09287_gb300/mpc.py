@@ -183,6 +183,15 @@ class Context:
             self._check(rc)
         return rc, tr
 
+    def gather(self, xs, n_in: int, idx):
+        """out[k] = x[idx[k]] (0 where idx[k] < 0) on every share component; idx: numpy int64."""
+        idx_d = self.torch.from_numpy(np.ascontiguousarray(idx, dtype=np.int64)).to(self.device)
+        out = self.shares(idx_d.numel())
+        self._check(self.lib.mpc_gather(self.h, C.c_void_p(_ptr(xs)), n_in, C.c_void_p(_ptr(idx_d)),
+                                        idx_d.numel(), C.c_void_p(_ptr(out))))
+        self.sync()   # idx_d must outlive the enqueued gather
+        return out
+
     @staticmethod
     def nonlinear_R(np_list):
         """Default rounds (R0, R1, R2) of a non-linear layer's three verification batches for

@@ -1,0 +1,164 @@
+"""Secure CNN inference through libmpc3: convolutions as im2col share GEMMs (config C4, Net A:
+28x28x1 input, conv 5x5x16, 2x2 max-pool, conv 5x5x16, 2x2 max-pool, FC 256-100-10; reading A17).
+
+A convolution is a local im2col rearrangement of the shares (mpc_gather: every party applies the
+same index map to its components), one Pi_Inner matrix product with Pi_Trunc^k (Sec. 4.1: each
+output is one inner product) and its verification, and a local rearrangement back to NCHW.
+Max-pool and ReLU are the Sec. 4.3 layers; they commute (max of ReLUs = ReLU of the max), so
+every conv block pools first and applies ReLU to the 4x smaller result.  Non-linear layers are
+called per chunk of at most `nl_chunk` elements, each chunk with its own verification.  The index
+maps are integer plumbing computed here; all share arithmetic runs in libmpc3's kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import mpc as M
+
+
+# ---- index maps -------------------------------------------------------------------------------
+def im2col_index(B, C, H, W, kh, kw):
+    """Rows (b, i, j) of the valid output, columns (c, di, dj): index into the NCHW input."""
+    Ho, Wo = H - kh + 1, W - kw + 1
+    b, i, j, c, di, dj = np.meshgrid(np.arange(B), np.arange(Ho), np.arange(Wo), np.arange(C),
+                                     np.arange(kh), np.arange(kw), indexing="ij")
+    return (((b * C + c) * H + i + di) * W + j + dj).reshape(-1).astype(np.int64), Ho, Wo
+
+
+def rows_to_nchw_index(B, Co, Ho, Wo):
+    """Output element (b, oc, i, j) <- product row (b, i, j), column oc."""
+    b, oc, i, j = np.meshgrid(np.arange(B), np.arange(Co), np.arange(Ho), np.arange(Wo), indexing="ij")
+    return (((b * Ho + i) * Wo + j) * Co + oc).reshape(-1).astype(np.int64)
+
+
+def conv_weight_matrix(w):
+    """(C_out, C, kh, kw) -> (C kh kw, C_out) with rows (c, di, dj)."""
+    return np.ascontiguousarray(w.reshape(w.shape[0], -1).T)
+
+
+# ---- plaintext model ----------------------------------------------------------------------------
+def he_normal(g, shape, fan_in):
+    return g.normal(0.0, np.sqrt(2.0 / fan_in), shape)
+
+
+def net_a_params(seed_name: str):
+    from .workloads import rng
+    g = rng(seed_name)
+    return {"c1": he_normal(g, (16, 1, 5, 5), 25), "c2": he_normal(g, (16, 16, 5, 5), 400),
+            "f1": he_normal(g, (256, 100), 256), "f2": he_normal(g, (100, 10), 100)}
+
+
+def _conv_fp64(x, w):
+    B, C, H, W = x.shape
+    idx, Ho, Wo = im2col_index(B, C, H, W, w.shape[2], w.shape[3])
+    cols = x.reshape(-1)[idx].reshape(B * Ho * Wo, -1)
+    z = cols @ conv_weight_matrix(w)
+    return z.reshape(B, Ho, Wo, -1).transpose(0, 3, 1, 2)
+
+
+def _pool_fp64(x):
+    return np.maximum(np.maximum(x[:, :, 0::2, 0::2], x[:, :, 0::2, 1::2]),
+                      np.maximum(x[:, :, 1::2, 0::2], x[:, :, 1::2, 1::2]))
+
+
+def net_a_fp64(x, p):
+    h = np.maximum(_pool_fp64(_conv_fp64(x, p["c1"])), 0.0)
+    h = np.maximum(_pool_fp64(_conv_fp64(h, p["c2"])), 0.0)
+    h = h.reshape(h.shape[0], -1)
+    h = np.maximum(h @ p["f1"], 0.0)
+    return h @ p["f2"]
+
+
+# ---- secure model -------------------------------------------------------------------------------
+class _Ids:
+    def __init__(self, base):
+        self.v = base
+
+    def take(self, k=1):
+        v = self.v
+        self.v += k
+        return v
+
+
+def _matmul_verified(ctx, ids, h, gw, Mr, N, K, k):
+    c = ids.take(2)
+    zpre, zout, pq = ctx.matmul(c, h, gw, Mr, N, K, k)
+    rc, _ = ctx.verify_matmul(c + 1, h, gw, zpre, pq, Mr, N, K, k, c)
+    if rc != M.MPC_OK:
+        raise M.MpcError(rc, "matrix-product layer rejected")
+    return zout
+
+
+def _relu_chunked(ctx, ids, h, n, chunk):
+    if n <= chunk:
+        c = ids.take(2)
+        rc, out, _ = ctx.relu(c, c + 1, h, n)
+        if rc != M.MPC_OK:
+            raise M.MpcError(rc, "ReLU rejected")
+        return out
+    parts = []
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        part = ctx.gather(h, n, np.arange(s, e, dtype=np.int64))
+        parts.append((_relu_chunked(ctx, ids, part, e - s, chunk), e - s))
+    return _concat(ctx, parts)
+
+
+def _concat(ctx, parts):
+    n = sum(m for _, m in parts)
+    out = ctx.shares(n)
+    off = 0
+    for t, m in parts:
+        for c in range(6):
+            out[c * n + off: c * n + off + m].copy_(t[c * m:(c + 1) * m])
+        off += m
+    return out
+
+
+def _pool_chunked(ctx, ids, h, shape, chunk_images):
+    B, C, H, W = shape
+    per = C * H * W
+    parts = []
+    for b0 in range(0, B, chunk_images):
+        b1 = min(B, b0 + chunk_images)
+        part = ctx.gather(h, B * per, np.arange(b0 * per, b1 * per, dtype=np.int64))
+        c = ids.take(2)
+        rc, out, _ = ctx.maxpool2(c, c + 1, part, (b1 - b0, C, H, W))
+        if rc != M.MPC_OK:
+            raise M.MpcError(rc, "max-pool rejected")
+        parts.append((out, (b1 - b0) * C * (H // 2) * (W // 2)))
+    return _concat(ctx, parts)
+
+
+def _conv_block(ctx, ids, h, shape, w_fixed, k, pool_chunk, relu_chunk):
+    B, C, H, W = shape
+    Co, _, kh, kw = w_fixed.shape
+    idx, Ho, Wo = im2col_index(B, C, H, W, kh, kw)
+    cols = ctx.gather(h, B * C * H * W, idx)
+    gw = ctx.share_input(ids.take(), conv_weight_matrix(w_fixed).reshape(-1))
+    Mr, K = B * Ho * Wo, C * kh * kw
+    z = _matmul_verified(ctx, ids, cols, gw, Mr, Co, K, k)
+    z = ctx.gather(z, Mr * Co, rows_to_nchw_index(B, Co, Ho, Wo))
+    z = _pool_chunked(ctx, ids, z, (B, Co, Ho, Wo), pool_chunk)
+    n = B * Co * (Ho // 2) * (Wo // 2)
+    return _relu_chunked(ctx, ids, z, n, relu_chunk), (B, Co, Ho // 2, Wo // 2)
+
+
+def net_a_secure(ctx: "M.Context", x_fixed, p_fixed, k: int = 13, call_base: int = 5000,
+                 pool_chunk: int = 4, relu_chunk: int = 1 << 15):
+    """Secure Net A forward.  x_fixed: (B, 1, 28, 28) u64; p_fixed: the fixed-point parameters.
+    Returns the opened logits (B, 10), fixed-point with k bits."""
+    ids = _Ids(call_base)
+    B = x_fixed.shape[0]
+    h = ctx.share_input(ids.take(), np.ascontiguousarray(x_fixed).reshape(-1))
+    h, shape = _conv_block(ctx, ids, h, x_fixed.shape, p_fixed["c1"], k, pool_chunk, relu_chunk)
+    h, shape = _conv_block(ctx, ids, h, shape, p_fixed["c2"], k, pool_chunk, relu_chunk)
+    flat = int(np.prod(shape[1:]))
+    for name, last in (("f1", False), ("f2", True)):
+        w = p_fixed[name]
+        gw = ctx.share_input(ids.take(), np.ascontiguousarray(w).reshape(-1))
+        h = _matmul_verified(ctx, ids, h, gw, B, w.shape[1], flat, k)
+        flat = w.shape[1]
+        if not last:
+            h = _relu_chunked(ctx, ids, h, B * flat, relu_chunk)
+    return ctx.reconstruct(h, B * flat).reshape(B, flat)
