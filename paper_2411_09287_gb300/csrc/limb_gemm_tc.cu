@@ -860,7 +860,7 @@ int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nte
   CUtensorMap ma, mb;
   if (!make_map(&ma, Ap, M, Kp, TC_BM) || !make_map(&mb, Bp, N, Kp, TC_BN)) return -2;
   const size_t smem = (size_t)NSTAGE * STAGE + 1024;
-  cudaFuncSetAttribute(k_limb_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  set_max_dynamic_smem(reinterpret_cast<const void*>(k_limb_gemm_tc), (int)smem);
   dim3 grid((unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)((N + TC_BN - 1) / TC_BN));
   if (ev0) cudaEventRecord(ev0, st);
   k_limb_gemm_tc<<<grid, TC_THREADS, smem, st>>>(ma, mb, M, N, Kp, epi.out, epi.ldc, err, err_flag);
@@ -891,7 +891,7 @@ int gr_matmul_tc(cudaStream_t st, long long R, const u64* p0, const u64* p1, u64
   }
   const long long ntiles = (R + TC_BM - 1) / TC_BM;
   const unsigned grid = (unsigned)(ntiles < nsm ? ntiles : nsm);
-  cudaFuncSetAttribute(k_gr_matmul_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GM_SMEM);
+  set_max_dynamic_smem(reinterpret_cast<const void*>(k_gr_matmul_tc), (int)GM_SMEM);
   k_gr_matmul_tc<<<grid, GM_THREADS, GM_SMEM, st>>>(R, p0, p1, s1, lda, a_bits, Mmat, add0,
                                                      ld_add0 ? ld_add0 : ldc, out, ldc, err, err_flag);
   return 0;
@@ -912,7 +912,7 @@ int gram3_tc(cudaStream_t st, long long Dh, const u64* x, const u64* y, u64* P, 
   long long split = nsm / 2;
   if (split > nch) split = nch;
   if (split < 1) split = 1;
-  cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GR_SMEM);
+  set_max_dynamic_smem(reinterpret_cast<const void*>(k_gram_tc), (int)GR_SMEM);
   k_gram_tc<<<dim3((unsigned)split, 2), GM_THREADS, GR_SMEM, st>>>(Dh, x, y, P, err, err_flag);
   return 0;
 }

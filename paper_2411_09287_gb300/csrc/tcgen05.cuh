@@ -7,6 +7,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
+#include <set>
+#include <utility>
 
 namespace mpc3 {
 namespace tc {
@@ -133,6 +136,18 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, unsigned r[16]) {
 }
 __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+// Raise a kernel's dynamic shared-memory limit once per device (not on every launch, so that a
+// stream being captured into a CUDA graph sees launches only).
+inline void set_max_dynamic_smem(const void* kernel, int bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.insert({kernel, dev}).second)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link needed)

@@ -311,7 +311,7 @@ int launch_trunc_s_tc(cudaStream_t st, const u64* B1T, const u64* B2T, long long
           box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return -2;
-  cudaFuncSetAttribute(k_trunc_s_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S_SMEM);
+  set_max_dynamic_smem(reinterpret_cast<const void*>(k_trunc_s_tc), (int)S_SMEM);
   dim3 grid(4096 / S_TPAIRS, 1024 / S_TCOLS, (unsigned)nhi);
   k_trunc_s_tc<<<grid, S_THREADS, S_SMEM, st>>>(mb, B1T, B2T, Epad / 64, L, S_hi, err, err_flag);
   return 0;

@@ -63,7 +63,7 @@ class Context:
     """One three-party run: keys from `seed`, ledger, abort state; work on the current stream."""
 
     def __init__(self, seed: bytes, device: int = 0, reduce_mode: int = REDUCE_POINT_X,
-                 gemm_path: int = GEMM_U64, stream=None):
+                 gemm_path: int = GEMM_LIMB_TC, stream=None):
         torch = _torch()
         self.torch = torch
         self.lib = _lib.load()
@@ -85,6 +85,11 @@ class Context:
             raise MpcError(rc, "mpc_create failed")
         self.h = h
         self._ws = None
+
+    def set_stream(self, stream):
+        """Enqueue subsequent work on `stream` (a torch.cuda.Stream), e.g. a graph-capture stream."""
+        self._check(self.lib.mpc_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
+        self.stream = stream
 
     def close(self):
         if getattr(self, "h", None):

@@ -1,0 +1,217 @@
+"""Continuous-batching server for secure inference on one GPU (config C5 pattern).
+
+Requests (a batch of 1..256 inputs each) arrive over time.  A dispatcher admits arrived requests
+while the images in flight fit a device-memory budget, packs the admitted requests of one model
+into a single secure forward pass (up to `max_batch` images), and hands it to the first idle
+worker.  Each worker owns a libmpc3 context on its own CUDA stream, so packed batches of
+different workers run concurrently on the device (the library's calls release the GIL).  Logits
+are split back per request; latency is arrival -> opened logits.
+
+Every request's logits stay within the protocol's error bound of the float64 model whether the
+request runs alone or packed with others (the masks differ, the opened values agree within the
+truncation error).
+"""
+from __future__ import annotations
+
+import hashlib
+import queue
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import mpc as M
+from . import secure_cnn as SC
+from . import secure_mlp as SM
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float            # seconds after the start of the run
+    x: np.ndarray             # (b, ...) float inputs
+    logits: np.ndarray = None
+    done: float = None
+
+
+class Model:
+    """A fixed-point model with a secure forward pass and its float64 reference."""
+
+    def __init__(self, kind: str, k: int = 13):
+        self.kind, self.k = kind, k
+        if kind == "mlp":
+            w = SM.mlp_weights([784, 128, 128, 10], "C2-weights")
+            self.wf = [M.encode_fixed(a, k) for a in w]
+            self.in_shape = (784,)
+        elif kind == "neta":
+            p = SC.net_a_params("C4-netA-weights")
+            self.pf = {n: M.encode_fixed(a, k) for n, a in p.items()}
+            self.in_shape = (1, 28, 28)
+        else:
+            raise ValueError(kind)
+
+    def secure(self, ctx, x, call_base):
+        xf = M.encode_fixed(x, self.k)
+        if self.kind == "mlp":
+            out = SM.secure_forward(ctx, xf, self.wf, self.k, call_base)
+        else:
+            out = SC.net_a_secure(ctx, xf, self.pf, self.k, call_base)
+        return M.decode_fixed(out, self.k)
+
+    def fp64(self, x):
+        xd = M.decode_fixed(M.encode_fixed(x, self.k), self.k)
+        if self.kind == "mlp":
+            return SM.fp64_forward(xd, [M.decode_fixed(a, self.k) for a in self.wf])
+        return SC.net_a_fp64(xd, {n: M.decode_fixed(a, self.k) for n, a in self.pf.items()})
+
+    def bytes_per_image(self, ctx, b: int) -> float:
+        """Peak workspace of one packed batch of b images (the largest single call) / b."""
+        if self.kind == "mlp":
+            sizes = [784, 128, 128, 10]
+            ws = []
+            for i in range(3):
+                ws.append(ctx.ws_size(M.OP_MATMUL, b, sizes[i + 1], sizes[i], self.k))
+                ws.append(ctx.ws_size(M.OP_VERIFY_MATMUL, b, sizes[i + 1], sizes[i], self.k))
+                if i < 2:
+                    ws.append(ctx.ws_size(M.OP_RELU, b * sizes[i + 1]))
+        else:
+            ws = [ctx.ws_size(M.OP_VERIFY_MATMUL, b * 576, 16, 25, self.k),
+                  ctx.ws_size(M.OP_VERIFY_MATMUL, b * 64, 16, 400, self.k),
+                  ctx.ws_size(M.OP_MAXPOOL2, min(b, 4) * 16, 24, 24)]
+        return max(ws) / b
+
+
+class _Worker(threading.Thread):
+    def __init__(self, wid, server):
+        super().__init__(daemon=True)
+        import torch
+        self.wid, self.server = wid, server
+        self.stream = torch.cuda.Stream()
+        seed = hashlib.sha256(f"serving-worker-{wid}".encode()).digest()
+        self.ctx = M.Context(seed, gemm_path=server.gemm_path, stream=self.stream)
+        self.inbox = queue.Queue()
+        self.calls = 1 + wid * (1 << 36)          # disjoint call-id spaces per worker
+        self.busy = threading.Event()
+
+    def run(self):
+        import torch
+        while True:
+            job = self.inbox.get()
+            if job is None:
+                return
+            reqs = job
+            x = np.concatenate([r.x for r in reqs], axis=0)
+            with torch.cuda.stream(self.stream):
+                logits = self.server.model.secure(self.ctx, x, self.calls)
+            self.calls += 1 << 16
+            t = time.perf_counter() - self.server.t0
+            off = 0
+            for r in reqs:
+                b = r.x.shape[0]
+                r.logits = logits[off: off + b]
+                r.done = t
+                off += b
+            with self.server.lock:
+                self.server.in_flight -= x.shape[0]
+            self.busy.clear()
+            self.server.wake.set()
+
+
+class Server:
+    def __init__(self, model: Model, n_workers: int = 2, max_batch: int = 256,
+                 mem_budget_bytes: float = 64e9, gemm_path: int = M.GEMM_LIMB_TC):
+        self.model, self.max_batch, self.gemm_path = model, max_batch, gemm_path
+        self.workers = [_Worker(i, self) for i in range(n_workers)]
+        self.lock = threading.Lock()
+        self.wake = threading.Event()
+        self.in_flight = 0
+        per = model.bytes_per_image(self.workers[0].ctx, max_batch)
+        self.max_in_flight = max(1, int(mem_budget_bytes // max(per, 1.0)))
+        self.t0 = None
+
+    def serve(self, requests):
+        """Run all requests (sorted by arrival); returns them with logits and completion times."""
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        for w in self.workers:
+            w.start()
+        self.t0 = time.perf_counter()
+        pending = []
+        i = 0
+        while i < len(reqs) or pending:
+            now = time.perf_counter() - self.t0
+            while i < len(reqs) and reqs[i].arrival <= now:
+                pending.append(reqs[i])
+                i += 1
+            idle = [w for w in self.workers if not w.busy.is_set()]
+            if pending and idle:
+                pack, n = [], 0
+                with self.lock:
+                    room = self.max_in_flight - self.in_flight
+                while pending and n + pending[0].x.shape[0] <= min(self.max_batch, room):
+                    r = pending.pop(0)
+                    pack.append(r)
+                    n += r.x.shape[0]
+                if pack:
+                    with self.lock:
+                        self.in_flight += n
+                    w = idle[0]
+                    w.busy.set()
+                    w.inbox.put(pack)
+                    continue
+            # sleep until the next arrival or a worker finishes
+            nxt = reqs[i].arrival - now if i < len(reqs) else 0.05
+            self.wake.wait(timeout=max(0.0005, min(nxt, 0.05)))
+            self.wake.clear()
+        for w in self.workers:
+            while w.busy.is_set():
+                time.sleep(0.001)
+            w.inbox.put(None)
+        for w in self.workers:
+            w.join()
+        return reqs
+
+    @staticmethod
+    def stats(reqs):
+        lat = np.array([r.done - r.arrival for r in reqs])
+        imgs = sum(r.x.shape[0] for r in reqs)
+        span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
+        return {"requests": len(reqs), "images": int(imgs), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "images_per_s": imgs / span}
+
+
+def poisson_requests(model: Model, n: int, rate: float, max_b: int, seed: str):
+    from .workloads import rng
+    g = rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += g.exponential(1.0 / rate)
+        b = int(g.integers(1, max_b + 1))
+        out.append(Request(i, t, g.uniform(0.0, 1.0, (b,) + model.in_shape)))
+    return out
+
+
+def main():
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="secure-inference serving run")
+    ap.add_argument("--model", choices=["mlp", "neta"], default="mlp")
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--requests", type=int, default=100)
+    ap.add_argument("--max-b", type=int, default=256)
+    ap.add_argument("--max-batch", type=int, default=256)
+    ap.add_argument("--workers", type=int, default=2)
+    a = ap.parse_args()
+    model = Model(a.model)
+    reqs = poisson_requests(model, a.requests, a.rate, a.max_b, f"C5-{a.model}-{a.rate}")
+    srv = Server(model, a.workers, a.max_batch)
+    out = srv.serve(reqs)
+    st = Server.stats(out)
+    err = max(float(np.max(np.abs(r.logits - model.fp64(r.x)))) for r in out)
+    st.update({"model": a.model, "rate": a.rate, "max_abs_err_vs_fp64": err})
+    print(json.dumps(st))
+
+
+if __name__ == "__main__":
+    main()
