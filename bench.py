@@ -181,8 +181,8 @@ NCU_TRAFFIC_E = 2 ** 20
 NCU_TRAFFIC = {   # bytes per step at E = 2^20 (profiles/traffic_verify_kernels_n1024.md)
     "k_trunc_s": 0.419e9,
     "k_limb_gemm": 0.485e9,
-    "k_gr_matmul": 8.257e9,
-    "k_gram": 2.308e9,
+    "k_gr_matmul": None,   # changed since the capture
+    "k_gram": None,
     "k_gr_mul_rows": 3.138e9,
 }
 ALU_NOTE = "peak derived: 152 SMs x 64 IMAD/clk x max SM clock; a u64 MAC is 3 IMAD"
@@ -191,8 +191,9 @@ ALU_NOTE = "peak derived: 152 SMs x 64 IMAD/clk x max SM clock; a u64 MAC is 3 I
 def rooflines(phases, steps, peaks, clk, M, N, K, E, gemm_path):
     """Roofline records of the dominant kernels: CUDA-event time of each kernel inside the step
     and the algorithmic u64 multiply-accumulates the library attributes to it.  Tensor kernels
-    count the digit products they must form (36 bf16 digit pairs per u64 MAC for the 8-bit
-    balanced digits, 16 e4m3 limbs per bit-times-u64 MAC for the S matrix), 2 FLOP each, against
+    count the digit products they form (36 f16 digit pairs per u64 MAC for the 8-bit balanced
+    digits, 8 where one operand is a bit; 16 e4m3 limbs per bit-times-u64 MAC for the S matrix;
+    the library reports the work in 36-pair units), 2 FLOP each, against
     the measured cuBLAS bf16 rate (sustained: they run inside a long step) or twice it for e4m3
     (the nominal fp8 : bf16 ratio).  CUDA-core kernels count 3 IMAD per u64 MAC."""
     bf16 = peaks.get("bf16_tflops_sustained")
@@ -220,7 +221,7 @@ def rooflines(phases, steps, peaks, clk, M, N, K, E, gemm_path):
         for k, what in (("k_limb_gemm", "limb-split products"), ("k_gr_matmul", "GR-matrix products"),
                         ("k_gram", "Gram sums")):
             rec(k, 2 * 36, bf16, "TFLOP/s", "tensor",
-                f"tcgen05 kind::f16 {what}, 36 bf16 digit pairs per MAC; peak = measured bf16 (sustained)")
+                f"tcgen05 kind::f16 {what}, 36 f16 digit pairs per MAC; peak = measured bf16 (sustained)")
         rec("k_gr_mul_rows", 3, alu, "Tops/s (int32 IMAD)", "alu", ALU_NOTE)
     else:
         rec("gemm", 3, alu, "Tops/s (int32 IMAD)", "alu", "u64 CUDA-core GEMM; " + ALU_NOTE,

@@ -1327,7 +1327,8 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
       for (int v = 0; v < 4; ++v) {
         g_launches += 1;
         {
-          Phase kp(ctx, MPC_PROF_K_GR_MATMUL, (double)E * 4096);
+          // A has digit plane 0 only: 8 of the 36 digit-pair products (work in 36-pair units)
+          Phase kp(ctx, MPC_PROF_K_GR_MATMUL, (double)E * 4096 * 8.0 / 36.0);
           if (gr_matmul_tc(st, E, bits[v], nullptr, 1, 1, 1, mats[v], nullptr, 0, outs[v], 64,
                            ctx->status, ST_TIMEOUT))
             return fail(ctx, MPC_ERR_CUDA, "verify_matmul: folded-vector product");

@@ -1,10 +1,10 @@
-// Exact Z_2^64 GEMM on the 5th-generation tensor cores (tcgen05, kind::f16 with bf16 inputs,
+// Exact Z_2^64 GEMM on the 5th-generation tensor cores (tcgen05, kind::f16 with f16 inputs,
 // f32 accumulators in tensor memory): the "limb tensor-core path" of the local products of
 // Pi_Inner (Fig. DPP, Sec. 4.1).
 //
 // Each u64 operand value is split into 8 balanced signed digits d_0..d_7 in [-128, 127] with
 // v = sum_i 2^(8i) d_i mod 2^64 (carry-propagating split; the carry out of d_7 vanishes mod 2^64).
-// bf16 holds every such digit exactly.  Only digit pairs with i + j < 8 contribute mod 2^64:
+// f16 holds every such digit exactly.  Only digit pairs with i + j < 8 contribute mod 2^64:
 //   C = sum_{s<8} 2^(8s) C_s,   C_s = sum_{i+j=s} A_i B_j      (36 digit-plane products).
 // Each C_s has its own TMEM accumulator (8 x 64 columns = all 512).  One K chunk is 32 deep, so
 // |C_s| <= 8 * 32 * 2^14 = 2^22 within a chunk: every f32 partial sum is an exact integer, and
@@ -25,6 +25,8 @@
 // Every mbarrier wait is bounded (clock64, about one second) and also gives up once another
 // warp has recorded a failure; a failure sets err_flag in *err, the CTA lets its TMA copies and
 // MMAs finish (bounded), frees its tensor memory and returns without writing its tile.
+#include <type_traits>
+
 #include "kernels.h"
 #include "tcgen05.cuh"
 
@@ -42,8 +44,8 @@ constexpr int NSTAGE = 2;
 constexpr int NDRAIN = 8;
 constexpr int TC_THREADS = (NDRAIN + 2) * 32;
 
-// Instruction descriptor, kind::f16: f32 accumulator, bf16 A and B, both K-major, M = 128, N = 64.
-constexpr unsigned IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TC_BN >> 3) << 17) |
+// Instruction descriptor, kind::f16: f32 accumulator, f16 A and B, both K-major, M = 128, N = 64.
+constexpr unsigned IDESC = (1u << 4) | ((unsigned)(TC_BN >> 3) << 17) |
                            ((unsigned)(TC_BM >> 4) << 24);
 
 template <int ACC>
@@ -73,7 +75,8 @@ __host__ __device__ constexpr int group_s(int G, int g) { return G == 0 ? (g < 2
 // All MMAs of one accumulator group for one K chunk, fully unrolled: a_desc / b_desc are the
 // descriptors of digit plane 0 of the stage; plane i is A_TILE (B_TILE) bytes further on, and
 // each k16 step advances 32 bytes inside the swizzled rows.
-template <int G>
+// With A0 set, A has digit plane 0 only (0/1 entries): C_s = A_0 B_s, one pair per accumulator.
+template <int G, bool A0 = false>
 __device__ __forceinline__ void issue_group(unsigned tmem, u64 a_desc, u64 b_desc) {
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
@@ -82,7 +85,7 @@ __device__ __forceinline__ void issue_group(unsigned tmem, u64 a_desc, u64 b_des
     for (int kk = 0; kk < TC_BK / 16; ++kk) {
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        if (i <= s) {
+        if (i <= s && (!A0 || i == 0)) {
           const u64 ad = a_desc + (u64)((i * A_TILE) >> 4) + (u64)(kk * 2);
           const u64 bd = b_desc + (u64)(((s - i) * B_TILE) >> 4) + (u64)(kk * 2);
           if (kk == 0 && i == 0) mma_f16<0>(tmem + (unsigned)acc_col(s), ad, bd);
@@ -272,32 +275,51 @@ __device__ __forceinline__ u64 load_opnd(const Opnd& o, long long r, long long c
   return v;
 }
 
-// 8 consecutive u64 values -> 8 digit planes of 8 bf16 each (one 16-byte unit per plane).
+// 8 consecutive u64 values -> 8 digit planes of 8 f16 each (one 16-byte unit per plane).
 // The balanced digits of v are the bytes of v + 0x8080808080808080 minus 128 (the digit set
-// [-128, 127] is a complete residue system, so this is the carry-propagating split); the bf16
-// of an integer d in [-128, 127] is the high half of the f32 (2^23 + 2^22 + d) - (2^23 + 2^22).
-__device__ __forceinline__ unsigned bf16_of_byte(unsigned byte) {   // bf16(byte - 128)
-  return __float_as_uint(__uint_as_float(0x4B400000u - 128u + byte) - 12582912.0f);
+// [-128, 127] is a complete residue system, so this is the carry-propagating split).  A byte b
+// placed under the f16 exponent byte 0x64 is the f16 of 1024 + b (the spacing of f16 values on
+// [1024, 2048) is 1), so one packed f16 subtraction of 1152 per pair of digits leaves b - 128
+// exactly.  Per pair of words and 32-bit half: four byte permutes place bytes (0, 2) and (1, 3)
+// of each word under the exponent byte, four more pair the two words along K, four subtractions.
+__device__ __forceinline__ unsigned f16x2_minus_1152(unsigned x) {
+  unsigned r;
+  asm("sub.rn.f16x2 %0, %1, %2;\n" : "=r"(r) : "r"(x), "r"(0x64806480u));
+  return r;
 }
 __device__ __forceinline__ void split8_store(const u64 v[8], unsigned char* plane0,
                                              long long plane_stride, int off) {
-  u64 w[8];
+  unsigned pk[8][4];   // [plane][k pair m]: f16 digits of words 2m (low half) and 2m + 1
 #pragma unroll
-  for (int q = 0; q < 8; ++q) w[q] = v[q] + 0x8080808080808080ull;
+  for (int m = 0; m < 4; ++m) {
+    const u64 a = v[2 * m] + 0x8080808080808080ull, b = v[2 * m + 1] + 0x8080808080808080ull;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    unsigned pk[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const unsigned lo = bf16_of_byte((unsigned)(w[2 * m] >> (8 * i)) & 0xFFu);
-      const unsigned hi = bf16_of_byte((unsigned)(w[2 * m + 1] >> (8 * i)) & 0xFFu);
-      pk[m] = __byte_perm(lo, hi, 0x7632);   // high halves: bf16(lo) | bf16(hi) << 16
+    for (int h = 0; h < 2; ++h) {
+      const unsigned xa = (unsigned)(a >> (32 * h)), xb = (unsigned)(b >> (32 * h));
+      const unsigned a02 = __byte_perm(xa, 0x64u, 0x4240), a13 = __byte_perm(xa, 0x64u, 0x4341);
+      const unsigned b02 = __byte_perm(xb, 0x64u, 0x4240), b13 = __byte_perm(xb, 0x64u, 0x4341);
+      pk[4 * h + 0][m] = f16x2_minus_1152(__byte_perm(a02, b02, 0x5410));
+      pk[4 * h + 2][m] = f16x2_minus_1152(__byte_perm(a02, b02, 0x7632));
+      pk[4 * h + 1][m] = f16x2_minus_1152(__byte_perm(a13, b13, 0x5410));
+      pk[4 * h + 3][m] = f16x2_minus_1152(__byte_perm(a13, b13, 0x7632));
     }
-    *reinterpret_cast<uint4*>(plane0 + i * plane_stride + off) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    *reinterpret_cast<uint4*>(plane0 + i * plane_stride + off) =
+        make_uint4(pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
+}
+// 8 bits (k = 0..7, bit k of `bits`) -> the 16-byte unit of digit plane 0 (f16 0 or 1); the
+// other planes of such an operand are zero.
+__device__ __forceinline__ uint4 bits_plane0(unsigned bits) {
+  unsigned pk[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+    pk[m] = ((bits >> (2 * m)) & 1u) * 0x3C00u + ((bits >> (2 * m + 1)) & 1u) * 0x3C000000u;
+  return make_uint4(pk[0], pk[1], pk[2], pk[3]);
 }
 
-// planes[i][row][k'] (bf16), row-major with pitch Kp; element (row, k') of the concatenated
+// planes[i][row][k'] (f16), row-major with pitch Kp; element (row, k') of the concatenated
 // operand: term t = k' / K, column k' mod K; values beyond nterms*K are zero.
 __global__ void k_split_digits(GemmTerm t0, GemmTerm t1, int nterms, int which /*0 A, 1 B*/,
                                long long R, long long K, long long Kp,
@@ -372,15 +394,20 @@ bool make_map(CUtensorMap* map, void* planes, long long rows, long long Kp, int 
 // Same digit scheme and accumulator groups as k_limb_gemm_tc; the differences:
 //   - persistent CTAs loop over 128-row tiles; K = 64 is two chunks of 32;
 //   - B = M^T is split into digit planes once per CTA and stays in shared memory (64 KB);
-//   - three producer warps load the A rows from global memory and split them into the swizzled
-//     digit planes directly (no digit-plane copy in HBM); the MMA issuer and the 8 drain warps
-//     are as before, the drain warps add add0 and store the tile.
-constexpr int GM_PROD = 3;
-constexpr int GM_THREADS = (NDRAIN + GM_PROD + 1) * 32;   // 416
+//   - three producer warps load the A rows from global memory (all of a chunk's loads issued
+//     before the first is used) and split them into the swizzled digit planes directly (no
+//     digit-plane copy in HBM); the MMA issuer is as before; eight drain warps (each 32 rows x 32
+//     columns) add add0 and store the tile;
+//   - a_bits mode (A = the bits of one word per row): A has digit plane 0 only, so the producers
+//     write that plane alone and the issuer runs the 8 pairs (0, s) instead of 36.
+constexpr int GM_NDRAIN = 8;                              // drain warps: 32 rows x GM_DC columns
+constexpr int GM_DC = 256 / GM_NDRAIN;                    // columns per drain warp (32)
+constexpr int GM_PROD = 3;                                // producer warps
+constexpr int GM_THREADS = (GM_NDRAIN + GM_PROD + 1) * 32;   // 384
 constexpr int GM_BCHUNK = 8 * B_TILE;                     // 32 KB: B planes of one K chunk
 constexpr size_t GM_SMEM = (size_t)2 * GM_BCHUNK + (size_t)NSTAGE * 8 * A_TILE + 1024;
 
-// byte offset of 16-byte unit u (8 bf16 along K) of row r inside a K-major 64-byte-swizzled tile
+// byte offset of 16-byte unit u (8 f16 along K) of row r inside a K-major 64-byte-swizzled tile
 __device__ __forceinline__ int sw64_off(int r, int u) {
   return (r >> 3) * 512 + (r & 7) * 64 + ((u ^ ((r >> 1) & 3)) << 4);
 }
@@ -418,7 +445,7 @@ k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ 
     }
     for (int g = 0; g < 2; ++g) {
       mbar_init(&accf_bar[g], 1);
-      mbar_init(&acce_bar[g], NDRAIN);
+      mbar_init(&acce_bar[g], GM_NDRAIN);
     }
     mbar_init(&done_bar, 1);
     abort_flag = 0;
@@ -435,9 +462,9 @@ k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ 
     atomicOr(err, err_flag);
   };
 
-  if (warp >= NDRAIN && warp < NDRAIN + GM_PROD) {
+  if (warp >= GM_NDRAIN && warp < GM_NDRAIN + GM_PROD) {
     // ---- producers: B planes once, then the A planes of every (tile, chunk) ----
-    const int pt = tid - NDRAIN * 32;   // 0 .. 32 GM_PROD - 1
+    const int pt = tid - GM_NDRAIN * 32;   // 0 .. 32 GM_PROD - 1
     for (int it = pt; it < 64 * 8; it += GM_PROD * 32) {   // (row c of M^T, unit of 8 k)
       const int c = it >> 3, k8 = it & 7;
       u64 v[8];
@@ -495,52 +522,63 @@ k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ 
         for (int q = 0; q < NIT; ++q) {
           const int item = pt + q * GM_PROD * 32;
           if (item < 512) {
-            const u64 sh = wd[q] >> (kc * 32 + (item & 3) * 8);
-            u64 v[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = (sh >> j) & 1ull;
-            split8_store(v, As, A_TILE, sw64_off(item >> 2, item & 3));
+            const unsigned by = (unsigned)(wd[q] >> (kc * 32 + (item & 3) * 8)) & 0xFFu;
+            *reinterpret_cast<uint4*>(As + sw64_off(item >> 2, item & 3)) = bits_plane0(by);
           }
         }
       } else {
+        // a round's loads are all issued before the first is used: one memory latency per
+        // round, one round per chunk (two when p1 doubles the loads)
+        auto round = [&](auto nq, auto q0c, auto with_p1) {
+          constexpr int NQ = decltype(nq)::value, Q0 = decltype(q0c)::value;
+          constexpr bool P1 = decltype(with_p1)::value;
+          u64 v[NQ][8], w[P1 ? NQ : 1][8];
 #pragma unroll
-      for (int q0 = 0; q0 < NIT; q0 += 2) {         // two items in flight per thread
-        u64 v[2][8];
+          for (int q = 0; q < NQ; ++q) {
+            const int item = pt + (Q0 + q) * GM_PROD * 32;   // 512 items: (row, unit of 8 k)
+            const long long row = tile * TC_BM + (item >> 2);
+            const bool in = item < 512 && row < R;
+            const long long off = row * lda + kc * 32 + (item & 3) * 8;
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int item = pt + (q0 + q) * GM_PROD * 32;   // 512 items: (row, unit of 8 k)
-          const int r = item >> 2, k8 = item & 3;
-          const long long row = tile * TC_BM + r;
-          const long long off = row * lda + kc * 32 + k8 * 8;
-#pragma unroll
-          for (int j = 0; j < 8; j += 2) {
-            if (item < 512 && row < R) {
-              const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(p0 + off + j);
+            for (int j = 0; j < 8; j += 2) {
+              const ulonglong2 a =
+                  in ? *reinterpret_cast<const ulonglong2*>(p0 + off + j) : make_ulonglong2(0, 0);
               v[q][j] = a.x;
               v[q][j + 1] = a.y;
-              if (p1) {
-                const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(p1 + off + j);
-                v[q][j] += s1 * b.x;
-                v[q][j + 1] += s1 * b.y;
+              if (P1) {
+                const ulonglong2 b =
+                    in ? *reinterpret_cast<const ulonglong2*>(p1 + off + j) : make_ulonglong2(0, 0);
+                w[P1 ? q : 0][j] = b.x;
+                w[P1 ? q : 0][j + 1] = b.y;
               }
-            } else {
-              v[q][j] = v[q][j + 1] = 0;
             }
           }
-        }
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int item = pt + (q0 + q) * GM_PROD * 32;
-          if (item < 512) split8_store(v[q], As, A_TILE, sw64_off(item >> 2, item & 3));
+          for (int q = 0; q < NQ; ++q) {
+            const int item = pt + (Q0 + q) * GM_PROD * 32;
+            if (P1) {
+#pragma unroll
+              for (int j = 0; j < 8; ++j) v[q][j] += s1 * w[P1 ? q : 0][j];
+            }
+            if (item < 512) split8_store(v[q], As, A_TILE, sw64_off(item >> 2, item & 3));
+          }
+        };
+        using I0 = std::integral_constant<int, 0>;
+        if (p1) {
+          constexpr int H = (NIT + 1) / 2;
+          round(std::integral_constant<int, H>(), I0(), std::true_type());
+          round(std::integral_constant<int, NIT - H>(), std::integral_constant<int, H>(),
+                std::true_type());
+        } else {
+          round(std::integral_constant<int, NIT>(), I0(), std::false_type());
         }
-      }
       }
       fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(&full_bar[st]);
     }
     if (!ok && lane == 0) fail();
-  } else if (warp == NDRAIN + GM_PROD) {
+  } else if (warp == GM_NDRAIN + GM_PROD) {
     // ---- MMA issuer ----
     if (lane == 0) {
       const u64 da0 = smem_desc(Asm, 64);
@@ -553,24 +591,26 @@ k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ 
         const u64 bd = db0 + (u64)(((int)(u & 1) * GM_BCHUNK) >> 4);
         if (u > 0 && !mbar_wait(&acce_bar[0], (unsigned)((u - 1) & 1), abort)) { fail(); break; }
         tc_fence_after();
-        issue_group<0>(tmem, ad, bd);
+        if (a_bits) issue_group<0, true>(tmem, ad, bd);
+        else issue_group<0>(tmem, ad, bd);
         mma_commit(&accf_bar[0]);
         if (u > 0 && !mbar_wait(&acce_bar[1], (unsigned)((u - 1) & 1), abort)) { fail(); break; }
         tc_fence_after();
-        issue_group<1>(tmem, ad, bd);
+        if (a_bits) issue_group<1, true>(tmem, ad, bd);
+        else issue_group<1>(tmem, ad, bd);
         mma_commit(&accf_bar[1]);
         mma_commit(&empty_bar[st]);
       }
       mma_commit(&done_bar);
       mbar_wait_plain(&done_bar, 0u);
     }
-  } else if (warp < NDRAIN) {
-    // ---- drain warps: rows 32 (w % 4) + lane, columns 32 (w / 4) .. +31 ----
+  } else if (warp < GM_NDRAIN) {
+    // ---- drain warps: rows 32 (w % 4) + lane, columns GM_DC (w / 4) .. +GM_DC-1 ----
     const int q4 = warp & 3, h = warp >> 2;
-    const unsigned tl = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)(h * 32);
-    u64 acc[32];
+    const unsigned tl = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)(h * GM_DC);
+    u64 acc[GM_DC];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = 0;
+    for (int c = 0; c < GM_DC; ++c) acc[c] = 0;
     bool ok = true;
     for (long long u = 0; u < nunits && ok; ++u) {
       const unsigned par = (unsigned)(u & 1);
@@ -582,7 +622,7 @@ k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ 
         const int s0 = g == 0 ? 0 : 2;
         const int s1d = g == 0 ? 6 : 4;
 #pragma unroll
-        for (int c16 = 0; c16 < 2; ++c16) {
+        for (int c16 = 0; c16 < GM_DC / 16; ++c16) {
           unsigned x0[16], x1[16];
           // pair (s0, s0 + 1): + ws (g = 0) or 2^16 ws (g = 1), ws sign-extended
           tmem_ld16(tl + (unsigned)(acc_col(s0) + c16 * 16), x0);
@@ -613,21 +653,23 @@ k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ 
         const long long r = tile * TC_BM + q4 * 32 + lane;
         const u64 corr = (u64)(2u * CHUNK_HI_BIAS) << 32;
         if (r < R) {
-          const u64* a0p = add0 ? add0 + r * ld_add0 + h * 32 : nullptr;
-          u64* o = out + r * ldc + h * 32;
+          const u64* a0p = add0 ? add0 + r * ld_add0 + h * GM_DC : nullptr;
+          u64* o = out + r * ldc + h * GM_DC;
 #pragma unroll
-          for (int c = 0; c < 32; c += 2) {
-            u64 x0 = acc[c] - corr, x1 = acc[c + 1] - corr;
-            if (a0p) {
-              const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(a0p + c);
-              x0 += a.x;
-              x1 += a.y;
-            }
-            *reinterpret_cast<ulonglong2*>(o + c) = make_ulonglong2(x0, x1);
+          for (int c0 = 0; c0 < GM_DC; c0 += 8) {   // 8 columns at a time (bounded live range)
+            ulonglong2 a[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              a[q] = a0p ? *reinterpret_cast<const ulonglong2*>(a0p + c0 + 2 * q) : make_ulonglong2(0, 0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              *reinterpret_cast<ulonglong2*>(o + c0 + 2 * q) =
+                  make_ulonglong2(acc[c0 + 2 * q] - corr + a[q].x, acc[c0 + 2 * q + 1] - corr + a[q].y);
+            asm volatile("" ::: "memory");
           }
         }
 #pragma unroll
-        for (int c = 0; c < 32; ++c) acc[c] = 0;
+        for (int c = 0; c < GM_DC; ++c) acc[c] = 0;
       }
     }
     if (!ok && lane == 0) fail();
@@ -676,7 +718,7 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
     }
     for (int g = 0; g < 2; ++g) {
       mbar_init(&accf_bar[g], 1);
-      mbar_init(&acce_bar[g], NDRAIN);
+      mbar_init(&acce_bar[g], GM_NDRAIN);
     }
     mbar_init(&done_bar, 1);
     abort_flag = 0;
@@ -693,10 +735,10 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
     atomicOr(err, err_flag);
   };
 
-  if (warp >= NDRAIN && warp < NDRAIN + GM_PROD) {
+  if (warp >= GM_NDRAIN && warp < GM_NDRAIN + GM_PROD) {
     // ---- producers: 512 A items (x rows a = item % 128, 8 pairs k8 = item / 128) and 256 B
     // items (y rows b = item % 64, k8 = item / 64), lanes on consecutive coefficients ----
-    const int pt = tid - NDRAIN * 32;
+    const int pt = tid - GM_NDRAIN * 32;
     constexpr int NITEM = 768;
     constexpr int NIT = (NITEM + GM_PROD * 32 - 1) / (GM_PROD * 32);
     bool ok = true;
@@ -719,10 +761,10 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
       unsigned char* As = base + st * STAGE;
       unsigned char* Bs = As + 8 * A_TILE;
 #pragma unroll
-      for (int q0 = 0; q0 < NIT; q0 += 2) {
-        u64 v[2][8];
+      for (int q0 = 0; q0 < NIT; q0 += 4) {         // four items' loads in flight per thread
+        u64 v[4][8];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < 4; ++q) {
           const int item = pt + (q0 + q) * GM_PROD * 32;
           const bool isA = item < 512;
           const int it = isA ? item : item - 512;
@@ -737,7 +779,7 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
           }
         }
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < 4; ++q) {
           const int item = pt + (q0 + q) * GM_PROD * 32;
           if (item < 512) split8_store(v[q], As, A_TILE, sw64_off(item & 127, item >> 7));
           else if (item < NITEM) split8_store(v[q], Bs, B_TILE, sw64_off((item - 512) & 63, (item - 512) >> 6));
@@ -748,7 +790,7 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
       if (lane == 0) mbar_arrive(&full_bar[st]);
     }
     if (!ok && lane == 0) fail();
-  } else if (warp == NDRAIN + GM_PROD) {
+  } else if (warp == GM_NDRAIN + GM_PROD) {
     // ---- MMA issuer ----
     if (lane == 0) {
       const u64 d0 = smem_desc(base, 64);
@@ -771,13 +813,13 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
       mma_commit(&done_bar);
       mbar_wait_plain(&done_bar, 0u);
     }
-  } else if (warp < NDRAIN) {
-    // ---- drain warps: tile rows 32 (w % 4) + lane, columns 32 (w / 4) .. +31 ----
+  } else if (warp < GM_NDRAIN) {
+    // ---- drain warps: tile rows 32 (w % 4) + lane, columns GM_DC (w / 4) .. +GM_DC-1 ----
     const int q4 = warp & 3, h = warp >> 2;
-    const unsigned tl = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)(h * 32);
-    u64 acc[32];
+    const unsigned tl = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)(h * GM_DC);
+    u64 acc[GM_DC];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = 0;
+    for (int c = 0; c < GM_DC; ++c) acc[c] = 0;
     bool ok = true;
     for (long long u = 0; u < nunits && ok; ++u) {
       const unsigned pu = (unsigned)(u & 1);
@@ -789,7 +831,7 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
         const int s0 = g == 0 ? 0 : 2;
         const int s1d = g == 0 ? 6 : 4;
 #pragma unroll
-        for (int c16 = 0; c16 < 2; ++c16) {
+        for (int c16 = 0; c16 < GM_DC / 16; ++c16) {
           unsigned x0[16], x1[16];
           tmem_ld16(tl + (unsigned)(acc_col(s0) + c16 * 16), x0);
           tmem_ld16(tl + (unsigned)(acc_col(s0 + 1) + c16 * 16), x1);
@@ -819,9 +861,9 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
       const int a = q4 * 32 + lane;                // tile row: x parity a / 64, coefficient a % 64
       const int xpar = a >> 6;
       // (x parity, y parity) -> P block: (0,0) -> 0, (1,1) -> 1, mixed -> 2
-      u64* dst = P + (xpar == par ? xpar : 2) * 4096 + (a & 63) * 64 + h * 32;
+      u64* dst = P + (xpar == par ? xpar : 2) * 4096 + (a & 63) * 64 + h * GM_DC;
 #pragma unroll
-      for (int c = 0; c < 32; ++c)
+      for (int c = 0; c < GM_DC; ++c)
         atomicAdd(reinterpret_cast<unsigned long long*>(dst + c), (unsigned long long)(acc[c] - corr));
     } else if (!ok && lane == 0) {
       fail();
