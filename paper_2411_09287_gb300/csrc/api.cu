@@ -59,6 +59,8 @@ inline void counted(int k, F f, A... a) {
 #define launch_trunc_update_vw(...) counted(1, mpc3::launch_trunc_update_vw, __VA_ARGS__)
 #define launch_trunc_materialize(...) counted(1, mpc3::launch_trunc_materialize, __VA_ARGS__)
 #define launch_gr_mul_rows(...) counted(1, mpc3::launch_gr_mul_rows, __VA_ARGS__)
+#define launch_gr_mulmat_batch(...) counted(1, mpc3::launch_gr_mulmat_batch, __VA_ARGS__)
+#define launch_word_transpose(...) counted(1, mpc3::launch_word_transpose, __VA_ARGS__)
 #define launch_scalar_gr_sum(...) counted(1, mpc3::launch_scalar_gr_sum, __VA_ARGS__)
 #define launch_gr_rec1(...) counted(1, mpc3::launch_gr_rec1, __VA_ARGS__)
 #define launch_gr_inner_finish_all(...) counted(1, mpc3::launch_gr_inner_finish_all, __VA_ARGS__)
@@ -781,6 +783,11 @@ struct VMatPlan {
   u64 *b1, *b2, *Rtab, *S, *Zpq, *V, *W, *hsum, *S3, *zt, *S_hi, *Pst, *Thi, *Mhi;
   u64 *B1T, *B2T;   // bit-transposed b1, b2: [j][e / 64]
   unsigned char* TL8;
+  // tensor-core materialisation with r^(2e) = r^(2 Lm e_hi) r^(2 e_lo), e = e_hi Lm + e_lo:
+  // Tm[e_lo][j] = r^(2 e_lo) (-V_j), Bm[e_hi] = M(r^(2 Lm e_hi)), Vm[j] = M(-V_j), bT = b1 in
+  // (e_lo, e_hi) order (nhm x Lm view transposed)
+  long long Lm = 0, nhm = 0;
+  u64 *Tm = nullptr, *Bm = nullptr, *Vm = nullptr, *bT = nullptr;
   Dense dt;
   IVBuf ivt;
   void* tcs = nullptr;   // tensor-core digit planes (limb path only)
@@ -830,6 +837,16 @@ VMatPlan plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R
     p.hsum = a.take<u64>(128);
     p.S3 = a.take<u64>(2 * 192);
     p.zt = a.take<u64>(2 * 384);
+    if (tc && p.kd == 6 && E >= 65536) {
+      long long sq = 1;
+      while (sq * sq < E) ++sq;
+      p.Lm = (sq + 127) / 128 * 128;
+      p.nhm = ((E + p.Lm - 1) / p.Lm + 127) / 128 * 128;
+      p.Tm = a.take<u64>(p.Lm * 4096);
+      p.Bm = a.take<u64>((E + p.Lm - 1) / p.Lm * 4096);
+      p.Vm = a.take<u64>(64 * 4096);
+      p.bT = a.take<u64>(p.nhm * p.Lm);
+    }
     const bool xc[6] = {true, false, false, true, false, false};
     const bool yc[6] = {false, true, false, false, false, true};
     p.dt = plan_dense(a, p.Dt, xc, yc);
@@ -1324,15 +1341,67 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
       const u64* bits[4] = {p.b1, p.b1, p.b2, p.b2};
       const u64* mats[4] = {nV, nV, nW, nW};
       u64* outs[4] = {tx.c[0], tx.c[3], ty.c[1], ty.c[5]};
-      for (int v = 0; v < 4; ++v) {
+      auto grmm = [&](const GrMMArgs& g, double work) {
         g_launches += 1;
-        {
-          // A has digit plane 0 only: 8 of the 36 digit-pair products (work in 36-pair units)
-          Phase kp(ctx, MPC_PROF_K_GR_MATMUL, (double)E * 4096 * 8.0 / 36.0);
-          if (gr_matmul_tc(st, E, bits[v], nullptr, 1, 1, 1, mats[v], nullptr, 0, outs[v], 64,
-                           ctx->status, ST_TIMEOUT))
+        Phase kp(ctx, MPC_PROF_K_GR_MATMUL, work);
+        return gr_matmul_tc_ex(st, g, ctx->status, ST_TIMEOUT);
+      };
+      if (p.Lm) {
+        // x_e = r^(2 Lm e_hi) (sum_j b_{e,j} r^(2 e_lo) (-V_j)): the per-row factor r^(2e) split
+        // into two grouped GR matrix products on the tensor cores.
+        const long long Lm = p.Lm, nhm = p.nhm, nB = (E + Lm - 1) / Lm;
+        launch_gr_mulmat_batch(st, 64, nV, 64, p.Vm);
+        launch_gr_mulmat_batch(st, nB, p.Rtab, Lm * 64, p.Bm);
+        launch_word_transpose(st, nhm, Lm, E, p.b1, p.bT);
+        GrMMArgs g{};
+        // Tm: rows sigma = j Lm + e_lo read r^(2 e_lo) and use matrix j; written at [e_lo][j]
+        g.R = 64 * Lm;
+        g.p0 = p.Rtab;
+        g.in = GrRowMap{Lm, 64, 0};
+        g.Mmat = p.Vm;
+        g.mrows = Lm;
+        g.out = p.Tm;
+        g.om = GrRowMap{Lm, 4096, 64};
+        if (grmm(g, 64.0 * Lm * 4096)) return fail(ctx, MPC_ERR_CUDA, "verify_matmul: r^(2e) V table");
+        for (int v = 0; v < 2; ++v) {
+          // rows rho = e_lo nhm + e_hi (bits b_e), matrix Tm[e_lo], result at row e
+          GrMMArgs ga{};
+          ga.R = nhm * Lm;
+          ga.p0 = p.bT;
+          ga.in = GrRowMap{0, 1, 0};
+          ga.a_bits = 1;
+          ga.Mmat = p.Tm;
+          ga.mrows = nhm;
+          ga.out = outs[v];
+          ga.om = GrRowMap{nhm, Lm * 64, 64};
+          ga.out_lim = E * 64;
+          if (grmm(ga, (double)nhm * Lm * 4096 * 8.0 / 36.0))
             return fail(ctx, MPC_ERR_CUDA, "verify_matmul: folded-vector product");
+          // in place: rows e, matrix M(r^(2 Lm e_hi)) for e_hi = e / Lm
+          GrMMArgs gb{};
+          gb.R = E;
+          gb.p0 = outs[v];
+          gb.in = GrRowMap{0, 64, 0};
+          gb.Mmat = p.Bm;
+          gb.mrows = Lm;
+          gb.out = outs[v];
+          gb.om = GrRowMap{0, 64, 0};
+          if (grmm(gb, (double)E * 4096))
+            return fail(ctx, MPC_ERR_CUDA, "verify_matmul: r^(2e) factor");
         }
+      }
+      for (int v = p.Lm ? 2 : 0; v < 4; ++v) {
+        GrMMArgs g{};
+        g.R = E;
+        g.p0 = bits[v];
+        g.in = GrRowMap{0, 1, 0};
+        g.a_bits = 1;
+        g.Mmat = mats[v];
+        g.out = outs[v];
+        g.om = GrRowMap{0, 64, 0};
+        // A has digit plane 0 only: 8 of the 36 digit-pair products (work in 36-pair units)
+        if (grmm(g, (double)E * 4096 * 8.0 / 36.0))
+          return fail(ctx, MPC_ERR_CUDA, "verify_matmul: folded-vector product");
         if (v < 2) {
           Phase kp(ctx, MPC_PROF_K_GR_MUL_ROWS, (double)E * 4096);
           launch_gr_mul_rows(st, E, outs[v], p.Rtab, outs[v]);

@@ -99,6 +99,33 @@ __global__ void k_gr_mulmat2(const u64* a, const u64* b, u64* M) {
   for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) M[blockIdx.x * 4096 + i] = buf[i];
 }
 
+// M[i] = multiplication matrix of the GR element src + i * stride, for i < n (one block each).
+__global__ void k_gr_mulmat_batch(const u64* src, long long stride, u64* M) {
+  __shared__ u64 buf[64 * 64];
+  gr_mulmat_block(src + blockIdx.x * stride, buf);
+  u64* dst = M + (long long)blockIdx.x * 4096;
+  for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) dst[i] = buf[i];
+}
+
+// out[c * rows + r] = in[r * cols + c] for r < rows, c < cols; entries with r * cols + c >= n
+// read as 0 (32 x 32 tiles through shared memory).
+__global__ void k_word_transpose(long long rows, long long cols, long long n, const u64* in,
+                                 u64* out) {
+  __shared__ u64 tile[32][33];
+  const long long r0 = (long long)blockIdx.y * 32, c0 = (long long)blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads: 8 rows per pass
+  for (int k = ty; k < 32; k += 8) {
+    const long long r = r0 + k, c = c0 + tx;
+    const long long i = r * cols + c;
+    tile[k][tx] = (r < rows && c < cols && i < n) ? in[i] : 0ull;
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const long long c = c0 + k, r = r0 + tx;
+    if (c < cols && r < rows) out[c * rows + r] = tile[tx][k];
+  }
+}
+
 // ---- inverses of the interpolation constants (Pi_Reduce with points 0, 1, x) ------------------
 __device__ u64 gf2_64_mul(u64 a, u64 b) {   // GF(2)[x]/(x^64 + x^4 + x^3 + x + 1)
   u64 r = 0;
@@ -694,6 +721,19 @@ void launch_gr_lincomb(cudaStream_t st, const u64* ca, const u64* a, const u64* 
 
 void launch_gr_mulmat2(cudaStream_t st, const u64* a, const u64* b, u64* M) {
   k_gr_mulmat2<<<b ? 2 : 1, 64, 0, st>>>(a, b, M);
+}
+
+void launch_gr_mulmat_batch(cudaStream_t st, long long n, const u64* src, long long stride,
+                            u64* M) {
+  if (n <= 0) return;
+  k_gr_mulmat_batch<<<(unsigned)n, 64, 0, st>>>(src, stride, M);
+}
+
+void launch_word_transpose(cudaStream_t st, long long rows, long long cols, long long n,
+                           const u64* in, u64* out) {
+  if (rows <= 0 || cols <= 0) return;
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+  k_word_transpose<<<grid, 256, 0, st>>>(rows, cols, n, in, out);
 }
 
 void launch_gr_inverses(cudaStream_t st, u64* out) { k_gr_inverses<<<1, 64, 0, st>>>(out); }

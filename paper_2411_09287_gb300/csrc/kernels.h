@@ -64,6 +64,32 @@ int gr_matmul_tc(cudaStream_t st, long long R, const u64* p0, const u64* p1, u64
                  int a_bits, const u64* Mmat, const u64* add0, long long ld_add0, u64* out,
                  long long ldc, unsigned* err, unsigned err_flag);
 
+// Row map of a GR matrix product: logical row rho sits at word offset (rho % q) s1 + (rho / q) s2
+// (q = 0: rho s1).  q must be a multiple of 128.
+struct GrRowMap {
+  long long q, s1, s2;
+};
+// The general form: rows rho < R, A row rho at p0 + in(rho) (+ s1 p1 + in(rho)), or with a_bits
+// the word p0[in(rho)]; matrix rho / mrows at Mmat + 4096 (rho / mrows) (mrows = 0: one matrix,
+// else a multiple of 128); out row rho at out + om(rho), written only when om(rho) < out_lim
+// (0: no limit); add0 row rho at add0 + rho ld_add0 (0: 64).
+struct GrMMArgs {
+  long long R;
+  const u64* p0;
+  const u64* p1;
+  u64 s1;
+  GrRowMap in;
+  int a_bits;
+  const u64* Mmat;
+  long long mrows;
+  const u64* add0;
+  long long ld_add0;
+  u64* out;
+  GrRowMap om;
+  long long out_lim;
+};
+int gr_matmul_tc_ex(cudaStream_t st, const GrMMArgs& a, unsigned* err, unsigned err_flag);
+
 // P[0..2] (3 x 4096 words, accumulated mod 2^64) += the Gram sums G(x_e, y_e), G(x_o, y_o),
 // G(x_e, y_o) + G(x_o, y_e) over the Dh element pairs (x_{2i}, x_{2i+1}) of x and y (rows of 64
 // words, contiguous).  Exact, on the tensor cores; returns -1 for misaligned inputs.
@@ -129,6 +155,13 @@ void launch_scalar_gr_sum(cudaStream_t st, long long n, const u64* A, long long 
                           const u64* R, u64* out);
 // out[e] = a[e] * b[e] (GR products of n row pairs; out may alias a or b)
 void launch_gr_mul_rows(cudaStream_t st, long long n, const u64* a, const u64* b, u64* out);
+// M + 4096 i = multiplication matrix (M[b][c] = coefficient c of g x^b) of g = src + i stride,
+// i < n.
+void launch_gr_mulmat_batch(cudaStream_t st, long long n, const u64* src, long long stride,
+                            u64* M);
+// out (cols x rows) = transpose of in viewed as rows x cols; source indices >= n read as 0.
+void launch_word_transpose(cudaStream_t st, long long rows, long long cols, long long n,
+                           const u64* in, u64* out);
 void launch_trunc_materialize(cudaStream_t st, long long E, const u64* words, const u64* VW,
                               const u64* R, int kd, u64* out);
 void launch_gr_rec1(cudaStream_t st, const u64* s6, u64 xor_mask, int xor_idx, u64* out,

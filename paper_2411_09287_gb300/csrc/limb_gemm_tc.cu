@@ -25,6 +25,7 @@
 // Every mbarrier wait is bounded (clock64, about one second) and also gives up once another
 // warp has recorded a failure; a failure sets err_flag in *err, the CTA lets its TMA copies and
 // MMAs finish (bounded), frees its tensor memory and returns without writing its tile.
+#include <climits>
 #include <type_traits>
 
 #include "kernels.h"
@@ -393,7 +394,12 @@ bool make_map(CUtensorMap* map, void* planes, long long rows, long long Kp, int 
 // (row stride lda) and M a 64 x 64 u64 matrix (the multiplication matrix of a GR element).
 // Same digit scheme and accumulator groups as k_limb_gemm_tc; the differences:
 //   - persistent CTAs loop over 128-row tiles; K = 64 is two chunks of 32;
-//   - B = M^T is split into digit planes once per CTA and stays in shared memory (64 KB);
+//   - B = M^T is split into digit planes in shared memory (64 KB) when a CTA's tile range enters
+//     a new matrix group (rows rho of group rho / mrows use matrix rho / mrows; one group by
+//     default), after the MMAs of the previous tile have finished reading the old planes;
+//   - rows go through row maps: A row rho is read at p0 + map_in(rho) and its result written at
+//     out + map_out(rho) (map(rho) = (rho % q) s1 + (rho / q) s2 words), which lets one launch
+//     gather strided rows or scatter a transposed order;
 //   - three producer warps load the A rows from global memory (all of a chunk's loads issued
 //     before the first is used) and split them into the swizzled digit planes directly (no
 //     digit-plane copy in HBM); the MMA issuer is as before; eight drain warps (each 32 rows x 32
@@ -416,11 +422,12 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
 
+__device__ __forceinline__ long long rowmap(const GrRowMap& m, long long rho) {
+  return m.q ? (rho % m.q) * m.s1 + (rho / m.q) * m.s2 : rho * m.s1;
+}
+
 __global__ void __launch_bounds__(GM_THREADS, 1)
-k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ p1, u64 s1,
-               long long lda, int a_bits, const u64* __restrict__ Mmat,
-               const u64* __restrict__ add0, long long ld_add0, u64* __restrict__ out,
-               long long ldc, unsigned* __restrict__ err, unsigned err_flag) {
+k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) {
   extern __shared__ unsigned char dsm[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
@@ -434,9 +441,21 @@ k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ 
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
+  const long long R = a.R;
+  const u64* p0 = a.p0;   // may alias out (a row is read before its tile is written)
+  const u64* p1 = a.p1;
+  const u64 s1 = a.s1;
+  const int a_bits = a.a_bits;
+  // CTA b takes tiles b, b + G, b + 2G, ... (G = gridDim.x), or with matrix groups the
+  // contiguous range [t0, t0 + count), so that it meets each matrix in one run
   const long long ntiles = (R + TC_BM - 1) / TC_BM;
-  const long long my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const long long nunits = 2 * my_tiles;
+  const long long G = gridDim.x;
+  const bool contig = a.mrows != 0;
+  const long long t0 = contig ? ntiles * blockIdx.x / G : blockIdx.x;
+  const long long tstep = contig ? 1 : G;
+  const long long count = contig ? ntiles * (blockIdx.x + 1) / G - t0
+                                 : (ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / G + 1 : 0);
+  const long long nunits = 2 * count;
 
   if (tid == 0) {
     for (int i = 0; i < NSTAGE; ++i) {
@@ -465,14 +484,9 @@ k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ 
   if (warp >= GM_NDRAIN && warp < GM_NDRAIN + GM_PROD) {
     // ---- producers: B planes once, then the A planes of every (tile, chunk) ----
     const int pt = tid - GM_NDRAIN * 32;   // 0 .. 32 GM_PROD - 1
-    for (int it = pt; it < 64 * 8; it += GM_PROD * 32) {   // (row c of M^T, unit of 8 k)
-      const int c = it >> 3, k8 = it & 7;
-      u64 v[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = Mmat[(k8 * 8 + q) * 64 + c];
-      split8_store(v, Bsm + (k8 >> 2) * GM_BCHUNK, B_TILE, sw64_off(c, k8 & 3));
-    }
+    const long long lda = a.in.s1;           // A row (bit word) stride inside a tile
     bool ok = true;
+    long long cur_m = -1;
     for (long long u = 0; u < nunits && ok; ++u) {
       const int st = (int)(u % NSTAGE);
       if (u >= NSTAGE) {
@@ -480,34 +494,43 @@ k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ 
                         mbar_wait(&empty_bar[st], (unsigned)(((u / NSTAGE) + 1) & 1), abort));
         if (!ok) break;
       }
-      const long long tile = blockIdx.x + (u >> 1) * gridDim.x;
+      const long long tile = t0 + (u >> 1) * tstep;
       const int kc = (int)(u & 1);
+      const long long rho0 = tile * TC_BM;
       unsigned char* As = Asm + st * 8 * A_TILE;
-      if (kc == 0 && pt == 0) {   // bring the next tile's rows into L2 while this one runs
-        const long long nt = tile + gridDim.x;
-        if (nt < (R + TC_BM - 1) / TC_BM) {
-          const long long r0 = nt * TC_BM;
+      if (kc == 0) {
+        const long long mi = a.mrows ? rho0 / a.mrows : 0;
+        if (mi != cur_m) {
+          // B = M^T of this tile's matrix; the previous tile's MMAs must have finished reading
+          if (u > 0) {
+            ok = __all_sync(0xffffffffu, mbar_wait(&empty_bar[(u - 1) % NSTAGE],
+                                                   (unsigned)(((u - 1) / NSTAGE) & 1), abort));
+            if (!ok) break;
+          }
+          const u64* Mm = a.Mmat + mi * 4096;
+          for (int it = pt; it < 64 * 8; it += GM_PROD * 32) {   // (row c of M^T, unit of 8 k)
+            const int c = it >> 3, k8 = it & 7;
+            u64 v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = Mm[(k8 * 8 + q) * 64 + c];
+            split8_store(v, Bsm + (k8 >> 2) * GM_BCHUNK, B_TILE, sw64_off(c, k8 & 3));
+          }
+          cur_m = mi;
+        }
+        if (pt == 0 && (u >> 1) + 1 < count && lda <= 128) {   // next tile's rows into L2
+          const long long r0 = (tile + tstep) * TC_BM;
           const long long nr = (R - r0 < TC_BM) ? R - r0 : TC_BM;
-          if (a_bits) {   // whole 16-byte units inside the word array only
-            const unsigned bytes = (unsigned)((nr * 8) & ~15ll);
-            if (bytes) prefetch_l2(p0 + r0, bytes);
-          } else {
-            // rows r0 .. r0 + nr - 1 of p0 and p1 (and add0): spans of lda words per row
-            const u64* lo = p0 + r0 * lda;
-            const u64* hi = p0 + (r0 + nr - 1) * lda + 64;
-            if (p1) {
-              const u64* l1 = p1 + r0 * lda;
-              const u64* h1 = p1 + (r0 + nr - 1) * lda + 64;
-              lo = l1 < lo ? l1 : lo;
-              hi = h1 > hi ? h1 : hi;
-            }
-            const long long bytes = (long long)(hi - lo) * 8;
+          const long long nb = rowmap(a.in, r0);
+          const long long words = (nr - 1) * lda + (a_bits ? 1 : 64);
+          const long long bytes = (words * 8) & ~15ll;   // whole 16-byte units inside the rows
+          for (int w2 = 0; w2 < (p1 ? 2 : 1); ++w2) {
+            const char* lo = reinterpret_cast<const char*>((w2 ? p1 : p0) + nb);
             for (long long o = 0; o < bytes; o += 65536)
-              prefetch_l2(reinterpret_cast<const char*>(lo) + o,
-                          (unsigned)((bytes - o < 65536 ? bytes - o : 65536) & ~15ll));
+              prefetch_l2(lo + o, (unsigned)(bytes - o < 65536 ? bytes - o : 65536));
           }
         }
       }
+      const long long ib = rowmap(a.in, rho0);   // word offset of the tile's first A row
       constexpr int NIT = (512 + GM_PROD * 32 - 1) / (GM_PROD * 32);   // items per thread
       if (a_bits) {
         // one word per item row: load all of this thread's words first (one latency per chunk)
@@ -515,8 +538,8 @@ k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ 
 #pragma unroll
         for (int q = 0; q < NIT; ++q) {
           const int item = pt + q * GM_PROD * 32;
-          const long long row = tile * TC_BM + (item >> 2);
-          wd[q] = (item < 512 && row < R) ? p0[row] : 0ull;
+          const bool in = item < 512 && rho0 + (item >> 2) < R;
+          wd[q] = in ? p0[ib + (item >> 2) * lda] : 0ull;
         }
 #pragma unroll
         for (int q = 0; q < NIT; ++q) {
@@ -536,9 +559,8 @@ k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ 
 #pragma unroll
           for (int q = 0; q < NQ; ++q) {
             const int item = pt + (Q0 + q) * GM_PROD * 32;   // 512 items: (row, unit of 8 k)
-            const long long row = tile * TC_BM + (item >> 2);
-            const bool in = item < 512 && row < R;
-            const long long off = row * lda + kc * 32 + (item & 3) * 8;
+            const bool in = item < 512 && rho0 + (item >> 2) < R;
+            const long long off = ib + (item >> 2) * lda + kc * 32 + (item & 3) * 8;
 #pragma unroll
             for (int j = 0; j < 8; j += 2) {
               const ulonglong2 a =
@@ -649,12 +671,12 @@ k_gr_matmul_tc(long long R, const u64* __restrict__ p0, const u64* __restrict__ 
         if (lane == 0) mbar_arrive(&acce_bar[g]);
       }
       if (ok && (u & 1)) {   // tile complete: remove the biases of its two chunks, add, store
-        const long long tile = blockIdx.x + (u >> 1) * gridDim.x;
-        const long long r = tile * TC_BM + q4 * 32 + lane;
+        const long long r = (t0 + (u >> 1) * tstep) * TC_BM + q4 * 32 + lane;
         const u64 corr = (u64)(2u * CHUNK_HI_BIAS) << 32;
-        if (r < R) {
-          const u64* a0p = add0 ? add0 + r * ld_add0 + h * GM_DC : nullptr;
-          u64* o = out + r * ldc + h * GM_DC;
+        const long long ob = r < R ? rowmap(a.om, r) : a.out_lim;
+        if (ob < a.out_lim) {
+          const u64* a0p = a.add0 ? a.add0 + r * a.ld_add0 + h * GM_DC : nullptr;
+          u64* o = a.out + ob + h * GM_DC;
 #pragma unroll
           for (int c0 = 0; c0 < GM_DC; c0 += 8) {   // 8 columns at a time (bounded live range)
             ulonglong2 a[4];
@@ -914,16 +936,21 @@ int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nte
   return 0;
 }
 
-int gr_matmul_tc(cudaStream_t st, long long R, const u64* p0, const u64* p1, u64 s1, long long lda,
-                 int a_bits, const u64* Mmat, const u64* add0, long long ld_add0, u64* out,
-                 long long ldc, unsigned* err, unsigned err_flag) {
-  if (R <= 0) return 0;
-  if (a_bits) lda = 0;
-  // 16-byte vector accesses: row strides and bases must keep 2-word alignment
-  if ((lda & 1) || (ldc & 1) || (add0 && (ld_add0 & 1)) ||
-      ((reinterpret_cast<uintptr_t>(p0) | reinterpret_cast<uintptr_t>(p1) |
-        reinterpret_cast<uintptr_t>(add0) | reinterpret_cast<uintptr_t>(out)) & 15))
+int gr_matmul_tc_ex(cudaStream_t st, const GrMMArgs& args, unsigned* err, unsigned err_flag) {
+  GrMMArgs a = args;
+  if (a.R <= 0) return 0;
+  if (a.add0 && !a.ld_add0) a.ld_add0 = 64;
+  auto odd = [](long long v) { return (v & 1) != 0; };
+  const bool bad_in = !a.a_bits && (odd(a.in.s1) || odd(a.in.s2));
+  // 16-byte vector accesses need even word offsets; a tile must not straddle a map period or
+  // a matrix group
+  if (bad_in || odd(a.om.s1) || odd(a.om.s2) || (a.add0 && odd(a.ld_add0)) ||
+      (a.in.q % TC_BM) || (a.om.q % TC_BM) || (a.mrows % TC_BM) || a.in.q < 0 || a.om.q < 0 ||
+      a.mrows < 0 ||
+      ((reinterpret_cast<uintptr_t>(a.p0) | reinterpret_cast<uintptr_t>(a.p1) |
+        reinterpret_cast<uintptr_t>(a.add0) | reinterpret_cast<uintptr_t>(a.out)) & 15))
     return -1;
+  if (a.out_lim <= 0) a.out_lim = LLONG_MAX;
   static int nsm = 0;
   if (!nsm) {
     int dev = 0;
@@ -931,12 +958,29 @@ int gr_matmul_tc(cudaStream_t st, long long R, const u64* p0, const u64* p1, u64
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (nsm <= 0) nsm = 148;
   }
-  const long long ntiles = (R + TC_BM - 1) / TC_BM;
+  const long long ntiles = (a.R + TC_BM - 1) / TC_BM;
   const unsigned grid = (unsigned)(ntiles < nsm ? ntiles : nsm);
   set_max_dynamic_smem(reinterpret_cast<const void*>(k_gr_matmul_tc), (int)GM_SMEM);
-  k_gr_matmul_tc<<<grid, GM_THREADS, GM_SMEM, st>>>(R, p0, p1, s1, lda, a_bits, Mmat, add0,
-                                                     ld_add0 ? ld_add0 : ldc, out, ldc, err, err_flag);
+  k_gr_matmul_tc<<<grid, GM_THREADS, GM_SMEM, st>>>(a, err, err_flag);
   return 0;
+}
+
+int gr_matmul_tc(cudaStream_t st, long long R, const u64* p0, const u64* p1, u64 s1, long long lda,
+                 int a_bits, const u64* Mmat, const u64* add0, long long ld_add0, u64* out,
+                 long long ldc, unsigned* err, unsigned err_flag) {
+  GrMMArgs a{};
+  a.R = R;
+  a.p0 = p0;
+  a.p1 = p1;
+  a.s1 = s1;
+  a.in = GrRowMap{0, a_bits ? 1 : lda, 0};
+  a.a_bits = a_bits;
+  a.Mmat = Mmat;
+  a.add0 = add0;
+  a.ld_add0 = ld_add0 ? ld_add0 : ldc;
+  a.out = out;
+  a.om = GrRowMap{0, ldc, 0};
+  return gr_matmul_tc_ex(st, a, err, err_flag);
 }
 
 int gram3_tc(cudaStream_t st, long long Dh, const u64* x, const u64* y, u64* P, unsigned* err,
