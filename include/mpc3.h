@@ -159,7 +159,7 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
                       void* workspace, size_t workspace_bytes, uint64_t* trace);
 
 /* Pi_Rec (Sec. 2): P0 sends [r]_1 to P2 and [r]_2 to P1, P1 sends m to P0; P1 sends H([r]_1) to
- * P2, P2 sends H(m) to P0 and H([r]_2) to P1 (H = SHA-256 Merkle root, 64 KiB leaves).  On any
+ * P2, P2 sends H(m) to P0 and H([r]_2) to P1 (H = SHA-256 Merkle root, 1 KiB leaves).  On any
  * mismatch the call returns MPC_ERR_ABORT; otherwise out = m - [r]_1 - [r]_2 (n words, host if
  * out_on_host, else device).  Refused with MPC_ERR_PENDING while products are unverified. */
 int mpc_reconstruct(mpc_ctx* ctx, const uint64_t* xs, int64_t n, uint64_t* out, int out_on_host,
@@ -180,6 +180,14 @@ int mpc_reconstruct(mpc_ctx* ctx, const uint64_t* xs, int64_t n, uint64_t* out, 
  *   unverified. */
 #define MPC_NOALLOC_MAX_N 262144
 int mpc_reconstruct_noalloc(mpc_ctx* ctx, const uint64_t* xs, int64_t n, uint64_t* out);
+
+/* H of Pi_Rec on its own (Sec. 2, verifiable reconstruction): the SHA-256 Merkle root (1024-byte
+ * leaves of the little-endian byte image, node = SHA-256(left || right), an odd node promoted
+ * unchanged, the empty array hashing to SHA-256 of the empty string) of n device words, exactly
+ * as mpc_reconstruct computes it for its messages.
+ *   data: n device words (borrowed; n >= 0); digest: 32 host bytes (written, FIPS byte order).
+ *   Allocates its scratch on the device, synchronises the context's stream and frees it. */
+int mpc_hash_u64(mpc_ctx* ctx, const uint64_t* data, int64_t n, uint8_t* digest);
 
 /* Local rearrangement of a sharing (Sec. 2, linear homomorphic property: every party applies the
  * same public map to each component it holds; no communication): out[k] = x[idx[k]], or 0 when

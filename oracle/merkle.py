@@ -1,10 +1,11 @@
-"""Hash H of Pi_Rec: SHA-256 Merkle root over 64 KiB leaves (oracle; test infrastructure only).
+"""Hash H of Pi_Rec: SHA-256 Merkle root over 1 KiB leaves (oracle; test infrastructure only).
 
 Paper, Sec. 2 "Verifiability of share reconstruction": in Pi_Rec, P1 sends H([r_x]_1) to P2, P2
 sends H(m_x) to P0 and H([r_x]_2) to P1; a party aborts when a received value and a received hash
-disagree.  The paper does not name H.  Reading: SHA-256 (FIPS 180-4) of each 65536-byte leaf of the
+disagree.  The paper does not name H.  Reading: SHA-256 (FIPS 180-4) of each 1024-byte leaf of the
 little-endian byte image of the u64 array (the last leaf may be shorter), then a binary tree whose
-node is SHA-256(left || right); an odd node at the end of a level is promoted unchanged.  An empty
+node is SHA-256(left || right); an odd node at the end of a level is promoted unchanged.  (Any
+collision-resistant H serves the check; short leaves let many leaves be hashed in parallel.)  An empty
 array hashes to SHA-256 of the empty string.  The array length is public, so no domain prefix is
 needed.
 
@@ -16,7 +17,7 @@ import hashlib
 
 import numpy as np
 
-LEAF_BYTES = 65536
+LEAF_BYTES = 1024
 
 
 def sha256(b: bytes) -> bytes:

@@ -47,6 +47,7 @@ _SIGS = {
     "mpc_reconstruct_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "mpc_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "mpc_gather": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p]),
+    "mpc_hash_u64": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "mpc_relu": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p, C.c_int64, C.c_void_p,
                            C.c_void_p, C.c_size_t, C.c_void_p]),
     "mpc_maxpool2": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p, C.c_int64, C.c_int64,

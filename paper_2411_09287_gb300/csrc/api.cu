@@ -277,7 +277,8 @@ Epi epi_atomic(u64* out, long long ldc, u64 sign = 1) {
   return e;
 }
 
-int nsplit_for(long long K) { return (int)std::min<long long>(1024, std::max<long long>(1, K / 512)); }
+// split-K factor of the 64 x 64 Gram products: enough CTAs to fill the GPU down to K ~ 2^12
+int nsplit_for(long long K) { return (int)std::min<long long>(1024, std::max<long long>(1, K / 32)); }
 
 // out (atomic, 64x64) += sign * sum_i U_i (x) V_i with U = U0 + su U1, V = V0 + sv V1.
 void gram(mpc_ctx* ctx, u64* P, const u64* U0, const u64* U1, u64 su, long long ldu, const u64* V0,
@@ -2143,6 +2144,26 @@ int mpc_maxpool2(mpc_ctx* ctx, uint64_t call_id, uint64_t verify_id, const uint6
     CK(cudaMemcpyAsync(out + c * nw, p.o[1] + c * np[1], (size_t)nw * 8, cudaMemcpyDeviceToDevice, st));
   if ((rc = cuda_check(ctx, "maxpool2"))) return rc;
   return nl_finish(ctx);
+}
+
+int mpc_hash_u64(mpc_ctx* ctx, const uint64_t* data, int64_t n, uint8_t* digest) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (n < 0) return fail(ctx, MPC_ERR_SHAPE, "hash: bad size");
+  if ((n > 0 && !data) || !digest) return fail(ctx, MPC_ERR_ARG, "hash: bad argument");
+  u32* scratch = nullptr;
+  const size_t words = hash_scratch_words(n) + 8;
+  cudaError_t e = cudaMalloc(&scratch, words * sizeof(u32));
+  if (e != cudaSuccess) return fail(ctx, MPC_ERR_CUDA, "hash: scratch allocation");
+  u32 h[8];
+  launch_hash_u64(ctx->st, data, n, scratch, scratch + words - 8);
+  e = cudaMemcpyAsync(h, scratch + words - 8, sizeof(h), cudaMemcpyDeviceToHost, ctx->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+  cudaFree(scratch);
+  if (e != cudaSuccess) return fail(ctx, MPC_ERR_CUDA, cudaGetErrorString(e));
+  for (int q = 0; q < 8; ++q)
+    for (int b = 0; b < 4; ++b) digest[4 * q + b] = (uint8_t)(h[q] >> (24 - 8 * b));
+  return cuda_check(ctx, "hash");
 }
 
 int mpc_gather(mpc_ctx* ctx, const uint64_t* xs, int64_t n_in, const int64_t* idx, int64_t n_out,

@@ -121,6 +121,16 @@ void launch_open_p1(cudaStream_t st, const u64* p1_m, const u64* p1_r1, const u6
                     long long n, u64* out);
 
 // ---- SHA-256 Merkle hash (sha_kernels.cu) ---------------------------------------------------
+// Merkle hash of Pi_Rec: 1024-byte leaves, subtree roots of 64 aligned leaves per CTA.
+constexpr long long HASH_LEAF_BYTES = 1024;
+constexpr long long HASH_CTA_LEAVES = 64;
+constexpr long long hash_scratch_words_for(long long n) {
+  return 16 * (((8 * n + HASH_LEAF_BYTES - 1) / HASH_LEAF_BYTES > 1
+                    ? (8 * n + HASH_LEAF_BYTES - 1) / HASH_LEAF_BYTES
+                    : 1) +
+               HASH_CTA_LEAVES - 1) /
+         HASH_CTA_LEAVES;
+}
 // digest (8 words) of the n-word array; scratch needs hash_scratch_words(n) 32-bit words.
 void launch_hash_u64(cudaStream_t st, const u64* data, long long n, u32* scratch, u32* digest);
 void launch_digest_check(cudaStream_t st, const u32* a0, const u32* b0, const u32* a1,

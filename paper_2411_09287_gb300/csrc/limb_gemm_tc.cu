@@ -49,12 +49,12 @@ constexpr int TC_THREADS = (NDRAIN + 2) * 32;
 constexpr unsigned IDESC = (1u << 4) | ((unsigned)(TC_BN >> 3) << 17) |
                            ((unsigned)(TC_BM >> 4) << 24);
 
-template <int ACC>
-__device__ __forceinline__ void mma_f16(unsigned d_tmem, u64 adesc, u64 bdesc) {
+// D (+)= A B; acc = 0 overwrites the accumulator, 1 adds to it
+__device__ __forceinline__ void mma_f16(unsigned d_tmem, u64 adesc, u64 bdesc, unsigned acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "n"(ACC));
+      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc));
 }
 // Bit pattern of (v + 1.5 * 2^23) for an integer-valued f32 v in [-2^22, 2^22]: equals
 // v + MAGIC_I exactly (the sum lies in [2^23, 2^24], where every integer is a float).
@@ -77,8 +77,10 @@ __host__ __device__ constexpr int group_s(int G, int g) { return G == 0 ? (g < 2
 // descriptors of digit plane 0 of the stage; plane i is A_TILE (B_TILE) bytes further on, and
 // each k16 step advances 32 bytes inside the swizzled rows.
 // With A0 set, A has digit plane 0 only (0/1 entries): C_s = A_0 B_s, one pair per accumulator.
+// fresh = 0 adds the chunk to what the accumulators hold instead of starting them anew.
 template <int G, bool A0 = false>
-__device__ __forceinline__ void issue_group(unsigned tmem, u64 a_desc, u64 b_desc) {
+__device__ __forceinline__ void issue_group(unsigned tmem, u64 a_desc, u64 b_desc,
+                                            unsigned fresh = 1) {
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
     const int s = group_s(G, g);
@@ -89,8 +91,7 @@ __device__ __forceinline__ void issue_group(unsigned tmem, u64 a_desc, u64 b_des
         if (i <= s && (!A0 || i == 0)) {
           const u64 ad = a_desc + (u64)((i * A_TILE) >> 4) + (u64)(kk * 2);
           const u64 bd = b_desc + (u64)(((s - i) * B_TILE) >> 4) + (u64)(kk * 2);
-          if (kk == 0 && i == 0) mma_f16<0>(tmem + (unsigned)acc_col(s), ad, bd);
-          else mma_f16<1>(tmem + (unsigned)acc_col(s), ad, bd);
+          mma_f16(tmem + (unsigned)acc_col(s), ad, bd, (kk == 0 && i == 0) ? (fresh ^ 1u) : 1u);
         }
       }
     }
@@ -611,16 +612,21 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
         tc_fence_after();
         const u64 ad = da0 + (u64)((st * 8 * A_TILE) >> 4);
         const u64 bd = db0 + (u64)(((int)(u & 1) * GM_BCHUNK) >> 4);
-        if (u > 0 && !mbar_wait(&acce_bar[0], (unsigned)((u - 1) & 1), abort)) { fail(); break; }
+        // with a_bits both K chunks go into the same accumulation (|C_s| <= 64 * 128), drained
+        // once per tile; otherwise every chunk is drained
+        const int kc = (int)(u & 1);
+        const bool first = !a_bits || kc == 0, last = !a_bits || kc == 1;
+        const long long v = a_bits ? (u >> 1) : u;   // accumulation index
+        if (first && v > 0 && !mbar_wait(&acce_bar[0], (unsigned)((v - 1) & 1), abort)) { fail(); break; }
         tc_fence_after();
-        if (a_bits) issue_group<0, true>(tmem, ad, bd);
+        if (a_bits) issue_group<0, true>(tmem, ad, bd, first ? 1u : 0u);
         else issue_group<0>(tmem, ad, bd);
-        mma_commit(&accf_bar[0]);
-        if (u > 0 && !mbar_wait(&acce_bar[1], (unsigned)((u - 1) & 1), abort)) { fail(); break; }
+        if (last) mma_commit(&accf_bar[0]);
+        if (first && v > 0 && !mbar_wait(&acce_bar[1], (unsigned)((v - 1) & 1), abort)) { fail(); break; }
         tc_fence_after();
-        if (a_bits) issue_group<1, true>(tmem, ad, bd);
+        if (a_bits) issue_group<1, true>(tmem, ad, bd, first ? 1u : 0u);
         else issue_group<1>(tmem, ad, bd);
-        mma_commit(&accf_bar[1]);
+        if (last) mma_commit(&accf_bar[1]);
         mma_commit(&empty_bar[st]);
       }
       mma_commit(&done_bar);
@@ -634,8 +640,9 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
 #pragma unroll
     for (int c = 0; c < GM_DC; ++c) acc[c] = 0;
     bool ok = true;
-    for (long long u = 0; u < nunits && ok; ++u) {
-      const unsigned par = (unsigned)(u & 1);
+    const long long nacc = a_bits ? nunits / 2 : nunits;   // accumulations to drain
+    for (long long v = 0; v < nacc && ok; ++v) {
+      const unsigned par = (unsigned)(v & 1);
 #pragma unroll
       for (int g = 0; g < 2; ++g) {
         ok = __all_sync(0xffffffffu, mbar_wait(&accf_bar[g], par, abort));
@@ -670,23 +677,23 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
         __syncwarp();
         if (lane == 0) mbar_arrive(&acce_bar[g]);
       }
-      if (ok && (u & 1)) {   // tile complete: remove the biases of its two chunks, add, store
-        const long long r = (t0 + (u >> 1) * tstep) * TC_BM + q4 * 32 + lane;
-        const u64 corr = (u64)(2u * CHUNK_HI_BIAS) << 32;
+      if (ok && (a_bits || (v & 1))) {   // tile complete: remove the drains' biases, add, store
+        const long long r = (t0 + (a_bits ? v : v >> 1) * tstep) * TC_BM + q4 * 32 + lane;
+        const u64 corr = (u64)((a_bits ? 1u : 2u) * CHUNK_HI_BIAS) << 32;
         const long long ob = r < R ? rowmap(a.om, r) : a.out_lim;
         if (ob < a.out_lim) {
           const u64* a0p = a.add0 ? a.add0 + r * a.ld_add0 + h * GM_DC : nullptr;
           u64* o = a.out + ob + h * GM_DC;
 #pragma unroll
           for (int c0 = 0; c0 < GM_DC; c0 += 8) {   // 8 columns at a time (bounded live range)
-            ulonglong2 a[4];
+            ulonglong2 a0v[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-              a[q] = a0p ? *reinterpret_cast<const ulonglong2*>(a0p + c0 + 2 * q) : make_ulonglong2(0, 0);
+              a0v[q] = a0p ? *reinterpret_cast<const ulonglong2*>(a0p + c0 + 2 * q) : make_ulonglong2(0, 0);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-              *reinterpret_cast<ulonglong2*>(o + c0 + 2 * q) =
-                  make_ulonglong2(acc[c0 + 2 * q] - corr + a[q].x, acc[c0 + 2 * q + 1] - corr + a[q].y);
+              *reinterpret_cast<ulonglong2*>(o + c0 + 2 * q) = make_ulonglong2(
+                  acc[c0 + 2 * q] - corr + a0v[q].x, acc[c0 + 2 * q + 1] - corr + a0v[q].y);
             asm volatile("" ::: "memory");
           }
         }

@@ -42,8 +42,7 @@ using namespace mpc3::internal;
 namespace {
 
 constexpr long long kMaxN = MPC_NOALLOC_MAX_N;
-constexpr long long kLeaves = (kMaxN * 8 + 65535) / 65536;
-constexpr long long kHashWords = 16 * kLeaves;   // 32-bit words of scratch per hash
+constexpr long long kHashWords = hash_scratch_words_for(kMaxN);   // 32-bit words per hash
 
 struct NoallocScratch {
   u64 in_p2_r1[kMaxN];      // [r]_1 as received by P2 from P0

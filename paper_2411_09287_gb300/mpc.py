@@ -197,6 +197,13 @@ class Context:
         self.sync()   # idx_d must outlive the enqueued gather
         return out
 
+    def hash_u64(self, data) -> bytes:
+        """H of Pi_Rec (SHA-256 Merkle root, 1 KiB leaves) of a device u64 tensor."""
+        d = (C.c_uint8 * 32)()
+        self._check(self.lib.mpc_hash_u64(self.h, C.c_void_p(_ptr(data) if data.numel() else 0),
+                                          data.numel(), d))
+        return bytes(d)
+
     @staticmethod
     def nonlinear_R(np_list):
         """Default rounds (R0, R1, R2) of a non-linear layer's three verification batches for

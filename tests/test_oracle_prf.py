@@ -60,3 +60,7 @@ def test_merkle_shapes():
     assert merkle_root_bytes(a + b + c) == h(h(h(a) + h(b)) + h(c))   # odd node promoted
     arr = np.arange(10, dtype=np.uint64)
     assert hash_u64(arr) == h(arr.astype("<u8").tobytes())
+    # five leaves: promotions on two levels
+    ls = [os.urandom(LEAF_BYTES) for _ in range(4)] + [c]
+    hh = [h(x) for x in ls]
+    assert merkle_root_bytes(b"".join(ls)) == h(h(h(hh[0] + hh[1]) + h(hh[2] + hh[3])) + hh[4])
