@@ -6,13 +6,15 @@
 // v = sum_i 2^(8i) d_i mod 2^64 (carry-propagating split; the carry out of d_7 vanishes mod 2^64).
 // f16 holds every such digit exactly.  Only digit pairs with i + j < 8 contribute mod 2^64:
 //   C = sum_{s<8} 2^(8s) C_s,   C_s = sum_{i+j=s} A_i B_j      (36 digit-plane products).
-// Each C_s has its own TMEM accumulator (8 x 64 columns = all 512).  One K chunk is 32 deep, so
-// |C_s| <= 8 * 32 * 2^14 = 2^22 within a chunk: every f32 partial sum is an exact integer, and
-// adding 1.5 * 2^23 turns it into an integer-valued float whose bit pattern minus 0x4B400000 is
-// that integer (exact on [-2^22, 2^22]).  After each chunk the accumulators are drained into
-// 64-bit registers, which wrap mod 2^64 as required:
+// Each C_s has its own TMEM accumulator (8 x 64 columns = all 512).  An accumulation runs over
+// at most 64 of K (two chunks of 32), so |C_s| <= (s + 1) * 64 * 2^14: every f32 partial sum is
+// an exact integer.  For s <= 3 (|C_s| <= 2^22), adding 1.5 * 2^23 turns it into an
+// integer-valued float whose bit pattern minus 0x4B400000 is that integer; for s >= 4
+// (|C_s| <= 2^23) a float-to-int conversion does it.  After each accumulation the accumulators
+// are drained into 64-bit registers, which wrap mod 2^64 as required:
 //   acc += (v0 + 2^8 v1) + 2^16 (v2 + 2^8 v3) + 2^32 (v4 + 2^8 v5) + 2^48 (v6 + 2^8 v7),
-// each bracket computed in 32-bit arithmetic (|v_s + 2^8 v_(s+1)| < 2^31).
+// each bracket computed in 32-bit arithmetic (|v0 + 2^8 v1|, |v2 + 2^8 v3| < 2^31; the two high
+// brackets only matter mod 2^32 and 2^16).
 //
 // CTA = one 128 x 64 output tile, 10 warps with fixed roles:
 //   warps 0..7  drain: warp w reads TMEM lanes 32 (w % 4) .. +31 (= tile rows) and columns
@@ -60,10 +62,14 @@ __device__ __forceinline__ void mma_f16(unsigned d_tmem, u64 adesc, u64 bdesc, u
 // v + MAGIC_I exactly (the sum lies in [2^23, 2^24], where every integer is a float).
 constexpr unsigned MAGIC_I = 0x4B400000u;
 constexpr unsigned PAIR_BIAS = MAGIC_I + 256u * MAGIC_I;   // bias of v_s + 2^8 v_(s+1), mod 2^32
-// per chunk, group GA adds PAIR_BIAS << 16 and group GB adds PAIR_BIAS to the high word
-constexpr unsigned CHUNK_HI_BIAS = (PAIR_BIAS << 16) + PAIR_BIAS;
 __device__ __forceinline__ int f2i_biased(unsigned bits) {
   return __float_as_int(__uint_as_float(bits) + 12582912.0f);
+}
+// the integer value of an integer-valued f32 (exact for |v| <= 2^24)
+__device__ __forceinline__ unsigned f32_int(unsigned bits) {
+  int r;
+  asm("cvt.rni.s32.f32 %0, %1;\n" : "=r"(r) : "f"(__uint_as_float(bits)));
+  return (unsigned)r;
 }
 
 // TMEM column of accumulator s: group GA = {0, 1, 6, 7} in columns 0..255, GB = {2..5} above
@@ -72,6 +78,35 @@ __host__ __device__ constexpr int acc_col(int s) {
 }
 // digit weight of the g-th accumulator of group G (GA = {0, 1, 6, 7}, GB = {2, 3, 4, 5})
 __host__ __device__ constexpr int group_s(int G, int g) { return G == 0 ? (g < 2 ? g : g + 4) : g + 2; }
+
+// Drain of accumulator group G for the 16 TMEM columns at tl + col: acc[j] += G = 0:
+// (v0 + 2^8 v1) + 2^48 (v6 + 2^8 v7), G = 1: 2^16 (v2 + 2^8 v3) + 2^32 (v4 + 2^8 v5).
+template <int G>
+__device__ __forceinline__ void drain16(unsigned tl, int col, u64* acc) {
+  constexpr int s0 = G == 0 ? 0 : 2, s1 = G == 0 ? 6 : 4;
+  unsigned x0[16], x1[16];
+  tmem_ld16(tl + (unsigned)(acc_col(s0) + col), x0);
+  tmem_ld16(tl + (unsigned)(acc_col(s0 + 1) + col), x1);
+  tmem_ld_wait();
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {   // + ws (G = 0) or 2^16 ws (G = 1), ws sign-extended
+    const unsigned ws =
+        (unsigned)f2i_biased(x0[j]) + (unsigned)f2i_biased(x1[j]) * 256u - PAIR_BIAS;
+    acc[j] += G == 0 ? (u64)(long long)(int)ws : (u64)(long long)(int)ws << 16;
+  }
+#pragma unroll
+  for (int h8 = 0; h8 < 16; h8 += 8) {   // + 2^48 whi (G = 0) or 2^32 whi (G = 1)
+    unsigned y0[8], y1[8];                // (8 columns at a time: conversions have long latency)
+    tmem_ld8(tl + (unsigned)(acc_col(s1) + col + h8), y0);
+    tmem_ld8(tl + (unsigned)(acc_col(s1 + 1) + col + h8), y1);
+    tmem_ld_wait();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const unsigned whi = f32_int(y0[j]) + f32_int(y1[j]) * 256u;
+      acc[h8 + j] += (u64)(G == 0 ? (whi << 16) : whi) << 32;
+    }
+  }
+}
 
 // All MMAs of one accumulator group for one K chunk, fully unrolled: a_desc / b_desc are the
 // descriptors of digit plane 0 of the stage; plane i is A_TILE (B_TILE) bytes further on, and
@@ -181,14 +216,17 @@ k_limb_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const u64 ad = d0 + (u64)((st * STAGE) >> 4);
         const u64 bd = ad + (u64)((8 * A_TILE) >> 4);
-        if (c > 0 && !mbar_wait(&acce_bar[0], (unsigned)((c - 1) & 1), abort)) { fail(); break; }
+        // accumulation v takes chunks 2v and 2v + 1 (K <= 64 per accumulation)
+        const bool first = !(c & 1), last = (c & 1) || c == nchunks - 1;
+        const int v = c >> 1;
+        if (first && v > 0 && !mbar_wait(&acce_bar[0], (unsigned)((v - 1) & 1), abort)) { fail(); break; }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        issue_group<0>(tmem, ad, bd);
-        mma_commit(&accf_bar[0]);
-        if (c > 0 && !mbar_wait(&acce_bar[1], (unsigned)((c - 1) & 1), abort)) { fail(); break; }
+        issue_group<0>(tmem, ad, bd, first ? 1u : 0u);
+        if (last) mma_commit(&accf_bar[0]);
+        if (first && v > 0 && !mbar_wait(&acce_bar[1], (unsigned)((v - 1) & 1), abort)) { fail(); break; }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        issue_group<1>(tmem, ad, bd);
-        mma_commit(&accf_bar[1]);
+        issue_group<1>(tmem, ad, bd, first ? 1u : 0u);
+        if (last) mma_commit(&accf_bar[1]);
         mma_commit(&empty_bar[st]);   // the stage is free once these MMAs have read it
       }
       // every MMA issued must complete before the tensor memory is released
@@ -203,39 +241,18 @@ k_limb_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
     for (int c = 0; c < 32; ++c) acc[c] = 0;
     bool ok = true;
-    for (int c = 0; c < nchunks && ok; ++c) {
-      const unsigned par = (unsigned)(c & 1);
-#pragma unroll
+    const int nacc = (nchunks + 1) / 2;
+    for (int v = 0; v < nacc && ok; ++v) {
+      const unsigned par = (unsigned)(v & 1);
+#pragma unroll 1
       for (int g = 0; g < 2; ++g) {
         ok = __all_sync(0xffffffffu, mbar_wait(&accf_bar[g], par, abort));
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const int s0 = g == 0 ? 0 : 2;   // the group's digit-weight pairs (s0, s0+1), (s1, s1+1)
-        const int s1 = g == 0 ? 6 : 4;
 #pragma unroll
         for (int c16 = 0; c16 < 2; ++c16) {
-          unsigned a0[16], a1[16], b0[16], b1[16];
-          tmem_ld16(tl + (unsigned)(acc_col(s0) + c16 * 16), a0);
-          tmem_ld16(tl + (unsigned)(acc_col(s0 + 1) + c16 * 16), a1);
-          tmem_ld16(tl + (unsigned)(acc_col(s1) + c16 * 16), b0);
-          tmem_ld16(tl + (unsigned)(acc_col(s1 + 1) + c16 * 16), b1);
-          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            // biased pair sums: w = C_s + 2^8 C_(s+1) + PAIR_BIAS (mod 2^32)
-            const unsigned wlo = (unsigned)f2i_biased(a0[j]) + (unsigned)f2i_biased(a1[j]) * 256u;
-            const unsigned whi = (unsigned)f2i_biased(b0[j]) + (unsigned)f2i_biased(b1[j]) * 256u;
-            const unsigned ws = wlo - PAIR_BIAS;   // exact, |ws| < 2^31: its sign extends it
-            unsigned add_lo, add_hi;
-            if (g == 0) {   // + ws + 2^48 whi; the bias of whi is removed once per tile
-              add_lo = ws;
-              add_hi = (unsigned)((int)ws >> 31) + (whi << 16);
-            } else {        // + 2^16 ws + 2^32 whi
-              add_lo = ws << 16;
-              add_hi = (unsigned)((int)ws >> 16) + whi;
-            }
-            acc[c16 * 16 + j] += ((u64)add_hi << 32) | add_lo;
-          }
+          if (g == 0) drain16<0>(tl, c16 * 16, acc + c16 * 16);
+          else drain16<1>(tl, c16 * 16, acc + c16 * 16);
         }
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         __syncwarp();
@@ -245,12 +262,10 @@ k_limb_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (ok && !*abort) {
       const long long r = m0 + q * 32 + lane;
       const long long cb = n0 + h * 32;
-      // remove the biases of whi that every chunk added to the high word
-      const u64 corr = (u64)((unsigned)nchunks * CHUNK_HI_BIAS) << 32;
       if (r < M) {
 #pragma unroll
         for (int c = 0; c < 32; ++c)
-          if (cb + c < N) C[r * ldc + cb + c] = acc[c] - corr;
+          if (cb + c < N) C[r * ldc + cb + c] = acc[c];
       }
     } else if (!ok) {
       if (lane == 0) fail();
@@ -612,20 +627,19 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
         tc_fence_after();
         const u64 ad = da0 + (u64)((st * 8 * A_TILE) >> 4);
         const u64 bd = db0 + (u64)(((int)(u & 1) * GM_BCHUNK) >> 4);
-        // with a_bits both K chunks go into the same accumulation (|C_s| <= 64 * 128), drained
-        // once per tile; otherwise every chunk is drained
+        // both K chunks of a tile go into one accumulation, drained once per tile
         const int kc = (int)(u & 1);
-        const bool first = !a_bits || kc == 0, last = !a_bits || kc == 1;
-        const long long v = a_bits ? (u >> 1) : u;   // accumulation index
+        const bool first = kc == 0, last = kc == 1;
+        const long long v = u >> 1;   // accumulation (tile) index
         if (first && v > 0 && !mbar_wait(&acce_bar[0], (unsigned)((v - 1) & 1), abort)) { fail(); break; }
         tc_fence_after();
         if (a_bits) issue_group<0, true>(tmem, ad, bd, first ? 1u : 0u);
-        else issue_group<0>(tmem, ad, bd);
+        else issue_group<0>(tmem, ad, bd, first ? 1u : 0u);
         if (last) mma_commit(&accf_bar[0]);
         if (first && v > 0 && !mbar_wait(&acce_bar[1], (unsigned)((v - 1) & 1), abort)) { fail(); break; }
         tc_fence_after();
         if (a_bits) issue_group<1, true>(tmem, ad, bd, first ? 1u : 0u);
-        else issue_group<1>(tmem, ad, bd);
+        else issue_group<1>(tmem, ad, bd, first ? 1u : 0u);
         if (last) mma_commit(&accf_bar[1]);
         mma_commit(&empty_bar[st]);
       }
@@ -640,46 +654,25 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
 #pragma unroll
     for (int c = 0; c < GM_DC; ++c) acc[c] = 0;
     bool ok = true;
-    const long long nacc = a_bits ? nunits / 2 : nunits;   // accumulations to drain
+    const long long nacc = nunits / 2;   // one accumulation per tile
     for (long long v = 0; v < nacc && ok; ++v) {
       const unsigned par = (unsigned)(v & 1);
-#pragma unroll
+#pragma unroll 1
       for (int g = 0; g < 2; ++g) {
         ok = __all_sync(0xffffffffu, mbar_wait(&accf_bar[g], par, abort));
         if (!ok) break;
         tc_fence_after();
-        const int s0 = g == 0 ? 0 : 2;
-        const int s1d = g == 0 ? 6 : 4;
 #pragma unroll
         for (int c16 = 0; c16 < GM_DC / 16; ++c16) {
-          unsigned x0[16], x1[16];
-          // pair (s0, s0 + 1): + ws (g = 0) or 2^16 ws (g = 1), ws sign-extended
-          tmem_ld16(tl + (unsigned)(acc_col(s0) + c16 * 16), x0);
-          tmem_ld16(tl + (unsigned)(acc_col(s0 + 1) + c16 * 16), x1);
-          tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const unsigned ws =
-                (unsigned)f2i_biased(x0[j]) + (unsigned)f2i_biased(x1[j]) * 256u - PAIR_BIAS;
-            acc[c16 * 16 + j] += g == 0 ? (u64)(long long)(int)ws : (u64)(long long)(int)ws << 16;
-          }
-          // pair (s1, s1 + 1): + 2^48 whi (g = 0) or 2^32 whi (g = 1); its bias is removed per tile
-          tmem_ld16(tl + (unsigned)(acc_col(s1d) + c16 * 16), x0);
-          tmem_ld16(tl + (unsigned)(acc_col(s1d + 1) + c16 * 16), x1);
-          tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const unsigned whi = (unsigned)f2i_biased(x0[j]) + (unsigned)f2i_biased(x1[j]) * 256u;
-            acc[c16 * 16 + j] += (u64)(g == 0 ? (whi << 16) : whi) << 32;
-          }
+          if (g == 0) drain16<0>(tl, c16 * 16, acc + c16 * 16);
+          else drain16<1>(tl, c16 * 16, acc + c16 * 16);
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&acce_bar[g]);
       }
-      if (ok && (a_bits || (v & 1))) {   // tile complete: remove the drains' biases, add, store
-        const long long r = (t0 + (a_bits ? v : v >> 1) * tstep) * TC_BM + q4 * 32 + lane;
-        const u64 corr = (u64)((a_bits ? 1u : 2u) * CHUNK_HI_BIAS) << 32;
+      if (ok) {   // tile complete: add add0, store
+        const long long r = (t0 + v * tstep) * TC_BM + q4 * 32 + lane;
         const long long ob = r < R ? rowmap(a.om, r) : a.out_lim;
         if (ob < a.out_lim) {
           const u64* a0p = a.add0 ? a.add0 + r * a.ld_add0 + h * GM_DC : nullptr;
@@ -692,8 +685,8 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
               a0v[q] = a0p ? *reinterpret_cast<const ulonglong2*>(a0p + c0 + 2 * q) : make_ulonglong2(0, 0);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-              *reinterpret_cast<ulonglong2*>(o + c0 + 2 * q) = make_ulonglong2(
-                  acc[c0 + 2 * q] - corr + a0v[q].x, acc[c0 + 2 * q + 1] - corr + a0v[q].y);
+              *reinterpret_cast<ulonglong2*>(o + c0 + 2 * q) =
+                  make_ulonglong2(acc[c0 + 2 * q] + a0v[q].x, acc[c0 + 2 * q + 1] + a0v[q].y);
             asm volatile("" ::: "memory");
           }
         }
@@ -829,14 +822,17 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
         tc_fence_after();
         const u64 ad = d0 + (u64)((st * STAGE) >> 4);
         const u64 bd = ad + (u64)((8 * A_TILE) >> 4);
-        if (u > 0 && !mbar_wait(&acce_bar[0], (unsigned)((u - 1) & 1), abort)) { fail(); break; }
+        // accumulation v takes chunks 2v and 2v + 1 (64 element pairs)
+        const bool first = !(u & 1), last = (u & 1) || u == nunits - 1;
+        const long long v = u >> 1;
+        if (first && v > 0 && !mbar_wait(&acce_bar[0], (unsigned)((v - 1) & 1), abort)) { fail(); break; }
         tc_fence_after();
-        issue_group<0>(tmem, ad, bd);
-        mma_commit(&accf_bar[0]);
-        if (u > 0 && !mbar_wait(&acce_bar[1], (unsigned)((u - 1) & 1), abort)) { fail(); break; }
+        issue_group<0>(tmem, ad, bd, first ? 1u : 0u);
+        if (last) mma_commit(&accf_bar[0]);
+        if (first && v > 0 && !mbar_wait(&acce_bar[1], (unsigned)((v - 1) & 1), abort)) { fail(); break; }
         tc_fence_after();
-        issue_group<1>(tmem, ad, bd);
-        mma_commit(&accf_bar[1]);
+        issue_group<1>(tmem, ad, bd, first ? 1u : 0u);
+        if (last) mma_commit(&accf_bar[1]);
         mma_commit(&empty_bar[st]);
       }
       mma_commit(&done_bar);
@@ -850,35 +846,18 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
 #pragma unroll
     for (int c = 0; c < GM_DC; ++c) acc[c] = 0;
     bool ok = true;
-    for (long long u = 0; u < nunits && ok; ++u) {
-      const unsigned pu = (unsigned)(u & 1);
-#pragma unroll
+    const long long nacc = (nunits + 1) / 2;
+    for (long long v = 0; v < nacc && ok; ++v) {
+      const unsigned pv = (unsigned)(v & 1);
+#pragma unroll 1
       for (int g = 0; g < 2; ++g) {
-        ok = __all_sync(0xffffffffu, mbar_wait(&accf_bar[g], pu, abort));
+        ok = __all_sync(0xffffffffu, mbar_wait(&accf_bar[g], pv, abort));
         if (!ok) break;
         tc_fence_after();
-        const int s0 = g == 0 ? 0 : 2;
-        const int s1d = g == 0 ? 6 : 4;
 #pragma unroll
         for (int c16 = 0; c16 < GM_DC / 16; ++c16) {
-          unsigned x0[16], x1[16];
-          tmem_ld16(tl + (unsigned)(acc_col(s0) + c16 * 16), x0);
-          tmem_ld16(tl + (unsigned)(acc_col(s0 + 1) + c16 * 16), x1);
-          tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const unsigned ws =
-                (unsigned)f2i_biased(x0[j]) + (unsigned)f2i_biased(x1[j]) * 256u - PAIR_BIAS;
-            acc[c16 * 16 + j] += g == 0 ? (u64)(long long)(int)ws : (u64)(long long)(int)ws << 16;
-          }
-          tmem_ld16(tl + (unsigned)(acc_col(s1d) + c16 * 16), x0);
-          tmem_ld16(tl + (unsigned)(acc_col(s1d + 1) + c16 * 16), x1);
-          tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const unsigned whi = (unsigned)f2i_biased(x0[j]) + (unsigned)f2i_biased(x1[j]) * 256u;
-            acc[c16 * 16 + j] += (u64)(g == 0 ? (whi << 16) : whi) << 32;
-          }
+          if (g == 0) drain16<0>(tl, c16 * 16, acc + c16 * 16);
+          else drain16<1>(tl, c16 * 16, acc + c16 * 16);
         }
         tc_fence_before();
         __syncwarp();
@@ -886,14 +865,13 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
       }
     }
     if (ok && !*abort && nunits > 0) {
-      const u64 corr = (u64)((unsigned)nunits * CHUNK_HI_BIAS) << 32;
       const int a = q4 * 32 + lane;                // tile row: x parity a / 64, coefficient a % 64
       const int xpar = a >> 6;
       // (x parity, y parity) -> P block: (0,0) -> 0, (1,1) -> 1, mixed -> 2
       u64* dst = P + (xpar == par ? xpar : 2) * 4096 + (a & 63) * 64 + h * GM_DC;
 #pragma unroll
       for (int c = 0; c < GM_DC; ++c)
-        atomicAdd(reinterpret_cast<unsigned long long*>(dst + c), (unsigned long long)(acc[c] - corr));
+        atomicAdd(reinterpret_cast<unsigned long long*>(dst + c), (unsigned long long)acc[c]);
     } else if (!ok && lane == 0) {
       fail();
     }
