@@ -69,7 +69,8 @@ int gr_matmul_tc(cudaStream_t st, long long R, const u64* p0, const u64* p1, u64
 struct GrRowMap {
   long long q, s1, s2;
 };
-// The general form: rows rho < R, A row rho at p0 + in(rho) (+ s1 p1 + in(rho)), or with a_bits
+// The general form: rows rho < R, A row rho at p0 + in(rho) (minus p1 + in(rho): s1 must be -1
+// when p1 is given; returns -1 otherwise), or with a_bits
 // the word p0[in(rho)]; matrix rho / mrows at Mmat + 4096 (rho / mrows) (mrows = 0: one matrix,
 // else a multiple of 128); out row rho at out + om(rho), written only when om(rho) < out_lim
 // (0: no limit); add0 row rho at add0 + rho ld_add0 (0: 64).

@@ -84,26 +84,22 @@ __host__ __device__ constexpr int group_s(int G, int g) { return G == 0 ? (g < 2
 template <int G>
 __device__ __forceinline__ void drain16(unsigned tl, int col, u64* acc) {
   constexpr int s0 = G == 0 ? 0 : 2, s1 = G == 0 ? 6 : 4;
-  unsigned x0[16], x1[16];
-  tmem_ld16(tl + (unsigned)(acc_col(s0) + col), x0);
-  tmem_ld16(tl + (unsigned)(acc_col(s0 + 1) + col), x1);
-  tmem_ld_wait();
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {   // + ws (G = 0) or 2^16 ws (G = 1), ws sign-extended
-    const unsigned ws =
-        (unsigned)f2i_biased(x0[j]) + (unsigned)f2i_biased(x1[j]) * 256u - PAIR_BIAS;
-    acc[j] += G == 0 ? (u64)(long long)(int)ws : (u64)(long long)(int)ws << 16;
-  }
-#pragma unroll
-  for (int h8 = 0; h8 < 16; h8 += 8) {   // + 2^48 whi (G = 0) or 2^32 whi (G = 1)
-    unsigned y0[8], y1[8];                // (8 columns at a time: conversions have long latency)
+  for (int h8 = 0; h8 < 16; h8 += 8) {   // 8 columns at a time (bounded register use)
+    unsigned x0[8], x1[8], y0[8], y1[8];
+    tmem_ld8(tl + (unsigned)(acc_col(s0) + col + h8), x0);
+    tmem_ld8(tl + (unsigned)(acc_col(s0 + 1) + col + h8), x1);
     tmem_ld8(tl + (unsigned)(acc_col(s1) + col + h8), y0);
     tmem_ld8(tl + (unsigned)(acc_col(s1 + 1) + col + h8), y1);
     tmem_ld_wait();
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
+      // + ws (G = 0) or 2^16 ws (G = 1), ws sign-extended; + 2^48 whi (G = 0) or 2^32 whi (G = 1)
+      const unsigned ws =
+          (unsigned)f2i_biased(x0[j]) + (unsigned)f2i_biased(x1[j]) * 256u - PAIR_BIAS;
       const unsigned whi = f32_int(y0[j]) + f32_int(y1[j]) * 256u;
-      acc[h8 + j] += (u64)(G == 0 ? (whi << 16) : whi) << 32;
+      acc[h8 + j] += (G == 0 ? (u64)(long long)(int)ws : (u64)(long long)(int)ws << 16) +
+                     ((u64)(G == 0 ? (whi << 16) : whi) << 32);
     }
   }
 }
@@ -427,7 +423,12 @@ constexpr int GM_DC = 256 / GM_NDRAIN;                    // columns per drain w
 constexpr int GM_PROD = 3;                                // producer warps
 constexpr int GM_THREADS = (GM_NDRAIN + GM_PROD + 1) * 32;   // 384
 constexpr int GM_BCHUNK = 8 * B_TILE;                     // 32 KB: B planes of one K chunk
-constexpr size_t GM_SMEM = (size_t)2 * GM_BCHUNK + (size_t)NSTAGE * 8 * A_TILE + 1024;
+// per drain warp: a 32-row x 4-column u64 block for the transposed (coalesced) stores, rows 48
+// bytes apart so that both the row-wise writes and the 16-byte-chunk reads are conflict-free
+constexpr int GM_OROW = 48;
+constexpr int GM_OSTAGE = 32 * GM_OROW;
+constexpr size_t GM_SMEM = (size_t)2 * GM_BCHUNK + (size_t)NSTAGE * 8 * A_TILE +
+                           (size_t)GM_NDRAIN * GM_OSTAGE + 1024;
 
 // byte offset of 16-byte unit u (8 f16 along K) of row r inside a K-major 64-byte-swizzled tile
 __device__ __forceinline__ int sw64_off(int r, int u) {
@@ -449,6 +450,7 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
       (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
   unsigned char* Bsm = base;                       // [2 chunks][8 planes][64 rows][64 B]
   unsigned char* Asm = base + 2 * GM_BCHUNK;       // [NSTAGE][8 planes][128 rows][64 B]
+  unsigned char* Osm = Asm + NSTAGE * 8 * A_TILE;  // [drain warp][32 rows][48 B]
   __shared__ __align__(8) u64 full_bar[NSTAGE], empty_bar[NSTAGE];
   __shared__ __align__(8) u64 accf_bar[2], acce_bar[2], done_bar;
   __shared__ unsigned tmem_slot;
@@ -498,58 +500,65 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
   };
 
   if (warp >= GM_NDRAIN && warp < GM_NDRAIN + GM_PROD) {
-    // ---- producers: B planes once, then the A planes of every (tile, chunk) ----
+    // ---- producers: B planes per matrix group, the A planes of every (tile, chunk) ----
     const int pt = tid - GM_NDRAIN * 32;   // 0 .. 32 GM_PROD - 1
     const long long lda = a.in.s1;           // A row (bit word) stride inside a tile
     bool ok = true;
     long long cur_m = -1;
-    for (long long u = 0; u < nunits && ok; ++u) {
+    // Before unit u is written: its stage must have been read by the MMAs of unit u - NSTAGE;
+    // at a tile's first chunk, B is rebuilt when the matrix group changes (after the previous
+    // tile's MMAs) and the next tile's rows are prefetched into L2.
+    auto begin_unit = [&](long long u) -> bool {
       const int st = (int)(u % NSTAGE);
-      if (u >= NSTAGE) {
-        ok = __all_sync(0xffffffffu,
-                        mbar_wait(&empty_bar[st], (unsigned)(((u / NSTAGE) + 1) & 1), abort));
-        if (!ok) break;
-      }
+      if (u >= NSTAGE &&
+          !__all_sync(0xffffffffu, mbar_wait(&empty_bar[st], (unsigned)(((u / NSTAGE) + 1) & 1), abort)))
+        return false;
+      if (u & 1) return true;
       const long long tile = t0 + (u >> 1) * tstep;
-      const int kc = (int)(u & 1);
       const long long rho0 = tile * TC_BM;
-      unsigned char* As = Asm + st * 8 * A_TILE;
-      if (kc == 0) {
-        const long long mi = a.mrows ? rho0 / a.mrows : 0;
-        if (mi != cur_m) {
-          // B = M^T of this tile's matrix; the previous tile's MMAs must have finished reading
-          if (u > 0) {
-            ok = __all_sync(0xffffffffu, mbar_wait(&empty_bar[(u - 1) % NSTAGE],
-                                                   (unsigned)(((u - 1) / NSTAGE) & 1), abort));
-            if (!ok) break;
-          }
-          const u64* Mm = a.Mmat + mi * 4096;
-          for (int it = pt; it < 64 * 8; it += GM_PROD * 32) {   // (row c of M^T, unit of 8 k)
-            const int c = it >> 3, k8 = it & 7;
-            u64 v[8];
+      const long long mi = a.mrows ? rho0 / a.mrows : 0;
+      if (mi != cur_m) {
+        if (u > 0 && !__all_sync(0xffffffffu, mbar_wait(&empty_bar[(u - 1) % NSTAGE],
+                                                         (unsigned)(((u - 1) / NSTAGE) & 1), abort)))
+          return false;
+        const u64* Mm = a.Mmat + mi * 4096;
+        for (int it = pt; it < 64 * 8; it += GM_PROD * 32) {   // (row c of M^T, unit of 8 k)
+          const int c = it >> 3, k8 = it & 7;
+          u64 v[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = Mm[(k8 * 8 + q) * 64 + c];
-            split8_store(v, Bsm + (k8 >> 2) * GM_BCHUNK, B_TILE, sw64_off(c, k8 & 3));
-          }
-          cur_m = mi;
+          for (int q = 0; q < 8; ++q) v[q] = Mm[(k8 * 8 + q) * 64 + c];
+          split8_store(v, Bsm + (k8 >> 2) * GM_BCHUNK, B_TILE, sw64_off(c, k8 & 3));
         }
-        if (pt == 0 && (u >> 1) + 1 < count && lda <= 128) {   // next tile's rows into L2
-          const long long r0 = (tile + tstep) * TC_BM;
-          const long long nr = (R - r0 < TC_BM) ? R - r0 : TC_BM;
-          const long long nb = rowmap(a.in, r0);
-          const long long words = (nr - 1) * lda + (a_bits ? 1 : 64);
-          const long long bytes = (words * 8) & ~15ll;   // whole 16-byte units inside the rows
-          for (int w2 = 0; w2 < (p1 ? 2 : 1); ++w2) {
-            const char* lo = reinterpret_cast<const char*>((w2 ? p1 : p0) + nb);
-            for (long long o = 0; o < bytes; o += 65536)
-              prefetch_l2(lo + o, (unsigned)(bytes - o < 65536 ? bytes - o : 65536));
-          }
+        cur_m = mi;
+      }
+      if (pt == 0 && (u >> 1) + 1 < count && lda <= 128) {   // next tile's rows into L2
+        const long long r0 = (tile + tstep) * TC_BM;
+        const long long nr = (R - r0 < TC_BM) ? R - r0 : TC_BM;
+        const long long nb = rowmap(a.in, r0);
+        const long long words = (nr - 1) * lda + (a_bits ? 1 : 64);
+        const long long bytes = (words * 8) & ~15ll;   // whole 16-byte units inside the rows
+        for (int w2 = 0; w2 < (p1 ? 2 : 1); ++w2) {
+          const char* lo = reinterpret_cast<const char*>((w2 ? p1 : p0) + nb);
+          for (long long o = 0; o < bytes; o += 65536)
+            prefetch_l2(lo + o, (unsigned)(bytes - o < 65536 ? bytes - o : 65536));
         }
       }
-      const long long ib = rowmap(a.in, rho0);   // word offset of the tile's first A row
+      return true;
+    };
+    auto end_unit = [&](long long u) {
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full_bar[u % NSTAGE]);
+    };
+    if (a_bits) {
       constexpr int NIT = (512 + GM_PROD * 32 - 1) / (GM_PROD * 32);   // items per thread
-      if (a_bits) {
-        // one word per item row: load all of this thread's words first (one latency per chunk)
+      for (long long u = 0; u < nunits; ++u) {
+        if (!(ok = begin_unit(u))) break;
+        const long long rho0 = (t0 + (u >> 1) * tstep) * TC_BM;
+        const int kc = (int)(u & 1);
+        const long long ib = rowmap(a.in, rho0);   // word index of the tile's first bit word
+        unsigned char* As = Asm + (u % NSTAGE) * 8 * A_TILE;
+        // one word per item row: all of this thread's words first (one latency per chunk)
         u64 wd[NIT];
 #pragma unroll
         for (int q = 0; q < NIT; ++q) {
@@ -565,55 +574,70 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
             *reinterpret_cast<uint4*>(As + sw64_off(item >> 2, item & 3)) = bits_plane0(by);
           }
         }
-      } else {
-        // a round's loads are all issued before the first is used: one memory latency per
-        // round, one round per chunk (two when p1 doubles the loads)
-        auto round = [&](auto nq, auto q0c, auto with_p1) {
-          constexpr int NQ = decltype(nq)::value, Q0 = decltype(q0c)::value;
-          constexpr bool P1 = decltype(with_p1)::value;
-          u64 v[NQ][8], w[P1 ? NQ : 1][8];
+        end_unit(u);
+      }
+    } else {
+      // A rows in rounds of NQ items (8 words each) per thread, RPU rounds per unit; the loads
+      // of round k + 1 are in flight while round k is split into the stage, across unit ends
+      auto stream = [&](auto nqc, auto p1c) {
+        constexpr int NQ = decltype(nqc)::value;
+        constexpr bool P1 = decltype(p1c)::value;
+        constexpr int RPU = (512 + NQ * GM_PROD * 32 - 1) / (NQ * GM_PROD * 32);
+        const long long nrounds = nunits * RPU;
+        u64 cv[NQ][8], nv[NQ][8], nw[NQ][8];   // current round (p0 - p1 formed), next round
+        auto issue = [&](long long k, u64 (&v)[NQ][8], u64 (&w)[NQ][8]) {
+          const long long u = k / RPU;
+          const int r = (int)(k - u * RPU);
+          const long long rho0 = (t0 + (u >> 1) * tstep) * TC_BM;
+          const long long ib = rowmap(a.in, rho0) + (u & 1) * 32;
 #pragma unroll
           for (int q = 0; q < NQ; ++q) {
-            const int item = pt + (Q0 + q) * GM_PROD * 32;   // 512 items: (row, unit of 8 k)
+            const int item = pt + (r * NQ + q) * GM_PROD * 32;   // (row, unit of 8 k)
             const bool in = item < 512 && rho0 + (item >> 2) < R;
-            const long long off = ib + (item >> 2) * lda + kc * 32 + (item & 3) * 8;
+            const long long off = ib + (item >> 2) * lda + (item & 3) * 8;
 #pragma unroll
             for (int j = 0; j < 8; j += 2) {
-              const ulonglong2 a =
+              const ulonglong2 x =
                   in ? *reinterpret_cast<const ulonglong2*>(p0 + off + j) : make_ulonglong2(0, 0);
-              v[q][j] = a.x;
-              v[q][j + 1] = a.y;
+              v[q][j] = x.x;
+              v[q][j + 1] = x.y;
               if (P1) {
-                const ulonglong2 b =
+                const ulonglong2 y =
                     in ? *reinterpret_cast<const ulonglong2*>(p1 + off + j) : make_ulonglong2(0, 0);
-                w[P1 ? q : 0][j] = b.x;
-                w[P1 ? q : 0][j + 1] = b.y;
+                w[q][j] = y.x;
+                w[q][j + 1] = y.y;
               }
             }
           }
+        };
+        // the next round becomes the current one (the subtraction waits for its loads)
+        auto take_next = [&]() {
+#pragma unroll
+          for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) cv[q][j] = P1 ? nv[q][j] - nw[q][j] : nv[q][j];
+        };
+        if (nrounds > 0) {
+          issue(0, nv, nw);
+          take_next();
+        }
+        for (long long k = 0; k < nrounds; ++k) {
+          const long long u = k / RPU;
+          const int r = (int)(k - u * RPU);
+          if (k + 1 < nrounds) issue(k + 1, nv, nw);
+          if (r == 0 && !(ok = begin_unit(u))) break;
+          unsigned char* As = Asm + (u % NSTAGE) * 8 * A_TILE;
 #pragma unroll
           for (int q = 0; q < NQ; ++q) {
-            const int item = pt + (Q0 + q) * GM_PROD * 32;
-            if (P1) {
-#pragma unroll
-              for (int j = 0; j < 8; ++j) v[q][j] += s1 * w[P1 ? q : 0][j];
-            }
-            if (item < 512) split8_store(v[q], As, A_TILE, sw64_off(item >> 2, item & 3));
+            const int item = pt + (r * NQ + q) * GM_PROD * 32;
+            if (item < 512) split8_store(cv[q], As, A_TILE, sw64_off(item >> 2, item & 3));
           }
-        };
-        using I0 = std::integral_constant<int, 0>;
-        if (p1) {
-          constexpr int H = (NIT + 1) / 2;
-          round(std::integral_constant<int, H>(), I0(), std::true_type());
-          round(std::integral_constant<int, NIT - H>(), std::integral_constant<int, H>(),
-                std::true_type());
-        } else {
-          round(std::integral_constant<int, NIT>(), I0(), std::false_type());
+          if (r == RPU - 1) end_unit(u);
+          if (k + 1 < nrounds) take_next();
         }
-      }
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&full_bar[st]);
+      };
+      if (p1) stream(std::integral_constant<int, 2>(), std::true_type());
+      else stream(std::integral_constant<int, 3>(), std::false_type());
     }
     if (!ok && lane == 0) fail();
   } else if (warp == GM_NDRAIN + GM_PROD) {
@@ -671,24 +695,49 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
         __syncwarp();
         if (lane == 0) mbar_arrive(&acce_bar[g]);
       }
-      if (ok) {   // tile complete: add add0, store
+      if (ok) {   // tile complete: add add0, store (4 columns at a time through shared memory)
         const long long r = (t0 + v * tstep) * TC_BM + q4 * 32 + lane;
-        const long long ob = r < R ? rowmap(a.om, r) : a.out_lim;
-        if (ob < a.out_lim) {
-          const u64* a0p = a.add0 ? a.add0 + r * a.ld_add0 + h * GM_DC : nullptr;
-          u64* o = a.out + ob + h * GM_DC;
+        const long long ob = r < R ? rowmap(a.om, r) : -1;   // this lane's row: word offset
+        const bool live = ob >= 0 && ob < a.out_lim;
+        // the rows this lane stores in the two passes (16 rows per pass, 2 lanes per row)
+        long long obr[2], rg[2];
 #pragma unroll
-          for (int c0 = 0; c0 < GM_DC; c0 += 8) {   // 8 columns at a time (bounded live range)
-            ulonglong2 a0v[4];
+        for (int pass = 0; pass < 2; ++pass) {
+          const int rr = pass * 16 + (lane >> 1);
+          obr[pass] = __shfl_sync(0xffffffffu, live ? ob : -1, rr);
+          rg[pass] = __shfl_sync(0xffffffffu, r, rr);
+        }
+        unsigned char* os = Osm + warp * GM_OSTAGE;
+        // add0 words of the stored 16-byte chunks, loaded before the first store (one latency)
+        ulonglong2 ad[GM_DC / 4][2];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-              a0v[q] = a0p ? *reinterpret_cast<const ulonglong2*>(a0p + c0 + 2 * q) : make_ulonglong2(0, 0);
+        for (int c0 = 0; c0 < GM_DC; c0 += 4)
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-              *reinterpret_cast<ulonglong2*>(o + c0 + 2 * q) =
-                  make_ulonglong2(acc[c0 + 2 * q] + a0v[q].x, acc[c0 + 2 * q + 1] + a0v[q].y);
-            asm volatile("" ::: "memory");
+          for (int pass = 0; pass < 2; ++pass) {
+            const long long col = h * GM_DC + c0 + 2 * (lane & 1);
+            ad[c0 / 4][pass] = (a.add0 && obr[pass] >= 0)
+                                   ? *reinterpret_cast<const ulonglong2*>(a.add0 + rg[pass] * a.ld_add0 + col)
+                                   : make_ulonglong2(0, 0);
           }
+#pragma unroll
+        for (int c0 = 0; c0 < GM_DC; c0 += 4) {
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+            *reinterpret_cast<ulonglong2*>(os + lane * GM_OROW + q * 16) =
+                make_ulonglong2(acc[c0 + 2 * q], acc[c0 + 2 * q + 1]);
+          __syncwarp();
+#pragma unroll
+          for (int pass = 0; pass < 2; ++pass) {
+            const int rr = pass * 16 + (lane >> 1), ch = lane & 1;
+            ulonglong2 w = *reinterpret_cast<const ulonglong2*>(os + rr * GM_OROW + ch * 16);
+            if (obr[pass] >= 0) {
+              const long long col = h * GM_DC + c0 + 2 * ch;
+              w.x += ad[c0 / 4][pass].x;
+              w.y += ad[c0 / 4][pass].y;
+              *reinterpret_cast<ulonglong2*>(a.out + obr[pass] + col) = w;
+            }
+          }
+          __syncwarp();
         }
 #pragma unroll
         for (int c = 0; c < GM_DC; ++c) acc[c] = 0;
@@ -925,6 +974,7 @@ int gr_matmul_tc_ex(cudaStream_t st, const GrMMArgs& args, unsigned* err, unsign
   GrMMArgs a = args;
   if (a.R <= 0) return 0;
   if (a.add0 && !a.ld_add0) a.ld_add0 = 64;
+  if (a.p1 && a.s1 != ~0ull) return -1;   // the kernel forms p0 - p1 only
   auto odd = [](long long v) { return (v & 1) != 0; };
   const bool bad_in = !a.a_bits && (odd(a.in.s1) || odd(a.in.s2));
   // 16-byte vector accesses need even word offsets; a tile must not straddle a map period or
