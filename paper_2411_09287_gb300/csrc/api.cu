@@ -831,7 +831,7 @@ VMatPlan plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R
     p.S_hi = a.take<u64>(p.nhi * 4096 * 64);
     p.Pst = a.take<u64>(64ll * 262144);
     p.Thi = a.take<u64>(p.nhi * 64);
-    p.Mhi = a.take<u64>(4096);
+    p.Mhi = a.take<u64>(std::max<long long>(1, p.nhi - 1) * 4096);
     p.Zpq = a.take<u64>(12 * 64);
     p.V = a.take<u64>(4096);
     p.W = a.take<u64>(4096);
@@ -1271,12 +1271,28 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
     if (p.nhi > 1) {
       launch_gr_mul1(st, p.Rtab + (p.L - 1) * 64, s.aux + 64, s.aux + 128);   // r^(2L)
       launch_gr_powers(st, s.aux + 128, p.nhi, p.Thi);
-      for (long long h = 1; h < p.nhi; ++h) {
-        launch_gr_mulmat2(st, p.Thi + h * 64, nullptr, p.Mhi);
-        if ((rc = gr_matmul(ctx, p.L, p.Rtab, nullptr, 1, 64, p.Mhi, nullptr, 0,
+      // rows h L + e_lo (h >= 1) = r^(2 L h) r^(2 e_lo): one grouped product, matrix h - 1 for
+      // the rows (h - 1) L .. h L - 1 of the block, each reading row e_lo of the first block
+      launch_gr_mulmat_batch(st, p.nhi - 1, p.Thi + 64, 64, p.Mhi);
+      bool done = false;
+      if (ctx->gemm_path == MPC_GEMM_LIMB_TC) {
+        GrMMArgs g{};
+        g.R = (p.nhi - 1) * p.L;
+        g.p0 = p.Rtab;
+        g.in = GrRowMap{p.L, 64, 0};
+        g.Mmat = p.Mhi;
+        g.mrows = p.L;
+        g.out = p.Rtab + p.L * 64;
+        g.om = GrRowMap{0, 64, 0};
+        g_launches += 1;
+        Phase kp(ctx, MPC_PROF_K_GR_MATMUL, (double)g.R * 4096);
+        done = gr_matmul_tc_ex(st, g, ctx->status, ST_TIMEOUT) == 0;
+        if (!done) g_launches -= 1;
+      }
+      for (long long h = 1; h < p.nhi && !done; ++h)
+        if ((rc = gr_matmul(ctx, p.L, p.Rtab, nullptr, 1, 64, p.Mhi + (h - 1) * 4096, nullptr, 0,
                             p.Rtab + h * p.L * 64, 64)))
           return rc;
-      }
     }
     CK(cudaMemsetAsync(p.Zpq, 0, 12 * 64 * 8, st));
     // sum_e r^(2e) p_c[e], sum_e r^(2e) q_c[e]: (12 x E) . (E x 64)

@@ -553,39 +553,45 @@ k_gr_mul_rows(long long n, const u64* __restrict__ a, const u64* __restrict__ b,
 
 // out[c] += sum_{e < n} A[c][e] * R[e] for c < nrows <= 16: GR elements R[e] (rows of 64 words)
 // scaled by ring scalars and summed (e.g. sum_e r^(2e) p_c[e] for the truncation batch).  Each
-// block takes a contiguous slice of e; thread (t, cg) owns coefficient t of rows c = cg, cg + 4, ..;
-// the block's slice of A is staged in shared memory 64 e at a time; partial sums are added
-// atomically at the end.
+// block takes a contiguous slice of e, 256 e at a time: the slice of A is staged in shared memory
+// as [e][c] (a broadcast read per e), and each 64-thread group takes 64 of the 256 e, thread t
+// coefficient t of every row c; partial sums are added atomically at the end.
+template <int NR>
 __global__ void __launch_bounds__(256)
 k_scalar_gr_sum(long long n, const u64* __restrict__ A, long long lda, int nrows,
                 const u64* __restrict__ R, u64* __restrict__ out) {
-  __shared__ u64 as[16][64];
-  const int t = threadIdx.x & 63, cg = threadIdx.x >> 6;
+  __shared__ __align__(16) u64 as[256][NR];
+  const int t = threadIdx.x & 63, grp = threadIdx.x >> 6;
   const long long per = (n + gridDim.x - 1) / gridDim.x;
   const long long e0 = per * blockIdx.x;
   const long long e1 = (e0 + per < n) ? e0 + per : n;
-  u64 acc[4] = {0, 0, 0, 0};
-  for (long long eb = e0; eb < e1; eb += 64) {
-    const int cnt = (int)((e1 - eb < 64) ? e1 - eb : 64);
+  u64 acc[NR];
+#pragma unroll
+  for (int c = 0; c < NR; ++c) acc[c] = 0;
+  for (long long eb = e0; eb < e1; eb += 256) {
     __syncthreads();
-    for (int i = threadIdx.x; i < nrows * 64; i += blockDim.x) {
-      const int c = i >> 6, k = i & 63;
-      as[c][k] = (k < cnt) ? A[c * lda + eb + k] : 0ull;
+    for (int i = threadIdx.x; i < NR * 256; i += 256) {
+      const int c = i >> 8, k = i & 255;
+      as[k][c] = (c < nrows && eb + k < e1) ? A[c * lda + eb + k] : 0ull;
     }
     __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < cnt; ++k) {
-      const u64 r = R[(eb + k) * 64 + t];
+    const int kmax = (int)((e1 - eb - grp * 64 < 64) ? e1 - eb - grp * 64 : 64);
+#pragma unroll 2
+    for (int k = 0; k < kmax; ++k) {
+      const int kk = grp * 64 + k;
+      const u64 r = R[(eb + kk) * 64 + t];
 #pragma unroll
-      for (int m = 0; m < 4; ++m)
-        if (cg + 4 * m < nrows) acc[m] += as[cg + 4 * m][k] * r;
+      for (int c = 0; c < NR; c += 2) {
+        const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(&as[kk][c]);
+        acc[c] += w.x * r;
+        acc[c + 1] += w.y * r;
+      }
     }
   }
 #pragma unroll
-  for (int m = 0; m < 4; ++m)
-    if (cg + 4 * m < nrows)
-      atomicAdd(reinterpret_cast<unsigned long long*>(out + (cg + 4 * m) * 64 + t),
-                (unsigned long long)acc[m]);
+  for (int c = 0; c < NR; ++c)
+    if (c < nrows)
+      atomicAdd(reinterpret_cast<unsigned long long*>(out + c * 64 + t), (unsigned long long)acc[c]);
 }
 
 // ---- fused small steps (single GR elements) -----------------------------------------------
@@ -843,7 +849,10 @@ void launch_scalar_gr_sum(cudaStream_t st, long long n, const u64* A, long long 
   if (n <= 0 || nrows <= 0) return;
   long long g = (n + 4095) / 4096;
   if (g > 152 * 8) g = 152 * 8;
-  k_scalar_gr_sum<<<(unsigned)g, 256, 0, st>>>(n, A, lda, nrows, R, out);
+  if (nrows <= 12)
+    k_scalar_gr_sum<12><<<(unsigned)g, 256, 0, st>>>(n, A, lda, nrows, R, out);
+  else
+    k_scalar_gr_sum<16><<<(unsigned)g, 256, 0, st>>>(n, A, lda, nrows, R, out);
 }
 
 }  // namespace mpc3

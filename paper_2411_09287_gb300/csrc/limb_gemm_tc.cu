@@ -811,54 +811,74 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
     // items (y rows b = item % 64, k8 = item / 64), lanes on consecutive coefficients ----
     const int pt = tid - GM_NDRAIN * 32;
     constexpr int NITEM = 768;
-    constexpr int NIT = (NITEM + GM_PROD * 32 - 1) / (GM_PROD * 32);
+    // rounds of NQ items per thread, RPU rounds per unit; the loads of round k + 1 are in flight
+    // while round k is split into the stage, across unit ends
+    constexpr int NQ = 2;
+    constexpr int RPU = (NITEM + NQ * GM_PROD * 32 - 1) / (NQ * GM_PROD * 32);
+    const long long nrounds = nunits * RPU;
     bool ok = true;
-    for (long long u = 0; u < nunits && ok; ++u) {
-      const int st = (int)(u % NSTAGE);
-      if (u >= NSTAGE) {
-        ok = __all_sync(0xffffffffu,
-                        mbar_wait(&empty_bar[st], (unsigned)(((u / NSTAGE) + 1) & 1), abort));
-        if (!ok) break;
+    u64 cv[NQ][8], nv[NQ][8];
+    auto issue = [&](long long k, u64 (&v)[NQ][8]) {
+      const long long u = k / RPU;
+      const int r = (int)(k - u * RPU);
+      const long long i0 = (c0 + u) * TC_BK;   // first element pair of the chunk
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int item = pt + (r * NQ + q) * GM_PROD * 32;
+        const bool isA = item < 512;
+        const int it = isA ? item : item - 512;
+        const int row = isA ? (it & 127) : (it & 63);
+        const int k8 = isA ? (it >> 7) : (it >> 6);
+        // A row a: coefficient a % 64 of x_{2i + a / 64}; B row b: coefficient b of y_{2i + par}
+        const u64* src = isA ? x + (row >> 6) * 64 + (row & 63) : y + par * 64 + row;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const long long i = i0 + k8 * 8 + j;
+          v[q][j] = (item < NITEM && i < Dh) ? src[i * 128] : 0ull;
+        }
       }
-      const long long i0 = (c0 + u) * TC_BK;       // first element pair of the chunk
-      if (pt == 0 && u + 1 < nunits) {             // next chunk's 32 pairs (64 rows) of x and y
-        const long long i1 = i0 + TC_BK;
-        const long long np = (Dh - i1 < TC_BK) ? Dh - i1 : TC_BK;
-        if (np > 0) {
-          prefetch_l2(x + i1 * 128, (unsigned)(np * 1024));
-          prefetch_l2(y + i1 * 128, (unsigned)(np * 1024));
+    };
+    if (nrounds > 0) issue(0, cv);
+    for (long long k = 0; k < nrounds; ++k) {
+      const long long u = k / RPU;
+      const int r = (int)(k - u * RPU);
+      const int st = (int)(u % NSTAGE);
+      if (k + 1 < nrounds) issue(k + 1, nv);
+      if (r == 0) {
+        if (u >= NSTAGE &&
+            !(ok = __all_sync(0xffffffffu,
+                              mbar_wait(&empty_bar[st], (unsigned)(((u / NSTAGE) + 1) & 1), abort))))
+          break;
+        const long long i1 = (c0 + u + 1) * TC_BK;
+        if (pt == 0 && u + 1 < nunits) {   // next chunk's 32 pairs (64 rows) of x and y
+          const long long np = (Dh - i1 < TC_BK) ? Dh - i1 : TC_BK;
+          if (np > 0) {
+            prefetch_l2(x + i1 * 128, (unsigned)(np * 1024));
+            prefetch_l2(y + i1 * 128, (unsigned)(np * 1024));
+          }
         }
       }
       unsigned char* As = base + st * STAGE;
-      unsigned char* Bs = As + 8 * A_TILE;
 #pragma unroll
-      for (int q0 = 0; q0 < NIT; q0 += 4) {         // four items' loads in flight per thread
-        u64 v[4][8];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int item = pt + (q0 + q) * GM_PROD * 32;
+      for (int q = 0; q < NQ; ++q) {
+        const int item = pt + (r * NQ + q) * GM_PROD * 32;
+        if (item < NITEM) {
           const bool isA = item < 512;
           const int it = isA ? item : item - 512;
-          const int row = isA ? (it & 127) : (it & 63);
-          const int k8 = isA ? (it >> 7) : (it >> 6);
-          // A row a: coefficient a % 64 of x_{2i + a / 64}; B row b: coefficient b of y_{2i + par}
-          const u64* src = isA ? x + (row >> 6) * 64 + (row & 63) : y + par * 64 + row;
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const long long i = i0 + k8 * 8 + j;
-            v[q][j] = (item < NITEM && i < Dh) ? src[i * 128] : 0ull;
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int item = pt + (q0 + q) * GM_PROD * 32;
-          if (item < 512) split8_store(v[q], As, A_TILE, sw64_off(item & 127, item >> 7));
-          else if (item < NITEM) split8_store(v[q], Bs, B_TILE, sw64_off((item - 512) & 63, (item - 512) >> 6));
+          unsigned char* dst = isA ? As : As + 8 * A_TILE;
+          const int off = isA ? sw64_off(it & 127, it >> 7) : sw64_off(it & 63, it >> 6);
+          split8_store(cv[q], dst, isA ? A_TILE : B_TILE, off);
         }
       }
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&full_bar[st]);
+      if (r == RPU - 1) {
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full_bar[st]);
+      }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) cv[q][j] = nv[q][j];
     }
     if (!ok && lane == 0) fail();
   } else if (warp == GM_NDRAIN + GM_PROD) {
