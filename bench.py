@@ -178,12 +178,12 @@ def run_reference(args, rank: int, world: int):
 # proportion to E (operand digit planes, folded vectors, bit words, tables), so the bench scales
 # the figure by E / 2^20.  The summaries, with the commands that produced them: profiles/.
 NCU_TRAFFIC_E = 2 ** 20
-NCU_TRAFFIC = {   # bytes per step at E = 2^20 (profiles/traffic_verify_kernels_n1024.md)
-    "k_trunc_s": 0.419e9,
-    "k_limb_gemm": 0.485e9,
-    "k_gr_matmul": None,   # changed since the capture
-    "k_gram": None,
-    "k_gr_mul_rows": 3.138e9,
+NCU_TRAFFIC = {   # bytes per step at E = 2^20 (profiles/traffic_gr_kernels_n1024.md)
+    "k_trunc_s": 0.418e9,
+    "k_limb_gemm": 0.484e9,
+    "k_gr_matmul": 10.602e9,
+    "k_gram": 2.151e9,
+    "k_gr_mul_rows": None,   # not launched at these sizes (the tensor-core form replaces it)
 }
 ALU_NOTE = "peak derived: 152 SMs x 64 IMAD/clk x max SM clock; a u64 MAC is 3 IMAD"
 
