@@ -799,10 +799,18 @@ VMatPlan plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R
   VMatPlan p;
   p.R0 = R0 < 0 ? default_R(K) : R0;
   p.s = plan_small(a);
-  // digit planes of the batch-0 products (X^T P, W Q, Z Q) on the tensor-core path
+  // digit planes of the batch-0 products (X^T P, W Q, Z Q) and of the truncation batch's S_hi
+  // combination (64 x 262144 x nhi) on the tensor-core path
+  long long nhi_tc = 0;
+  if (t >= 0) {
+    const long long E = M * N, L = E >= 65536 ? 65536 : ((E + 127) / 128) * 128;
+    nhi_tc = (E + L - 1) / L;
+    if (nhi_tc < 32) nhi_tc = 0;   // short combinations stay on the CUDA cores (no plane scratch)
+  }
   p.tcs = tc ? (void*)a.take<unsigned char>((long long)std::max(
                    {limb_tc_scratch_bytes(K, 64, M, 1), limb_tc_scratch_bytes(K, 64, N, 1),
-                    limb_tc_scratch_bytes(6 * M, 64, N, 1)}))
+                    limb_tc_scratch_bytes(6 * M, 64, N, 1),
+                    nhi_tc ? limb_tc_scratch_bytes(64, 262144, nhi_tc, 1) : (size_t)0}))
              : nullptr;
   p.Q = a.take<u64>(N * 64);
   p.P = a.take<u64>(M * 64);
@@ -1318,7 +1326,9 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
       GemmTerm T;
       T.A = op(p.Rtab, p.L * 64, 1);       // A[a][e_hi] = coefficient a of r^(2 L e_hi)
       T.B = op(p.S_hi, 262144);            // B[e_hi][(p, b)]
-      gemm_u64(st, 64, 262144, p.nhi, 1, &T, epi_store(p.Pst, 262144), 1);
+      if ((rc = dense_gemm(ctx, 64, 262144, p.nhi, T, epi_store(p.Pst, 262144),
+                           p.nhi >= 32 ? p.tcs : nullptr)))
+        return rc;
       launch_fold_reduce_strided(st, p.Pst, 262144, 4096, p.S);
     }
     delete phase;

@@ -133,6 +133,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 k_limb_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                long long M, long long N, long long Kp, u64* __restrict__ C, long long ldc,
                unsigned* __restrict__ err, unsigned err_flag) {
+  // split K over gridDim.z: this CTA takes chunks [cbeg, cbeg + nchunks); with more than one
+  // split the partial tiles are added atomically into C (zeroed by the host)
   extern __shared__ unsigned char dsm[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
@@ -146,7 +148,10 @@ k_limb_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   const int warp = tid >> 5, lane = tid & 31;
   const long long m0 = (long long)blockIdx.x * TC_BM;
   const long long n0 = (long long)blockIdx.y * TC_BN;
-  const int nchunks = (int)(Kp / TC_BK);
+  const int nall = (int)(Kp / TC_BK);
+  const int cbeg = (int)((long long)nall * blockIdx.z / gridDim.z);
+  const int nchunks = (int)((long long)nall * (blockIdx.z + 1) / gridDim.z) - cbeg;
+  const bool split = gridDim.z > 1;
 
   if (tid == 0) {
     for (int i = 0; i < NSTAGE; ++i) {
@@ -190,7 +195,7 @@ k_limb_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         unsigned char* As = base + st * STAGE;
         unsigned char* Bs = As + 8 * A_TILE;
         mbar_expect_tx(&full_bar[st], (unsigned)STAGE);
-        const int kx = c * TC_BK;
+        const int kx = (cbeg + c) * TC_BK;
 #pragma unroll 1
         for (int i = 0; i < 8; ++i) {
           tma_load_3d(As + i * A_TILE, &tmA, &full_bar[st], kx, (int)m0, i);
@@ -256,13 +261,37 @@ k_limb_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       }
     }
     if (ok && !*abort) {
+      // through a per-warp 32-row x 4-column block of shared memory, so that every store (or
+      // atomic) instruction covers 16 rows x 32 contiguous bytes
       const long long r = m0 + q * 32 + lane;
       const long long cb = n0 + h * 32;
-      if (r < M) {
+      unsigned char* os = base + NSTAGE * STAGE + warp * (32 * 48);
 #pragma unroll
-        for (int c = 0; c < 32; ++c)
-          if (cb + c < N) C[r * ldc + cb + c] = acc[c];
+      for (int c0 = 0; c0 < 32; c0 += 4) {
+#pragma unroll
+        for (int qq = 0; qq < 2; ++qq)
+          *reinterpret_cast<ulonglong2*>(os + lane * 48 + qq * 16) =
+              make_ulonglong2(acc[c0 + 2 * qq], acc[c0 + 2 * qq + 1]);
+        __syncwarp();
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+          const int rr = pass * 16 + (lane >> 1), ch = lane & 1;
+          const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(os + rr * 48 + ch * 16);
+          const long long row = m0 + q * 32 + rr, col = cb + c0 + 2 * ch;
+          if (row < M) {
+            u64* dst = C + row * ldc + col;
+            if (split) {
+              if (col < N) atomicAdd(reinterpret_cast<unsigned long long*>(dst), (unsigned long long)w.x);
+              if (col + 1 < N) atomicAdd(reinterpret_cast<unsigned long long*>(dst + 1), (unsigned long long)w.y);
+            } else {
+              if (col < N) dst[0] = w.x;
+              if (col + 1 < N) dst[1] = w.y;
+            }
+          }
+        }
+        __syncwarp();
       }
+      (void)r;
     } else if (!ok) {
       if (lane == 0) fail();
     }
@@ -977,9 +1006,23 @@ int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nte
   k_split_digits<<<(unsigned)gb, tpb, 0, st>>>(terms[0], t1, nterms, 1, N, K, Kp, Bp);
   CUtensorMap ma, mb;
   if (!make_map(&ma, Ap, M, Kp, TC_BM) || !make_map(&mb, Bp, N, Kp, TC_BN)) return -2;
-  const size_t smem = (size_t)NSTAGE * STAGE + 1024;
+  const size_t smem = (size_t)NSTAGE * STAGE + (size_t)NDRAIN * 32 * 48 + 1024;
   set_max_dynamic_smem(reinterpret_cast<const void*>(k_limb_gemm_tc), (int)smem);
-  dim3 grid((unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)((N + TC_BN - 1) / TC_BN));
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 148;
+  }
+  const long long tiles = ((M + TC_BM - 1) / TC_BM) * ((N + TC_BN - 1) / TC_BN);
+  const long long nch = Kp / TC_BK;
+  // thin products: split K (at least 8 chunks each) while the CTAs still fit one wave
+  long long nsplit = 1;
+  while (tiles * nsplit * 2 <= nsm && nch / (nsplit * 2) >= 8) nsplit *= 2;
+  if (nsplit > 1) cudaMemset2DAsync(epi.out, (size_t)epi.ldc * 8, 0, (size_t)N * 8, (size_t)M, st);
+  dim3 grid((unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)((N + TC_BN - 1) / TC_BN),
+            (unsigned)nsplit);
   if (ev0) cudaEventRecord(ev0, st);
   k_limb_gemm_tc<<<grid, TC_THREADS, smem, st>>>(ma, mb, M, N, Kp, epi.out, epi.ldc, err, err_flag);
   if (ev1) cudaEventRecord(ev1, st);

@@ -202,12 +202,14 @@ def test_tc_gemm_full_range_words(mpc, M, N, K):
     assert_shared_equal(gpu_shared(mpc, zpre, (M, N)), res.z_pre, "zpre")
 
 
-@pytest.mark.parametrize("M,N,K", [(300, 300, 16), (64, 1100, 8)])
+@pytest.mark.parametrize("M,N,K", [(300, 300, 16), (64, 1100, 8), (2048, 1024, 16)])
 def test_tc_and_u64_paths_give_identical_verification(mpc, M, N, K):
     """At sizes whose trunc batch spans several e_hi blocks (E > 65536) and many row tiles, the
-    tensor-core path (limb GEMMs, tensor-core folds and table products) and the u64 CUDA-core
-    path give the same products, the same verification transcript and the same opened output;
-    both paths are pinned to the oracle on the smaller shapes above."""
+    tensor-core path (limb GEMMs, tensor-core folds and table products, the grouped products of
+    the r^(2e) factor; at E = 2^21 also the tensor-core S_hi combination and split-K batch-0
+    products) and the u64 CUDA-core path give the same products, the same verification
+    transcript and the same opened output; both paths are pinned to the oracle on the smaller
+    shapes above."""
     seed = seed_of(f"paths-{M}-{N}-{K}")
     g = workloads.rng(f"paths-{M}-{N}-{K}")
     X = mpc.encode_fixed(g.uniform(-4, 4, (M, K)), 13)
@@ -225,9 +227,8 @@ def test_tc_and_u64_paths_give_identical_verification(mpc, M, N, K):
     assert np.array_equal(res[0][1], res[1][1])
     assert np.array_equal(res[0][2], res[1][2])
     # the opened product is the plaintext product, truncated (one-LSB carry allowed)
-    Z = (X.astype(object) @ W.astype(object))
-    ref = np.array([[(int(v) % 2**64) for v in row] for row in Z], dtype=np.uint64)
-    sref = ref.view(np.int64) >> 13
+    # |entries| < 2^15 and K <= 16, so the int64 product is exact
+    sref = (X.view(np.int64) @ W.view(np.int64)) >> 13
     got = res[1][2].reshape(M, N).view(np.int64)
     assert np.all(np.abs(got - sref) <= 1)
 
