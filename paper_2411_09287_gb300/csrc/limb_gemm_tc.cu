@@ -104,10 +104,33 @@ __device__ __forceinline__ void drain16(unsigned tl, int col, u64* acc) {
   }
 }
 
+// The same for the merged pairs of a bit-operand product: accumulator s (s even) holds
+// C_s + 2^8 C_(s+1) (|.| < 2^22, the magic-number pattern suffices).
+template <int G>
+__device__ __forceinline__ void drain16_pairs(unsigned tl, int col, u64* acc) {
+  constexpr int s0 = G == 0 ? 0 : 2, s1 = G == 0 ? 6 : 4;
+#pragma unroll
+  for (int h8 = 0; h8 < 16; h8 += 8) {
+    unsigned x0[8], y0[8];
+    tmem_ld8(tl + (unsigned)(acc_col(s0) + col + h8), x0);
+    tmem_ld8(tl + (unsigned)(acc_col(s1) + col + h8), y0);
+    tmem_ld_wait();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const unsigned ws = (unsigned)f2i_biased(x0[j]) - MAGIC_I;
+      const unsigned whi = (unsigned)f2i_biased(y0[j]) - MAGIC_I;
+      acc[h8 + j] += (G == 0 ? (u64)(long long)(int)ws : (u64)(long long)(int)ws << 16) +
+                     ((u64)(G == 0 ? (whi << 16) : whi) << 32);
+    }
+  }
+}
+
 // All MMAs of one accumulator group for one K chunk, fully unrolled: a_desc / b_desc are the
 // descriptors of digit plane 0 of the stage; plane i is A_TILE (B_TILE) bytes further on, and
 // each k16 step advances 32 bytes inside the swizzled rows.
-// With A0 set, A has digit plane 0 only (0/1 entries): C_s = A_0 B_s, one pair per accumulator.
+// With A0 set, A has digit plane 0 only (0/1 entries) and the odd B planes hold 256 B_s: the pair
+// (s, s + 1), s even, goes into the accumulator of s as C_s + 2^8 C_(s+1) (|.| <= 64 (128 +
+// 2^15) < 2^22 per 64 of K), four accumulators instead of eight.
 // fresh = 0 adds the chunk to what the accumulators hold instead of starting them anew.
 template <int G, bool A0 = false>
 __device__ __forceinline__ void issue_group(unsigned tmem, u64 a_desc, u64 b_desc,
@@ -115,6 +138,7 @@ __device__ __forceinline__ void issue_group(unsigned tmem, u64 a_desc, u64 b_des
 #pragma unroll
   for (int g = 0; g < 4; ++g) {
     const int s = group_s(G, g);
+    const int sa = A0 ? (s & ~1) : s;   // target accumulator
 #pragma unroll
     for (int kk = 0; kk < TC_BK / 16; ++kk) {
 #pragma unroll
@@ -122,7 +146,8 @@ __device__ __forceinline__ void issue_group(unsigned tmem, u64 a_desc, u64 b_des
         if (i <= s && (!A0 || i == 0)) {
           const u64 ad = a_desc + (u64)((i * A_TILE) >> 4) + (u64)(kk * 2);
           const u64 bd = b_desc + (u64)(((s - i) * B_TILE) >> 4) + (u64)(kk * 2);
-          mma_f16(tmem + (unsigned)acc_col(s), ad, bd, (kk == 0 && i == 0) ? (fresh ^ 1u) : 1u);
+          const bool first = kk == 0 && i == 0 && sa == s;
+          mma_f16(tmem + (unsigned)acc_col(sa), ad, bd, first ? (fresh ^ 1u) : 1u);
         }
       }
     }
@@ -329,8 +354,15 @@ __device__ __forceinline__ unsigned f16x2_minus_1152(unsigned x) {
   asm("sub.rn.f16x2 %0, %1, %2;\n" : "=r"(r) : "r"(x), "r"(0x64806480u));
   return r;
 }
+__device__ __forceinline__ unsigned f16x2_times_256(unsigned x) {   // exact for |x| <= 128
+  unsigned r;
+  asm("mul.rn.f16x2 %0, %1, %2;\n" : "=r"(r) : "r"(x), "r"(0x5C005C00u));
+  return r;
+}
+// scale_odd: the odd digit planes are stored times 2^8 (B of a bit-operand product)
 __device__ __forceinline__ void split8_store(const u64 v[8], unsigned char* plane0,
-                                             long long plane_stride, int off) {
+                                             long long plane_stride, int off,
+                                             bool scale_odd = false) {
   unsigned pk[8][4];   // [plane][k pair m]: f16 digits of words 2m (low half) and 2m + 1
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
@@ -345,6 +377,12 @@ __device__ __forceinline__ void split8_store(const u64 v[8], unsigned char* plan
       pk[4 * h + 1][m] = f16x2_minus_1152(__byte_perm(a13, b13, 0x5410));
       pk[4 * h + 3][m] = f16x2_minus_1152(__byte_perm(a13, b13, 0x7632));
     }
+  }
+  if (scale_odd) {
+#pragma unroll
+    for (int i = 1; i < 8; i += 2)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) pk[i][m] = f16x2_times_256(pk[i][m]);
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i)
@@ -446,7 +484,8 @@ bool make_map(CUtensorMap* map, void* planes, long long rows, long long Kp, int 
 //     digit-plane copy in HBM); the MMA issuer is as before; eight drain warps (each 32 rows x 32
 //     columns) add add0 and store the tile;
 //   - a_bits mode (A = the bits of one word per row): A has digit plane 0 only, so the producers
-//     write that plane alone and the issuer runs the 8 pairs (0, s) instead of 36.
+//     write that plane alone and the issuer runs the 8 pairs (0, s) instead of 36, merged two by
+//     two into four accumulators (odd B planes stored times 2^8), which halves the drain.
 constexpr int GM_NDRAIN = 8;                              // drain warps: 32 rows x GM_DC columns
 constexpr int GM_DC = 256 / GM_NDRAIN;                    // columns per drain warp (32)
 constexpr int GM_PROD = 3;                                // producer warps
@@ -556,7 +595,7 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
           u64 v[8];
 #pragma unroll
           for (int q = 0; q < 8; ++q) v[q] = Mm[(k8 * 8 + q) * 64 + c];
-          split8_store(v, Bsm + (k8 >> 2) * GM_BCHUNK, B_TILE, sw64_off(c, k8 & 3));
+          split8_store(v, Bsm + (k8 >> 2) * GM_BCHUNK, B_TILE, sw64_off(c, k8 & 3), a_bits != 0);
         }
         cur_m = mi;
       }
@@ -717,8 +756,13 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
         tc_fence_after();
 #pragma unroll
         for (int c16 = 0; c16 < GM_DC / 16; ++c16) {
-          if (g == 0) drain16<0>(tl, c16 * 16, acc + c16 * 16);
-          else drain16<1>(tl, c16 * 16, acc + c16 * 16);
+          if (a_bits) {
+            if (g == 0) drain16_pairs<0>(tl, c16 * 16, acc + c16 * 16);
+            else drain16_pairs<1>(tl, c16 * 16, acc + c16 * 16);
+          } else {
+            if (g == 0) drain16<0>(tl, c16 * 16, acc + c16 * 16);
+            else drain16<1>(tl, c16 * 16, acc + c16 * 16);
+          }
         }
         tc_fence_before();
         __syncwarp();
