@@ -22,6 +22,44 @@ inline unsigned grid_for(long long n8) {
 
 __device__ __forceinline__ u64 asr64(u64 v, int t) { return (u64)(((long long)v) >> t); }
 
+// v, with a compiler scheduling fence: code that uses the result is not hoisted above the memory
+// operations before it (keeps one ChaCha20 block live at a time)
+__device__ __forceinline__ u64 seq_u64(u64 v) {
+  u64 r;
+  asm volatile("mov.b64 %0, %1;\n" : "=l"(r) : "l"(v) : "memory");
+  return r;
+}
+
+// Warp-cooperative transfers of 8 consecutive elements per lane (lane l owns elements
+// e0 + 8 l .. e0 + 8 l + 7), staged through a per-warp shared block (32 x 9 words) so that every
+// global access instruction covers 32 consecutive words.  All 32 lanes must call them together.
+__device__ __forceinline__ void store8w(u64* __restrict__ out, long long e0, long long n,
+                                        const u64 v[8], u64* st) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) st[lane * 9 + j] = v[j];
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int idx = j * 32 + lane;
+    if (e0 + idx < n) out[e0 + idx] = st[(idx >> 3) * 9 + (idx & 7)];
+  }
+  __syncwarp();
+}
+__device__ __forceinline__ void load8w(const u64* __restrict__ in, long long e0, long long n,
+                                       u64 v[8], u64* st) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int idx = j * 32 + lane;
+    st[(idx >> 3) * 9 + (idx & 7)] = (e0 + idx < n) ? in[e0 + idx] : 0ull;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = st[lane * 9 + j];
+  __syncwarp();
+}
+
 // Pi_<.>^{l,0}(x): [r]_1 from eta01 (P0, P1), [r]_2 from eta02 (P0, P2); P0 forms
 // m = x + [r]_1 + [r]_2 (its outgoing message to P1 and P2).
 __global__ void k_share_input(const u64* __restrict__ x, long long n, Key k01, Key k02, u32 tag1,
@@ -150,84 +188,138 @@ __global__ void k_exchange_finish(long long n, const u64* __restrict__ p1_own,
 // P0's additive shares: [r_x]_1 = Gamma_p + b1 - [r_p]_1, [r_x]_2 = b2 - [r_p]_2 (and the same for
 // r_z with asr(b1, t), asr(b2, t), Gamma_q, r_q).
 // pq layout: <p> at pq[0..6E), <q> at pq[6E..12E).
-__global__ void k_trunc_p0(long long E, Key k01, Key k02, u64 obj, int t, u32 ttb1, u32 ttb2,
-                           u32 tp1, u32 tp2, u32 tpg, u32 tq1, u32 tq2, u32 tqg,
-                           u64* __restrict__ zpre, u64* __restrict__ zout, u64* __restrict__ pq,
-                           u64* __restrict__ gp2_out, u64* __restrict__ gq2_out,
-                           u64* __restrict__ mp1_out, u64* __restrict__ mq1_out) {
+__global__ void __launch_bounds__(TPB, 1)
+k_trunc_p0(long long E, Key k01, Key k02, u64 obj, int t, u32 ttb1, u32 ttb2,
+           u32 tp1, u32 tp2, u32 tpg, u32 tq1, u32 tq2, u32 tqg,
+           u64* __restrict__ zpre, u64* __restrict__ zout, u64* __restrict__ pq,
+           u64* __restrict__ gp2_out, u64* __restrict__ gq2_out,
+           u64* __restrict__ mp1_out, u64* __restrict__ mq1_out) {
+  __shared__ u64 stage[TPB / 32][32 * 9];
+  u64* st = stage[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
   const long long nb = (E + 7) / 8;
   u64* p = pq;
   u64* q = pq + 6 * E;
-  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
-       b += (long long)gridDim.x * blockDim.x) {
-    u64 b1[8], b2[8], rp1[8], rp2[8], gp1[8], rq1[8], rq2[8], gq1[8];
-    prf_block8(k01, ttb1, obj, (u64)b, b1);
-    prf_block8(k02, ttb2, obj, (u64)b, b2);
-    prf_block8(k01, tp1, obj, (u64)b, rp1);
-    prf_block8(k02, tp2, obj, (u64)b, rp2);
-    prf_block8(k01, tpg, obj, (u64)b, gp1);
-    prf_block8(k01, tq1, obj, (u64)b, rq1);
-    prf_block8(k02, tq2, obj, (u64)b, rq2);
-    prf_block8(k01, tqg, obj, (u64)b, gq1);
+  // one stream at a time (few registers live); gamma_p = -2a + r_p1 + r_p2 with a = b1 & b2, so
+  // [r_x]_1 = gamma_p + b1 - r_p1 = b1 - 2a + r_p2 (and the same for q with asr(., t))
+  for (long long bw = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); bw < nb;
+       bw += (long long)gridDim.x * blockDim.x) {
+    const u64 b = (u64)(bw + lane);
+    const long long e0 = bw * 8;
+    u64 b1[8], b2[8], x[8], g[8];
+    prf_block8(k01, ttb1, obj, b, b1);
+    prf_block8(k02, ttb2, obj, b, b2);
+    // <p>
+    prf_block8(k01, tp1, obj, seq_u64(b), x);   // r_p1: P0 and P1 copies
+    store8w(p, e0, E, x, st);
+    store8w(p + 3 * E, e0, E, x, st);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) g[j] = x[j] - 2 * (b1[j] & b2[j]);
+    prf_block8(k02, tp2, obj, seq_u64(b), x);   // r_p2: P0 and P2 copies
+    store8w(p + E, e0, E, x, st);
+    store8w(p + 5 * E, e0, E, x, st);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const long long e = b * 8 + j;
-      if (e >= E) continue;
-      const u64 a = b1[j] & b2[j];
-      const u64 gamma_p = (u64)0 - 2 * a + rp1[j] + rp2[j];
-      const u64 gamma_q = (u64)0 - 2 * asr64(a, t) + rq1[j] + rq2[j];
-      gp2_out[e] = gamma_p - gp1[j];
-      gq2_out[e] = gamma_q - gq1[j];
-      mp1_out[e] = gp1[j];          // P1's [m_p]_1 = [Gamma_p]_1 (its own PRG draw)
-      mq1_out[e] = gq1[j];
-      // <p>, <q> mask components (P0 copies and the pair parties' copies)
-      p[e] = rp1[j]; p[E + e] = rp2[j]; p[3 * E + e] = rp1[j]; p[5 * E + e] = rp2[j];
-      q[e] = rq1[j]; q[E + e] = rq2[j]; q[3 * E + e] = rq1[j]; q[5 * E + e] = rq2[j];
-      // P0's additive shares of r_x (mask of the product wire) and r_z (mask of the output)
-      zpre[e] = gamma_p + b1[j] - rp1[j];
-      zpre[E + e] = b2[j] - rp2[j];
-      zout[e] = gamma_q + asr64(b1[j], t) - rq1[j];
-      zout[E + e] = asr64(b2[j], t) - rq2[j];
+      g[j] += x[j];
+      x[j] = b1[j] - 2 * (b1[j] & b2[j]) + x[j];   // [r_x]_1 = b1 - 2a + r_p2
     }
+    store8w(zpre, e0, E, x, st);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = b2[j] - (x[j] - b1[j] + 2 * (b1[j] & b2[j]));   // [r_x]_2 = b2 - r_p2
+    store8w(zpre + E, e0, E, x, st);
+    prf_block8(k01, tpg, obj, seq_u64(b), x);   // P1's [m_p]_1 = [Gamma_p]_1 (its own PRG draw)
+    store8w(mp1_out, e0, E, x, st);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = g[j] - x[j];
+    store8w(gp2_out, e0, E, x, st);
+    // <q>
+    prf_block8(k01, tq1, obj, seq_u64(b), x);
+    store8w(q, e0, E, x, st);
+    store8w(q + 3 * E, e0, E, x, st);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) g[j] = x[j] - 2 * asr64(b1[j] & b2[j], t);
+    prf_block8(k02, tq2, obj, seq_u64(b), x);
+    store8w(q + E, e0, E, x, st);
+    store8w(q + 5 * E, e0, E, x, st);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      g[j] += x[j];
+      x[j] = asr64(b1[j], t) - 2 * asr64(b1[j] & b2[j], t) + x[j];   // [r_z]_1
+    }
+    store8w(zout, e0, E, x, st);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)   // [r_z]_2 = asr(b2, t) - r_q2
+      x[j] = asr64(b2[j], t) - (x[j] - asr64(b1[j], t) + 2 * asr64(b1[j] & b2[j], t));
+    store8w(zout + E, e0, E, x, st);
+    prf_block8(k01, tqg, obj, seq_u64(b), x);
+    store8w(mq1_out, e0, E, x, st);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = g[j] - x[j];
+    store8w(gq2_out, e0, E, x, st);
   }
 }
 
 // Pi_Trunc^t preprocessing, P1's and P2's part after the messages: m_p = [m_p]_1 + [m_p]_2 at each
 // of P1, P2; [r_x]_1 := m_{r_x} - [r_{r_x}]_1 at P1, [r_x]_2 := -[r_{r_x}]_2 at P2 (same for r_z).
-__global__ void k_trunc_finish(long long E, Key k01, Key k02, u64 obj, int t, u32 ttb1,
-                               u32 ttb2, const u64* __restrict__ p1_in_mp,
-                               const u64* __restrict__ p1_in_mq, const u64* __restrict__ p2_in_mp,
-                               const u64* __restrict__ p2_in_mq, const u64* __restrict__ p2_gp2,
-                               const u64* __restrict__ p2_gq2, const u64* __restrict__ p1_mp1,
-                               const u64* __restrict__ p1_mq1, u64* __restrict__ zpre,
-                               u64* __restrict__ zout, u64* __restrict__ pq) {
+__global__ void __launch_bounds__(TPB, 2)
+k_trunc_finish(long long E, Key k01, Key k02, u64 obj, int t, u32 ttb1,
+               u32 ttb2, const u64* __restrict__ p1_in_mp,
+               const u64* __restrict__ p1_in_mq, const u64* __restrict__ p2_in_mp,
+               const u64* __restrict__ p2_in_mq, const u64* __restrict__ p2_gp2,
+               const u64* __restrict__ p2_gq2, const u64* __restrict__ p1_mp1,
+               const u64* __restrict__ p1_mq1, u64* __restrict__ zpre,
+               u64* __restrict__ zout, u64* __restrict__ pq) {
+  __shared__ u64 stage[TPB / 32][32 * 9];
+  u64* st = stage[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
   const long long nb = (E + 7) / 8;
   u64* p = pq;
   u64* q = pq + 6 * E;
-  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
-       b += (long long)gridDim.x * blockDim.x) {
-    u64 b1[8], b2[8];
-    prf_block8(k01, ttb1, obj, (u64)b, b1);
-    prf_block8(k02, ttb2, obj, (u64)b, b2);
+  for (long long bw = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); bw < nb;
+       bw += (long long)gridDim.x * blockDim.x) {
+    const u64 b = (u64)(bw + lane);
+    const long long e0 = bw * 8;
+    u64 bb[8], m[8], x[8];
+    prf_block8(k01, ttb1, obj, b, bb);   // b1 (P1)
+    // P1: m_p, m_q and its [r_x]_1, [r_z]_1
+    load8w(p1_mp1, e0, E, m, st);
+    load8w(p1_in_mp, e0, E, x, st);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const long long e = b * 8 + j;
-      if (e >= E) continue;
-      // P1
-      const u64 mp_1 = p1_mp1[e] + p1_in_mp[e];
-      const u64 mq_1 = p1_mq1[e] + p1_in_mq[e];
-      p[2 * E + e] = mp_1;
-      q[2 * E + e] = mq_1;
-      zpre[3 * E + e] = mp_1 + b1[j] - p[3 * E + e];
-      zout[3 * E + e] = mq_1 + asr64(b1[j], t) - q[3 * E + e];
-      // P2
-      const u64 mp_2 = p2_in_mp[e] + p2_gp2[e];
-      const u64 mq_2 = p2_in_mq[e] + p2_gq2[e];
-      p[4 * E + e] = mp_2;
-      q[4 * E + e] = mq_2;
-      zpre[5 * E + e] = b2[j] - p[5 * E + e];
-      zout[5 * E + e] = asr64(b2[j], t) - q[5 * E + e];
-    }
+    for (int j = 0; j < 8; ++j) m[j] += x[j];
+    store8w(p + 2 * E, e0, E, m, st);
+    load8w(p + 3 * E, e0, E, x, st);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) m[j] = m[j] + bb[j] - x[j];
+    store8w(zpre + 3 * E, e0, E, m, st);
+    load8w(p1_mq1, e0, E, m, st);
+    load8w(p1_in_mq, e0, E, x, st);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) m[j] += x[j];
+    store8w(q + 2 * E, e0, E, m, st);
+    load8w(q + 3 * E, e0, E, x, st);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) m[j] = m[j] + asr64(bb[j], t) - x[j];
+    store8w(zout + 3 * E, e0, E, m, st);
+    // P2
+    prf_block8(k02, ttb2, obj, b, bb);   // b2 (P2)
+    load8w(p2_in_mp, e0, E, m, st);
+    load8w(p2_gp2, e0, E, x, st);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) m[j] += x[j];
+    store8w(p + 4 * E, e0, E, m, st);
+    load8w(p + 5 * E, e0, E, x, st);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) m[j] = bb[j] - x[j];
+    store8w(zpre + 5 * E, e0, E, m, st);
+    load8w(p2_in_mq, e0, E, m, st);
+    load8w(p2_gq2, e0, E, x, st);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) m[j] += x[j];
+    store8w(q + 4 * E, e0, E, m, st);
+    load8w(q + 5 * E, e0, E, x, st);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) m[j] = asr64(bb[j], t) - x[j];
+    store8w(zout + 5 * E, e0, E, m, st);
   }
 }
 
