@@ -346,14 +346,37 @@ struct View {
 // Party sums of a secure GR inner product sum_i u_i v_i (Sec. 2 inner product over GR):
 //   S0 = sum r_u r_v (P0), S1 = -sum (m_u [r_v]_1 + m_v [r_u]_1) (P1),
 //   S2 = sum m_u (m_v - [r_v]_2) - m_v [r_u]_2 (P2).  Pmat: 3 x 4096 scratch; S: 3 x 64 out.
+// The same Gram sums collected for one batched launch.
+struct GramBatch {
+  GemmTerm T[GRAM_BATCH_MAX];
+  Epi e[GRAM_BATCH_MAX];
+  int n = 0;
+  void add(u64* P, const u64* U0, const u64* U1, u64 su, long long ldu, const u64* V0,
+           const u64* V1, u64 sv, long long ldv, u64 sign) {
+    u64 us = 1, vs = 1;
+    if (!U0) { U0 = U1; U1 = nullptr; us = su; }
+    if (!V0) { V0 = V1; V1 = nullptr; vs = sv; }
+    if (!U0 || !V0 || n >= GRAM_BATCH_MAX) return;
+    T[n].A = op(U0, ldu, 1, U1, su, us);
+    T[n].B = op(V0, ldv, 0, V1, sv, vs);
+    e[n] = epi_atomic(P, 64, sign);
+    ++n;
+  }
+};
+
 int party_sums(mpc_ctx* ctx, const View& u, const View& v, long long count, u64* Pmat, u64* S) {
   CK(cudaMemsetAsync(Pmat, 0, 3 * 4096 * 8, ctx->st));
   const u64 M1 = ~0ull;  // -1
-  gram(ctx, Pmat, u.c[0], u.c[1], 1, u.ld, v.c[0], v.c[1], 1, v.ld, count, 1);
-  gram(ctx, Pmat + 4096, u.c[2], nullptr, 1, u.ld, v.c[3], nullptr, 1, v.ld, count, M1);
-  gram(ctx, Pmat + 4096, v.c[2], nullptr, 1, v.ld, u.c[3], nullptr, 1, u.ld, count, M1);
-  gram(ctx, Pmat + 8192, u.c[4], nullptr, 1, u.ld, v.c[4], v.c[5], M1, v.ld, count, 1);
-  gram(ctx, Pmat + 8192, v.c[4], nullptr, 1, v.ld, u.c[5], nullptr, 1, u.ld, count, M1);
+  GramBatch gb;
+  gb.add(Pmat, u.c[0], u.c[1], 1, u.ld, v.c[0], v.c[1], 1, v.ld, 1);
+  gb.add(Pmat + 4096, u.c[2], nullptr, 1, u.ld, v.c[3], nullptr, 1, v.ld, M1);
+  gb.add(Pmat + 4096, v.c[2], nullptr, 1, v.ld, u.c[3], nullptr, 1, u.ld, M1);
+  gb.add(Pmat + 8192, u.c[4], nullptr, 1, u.ld, v.c[4], v.c[5], M1, v.ld, 1);
+  gb.add(Pmat + 8192, v.c[4], nullptr, 1, v.ld, u.c[5], nullptr, 1, u.ld, M1);
+  if (count > 0 && gb.n > 0) {
+    g_launches += 1;
+    gemm_u64_gram_batch(ctx->st, count, gb.n, gb.T, gb.e, nsplit_for(count));
+  }
   launch_gr_fold_reduce(ctx->st, Pmat, 3, S);
   return cuda_check(ctx, "party_sums");
 }
@@ -552,12 +575,50 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
   launch_gr_lagrange(st, s.zp, ctx->reduce_mode, ctx->cst + CST_INV, s.coef);
   launch_gr_combine_z(st, s.coef, s.h0, s.h2, z, zo);
   launch_gr_mulmat2(st, s.coef, nullptr, s.MM);   // M_zeta
-  for (int c = 0; c < 6; ++c) {
+  // f(zeta) = f(0) + zeta (f(1) - f(0)): rows [x_{2i+1} - x_{2i}] times M_zeta, plus x_{2i}.
+  // When the vectors sit at one stride (x_0, y_0, x_1, y_1, ... as the dense plans allocate
+  // them), all of them go through one launch: segment s of Dh rows (padded to whole tiles).
+  bool batched = false;
+  if (ctx->gemm_path == MPC_GEMM_LIMB_TC) {
+    const u64* ins[12];
+    u64* outs[12];
+    int n = 0;
+    for (int c = 0; c < 6; ++c)
+      for (int side = 0; side < 2; ++side) {
+        ins[n] = side ? y.c[c] : x.c[c];
+        outs[n] = side ? yo.c[c] : xo.c[c];
+        ++n;
+      }
+    bool even = true;
+    for (int i = 0; i < 12 && even; ++i) even = ins[i] && outs[i];
+    const long long sin = even ? ins[1] - ins[0] : 0, sout = even ? outs[1] - outs[0] : 0;
+    for (int i = 1; i < 12 && even; ++i)
+      even = ins[i] - ins[0] == i * sin && outs[i] - outs[0] == i * sout;
+    if (even && sin > 0 && sout > 0) {
+      const long long Rp = (Dh + 127) / 128 * 128;
+      GrMMArgs g{};
+      g.R = 12 * Rp;
+      g.p0 = ins[0] + 64;
+      g.p1 = ins[0];
+      g.s1 = ~0ull;
+      g.in = GrRowMap{Rp, 128, sin};
+      g.qvalid = Dh;
+      g.Mmat = s.MM;
+      g.add0 = ins[0];
+      g.add0_in = 1;
+      g.out = outs[0];
+      g.om = GrRowMap{Rp, 64, sout};
+      g_launches += 1;
+      Phase kp(ctx, MPC_PROF_K_GR_MATMUL, 12.0 * Dh * 4096);
+      batched = gr_matmul_tc_ex(st, g, ctx->status, ST_TIMEOUT) == 0;
+      if (!batched) g_launches -= 1;
+    }
+  }
+  for (int c = 0; c < 6 && !batched; ++c) {
     for (int side = 0; side < 2; ++side) {
       const u64* in = side ? y.c[c] : x.c[c];
       u64* out = side ? yo.c[c] : xo.c[c];
       if (!in) continue;
-      // f(zeta) = f(0) + zeta (f(1) - f(0)): rows [x_{2i+1} - x_{2i}] times M_zeta, plus x_{2i}
       if ((rc = gr_matmul(ctx, Dh, in + 64, in, ~0ull, 128, s.MM, in, 128, out, 64))) return rc;
     }
   }

@@ -33,10 +33,12 @@ __device__ __forceinline__ u64 ld_opnd(const Opnd& o, long long r, long long c, 
   return v;
 }
 
+// The tile (bx, by) of split bz; a kernel body shared by the plain and the batched launches.
 template <int BM, int BN, int BK, int TM, int TN>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
-gemm_u64_kernel(long long M, long long N, long long K, int nterms, GemmTerm t0, GemmTerm t1,
-                Epi epi, long long k_per_split) {
+__device__ __forceinline__ void gemm_u64_body(long long M, long long N, long long K, int nterms,
+                                              const GemmTerm& t0, const GemmTerm& t1,
+                                              const Epi& epi, long long k_per_split,
+                                              long long bx, long long by, long long bz) {
   constexpr int NT = (BM / TM) * (BN / TN);
   constexpr int A_PER = BM * BK / NT;
   constexpr int B_PER = BK * BN / NT;
@@ -47,9 +49,9 @@ gemm_u64_kernel(long long M, long long N, long long K, int nterms, GemmTerm t0, 
   const int tid = threadIdx.x;
   const int tx = tid % (BN / TN);
   const int ty = tid / (BN / TN);
-  const long long m0 = (long long)blockIdx.x * BM;
-  const long long n0 = (long long)blockIdx.y * BN;
-  const long long kbeg = (long long)blockIdx.z * k_per_split;
+  const long long m0 = bx * BM;
+  const long long n0 = by * BN;
+  const long long kbeg = bz * k_per_split;
   const long long kend = (kbeg + k_per_split < K) ? (kbeg + k_per_split) : K;
 
   u64 acc[TM][TN];
@@ -169,7 +171,42 @@ gemm_u64_kernel(long long M, long long N, long long K, int nterms, GemmTerm t0, 
   }
 }
 
+template <int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+gemm_u64_kernel(long long M, long long N, long long K, int nterms, GemmTerm t0, GemmTerm t1,
+                Epi epi, long long k_per_split) {
+  gemm_u64_body<BM, BN, BK, TM, TN>(M, N, K, nterms, t0, t1, epi, k_per_split, blockIdx.x,
+                                    blockIdx.y, blockIdx.z);
+}
+
+// Independent 64 x 64 Gram sums (one term each, atomic epilogues) in one launch: grid.y picks
+// the sum.
+struct GramBatchArgs {
+  GemmTerm T[GRAM_BATCH_MAX];
+  Epi e[GRAM_BATCH_MAX];
+};
+__global__ void __launch_bounds__(256)
+gemm_u64_gram_batch_kernel(long long K, GramBatchArgs b, long long k_per_split) {
+  const int t = blockIdx.y;
+  gemm_u64_body<64, 64, 8, 4, 4>(64, 64, K, 1, b.T[t], b.T[t], b.e[t], k_per_split, 0, 0,
+                                 blockIdx.z);
+}
+
 }  // namespace
+
+void gemm_u64_gram_batch(cudaStream_t st, long long K, int n, const GemmTerm* terms,
+                         const Epi* epis, int nsplit) {
+  if (n <= 0 || K <= 0) return;
+  if (nsplit < 1) nsplit = 1;
+  GramBatchArgs b;
+  for (int i = 0; i < n && i < GRAM_BATCH_MAX; ++i) {
+    b.T[i] = terms[i];
+    b.e[i] = epis[i];
+  }
+  const long long kps = (K + nsplit - 1) / nsplit;
+  dim3 grid(1, (unsigned)(n < GRAM_BATCH_MAX ? n : GRAM_BATCH_MAX), (unsigned)nsplit);
+  gemm_u64_gram_batch_kernel<<<grid, 256, 0, st>>>(K, b, kps);
+}
 
 void gemm_u64(cudaStream_t st, long long M, long long N, long long K, int nterms,
               const GemmTerm* terms, const Epi& epi, int nsplit) {

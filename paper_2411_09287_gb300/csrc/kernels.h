@@ -40,6 +40,11 @@ struct Epi {
   u64* out;
   long long ldc;
 };
+// Up to GRAM_BATCH_MAX independent 64 x 64 Gram sums out_i += sign_i sum_k A_i[:, k] B_i[k, :]
+// (each a one-term product, K deep, with an atomic epilogue) in one launch.
+constexpr int GRAM_BATCH_MAX = 8;
+void gemm_u64_gram_batch(cudaStream_t st, long long K, int n, const GemmTerm* terms,
+                         const Epi* epis, int nsplit);
 // C(M x N) = sum over terms of A_t (M x K) * B_t (K x N), then the epilogue.  nsplit > 1 splits
 // K across grid.z and requires epi.atomic = 1.
 void gemm_u64(cudaStream_t st, long long M, long long N, long long K, int nterms,
@@ -88,6 +93,8 @@ struct GrMMArgs {
   u64* out;
   GrRowMap om;
   long long out_lim;
+  long long qvalid;   // > 0: only rows with rho % in.q < qvalid exist (padded segments)
+  int add0_in;        // add0 row rho at add0 + in(rho) (the input map) instead of rho ld_add0
 };
 int gr_matmul_tc_ex(cudaStream_t st, const GrMMArgs& a, unsigned* err, unsigned err_flag);
 

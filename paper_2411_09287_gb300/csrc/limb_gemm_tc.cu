@@ -601,9 +601,10 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
       }
       if (pt == 0 && (u >> 1) + 1 < count && lda <= 128) {   // next tile's rows into L2
         const long long r0 = (tile + tstep) * TC_BM;
-        const long long nr = (R - r0 < TC_BM) ? R - r0 : TC_BM;
+        long long nr = (R - r0 < TC_BM) ? R - r0 : TC_BM;
+        if (a.qvalid && a.qvalid - r0 % a.in.q < nr) nr = a.qvalid - r0 % a.in.q;
         const long long nb = rowmap(a.in, r0);
-        const long long words = (nr - 1) * lda + (a_bits ? 1 : 64);
+        const long long words = nr > 0 ? (nr - 1) * lda + (a_bits ? 1 : 64) : 0;
         const long long bytes = (words * 8) & ~15ll;   // whole 16-byte units inside the rows
         for (int w2 = 0; w2 < (p1 ? 2 : 1); ++w2) {
           const char* lo = reinterpret_cast<const char*>((w2 ? p1 : p0) + nb);
@@ -612,6 +613,15 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
         }
       }
       return true;
+    };
+    // rows of the tile at rho0 that exist (R, and the valid part of a padded segment)
+    auto tile_rows = [&](long long rho0) -> long long {
+      long long v = R - rho0;
+      if (a.qvalid) {
+        const long long rest = a.qvalid - rho0 % a.in.q;
+        v = rest < v ? rest : v;
+      }
+      return v;
     };
     auto end_unit = [&](long long u) {
       fence_proxy_async_smem();
@@ -625,13 +635,14 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
         const long long rho0 = (t0 + (u >> 1) * tstep) * TC_BM;
         const int kc = (int)(u & 1);
         const long long ib = rowmap(a.in, rho0);   // word index of the tile's first bit word
+        const long long vrows = tile_rows(rho0);
         unsigned char* As = Asm + (u % NSTAGE) * 8 * A_TILE;
         // one word per item row: all of this thread's words first (one latency per chunk)
         u64 wd[NIT];
 #pragma unroll
         for (int q = 0; q < NIT; ++q) {
           const int item = pt + q * GM_PROD * 32;
-          const bool in = item < 512 && rho0 + (item >> 2) < R;
+          const bool in = item < 512 && (item >> 2) < vrows;
           wd[q] = in ? p0[ib + (item >> 2) * lda] : 0ull;
         }
 #pragma unroll
@@ -658,10 +669,11 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
           const int r = (int)(k - u * RPU);
           const long long rho0 = (t0 + (u >> 1) * tstep) * TC_BM;
           const long long ib = rowmap(a.in, rho0) + (u & 1) * 32;
+          const long long vrows = tile_rows(rho0);
 #pragma unroll
           for (int q = 0; q < NQ; ++q) {
             const int item = pt + (r * NQ + q) * GM_PROD * 32;   // (row, unit of 8 k)
-            const bool in = item < 512 && rho0 + (item >> 2) < R;
+            const bool in = item < 512 && (item >> 2) < vrows;
             const long long off = ib + (item >> 2) * lda + (item & 3) * 8;
 #pragma unroll
             for (int j = 0; j < 8; j += 2) {
@@ -770,15 +782,18 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
       }
       if (ok) {   // tile complete: add add0, store (4 columns at a time through shared memory)
         const long long r = (t0 + v * tstep) * TC_BM + q4 * 32 + lane;
-        const long long ob = r < R ? rowmap(a.om, r) : -1;   // this lane's row: word offset
+        const bool exists = r < R && (!a.qvalid || r % a.in.q < a.qvalid);
+        const long long ob = exists ? rowmap(a.om, r) : -1;   // this lane's row: word offset
         const bool live = ob >= 0 && ob < a.out_lim;
         // the rows this lane stores in the two passes (16 rows per pass, 2 lanes per row)
+        // add0 offset of this lane's row
+        const long long ao = !a.add0 ? 0 : (a.add0_in ? (exists ? rowmap(a.in, r) : 0) : r * a.ld_add0);
         long long obr[2], rg[2];
 #pragma unroll
         for (int pass = 0; pass < 2; ++pass) {
           const int rr = pass * 16 + (lane >> 1);
           obr[pass] = __shfl_sync(0xffffffffu, live ? ob : -1, rr);
-          rg[pass] = __shfl_sync(0xffffffffu, r, rr);
+          rg[pass] = __shfl_sync(0xffffffffu, ao, rr);
         }
         unsigned char* os = Osm + warp * GM_OSTAGE;
         // add0 words of the stored 16-byte chunks, loaded before the first store (one latency)
@@ -789,7 +804,7 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
           for (int pass = 0; pass < 2; ++pass) {
             const long long col = h * GM_DC + c0 + 2 * (lane & 1);
             ad[c0 / 4][pass] = (a.add0 && obr[pass] >= 0)
-                                   ? *reinterpret_cast<const ulonglong2*>(a.add0 + rg[pass] * a.ld_add0 + col)
+                                   ? *reinterpret_cast<const ulonglong2*>(a.add0 + rg[pass] + col)
                                    : make_ulonglong2(0, 0);
           }
 #pragma unroll
@@ -1086,6 +1101,7 @@ int gr_matmul_tc_ex(cudaStream_t st, const GrMMArgs& args, unsigned* err, unsign
   const bool bad_in = !a.a_bits && (odd(a.in.s1) || odd(a.in.s2));
   // 16-byte vector accesses need even word offsets; a tile must not straddle a map period or
   // a matrix group
+  if ((a.qvalid && !a.in.q) || (a.add0_in && (a.a_bits || a.qvalid < 0))) return -1;
   if (bad_in || odd(a.om.s1) || odd(a.om.s2) || (a.add0 && odd(a.ld_add0)) ||
       (a.in.q % TC_BM) || (a.om.q % TC_BM) || (a.mrows % TC_BM) || a.in.q < 0 || a.om.q < 0 ||
       a.mrows < 0 ||
