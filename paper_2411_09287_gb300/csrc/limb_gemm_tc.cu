@@ -511,6 +511,9 @@ __device__ __forceinline__ long long rowmap(const GrRowMap& m, long long rho) {
   return m.q ? (rho % m.q) * m.s1 + (rho / m.q) * m.s2 : rho * m.s1;
 }
 
+// MODE 0: plain product, 1: fold (p0 - p1), 2: bit operand.  One instantiation per mode keeps
+// each kernel's code (and instruction-cache footprint) to the paths it runs.
+template <int MODE>
 __global__ void __launch_bounds__(GM_THREADS, 1)
 k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) {
   extern __shared__ unsigned char dsm[];
@@ -529,9 +532,9 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
   const int warp = tid >> 5, lane = tid & 31;
   const long long R = a.R;
   const u64* p0 = a.p0;   // may alias out (a row is read before its tile is written)
-  const u64* p1 = a.p1;
+  const u64* p1 = MODE == 1 ? a.p1 : nullptr;
   const u64 s1 = a.s1;
-  const int a_bits = a.a_bits;
+  constexpr int a_bits = MODE == 2 ? 1 : 0;
   // CTA b takes tiles b, b + G, b + 2G, ... (G = gridDim.x), or with matrix groups the
   // contiguous range [t0, t0 + count), so that it meets each matrix in one run
   const long long ntiles = (R + TC_BM - 1) / TC_BM;
@@ -716,7 +719,7 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
           if (k + 1 < nrounds) take_next();
         }
       };
-      if (p1) stream(std::integral_constant<int, 2>(), std::true_type());
+      if (MODE == 1) stream(std::integral_constant<int, 2>(), std::true_type());
       else stream(std::integral_constant<int, 3>(), std::false_type());
     }
     if (!ok && lane == 0) fail();
@@ -1118,8 +1121,14 @@ int gr_matmul_tc_ex(cudaStream_t st, const GrMMArgs& args, unsigned* err, unsign
   }
   const long long ntiles = (a.R + TC_BM - 1) / TC_BM;
   const unsigned grid = (unsigned)(ntiles < nsm ? ntiles : nsm);
-  set_max_dynamic_smem(reinterpret_cast<const void*>(k_gr_matmul_tc), (int)GM_SMEM);
-  k_gr_matmul_tc<<<grid, GM_THREADS, GM_SMEM, st>>>(a, err, err_flag);
+  const int mode = a.a_bits ? 2 : (a.p1 ? 1 : 0);
+  const void* fn = mode == 2 ? reinterpret_cast<const void*>(k_gr_matmul_tc<2>)
+                 : mode == 1 ? reinterpret_cast<const void*>(k_gr_matmul_tc<1>)
+                             : reinterpret_cast<const void*>(k_gr_matmul_tc<0>);
+  set_max_dynamic_smem(fn, (int)GM_SMEM);
+  if (mode == 2) k_gr_matmul_tc<2><<<grid, GM_THREADS, GM_SMEM, st>>>(a, err, err_flag);
+  else if (mode == 1) k_gr_matmul_tc<1><<<grid, GM_THREADS, GM_SMEM, st>>>(a, err, err_flag);
+  else k_gr_matmul_tc<0><<<grid, GM_THREADS, GM_SMEM, st>>>(a, err, err_flag);
   return 0;
 }
 
