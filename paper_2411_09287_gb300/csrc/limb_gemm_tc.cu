@@ -427,6 +427,38 @@ __global__ void k_split_digits(GemmTerm t0, GemmTerm t1, int nterms, int which /
   }
 }
 
+// The B split for a row-major K x R source (trans = 0): a 64 k x 32 r block goes through shared
+// memory, so that the reads run along r and every plane row gets 128 contiguous bytes per 8
+// threads (the direct split writes one 16-byte unit per row and thread).
+__global__ void __launch_bounds__(256)
+k_split_digits_bt(GemmTerm t0, GemmTerm t1, int nterms, long long R, long long K, long long Kp,
+                  unsigned short* __restrict__ planes) {
+  __shared__ u64 tile[32][65];
+  const long long r0 = (long long)blockIdx.x * 32;
+  const long long k0 = (long long)blockIdx.y * 64;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int kl = w * 8 + j;
+    const long long kk = k0 + kl;
+    u64 v = 0;
+    if (kk < (long long)nterms * K && r0 + lane < R) {
+      const GemmTerm& T = (kk < K) ? t0 : t1;
+      v = load_opnd(T.B, kk < K ? kk : kk - K, r0 + lane, K, R);
+    }
+    tile[lane][kl] = v;
+  }
+  __syncthreads();
+  const int rl = threadIdx.x >> 3, kc = threadIdx.x & 7;
+  const long long r = r0 + rl, kk0 = k0 + kc * 8;
+  if (r < R && kk0 < Kp) {
+    u64 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = tile[rl][kc * 8 + q];
+    split8_store(v, reinterpret_cast<unsigned char*>(planes + r * Kp + kk0), R * Kp * 2, 0);
+  }
+}
+
 // out[i] = acc_sign*out[i] + add0 + add1 + prf_sign*PRF(i) (the protocol epilogue of gemm_u64).
 __global__ void k_apply_epilogue(long long M, long long N, Epi epi) {
   const long long total = M * N;
@@ -1065,7 +1097,12 @@ int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nte
   if (ga > (1 << 20)) ga = 1 << 20;
   if (gb > (1 << 20)) gb = 1 << 20;
   k_split_digits<<<(unsigned)ga, tpb, 0, st>>>(terms[0], t1, nterms, 0, M, K, Kp, Ap);
-  k_split_digits<<<(unsigned)gb, tpb, 0, st>>>(terms[0], t1, nterms, 1, N, K, Kp, Bp);
+  if (terms[0].B.trans == 0 && t1.B.trans == 0 && (Kp + 63) / 64 <= 65535) {
+    dim3 g2((unsigned)((N + 31) / 32), (unsigned)((Kp + 63) / 64));
+    k_split_digits_bt<<<g2, 256, 0, st>>>(terms[0], t1, nterms, N, K, Kp, Bp);
+  } else {
+    k_split_digits<<<(unsigned)gb, tpb, 0, st>>>(terms[0], t1, nterms, 1, N, K, Kp, Bp);
+  }
   CUtensorMap ma, mb;
   if (!make_map(&ma, Ap, M, Kp, TC_BM) || !make_map(&mb, Bp, N, Kp, TC_BN)) return -2;
   const size_t smem = (size_t)NSTAGE * STAGE + (size_t)NDRAIN * 32 * 48 + 1024;
