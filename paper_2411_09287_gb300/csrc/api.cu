@@ -59,6 +59,8 @@ inline void counted(int k, F f, A... a) {
 #define launch_trunc_update_vw(...) counted(1, mpc3::launch_trunc_update_vw, __VA_ARGS__)
 #define launch_trunc_materialize(...) counted(1, mpc3::launch_trunc_materialize, __VA_ARGS__)
 #define launch_gr_mul_rows(...) counted(1, mpc3::launch_gr_mul_rows, __VA_ARGS__)
+#define launch_gather_rows_affine(...) counted(1, mpc3::launch_gather_rows_affine, __VA_ARGS__)
+#define launch_block_rowsum(...) counted(1, mpc3::launch_block_rowsum, __VA_ARGS__)
 #define launch_gr_mulmat_batch(...) counted(1, mpc3::launch_gr_mulmat_batch, __VA_ARGS__)
 #define launch_word_transpose(...) counted(1, mpc3::launch_word_transpose, __VA_ARGS__)
 #define launch_scalar_gr_sum(...) counted(1, mpc3::launch_scalar_gr_sum, __VA_ARGS__)
@@ -850,6 +852,11 @@ struct VMatPlan {
   // (e_lo, e_hi) order (nhm x Lm view transposed)
   long long Lm = 0, nhm = 0;
   u64 *Tm = nullptr, *Bm = nullptr, *Vm = nullptr, *bT = nullptr;
+  // compact table (E a multiple of L on that path): only r^(2 e_lo), e_lo < L, is materialised;
+  // sum_e r^(2e) pq_c[e] = sum_{e_hi} T_hi[e_hi] (sum_{e_lo} pq_c[e] r^(2 e_lo)) (a limb GEMM over
+  // the first block, then 12 nhi GR products), and the rows r^(2 Lm e_hi) come from T_hi x r^(2 e_lo)
+  bool compact = false;
+  u64 *Zhi = nullptr, *Zrep = nullptr, *Zprod = nullptr, *Prow = nullptr;
   Dense dt;
   IVBuf ivt;
   void* tcs = nullptr;   // tensor-core digit planes (limb path only)
@@ -862,16 +869,20 @@ VMatPlan plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R
   p.s = plan_small(a);
   // digit planes of the batch-0 products (X^T P, W Q, Z Q) and of the truncation batch's S_hi
   // combination (64 x 262144 x nhi) on the tensor-core path
-  long long nhi_tc = 0;
+  long long nhi_tc = 0, zrows_tc = 0, L_tc = 0;
   if (t >= 0) {
     const long long E = M * N, L = E >= 65536 ? 65536 : ((E + 127) / 128) * 128;
     nhi_tc = (E + L - 1) / L;
+    L_tc = L;
+    const int kd = std::min(R1 < 0 ? default_R(64 * E) : R1, 6);
+    if (tc && kd == 6 && E >= 65536 && E % L == 0) zrows_tc = 12 * nhi_tc;   // compact table
     if (nhi_tc < 32) nhi_tc = 0;   // short combinations stay on the CUDA cores (no plane scratch)
   }
   p.tcs = tc ? (void*)a.take<unsigned char>((long long)std::max(
                    {limb_tc_scratch_bytes(K, 64, M, 1), limb_tc_scratch_bytes(K, 64, N, 1),
                     limb_tc_scratch_bytes(6 * M, 64, N, 1),
-                    nhi_tc ? limb_tc_scratch_bytes(64, 262144, nhi_tc, 1) : (size_t)0}))
+                    nhi_tc ? limb_tc_scratch_bytes(64, 262144, nhi_tc, 1) : (size_t)0,
+                    zrows_tc ? limb_tc_scratch_bytes(zrows_tc, 64, L_tc, 1) : (size_t)0}))
              : nullptr;
   p.Q = a.take<u64>(N * 64);
   p.P = a.take<u64>(M * 64);
@@ -892,7 +903,8 @@ VMatPlan plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R
     p.nhi = p.Epad / p.L;
     p.b1 = a.take<u64>(p.Epad);
     p.b2 = a.take<u64>(p.Epad);
-    p.Rtab = a.take<u64>(p.Epad * 64);
+    p.compact = zrows_tc > 0;
+    p.Rtab = a.take<u64>((p.compact ? p.L : p.Epad) * 64);
     p.S = a.take<u64>(4096 * 64);
     p.TL8 = a.take<unsigned char>(1024 * p.L);
     p.B1T = a.take<u64>(p.Epad);
@@ -914,6 +926,12 @@ VMatPlan plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R
       p.nhm = ((E + p.Lm - 1) / p.Lm + 127) / 128 * 128;
       p.Tm = a.take<u64>(p.Lm * 4096);
       p.Bm = a.take<u64>((E + p.Lm - 1) / p.Lm * 4096);
+      if (p.compact) {
+        p.Zhi = a.take<u64>(12 * p.nhi * 64);
+        p.Zrep = a.take<u64>(12 * p.nhi * 64);
+        p.Zprod = a.take<u64>(12 * p.nhi * 64);
+        p.Prow = a.take<u64>(3 * ((E + p.Lm - 1) / p.Lm) * 64);
+      }
       p.Vm = a.take<u64>(64 * 4096);
       p.bT = a.take<u64>(p.nhm * p.Lm);
     }
@@ -1337,7 +1355,10 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
     // r^(2e) for e < Epad: r^(2 e_lo) for e_lo < L by repeated multiplication, then every further
     // block of L rows is that block times the constant r^(2 L e_hi) (a 64 x 64 matrix product)
     launch_gr_powers(st, s.aux + 64, p.L, p.Rtab);
-    if (p.nhi > 1) {
+    if (p.compact) {
+      launch_gr_mul1(st, p.Rtab + (p.L - 1) * 64, s.aux + 64, s.aux + 128);   // r^(2L)
+      launch_gr_powers(st, s.aux + 128, p.nhi, p.Thi);
+    } else if (p.nhi > 1) {
       launch_gr_mul1(st, p.Rtab + (p.L - 1) * 64, s.aux + 64, s.aux + 128);   // r^(2L)
       launch_gr_powers(st, s.aux + 128, p.nhi, p.Thi);
       // rows h L + e_lo (h >= 1) = r^(2 L h) r^(2 e_lo): one grouped product, matrix h - 1 for
@@ -1365,7 +1386,18 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
     }
     CK(cudaMemsetAsync(p.Zpq, 0, 12 * 64 * 8, st));
     // sum_e r^(2e) p_c[e], sum_e r^(2e) q_c[e]: (12 x E) . (E x 64)
-    launch_scalar_gr_sum(st, E, pq, E, 12, p.Rtab, p.Zpq);
+    if (p.compact) {
+      // Zhi[c nhi + h] = sum_{e_lo} pq_c[h L + e_lo] r^(2 e_lo) (E = nhi L: one strided view)
+      GemmTerm T;
+      T.A = op(pq, p.L);
+      T.B = op(p.Rtab, 64);
+      if ((rc = dense_gemm(ctx, 12 * p.nhi, 64, p.L, T, epi_store(p.Zhi, 64), p.tcs))) return rc;
+      launch_gather_rows_affine(st, 12 * p.nhi, p.Thi, 1, 1, p.nhi, p.Zrep);   // T_hi[h]
+      launch_gr_mul_rows(st, 12 * p.nhi, p.Zhi, p.Zrep, p.Zprod);
+      launch_block_rowsum(st, 12, p.nhi, p.Zprod, p.Zpq);
+    } else {
+      launch_scalar_gr_sum(st, E, pq, E, 12, p.Rtab, p.Zpq);
+    }
     u64* z0 = p.zt + 384;
     for (int c = 0; c < 6; ++c)   // z_c = sum r^(2e) p_c + r sum r^(2e) q_c
       launch_gr_lincomb(st, ctx->cst + CST_ONE, p.Zpq + c * 64, s.r, p.Zpq + (6 + c) * 64,
@@ -1385,7 +1417,8 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
           return fail(ctx, MPC_ERR_CUDA, "verify_matmul: tensor map of the limb table");
       }
       GemmTerm T;
-      T.A = op(p.Rtab, p.L * 64, 1);       // A[a][e_hi] = coefficient a of r^(2 L e_hi)
+      // A[a][e_hi] = coefficient a of r^(2 L e_hi)
+      T.A = p.compact ? op(p.Thi, 64, 1) : op(p.Rtab, p.L * 64, 1);
       T.B = op(p.S_hi, 262144);            // B[e_hi][(p, b)]
       if ((rc = dense_gemm(ctx, 64, 262144, p.nhi, T, epi_store(p.Pst, 262144),
                            p.nhi >= 32 ? p.tcs : nullptr)))
@@ -1439,7 +1472,17 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
         // into two grouped GR matrix products on the tensor cores.
         const long long Lm = p.Lm, nhm = p.nhm, nB = (E + Lm - 1) / Lm;
         launch_gr_mulmat_batch(st, 64, nV, 64, p.Vm);
-        launch_gr_mulmat_batch(st, nB, p.Rtab, Lm * 64, p.Bm);
+        if (p.compact) {   // r^(2 Lm e_hi) = T_hi[e / L] r^(2 (e mod L)), e = e_hi Lm
+          u64* ra = p.Prow;
+          u64* rb = p.Prow + nB * 64;
+          u64* rr = p.Prow + 2 * nB * 64;
+          launch_gather_rows_affine(st, nB, p.Thi, Lm, p.L, 0, ra);
+          launch_gather_rows_affine(st, nB, p.Rtab, Lm, 1, p.L, rb);
+          launch_gr_mul_rows(st, nB, ra, rb, rr);
+          launch_gr_mulmat_batch(st, nB, rr, 64, p.Bm);
+        } else {
+          launch_gr_mulmat_batch(st, nB, p.Rtab, Lm * 64, p.Bm);
+        }
         launch_word_transpose(st, nhm, Lm, E, p.b1, p.bT);
         GrMMArgs g{};
         // Tm: rows sigma = j Lm + e_lo read r^(2 e_lo) and use matrix j; written at [e_lo][j]

@@ -126,6 +126,24 @@ __global__ void k_word_transpose(long long rows, long long cols, long long n, co
   }
 }
 
+// out[i] = src[idx(i)] for rows of 64 words, idx(i) = ((i mul) / div) mod m (m = 0: no mod).
+__global__ void k_gather_rows_affine(long long n, const u64* __restrict__ src, long long mul,
+                                     long long div, long long m, u64* __restrict__ out) {
+  for (long long i = blockIdx.x; i < n; i += gridDim.x) {
+    long long idx = (i * mul) / div;
+    if (m) idx %= m;
+    out[i * 64 + threadIdx.x] = src[idx * 64 + threadIdx.x];
+  }
+}
+
+// out[c] = sum_{h < nper} in[c nper + h] for c < ncomp (rows of 64 words).
+__global__ void k_block_rowsum(long long nper, const u64* __restrict__ in, u64* __restrict__ out) {
+  const long long c = blockIdx.x;
+  u64 v = 0;
+  for (long long h = 0; h < nper; ++h) v += in[(c * nper + h) * 64 + threadIdx.x];
+  out[c * 64 + threadIdx.x] = v;
+}
+
 // ---- inverses of the interpolation constants (Pi_Reduce with points 0, 1, x) ------------------
 __device__ u64 gf2_64_mul(u64 a, u64 b) {   // GF(2)[x]/(x^64 + x^4 + x^3 + x + 1)
   u64 r = 0;
@@ -740,6 +758,17 @@ void launch_word_transpose(cudaStream_t st, long long rows, long long cols, long
   if (rows <= 0 || cols <= 0) return;
   dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
   k_word_transpose<<<grid, 256, 0, st>>>(rows, cols, n, in, out);
+}
+
+void launch_gather_rows_affine(cudaStream_t st, long long n, const u64* src, long long mul,
+                               long long div, long long m, u64* out) {
+  if (n <= 0) return;
+  k_gather_rows_affine<<<(unsigned)(n < 65536 ? n : 65536), 64, 0, st>>>(n, src, mul, div, m, out);
+}
+
+void launch_block_rowsum(cudaStream_t st, int ncomp, long long nper, const u64* in, u64* out) {
+  if (ncomp <= 0) return;
+  k_block_rowsum<<<(unsigned)ncomp, 64, 0, st>>>(nper, in, out);
 }
 
 void launch_gr_inverses(cudaStream_t st, u64* out) { k_gr_inverses<<<1, 64, 0, st>>>(out); }

@@ -173,6 +173,11 @@ void launch_scalar_gr_sum(cudaStream_t st, long long n, const u64* A, long long 
                           const u64* R, u64* out);
 // out[e] = a[e] * b[e] (GR products of n row pairs; out may alias a or b)
 void launch_gr_mul_rows(cudaStream_t st, long long n, const u64* a, const u64* b, u64* out);
+// out[i] = src[idx(i)] (rows of 64 words), idx(i) = ((i mul) / div) mod m (m = 0: no mod).
+void launch_gather_rows_affine(cudaStream_t st, long long n, const u64* src, long long mul,
+                               long long div, long long m, u64* out);
+// out[c] = sum over h < nper of in[c nper + h] (rows of 64 words), c < ncomp.
+void launch_block_rowsum(cudaStream_t st, int ncomp, long long nper, const u64* in, u64* out);
 // M + 4096 i = multiplication matrix (M[b][c] = coefficient c of g x^b) of g = src + i stride,
 // i < n.
 void launch_gr_mulmat_batch(cudaStream_t st, long long n, const u64* src, long long stride,
