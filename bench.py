@@ -179,9 +179,9 @@ def run_reference(args, rank: int, world: int):
 # the figure by E / 2^20.  The summaries, with the commands that produced them: profiles/.
 NCU_TRAFFIC_E = 2 ** 20
 NCU_TRAFFIC = {   # bytes per step at E = 2^20 (profiles/traffic_gr_kernels_n1024.md)
-    "k_trunc_s": 0.418e9,
-    "k_limb_gemm": None,     # changed since the capture
-    "k_gr_matmul": None,     # changed since the capture
+    "k_trunc_s": 0.395e9,
+    "k_limb_gemm": 0.763e9,
+    "k_gr_matmul": 9.970e9,
     "k_gram": 2.151e9,
     "k_gr_mul_rows": None,   # not launched at these sizes (the tensor-core form replaces it)
 }
