@@ -62,47 +62,49 @@ __device__ __forceinline__ void load8w(const u64* __restrict__ in, long long e0,
 
 // Pi_<.>^{l,0}(x): [r]_1 from eta01 (P0, P1), [r]_2 from eta02 (P0, P2); P0 forms
 // m = x + [r]_1 + [r]_2 (its outgoing message to P1 and P2).
-__global__ void k_share_input(const u64* __restrict__ x, long long n, Key k01, Key k02, u32 tag1,
-                              u32 tag2, u64 obj, u64* __restrict__ s, u64* __restrict__ m_out) {
+__global__ void __launch_bounds__(TPB)
+k_share_input(const u64* __restrict__ x, long long n, Key k01, Key k02, u32 tag1, u32 tag2,
+              u64 obj, u64* __restrict__ s, u64* __restrict__ m_out) {
+  __shared__ u64 stage[TPB / 32][32 * 9];
+  u64* st = stage[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
   const long long nb = (n + 7) / 8;
-  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
-       b += (long long)gridDim.x * blockDim.x) {
-    u64 r1[8], r2[8];
-    prf_block8(k01, tag1, obj, (u64)b, r1);
-    prf_block8(k02, tag2, obj, (u64)b, r2);
+  for (long long bw = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); bw < nb;
+       bw += (long long)gridDim.x * blockDim.x) {
+    const u64 b = (u64)(bw + lane);
+    const long long e0 = bw * 8;
+    u64 r1[8], r2[8], xv[8];
+    prf_block8(k01, tag1, obj, b, r1);
+    prf_block8(k02, tag2, obj, b, r2);
+    store8w(s, e0, n, r1, st);
+    store8w(s + n, e0, n, r2, st);
+    store8w(s + 3 * n, e0, n, r1, st);
+    store8w(s + 5 * n, e0, n, r2, st);
+    load8w(x, e0, n, xv, st);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const long long i = b * 8 + j;
-      if (i < n) {
-        s[i] = r1[j];
-        s[n + i] = r2[j];
-        s[3 * n + i] = r1[j];
-        s[5 * n + i] = r2[j];
-        m_out[i] = x[i] + r1[j] + r2[j];
-      }
-    }
+    for (int j = 0; j < 8; ++j) xv[j] += r1[j] + r2[j];
+    store8w(m_out, e0, n, xv, st);
   }
 }
 
 // [r] <- Pi_[.] (random) into the mask components of a sharing (output wires of Pi_Mult / Pi_Inner).
-__global__ void k_fill_masks(long long n, Key k01, Key k02, u32 tag1, u32 tag2, u64 obj,
-                             u64* __restrict__ s) {
+__global__ void __launch_bounds__(TPB)
+k_fill_masks(long long n, Key k01, Key k02, u32 tag1, u32 tag2, u64 obj, u64* __restrict__ s) {
+  __shared__ u64 stage[TPB / 32][32 * 9];
+  u64* st = stage[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
   const long long nb = (n + 7) / 8;
-  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
-       b += (long long)gridDim.x * blockDim.x) {
+  for (long long bw = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); bw < nb;
+       bw += (long long)gridDim.x * blockDim.x) {
+    const u64 b = (u64)(bw + lane);
+    const long long e0 = bw * 8;
     u64 r1[8], r2[8];
-    prf_block8(k01, tag1, obj, (u64)b, r1);
-    prf_block8(k02, tag2, obj, (u64)b, r2);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const long long i = b * 8 + j;
-      if (i < n) {
-        s[i] = r1[j];
-        s[n + i] = r2[j];
-        s[3 * n + i] = r1[j];
-        s[5 * n + i] = r2[j];
-      }
-    }
+    prf_block8(k01, tag1, obj, b, r1);
+    prf_block8(k02, tag2, obj, b, r2);
+    store8w(s, e0, n, r1, st);
+    store8w(s + n, e0, n, r2, st);
+    store8w(s + 3 * n, e0, n, r1, st);
+    store8w(s + 5 * n, e0, n, r2, st);
   }
 }
 

@@ -45,12 +45,21 @@ k_hash_leaves(const u64* __restrict__ data, long long n, long long nleaves,
     sha256_init(h);
     u32 blk[16];
     long long i = 0;
-    for (; i + 8 <= nw; i += 8) {   // full 64-byte blocks
+    // full 64-byte blocks; the next block's words are loaded before this one is compressed
+    u64 nx[8];
+    if (nw >= 8) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) nx[q] = data[w0 + q];
+    }
+    for (; i + 8 <= nw; i += 8) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const u64 v = data[w0 + i + q];
-        blk[2 * q] = bswap32((u32)v);
-        blk[2 * q + 1] = bswap32((u32)(v >> 32));
+        blk[2 * q] = bswap32((u32)nx[q]);
+        blk[2 * q + 1] = bswap32((u32)(nx[q] >> 32));
+      }
+      if (i + 16 <= nw) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) nx[q] = data[w0 + i + 8 + q];
       }
       sha256_compress(h, blk);
     }
