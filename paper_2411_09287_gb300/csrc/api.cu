@@ -9,6 +9,7 @@
 // mpc_reconstruct = Pi_Rec (Sec. 2).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <set>
@@ -920,10 +921,27 @@ VMatPlan plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R
     p.S3 = a.take<u64>(2 * 192);
     p.zt = a.take<u64>(2 * 384);
     if (tc && p.kd == 6 && E >= 65536) {
+      // Lm = 128 a with a odd near sqrt(E) / 128, and nhm = 128 b >= E / Lm with the fewest rows
+      // past E: the bit product writes its rows Lm rows apart, and a stride of a multiple of
+      // 2 MB (a even at E = 2^24) puts a tile's 128 rows on the same memory channels
       long long sq = 1;
       while (sq * sq < E) ++sq;
-      p.Lm = (sq + 127) / 128 * 128;
+      const long long a0 = (sq + 127) / 128;
+      p.Lm = 128 * a0;
       p.nhm = ((E + p.Lm - 1) / p.Lm + 127) / 128 * 128;
+      if (a0 >= 4) {   // strides of 512 KB and more
+        long long best = -1;
+        for (long long aa = (a0 * 3 / 4) | 1; aa <= 2 * a0 + 1; aa += 2) {
+          const long long bb = (E + 128 * 128 * aa - 1) / (128 * 128 * aa);
+          const long long rows = 128 * 128 * aa * bb;
+          if (best < 0 || rows < p.Lm * p.nhm ||
+              (rows == p.Lm * p.nhm && std::llabs(aa - a0) < std::llabs(best - a0))) {
+            best = aa;
+            p.Lm = 128 * aa;
+            p.nhm = 128 * bb;
+          }
+        }
+      }
       p.Tm = a.take<u64>(p.Lm * 4096);
       p.Bm = a.take<u64>((E + p.Lm - 1) / p.Lm * 4096);
       if (p.compact) {

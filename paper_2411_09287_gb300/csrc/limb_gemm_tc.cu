@@ -665,30 +665,40 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
     };
     if (a_bits) {
       constexpr int NIT = (512 + GM_PROD * 32 - 1) / (GM_PROD * 32);   // items per thread
-      for (long long u = 0; u < nunits; ++u) {
-        if (!(ok = begin_unit(u))) break;
-        const long long rho0 = (t0 + (u >> 1) * tstep) * TC_BM;
-        const int kc = (int)(u & 1);
+      // One bit word per row serves both K chunks of its tile (bytes 0..3, then 4..7); the
+      // words of tile t + 1 are in flight while tile t's two chunks are written.
+      auto load_tile = [&](long long t, u64 (&w)[NIT]) {
+        const long long rho0 = (t0 + t * tstep) * TC_BM;
         const long long ib = rowmap(a.in, rho0);   // word index of the tile's first bit word
         const long long vrows = tile_rows(rho0);
-        unsigned char* As = Asm + (u % NSTAGE) * 8 * A_TILE;
-        // one word per item row: all of this thread's words first (one latency per chunk)
-        u64 wd[NIT];
 #pragma unroll
         for (int q = 0; q < NIT; ++q) {
           const int item = pt + q * GM_PROD * 32;
           const bool in = item < 512 && (item >> 2) < vrows;
-          wd[q] = in ? p0[ib + (item >> 2) * lda] : 0ull;
+          w[q] = in ? p0[ib + (item >> 2) * lda] : 0ull;
         }
+      };
+      u64 wd[NIT], nd[NIT];
+      if (count > 0) load_tile(0, nd);
+      for (long long t = 0; t < count && ok; ++t) {
 #pragma unroll
-        for (int q = 0; q < NIT; ++q) {
-          const int item = pt + q * GM_PROD * 32;
-          if (item < 512) {
-            const unsigned by = (unsigned)(wd[q] >> (kc * 32 + (item & 3) * 8)) & 0xFFu;
-            *reinterpret_cast<uint4*>(As + sw64_off(item >> 2, item & 3)) = bits_plane0(by);
+        for (int q = 0; q < NIT; ++q) wd[q] = nd[q];
+        if (t + 1 < count) load_tile(t + 1, nd);
+#pragma unroll 1
+        for (int kc = 0; kc < 2; ++kc) {
+          const long long u = 2 * t + kc;
+          if (!(ok = begin_unit(u))) break;
+          unsigned char* As = Asm + (u % NSTAGE) * 8 * A_TILE;
+#pragma unroll
+          for (int q = 0; q < NIT; ++q) {
+            const int item = pt + q * GM_PROD * 32;
+            if (item < 512) {
+              const unsigned by = (unsigned)(wd[q] >> (kc * 32 + (item & 3) * 8)) & 0xFFu;
+              *reinterpret_cast<uint4*>(As + sw64_off(item >> 2, item & 3)) = bits_plane0(by);
+            }
           }
+          end_unit(u);
         }
-        end_unit(u);
       }
     } else {
       // A rows in rounds of NQ items (8 words each) per thread, RPU rounds per unit; the loads
@@ -796,6 +806,39 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
     const long long nacc = nunits / 2;   // one accumulation per tile
     for (long long v = 0; v < nacc && ok; ++v) {
       const unsigned par = (unsigned)(v & 1);
+      // the rows this lane stores in the two passes (16 rows per pass, 2 lanes per row) as word
+      // offsets (-1: none) and their add0 offsets
+      long long obr[2], rg[2];
+      auto tile_rows_out = [&]() {
+        const long long r = (t0 + v * tstep) * TC_BM + q4 * 32 + lane;   // this lane's row
+        const bool exists = r < R && (!a.qvalid || r % a.in.q < a.qvalid);
+        const long long ob = exists ? rowmap(a.om, r) : -1;
+        const bool live = ob >= 0 && ob < a.out_lim;
+        const long long ao =
+            !a.add0 ? 0 : (a.add0_in ? (exists ? rowmap(a.in, r) : 0) : r * a.ld_add0);
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+          const int rr = pass * 16 + (lane >> 1);
+          obr[pass] = __shfl_sync(0xffffffffu, live ? ob : -1, rr);
+          rg[pass] = __shfl_sync(0xffffffffu, ao, rr);
+        }
+      };
+      // add0 words of the stored 16-byte chunks: a fold has the rows and the first EARLY columns
+      // in flight during the drains; otherwise both come after them
+      constexpr int EARLY = MODE == 1 ? GM_DC / 2 : 0;
+      if (MODE == 1) tile_rows_out();
+      ulonglong2 ad[GM_DC / 4][2];
+      auto load_add0 = [&](int c0) {
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+          const long long col = h * GM_DC + c0 + 2 * (lane & 1);
+          ad[c0 / 4][pass] = (a.add0 && obr[pass] >= 0)
+                                 ? *reinterpret_cast<const ulonglong2*>(a.add0 + rg[pass] + col)
+                                 : make_ulonglong2(0, 0);
+        }
+      };
+#pragma unroll
+      for (int c0 = 0; c0 < EARLY; c0 += 4) load_add0(c0);
 #pragma unroll 1
       for (int g = 0; g < 2; ++g) {
         ok = __all_sync(0xffffffffu, mbar_wait(&accf_bar[g], par, abort));
@@ -816,32 +859,10 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
         if (lane == 0) mbar_arrive(&acce_bar[g]);
       }
       if (ok) {   // tile complete: add add0, store (4 columns at a time through shared memory)
-        const long long r = (t0 + v * tstep) * TC_BM + q4 * 32 + lane;
-        const bool exists = r < R && (!a.qvalid || r % a.in.q < a.qvalid);
-        const long long ob = exists ? rowmap(a.om, r) : -1;   // this lane's row: word offset
-        const bool live = ob >= 0 && ob < a.out_lim;
-        // the rows this lane stores in the two passes (16 rows per pass, 2 lanes per row)
-        // add0 offset of this lane's row
-        const long long ao = !a.add0 ? 0 : (a.add0_in ? (exists ? rowmap(a.in, r) : 0) : r * a.ld_add0);
-        long long obr[2], rg[2];
-#pragma unroll
-        for (int pass = 0; pass < 2; ++pass) {
-          const int rr = pass * 16 + (lane >> 1);
-          obr[pass] = __shfl_sync(0xffffffffu, live ? ob : -1, rr);
-          rg[pass] = __shfl_sync(0xffffffffu, ao, rr);
-        }
         unsigned char* os = Osm + warp * GM_OSTAGE;
-        // add0 words of the stored 16-byte chunks, loaded before the first store (one latency)
-        ulonglong2 ad[GM_DC / 4][2];
+        if (MODE != 1) tile_rows_out();
 #pragma unroll
-        for (int c0 = 0; c0 < GM_DC; c0 += 4)
-#pragma unroll
-          for (int pass = 0; pass < 2; ++pass) {
-            const long long col = h * GM_DC + c0 + 2 * (lane & 1);
-            ad[c0 / 4][pass] = (a.add0 && obr[pass] >= 0)
-                                   ? *reinterpret_cast<const ulonglong2*>(a.add0 + rg[pass] + col)
-                                   : make_ulonglong2(0, 0);
-          }
+        for (int c0 = EARLY; c0 < GM_DC; c0 += 4) load_add0(c0);
 #pragma unroll
         for (int c0 = 0; c0 < GM_DC; c0 += 4) {
 #pragma unroll
