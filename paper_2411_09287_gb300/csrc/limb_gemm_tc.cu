@@ -633,6 +633,8 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
           split8_store(v, Bsm + (k8 >> 2) * GM_BCHUNK, B_TILE, sw64_off(c, k8 & 3), a_bits != 0);
         }
         cur_m = mi;
+        // the next group's matrix into L2 (this CTA's tiles are contiguous, so it comes next)
+        if (pt == 0 && a.mrows && (mi + 1) * a.mrows < R) prefetch_l2(Mm + 4096, 4096 * 8);
       }
       if (pt == 0 && (u >> 1) + 1 < count && lda <= 128) {   // next tile's rows into L2
         const long long r0 = (tile + tstep) * TC_BM;
@@ -823,10 +825,10 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
           rg[pass] = __shfl_sync(0xffffffffu, ao, rr);
         }
       };
-      // add0 words of the stored 16-byte chunks: a fold has the rows and the first EARLY columns
-      // in flight during the drains; otherwise both come after them
+      // add0 words of the stored 16-byte chunks: a fold has the first EARLY columns in flight
+      // during the drains; the rows come before the drains except for bit operands
       constexpr int EARLY = MODE == 1 ? GM_DC / 2 : 0;
-      if (MODE == 1) tile_rows_out();
+      if (MODE != 2) tile_rows_out();
       ulonglong2 ad[GM_DC / 4][2];
       auto load_add0 = [&](int c0) {
 #pragma unroll
@@ -860,7 +862,7 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
       }
       if (ok) {   // tile complete: add add0, store (4 columns at a time through shared memory)
         unsigned char* os = Osm + warp * GM_OSTAGE;
-        if (MODE != 1) tile_rows_out();
+        if (MODE == 2) tile_rows_out();
 #pragma unroll
         for (int c0 = EARLY; c0 < GM_DC; c0 += 4) load_add0(c0);
 #pragma unroll
