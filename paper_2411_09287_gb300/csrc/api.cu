@@ -579,28 +579,35 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
   launch_gr_combine_z(st, s.coef, s.h0, s.h2, z, zo);
   launch_gr_mulmat2(st, s.coef, nullptr, s.MM);   // M_zeta
   // f(zeta) = f(0) + zeta (f(1) - f(0)): rows [x_{2i+1} - x_{2i}] times M_zeta, plus x_{2i}.
-  // When the vectors sit at one stride (x_0, y_0, x_1, y_1, ... as the dense plans allocate
-  // them), all of them go through one launch: segment s of Dh rows (padded to whole tiles).
+  // When the vectors present sit at one stride (x_0, y_0, x_1, y_1, ... as the dense plans
+  // allocate them, skipping absent components), all of them go through one launch: segment s of
+  // Dh rows (padded to whole tiles).  Only short vectors are batched: there one launch replaces
+  // several latency-bound ones, while on long ones the segment arithmetic of the batched row map
+  // costs more than the launches it saves.
   bool batched = false;
-  if (ctx->gemm_path == MPC_GEMM_LIMB_TC) {
+  if (ctx->gemm_path == MPC_GEMM_LIMB_TC && Dh <= 65536) {
     const u64* ins[12];
     u64* outs[12];
     int n = 0;
+    bool even = true;
     for (int c = 0; c < 6; ++c)
       for (int side = 0; side < 2; ++side) {
-        ins[n] = side ? y.c[c] : x.c[c];
-        outs[n] = side ? yo.c[c] : xo.c[c];
+        const u64* in = side ? y.c[c] : x.c[c];
+        u64* out = side ? yo.c[c] : xo.c[c];
+        if (!in) continue;
+        even = even && out;
+        ins[n] = in;
+        outs[n] = out;
         ++n;
       }
-    bool even = true;
-    for (int i = 0; i < 12 && even; ++i) even = ins[i] && outs[i];
+    even = even && n >= 2;
     const long long sin = even ? ins[1] - ins[0] : 0, sout = even ? outs[1] - outs[0] : 0;
-    for (int i = 1; i < 12 && even; ++i)
+    for (int i = 1; i < n && even; ++i)
       even = ins[i] - ins[0] == i * sin && outs[i] - outs[0] == i * sout;
     if (even && sin > 0 && sout > 0) {
       const long long Rp = (Dh + 127) / 128 * 128;
       GrMMArgs g{};
-      g.R = 12 * Rp;
+      g.R = n * Rp;
       g.p0 = ins[0] + 64;
       g.p1 = ins[0];
       g.s1 = ~0ull;
@@ -612,7 +619,7 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
       g.out = outs[0];
       g.om = GrRowMap{Rp, 64, sout};
       g_launches += 1;
-      Phase kp(ctx, MPC_PROF_K_GR_MATMUL, 12.0 * Dh * 4096);
+      Phase kp(ctx, MPC_PROF_K_GR_MATMUL, (double)n * Dh * 4096);
       batched = gr_matmul_tc_ex(st, g, ctx->status, ST_TIMEOUT) == 0;
       if (!batched) g_launches -= 1;
     }
