@@ -50,7 +50,10 @@ enum {
   MPC_ERR_PENDING = 8     /* reconstruction requested while products are unverified          */
 };
 
-/* third interpolation point of Pi_Reduce (Fig. Reduce): see DESIGN.md "readings" */
+/* third interpolation point of Pi_Reduce (Fig. Reduce), whose interpolation at 0, 1, 2 divides by 2
+ * (not a unit of GR(2^64, 64)): POINT_X interpolates at 0, 1, x (x the ring generator; x and
+ * 1 - x are units) for any challenge; POINT_2 keeps 0, 1, 2 and evaluates at zeta = 2 zeta' so
+ * that the Lagrange weights stay integral */
 enum { MPC_REDUCE_POINT_X = 0, MPC_REDUCE_POINT_2 = 1 };
 /* local products of Pi_Inner: exact u64 CUDA-core GEMM, or exact limb-split tensor-core GEMM */
 enum { MPC_GEMM_U64 = 0, MPC_GEMM_LIMB_TC = 1 };
@@ -148,11 +151,11 @@ int mpc_verify_mult(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, const 
 
 /* Pi_BIVerify (Fig. PBDP) of the layer produced by mpc_matmul(call_id = matmul_call_id):
  * batch 0 = the M N inner products of Z = X W, consolidated with weights r^(aN+b) and evaluated
- * as the K-dimensional claim sum_k Xt_k Wt_k = zt (rank-1 form); batch 1 (when
- * trunc_bits >= 0) = the 2 M N inner products of the truncation pairs, merged per output into one
- * 64-dimensional inner product.  R_main / R_trunc < 0 select the default
- * max(0, ceil(log2 D) - 6).  Returns as mpc_verify_mult.  trace (device, optional): batch 0 as in
- * mpc_verify_mult, then batch 1 at offset (R_main + 1) * 832. */
+ * as the K-dimensional claim sum_k Xt_k Wt_k = zt (rank-1 form: Xt = X^T P, Wt = W Q with P, Q
+ * the weight powers); batch 1 (when trunc_bits >= 0) = the 2 M N inner products of the truncation
+ * pairs, merged per output into one 64-dimensional inner product.  R_main / R_trunc < 0 select
+ * the default max(0, ceil(log2 D) - 6).  Returns as mpc_verify_mult.  trace (device, optional):
+ * batch 0 as in mpc_verify_mult, then batch 1 at offset (R_main + 1) * 832. */
 int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, const uint64_t* ws_,
                       const uint64_t* zpre, const uint64_t* pq, int64_t M, int64_t N, int64_t K,
                       int trunc_bits, uint64_t matmul_call_id, int R_main, int R_trunc,

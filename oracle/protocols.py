@@ -11,7 +11,7 @@ three parties' views.  Every random value comes from the pairwise PRG streams of
                     products), optionally with Pi_Trunc^t (Fig. trunc).
 * ``trunc_pair``    Pi_Trunc^t preprocessing (Fig. trunc).
 
-Readings of the paper (each also listed in the design doc):
+Readings of the paper (where it is silent, ambiguous or garbled):
   A1  m = x + r everywhere (Sec. 2 Notation); a bit sharing <b> := (0, b, 0) therefore carries
       [r] = -b so that its value is b.
   A2  Gamma = r_x r_y + r_z (Fig. MultP, Fig. DPP); "m_{y_i}" there means m_y.

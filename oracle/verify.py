@@ -17,7 +17,7 @@
                         inner products of one output share their y vector and are merged
                         (reading V1t); ``tran_trunc_literal`` is the unmerged 2*l*E form.
 
-Readings (also listed in the design doc):
+Readings of the paper (where it is silent, ambiguous or garbled):
   A4  lifting pads with zero coefficients (Fig. MTP text).
   A5  r, zeta', alpha are <.>^{l[x]}-random from the pairwise streams; r and zeta' are revealed
       with Pi_Rec, alpha is not.

@@ -1,6 +1,6 @@
-// Host-side launchers of libmpc3's kernels (internal interface between the protocol driver in
+// Host-side launchers of libmpc3's kernels (internal interface between the protocol code in
 // api.cu and the kernels).  Every launcher enqueues on `st` and returns nothing; launch errors
-// are collected by the driver with cudaGetLastError().
+// are collected by the protocol code with cudaGetLastError().
 #pragma once
 #include <cstddef>
 #include <cstdint>
