@@ -78,7 +78,8 @@ enum {
 /* workspace queries */
 enum {
   MPC_OP_SHARE = 0, MPC_OP_MULT = 1, MPC_OP_MATMUL = 2, MPC_OP_VERIFY_MULT = 3,
-  MPC_OP_VERIFY_MATMUL = 4, MPC_OP_RECONSTRUCT = 5, MPC_OP_RELU = 6, MPC_OP_MAXPOOL2 = 7
+  MPC_OP_VERIFY_MATMUL = 4, MPC_OP_RECONSTRUCT = 5, MPC_OP_RELU = 6, MPC_OP_MAXPOOL2 = 7,
+  MPC_OP_VERIFY_MULT_CALLS = 8
 };
 
 typedef struct mpc_ctx mpc_ctx;
@@ -105,9 +106,9 @@ int mpc_sync(mpc_ctx* ctx);
 int mpc_status(const mpc_ctx* ctx);
 
 /* Bytes of workspace an operation needs.  op = MPC_OP_*; (a, b, c) = (n, 0, 0) for SHARE, MULT,
- * VERIFY_MULT, RECONSTRUCT and RELU, (M, N, K) for MATMUL and VERIFY_MATMUL, (B C, H, W) for
- * MAXPOOL2; trunc_bits, R_main and
- * R_trunc as passed to the operation (R < 0: default; VERIFY_MULT takes its R in R_main).
+ * VERIFY_MULT, RECONSTRUCT and RELU, (total n of all calls, 0, 0) for VERIFY_MULT_CALLS, (M, N, K)
+ * for MATMUL and VERIFY_MATMUL, (B C, H, W) for MAXPOOL2; trunc_bits, R_main and R_trunc as passed
+ * to the operation (R < 0: default; VERIFY_MULT and VERIFY_MULT_CALLS take their R in R_main).
  * Returns -1 for invalid arguments. */
 int64_t mpc_workspace_size(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int64_t c,
                            int trunc_bits, int R_main, int R_trunc);
@@ -148,6 +149,23 @@ int mpc_matmul(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_
 int mpc_verify_mult(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, const uint64_t* ys,
                     const uint64_t* zs, int64_t n, uint64_t mult_call_id, int R,
                     void* workspace, size_t workspace_bytes, uint64_t* trace);
+
+/* Deferred Pi_MultVerify^R (Fig. PPEV) of the triples of several mpc_mult calls in one batch, e.g.
+ * every gate of a multiplication circuit checked once before any output is opened (outputs are
+ * reconstructed only after verification, Sec. 2).  Call l produced the n[l] triples (xs[l], ys[l],
+ * zs[l]) under call id call_ids[l]; the batch is their concatenation in the order given, so the
+ * transcript equals that of mpc_verify_mult on the concatenated sharings (component c of call l at
+ * offset n[0] + ... + n[l-1] of component c).  xs, ys, zs: host arrays of ncalls device pointers,
+ * each a sharing of 6 n[l] words; n, call_ids: host arrays of ncalls entries, read during the
+ * call only.  Workspace: mpc_workspace_size(MPC_OP_VERIFY_MULT_CALLS, n[0] + ... + n[ncalls-1],
+ * 0, 0, -1, R, -1).  Every listed call leaves the pending state once the check has run (a
+ * rejection makes the context abort).  R < 0 selects max(0, ceil(log2 N) - 6) for the total N.
+ * Returns as mpc_verify_mult; MPC_ERR_ARG / MPC_ERR_SHAPE for a null pointer, a bad id or
+ * n[l] <= 0.  trace: as mpc_verify_mult. */
+int mpc_verify_mult_calls(mpc_ctx* ctx, uint64_t verify_id, int ncalls,
+                          const uint64_t* const* xs, const uint64_t* const* ys,
+                          const uint64_t* const* zs, const int64_t* n, const uint64_t* call_ids,
+                          int R, void* workspace, size_t workspace_bytes, uint64_t* trace);
 
 /* Pi_BIVerify (Fig. PBDP) of the layer produced by mpc_matmul(call_id = matmul_call_id):
  * batch 0 = the M N inner products of Z = X W, consolidated with weights r^(aN+b) and evaluated

@@ -35,6 +35,10 @@ _SIGS = {
     "mpc_verify_mult": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_int64, C.c_uint64, C.c_int, C.c_void_p, C.c_size_t,
                                   C.c_void_p]),
+    "mpc_verify_mult_calls": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.POINTER(C.c_void_p),
+                                        C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                        C.POINTER(C.c_int64), C.POINTER(C.c_uint64), C.c_int,
+                                        C.c_void_p, C.c_size_t, C.c_void_p]),
     "mpc_verify_matmul": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int,
                                     C.c_uint64, C.c_int, C.c_int, C.c_void_p, C.c_size_t,

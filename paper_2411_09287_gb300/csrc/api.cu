@@ -841,6 +841,21 @@ VMultPlan plan_vmult(Arena& a, long long n, int R) {
   return p;
 }
 
+// deferred Pi_MultVerify over several calls: the gathered triples, then the verification plan
+struct VMultCallsPlan {
+  u64 *x, *y, *z;
+  VMultPlan v;
+};
+
+VMultCallsPlan plan_vmult_calls(Arena& a, long long n, int R) {
+  VMultCallsPlan p;
+  p.x = a.take<u64>(6 * n);
+  p.y = a.take<u64>(6 * n);
+  p.z = a.take<u64>(6 * n);
+  p.v = plan_vmult(a, n, R);
+  return p;
+}
+
 struct VMatPlan {
   Small s;
   u64 *Q, *P, *T, *Pz;
@@ -1088,6 +1103,10 @@ int64_t mpc_workspace_size(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int
       if (a <= 0) return -1;
       plan_vmult(ar, a, R_main);
       break;
+    case MPC_OP_VERIFY_MULT_CALLS:
+      if (a <= 0) return -1;
+      plan_vmult_calls(ar, a, R_main);
+      break;
     case MPC_OP_VERIFY_MATMUL:
       if (a <= 0 || b <= 0 || c <= 0) return -1;
       plan_vmat(ar, a, b, c, trunc_bits, R_main, R_trunc, ctx && ctx->gemm_path == MPC_GEMM_LIMB_TC);
@@ -1276,16 +1295,11 @@ int mpc_matmul(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_
   return cuda_check(ctx, "matmul");
 }
 
-int mpc_verify_mult(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, const uint64_t* ys,
-                    const uint64_t* zs, int64_t n, uint64_t mult_call_id, int R,
-                    void* workspace, size_t workspace_bytes, uint64_t* trace) {
-  int rc = guard(ctx);
-  if (rc) return rc;
-  if (n <= 0) return fail(ctx, MPC_ERR_SHAPE, "verify_mult: n <= 0");
-  if (!xs || !ys || !zs || !id_ok(verify_id)) return fail(ctx, MPC_ERR_ARG, "verify_mult: bad argument");
-  Arena ar{(char*)workspace, workspace_bytes, 0, false};
-  VMultPlan p = plan_vmult(ar, n, R);
-  if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "verify_mult: workspace too small");
+namespace {
+// Pi_MultVerify (Fig. PPEV) of the n triples (xs, ys, zs) in the plan's workspace, up to the
+// opened Delta; the caller reads the outcome with finish_verify.
+int verify_mult_body(mpc_ctx* ctx, uint64_t verify_id, const u64* xs, const u64* ys,
+                     const u64* zs, long long n, VMultPlan& p, u64* trace) {
   Phase phase(ctx, MPC_PROF_VERIFY_MULT);
   cudaStream_t st = ctx->st;
   const Small& s = p.s;
@@ -1306,9 +1320,57 @@ int mpc_verify_mult(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, const 
     gemm_u64(st, 6, 64, n, 1, &T, epi_atomic(s.zinit, 64), nsplit_for(n));
   }
   p.dv.cur = 0;
-  rc = run_dense(ctx, verify_id, 0, p.dv, n, s.zinit, 1, p.R, s, p.iv, trace);
+  return run_dense(ctx, verify_id, 0, p.dv, n, s.zinit, 1, p.R, s, p.iv, trace);
+}
+}  // namespace
+
+int mpc_verify_mult(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, const uint64_t* ys,
+                    const uint64_t* zs, int64_t n, uint64_t mult_call_id, int R,
+                    void* workspace, size_t workspace_bytes, uint64_t* trace) {
+  int rc = guard(ctx);
   if (rc) return rc;
+  if (n <= 0) return fail(ctx, MPC_ERR_SHAPE, "verify_mult: n <= 0");
+  if (!xs || !ys || !zs || !id_ok(verify_id)) return fail(ctx, MPC_ERR_ARG, "verify_mult: bad argument");
+  Arena ar{(char*)workspace, workspace_bytes, 0, false};
+  VMultPlan p = plan_vmult(ar, n, R);
+  if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "verify_mult: workspace too small");
+  if ((rc = verify_mult_body(ctx, verify_id, xs, ys, zs, n, p, trace))) return rc;
   return finish_verify(ctx, (mult_call_id << 1) | 0);
+}
+
+int mpc_verify_mult_calls(mpc_ctx* ctx, uint64_t verify_id, int ncalls,
+                          const uint64_t* const* xs, const uint64_t* const* ys,
+                          const uint64_t* const* zs, const int64_t* n, const uint64_t* call_ids,
+                          int R, void* workspace, size_t workspace_bytes, uint64_t* trace) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (ncalls <= 0 || !xs || !ys || !zs || !n || !call_ids || !id_ok(verify_id))
+    return fail(ctx, MPC_ERR_ARG, "verify_mult_calls: bad argument");
+  long long N = 0;
+  for (int l = 0; l < ncalls; ++l) {
+    if (n[l] <= 0 || n[l] > (1ll << 40)) return fail(ctx, MPC_ERR_SHAPE, "verify_mult_calls: bad n");
+    if (!xs[l] || !ys[l] || !zs[l] || !id_ok(call_ids[l]))
+      return fail(ctx, MPC_ERR_ARG, "verify_mult_calls: bad argument");
+    N += n[l];
+  }
+  Arena ar{(char*)workspace, workspace_bytes, 0, false};
+  VMultCallsPlan p = plan_vmult_calls(ar, N, R);
+  if (!workspace || !ar.ok())
+    return fail(ctx, MPC_ERR_WORKSPACE, "verify_mult_calls: workspace too small");
+  // the batch: component c of call l at c N + (n[0] + ... + n[l-1]) of each gathered sharing
+  long long off = 0;
+  for (int l = 0; l < ncalls; ++l) {
+    const size_t bytes = (size_t)n[l] * 8;
+    for (int c = 0; c < 6; ++c) {
+      CK(cudaMemcpyAsync(p.x + c * N + off, xs[l] + c * n[l], bytes, cudaMemcpyDeviceToDevice, ctx->st));
+      CK(cudaMemcpyAsync(p.y + c * N + off, ys[l] + c * n[l], bytes, cudaMemcpyDeviceToDevice, ctx->st));
+      CK(cudaMemcpyAsync(p.z + c * N + off, zs[l] + c * n[l], bytes, cudaMemcpyDeviceToDevice, ctx->st));
+    }
+    off += n[l];
+  }
+  if ((rc = verify_mult_body(ctx, verify_id, p.x, p.y, p.z, N, p.v, trace))) return rc;
+  for (int l = 1; l < ncalls; ++l) ctx->pending.erase((call_ids[l] << 1) | 0);
+  return finish_verify(ctx, (call_ids[0] << 1) | 0);
 }
 
 int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, const uint64_t* ws_,

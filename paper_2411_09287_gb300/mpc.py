@@ -21,7 +21,7 @@ MPC_ERR_TIMEOUT, MPC_ERR_VERIFY, MPC_ERR_ABORT, MPC_ERR_PENDING = 5, 6, 7, 8
 REDUCE_POINT_X, REDUCE_POINT_2 = 0, 1
 GEMM_U64, GEMM_LIMB_TC = 0, 1
 (OP_SHARE, OP_MULT, OP_MATMUL, OP_VERIFY_MULT, OP_VERIFY_MATMUL, OP_RECONSTRUCT, OP_RELU,
- OP_MAXPOOL2) = range(8)
+ OP_MAXPOOL2, OP_VERIFY_MULT_CALLS) = range(9)
 SITES = {"GAMMA2": 0, "MZ1": 1, "MZ2": 2, "MX_COPY_P1": 3, "REC_MSG": 4, "HIGH_BIT": 5,
          "AND_GAMMA2": 6}
 TRACE_GF_ROUND = 13
@@ -184,6 +184,24 @@ class Context:
         rc = self.lib.mpc_verify_mult(self.h, verify_id, C.c_void_p(_ptr(xs)), C.c_void_p(_ptr(ys)),
                                       C.c_void_p(_ptr(zs)), n, mult_call_id, R,
                                       C.c_void_p(_ptr(ws)), wsb, C.c_void_p(_ptr(tr)))
+        if rc not in (MPC_OK, MPC_ERR_VERIFY, MPC_ERR_ABORT):
+            self._check(rc)
+        return rc, tr
+
+    def verify_mult_calls(self, verify_id: int, triples, R: int = -1, trace: bool = False):
+        """Deferred Pi_MultVerify over the triples of several mult calls in one batch.
+        triples: list of (xs, ys, zs, n, mult_call_id).  Returns (code, trace) as verify_mult."""
+        k = len(triples)
+        N = sum(int(t[3]) for t in triples)
+        Rr = default_R(N) if R < 0 else R
+        tr = self.zeros((Rr + 1) * TRACE_ROUND) if trace else None
+        wsb = self.ws_size(OP_VERIFY_MULT_CALLS, N, R_main=R)
+        ws = self.workspace(wsb)
+        ptrs = [(C.c_void_p * k)(*(_ptr(t[j]) for t in triples)) for j in range(3)]
+        ns = (C.c_int64 * k)(*(int(t[3]) for t in triples))
+        ids = (C.c_uint64 * k)(*(int(t[4]) for t in triples))
+        rc = self.lib.mpc_verify_mult_calls(self.h, verify_id, k, ptrs[0], ptrs[1], ptrs[2], ns, ids,
+                                            R, C.c_void_p(_ptr(ws)), wsb, C.c_void_p(_ptr(tr)))
         if rc not in (MPC_OK, MPC_ERR_VERIFY, MPC_ERR_ABORT):
             self._check(rc)
         return rc, tr

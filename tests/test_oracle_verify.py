@@ -67,6 +67,46 @@ def test_mult_verify_rejects_faults(site, mask):
         pass
 
 
+def _concat(parts):
+    from oracle.shares import Shared
+    return Shared(*(np.concatenate([getattr(p, f) for p in parts]) for f in Shared.FIELDS))
+
+
+@pytest.mark.parametrize("fault_layer", [None, 0, 3, 5])
+def test_deferred_mult_verify_over_a_chain(fault_layer):
+    """A depth-6 chain z_(l+1) = z_l y_l of Pi_Mult gates checked once over all of its triples
+    (every gate of the circuit in one batch, before any output is opened): an honest run accepts
+    and opens the plaintext chain mod 2^64; an error in any one gate's message is rejected."""
+    from oracle.protocols import reconstruct
+    s = Session(SEED)
+    rng = np.random.default_rng(11)
+    n, D = 40, 6
+    x = rng.integers(0, 2**64, n, dtype=U64)
+    ys = [rng.integers(0, 2**64, n, dtype=U64) for _ in range(D)]
+    Z = share_input(s, x, 1)
+    trip = []
+    for layer in range(D):
+        Y = share_input(s, ys[layer], 10 + layer)
+        if layer == fault_layer:
+            s.arm_fault("MZ1", 7, 1 << 9)
+        Zn = mult(s, Z, Y, 100 + layer)
+        trip.append((Z, Y, Zn))
+        Z = Zn
+    batch = [_concat([t[i] for t in trip]) for i in range(3)]
+    try:
+        ok = mult_verify(s, *batch, 500)
+    except Abort:
+        ok = False
+    if fault_layer is None:
+        assert ok
+        want = x.copy()
+        for y in ys:
+            want = want * y
+        assert np.array_equal(reconstruct(s, Z), want)
+    else:
+        assert not ok
+
+
 @pytest.mark.parametrize("site,mask", [("GAMMA2", 1), ("MZ1", 1), ("MZ2", 5), ("HIGH_BIT", 0)])
 def test_matmul_verify_rejects_faults(site, mask):
     s = Session(SEED)
