@@ -57,3 +57,26 @@ def test_reference_arm_prints_on_rank_zero_only():
     with redirect_stdout(buf):
         bench.run_reference(args, rank=1, world=2)
     assert buf.getvalue() == ""
+
+
+def test_reference_arm_line_keeps_the_contract():
+    """The reference arm (the oracle on the host cores) prints one JSON line with the fields the
+    measurement contract names: the same metric, unit and direction as the GPU arm, and a
+    cpu_baseline / e2e pair describing its own run."""
+    import json
+    args = bench.parse(["--impl", "reference", "--n", "64", "--steps", "1", "--warmup", "3"])
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.run_reference(args, rank=0, world=1)
+    lines = [ln for ln in buf.getvalue().splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
+    assert d["unit"] == "ring-MAC/s" and d["higher_is_better"] is True and d["value"] > 0
+    assert d["metric"].startswith("secure Z_2^64 ring-MAC/s")
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"].startswith("secure GEMM 64x64x64")
