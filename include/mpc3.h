@@ -120,6 +120,16 @@ int64_t mpc_workspace_size(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int
 int mpc_share_input(mpc_ctx* ctx, uint64_t call_id, const uint64_t* x, int x_on_host, int64_t n,
                     uint64_t* xs, void* workspace, size_t workspace_bytes);
 
+/* Pi_<.>^{l,k}(x) (Sec. 2, Secret sharing) for an input owned by P_k, k in {0, 1, 2}.  The owner
+ * holds both seeds of the input's mask, so the sharing equals mpc_share_input's for the same
+ * call_id; only the messages differ.  k = 0 is mpc_share_input: P0 sends m_x to P1 and P2, 2 l
+ * bits per element.  k = 1 (2) keeps its own copy of m_x and sends m_x to P2 (P1), l bits per
+ * element.  Arguments, workspace (MPC_OP_SHARE) and return codes as mpc_share_input;
+ * MPC_ERR_ARG for another owner. */
+int mpc_share_input_from(mpc_ctx* ctx, uint64_t call_id, int owner, const uint64_t* x,
+                         int x_on_host, int64_t n, uint64_t* xs, void* workspace,
+                         size_t workspace_bytes);
+
 /* Pi_Mult (Fig. MultP), elementwise z_i = x_i y_i: preprocessing ([r_z] <- Pi_[.]; P0 shares
  * Gamma = r_x r_y + r_z, 1 l bits) and online phase (P1, P2 exchange [m_z]_j, 2 l bits).
  * xs, ys: device sharings of n elements; zs: device sharing written by the call.  The triples

@@ -57,18 +57,30 @@ def asr(v, t: int) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------------------------
-# Pi_<.>^{l,0}(x): P0 owns x
+# Pi_<.>^{l,k}(x): P_k owns x
 # ---------------------------------------------------------------------------------------------
-def share_input(sess: Session, x, call_id: int, phase: str = ONLINE) -> Shared:
-    """Offline: [r_x] <- Pi_[.] (r1 from eta01, r2 from eta02).  P0 holds both seeds and sends
-    m_x = x + [r_x]_1 + [r_x]_2 to P1 and P2."""
+def share_input(sess: Session, x, call_id: int, phase: str = ONLINE, owner: int = 0) -> Shared:
+    """Pi_<.>^{l,k} (Sec. 2, Secret sharing).  Offline: [r_x] <- Pi_[.] (r1 from eta01, r2 from
+    eta02); the owner P_k holds both seeds of this mask and sends m_x = x + [r_x]_1 + [r_x]_2 to
+    P1 and P2: P0 sends two messages, P1 (P2) keeps its own copy and sends one to P2 (P1).
+    Reading: "P_i send" there is the owner P_k, and the owner's seeds give the same r1, r2 as
+    P0's, so the sharing does not depend on k; only the messages do."""
+    if owner not in (0, 1, 2):
+        raise ValueError("owner must be 0, 1 or 2")
     x = np.asarray(x, dtype=U64) & sess.mask
     obj = obj_id(call_id)
     r1 = sess.prf(C_R1, P_SHARE, obj, x.size).reshape(x.shape)
     r2 = sess.prf(C_R2, P_SHARE, obj, x.size).reshape(x.shape)
     m = (x + r1 + r2) & sess.mask
-    m_p1 = sess.send(0, 1, phase, "share", m, site="MX_COPY_P1")
-    m_p2 = sess.send(0, 2, phase, "share", m)
+    if owner == 0:
+        m_p1 = sess.send(0, 1, phase, "share", m, site="MX_COPY_P1")
+        m_p2 = sess.send(0, 2, phase, "share", m)
+    elif owner == 1:
+        m_p1 = m.copy()
+        m_p2 = sess.send(1, 2, phase, "share", m)
+    else:
+        m_p1 = sess.send(2, 1, phase, "share", m, site="MX_COPY_P1")
+        m_p2 = m.copy()
     return Shared(r1.copy(), r2.copy(), m_p1, r1.copy(), m_p2, r2.copy())
 
 

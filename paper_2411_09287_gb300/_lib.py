@@ -27,6 +27,8 @@ _SIGS = {
                                        C.c_int, C.c_int, C.c_int]),
     "mpc_share_input": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int, C.c_int64,
                                   C.c_void_p, C.c_void_p, C.c_size_t]),
+    "mpc_share_input_from": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_int,
+                                       C.c_int64, C.c_void_p, C.c_void_p, C.c_size_t]),
     "mpc_mult": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_int64,
                            C.c_void_p, C.c_void_p, C.c_size_t]),
     "mpc_matmul": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_int64,

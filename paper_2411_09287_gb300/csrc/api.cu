@@ -1136,9 +1136,16 @@ int64_t mpc_workspace_size(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int
 
 int mpc_share_input(mpc_ctx* ctx, uint64_t call_id, const uint64_t* x, int x_on_host, int64_t n,
                     uint64_t* xs, void* workspace, size_t workspace_bytes) {
+  return mpc_share_input_from(ctx, call_id, 0, x, x_on_host, n, xs, workspace, workspace_bytes);
+}
+
+int mpc_share_input_from(mpc_ctx* ctx, uint64_t call_id, int owner, const uint64_t* x,
+                         int x_on_host, int64_t n, uint64_t* xs, void* workspace,
+                         size_t workspace_bytes) {
   int rc = guard(ctx);
   if (rc) return rc;
   if (n < 0) return fail(ctx, MPC_ERR_SHAPE, "n < 0");
+  if (owner < 0 || owner > 2) return fail(ctx, MPC_ERR_ARG, "share_input: owner must be 0, 1 or 2");
   if (n == 0) return MPC_OK;
   if (!x || !xs || !id_ok(call_id)) return fail(ctx, MPC_ERR_ARG, "share_input: bad argument");
   Arena ar{(char*)workspace, workspace_bytes, 0, false};
@@ -1152,10 +1159,18 @@ int mpc_share_input(mpc_ctx* ctx, uint64_t call_id, const uint64_t* x, int x_on_
     xd = stage;
   }
   launch_share_input(ctx->st, xd, n, ctx->k01, ctx->k02, make_obj(call_id, 0, 0), (u64*)xs, mout);
-  if ((rc = deliver(ctx, MPC_PHASE_ONLINE, MPC_PROTO_SHARE, mout, (u64*)xs + 2 * n, n,
-                    MPC_SITE_MX_COPY_P1)))
+  // m_x: components 2 (P1) and 4 (P2).  The owner P0 sends it to both; P1 or P2 keeps its own
+  // copy and sends one message to the other.  A message arriving at P1 is fault site MX_COPY_P1.
+  u64* m1 = (u64*)xs + 2 * n;
+  u64* m2 = (u64*)xs + 4 * n;
+  if (owner == 1)
+    CK(cudaMemcpyAsync(m1, mout, (size_t)n * 8, cudaMemcpyDeviceToDevice, ctx->st));
+  else if ((rc = deliver(ctx, MPC_PHASE_ONLINE, MPC_PROTO_SHARE, mout, m1, n, MPC_SITE_MX_COPY_P1)))
     return rc;
-  if ((rc = deliver(ctx, MPC_PHASE_ONLINE, MPC_PROTO_SHARE, mout, (u64*)xs + 4 * n, n, -1))) return rc;
+  if (owner == 2)
+    CK(cudaMemcpyAsync(m2, mout, (size_t)n * 8, cudaMemcpyDeviceToDevice, ctx->st));
+  else if ((rc = deliver(ctx, MPC_PHASE_ONLINE, MPC_PROTO_SHARE, mout, m2, n, -1)))
+    return rc;
   return cuda_check(ctx, "share_input");
 }
 

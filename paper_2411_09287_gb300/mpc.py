@@ -133,8 +133,9 @@ class Context:
         return int(v)
 
     # ---- protocols -------------------------------------------------------------------------------
-    def share_input(self, call_id: int, x, out=None):
-        """Pi_<.>^{l,0}(x).  x: CUDA int64 tensor (device input) or numpy uint64 array (host)."""
+    def share_input(self, call_id: int, x, out=None, owner: int = 0):
+        """Pi_<.>^{l,k}(x), k = owner (0: P0, the default).  x: CUDA int64 tensor (device input)
+        or numpy uint64 array (host)."""
         if isinstance(x, np.ndarray):
             xh = np.ascontiguousarray(x, dtype=np.uint64)
             n = xh.size
@@ -145,8 +146,13 @@ class Context:
         out = self.shares(n) if out is None else out
         wsb = self.ws_size(OP_SHARE, n)
         ws = self.workspace(wsb)
-        self._check(self.lib.mpc_share_input(self.h, call_id, C.c_void_p(ptr), on_host, n,
-                                             C.c_void_p(_ptr(out)), C.c_void_p(_ptr(ws)), wsb))
+        if owner == 0:
+            rc = self.lib.mpc_share_input(self.h, call_id, C.c_void_p(ptr), on_host, n,
+                                          C.c_void_p(_ptr(out)), C.c_void_p(_ptr(ws)), wsb)
+        else:
+            rc = self.lib.mpc_share_input_from(self.h, call_id, owner, C.c_void_p(ptr), on_host,
+                                               n, C.c_void_p(_ptr(out)), C.c_void_p(_ptr(ws)), wsb)
+        self._check(rc)
         if on_host:   # the host buffer must stay alive until the copy ran
             self.sync()
         return out

@@ -164,3 +164,41 @@ def test_inconsistent_replica_aborts_at_reconstruction():
     X = share_input(s, np.arange(10, dtype=U64), 1)
     with pytest.raises(Abort):
         reconstruct(s, X)
+
+
+@pytest.mark.parametrize("owner", [0, 1, 2])
+def test_input_owner_k_sharing(owner):
+    """Pi_<.>^{l,k} (Sec. 2): any party P_k can own an input.  The sharing reconstructs to x and,
+    with P_k holding both seeds of the mask, equals P0's sharing of the same call component for
+    component; P0 sends m_x twice (to P1 and P2, 2 l bits per element), P1 or P2 once (to the
+    other one, l bits), and a product of inputs owned by different parties verifies."""
+    from oracle.verify import mult_verify
+    rng = _rng(20 + owner)
+    x = rng.integers(0, 2**64, 50, dtype=U64)
+    y = rng.integers(0, 2**64, 50, dtype=U64)
+    s = Session(SEED)
+    X = share_input(s, x, 5, owner=owner)
+    msgs = [(e.src, e.dst, e.nbytes) for e in s.ledger]
+    want = {0: [(0, 1, 400), (0, 2, 400)], 1: [(1, 2, 400)], 2: [(2, 1, 400)]}[owner]
+    assert msgs == want
+    assert np.array_equal(reconstruct(s, X), x)
+    X0 = share_input(Session(SEED), x, 5, owner=0)
+    for a, b in zip(X.as_tuple(), X0.as_tuple()):
+        assert np.array_equal(a, b)
+    Y = share_input(s, y, 6, owner=(owner + 1) % 3)
+    Z = mult(s, X, Y, 7)
+    assert mult_verify(s, X, Y, Z, 8)
+    assert np.array_equal(reconstruct(s, Z), x * y)
+
+
+def test_owner_two_message_to_p1_inconsistent_aborts():
+    s = Session(SEED)
+    s.arm_fault("MX_COPY_P1", 4, 1 << 3)
+    X = share_input(s, np.arange(10, dtype=U64), 1, owner=2)
+    with pytest.raises(Abort):
+        reconstruct(s, X)
+
+
+def test_input_owner_out_of_range_rejected():
+    with pytest.raises(ValueError):
+        share_input(Session(SEED), np.arange(3, dtype=U64), 1, owner=3)
