@@ -118,6 +118,27 @@ class _Worker(threading.Thread):
             self.server.wake.set()
 
 
+def pack_requests(pending: list, limit: int):
+    """Admit the longest prefix of the arrival-ordered `pending` whose images fit `limit`; the
+    admitted requests leave `pending`.  Returns (requests, images)."""
+    pack, n = [], 0
+    while pending and n + pending[0].x.shape[0] <= limit:
+        r = pending.pop(0)
+        pack.append(r)
+        n += r.x.shape[0]
+    return pack, n
+
+
+def check_admissible(requests, max_batch: int, max_in_flight: int):
+    """Every request must fit one packed pass and the memory budget on its own; otherwise it could
+    never be admitted and the server would wait for it forever."""
+    cap = min(max_batch, max_in_flight)
+    for r in requests:
+        if r.x.shape[0] > cap:
+            raise ValueError(f"request {r.rid} has {r.x.shape[0]} images; at most {cap} fit "
+                             f"(max_batch {max_batch}, memory budget {max_in_flight} images)")
+
+
 class Server:
     def __init__(self, model: Model, n_workers: int = 2, max_batch: int = 256,
                  mem_budget_bytes: float = 64e9, gemm_path: int = M.GEMM_LIMB_TC):
@@ -133,6 +154,7 @@ class Server:
     def serve(self, requests):
         """Run all requests (sorted by arrival); returns them with logits and completion times."""
         reqs = sorted(requests, key=lambda r: r.arrival)
+        check_admissible(reqs, self.max_batch, self.max_in_flight)
         for w in self.workers:
             w.start()
         self.t0 = time.perf_counter()
@@ -145,13 +167,9 @@ class Server:
                 i += 1
             idle = [w for w in self.workers if not w.busy.is_set()]
             if pending and idle:
-                pack, n = [], 0
                 with self.lock:
                     room = self.max_in_flight - self.in_flight
-                while pending and n + pending[0].x.shape[0] <= min(self.max_batch, room):
-                    r = pending.pop(0)
-                    pack.append(r)
-                    n += r.x.shape[0]
+                pack, n = pack_requests(pending, min(self.max_batch, room))
                 if pack:
                     with self.lock:
                         self.in_flight += n
