@@ -1367,6 +1367,7 @@ int mpc_verify_mult_calls(mpc_ctx* ctx, uint64_t verify_id, int ncalls,
     if (!xs[l] || !ys[l] || !zs[l] || !id_ok(call_ids[l]))
       return fail(ctx, MPC_ERR_ARG, "verify_mult_calls: bad argument");
     N += n[l];
+    if (N > (1ll << 40)) return fail(ctx, MPC_ERR_SHAPE, "verify_mult_calls: batch too large");
   }
   Arena ar{(char*)workspace, workspace_bytes, 0, false};
   VMultCallsPlan p = plan_vmult_calls(ar, N, R);
