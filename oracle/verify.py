@@ -16,6 +16,8 @@
 * ``tran_trunc``        consolidation of the trunc pairs' 2E inner products of dimension l; the two
                         inner products of one output share their y vector and are merged
                         (reading V1t); ``tran_trunc_literal`` is the unmerged 2*l*E form.
+* ``trunc_chunks``      the split of a layer's trunc batch into independently verified chunks of
+                        consecutive outputs (reading C1); ``trunc_verify`` runs them.
 
 Readings of the paper (where it is silent, ambiguous or garbled):
   A4  lifting pads with zero coefficients (Fig. MTP text).
@@ -29,6 +31,12 @@ Readings of the paper (where it is silent, ambiguous or garbled):
       error that is a multiple of 2^(l-2) in z (L1 is always a multiple of 4); the tests show it.
   A7  the consolidation weight of triple i is r^i, with row-major (a, b) -> a N + b.
   A8  R = max(0, ceil(log2 D) - 6) unless given.
+  C1  A layer's trunc batch may be split into chunks of at most C consecutive outputs (row-major
+      e = a N + b).  Chunk i is a Pi_BIVerify batch of its own (Fig. PBDP): its own challenge r
+      from the streams of batch 1 + i, weights r^(2e') and r^(2e'+1) over the chunk-local index
+      e' = e - e0, its own R (default from its dimension 64 E_i).  The paper verifies a batch of
+      |G| inner products with error at most |G| / 2^(d-R-2) (Thm. multvv); split batches each
+      keep that bound for their own |G_i|, and a union bound over the chunks gives the layer's.
   Odd length in Pi_Reduce: one (0, 0) pair is appended.
 Parity: pinned by completeness (honest runs give Delta = 0), rejection of injected errors, brute
 force over every challenge on tiny rings against the bounds of Lemma transl / polyred / polyvv,
@@ -37,6 +45,7 @@ Lagrange identities, and literal-vs-consolidated agreement (tests/test_oracle_ve
 from __future__ import annotations
 
 import math
+from types import SimpleNamespace
 
 import numpy as np
 
@@ -323,10 +332,44 @@ def tran_trunc_literal(sess: Session, tp, r, t: int) -> tuple:
     return xs, ys, zs
 
 
+def trunc_chunks(E: int, chunk: int | None) -> list:
+    """Reading C1: the output ranges [e0, e1) of the chunks of a trunc batch of E outputs (one
+    range when chunk is None or at least E)."""
+    C = E if chunk is None else min(E, int(chunk))
+    return [(e0, min(E, e0 + C)) for e0 in range(0, E, C)]
+
+
+def trunc_chunk_pairs(tp, e0: int, e1: int) -> SimpleNamespace:
+    """The bits and <p>, <q> of outputs e0 .. e1-1 of a layer's trunc pairs."""
+    return SimpleNamespace(b1=tp.b1.reshape(-1)[e0:e1], b2=tp.b2.reshape(-1)[e0:e1],
+                           p=tp.p.map(lambda a: a.reshape(-1)[e0:e1]),
+                           q=tp.q.map(lambda a: a.reshape(-1)[e0:e1]))
+
+
 # ---------------------------------------------------------------------------------------------
 # protocol-level entry points
 # ---------------------------------------------------------------------------------------------
 BATCH_MAIN, BATCH_TRUNC = 0, 1
+MAX_TRUNC_CHUNKS = 15   # batch ids 1 .. 15 of the object-id layout
+
+
+def trunc_verify(sess: Session, tp, call_id: int, t: int, R: int | None = None,
+                 chunk: int | None = None, literal: bool = False, trace=None) -> list:
+    """Pi_BIVerify of a layer's trunc pairs, chunk by chunk (reading C1); one bool per chunk."""
+    E = tp.b1.size
+    parts = trunc_chunks(E, chunk)
+    assert len(parts) <= MAX_TRUNC_CHUNKS
+    oks = []
+    for i, (e0, e1) in enumerate(parts):
+        batch = BATCH_TRUNC + i
+        part = trunc_chunk_pairs(tp, e0, e1)
+        r_t = challenge_r(sess, call_id, batch)
+        if literal:
+            xs, ys, zs = tran_trunc_literal(sess, part, r_t, t)
+        else:
+            xs, ys, zs = tran_trunc(sess, part, r_t, t)
+        oks.append(bi_verify(sess, xs, ys, zs, call_id, batch, R, trace))
+    return oks
 
 
 def mult_verify(sess: Session, X: Shared, Y: Shared, Z: Shared, call_id: int,
@@ -339,10 +382,11 @@ def mult_verify(sess: Session, X: Shared, Y: Shared, Z: Shared, call_id: int,
 
 def matmul_verify(sess: Session, X: Shared, W: Shared, res, call_id: int, t: int | None,
                   R_main: int | None = None, R_trunc: int | None = None,
-                  literal: bool = False, trace=None) -> bool:
+                  literal: bool = False, trace=None, trunc_chunk: int | None = None) -> bool:
     """Pi_BIVerify (Fig. PBDP) of one matrix-product layer: the M*N inner products of the
     product (batch 0) and, with truncation, the 2*M*N inner products of its trunc pairs
-    (batch 1).  Returns True iff both batches verify."""
+    (batch 1, or batches 1, 2, ... of at most trunc_chunk outputs each, reading C1).  Returns
+    True iff every batch verifies."""
     r = challenge_r(sess, call_id, BATCH_MAIN)
     if literal:
         xs, ys, zs = tran_matmul_literal(sess, X, W, res.z_pre, r)
@@ -350,16 +394,12 @@ def matmul_verify(sess: Session, X: Shared, W: Shared, res, call_id: int, t: int
         xs, ys, zs = tran_matmul_rank1(sess, X, W, res.z_pre, r)
     ok = bi_verify(sess, xs, ys, zs, call_id, BATCH_MAIN, R_main, trace)
     if res.tp is not None:
-        r_t = challenge_r(sess, call_id, BATCH_TRUNC)
-        if literal:
-            xs, ys, zs = tran_trunc_literal(sess, res.tp, r_t, t)
-        else:
-            xs, ys, zs = tran_trunc(sess, res.tp, r_t, t)
-        ok = bi_verify(sess, xs, ys, zs, call_id, BATCH_TRUNC, R_trunc, trace) and ok
+        ok = all(trunc_verify(sess, res.tp, call_id, t, R_trunc, trunc_chunk, literal,
+                              trace)) and ok
     return ok
 
 
 __all__ = ["Abort", "bi_verify", "challenge_r", "default_R", "inner_verify", "lagrange",
            "matmul_verify", "mult_verify", "reduce_round", "secure_inner_gr", "secure_mult_gr",
            "tran_matmul_literal", "tran_matmul_rank1", "tran_mult", "tran_trunc",
-           "tran_trunc_literal", "trunc_u"]
+           "tran_trunc_literal", "trunc_chunk_pairs", "trunc_chunks", "trunc_u", "trunc_verify"]

@@ -334,3 +334,108 @@ def test_merged_equals_literal_trunc_consolidation():
         e_mrg = _relation_error(gr, *tran_trunc(s, res.tp, r, 13))
         assert np.array_equal(e_lit, e_mrg)
         assert np.any(e_mrg) == corrupt
+
+
+# ---------------------------------------------------------------------------------------------
+# reading C1: the trunc batch split into independently verified chunks of consecutive outputs
+# ---------------------------------------------------------------------------------------------
+def test_trunc_chunks_partition_the_outputs():
+    from oracle.verify import trunc_chunks
+    assert trunc_chunks(10, None) == [(0, 10)]
+    assert trunc_chunks(10, 10) == [(0, 10)]
+    assert trunc_chunks(10, 64) == [(0, 10)]
+    assert trunc_chunks(10, 4) == [(0, 4), (4, 8), (8, 10)]
+    assert trunc_chunks(12, 4) == [(0, 4), (4, 8), (8, 12)]
+    for E, C in [(1, 1), (7, 3), (100, 7), (2**26, 2**24)]:
+        parts = trunc_chunks(E, C)
+        assert parts[0][0] == 0 and parts[-1][1] == E
+        assert all(a1 == b0 for (_, a1), (b0, _) in zip(parts, parts[1:]))
+        assert all(0 < e1 - e0 <= C for e0, e1 in parts)
+
+
+def _chunk_relation_by_definition(s, tp, e0, e1, r, t):
+    """The relation error a chunk's batch certifies, straight from Fig. trunc's two inner
+    products: sum over the chunk's outputs of r^(2e') (sum_j c_j b1_j b2_j - p_e) +
+    r^(2e'+1) (sum_j c'_j b1_j b2_j - q_e), e' = e - e0 (scalars in Python integers mod 2^64)."""
+    from oracle.protocols import trunc_coeffs
+    gr = s.gr
+    c, cp = trunc_coeffs(t, gr.ell)
+    p = tp.p.open(gr.mask).reshape(-1)
+    q = tp.q.open(gr.mask).reshape(-1)
+    pw = gr.powers(r, 2 * (e1 - e0))
+    acc = gr.zeros()
+    for e in range(e0, e1):
+        b1, b2 = int(tp.b1.reshape(-1)[e]), int(tp.b2.reshape(-1)[e])
+        bb = [((b1 >> j) & 1) * ((b2 >> j) & 1) for j in range(gr.ell)]
+        dp = (sum(int(c[j]) * bb[j] for j in range(gr.ell)) - int(p[e])) % (1 << 64)
+        dq = (sum(int(cp[j]) * bb[j] for j in range(gr.ell)) - int(q[e])) % (1 << 64)
+        k = 2 * (e - e0)
+        acc = gr.add(acc, gr.add(gr.scale(pw[k], np.uint64(dp)), gr.scale(pw[k + 1], np.uint64(dq))))
+    return acc
+
+
+@pytest.mark.parametrize("corrupt", [None, 2, 9])
+def test_chunked_trunc_relation_equals_literal_and_definition(corrupt):
+    """Per chunk, the merged consolidation (what the verification runs) carries exactly the
+    relation error of the unmerged one and of Fig. trunc's definition over that chunk's outputs;
+    an error in output e shows up in e's chunk only."""
+    from oracle.verify import trunc_chunk_pairs, trunc_chunks
+    s = Session(SEED)
+    gr = s.gr
+    rng = np.random.default_rng(12)
+    SA = share_input(s, rng.integers(0, 2**64, (3, 4), dtype=U64), 1)
+    SB = share_input(s, rng.integers(0, 2**64, (4, 5), dtype=U64), 2)
+    res = matmul(s, SA, SB, 3, trunc_bits=13)
+    if corrupt is not None:
+        res.tp.q.p1_m.reshape(-1)[corrupt] ^= U64(1 << 40)
+    for i, (e0, e1) in enumerate(trunc_chunks(15, 4)):
+        part = trunc_chunk_pairs(res.tp, e0, e1)
+        r = challenge_r(s, 4, 1 + i)
+        e_mrg = _relation_error(gr, *tran_trunc(s, part, r, 13))
+        e_lit = _relation_error(gr, *tran_trunc_literal(s, part, r, 13))
+        e_def = _chunk_relation_by_definition(s, res.tp, e0, e1, r, 13)
+        assert np.array_equal(e_mrg, e_lit)
+        assert np.array_equal(e_mrg, e_def)
+        assert np.any(e_mrg) == (corrupt is not None and e0 <= corrupt < e1)
+
+
+@pytest.mark.parametrize("fault_out", [None, 0, 6, 14])
+def test_chunked_trunc_verify_accepts_honest_and_rejects_in_the_faulty_chunk(fault_out):
+    from oracle.verify import trunc_verify
+    s = Session(SEED)
+    rng = np.random.default_rng(13)
+    SA = share_input(s, rng.integers(0, 2**64, (3, 4), dtype=U64), 1)
+    SB = share_input(s, rng.integers(0, 2**64, (4, 5), dtype=U64), 2)
+    res = matmul(s, SA, SB, 3, trunc_bits=13)
+    if fault_out is not None:   # P0's Gamma of output fault_out's p inner product, as P2 sees it
+        res.tp.p.p2_m.reshape(-1)[fault_out] ^= U64(1)
+        res.tp.p.p1_m.reshape(-1)[fault_out] ^= U64(1)
+    oks = trunc_verify(s, res.tp, 4, 13, chunk=4)
+    want = [fault_out is None or not (4 * i <= fault_out < 4 * i + 4) for i in range(4)]
+    assert oks == want
+
+
+def test_one_chunk_is_the_unchunked_batch():
+    """With the chunk at least the batch, the chunked verification is the batch's own: the same
+    challenges, rounds and opened Delta."""
+    rng = np.random.default_rng(14)
+    A = rng.integers(0, 2**64, (2, 6), dtype=U64)
+    B = rng.integers(0, 2**64, (6, 3), dtype=U64)
+    traces = []
+    for chunk in (None, 6, 1000):
+        s = Session(SEED)
+        SA, SB = share_input(s, A, 1), share_input(s, B, 2)
+        res = matmul(s, SA, SB, 3, trunc_bits=13)
+        tr = []
+        assert matmul_verify(s, SA, SB, res, 4, 13, trace=tr, trunc_chunk=chunk)
+        traces.append(tr)
+    for other in traces[1:]:
+        assert len(other) == len(traces[0])
+        for a, b in zip(traces[0], other):
+            assert a.keys() == b.keys()
+            for k in a:
+                va, vb = a[k], b[k]
+                if hasattr(va, "as_tuple"):
+                    assert all(np.array_equal(x, y) for x, y in zip(va.as_tuple(), vb.as_tuple()))
+                else:
+                    assert np.array_equal(np.asarray(va), np.asarray(vb))
