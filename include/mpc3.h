@@ -44,7 +44,7 @@ enum {
   MPC_ERR_SHAPE = 2,      /* invalid sizes                                                   */
   MPC_ERR_WORKSPACE = 3,  /* workspace smaller than mpc_workspace_size()                     */
   MPC_ERR_CUDA = 4,       /* a CUDA call failed (message in mpc_last_error)                  */
-  MPC_ERR_TIMEOUT = 5,    /* reserved: a bounded device wait expired                         */
+  MPC_ERR_TIMEOUT = 5,    /* a bounded device wait expired (the context aborts)              */
   MPC_ERR_VERIFY = 6,     /* the batched check found Delta != 0 (Fig. DPV outputs 0)         */
   MPC_ERR_ABORT = 7,      /* Pi_Rec saw inconsistent messages, or the context is aborted     */
   MPC_ERR_PENDING = 8     /* reconstruction requested while products are unverified          */
@@ -92,6 +92,38 @@ typedef struct {
   void* stream;       /* cudaStream_t to run on; NULL: the library creates its own              */
 } mpc_config;
 
+/* Tuning of the verification's data layout and of the tensor-core launches.  No setting changes
+ * a protocol value: every one gives the same messages, revealed challenges, transcript and result
+ * (the parity tests compare several with the oracle).  They trade workspace against time, let an
+ * autotuner pick launch shapes, and let small problems take the code paths that only large ones
+ * take by default.  A field left 0 keeps its default; mpc_get_tuning returns resolved values.
+ *   trunc_block    L, the block of the truncation batch's weights r^(2e), e = e_hi L + e_lo (Fig.
+ *                  PBDP weights, Fig. trunc pairs): a batch of E >= L outputs is blocked, its
+ *                  S-matrix inner sums run per block and, when E is a multiple of L on the
+ *                  tensor-core path, only the first block of powers is kept.  Multiple of 128,
+ *                  at most 65536 (the S-matrix kernel's exactness bound); default 65536.
+ *   trunc_chunk    most outputs per verification chunk of the truncation batch (see
+ *                  mpc_verify_matmul); at least 1; default 2^24.
+ *   row_split      L', rows per block of the blocked batch's folded-vector products
+ *                  (x_e = r^(2 L' e_hi) sum_j b_(e,j) r^(2 e_lo) V_j, e = e_hi L' + e_lo);
+ *                  multiple of 128; default: the odd multiple of 128 near sqrt(E) that pads least.
+ *   tc_combine_min fewest e_hi blocks for which sum_(e_hi) r^(2 L e_hi) S_hi runs on the tensor
+ *                  cores (fewer: CUDA cores); default 32.
+ *   gemm_split_min fewest 32-deep K chunks per split-K slice of a thin tensor-core product;
+ *                  default 8.
+ *   gram_split     split-K slices of a tensor-core Gram sum (dense rounds); default 76.
+ *   fold_batch_max the folds of one Pi_Reduce round share one launch when the folded vectors
+ *                  have at most this many elements; default 65536. */
+typedef struct {
+  int64_t trunc_block;
+  int64_t trunc_chunk;
+  int64_t row_split;
+  int32_t tc_combine_min;
+  int32_t gemm_split_min;
+  int32_t gram_split;
+  int32_t fold_batch_max;
+} mpc_tuning;
+
 /* Create a context (keys, stream, device constants, ledger).  *out is NULL on failure. */
 int mpc_create(const mpc_config* cfg, mpc_ctx** out);
 /* Destroy a context; waits for its work.  NULL is ignored. */
@@ -100,6 +132,12 @@ void mpc_destroy(mpc_ctx* ctx);
 const char* mpc_last_error(const mpc_ctx* ctx);
 /* Run subsequent work on `stream` (cudaStream_t). */
 int mpc_set_stream(mpc_ctx* ctx, void* stream);
+/* Replace the context's tuning (NULL: all defaults).  MPC_ERR_ARG for a value out of range
+ * (negative, or trunc_block / row_split not a multiple of 128, trunc_block > 65536).  Workspace
+ * sizes depend on the tuning: query mpc_workspace_size after setting it. */
+int mpc_set_tuning(mpc_ctx* ctx, const mpc_tuning* tune);
+/* The tuning in force, defaults resolved (row_split 0 means: chosen per batch). */
+int mpc_get_tuning(const mpc_ctx* ctx, mpc_tuning* out);
 /* Wait for all enqueued work; returns MPC_ERR_CUDA on an asynchronous CUDA error. */
 int mpc_sync(mpc_ctx* ctx);
 /* MPC_OK, or MPC_ERR_ABORT once the context has aborted. */
@@ -181,13 +219,24 @@ int mpc_verify_mult_calls(mpc_ctx* ctx, uint64_t verify_id, int ncalls,
  * batch 0 = the M N inner products of Z = X W, consolidated with weights r^(aN+b) and evaluated
  * as the K-dimensional claim sum_k Xt_k Wt_k = zt (rank-1 form: Xt = X^T P, Wt = W Q with P, Q
  * the weight powers); batch 1 (when trunc_bits >= 0) = the 2 M N inner products of the truncation
- * pairs, merged per output into one 64-dimensional inner product.  R_main / R_trunc < 0 select
- * the default max(0, ceil(log2 D) - 6).  Returns as mpc_verify_mult.  trace (device, optional):
- * batch 0 as in mpc_verify_mult, then batch 1 at offset (R_main + 1) * 832. */
+ * pairs, merged per output into one 64-dimensional inner product.  Batch 1 is checked in chunks
+ * of at most tuning.trunc_chunk consecutive outputs (row-major e = aN + b): chunk i covers
+ * outputs [i C, min(E, (i + 1) C)) and is a batch of its own, with its own challenge r (the
+ * streams of batch 1 + i), weights r^(2e') over the chunk-local index e' and its own rounds
+ * (reading of Fig. PBDP: a layer's inner products may be split into independently verified
+ * batches; chunk i is sound up to |G_i| / 2^(d - R_i - 2), Thm. multvv).  At most 15 chunks, else
+ * MPC_ERR_SHAPE.  R_main / R_trunc < 0 select the default max(0, ceil(log2 D) - 6) (D = 64 E_i
+ * per chunk).  Returns as mpc_verify_mult.  trace (device, optional; mpc_trace_words words):
+ * batch 0 as in mpc_verify_mult, then each chunk's R_i + 1 blocks in chunk order. */
 int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, const uint64_t* ws_,
                       const uint64_t* zpre, const uint64_t* pq, int64_t M, int64_t N, int64_t K,
                       int trunc_bits, uint64_t matmul_call_id, int R_main, int R_trunc,
                       void* workspace, size_t workspace_bytes, uint64_t* trace);
+
+/* Words of the optional verification trace of op = MPC_OP_VERIFY_MULT, MPC_OP_VERIFY_MULT_CALLS
+ * or MPC_OP_VERIFY_MATMUL, arguments as mpc_workspace_size; -1 for invalid arguments. */
+int64_t mpc_trace_words(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int64_t c,
+                        int trunc_bits, int R_main, int R_trunc);
 
 /* Pi_Rec (Sec. 2): P0 sends [r]_1 to P2 and [r]_2 to P1, P1 sends m to P0; P1 sends H([r]_1) to
  * P2, P2 sends H(m) to P0 and H([r]_2) to P1 (H = SHA-256 Merkle root, 1 KiB leaves).  On any

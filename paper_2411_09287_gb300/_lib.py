@@ -16,12 +16,22 @@ class MpcConfig(C.Structure):
                 ("gemm_path", C.c_int), ("stream", C.c_void_p)]
 
 
+class MpcTuning(C.Structure):
+    _fields_ = [("trunc_block", C.c_int64), ("trunc_chunk", C.c_int64), ("row_split", C.c_int64),
+                ("tc_combine_min", C.c_int32), ("gemm_split_min", C.c_int32),
+                ("gram_split", C.c_int32), ("fold_batch_max", C.c_int32)]
+
+
 _SIGS = {
     "mpc_create": (C.c_int, [C.POINTER(MpcConfig), C.POINTER(C.c_void_p)]),
     "mpc_destroy": (None, [C.c_void_p]),
     "mpc_last_error": (C.c_char_p, [C.c_void_p]),
     "mpc_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mpc_sync": (C.c_int, [C.c_void_p]),
+    "mpc_set_tuning": (C.c_int, [C.c_void_p, C.POINTER(MpcTuning)]),
+    "mpc_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(MpcTuning)]),
+    "mpc_trace_words": (C.c_int64, [C.c_void_p, C.c_int, C.c_int64, C.c_int64, C.c_int64,
+                                    C.c_int, C.c_int, C.c_int]),
     "mpc_status": (C.c_int, [C.c_void_p]),
     "mpc_workspace_size": (C.c_int64, [C.c_void_p, C.c_int, C.c_int64, C.c_int64, C.c_int64,
                                        C.c_int, C.c_int, C.c_int]),

@@ -135,8 +135,23 @@ inline int default_R(long long D) { return D > 1 ? (int)std::max<long long>(0, c
 
 }  // namespace
 
+namespace {
+mpc_tuning default_tuning() {
+  mpc_tuning t;
+  t.trunc_block = 65536;
+  t.trunc_chunk = 1ll << 24;
+  t.row_split = 0;
+  t.tc_combine_min = 32;
+  t.gemm_split_min = 8;
+  t.gram_split = 76;
+  t.fold_batch_max = 65536;
+  return t;
+}
+}  // namespace
+
 struct mpc_ctx {
   int device = 0;
+  mpc_tuning tune = default_tuning();
   cudaStream_t st = nullptr;
   bool own_stream = false;
   Key k01{}, k02{}, k12{};
@@ -332,7 +347,8 @@ int dense_gemm(mpc_ctx* ctx, long long M, long long N, long long K, const GemmTe
       e1 = prof_event(ctx);
       ctx->recs.push_back({MPC_PROF_K_LIMB_GEMM, e0, e1, (double)M * N * K});
     }
-    if (limb_gemm_tc(ctx->st, M, N, K, 1, &T, e, scratch, ctx->status, ST_TIMEOUT, e0, e1))
+    if (limb_gemm_tc(ctx->st, M, N, K, 1, &T, e, scratch, ctx->status, ST_TIMEOUT, e0, e1,
+                     ctx->tune.gemm_split_min))
       return fail(ctx, MPC_ERR_CUDA, "tensor-core GEMM setup failed");
     return MPC_OK;
   }
@@ -543,7 +559,8 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
       g_launches += 1;
       {
         Phase kp(ctx, MPC_PROF_K_GRAM, 4.0 * Dh * 4096);
-        done = gram3_tc(st, Dh, x.c[0], y.c[1], s.Pmat, ctx->status, ST_TIMEOUT) == 0;
+        done = gram3_tc(st, Dh, x.c[0], y.c[1], s.Pmat, ctx->status, ST_TIMEOUT,
+                        ctx->tune.gram_split) == 0;
       }
       if (done) {
         launch_gr_fold_reduce(st, s.Pmat, 3, s.aux);
@@ -585,7 +602,7 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
   // several latency-bound ones, while on long ones the segment arithmetic of the batched row map
   // costs more than the launches it saves.
   bool batched = false;
-  if (ctx->gemm_path == MPC_GEMM_LIMB_TC && Dh <= 65536) {
+  if (ctx->gemm_path == MPC_GEMM_LIMB_TC && Dh <= ctx->tune.fold_batch_max) {
     const u64* ins[12];
     u64* outs[12];
     int n = 0;
@@ -856,17 +873,12 @@ VMultCallsPlan plan_vmult_calls(Arena& a, long long n, int R) {
   return p;
 }
 
-struct VMatPlan {
-  Small s;
-  u64 *Q, *P, *T, *Pz;
-  Dense dv;
-  IVBuf iv;
-  int R0;
-  // truncation batch
-  bool trunc;
-  int R1, kd;
-  long long Dt;
-  long long L, Epad, nhi;    // S = sum over e_hi < nhi of T_hi (x) (sum over e_lo < L ...)
+// One verification chunk of the truncation batch (E consecutive outputs of the layer).
+struct TruncPlan {
+  long long E = 0;
+  int R1 = 0, kd = 0;
+  long long Dt = 0;
+  long long L = 0, Epad = 0, nhi = 0;   // S = sum over e_hi < nhi of T_hi (x) (sum over e_lo < L ...)
   u64 *b1, *b2, *Rtab, *S, *Zpq, *V, *W, *hsum, *S3, *zt, *S_hi, *Pst, *Thi, *Mhi;
   u64 *B1T, *B2T;   // bit-transposed b1, b2: [j][e / 64]
   unsigned char* TL8;
@@ -879,33 +891,162 @@ struct VMatPlan {
   // sum_e r^(2e) pq_c[e] = sum_{e_hi} T_hi[e_hi] (sum_{e_lo} pq_c[e] r^(2 e_lo)) (a limb GEMM over
   // the first block, then 12 nhi GR products), and the rows r^(2 Lm e_hi) come from T_hi x r^(2 e_lo)
   bool compact = false;
+  bool tc_combine = false;   // sum_{e_hi} T_hi (x) S_hi on the tensor cores
   u64 *Zhi = nullptr, *Zrep = nullptr, *Zprod = nullptr, *Prow = nullptr;
+  u64* pqc = nullptr;        // the chunk's 12 rows of <p>, <q> gathered (chunked batches only)
   Dense dt;
   IVBuf ivt;
-  void* tcs = nullptr;   // tensor-core digit planes (limb path only)
 };
 
-VMatPlan plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R0, int R1,
-                   bool tc) {
-  VMatPlan p;
+struct VMatPlan {
+  Small s;
+  u64 *Q, *P, *T, *Pz;
+  Dense dv;
+  IVBuf iv;
+  int R0;
+  bool trunc = false;
+  long long nchunks = 0, C = 0;   // truncation batch: nchunks chunks of C outputs (the last ragged)
+  TruncPlan tp[2];                // plans of a full chunk and of the ragged last one
+  void* tcs = nullptr;            // tensor-core digit planes (limb path only)
+};
+
+// Layout decisions of a truncation chunk of E outputs (no allocation).
+struct TruncShape {
+  long long L, Epad, nhi, Lm = 0, nhm = 0;
+  int R1, kd;
+  bool compact = false, tc_combine = false, blocked = false;
+};
+
+TruncShape trunc_shape(long long E, int R1, bool tc, const mpc_tuning& tu) {
+  TruncShape h;
+  h.R1 = R1 < 0 ? default_R(64 * E) : R1;
+  h.kd = std::min(h.R1, 6);
+  const long long Lb = tu.trunc_block;
+  h.blocked = E >= Lb;
+  h.L = h.blocked ? Lb : ((E + 127) / 128) * 128;
+  h.Epad = ((E + h.L - 1) / h.L) * h.L;
+  h.nhi = h.Epad / h.L;
+  h.compact = tc && h.kd == 6 && h.blocked && E % h.L == 0;
+  h.tc_combine = tc && h.nhi >= tu.tc_combine_min;
+  if (tc && h.kd == 6 && h.blocked) {
+    if (tu.row_split > 0) {
+      h.Lm = tu.row_split;
+      h.nhm = ((E + h.Lm - 1) / h.Lm + 127) / 128 * 128;
+    } else {
+      // Lm = 128 a with a odd near sqrt(E) / 128, and nhm = 128 b >= E / Lm with the fewest rows
+      // past E: the bit product writes its rows Lm rows apart, and a stride of a multiple of
+      // 2 MB (a even at E = 2^24) puts a tile's 128 rows on the same memory channels
+      long long sq = 1;
+      while (sq * sq < E) ++sq;
+      const long long a0 = (sq + 127) / 128;
+      h.Lm = 128 * a0;
+      h.nhm = ((E + h.Lm - 1) / h.Lm + 127) / 128 * 128;
+      if (a0 >= 4) {   // strides of 512 KB and more
+        long long best = -1;
+        for (long long aa = (a0 * 3 / 4) | 1; aa <= 2 * a0 + 1; aa += 2) {
+          const long long bb = (E + 128 * 128 * aa - 1) / (128 * 128 * aa);
+          const long long rows = 128 * 128 * aa * bb;
+          if (best < 0 || rows < h.Lm * h.nhm ||
+              (rows == h.Lm * h.nhm && std::llabs(aa - a0) < std::llabs(best - a0))) {
+            best = aa;
+            h.Lm = 128 * aa;
+            h.nhm = 128 * bb;
+          }
+        }
+      }
+    }
+  }
+  return h;
+}
+
+// tensor-core scratch of a truncation chunk: the S_hi combination (64 x 262144 x nhi) and the
+// compact table's sum over the first block (12 nhi x 64 x L)
+size_t trunc_tc_scratch(const TruncShape& h) {
+  size_t b = 0;
+  if (h.tc_combine) b = std::max(b, limb_tc_scratch_bytes(64, 262144, h.nhi, 1));
+  if (h.compact) b = std::max(b, limb_tc_scratch_bytes(12 * h.nhi, 64, h.L, 1));
+  return b;
+}
+
+TruncPlan plan_trunc(Arena& a, long long E, int R1, bool tc, bool chunked, const mpc_tuning& tu) {
+  TruncPlan p;
+  const TruncShape h = trunc_shape(E, R1, tc, tu);
+  p.E = E;
+  p.R1 = h.R1;
+  p.kd = h.kd;
+  p.Dt = E * (64 >> p.kd);
+  p.L = h.L;
+  p.Epad = h.Epad;
+  p.nhi = h.nhi;
+  p.compact = h.compact;
+  p.tc_combine = h.tc_combine;
+  p.b1 = a.take<u64>(p.Epad);
+  p.b2 = a.take<u64>(p.Epad);
+  p.Rtab = a.take<u64>((p.compact ? p.L : p.Epad) * 64);
+  p.S = a.take<u64>(4096 * 64);
+  p.TL8 = a.take<unsigned char>(1024 * p.L);
+  p.B1T = a.take<u64>(p.Epad);
+  p.B2T = a.take<u64>(p.Epad);
+  p.S_hi = a.take<u64>(p.nhi * 4096 * 64);
+  p.Pst = a.take<u64>(64ll * 262144);
+  p.Thi = a.take<u64>(p.nhi * 64);
+  p.Mhi = a.take<u64>(std::max<long long>(1, p.nhi - 1) * 4096);
+  p.Zpq = a.take<u64>(12 * 64);
+  p.V = a.take<u64>(4096);
+  p.W = a.take<u64>(4096);
+  p.hsum = a.take<u64>(128);
+  p.S3 = a.take<u64>(2 * 192);
+  p.zt = a.take<u64>(2 * 384);
+  if (chunked) p.pqc = a.take<u64>(12 * E);
+  if (h.Lm) {
+    p.Lm = h.Lm;
+    p.nhm = h.nhm;
+    p.Tm = a.take<u64>(p.Lm * 4096);
+    p.Bm = a.take<u64>((E + p.Lm - 1) / p.Lm * 4096);
+    if (p.compact) {
+      p.Zhi = a.take<u64>(12 * p.nhi * 64);
+      p.Zrep = a.take<u64>(12 * p.nhi * 64);
+      p.Zprod = a.take<u64>(12 * p.nhi * 64);
+      p.Prow = a.take<u64>(3 * ((E + p.Lm - 1) / p.Lm) * 64);
+    }
+    p.Vm = a.take<u64>(64 * 4096);
+    p.bT = a.take<u64>(p.nhm * p.Lm);
+  }
+  const bool xc[6] = {true, false, false, true, false, false};
+  const bool yc[6] = {false, true, false, false, false, true};
+  p.dt = plan_dense(a, p.Dt, xc, yc);
+  p.ivt = plan_iv(a, dim_after(p.Dt, p.R1 - p.kd));
+  return p;
+}
+
+// Chunks of the truncation batch of E outputs: n chunks of C outputs, the last E - (n-1) C.
+void trunc_chunks(long long E, const mpc_tuning& tu, long long* n, long long* C) {
+  *C = std::min<long long>(E, tu.trunc_chunk);
+  *n = (E + *C - 1) / *C;
+}
+constexpr long long MAX_TRUNC_CHUNKS = 15;   // batch ids 1 .. 15 of the object-id layout
+
+// false when the layer cannot be planned (too many truncation chunks)
+bool plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R0, int R1, bool tc,
+               const mpc_tuning& tu, VMatPlan& p) {
   p.R0 = R0 < 0 ? default_R(K) : R0;
   p.s = plan_small(a);
-  // digit planes of the batch-0 products (X^T P, W Q, Z Q) and of the truncation batch's S_hi
-  // combination (64 x 262144 x nhi) on the tensor-core path
-  long long nhi_tc = 0, zrows_tc = 0, L_tc = 0;
-  if (t >= 0) {
-    const long long E = M * N, L = E >= 65536 ? 65536 : ((E + 127) / 128) * 128;
-    nhi_tc = (E + L - 1) / L;
-    L_tc = L;
-    const int kd = std::min(R1 < 0 ? default_R(64 * E) : R1, 6);
-    if (tc && kd == 6 && E >= 65536 && E % L == 0) zrows_tc = 12 * nhi_tc;   // compact table
-    if (nhi_tc < 32) nhi_tc = 0;   // short combinations stay on the CUDA cores (no plane scratch)
+  p.trunc = t >= 0;
+  const long long E = M * N;
+  long long Elast = 0;
+  size_t trunc_tcs = 0;
+  if (p.trunc) {
+    trunc_chunks(E, tu, &p.nchunks, &p.C);
+    if (p.nchunks > MAX_TRUNC_CHUNKS) return false;
+    Elast = E - (p.nchunks - 1) * p.C;
+    trunc_tcs = std::max(trunc_tc_scratch(trunc_shape(p.C, R1, tc, tu)),
+                         trunc_tc_scratch(trunc_shape(Elast, R1, tc, tu)));
   }
+  // digit planes of the batch-0 products (X^T P, W Q, Z Q) and of the truncation chunks'
+  // tensor-core products, on the tensor-core path
   p.tcs = tc ? (void*)a.take<unsigned char>((long long)std::max(
                    {limb_tc_scratch_bytes(K, 64, M, 1), limb_tc_scratch_bytes(K, 64, N, 1),
-                    limb_tc_scratch_bytes(6 * M, 64, N, 1),
-                    nhi_tc ? limb_tc_scratch_bytes(64, 262144, nhi_tc, 1) : (size_t)0,
-                    zrows_tc ? limb_tc_scratch_bytes(zrows_tc, 64, L_tc, 1) : (size_t)0}))
+                    limb_tc_scratch_bytes(6 * M, 64, N, 1), trunc_tcs}))
              : nullptr;
   p.Q = a.take<u64>(N * 64);
   p.P = a.take<u64>(M * 64);
@@ -914,73 +1055,250 @@ VMatPlan plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R
   const bool all[6] = {true, true, true, true, true, true};
   p.dv = plan_dense(a, K, all, all);
   p.iv = plan_iv(a, dim_after(K, p.R0));
-  p.trunc = t >= 0;
   if (p.trunc) {
-    const long long E = M * N;
-    const long long D0 = 64 * E;
-    p.R1 = R1 < 0 ? default_R(D0) : R1;
-    p.kd = std::min(p.R1, 6);
-    p.Dt = E * (64 >> p.kd);
-    p.L = E >= 65536 ? 65536 : ((E + 127) / 128) * 128;
-    p.Epad = ((E + p.L - 1) / p.L) * p.L;
-    p.nhi = p.Epad / p.L;
-    p.b1 = a.take<u64>(p.Epad);
-    p.b2 = a.take<u64>(p.Epad);
-    p.compact = zrows_tc > 0;
-    p.Rtab = a.take<u64>((p.compact ? p.L : p.Epad) * 64);
-    p.S = a.take<u64>(4096 * 64);
-    p.TL8 = a.take<unsigned char>(1024 * p.L);
-    p.B1T = a.take<u64>(p.Epad);
-    p.B2T = a.take<u64>(p.Epad);
-    p.S_hi = a.take<u64>(p.nhi * 4096 * 64);
-    p.Pst = a.take<u64>(64ll * 262144);
-    p.Thi = a.take<u64>(p.nhi * 64);
-    p.Mhi = a.take<u64>(std::max<long long>(1, p.nhi - 1) * 4096);
-    p.Zpq = a.take<u64>(12 * 64);
-    p.V = a.take<u64>(4096);
-    p.W = a.take<u64>(4096);
-    p.hsum = a.take<u64>(128);
-    p.S3 = a.take<u64>(2 * 192);
-    p.zt = a.take<u64>(2 * 384);
-    if (tc && p.kd == 6 && E >= 65536) {
-      // Lm = 128 a with a odd near sqrt(E) / 128, and nhm = 128 b >= E / Lm with the fewest rows
-      // past E: the bit product writes its rows Lm rows apart, and a stride of a multiple of
-      // 2 MB (a even at E = 2^24) puts a tile's 128 rows on the same memory channels
-      long long sq = 1;
-      while (sq * sq < E) ++sq;
-      const long long a0 = (sq + 127) / 128;
-      p.Lm = 128 * a0;
-      p.nhm = ((E + p.Lm - 1) / p.Lm + 127) / 128 * 128;
-      if (a0 >= 4) {   // strides of 512 KB and more
-        long long best = -1;
-        for (long long aa = (a0 * 3 / 4) | 1; aa <= 2 * a0 + 1; aa += 2) {
-          const long long bb = (E + 128 * 128 * aa - 1) / (128 * 128 * aa);
-          const long long rows = 128 * 128 * aa * bb;
-          if (best < 0 || rows < p.Lm * p.nhm ||
-              (rows == p.Lm * p.nhm && std::llabs(aa - a0) < std::llabs(best - a0))) {
-            best = aa;
-            p.Lm = 128 * aa;
-            p.nhm = 128 * bb;
-          }
-        }
-      }
-      p.Tm = a.take<u64>(p.Lm * 4096);
-      p.Bm = a.take<u64>((E + p.Lm - 1) / p.Lm * 4096);
-      if (p.compact) {
-        p.Zhi = a.take<u64>(12 * p.nhi * 64);
-        p.Zrep = a.take<u64>(12 * p.nhi * 64);
-        p.Zprod = a.take<u64>(12 * p.nhi * 64);
-        p.Prow = a.take<u64>(3 * ((E + p.Lm - 1) / p.Lm) * 64);
-      }
-      p.Vm = a.take<u64>(64 * 4096);
-      p.bT = a.take<u64>(p.nhm * p.Lm);
+    // the chunks run one after another: their plans share the rest of the workspace
+    const bool chunked = p.nchunks > 1;
+    const size_t off0 = a.off;
+    p.tp[0] = plan_trunc(a, p.C, R1, tc, chunked, tu);
+    const size_t off1 = a.off;
+    if (Elast != p.C) {
+      a.off = off0;
+      p.tp[1] = plan_trunc(a, Elast, R1, tc, chunked, tu);
+      a.off = std::max(off1, a.off);
+    } else {
+      p.tp[1] = p.tp[0];
     }
-    const bool xc[6] = {true, false, false, true, false, false};
-    const bool yc[6] = {false, true, false, false, false, true};
-    p.dt = plan_dense(a, p.Dt, xc, yc);
-    p.ivt = plan_iv(a, dim_after(p.Dt, p.R1 - p.kd));
   }
-  return p;
+  return true;
+}
+
+// One chunk of batch 1 of Pi_BIVerify (Fig. PBDP): the 2 E inner products of the truncation pairs
+// of outputs e0 .. e0 + E - 1 (E = p.E) of a layer of E_all outputs, with the challenge and round
+// streams of batch `batch`.  pq_all: the layer's 12 rows of <p>, <q> (stride E_all).
+int verify_trunc_chunk(mpc_ctx* ctx, TruncPlan& p, const Small& s, void* tcs, const u64* pq_all,
+                       long long E_all, long long e0, int trunc_bits, u64 verify_id, u32 batch,
+                       u64 matmul_call_id, u64* tr) {
+  cudaStream_t st = ctx->st;
+  Phase* phase = new Phase(ctx, MPC_PROF_TRUNC_SETUP);
+  const u64 mobj = make_obj(matmul_call_id, 0, 0);
+  const long long E = p.E;
+  int rc;
+  if (p.pqc)   // this chunk's outputs of the 12 rows of <p>, <q>, gathered to a stride of E
+    CK(cudaMemcpy2DAsync(p.pqc, (size_t)E * 8, pq_all + e0, (size_t)E_all * 8, (size_t)E * 8, 12,
+                         cudaMemcpyDeviceToDevice, st));
+  const u64* pq = p.pqc ? p.pqc : pq_all;
+  reveal(ctx, P_VER_R, make_obj(verify_id, batch, 0), s.tmp6, s.r);
+  launch_trunc_u(st, s.r, trunc_bits, p.V);                         // V_j = u_j
+  for (int j = 0; j < 64; ++j)
+    CK(cudaMemcpyAsync(p.W + j * 64, ctx->cst + CST_ONE, 512, cudaMemcpyDeviceToDevice, st));
+  if (p.Epad > E) {
+    CK(cudaMemsetAsync(p.b1 + E, 0, (size_t)(p.Epad - E) * 8, st));
+    CK(cudaMemsetAsync(p.b2 + E, 0, (size_t)(p.Epad - E) * 8, st));
+  }
+  launch_prf_words(st, E, ctx->k01, make_tag(P_TRUNC_BITS, C_TB1), mobj, p.b1, e0);
+  launch_prf_words(st, E, ctx->k02, make_tag(P_TRUNC_BITS, C_TB2), mobj, p.b2, e0);
+  launch_gr_mul1(st, s.r, s.r, s.aux + 64);                          // r^2
+  // r^(2e) for e < Epad: r^(2 e_lo) for e_lo < L by repeated multiplication, then every further
+  // block of L rows is that block times the constant r^(2 L e_hi) (a 64 x 64 matrix product)
+  launch_gr_powers(st, s.aux + 64, p.L, p.Rtab);
+  if (p.compact) {
+    launch_gr_mul1(st, p.Rtab + (p.L - 1) * 64, s.aux + 64, s.aux + 128);   // r^(2L)
+    launch_gr_powers(st, s.aux + 128, p.nhi, p.Thi);
+  } else if (p.nhi > 1) {
+    launch_gr_mul1(st, p.Rtab + (p.L - 1) * 64, s.aux + 64, s.aux + 128);   // r^(2L)
+    launch_gr_powers(st, s.aux + 128, p.nhi, p.Thi);
+    // rows h L + e_lo (h >= 1) = r^(2 L h) r^(2 e_lo): one grouped product, matrix h - 1 for
+    // the rows (h - 1) L .. h L - 1 of the block, each reading row e_lo of the first block
+    launch_gr_mulmat_batch(st, p.nhi - 1, p.Thi + 64, 64, p.Mhi);
+    bool done = false;
+    if (ctx->gemm_path == MPC_GEMM_LIMB_TC) {
+      GrMMArgs g{};
+      g.R = (p.nhi - 1) * p.L;
+      g.p0 = p.Rtab;
+      g.in = GrRowMap{p.L, 64, 0};
+      g.Mmat = p.Mhi;
+      g.mrows = p.L;
+      g.out = p.Rtab + p.L * 64;
+      g.om = GrRowMap{0, 64, 0};
+      g_launches += 1;
+      Phase kp(ctx, MPC_PROF_K_GR_MATMUL, (double)g.R * 4096);
+      done = gr_matmul_tc_ex(st, g, ctx->status, ST_TIMEOUT) == 0;
+      if (!done) g_launches -= 1;
+    }
+    for (long long h = 1; h < p.nhi && !done; ++h)
+      if ((rc = gr_matmul(ctx, p.L, p.Rtab, nullptr, 1, 64, p.Mhi + (h - 1) * 4096, nullptr, 0,
+                          p.Rtab + h * p.L * 64, 64)))
+        return rc;
+  }
+  CK(cudaMemsetAsync(p.Zpq, 0, 12 * 64 * 8, st));
+  // sum_e r^(2e) p_c[e], sum_e r^(2e) q_c[e]: (12 x E) . (E x 64)
+  if (p.compact) {
+    // Zhi[c nhi + h] = sum_{e_lo} pq_c[h L + e_lo] r^(2 e_lo) (E = nhi L: one strided view)
+    GemmTerm T;
+    T.A = op(pq, p.L);
+    T.B = op(p.Rtab, 64);
+    if ((rc = dense_gemm(ctx, 12 * p.nhi, 64, p.L, T, epi_store(p.Zhi, 64), tcs))) return rc;
+    launch_gather_rows_affine(st, 12 * p.nhi, p.Thi, 1, 1, p.nhi, p.Zrep);   // T_hi[h]
+    launch_gr_mul_rows(st, 12 * p.nhi, p.Zhi, p.Zrep, p.Zprod);
+    launch_block_rowsum(st, 12, p.nhi, p.Zprod, p.Zpq);
+  } else {
+    launch_scalar_gr_sum(st, E, pq, E, 12, p.Rtab, p.Zpq);
+  }
+  u64* z0 = p.zt + 384;
+  for (int c = 0; c < 6; ++c)   // z_c = sum r^(2e) p_c + r sum r^(2e) q_c
+    launch_gr_lincomb(st, ctx->cst + CST_ONE, p.Zpq + c * 64, s.r, p.Zpq + (6 + c) * 64,
+                      z0 + c * 64);
+  delete phase;
+  phase = new Phase(ctx, MPC_PROF_TRUNC_S);
+  {  // S_{j,j'} = sum_e r^(2e) b1_{e,j} b2_{e,j'} (P0), with r^(2e) = r^(2 L e_hi) r^(2 e_lo):
+     // tensor cores for the inner sums over e_lo, then sum_{e_hi} T_hi (x) S_hi as a GEMM + fold
+    launch_trunc_limb_table(st, p.Rtab, p.L, p.TL8);
+    launch_trunc_bit_transpose(st, p.b1, p.Epad, p.B1T);
+    launch_trunc_bit_transpose(st, p.b2, p.Epad, p.B2T);
+    {
+      Phase kphase(ctx, MPC_PROF_K_TRUNC_S, 4096.0 * 64 * E);
+      g_launches += 1;
+      if (launch_trunc_s_tc(st, p.B1T, p.B2T, p.Epad, p.TL8, p.L, p.nhi, p.S_hi, ctx->status,
+                            ST_TIMEOUT))
+        return fail(ctx, MPC_ERR_CUDA, "verify_matmul: tensor map of the limb table");
+    }
+    GemmTerm T;
+    // A[a][e_hi] = coefficient a of r^(2 L e_hi)
+    T.A = p.compact ? op(p.Thi, 64, 1) : op(p.Rtab, p.L * 64, 1);
+    T.B = op(p.S_hi, 262144);            // B[e_hi][(p, b)]
+    if ((rc = dense_gemm(ctx, 64, 262144, p.nhi, T, epi_store(p.Pst, 262144),
+                         p.tc_combine ? tcs : nullptr)))
+      return rc;
+    launch_fold_reduce_strided(st, p.Pst, 262144, 4096, p.S);
+  }
+  delete phase;
+  phase = new Phase(ctx, MPC_PROF_TRUNC_ROUNDS);
+  const u64* z = z0;
+  u64* zbuf[2] = {s.z[0], s.z[1]};
+  int zi = 0;
+  for (int k = 1; k <= p.kd; ++k) {   // rounds folding the 64 bits of each output
+    const u64 obj = make_obj(verify_id, batch, (u32)k);
+    CK(cudaMemsetAsync(p.hsum, 0, 128 * 8, st));
+    launch_trunc_round_h(st, p.V, p.W, p.S, k, ctx->cst + CST_LAM, p.hsum);
+    CK(cudaMemsetAsync(p.S3, 0, 2 * 192 * 8, st));
+    CK(cudaMemcpyAsync(p.S3, p.hsum, 512, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(p.S3 + 192, p.hsum + 64, 512, cudaMemcpyDeviceToDevice, st));
+    inner_finish(ctx, p.S3, P_VER_H0, obj, s.h0);
+    inner_finish(ctx, p.S3 + 192, P_VER_H2, obj, s.h2);
+    reveal(ctx, P_VER_ZETA, obj, s.tmp6, s.zp);
+    launch_gr_lagrange(st, s.zp, ctx->reduce_mode, ctx->cst + CST_INV, s.coef);
+    launch_gr_combine_z(st, s.coef, s.h0, s.h2, z, zbuf[zi]);
+    z = zbuf[zi];
+    zi ^= 1;
+    launch_trunc_update_vw(st, p.V, p.W, k, s.coef);
+    trace_round(ctx, tr, k, s);
+  }
+  delete phase;
+  phase = new Phase(ctx, MPC_PROF_TRUNC_MATERIALIZE);
+  // materialise the folded vectors: x.[r]_1 at P0 and P1, y.[r]_2 at P0 and P2
+  Vec& tx = p.dt.x[0];
+  Vec& ty = p.dt.y[0];
+  if (ctx->gemm_path == MPC_GEMM_LIMB_TC && p.kd == 6) {
+    // one folded element per output e: -sum_j V_j b_{e,j} as a product of the bit matrix with
+    // -V on the tensor cores, then (x only) the GR product with r^(2e), for each party's copy
+    u64* nV = s.MM;
+    u64* nW = s.MM + 4096;
+    launch_neg_copy(st, p.V, 4096, nV);
+    launch_neg_copy(st, p.W, 4096, nW);
+    const u64* bits[4] = {p.b1, p.b1, p.b2, p.b2};
+    const u64* mats[4] = {nV, nV, nW, nW};
+    u64* outs[4] = {tx.c[0], tx.c[3], ty.c[1], ty.c[5]};
+    auto grmm = [&](const GrMMArgs& g, double work) {
+      g_launches += 1;
+      Phase kp(ctx, MPC_PROF_K_GR_MATMUL, work);
+      return gr_matmul_tc_ex(st, g, ctx->status, ST_TIMEOUT);
+    };
+    if (p.Lm) {
+      // x_e = r^(2 Lm e_hi) (sum_j b_{e,j} r^(2 e_lo) (-V_j)): the per-row factor r^(2e) split
+      // into two grouped GR matrix products on the tensor cores.
+      const long long Lm = p.Lm, nhm = p.nhm, nB = (E + Lm - 1) / Lm;
+      launch_gr_mulmat_batch(st, 64, nV, 64, p.Vm);
+      if (p.compact) {   // r^(2 Lm e_hi) = T_hi[e / L] r^(2 (e mod L)), e = e_hi Lm
+        u64* ra = p.Prow;
+        u64* rb = p.Prow + nB * 64;
+        u64* rr = p.Prow + 2 * nB * 64;
+        launch_gather_rows_affine(st, nB, p.Thi, Lm, p.L, 0, ra);
+        launch_gather_rows_affine(st, nB, p.Rtab, Lm, 1, p.L, rb);
+        launch_gr_mul_rows(st, nB, ra, rb, rr);
+        launch_gr_mulmat_batch(st, nB, rr, 64, p.Bm);
+      } else {
+        launch_gr_mulmat_batch(st, nB, p.Rtab, Lm * 64, p.Bm);
+      }
+      launch_word_transpose(st, nhm, Lm, E, p.b1, p.bT);
+      GrMMArgs g{};
+      // Tm: rows sigma = j Lm + e_lo read r^(2 e_lo) and use matrix j; written at [e_lo][j]
+      g.R = 64 * Lm;
+      g.p0 = p.Rtab;
+      g.in = GrRowMap{Lm, 64, 0};
+      g.Mmat = p.Vm;
+      g.mrows = Lm;
+      g.out = p.Tm;
+      g.om = GrRowMap{Lm, 4096, 64};
+      if (grmm(g, 64.0 * Lm * 4096)) return fail(ctx, MPC_ERR_CUDA, "verify_matmul: r^(2e) V table");
+      for (int v = 0; v < 2; ++v) {
+        // rows rho = e_lo nhm + e_hi (bits b_e), matrix Tm[e_lo], result at row e
+        GrMMArgs ga{};
+        ga.R = nhm * Lm;
+        ga.p0 = p.bT;
+        ga.in = GrRowMap{0, 1, 0};
+        ga.a_bits = 1;
+        ga.Mmat = p.Tm;
+        ga.mrows = nhm;
+        ga.out = outs[v];
+        ga.om = GrRowMap{nhm, Lm * 64, 64};
+        ga.out_lim = E * 64;
+        if (grmm(ga, (double)nhm * Lm * 4096 * 8.0 / 36.0))
+          return fail(ctx, MPC_ERR_CUDA, "verify_matmul: folded-vector product");
+        // in place: rows e, matrix M(r^(2 Lm e_hi)) for e_hi = e / Lm
+        GrMMArgs gb{};
+        gb.R = E;
+        gb.p0 = outs[v];
+        gb.in = GrRowMap{0, 64, 0};
+        gb.Mmat = p.Bm;
+        gb.mrows = Lm;
+        gb.out = outs[v];
+        gb.om = GrRowMap{0, 64, 0};
+        if (grmm(gb, (double)E * 4096))
+          return fail(ctx, MPC_ERR_CUDA, "verify_matmul: r^(2e) factor");
+      }
+    }
+    for (int v = p.Lm ? 2 : 0; v < 4; ++v) {
+      GrMMArgs g{};
+      g.R = E;
+      g.p0 = bits[v];
+      g.in = GrRowMap{0, 1, 0};
+      g.a_bits = 1;
+      g.Mmat = mats[v];
+      g.out = outs[v];
+      g.om = GrRowMap{0, 64, 0};
+      // A has digit plane 0 only: 8 of the 36 digit-pair products (work in 36-pair units)
+      if (grmm(g, (double)E * 4096 * 8.0 / 36.0))
+        return fail(ctx, MPC_ERR_CUDA, "verify_matmul: folded-vector product");
+      if (v < 2) {
+        Phase kp(ctx, MPC_PROF_K_GR_MUL_ROWS, (double)E * 4096);
+        launch_gr_mul_rows(st, E, outs[v], p.Rtab, outs[v]);
+      }
+    }
+  } else {
+    launch_trunc_materialize(st, E, p.b1, p.V, p.Rtab, p.kd, tx.c[0]);
+    launch_trunc_materialize(st, E, p.b1, p.V, p.Rtab, p.kd, tx.c[3]);
+    launch_trunc_materialize(st, E, p.b2, p.W, nullptr, p.kd, ty.c[1]);
+    launch_trunc_materialize(st, E, p.b2, p.W, nullptr, p.kd, ty.c[5]);
+  }
+  delete phase;
+  if ((rc = cuda_check(ctx, "trunc batch"))) return rc;
+  phase = new Phase(ctx, MPC_PROF_TRUNC_TAIL);
+  // the claim entering the dense rounds must not alias their round scratch
+  CK(cudaMemcpyAsync(s.zinit, z, 384 * 8, cudaMemcpyDeviceToDevice, st));
+  p.dt.cur = 0;
+  rc = run_dense(ctx, verify_id, batch, p.dt, p.Dt, s.zinit, p.kd + 1, p.R1, s, p.ivt, tr);
+  delete phase;
+  return rc;
 }
 
 }  // namespace
@@ -1077,6 +1395,60 @@ int mpc_status(const mpc_ctx* ctx) {
   return ctx->aborted ? MPC_ERR_ABORT : MPC_OK;
 }
 
+int mpc_set_tuning(mpc_ctx* ctx, const mpc_tuning* tune) {
+  if (!ctx) return MPC_ERR_ARG;
+  mpc_tuning t = default_tuning();
+  if (tune) {
+    if (tune->trunc_block < 0 || tune->trunc_chunk < 0 || tune->row_split < 0 ||
+        tune->tc_combine_min < 0 || tune->gemm_split_min < 0 || tune->gram_split < 0 ||
+        tune->fold_batch_max < 0 || tune->trunc_block % 128 || tune->row_split % 128 ||
+        tune->trunc_block > 65536 || tune->gram_split > 65535)
+      return fail(ctx, MPC_ERR_ARG, "set_tuning: value out of range");
+    if (tune->trunc_block) t.trunc_block = tune->trunc_block;
+    if (tune->trunc_chunk) t.trunc_chunk = tune->trunc_chunk;
+    t.row_split = tune->row_split;
+    if (tune->tc_combine_min) t.tc_combine_min = tune->tc_combine_min;
+    if (tune->gemm_split_min) t.gemm_split_min = tune->gemm_split_min;
+    if (tune->gram_split) t.gram_split = tune->gram_split;
+    if (tune->fold_batch_max) t.fold_batch_max = tune->fold_batch_max;
+  }
+  ctx->tune = t;
+  return MPC_OK;
+}
+
+int mpc_get_tuning(const mpc_ctx* ctx, mpc_tuning* out) {
+  if (!ctx || !out) return MPC_ERR_ARG;
+  *out = ctx->tune;
+  return MPC_OK;
+}
+
+int64_t mpc_trace_words(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int64_t c,
+                        int trunc_bits, int R_main, int R_trunc) {
+  switch (op) {
+    case MPC_OP_VERIFY_MULT:
+    case MPC_OP_VERIFY_MULT_CALLS:
+      if (a <= 0) return -1;
+      return (int64_t)((R_main < 0 ? default_R(a) : R_main) + 1) * TRACE_ROUND;
+    case MPC_OP_VERIFY_MATMUL: {
+      if (a <= 0 || b <= 0 || c <= 0 || trunc_bits > 63) return -1;
+      int64_t w = (int64_t)((R_main < 0 ? default_R(c) : R_main) + 1) * TRACE_ROUND;
+      if (trunc_bits >= 0) {
+        const mpc_tuning tu = ctx ? ctx->tune : default_tuning();
+        long long n = 0, C = 0;
+        trunc_chunks(a * b, tu, &n, &C);
+        if (n > MAX_TRUNC_CHUNKS) return -1;
+        for (long long i = 0; i < n; ++i) {
+          const long long Ei = i == n - 1 ? a * b - (n - 1) * C : C;
+          w += (int64_t)((R_trunc < 0 ? default_R(64 * Ei) : R_trunc) + 1) * TRACE_ROUND;
+        }
+      }
+      return w;
+    }
+    default:
+      return -1;
+  }
+}
+
 namespace {
 void nl_plan_take(Arena& a, int nst, const long long np[2]);   // workspace of a non-linear layer
 }
@@ -1107,10 +1479,15 @@ int64_t mpc_workspace_size(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int
       if (a <= 0) return -1;
       plan_vmult_calls(ar, a, R_main);
       break;
-    case MPC_OP_VERIFY_MATMUL:
-      if (a <= 0 || b <= 0 || c <= 0) return -1;
-      plan_vmat(ar, a, b, c, trunc_bits, R_main, R_trunc, ctx && ctx->gemm_path == MPC_GEMM_LIMB_TC);
+    case MPC_OP_VERIFY_MATMUL: {
+      if (a <= 0 || b <= 0 || c <= 0 || trunc_bits > 63) return -1;
+      VMatPlan vp;
+      if (!plan_vmat(ar, a, b, c, trunc_bits, R_main, R_trunc,
+                     ctx && ctx->gemm_path == MPC_GEMM_LIMB_TC, ctx ? ctx->tune : default_tuning(),
+                     vp))
+        return -1;
       break;
+    }
     case MPC_OP_RELU: {
       if (a <= 0) return -1;
       const long long np[2] = {64 * ((a + 63) / 64), 0};
@@ -1227,7 +1604,8 @@ int mpc_matmul(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_
       e1 = prof_event(ctx);
       ctx->recs.push_back({MPC_PROF_K_LIMB_GEMM, e0, e1, (double)M * N * K * nterms});
     }
-    const int r = limb_gemm_tc(ctx->st, M, N, K, nterms, T, e, p.tc, ctx->status, ST_TIMEOUT, e0, e1);
+    const int r = limb_gemm_tc(ctx->st, M, N, K, nterms, T, e, p.tc, ctx->status, ST_TIMEOUT, e0, e1,
+                               ctx->tune.gemm_split_min);
     return r ? fail(ctx, MPC_ERR_CUDA, "matmul: tensor-core GEMM setup failed") : MPC_OK;
   };
   if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "matmul: workspace too small");
@@ -1401,8 +1779,10 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
       trunc_bits > 63)
     return fail(ctx, MPC_ERR_ARG, "verify_matmul: bad argument");
   Arena ar{(char*)workspace, workspace_bytes, 0, false};
-  VMatPlan p = plan_vmat(ar, M, N, K, trunc_bits, R_main, R_trunc,
-                         ctx->gemm_path == MPC_GEMM_LIMB_TC);
+  VMatPlan p;
+  if (!plan_vmat(ar, M, N, K, trunc_bits, R_main, R_trunc, ctx->gemm_path == MPC_GEMM_LIMB_TC,
+                 ctx->tune, p))
+    return fail(ctx, MPC_ERR_SHAPE, "verify_matmul: more than 15 truncation chunks");
   if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "verify_matmul: workspace too small");
   cudaStream_t st = ctx->st;
   const Small& s = p.s;
@@ -1439,223 +1819,16 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
   rc = run_dense(ctx, verify_id, 0, p.dv, K, s.zinit, 1, p.R0, s, p.iv, trace);
   delete phase;
   if (rc) return rc;
-  // ---- batch 1: the truncation pairs ----
+  // ---- batch 1: the truncation pairs, chunk by chunk ----
   if (trunc) {
-    phase = new Phase(ctx, MPC_PROF_TRUNC_SETUP);
     u64* tr = trace ? trace + (long long)(p.R0 + 1) * TRACE_ROUND : nullptr;
-    const u64 mobj = make_obj(matmul_call_id, 0, 0);
-    reveal(ctx, P_VER_R, make_obj(verify_id, 1, 0), s.tmp6, s.r);
-    launch_trunc_u(st, s.r, trunc_bits, p.V);                         // V_j = u_j
-    for (int j = 0; j < 64; ++j)
-      CK(cudaMemcpyAsync(p.W + j * 64, ctx->cst + CST_ONE, 512, cudaMemcpyDeviceToDevice, st));
-    if (p.Epad > E) {
-      CK(cudaMemsetAsync(p.b1 + E, 0, (size_t)(p.Epad - E) * 8, st));
-      CK(cudaMemsetAsync(p.b2 + E, 0, (size_t)(p.Epad - E) * 8, st));
-    }
-    launch_prf_words(st, E, ctx->k01, make_tag(P_TRUNC_BITS, C_TB1), mobj, p.b1);
-    launch_prf_words(st, E, ctx->k02, make_tag(P_TRUNC_BITS, C_TB2), mobj, p.b2);
-    launch_gr_mul1(st, s.r, s.r, s.aux + 64);                          // r^2
-    // r^(2e) for e < Epad: r^(2 e_lo) for e_lo < L by repeated multiplication, then every further
-    // block of L rows is that block times the constant r^(2 L e_hi) (a 64 x 64 matrix product)
-    launch_gr_powers(st, s.aux + 64, p.L, p.Rtab);
-    if (p.compact) {
-      launch_gr_mul1(st, p.Rtab + (p.L - 1) * 64, s.aux + 64, s.aux + 128);   // r^(2L)
-      launch_gr_powers(st, s.aux + 128, p.nhi, p.Thi);
-    } else if (p.nhi > 1) {
-      launch_gr_mul1(st, p.Rtab + (p.L - 1) * 64, s.aux + 64, s.aux + 128);   // r^(2L)
-      launch_gr_powers(st, s.aux + 128, p.nhi, p.Thi);
-      // rows h L + e_lo (h >= 1) = r^(2 L h) r^(2 e_lo): one grouped product, matrix h - 1 for
-      // the rows (h - 1) L .. h L - 1 of the block, each reading row e_lo of the first block
-      launch_gr_mulmat_batch(st, p.nhi - 1, p.Thi + 64, 64, p.Mhi);
-      bool done = false;
-      if (ctx->gemm_path == MPC_GEMM_LIMB_TC) {
-        GrMMArgs g{};
-        g.R = (p.nhi - 1) * p.L;
-        g.p0 = p.Rtab;
-        g.in = GrRowMap{p.L, 64, 0};
-        g.Mmat = p.Mhi;
-        g.mrows = p.L;
-        g.out = p.Rtab + p.L * 64;
-        g.om = GrRowMap{0, 64, 0};
-        g_launches += 1;
-        Phase kp(ctx, MPC_PROF_K_GR_MATMUL, (double)g.R * 4096);
-        done = gr_matmul_tc_ex(st, g, ctx->status, ST_TIMEOUT) == 0;
-        if (!done) g_launches -= 1;
-      }
-      for (long long h = 1; h < p.nhi && !done; ++h)
-        if ((rc = gr_matmul(ctx, p.L, p.Rtab, nullptr, 1, 64, p.Mhi + (h - 1) * 4096, nullptr, 0,
-                            p.Rtab + h * p.L * 64, 64)))
-          return rc;
-    }
-    CK(cudaMemsetAsync(p.Zpq, 0, 12 * 64 * 8, st));
-    // sum_e r^(2e) p_c[e], sum_e r^(2e) q_c[e]: (12 x E) . (E x 64)
-    if (p.compact) {
-      // Zhi[c nhi + h] = sum_{e_lo} pq_c[h L + e_lo] r^(2 e_lo) (E = nhi L: one strided view)
-      GemmTerm T;
-      T.A = op(pq, p.L);
-      T.B = op(p.Rtab, 64);
-      if ((rc = dense_gemm(ctx, 12 * p.nhi, 64, p.L, T, epi_store(p.Zhi, 64), p.tcs))) return rc;
-      launch_gather_rows_affine(st, 12 * p.nhi, p.Thi, 1, 1, p.nhi, p.Zrep);   // T_hi[h]
-      launch_gr_mul_rows(st, 12 * p.nhi, p.Zhi, p.Zrep, p.Zprod);
-      launch_block_rowsum(st, 12, p.nhi, p.Zprod, p.Zpq);
-    } else {
-      launch_scalar_gr_sum(st, E, pq, E, 12, p.Rtab, p.Zpq);
-    }
-    u64* z0 = p.zt + 384;
-    for (int c = 0; c < 6; ++c)   // z_c = sum r^(2e) p_c + r sum r^(2e) q_c
-      launch_gr_lincomb(st, ctx->cst + CST_ONE, p.Zpq + c * 64, s.r, p.Zpq + (6 + c) * 64,
-                        z0 + c * 64);
-    delete phase;
-    phase = new Phase(ctx, MPC_PROF_TRUNC_S);
-    {  // S_{j,j'} = sum_e r^(2e) b1_{e,j} b2_{e,j'} (P0), with r^(2e) = r^(2 L e_hi) r^(2 e_lo):
-       // tensor cores for the inner sums over e_lo, then sum_{e_hi} T_hi (x) S_hi as a GEMM + fold
-      launch_trunc_limb_table(st, p.Rtab, p.L, p.TL8);
-      launch_trunc_bit_transpose(st, p.b1, p.Epad, p.B1T);
-      launch_trunc_bit_transpose(st, p.b2, p.Epad, p.B2T);
-      {
-        Phase kphase(ctx, MPC_PROF_K_TRUNC_S, 4096.0 * 64 * E);
-        g_launches += 1;
-        if (launch_trunc_s_tc(st, p.B1T, p.B2T, p.Epad, p.TL8, p.L, p.nhi, p.S_hi, ctx->status,
-                              ST_TIMEOUT))
-          return fail(ctx, MPC_ERR_CUDA, "verify_matmul: tensor map of the limb table");
-      }
-      GemmTerm T;
-      // A[a][e_hi] = coefficient a of r^(2 L e_hi)
-      T.A = p.compact ? op(p.Thi, 64, 1) : op(p.Rtab, p.L * 64, 1);
-      T.B = op(p.S_hi, 262144);            // B[e_hi][(p, b)]
-      if ((rc = dense_gemm(ctx, 64, 262144, p.nhi, T, epi_store(p.Pst, 262144),
-                           p.nhi >= 32 ? p.tcs : nullptr)))
+    for (long long i = 0; i < p.nchunks; ++i) {
+      TruncPlan& tp = p.tp[i == p.nchunks - 1 ? 1 : 0];
+      if ((rc = verify_trunc_chunk(ctx, tp, s, p.tcs, pq, E, i * p.C, trunc_bits, verify_id,
+                                   (u32)(1 + i), matmul_call_id, tr)))
         return rc;
-      launch_fold_reduce_strided(st, p.Pst, 262144, 4096, p.S);
+      if (tr) tr += (long long)(tp.R1 + 1) * TRACE_ROUND;
     }
-    delete phase;
-    phase = new Phase(ctx, MPC_PROF_TRUNC_ROUNDS);
-    const u64* z = z0;
-    u64* zbuf[2] = {s.z[0], s.z[1]};
-    int zi = 0;
-    for (int k = 1; k <= p.kd; ++k) {   // rounds folding the 64 bits of each output
-      const u64 obj = make_obj(verify_id, 1, (u32)k);
-      CK(cudaMemsetAsync(p.hsum, 0, 128 * 8, st));
-      launch_trunc_round_h(st, p.V, p.W, p.S, k, ctx->cst + CST_LAM, p.hsum);
-      CK(cudaMemsetAsync(p.S3, 0, 2 * 192 * 8, st));
-      CK(cudaMemcpyAsync(p.S3, p.hsum, 512, cudaMemcpyDeviceToDevice, st));
-      CK(cudaMemcpyAsync(p.S3 + 192, p.hsum + 64, 512, cudaMemcpyDeviceToDevice, st));
-      inner_finish(ctx, p.S3, P_VER_H0, obj, s.h0);
-      inner_finish(ctx, p.S3 + 192, P_VER_H2, obj, s.h2);
-      reveal(ctx, P_VER_ZETA, obj, s.tmp6, s.zp);
-      launch_gr_lagrange(st, s.zp, ctx->reduce_mode, ctx->cst + CST_INV, s.coef);
-      launch_gr_combine_z(st, s.coef, s.h0, s.h2, z, zbuf[zi]);
-      z = zbuf[zi];
-      zi ^= 1;
-      launch_trunc_update_vw(st, p.V, p.W, k, s.coef);
-      trace_round(ctx, tr, k, s);
-    }
-    delete phase;
-    phase = new Phase(ctx, MPC_PROF_TRUNC_MATERIALIZE);
-    // materialise the folded vectors: x.[r]_1 at P0 and P1, y.[r]_2 at P0 and P2
-    Vec& tx = p.dt.x[0];
-    Vec& ty = p.dt.y[0];
-    if (ctx->gemm_path == MPC_GEMM_LIMB_TC && p.kd == 6) {
-      // one folded element per output e: -sum_j V_j b_{e,j} as a product of the bit matrix with
-      // -V on the tensor cores, then (x only) the GR product with r^(2e), for each party's copy
-      u64* nV = s.MM;
-      u64* nW = s.MM + 4096;
-      launch_neg_copy(st, p.V, 4096, nV);
-      launch_neg_copy(st, p.W, 4096, nW);
-      const u64* bits[4] = {p.b1, p.b1, p.b2, p.b2};
-      const u64* mats[4] = {nV, nV, nW, nW};
-      u64* outs[4] = {tx.c[0], tx.c[3], ty.c[1], ty.c[5]};
-      auto grmm = [&](const GrMMArgs& g, double work) {
-        g_launches += 1;
-        Phase kp(ctx, MPC_PROF_K_GR_MATMUL, work);
-        return gr_matmul_tc_ex(st, g, ctx->status, ST_TIMEOUT);
-      };
-      if (p.Lm) {
-        // x_e = r^(2 Lm e_hi) (sum_j b_{e,j} r^(2 e_lo) (-V_j)): the per-row factor r^(2e) split
-        // into two grouped GR matrix products on the tensor cores.
-        const long long Lm = p.Lm, nhm = p.nhm, nB = (E + Lm - 1) / Lm;
-        launch_gr_mulmat_batch(st, 64, nV, 64, p.Vm);
-        if (p.compact) {   // r^(2 Lm e_hi) = T_hi[e / L] r^(2 (e mod L)), e = e_hi Lm
-          u64* ra = p.Prow;
-          u64* rb = p.Prow + nB * 64;
-          u64* rr = p.Prow + 2 * nB * 64;
-          launch_gather_rows_affine(st, nB, p.Thi, Lm, p.L, 0, ra);
-          launch_gather_rows_affine(st, nB, p.Rtab, Lm, 1, p.L, rb);
-          launch_gr_mul_rows(st, nB, ra, rb, rr);
-          launch_gr_mulmat_batch(st, nB, rr, 64, p.Bm);
-        } else {
-          launch_gr_mulmat_batch(st, nB, p.Rtab, Lm * 64, p.Bm);
-        }
-        launch_word_transpose(st, nhm, Lm, E, p.b1, p.bT);
-        GrMMArgs g{};
-        // Tm: rows sigma = j Lm + e_lo read r^(2 e_lo) and use matrix j; written at [e_lo][j]
-        g.R = 64 * Lm;
-        g.p0 = p.Rtab;
-        g.in = GrRowMap{Lm, 64, 0};
-        g.Mmat = p.Vm;
-        g.mrows = Lm;
-        g.out = p.Tm;
-        g.om = GrRowMap{Lm, 4096, 64};
-        if (grmm(g, 64.0 * Lm * 4096)) return fail(ctx, MPC_ERR_CUDA, "verify_matmul: r^(2e) V table");
-        for (int v = 0; v < 2; ++v) {
-          // rows rho = e_lo nhm + e_hi (bits b_e), matrix Tm[e_lo], result at row e
-          GrMMArgs ga{};
-          ga.R = nhm * Lm;
-          ga.p0 = p.bT;
-          ga.in = GrRowMap{0, 1, 0};
-          ga.a_bits = 1;
-          ga.Mmat = p.Tm;
-          ga.mrows = nhm;
-          ga.out = outs[v];
-          ga.om = GrRowMap{nhm, Lm * 64, 64};
-          ga.out_lim = E * 64;
-          if (grmm(ga, (double)nhm * Lm * 4096 * 8.0 / 36.0))
-            return fail(ctx, MPC_ERR_CUDA, "verify_matmul: folded-vector product");
-          // in place: rows e, matrix M(r^(2 Lm e_hi)) for e_hi = e / Lm
-          GrMMArgs gb{};
-          gb.R = E;
-          gb.p0 = outs[v];
-          gb.in = GrRowMap{0, 64, 0};
-          gb.Mmat = p.Bm;
-          gb.mrows = Lm;
-          gb.out = outs[v];
-          gb.om = GrRowMap{0, 64, 0};
-          if (grmm(gb, (double)E * 4096))
-            return fail(ctx, MPC_ERR_CUDA, "verify_matmul: r^(2e) factor");
-        }
-      }
-      for (int v = p.Lm ? 2 : 0; v < 4; ++v) {
-        GrMMArgs g{};
-        g.R = E;
-        g.p0 = bits[v];
-        g.in = GrRowMap{0, 1, 0};
-        g.a_bits = 1;
-        g.Mmat = mats[v];
-        g.out = outs[v];
-        g.om = GrRowMap{0, 64, 0};
-        // A has digit plane 0 only: 8 of the 36 digit-pair products (work in 36-pair units)
-        if (grmm(g, (double)E * 4096 * 8.0 / 36.0))
-          return fail(ctx, MPC_ERR_CUDA, "verify_matmul: folded-vector product");
-        if (v < 2) {
-          Phase kp(ctx, MPC_PROF_K_GR_MUL_ROWS, (double)E * 4096);
-          launch_gr_mul_rows(st, E, outs[v], p.Rtab, outs[v]);
-        }
-      }
-    } else {
-      launch_trunc_materialize(st, E, p.b1, p.V, p.Rtab, p.kd, tx.c[0]);
-      launch_trunc_materialize(st, E, p.b1, p.V, p.Rtab, p.kd, tx.c[3]);
-      launch_trunc_materialize(st, E, p.b2, p.W, nullptr, p.kd, ty.c[1]);
-      launch_trunc_materialize(st, E, p.b2, p.W, nullptr, p.kd, ty.c[5]);
-    }
-    delete phase;
-    if ((rc = cuda_check(ctx, "trunc batch"))) return rc;
-    phase = new Phase(ctx, MPC_PROF_TRUNC_TAIL);
-    // the claim entering the dense rounds must not alias their round scratch
-    CK(cudaMemcpyAsync(s.zinit, z, 384 * 8, cudaMemcpyDeviceToDevice, st));
-    p.dt.cur = 0;
-    rc = run_dense(ctx, verify_id, 1, p.dt, p.Dt, s.zinit, p.kd + 1, p.R1, s, p.ivt, tr);
-    delete phase;
-    if (rc) return rc;
   }
   return finish_verify(ctx, (matmul_call_id << 1) | 1);
 }
@@ -1939,9 +2112,9 @@ int compare_select(mpc_ctx* ctx, u64 call_id, int stage, const u64* a, const u64
   launch_addsub(st, 6 * np, a, b, 1, p.d);                                  // d = a - b
   g_launches += 1;
   // edaBits (Fig. edabits)
-  launch_prf_words(st, 64 * W, ctx->k01, make_tag(P_EDABIT, C_R1), obj, p.b1w);
-  launch_prf_words(st, 64 * W, ctx->k02, make_tag(P_EDABIT, C_R2), obj, p.b2w);
-  launch_prf_words(st, 64 * W, ctx->k12, make_tag(P_EDABIT, C_M12), obj, p.mbw);
+  launch_prf_words(st, 64 * W, ctx->k01, make_tag(P_EDABIT, C_R1), obj, p.b1w, 0ll);
+  launch_prf_words(st, 64 * W, ctx->k02, make_tag(P_EDABIT, C_R2), obj, p.b2w, 0ll);
+  launch_prf_words(st, 64 * W, ctx->k12, make_tag(P_EDABIT, C_M12), obj, p.mbw, 0ll);
   if ((rc = bool_from_planes(ctx, p.b1w, p.b2w, p.mbw, 64 * W, p.rbits))) return rc;
   launch_bits_to_arith(st, p.b1w, N, 0, p.B1);
   launch_bits_to_arith(st, p.b2w, N, 1, p.B2);
@@ -1983,9 +2156,9 @@ int compare_select(mpc_ctx* ctx, u64 call_id, int stage, const u64* a, const u64
   launch_msb_out(st, p.rbits, G, p.dpl + 63 * W, W, 1, p.ge);               // [d >= 0] = NOT msb
   g_launches += 1;
   // daBit and B2A
-  launch_prf_words(st, W, ctx->k01, make_tag(P_DABIT, C_R1), obj, p.r1w);
-  launch_prf_words(st, W, ctx->k02, make_tag(P_DABIT, C_R2), obj, p.r2w);
-  launch_prf_words(st, W, ctx->k12, make_tag(P_DABIT, C_M12), obj, p.r3w);
+  launch_prf_words(st, W, ctx->k01, make_tag(P_DABIT, C_R1), obj, p.r1w, 0ll);
+  launch_prf_words(st, W, ctx->k02, make_tag(P_DABIT, C_R2), obj, p.r2w, 0ll);
+  launch_prf_words(st, W, ctx->k12, make_tag(P_DABIT, C_M12), obj, p.r3w, 0ll);
   if ((rc = bool_from_planes(ctx, p.r1w, p.r2w, p.r3w, W, p.rb))) return rc;
   launch_bits_to_arith(st, p.r1w, np, 0, p.A1);
   launch_bits_to_arith(st, p.r2w, np, 1, p.A2);

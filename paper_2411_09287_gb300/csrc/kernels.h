@@ -59,7 +59,7 @@ size_t limb_tc_scratch_bytes(long long M, long long N, long long K, int nterms);
 // ev0 / ev1 (may be null) are recorded on st around the tensor-core kernel alone.
 int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nterms,
                  const GemmTerm* terms, const Epi& epi, void* scratch, unsigned* err,
-                 unsigned err_flag, cudaEvent_t ev0, cudaEvent_t ev1);
+                 unsigned err_flag, cudaEvent_t ev0, cudaEvent_t ev1, int split_min = 0);
 
 // out[i][c] = add0[i][c] + sum_k A[i][k] M[k][c], i < R, k, c < 64 (M row-major 64 x 64) with
 // A[i][k] = p0[i][k] + s1 p1[i][k] (p1 may be null), or, with a_bits, A[i][k] = bit k of the word
@@ -102,7 +102,7 @@ int gr_matmul_tc_ex(cudaStream_t st, const GrMMArgs& a, unsigned* err, unsigned 
 // G(x_e, y_o) + G(x_o, y_e) over the Dh element pairs (x_{2i}, x_{2i+1}) of x and y (rows of 64
 // words, contiguous).  Exact, on the tensor cores; returns -1 for misaligned inputs.
 int gram3_tc(cudaStream_t st, long long Dh, const u64* x, const u64* y, u64* P, unsigned* err,
-             unsigned err_flag);
+             unsigned err_flag, int nsplit = 0);
 
 // ---- elementwise protocol kernels (prf_kernels.cu) ------------------------------------------
 void launch_share_input(cudaStream_t st, const u64* x, long long n, Key k01, Key k02, u64 obj,
@@ -194,8 +194,10 @@ void launch_gr_inner_finish_all(cudaStream_t st, const u64* S, Key k01, Key k02,
 void launch_gr_quad_combine(cudaStream_t st, const u64* lam, const u64* S00, const u64* S01,
                             const u64* S10, const u64* S11, u64* out);
 void launch_mode_consts(cudaStream_t st, int mode, u64* cst);
-// PRF words of one stream into an array (e.g. the truncation bits b1, b2 of every output)
-void launch_prf_words(cudaStream_t st, long long n, Key key, u32 tag, u64 obj, u64* out);
+// PRF words off .. off + n - 1 of one stream into out[0 .. n) (e.g. the truncation bits b1, b2
+// of the outputs of one verification chunk)
+void launch_prf_words(cudaStream_t st, long long n, Key key, u32 tag, u64 obj, u64* out,
+                      long long off = 0);
 
 // ---- trunc-batch S matrix on the tensor cores (trunc_s.cu) ----------------------------------
 void launch_trunc_limb_table(cudaStream_t st, const u64* Tlo, long long L, unsigned char* TL8);

@@ -1107,7 +1107,7 @@ size_t limb_tc_scratch_bytes(long long M, long long N, long long K, int nterms) 
 
 int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nterms,
                  const GemmTerm* terms, const Epi& epi, void* scratch, unsigned* err,
-                 unsigned err_flag, cudaEvent_t ev0, cudaEvent_t ev1) {
+                 unsigned err_flag, cudaEvent_t ev0, cudaEvent_t ev1, int split_min) {
   if (M <= 0 || N <= 0) return 0;
   if (epi.atomic) return -1;
   const long long Kp = ((nterms * K + TC_BK - 1) / TC_BK) * TC_BK;
@@ -1139,9 +1139,10 @@ int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nte
   }
   const long long tiles = ((M + TC_BM - 1) / TC_BM) * ((N + TC_BN - 1) / TC_BN);
   const long long nch = Kp / TC_BK;
-  // thin products: split K (at least 8 chunks each) while the CTAs still fit one wave
+  // thin products: split K (at least split_min chunks each) while the CTAs still fit one wave
+  if (split_min <= 0) split_min = 8;
   long long nsplit = 1;
-  while (tiles * nsplit * 2 <= nsm && nch / (nsplit * 2) >= 8) nsplit *= 2;
+  while (tiles * nsplit * 2 <= nsm && nch / (nsplit * 2) >= split_min) nsplit *= 2;
   if (nsplit > 1) cudaMemset2DAsync(epi.out, (size_t)epi.ldc * 8, 0, (size_t)N * 8, (size_t)M, st);
   dim3 grid((unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)((N + TC_BN - 1) / TC_BN),
             (unsigned)nsplit);
@@ -1211,7 +1212,7 @@ int gr_matmul_tc(cudaStream_t st, long long R, const u64* p0, const u64* p1, u64
 }
 
 int gram3_tc(cudaStream_t st, long long Dh, const u64* x, const u64* y, u64* P, unsigned* err,
-             unsigned err_flag) {
+             unsigned err_flag, int nsplit) {
   if (Dh <= 0) return 0;
   if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) return -1;
   static int nsm = 0;
@@ -1222,7 +1223,7 @@ int gram3_tc(cudaStream_t st, long long Dh, const u64* x, const u64* y, u64* P, 
     if (nsm <= 0) nsm = 148;
   }
   const long long nch = (Dh + TC_BK - 1) / TC_BK;
-  long long split = nsm / 2;
+  long long split = nsplit > 0 ? nsplit : nsm / 2;
   if (split > nch) split = nch;
   if (split < 1) split = 1;
   set_max_dynamic_smem(reinterpret_cast<const void*>(k_gram_tc), (int)GR_SMEM);

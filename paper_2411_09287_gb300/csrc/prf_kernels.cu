@@ -327,15 +327,20 @@ k_trunc_finish(long long E, Key k01, Key k02, u64 obj, int t, u32 ttb1,
 
 __global__ void k_xor_one(u64* p, u64 mask) { *p ^= mask; }
 
-__global__ void k_prf_words(long long n, Key key, u32 tag, u64 obj, u64* __restrict__ out) {
-  const long long nb = (n + 7) / 8;
-  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
-       b += (long long)gridDim.x * blockDim.x) {
+// stream words off .. off + n - 1 (block b holds words 8b .. 8b + 7) into out[0 .. n)
+__global__ void k_prf_words(long long n, long long off, Key key, u32 tag, u64 obj,
+                            u64* __restrict__ out) {
+  const long long b0 = off / 8, nb = (off + n + 7) / 8 - b0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nb;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long b = b0 + i;
     u64 w[8];
     prf_block8(key, tag, obj, (u64)b, w);
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-      if (b * 8 + j < n) out[b * 8 + j] = w[j];
+    for (int j = 0; j < 8; ++j) {
+      const long long g = b * 8 + j - off;
+      if (g >= 0 && g < n) out[g] = w[j];
+    }
   }
 }
 
@@ -422,9 +427,10 @@ void launch_trunc_finish(cudaStream_t st, long long E, Key k01, Key k02, u64 obj
 
 void launch_xor_one(cudaStream_t st, u64* p, u64 mask) { k_xor_one<<<1, 1, 0, st>>>(p, mask); }
 
-void launch_prf_words(cudaStream_t st, long long n, Key key, u32 tag, u64 obj, u64* out) {
-  if (n <= 0) return;
-  k_prf_words<<<grid_for((n + 7) / 8), TPB, 0, st>>>(n, key, tag, obj, out);
+void launch_prf_words(cudaStream_t st, long long n, Key key, u32 tag, u64 obj, u64* out,
+                      long long off) {
+  if (n <= 0 || off < 0) return;
+  k_prf_words<<<grid_for((off + n + 7) / 8 - off / 8), TPB, 0, st>>>(n, off, key, tag, obj, out);
 }
 
 void launch_open_p1(cudaStream_t st, const u64* m, const u64* r1, const u64* r2, long long n,

@@ -63,7 +63,7 @@ class Context:
     """One three-party run: keys from `seed`, ledger, abort state; work on the current stream."""
 
     def __init__(self, seed: bytes, device: int = 0, reduce_mode: int = REDUCE_POINT_X,
-                 gemm_path: int = GEMM_LIMB_TC, stream=None):
+                 gemm_path: int = GEMM_LIMB_TC, stream=None, tuning: dict | None = None):
         torch = _torch()
         self.torch = torch
         self.lib = _lib.load()
@@ -85,6 +85,31 @@ class Context:
             raise MpcError(rc, "mpc_create failed")
         self.h = h
         self._ws = None
+        if tuning:
+            self.set_tuning(**tuning)
+
+    TUNING_FIELDS = tuple(f for f, _ in _lib.MpcTuning._fields_)
+
+    def set_tuning(self, **fields):
+        """mpc_set_tuning: fields of mpc_tuning by name; unnamed fields keep their defaults."""
+        t = _lib.MpcTuning()
+        for k, v in fields.items():
+            if k not in self.TUNING_FIELDS:
+                raise KeyError(k)
+            setattr(t, k, int(v))
+        self._check(self.lib.mpc_set_tuning(self.h, C.byref(t)))
+
+    def tuning(self) -> dict:
+        t = _lib.MpcTuning()
+        self._check(self.lib.mpc_get_tuning(self.h, C.byref(t)))
+        return {k: int(getattr(t, k)) for k in self.TUNING_FIELDS}
+
+    def trace_words(self, op: int, a: int, b: int = 0, c: int = 0, trunc_bits: int = -1,
+                    R_main: int = -1, R_trunc: int = -1) -> int:
+        v = self.lib.mpc_trace_words(self.h, op, a, b, c, trunc_bits, R_main, R_trunc)
+        if v < 0:
+            raise MpcError(MPC_ERR_ARG, "bad trace query")
+        return int(v)
 
     def set_stream(self, stream):
         """Enqueue subsequent work on `stream` (a torch.cuda.Stream), e.g. a graph-capture stream."""
@@ -275,9 +300,7 @@ class Context:
     def verify_matmul(self, verify_id: int, xs, ws_, zpre, pq, M: int, N: int, K: int,
                       trunc_bits: int, matmul_call_id: int, R_main: int = -1, R_trunc: int = -1,
                       trace: bool = False):
-        R0 = default_R(K) if R_main < 0 else R_main
-        R1 = default_R(64 * M * N) if R_trunc < 0 else R_trunc
-        ntr = (R0 + 1) * TRACE_ROUND + ((R1 + 1) * TRACE_ROUND if trunc_bits >= 0 else 0)
+        ntr = self.trace_words(OP_VERIFY_MATMUL, M, N, K, trunc_bits, R_main, R_trunc)
         tr = self.zeros(ntr) if trace else None
         wsb = self.ws_size(OP_VERIFY_MATMUL, M, N, K, trunc_bits, R_main, R_trunc)
         ws = self.workspace(wsb)
