@@ -1,16 +1,21 @@
 """Benchmark: one secure Z_2^64 GEMM layer per step on GB300, through libmpc3's C-ABI.
 
-Step = the whole hot path on one batch of synthetic input:
-  input sharing of X (n x n) and W (n x n)          Pi_<.>^{l,0}
-  Pi_Inner for all n^2 outputs + Pi_Trunc^13          (offline Gamma, trunc pairs, online products)
-  Pi_BIVerify of the layer (batch 0: the n^2 inner products; batch 1: the truncation pairs)
-  Pi_Rec of the n x n output
-Metric: secure ring-MAC/s = n^3 / step time (plaintext-equivalent multiply-accumulates of the
+Step = the whole hot path on one batch of synthetic input (default n = M = N = K = 8192):
+  input sharing of X (M x K) and W (K x N)          Pi_<.>^{l,0}
+  Pi_Inner for all M N outputs + Pi_Trunc^13         (offline Gamma, trunc pairs, online products)
+  Pi_BIVerify of the layer (batch 0: the M N inner products; batch 1: the truncation pairs, in
+  chunks of 2^24 outputs)
+  Pi_Rec of the M x N output
+Metric: secure ring-MAC/s = M N K / step time (plaintext-equivalent multiply-accumulates of the
 secure product, verification included).  Inputs are resident in HBM when timing starts ("value");
 "e2e" repeats the step through the same C-ABI with the inputs in pinned host memory and the
 output read back to pinned host memory.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 4096] [--impl ours|reference]
+The same step also runs on the other GEMM path (the u64 CUDA-core products when the main path is
+the limb-split tensor-core one) on the same layer and inputs, reported under "other_path".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 8192 | --shape MxNxK]
+                  [--gemm-path tc|u64] [--other-path-steps S] [--impl ours|reference]
 """
 from __future__ import annotations
 
@@ -43,9 +48,10 @@ def max_over_ranks(x: float, world: int, device="cuda") -> float:
     return float(t.item())
 
 
-def job_value(n: int, world: int, seconds_per_step: float) -> float:
-    """Whole-job secure ring-MAC/s: every rank runs one n x n x n layer per step."""
-    return world * float(n) ** 3 / seconds_per_step
+def job_value(n: int, world: int, seconds_per_step: float, shape=None) -> float:
+    """Whole-job secure ring-MAC/s: every rank runs one n x n x n (or M x N x K) layer per step."""
+    M, N, K = shape if shape else (n, n, n)
+    return world * float(M) * N * K / seconds_per_step
 
 
 def parse(argv=None):
@@ -53,7 +59,11 @@ def parse(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--shape", default=None, help="MxNxK instead of a square n (e.g. 16384x256x4096)")
+    ap.add_argument("--other-path-steps", type=int, default=1,
+                    help="timed steps of the other GEMM path on the same layer (0: skip)")
+    ap.add_argument("--other-path-warmup", type=int, default=1)
     ap.add_argument("--trunc", type=int, default=13)
     ap.add_argument("--gemm-path", choices=["u64", "tc"], default="tc")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -196,20 +206,21 @@ def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
     steps, warm = args.steps, args.warmup
+    M, N, K = parse_shape(args)
     rows, cols = 1, 16
     pool = OraclePool(host_cores())
     try:
         for i in range(warm):
-            pool.run(args.n, rows, cols, args.trunc, b"\x01" * 32, 100 + i * 1000)
-        dt = sum(pool.run(args.n, rows, cols, args.trunc, b"\x02" * 32, 100000 + i * 1000)
+            pool.run(K, rows, cols, args.trunc, b"\x01" * 32, 100 + i * 1000)
+        dt = sum(pool.run(K, rows, cols, args.trunc, b"\x02" * 32, 100000 + i * 1000)
                  for i in range(steps)) / steps
     finally:
         pool.close()
-    v = pool.cores * rows * cols * args.n / dt
+    v = pool.cores * rows * cols * K / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": steps, "warmup": warm, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"secure GEMM {args.n}x{args.n}x{args.n} + trunc + verify + rec",
+            "config": {"workload": f"secure GEMM {M}x{N}x{K} (M x N x K) + trunc + verify + rec",
                        "sample_rows": rows, "sample_cols": cols},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
                              "sample": f"per step, {pool.cores} x one {rows}x{cols} output slab "
@@ -277,6 +288,111 @@ def rooflines(phases, steps, peaks, clk, M, N, K, E, gemm_path):
     return out
 
 
+class Layer:
+    """One secure GEMM layer per step through the C-ABI on one context: buffers, workspace and the
+    step itself (the same call sequence for both GEMM paths)."""
+
+    def __init__(self, mpc, torch, M, N, K, t, seed, device, gemm_path, X, W, Xd, Wd):
+        import ctypes as C
+        self.mpc, self.torch, self.C = mpc, torch, C
+        self.M, self.N, self.K, self.t = M, N, K, t
+        self.E = E = M * N
+        self.ctx = ctx = mpc.Context(seed, device=device, gemm_path=gemm_path)
+        self.X, self.W = X, W
+        self.xs, self.wsh = ctx.shares(M * K), ctx.shares(K * N)
+        self.zpre, self.zout, self.pq = ctx.shares(E), ctx.shares(E), ctx.empty(12 * E)
+        self.out_dev = ctx.empty(E)
+        # one workspace for every call of the step
+        self.wsb = max(ctx.ws_size(mpc.OP_SHARE, max(M * K, K * N)),
+                       ctx.ws_size(mpc.OP_MATMUL, M, N, K, t),
+                       ctx.ws_size(mpc.OP_VERIFY_MATMUL, M, N, K, t),
+                       ctx.ws_size(mpc.OP_RECONSTRUCT, E))
+        self.ws = ctx.workspace(self.wsb)
+        self.lib, self.h = ctx.lib, ctx.h
+        self.call = 1
+        self.dev_args = (self.P(Xd), self.P(Wd), 0, self.P(self.out_dev), 0)
+
+    def P(self, tt):
+        return self.C.c_void_p(tt.data_ptr())
+
+    def check(self, rc, what):
+        if rc != self.mpc.MPC_OK:
+            raise self.mpc.MpcError(rc, f"{what}: {self.lib.mpc_last_error(self.h).decode()}")
+
+    def step(self, x_ptr, w_ptr, on_host, out_ptr, out_host):
+        lib, h, P, M, N, K, t = self.lib, self.h, self.P, self.M, self.N, self.K, self.t
+        ws, wsb, c = self.ws, self.wsb, self.call
+        self.call += 8
+        self.check(lib.mpc_share_input(h, c, x_ptr, on_host, M * K, P(self.xs), P(ws), wsb), "share X")
+        self.check(lib.mpc_share_input(h, c + 1, w_ptr, on_host, K * N, P(self.wsh), P(ws), wsb),
+                   "share W")
+        self.check(lib.mpc_matmul(h, c + 2, P(self.xs), P(self.wsh), M, N, K, t, P(self.zpre),
+                                  P(self.zout), P(self.pq), P(ws), wsb), "matmul")
+        self.check(lib.mpc_verify_matmul(h, c + 3, P(self.xs), P(self.wsh), P(self.zpre),
+                                         P(self.pq), M, N, K, t, c + 2, -1, -1, P(ws), wsb, None),
+                   "verify")
+        self.check(lib.mpc_reconstruct(h, P(self.zout), self.E, out_ptr, out_host, P(ws), wsb),
+                   "reconstruct")
+
+    def sampled_check(self, nsamples: int = 16):
+        """On sampled outputs (a, b): the pre-truncation product reconstructs to (X W)_ab mod 2^64
+        (Python integers), and the opened truncated output is (X W)_ab >>_arith t up to Pi_Trunc's
+        error (Fig. trunc, Sec. 4.2): with m = x + r, (m >>_a t) - (r >>_a t) = (x >>_a t) + c -
+        2^(l-t) w, c in {0, 1} the carry and w in {-1, 0, 1} the wrap of x + r; a wrap has
+        probability about |x| / 2^l, common for the uniform 64-bit words of this workload, so the
+        check is the residue mod 2^(l-t) and the wraps are counted."""
+        mpc, M, N, K, t, E = self.mpc, self.M, self.N, self.K, self.t, self.E
+        zp = self.torch.empty(E, dtype=self.torch.int64, device=self.out_dev.device)
+        self.check(self.lib.mpc_reconstruct(self.h, self.P(self.zpre), E, self.P(zp), 0,
+                                            self.P(self.ws), self.wsb), "reconstruct zpre")
+        zp = mpc.to_u64(zp)
+        o = mpc.to_u64(self.out_dev)
+        g = np.random.default_rng(0)
+        wraps = 0
+        for _ in range(nsamples):
+            a, b = int(g.integers(0, M)), int(g.integers(0, N))
+            ref = sum(int(self.X[a, k]) * int(self.W[k, b]) for k in range(K)) % (1 << 64)
+            assert int(zp[a * N + b]) == ref, f"secure product differs from X W at ({a}, {b})"
+            sref = ref - (1 << 64) if ref >> 63 else ref
+            got = int(o[a * N + b])
+            got = got - (1 << 64) if got >> 63 else got
+            d = (got - (sref >> t)) % (1 << 64)
+            assert d % (1 << (64 - t)) in (0, 1), f"truncated output off at ({a}, {b}): {d:#x}"
+            wraps += d > 1
+        return wraps
+
+    def timed(self, steps, world, dist):
+        """`steps` steps on resident inputs, CUDA events on the context's stream; returns ms per
+        step and the library's kernel launches per step."""
+        torch = self.torch
+        stream = torch.cuda.current_stream()
+        l0 = self.ctx.launch_count()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            self.step(*self.dev_args)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        return ev0.elapsed_time(ev1) / steps, (self.ctx.launch_count() - l0) // steps
+
+    def close(self):
+        self.ws = None
+        self.ctx.close()
+
+
+def parse_shape(args):
+    if args.shape:
+        M, N, K = (int(v) for v in args.shape.lower().split("x"))
+    else:
+        M = N = K = args.n
+    return M, N, K
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -294,86 +410,30 @@ def main():
 
     from paper_2411_09287_gb300 import mpc, workloads
 
-    n, t = args.n, args.trunc
-    M = N = K = n
+    M, N, K = parse_shape(args)
+    t = args.trunc
     E = M * N
-    gemm_path = mpc.GEMM_U64 if args.gemm_path == "u64" else mpc.GEMM_LIMB_TC
-    ctx = mpc.Context(workloads.master_seed(f"C3-{n}") , device=local, gemm_path=gemm_path)
-    X, W = workloads.gemm_square(n)
-    Xd, Wd = mpc.from_u64(ctx, X.reshape(-1)), mpc.from_u64(ctx, W.reshape(-1))
-    xs, wsh = ctx.shares(M * K), ctx.shares(K * N)
-    zpre, zout, pq = ctx.shares(E), ctx.shares(E), ctx.empty(12 * E)
-    out_dev = ctx.empty(E)
-    # one workspace for every call of the step
-    wsb = max(ctx.ws_size(mpc.OP_SHARE, M * K), ctx.ws_size(mpc.OP_MATMUL, M, N, K, t),
-              ctx.ws_size(mpc.OP_VERIFY_MATMUL, M, N, K, t), ctx.ws_size(mpc.OP_RECONSTRUCT, E))
-    ws = ctx.workspace(wsb)
-    lib, h = ctx.lib, ctx.h
-    import ctypes as C
-    P = lambda tt: C.c_void_p(tt.data_ptr())
-    call = [1]
-
-    def check(rc, what):
-        if rc != mpc.MPC_OK:
-            raise mpc.MpcError(rc, f"{what}: {lib.mpc_last_error(h).decode()}")
-
-    def step(x_ptr, w_ptr, on_host, out_ptr, out_host):
-        c = call[0]
-        call[0] += 8
-        check(lib.mpc_share_input(h, c, x_ptr, on_host, M * K, P(xs), P(ws), wsb), "share X")
-        check(lib.mpc_share_input(h, c + 1, w_ptr, on_host, K * N, P(wsh), P(ws), wsb), "share W")
-        check(lib.mpc_matmul(h, c + 2, P(xs), P(wsh), M, N, K, t, P(zpre), P(zout), P(pq), P(ws),
-                             wsb), "matmul")
-        check(lib.mpc_verify_matmul(h, c + 3, P(xs), P(wsh), P(zpre), P(pq), M, N, K, t, c + 2,
-                                    -1, -1, P(ws), wsb, None), "verify")
-        check(lib.mpc_reconstruct(h, P(zout), E, out_ptr, out_host, P(ws), wsb), "reconstruct")
-
-    stream = torch.cuda.current_stream()
-    dev_args = (P(Xd), P(Wd), 0, P(out_dev), 0)
+    name = f"{M}x{N}x{K}"
+    seed = workloads.master_seed(f"C3-{M}" if M == N == K else f"C3-{name}")
+    X, W = workloads.gemm_square(M) if M == N == K else workloads.gemm_shape(M, N, K)
+    main_path = mpc.GEMM_U64 if args.gemm_path == "u64" else mpc.GEMM_LIMB_TC
+    Xd, Wd = (torch.from_numpy(a.reshape(-1).view(np.int64)).to(f"cuda:{local}") for a in (X, W))
+    L = Layer(mpc, torch, M, N, K, t, seed, local, main_path, X, W, Xd, Wd)
     for _ in range(args.warmup):
-        step(*dev_args)
+        L.step(*L.dev_args)
     torch.cuda.synchronize()
-
-    def sampled_check():
-        """The pre-truncation product reconstructs to X W mod 2^64 on sampled outputs (checked
-        with Python integers), and the truncated output is within the probabilistic-truncation
-        error model of it (off by one, or a wrap)."""
-        zp = ctx.torch.empty(E, dtype=torch.int64, device="cuda")
-        check(lib.mpc_reconstruct(h, P(zpre), E, P(zp), 0, P(ws), wsb), "reconstruct zpre")
-        zp = mpc.to_u64(zp)
-        o = mpc.to_u64(out_dev)
-        g = np.random.default_rng(0)
-        for _ in range(16):
-            a, b = int(g.integers(0, M)), int(g.integers(0, N))
-            ref = sum(int(X[a, k]) * int(W[k, b]) for k in range(K)) % (1 << 64)
-            assert int(zp[a * N + b]) == ref, f"secure product differs from X W at ({a}, {b})"
-        return o
-
     if args.warmup > 0:   # (with no warm-up step there is no product to check yet)
-        sampled_check()
+        L.sampled_check()
 
     # ---- timed region: inputs resident in HBM ----
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    ctx.profile(True)
-    l0 = ctx.launch_count()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step(*dev_args)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    launches = (ctx.launch_count() - l0) // args.steps
-    phases = ctx.profile_read()
-    ctx.profile(False)
+    L.ctx.profile(True)
+    ms, launches = L.timed(args.steps, world, dist)
+    phases = L.ctx.profile_read()
+    L.ctx.profile(False)
     clk = clocks.stop()
-    sampled_check()
+    wraps = L.sampled_check()
 
     # ---- e2e: host inputs (pinned) -> device, output -> pinned host ----
     e2e = None
@@ -381,25 +441,58 @@ def main():
         Xh = torch.from_numpy(X.reshape(-1).view(np.int64)).pin_memory()
         Wh = torch.from_numpy(W.reshape(-1).view(np.int64)).pin_memory()
         Oh = torch.empty(E, dtype=torch.int64).pin_memory()
-        host_args = (P(Xh), P(Wh), 1, P(Oh), 1)
-        step(*host_args)
+        host_args = (L.P(Xh), L.P(Wh), 1, L.P(Oh), 1)
+        L.step(*host_args)
         torch.cuda.synchronize()
         e_steps = max(1, min(args.steps, 3))
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(e_steps):
-            step(*host_args)
+            L.step(*host_args)
         torch.cuda.synchronize()
         dt = max_over_ranks((time.perf_counter() - t0) / e_steps, world)
-        sampled_check()
-        e2e = {"value": job_value(n, world, dt), "unit": UNIT, "ms_per_step": dt * 1e3,
-               "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": n * n * 8}
+        L.sampled_check()
+        e2e = {"value": job_value(0, world, dt, (M, N, K)), "unit": UNIT, "ms_per_step": dt * 1e3,
+               "h2d_bytes_per_step": (M * K + K * N) * 8, "d2h_bytes_per_step": E * 8}
+        del Xh, Wh, Oh
 
     ms = max_over_ranks(ms, world)
-    value = job_value(n, world, ms * 1e-3)
+    value = job_value(0, world, ms * 1e-3, (M, N, K))
+    wsb = L.wsb
+    L.close()
+    del L
 
-    # ---- roofline of the dominant phase ----
+    # ---- the other GEMM path on the same layer and inputs ----
+    other = None
+    if args.other_path_steps > 0:
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        o_path = mpc.GEMM_LIMB_TC if main_path == mpc.GEMM_U64 else mpc.GEMM_U64
+        O = Layer(mpc, torch, M, N, K, t, seed, local, o_path, X, W, Xd, Wd)
+        for _ in range(args.other_path_warmup):
+            O.step(*O.dev_args)
+        torch.cuda.synchronize()
+        oclk = ClockSampler(torch.cuda.current_device())
+        oclk.start()
+        O.ctx.profile(True)
+        oms, olaunch = O.timed(args.other_path_steps, world, dist)
+        ophases = O.ctx.profile_read()
+        O.ctx.profile(False)
+        oc = oclk.stop()
+        O.sampled_check()
+        oms = max_over_ranks(oms, world)
+        oname = "u64" if o_path == mpc.GEMM_U64 else "tc"
+        other = {"gemm_path": oname, "value": job_value(0, world, oms * 1e-3, (M, N, K)),
+                 "unit": UNIT, "ms_per_step": oms, "steps": args.other_path_steps,
+                 "warmup": args.other_path_warmup, "gpu_launches": olaunch, "clocks": oc,
+                 "phases_ms": {k: round(v[0] / args.other_path_steps, 3)
+                               for k, v in ophases.items() if v[0] > 0},
+                 "speedup_of_main_path": oms / ms}
+        O.close()
+        del O
+
+    # ---- roofline of the dominant kernel ----
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else open(os.devnull) as f:
         try:
@@ -409,32 +502,38 @@ def main():
     per = {k: v[0] / args.steps for k, v in phases.items()}
     roofs = rooflines(phases, args.steps, peaks, clk, M, N, K, E, args.gemm_path)
     roof = max(roofs.values(), key=lambda r: r["ms_per_step"]) if roofs else None
+    if other is not None:
+        opk = "u64" if other["gemm_path"] == "u64" else "tc"
+        other["rooflines"] = rooflines(ophases, args.other_path_steps, peaks, oc, M, N, K, E, opk)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"secure GEMM {n}x{n}x{n} over Z_2^64 (uniform u64 shares) + "
-                               f"Pi_Trunc^{t} + Pi_BIVerify (2 batches) + Pi_Rec",
+        "config": {"workload": f"secure GEMM {name} (M x N x K) over Z_2^64 (uniform u64 shares) + "
+                               f"Pi_Trunc^{t} + Pi_BIVerify (2 batches, trunc batch in chunks of "
+                               f"2^24 outputs) + Pi_Rec",
                    "M": M, "N": N, "K": K, "trunc_bits": t, "gemm_path": args.gemm_path,
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (working set "
-                                                            f"{(wsb + 8 * 6 * (2 * n * n + 4 * E)) / 2**30:.1f} GiB)"},
+                                                            f"{(wsb + 8 * 6 * (M * K + K * N + 4 * E)) / 2**30:.1f} GiB)"},
         "roofline": roof,
         "rooflines": roofs,
         "phases_ms": {k: round(v, 3) for k, v in per.items() if v > 0},
         "gpu_launches": launches,
         "clocks": clk,
+        "trunc_wraps_sampled": wraps,
     }
+    if other is not None:
+        line["other_path"] = other
     if e2e:
         line["e2e"] = e2e
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            line["cpu_baseline"] = cpu_baseline(n, t)
+            line["cpu_baseline"] = cpu_baseline(K, t)
         except Exception as ex:   # reported, never silently replaced
             line["cpu_baseline"] = {"error": str(ex)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
 

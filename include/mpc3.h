@@ -107,6 +107,8 @@ typedef struct {
  *   row_split      L', rows per block of the blocked batch's folded-vector products
  *                  (x_e = r^(2 L' e_hi) sum_j b_(e,j) r^(2 e_lo) V_j, e = e_hi L' + e_lo);
  *                  multiple of 128; default: the odd multiple of 128 near sqrt(E) that pads least.
+ *                  A batch uses at most E rounded up to a multiple of 128; a row_split above
+ *                  trunc_block keeps the whole table of powers (no compact table).
  *   tc_combine_min fewest e_hi blocks for which sum_(e_hi) r^(2 L e_hi) S_hi runs on the tensor
  *                  cores (fewer: CUDA cores); default 32.
  *   gemm_split_min fewest 32-deep K chunks per split-K slice of a thin tensor-core product;

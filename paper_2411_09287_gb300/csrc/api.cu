@@ -930,7 +930,8 @@ TruncShape trunc_shape(long long E, int R1, bool tc, const mpc_tuning& tu) {
   h.tc_combine = tc && h.nhi >= tu.tc_combine_min;
   if (tc && h.kd == 6 && h.blocked) {
     if (tu.row_split > 0) {
-      h.Lm = tu.row_split;
+      // at most E rounded up to a tile: the row-split table reads r^(2 e_lo) for e_lo < Lm
+      h.Lm = std::min<long long>(tu.row_split, (E + 127) / 128 * 128);
       h.nhm = ((E + h.Lm - 1) / h.Lm + 127) / 128 * 128;
     } else {
       // Lm = 128 a with a odd near sqrt(E) / 128, and nhm = 128 b >= E / Lm with the fewest rows
@@ -955,6 +956,8 @@ TruncShape trunc_shape(long long E, int R1, bool tc, const mpc_tuning& tu) {
         }
       }
     }
+    // the compact table keeps r^(2 e_lo) for e_lo < L only, and the row-split table reads e_lo < Lm
+    if (h.Lm > h.L) h.compact = false;
   }
   return h;
 }

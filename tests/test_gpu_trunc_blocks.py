@@ -9,7 +9,8 @@ any protocol value, so small layers take them here:
     limb GEMM and 12 nhi GR products);
   - row_split L': the folded-vector product of x_e = r^(2 L' e_hi) sum_j b_(e,j) r^(2 e_lo) V_j
     with its transposed bit rows, output row map and padded rows (out_lim), and, in compact mode,
-    the rows r^(2 L' e_hi) gathered as T_hi[e / L] r^(2 (e mod L)) with e mod L != 0;
+    the rows r^(2 L' e_hi) gathered as T_hi[e / L] r^(2 (e mod L)) with e mod L != 0 (L = 384,
+    L' = 256: e = 0, 256, 512); L' above L (the whole table of powers is kept);
   - tc_combine_min: sum_(e_hi) r^(2 L e_hi) S_hi on the tensor cores;
   - trunc_chunk: the batch split into independently verified chunks (reading C1), ragged last
     chunk included.
@@ -45,7 +46,8 @@ CASES = {
     # name: (M, N, K, tuning)
     "compact-2blocks-tccombine": (16, 16, 16, dict(trunc_block=128, tc_combine_min=2)),
     "ragged-2blocks": (10, 20, 8, dict(trunc_block=128)),
-    "compact-rowsplit-offset": (16, 32, 8, dict(trunc_block=256, row_split=384, tc_combine_min=2)),
+    "compact-rowsplit-offset": (24, 32, 8, dict(trunc_block=384, row_split=256, tc_combine_min=2)),
+    "rowsplit-above-block": (16, 16, 8, dict(trunc_block=128, row_split=384)),
     "chunks-ragged": (15, 20, 8, dict(trunc_block=128, trunc_chunk=128)),
 }
 
