@@ -208,10 +208,11 @@ int mpc_verify_mult(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, const 
  * offset n[0] + ... + n[l-1] of component c).  xs, ys, zs: host arrays of ncalls device pointers,
  * each a sharing of 6 n[l] words; n, call_ids: host arrays of ncalls entries, read during the
  * call only.  Workspace: mpc_workspace_size(MPC_OP_VERIFY_MULT_CALLS, n[0] + ... + n[ncalls-1],
- * 0, 0, -1, R, -1).  Every listed call leaves the pending state once the check has run (a
+ * 0, 0, -1, R, -1).  Every listed call leaves the pending state once the check has accepted (a
  * rejection makes the context abort).  R < 0 selects max(0, ceil(log2 N) - 6) for the total N.
- * Returns as mpc_verify_mult; MPC_ERR_ARG / MPC_ERR_SHAPE for a null pointer, a bad id or
- * n[l] <= 0.  trace: as mpc_verify_mult. */
+ * Returns as mpc_verify_mult; MPC_ERR_ARG / MPC_ERR_SHAPE for a null pointer, a bad id, a call
+ * id that is not a pending mpc_mult call or is listed twice, or n[l] <= 0.  trace: as
+ * mpc_verify_mult. */
 int mpc_verify_mult_calls(mpc_ctx* ctx, uint64_t verify_id, int ncalls,
                           const uint64_t* const* xs, const uint64_t* const* ys,
                           const uint64_t* const* zs, const int64_t* n, const uint64_t* call_ids,

@@ -782,11 +782,13 @@ Dense plan_dense(Arena& a, long long D, const bool xc[6], const bool yc[6]) {
   return d;
 }
 
+// Reads the status word after a verification; the products under pend_key leave the pending
+// set only on a clean status (after a failure the context is aborted for good).
 int finish_verify(mpc_ctx* ctx, u64 pend_key) {
   u32 stv = 0;
   int rc = read_status(ctx, &stv);
   if (rc) return rc;
-  ctx->pending.erase(pend_key);
+  if (!(stv & (ST_ABORT | ST_VERIFY))) ctx->pending.erase(pend_key);
   if (stv & ST_ABORT) {
     ctx->aborted = true;
     return fail(ctx, MPC_ERR_ABORT, "Pi_Rec: inconsistent messages");
@@ -1747,6 +1749,12 @@ int mpc_verify_mult_calls(mpc_ctx* ctx, uint64_t verify_id, int ncalls,
     if (n[l] <= 0 || n[l] > (1ll << 40)) return fail(ctx, MPC_ERR_SHAPE, "verify_mult_calls: bad n");
     if (!xs[l] || !ys[l] || !zs[l] || !id_ok(call_ids[l]))
       return fail(ctx, MPC_ERR_ARG, "verify_mult_calls: bad argument");
+    // only products still awaiting verification, each once
+    if (!ctx->pending.count((call_ids[l] << 1) | 0))
+      return fail(ctx, MPC_ERR_ARG, "verify_mult_calls: a call id is not a pending mpc_mult call");
+    for (int j = 0; j < l; ++j)
+      if (call_ids[j] == call_ids[l])
+        return fail(ctx, MPC_ERR_ARG, "verify_mult_calls: a call id is listed twice");
     N += n[l];
     if (N > (1ll << 40)) return fail(ctx, MPC_ERR_SHAPE, "verify_mult_calls: batch too large");
   }
@@ -1766,8 +1774,9 @@ int mpc_verify_mult_calls(mpc_ctx* ctx, uint64_t verify_id, int ncalls,
     off += n[l];
   }
   if ((rc = verify_mult_body(ctx, verify_id, p.x, p.y, p.z, N, p.v, trace))) return rc;
+  if ((rc = finish_verify(ctx, (call_ids[0] << 1) | 0))) return rc;
   for (int l = 1; l < ncalls; ++l) ctx->pending.erase((call_ids[l] << 1) | 0);
-  return finish_verify(ctx, (call_ids[0] << 1) | 0);
+  return MPC_OK;
 }
 
 int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, const uint64_t* ws_,

@@ -13,6 +13,7 @@ truncation error).
 """
 from __future__ import annotations
 
+import contextlib
 import hashlib
 import queue
 import threading
@@ -33,6 +34,7 @@ class Request:
     x: np.ndarray             # (b, ...) float inputs
     logits: np.ndarray = None
     done: float = None
+    error: BaseException = None   # set when the packed pass that carried the request failed
 
 
 class Model:
@@ -83,39 +85,55 @@ class Model:
 
 
 class _Worker(threading.Thread):
-    def __init__(self, wid, server):
+    def __init__(self, wid, server, ctx=None, stream=None):
         super().__init__(daemon=True)
-        import torch
         self.wid, self.server = wid, server
-        self.stream = torch.cuda.Stream()
-        seed = hashlib.sha256(f"serving-worker-{wid}".encode()).digest()
-        self.ctx = M.Context(seed, gemm_path=server.gemm_path, stream=self.stream)
+        if ctx is None:
+            import torch
+            stream = torch.cuda.Stream()
+            seed = hashlib.sha256(f"serving-worker-{wid}".encode()).digest()
+            ctx = M.Context(seed, gemm_path=server.gemm_path, stream=stream)
+        self.ctx, self.stream = ctx, stream
         self.inbox = queue.Queue()
         self.calls = 1 + wid * (1 << 36)          # disjoint call-id spaces per worker
         self.busy = threading.Event()
 
-    def run(self):
+    def _on_stream(self):
+        if self.stream is None:
+            return contextlib.nullcontext()
         import torch
+        return torch.cuda.stream(self.stream)
+
+    def run(self):
         while True:
             job = self.inbox.get()
             if job is None:
                 return
             reqs = job
-            x = np.concatenate([r.x for r in reqs], axis=0)
-            with torch.cuda.stream(self.stream):
-                logits = self.server.model.secure(self.ctx, x, self.calls)
-            self.calls += 1 << 16
-            t = time.perf_counter() - self.server.t0
-            off = 0
-            for r in reqs:
-                b = r.x.shape[0]
-                r.logits = logits[off: off + b]
-                r.done = t
-                off += b
-            with self.server.lock:
-                self.server.in_flight -= x.shape[0]
-            self.busy.clear()
-            self.server.wake.set()
+            n = sum(r.x.shape[0] for r in reqs)
+            try:
+                x = np.concatenate([r.x for r in reqs], axis=0)
+                with self._on_stream():
+                    logits = self.server.model.secure(self.ctx, x, self.calls)
+                t = time.perf_counter() - self.server.t0
+                off = 0
+                for r in reqs:
+                    b = r.x.shape[0]
+                    r.logits = logits[off: off + b]
+                    r.done = t
+                    off += b
+            except BaseException as ex:   # an aborted protocol, a CUDA error, an OOM ...
+                t = time.perf_counter() - self.server.t0
+                for r in reqs:
+                    r.error, r.done = ex, t
+                with self.server.lock:
+                    self.server.errors.append(ex)
+            finally:
+                self.calls += 1 << 16
+                with self.server.lock:
+                    self.server.in_flight -= n
+                self.busy.clear()
+                self.server.wake.set()
 
 
 def pack_requests(pending: list, limit: int):
@@ -141,18 +159,25 @@ def check_admissible(requests, max_batch: int, max_in_flight: int):
 
 class Server:
     def __init__(self, model: Model, n_workers: int = 2, max_batch: int = 256,
-                 mem_budget_bytes: float = 64e9, gemm_path: int = M.GEMM_LIMB_TC):
+                 mem_budget_bytes: float = 64e9, gemm_path: int = M.GEMM_LIMB_TC,
+                 make_context=None):
+        """make_context(worker id) -> (context, CUDA stream or None) replaces the default context
+        per worker (one on a new stream)."""
         self.model, self.max_batch, self.gemm_path = model, max_batch, gemm_path
-        self.workers = [_Worker(i, self) for i in range(n_workers)]
         self.lock = threading.Lock()
         self.wake = threading.Event()
         self.in_flight = 0
+        self.errors = []
+        self.workers = [_Worker(i, self, *(make_context(i) if make_context else (None, None)))
+                        for i in range(n_workers)]
         per = model.bytes_per_image(self.workers[0].ctx, max_batch)
         self.max_in_flight = max(1, int(mem_budget_bytes // max(per, 1.0)))
         self.t0 = None
 
     def serve(self, requests):
-        """Run all requests (sorted by arrival); returns them with logits and completion times."""
+        """Run all requests (sorted by arrival); returns them with logits and completion times.
+        If a packed pass fails, no further requests are admitted, the workers are shut down and
+        the first failure is raised (the failed requests carry it in .error)."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         check_admissible(reqs, self.max_batch, self.max_in_flight)
         for w in self.workers:
@@ -160,7 +185,7 @@ class Server:
         self.t0 = time.perf_counter()
         pending = []
         i = 0
-        while i < len(reqs) or pending:
+        while (i < len(reqs) or pending) and not self.errors:
             now = time.perf_counter() - self.t0
             while i < len(reqs) and reqs[i].arrival <= now:
                 pending.append(reqs[i])
@@ -187,6 +212,8 @@ class Server:
             w.inbox.put(None)
         for w in self.workers:
             w.join()
+        if self.errors:
+            raise RuntimeError(f"a packed secure pass failed: {self.errors[0]!r}") from self.errors[0]
         return reqs
 
     @staticmethod

@@ -142,6 +142,14 @@ def test_deferred_rejects_bad_arguments(mpc):
         ctx.verify_mult_calls(3, [])
     with pytest.raises(mpc.MpcError):
         ctx.verify_mult_calls(3, [(gx, gx, gz, 10, 1 << 50)])   # call id out of range
+    with pytest.raises(mpc.MpcError):
+        ctx.verify_mult_calls(3, [(gx, gx, gz, 10, 7)])         # no such pending mpc_mult call
+    with pytest.raises(mpc.MpcError):
+        ctx.verify_mult_calls(3, [(gx, gx, gz, 10, 2), (gx, gx, gz, 10, 2)])   # listed twice
+    with pytest.raises(mpc.MpcError):                           # still pending: refused
+        ctx.reconstruct(gz, 10)
     rc, _ = ctx.verify_mult_calls(3, [(gx, gx, gz, 10, 2)])
     assert rc == mpc.MPC_OK
     assert np.array_equal(ctx.reconstruct(gz, 10), x * x)
+    with pytest.raises(mpc.MpcError):                           # verified: no longer pending
+        ctx.verify_mult_calls(4, [(gx, gx, gz, 10, 2)])

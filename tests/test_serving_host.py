@@ -46,3 +46,36 @@ def test_requests_that_can_never_fit_are_refused(max_batch, max_in_flight, ok):
     else:
         with pytest.raises(ValueError):
             S.check_admissible(reqs, max_batch, max_in_flight)
+
+
+class _StubModel:
+    """secure() fails on the chosen call; bytes_per_image is a constant."""
+
+    def __init__(self, fail_on: int):
+        self.fail_on, self.calls = fail_on, 0
+
+    def bytes_per_image(self, ctx, b):
+        return 1.0
+
+    def secure(self, ctx, x, call_base):
+        self.calls += 1
+        if self.calls == self.fail_on:
+            raise RuntimeError("protocol aborted")
+        return np.full((x.shape[0], 10), float(call_base))
+
+
+@pytest.mark.parametrize("fail_on", [None, 1, 3])
+def test_a_failed_pass_is_reported_and_never_hangs_the_server(fail_on):
+    model = _StubModel(fail_on or 10**9)
+    srv = S.Server(model, n_workers=2, max_batch=4, mem_budget_bytes=64,
+                   make_context=lambda wid: (f"stub context {wid}", None))
+    reqs = _reqs([1, 2, 3, 1, 2, 4, 1])
+    if fail_on is None:
+        out = srv.serve(reqs)
+        assert all(r.logits is not None and r.error is None for r in out)
+    else:
+        with pytest.raises(RuntimeError, match="protocol aborted"):
+            srv.serve(reqs)
+        assert any(r.error is not None for r in reqs)
+    assert srv.in_flight == 0
+    assert all(not w.is_alive() for w in srv.workers)

@@ -33,12 +33,25 @@ def test_noalloc_matches_reconstruct_on_consecutive_calls(mpc):
     for i, n in enumerate(sizes):
         x = workloads.uniform_words(n, f"noalloc-{i}")
         shared.append((n, x, ctx.share_input(10 + i, x)))
+    torch = ctx.torch
     for rep in range(2):                          # two calls in a row per input
         for n, x, xs in shared:
+            l0 = ctx.ledger()
             ref = ctx.reconstruct(xs, n, to_host=False)
+            l1 = ctx.ledger()
             out = ctx.empty(n)
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]
             rc = _noalloc(ctx, xs, n, out)
             assert rc == mpc.MPC_OK, ctx.lib.mpc_last_error(ctx.h).decode()
+            ctx.sync()
+            if rep > 0:   # after the first call on the device, nothing is allocated at all
+                assert torch.cuda.mem_get_info()[0] == free0, "device memory changed"
+            l2 = ctx.ledger()
+            # the same messages as mpc_reconstruct: equal ledger increments
+            assert l2[1] - l1[1] == l1[1] - l0[1]
+            for k in l0[0]:
+                assert l2[0][k] - l1[0][k] == l1[0][k] - l0[0][k], k
             got = mpc.to_u64(out)[:n]
             assert np.array_equal(got, mpc.to_u64(ref)[:n]), f"rep {rep}, n {n}"
             assert np.array_equal(got, x)
