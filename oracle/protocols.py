@@ -10,6 +10,9 @@ three parties' views.  Every random value comes from the pairwise PRG streams of
 * ``matmul``        Pi_Inner for every output of X.W (Sec. 4.1: a matrix product is m inner
                     products), optionally with Pi_Trunc^t (Fig. trunc).
 * ``trunc_pair``    Pi_Trunc^t preprocessing (Fig. trunc).
+* ``trunc``         Pi_Trunc^t of an existing sharing (Fig. trunc, reading T5).
+* ``conv2d``        a convolution as one Pi_Inner per output (Sec. 4.1), on the im2col rows of the
+                    input written out from the definition of a convolution.
 
 Readings of the paper (where it is silent, ambiguous or garbled):
   A1  m = x + r everywhere (Sec. 2 Notation); a bit sharing <b> := (0, b, 0) therefore carries
@@ -19,6 +22,16 @@ Readings of the paper (where it is silent, ambiguous or garbled):
   T2  m_z = m_x >>_arith t ("rshift", Fig. trunc).
   T3  [r_x]_1 := m_{r_x} - [r_{r_x}]_1 (P1) and [r_x]_2 := -[r_{r_x}]_2 (P2); P0 computes both
       from m_{r_x} = Gamma (it knows every r).  Same for r_z.
+  T5  Fig. trunc assigns the pair's r_x to the input wire before the gate that produces it runs
+      ("executed preferentially"), as ``matmul`` does.  For a sharing <x> whose mask r is not a
+      pair's r_x, the mask is switched to r_x first: P1 sends d1 = [r_x]_1 - [r]_1 to P2 and P2
+      sends d2 = [r_x]_2 - [r]_2 to P1 (l bits each), both set m' = m + d1 + d2 = x + r_x, and
+      P0, who knows d1 and d2, sends H(d1) to P2 and H(d2) to P1 (a party whose received d
+      disagrees with the hash aborts, as in Pi_Rec); then m_z = m' >>_arith t.  This is the
+      standalone truncation with 2 l bits online that the paper attributes to SWIFT.
+  D1  Fixed point: floor(x 2^k) mod 2^l (Sec. 2 Notation); a value whose x 2^k lies outside
+      [-2^63, 2^63) saturates to the nearest end, and NaN encodes 0 (the paper assumes values in
+      range and says nothing about the others).
 Parity: pinned (tests/test_oracle_protocols.py) by reconstruction against plaintext products mod
 2^l, the truncation error model of Sec. 4.2, and the communication counts of Table 1.
 """
@@ -43,8 +56,15 @@ class Abort(Exception):
 # fixed point (Sec. 2 Notation): x >= 0 -> floor(x 2^k); x < 0 -> 2^l + floor(x 2^k)
 # ---------------------------------------------------------------------------------------------
 def encode_fixed(x, k: int) -> np.ndarray:
-    v = np.floor(np.asarray(x, dtype=np.float64) * float(1 << k)).astype(np.int64)
-    return v.astype(np.uint64)
+    """floor(x 2^k) as a two's-complement word (reading D1 for values out of range and NaN)."""
+    v = np.floor(np.asarray(x, dtype=np.float64) * float(1 << k))
+    lo, hi = -9223372036854775808.0, 9223372036854775808.0    # -2^63, 2^63
+    out = np.zeros(v.shape, dtype=np.int64)
+    ok = (v >= lo) & (v < hi)
+    out[ok] = v[ok].astype(np.int64)
+    out[v >= hi] = np.iinfo(np.int64).max
+    out[v < lo] = np.iinfo(np.int64).min
+    return out.astype(np.uint64)
 
 
 def decode_fixed(v, k: int) -> np.ndarray:
@@ -320,3 +340,71 @@ def matmul(sess: Session, X: Shared, W: Shared, call_id: int, trunc_bits: int | 
                  asr(mz_p1, t) & mask, tp.rz1_p1.reshape(M, N).copy(),
                  asr(mz_p2, t) & mask, tp.rz2_p2.reshape(M, N).copy())
     return MatmulResult(z_pre, out, tp)
+
+
+# ---------------------------------------------------------------------------------------------
+# Pi_Trunc^t of an existing sharing (reading T5)
+# ---------------------------------------------------------------------------------------------
+def trunc(sess: Session, x: Shared, call_id: int, t: int):
+    """Fig. trunc on <x> of any mask: the pairs' preprocessing (6 l bits offline), the switch of
+    the wire's mask to r_x (2 l bits online and two hashes), then m_z = m' >>_arith t.
+    Returns (<z>, TruncPair)."""
+    mask = sess.mask
+    shape = x.p1_m.shape
+    E = x.p1_m.size
+    tp = trunc_pair(sess, call_id, E, t)
+    f = lambda a: a.reshape(-1)
+    d1 = (tp.rx1_p1 - f(x.p1_r1)) & mask              # P1
+    d2 = (tp.rx2_p2 - f(x.p2_r2)) & mask              # P2
+    d1_p0 = (tp.rx1_p0 - f(x.p0_r1)) & mask           # P0 knows both
+    d2_p0 = (tp.rx2_p0 - f(x.p0_r2)) & mask
+    d1_at_p2 = sess.send(1, 2, ONLINE, "trunc", d1, site="TRUNC_D1")
+    d2_at_p1 = sess.send(2, 1, ONLINE, "trunc", d2)
+    w = sess.wire
+    h1_at_p2 = sess.send_hash(0, 2, ONLINE, "trunc", hash_u64(w(d1_p0)))
+    h2_at_p1 = sess.send_hash(0, 1, ONLINE, "trunc", hash_u64(w(d2_p0)))
+    if hash_u64(w(d2_at_p1)) != h2_at_p1:
+        raise Abort("P1: d2 from P2 disagrees with H(d2) from P0")
+    if hash_u64(w(d1_at_p2)) != h1_at_p2:
+        raise Abort("P2: d1 from P1 disagrees with H(d1) from P0")
+    m1 = (f(x.p1_m) + d1 + d2_at_p1) & mask           # m' = x + r_x at P1
+    m2 = (f(x.p2_m) + d1_at_p2 + d2) & mask           # and at P2
+    out = Shared(tp.rz1_p0.copy(), tp.rz2_p0.copy(), asr(m1, t) & mask, tp.rz1_p1.copy(),
+                 asr(m2, t) & mask, tp.rz2_p2.copy())
+    return out.map(lambda a: a.reshape(shape)), tp
+
+
+# ---------------------------------------------------------------------------------------------
+# convolution: one inner product per output (Sec. 4.1)
+# ---------------------------------------------------------------------------------------------
+def conv_out_size(H: int, W: int, kh: int, kw: int, stride: int, pad: int):
+    return (H + 2 * pad - kh) // stride + 1, (W + 2 * pad - kw) // stride + 1
+
+
+def im2col_rows(x, B: int, C: int, H: int, W: int, kh: int, kw: int, stride: int, pad: int):
+    """The input of every output's inner product, from the definition of a convolution:
+    row (b, i, j), column (c, di, dj) holds x[b, c, i stride + di - pad, j stride + dj - pad],
+    0 outside the image.  x: (B, C, H, W) words (one share component)."""
+    Ho, Wo = conv_out_size(H, W, kh, kw, stride, pad)
+    out = np.zeros((B * Ho * Wo, C * kh * kw), dtype=np.uint64)
+    for b in range(B):
+        for i in range(Ho):
+            for j in range(Wo):
+                row = (b * Ho + i) * Wo + j
+                for c in range(C):
+                    for di in range(kh):
+                        for dj in range(kw):
+                            y, z = i * stride + di - pad, j * stride + dj - pad
+                            if 0 <= y < H and 0 <= z < W:
+                                out[row, (c * kh + di) * kw + dj] = x[b, c, y, z]
+    return out
+
+
+def conv2d(sess: Session, X: Shared, Wm: Shared, call_id: int, geom, trunc_bits: int | None = None):
+    """Convolution of the NCHW sharing X (geom = (B, C, H, W, kh, kw, stride, pad)) with the
+    weight sharing Wm of the (C kh kw) x C_out matrix (rows (c, di, dj)): every component is
+    lowered to its im2col rows (a local, public rearrangement), then one Pi_Inner per output
+    (``matmul``).  Output rows (b, i, j), columns c_out.  Returns (cols, MatmulResult)."""
+    B, C, H, W, kh, kw, stride, pad = geom
+    cols = X.map(lambda a: im2col_rows(a.reshape(B, C, H, W), B, C, H, W, kh, kw, stride, pad))
+    return cols, matmul(sess, cols, Wm, call_id, trunc_bits)

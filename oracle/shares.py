@@ -35,7 +35,7 @@ P_VER_R, P_VER_ZETA, P_VER_H0, P_VER_H2, P_VER_ALPHA, P_VER_XA, P_VER_DELTA = (
 
 OFFLINE, ONLINE, VERIFY = "offline", "online", "verify"
 
-FAULT_SITES = ("GAMMA2", "MZ1", "MZ2", "MX_COPY_P1", "REC_MSG", "HIGH_BIT")
+FAULT_SITES = ("GAMMA2", "MZ1", "MZ2", "MX_COPY_P1", "REC_MSG", "HIGH_BIT", "TRUNC_D1")
 
 
 def tag(purpose: int, comp: int) -> int:

@@ -202,3 +202,84 @@ def test_owner_two_message_to_p1_inconsistent_aborts():
 def test_input_owner_out_of_range_rejected():
     with pytest.raises(ValueError):
         share_input(Session(SEED), np.arange(3, dtype=U64), 1, owner=3)
+
+
+# ---------------------------------------------------------------------------------------------
+# reading D1 (fixed point out of range), standalone Pi_Trunc (reading T5), convolution lowering
+# ---------------------------------------------------------------------------------------------
+def test_encode_fixed_saturates_and_maps_nan_to_zero():
+    k = 13
+    big = np.array([2.0 ** 60, -(2.0 ** 60), np.inf, -np.inf, np.nan, 2.0 ** 50 - 1.0])
+    v = encode_fixed(big, k).astype(np.int64)
+    assert v[0] == np.iinfo(np.int64).max and v[2] == np.iinfo(np.int64).max
+    assert v[1] == np.iinfo(np.int64).min and v[3] == np.iinfo(np.int64).min
+    assert v[4] == 0
+    assert v[5] == (2 ** 50 - 1) * 2 ** 13        # in range: exact
+    # the boundary: x 2^k = -2^63 is representable, 2^63 is not
+    edge = encode_fixed(np.array([-(2.0 ** 50), 2.0 ** 50]), k).astype(np.int64)
+    assert edge[0] == np.iinfo(np.int64).min and edge[1] == np.iinfo(np.int64).max
+
+
+def test_standalone_trunc_opens_the_shifted_value_and_counts_its_messages():
+    from oracle.protocols import trunc
+    from oracle.verify import trunc_verify
+    s = Session(SEED)
+    rng = np.random.default_rng(21)
+    x = encode_fixed(rng.uniform(-1000, 1000, 300), 26)      # |x| < 2^36: no wrap expected
+    X = share_input(s, x, 1)
+    s.ledger.clear()
+    Z, tp = trunc(s, X, 2, 13)
+    got = reconstruct(s, Z).astype(np.int64)
+    want = x.astype(np.int64) >> 13
+    assert np.all((got - want == 0) | (got - want == 1))
+    assert np.any(got - want == 1) and np.any(got == want)   # both carries occur
+    off = s.ledger_bytes(OFFLINE, "trunc")
+    on = s.ledger_bytes(ONLINE, "trunc")
+    assert off == 6 * 8 * 300                                 # Table 1 / Sec. 4.2: 6 l offline
+    assert on == 2 * 8 * 300 + 2 * 32                         # mask switch: 2 l + two hashes
+    assert all(trunc_verify(s, tp, 2, 13))
+
+
+def test_standalone_trunc_rejects_a_corrupted_mask_switch():
+    from oracle.protocols import trunc
+    s = Session(SEED)
+    X = share_input(s, encode_fixed(np.linspace(-3, 3, 40), 26), 1)
+    s.arm_fault("TRUNC_D1", 7, 1 << 20)
+    with pytest.raises(Abort):
+        trunc(s, X, 2, 13)
+
+
+def _conv_by_definition(x, w, stride, pad):
+    """out[b, o, i, j] = sum_{c, di, dj} x[b, c, i s + di - p, j s + dj - p] w[o, c, di, dj]
+    mod 2^64, with Python integers, over a zero-padded copy made with numpy.pad."""
+    B, C, H, W = x.shape
+    O, _, kh, kw = w.shape
+    xp = np.pad(x, ((0, 0), (0, 0), (pad, pad), (pad, pad)))
+    Ho, Wo = (H + 2 * pad - kh) // stride + 1, (W + 2 * pad - kw) // stride + 1
+    out = np.zeros((B, O, Ho, Wo), dtype=np.uint64)
+    for b in range(B):
+        for o in range(O):
+            for i in range(Ho):
+                for j in range(Wo):
+                    win = xp[b, :, i * stride:i * stride + kh, j * stride:j * stride + kw]
+                    acc = sum(int(a) * int(c) for a, c in zip(win.reshape(-1), w[o].reshape(-1)))
+                    out[b, o, i, j] = acc % (1 << 64)
+    return out
+
+
+@pytest.mark.parametrize("geom", [(2, 3, 6, 5, 3, 3, 1, 0), (1, 2, 7, 7, 3, 2, 2, 1),
+                                  (2, 1, 5, 5, 5, 5, 1, 2)])
+def test_conv2d_opens_the_convolution(geom):
+    from oracle.protocols import conv2d, conv_out_size
+    B, C, H, W, kh, kw, stride, pad = geom
+    O = 4
+    s = Session(SEED)
+    rng = np.random.default_rng(22)
+    x = rng.integers(0, 2**64, (B, C, H, W), dtype=np.uint64)
+    w = rng.integers(0, 2**64, (O, C, kh, kw), dtype=np.uint64)
+    wm = np.ascontiguousarray(w.reshape(O, -1).T)             # rows (c, di, dj)
+    X, Wm = share_input(s, x, 1), share_input(s, wm, 2)
+    cols, res = conv2d(s, X, Wm, 3, geom)
+    Ho, Wo = conv_out_size(H, W, kh, kw, stride, pad)
+    got = reconstruct(s, res.z_pre).reshape(B, Ho, Wo, O).transpose(0, 3, 1, 2)
+    assert np.array_equal(got, _conv_by_definition(x, w, stride, pad))
