@@ -73,13 +73,15 @@ enum {
   MPC_SITE_HIGH_BIT = 5,    /* [Gamma]_2 XOR 2^63: the ring attack of Sec. 3                 */
   MPC_SITE_AND_GAMMA2 = 6,  /* P0 -> P2 [Gamma]_2 of a Boolean AND gate (non-linear layers):
                                flips bit `index` of the packed message when mask & 1            */
-  MPC_NSITE = 7
+  MPC_SITE_TRUNC_D1 = 7,    /* P1 -> P2 mask-switch message d1 of mpc_trunc                   */
+  MPC_NSITE = 8
 };
 /* workspace queries */
 enum {
   MPC_OP_SHARE = 0, MPC_OP_MULT = 1, MPC_OP_MATMUL = 2, MPC_OP_VERIFY_MULT = 3,
   MPC_OP_VERIFY_MATMUL = 4, MPC_OP_RECONSTRUCT = 5, MPC_OP_RELU = 6, MPC_OP_MAXPOOL2 = 7,
-  MPC_OP_VERIFY_MULT_CALLS = 8
+  MPC_OP_VERIFY_MULT_CALLS = 8, MPC_OP_SHARE_FIXED = 9, MPC_OP_RECONSTRUCT_FIXED = 10,
+  MPC_OP_TRUNC = 11, MPC_OP_VERIFY_TRUNC = 12
 };
 
 typedef struct mpc_ctx mpc_ctx;
@@ -146,10 +148,11 @@ int mpc_sync(mpc_ctx* ctx);
 int mpc_status(const mpc_ctx* ctx);
 
 /* Bytes of workspace an operation needs.  op = MPC_OP_*; (a, b, c) = (n, 0, 0) for SHARE, MULT,
- * VERIFY_MULT, RECONSTRUCT and RELU, (total n of all calls, 0, 0) for VERIFY_MULT_CALLS, (M, N, K)
- * for MATMUL and VERIFY_MATMUL, (B C, H, W) for MAXPOOL2; trunc_bits, R_main and R_trunc as passed
- * to the operation (R < 0: default; VERIFY_MULT and VERIFY_MULT_CALLS take their R in R_main).
- * Returns -1 for invalid arguments. */
+ * VERIFY_MULT, RECONSTRUCT, RELU, SHARE_FIXED, RECONSTRUCT_FIXED, TRUNC and VERIFY_TRUNC, (total n
+ * of all calls, 0, 0) for VERIFY_MULT_CALLS, (M, N, K) for MATMUL and VERIFY_MATMUL (a
+ * convolution: M = B Ho Wo, N = C_out, K = C kh kw), (B C, H, W) for MAXPOOL2; trunc_bits, R_main
+ * and R_trunc as passed to the operation (R < 0: default; VERIFY_MULT and VERIFY_MULT_CALLS take
+ * their R in R_main, VERIFY_TRUNC in R_trunc).  Returns -1 for invalid arguments. */
 int64_t mpc_workspace_size(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int64_t c,
                            int trunc_bits, int R_main, int R_trunc);
 
@@ -236,8 +239,9 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
                       int trunc_bits, uint64_t matmul_call_id, int R_main, int R_trunc,
                       void* workspace, size_t workspace_bytes, uint64_t* trace);
 
-/* Words of the optional verification trace of op = MPC_OP_VERIFY_MULT, MPC_OP_VERIFY_MULT_CALLS
- * or MPC_OP_VERIFY_MATMUL, arguments as mpc_workspace_size; -1 for invalid arguments. */
+/* Words of the optional verification trace of op = MPC_OP_VERIFY_MULT, MPC_OP_VERIFY_MULT_CALLS,
+ * MPC_OP_VERIFY_MATMUL or MPC_OP_VERIFY_TRUNC, arguments as mpc_workspace_size; -1 for invalid
+ * arguments. */
 int64_t mpc_trace_words(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int64_t c,
                         int trunc_bits, int R_main, int R_trunc);
 
@@ -263,6 +267,66 @@ int mpc_reconstruct(mpc_ctx* ctx, const uint64_t* xs, int64_t n, uint64_t* out, 
  *   unverified. */
 #define MPC_NOALLOC_MAX_N 262144
 int mpc_reconstruct_noalloc(mpc_ctx* ctx, const uint64_t* xs, int64_t n, uint64_t* out);
+
+/* Fixed-point input sharing (Sec. 2 Notation: x is encoded as floor(x 2^k) mod 2^l, two's
+ * complement for x < 0), then Pi_<.>^{l,k}(x) exactly as mpc_share_input_from (owner 0, 1 or 2).
+ * x 2^k outside [-2^63, 2^63) saturates to the nearest end and NaN encodes 0 (the paper assumes
+ * values in range).  x: n doubles, on the host if x_on_host (copied in; the call then waits for
+ * the copy, so x may be reused on return) else on the device; frac_bits: k in 0 .. 62.
+ * Workspace: MPC_OP_SHARE_FIXED.  Returns as mpc_share_input. */
+int mpc_share_fixed(mpc_ctx* ctx, uint64_t call_id, int owner, const double* x, int x_on_host,
+                    int64_t n, int frac_bits, uint64_t* xs, void* workspace,
+                    size_t workspace_bytes);
+
+/* Pi_Rec (as mpc_reconstruct), then the fixed-point decoding of Sec. 2 Notation: out[i] = the
+ * opened word read as a signed 64-bit integer, divided by 2^k.  out: n doubles, host if
+ * out_on_host (the call waits for them) else device.  Workspace: MPC_OP_RECONSTRUCT_FIXED.
+ * Returns as mpc_reconstruct (out is zeroed on an abort when it is on the host). */
+int mpc_reconstruct_fixed(mpc_ctx* ctx, const uint64_t* xs, int64_t n, int frac_bits, double* out,
+                          int out_on_host, void* workspace, size_t workspace_bytes);
+
+/* A convolution as one Pi_Inner per output (Sec. 4.1: an m-dimensional convolution output is m
+ * separate inner products), with Pi_Trunc^t when trunc_bits >= 0.  The library lowers the input
+ * to the im2col rows of those inner products, then runs mpc_matmul on them:
+ *   geom = {B, C, H, W, kh, kw, stride, pad}: xs is the NCHW sharing of B images of C x H x W;
+ *   the kh x kw kernel moves by `stride` over the image padded with `pad` zeros on every side,
+ *   Ho = (H + 2 pad - kh) / stride + 1 rows and Wo likewise;
+ *   ws_: sharing of the (C kh kw) x C_out weight matrix, row (c, di, dj) = (c kh + di) kw + dj;
+ *   cols (written): the 6 (B Ho Wo) (C kh kw)-word sharing of the lowered input, row
+ *   (b, i, j) = (b Ho + i) Wo + j holding x[b][c][i stride + di - pad][j stride + dj - pad] (0 in
+ *   the padding); keep it for the verification, which is mpc_verify_matmul(xs = cols, ws_, zpre,
+ *   pq, B Ho Wo, C_out, C kh kw, trunc_bits, call_id, ...);
+ *   zpre, zout, pq as mpc_matmul with M = B Ho Wo, N = C_out, K = C kh kw: output row (b, i, j),
+ *   column c_out (NHWC order).
+ * Workspace: MPC_OP_MATMUL with (M, N, K) above.  MPC_ERR_SHAPE for a bad geometry. */
+int mpc_conv2d(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_t* ws_,
+               const int32_t geom[8], int64_t C_out, int trunc_bits, uint64_t* cols,
+               uint64_t* zpre, uint64_t* zout, uint64_t* pq, void* workspace,
+               size_t workspace_bytes);
+
+/* Pi_Trunc^t (Fig. trunc) of a sharing <x> of n elements: <z> with z = x >>_arith t, up to the
+ * one-LSB carry and the wrap of probability about |x| / 2^l that the paper states (Sec. 4.2).
+ * Preprocessing as in Fig. trunc: the pairs (r_x, r_z = r_x >>_arith t) from 2 x 64 random bits
+ * per element and two Pi_Inner of dimension 64 (6 l bits offline).  Fig. trunc assigns r_x to
+ * the input wire before the gate that produces it runs (mpc_matmul does); x here was produced
+ * with another mask r, so its mask is switched first: P1 sends d1 = [r_x]_1 - [r]_1 to P2, P2
+ * sends d2 = [r_x]_2 - [r]_2 to P1 (2 l bits online), P0, who knows both, sends H(d1) to P2 and
+ * H(d2) to P1, and both set m' = m + d1 + d2 = x + r_x; then m_z = m' >>_arith t.
+ *   xs: sharing of n elements (read); out: sharing of n elements (written, not xs);
+ *   pq: 12 n words (written): <p>, <q> of the pairs, for mpc_verify_trunc.
+ * Workspace: MPC_OP_TRUNC.  Waits for the hash check; MPC_ERR_ABORT when a received d disagrees
+ * with P0's hash.  The pairs stay pending until mpc_verify_trunc(trunc_call_id = call_id). */
+int mpc_trunc(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, int64_t n, int t, uint64_t* out,
+              uint64_t* pq, void* workspace, size_t workspace_bytes);
+
+/* Pi_BIVerify (Fig. PBDP) of the 2 n inner products of the truncation pairs of
+ * mpc_trunc(call_id = trunc_call_id): exactly batch 1 of mpc_verify_matmul, in chunks of at most
+ * tuning.trunc_chunk outputs (batches 1, 2, ... of verify_id).  R < 0: the default per chunk.
+ * Workspace: MPC_OP_VERIFY_TRUNC (R in R_trunc); trace: mpc_trace_words(MPC_OP_VERIFY_TRUNC, n,
+ * 0, 0, t, -1, R) words, chunk after chunk.  Returns as mpc_verify_mult. */
+int mpc_verify_trunc(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* pq, int64_t n, int t,
+                     uint64_t trunc_call_id, int R, void* workspace, size_t workspace_bytes,
+                     uint64_t* trace);
 
 /* H of Pi_Rec on its own (Sec. 2, verifiable reconstruction): the SHA-256 Merkle root (1024-byte
  * leaves of the little-endian byte image, node = SHA-256(left || right), an odd node promoted

@@ -900,6 +900,12 @@ struct TruncPlan {
   IVBuf ivt;
 };
 
+// A truncation batch of E outputs: nchunks chunks of C outputs (the last one ragged).
+struct TruncBatch {
+  long long E = 0, nchunks = 0, C = 0;
+  TruncPlan tp[2];   // plans of a full chunk and of the ragged last one
+};
+
 struct VMatPlan {
   Small s;
   u64 *Q, *P, *T, *Pz;
@@ -907,8 +913,7 @@ struct VMatPlan {
   IVBuf iv;
   int R0;
   bool trunc = false;
-  long long nchunks = 0, C = 0;   // truncation batch: nchunks chunks of C outputs (the last ragged)
-  TruncPlan tp[2];                // plans of a full chunk and of the ragged last one
+  TruncBatch tb;
   void* tcs = nullptr;            // tensor-core digit planes (limb path only)
 };
 
@@ -1031,6 +1036,36 @@ void trunc_chunks(long long E, const mpc_tuning& tu, long long* n, long long* C)
 }
 constexpr long long MAX_TRUNC_CHUNKS = 15;   // batch ids 1 .. 15 of the object-id layout
 
+// Tensor-core scratch of a truncation batch of E outputs (the larger of its two chunk shapes);
+// -1 when it has more than MAX_TRUNC_CHUNKS chunks.
+long long trunc_batch_tcs(long long E, int R1, bool tc, const mpc_tuning& tu) {
+  long long n = 0, C = 0;
+  trunc_chunks(E, tu, &n, &C);
+  if (n > MAX_TRUNC_CHUNKS) return -1;
+  const long long Elast = E - (n - 1) * C;
+  return (long long)std::max(trunc_tc_scratch(trunc_shape(C, R1, tc, tu)),
+                             trunc_tc_scratch(trunc_shape(Elast, R1, tc, tu)));
+}
+
+// The chunks run one after another: their plans share the rest of the workspace.
+void plan_trunc_batch(Arena& a, long long E, int R1, bool tc, const mpc_tuning& tu,
+                      TruncBatch& b) {
+  b.E = E;
+  trunc_chunks(E, tu, &b.nchunks, &b.C);
+  const long long Elast = E - (b.nchunks - 1) * b.C;
+  const bool chunked = b.nchunks > 1;
+  const size_t off0 = a.off;
+  b.tp[0] = plan_trunc(a, b.C, R1, tc, chunked, tu);
+  const size_t off1 = a.off;
+  if (Elast != b.C) {
+    a.off = off0;
+    b.tp[1] = plan_trunc(a, Elast, R1, tc, chunked, tu);
+    a.off = std::max(off1, a.off);
+  } else {
+    b.tp[1] = b.tp[0];
+  }
+}
+
 // false when the layer cannot be planned (too many truncation chunks)
 bool plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R0, int R1, bool tc,
                const mpc_tuning& tu, VMatPlan& p) {
@@ -1038,20 +1073,13 @@ bool plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R0, i
   p.s = plan_small(a);
   p.trunc = t >= 0;
   const long long E = M * N;
-  long long Elast = 0;
-  size_t trunc_tcs = 0;
-  if (p.trunc) {
-    trunc_chunks(E, tu, &p.nchunks, &p.C);
-    if (p.nchunks > MAX_TRUNC_CHUNKS) return false;
-    Elast = E - (p.nchunks - 1) * p.C;
-    trunc_tcs = std::max(trunc_tc_scratch(trunc_shape(p.C, R1, tc, tu)),
-                         trunc_tc_scratch(trunc_shape(Elast, R1, tc, tu)));
-  }
+  long long trunc_tcs = 0;
+  if (p.trunc && (trunc_tcs = trunc_batch_tcs(E, R1, tc, tu)) < 0) return false;
   // digit planes of the batch-0 products (X^T P, W Q, Z Q) and of the truncation chunks'
   // tensor-core products, on the tensor-core path
   p.tcs = tc ? (void*)a.take<unsigned char>((long long)std::max(
                    {limb_tc_scratch_bytes(K, 64, M, 1), limb_tc_scratch_bytes(K, 64, N, 1),
-                    limb_tc_scratch_bytes(6 * M, 64, N, 1), trunc_tcs}))
+                    limb_tc_scratch_bytes(6 * M, 64, N, 1), (size_t)trunc_tcs}))
              : nullptr;
   p.Q = a.take<u64>(N * 64);
   p.P = a.take<u64>(M * 64);
@@ -1060,20 +1088,23 @@ bool plan_vmat(Arena& a, long long M, long long N, long long K, int t, int R0, i
   const bool all[6] = {true, true, true, true, true, true};
   p.dv = plan_dense(a, K, all, all);
   p.iv = plan_iv(a, dim_after(K, p.R0));
-  if (p.trunc) {
-    // the chunks run one after another: their plans share the rest of the workspace
-    const bool chunked = p.nchunks > 1;
-    const size_t off0 = a.off;
-    p.tp[0] = plan_trunc(a, p.C, R1, tc, chunked, tu);
-    const size_t off1 = a.off;
-    if (Elast != p.C) {
-      a.off = off0;
-      p.tp[1] = plan_trunc(a, Elast, R1, tc, chunked, tu);
-      a.off = std::max(off1, a.off);
-    } else {
-      p.tp[1] = p.tp[0];
-    }
-  }
+  if (p.trunc) plan_trunc_batch(a, E, R1, tc, tu, p.tb);
+  return true;
+}
+
+// plan of a standalone truncation batch's verification (mpc_verify_trunc)
+struct VTruncPlan {
+  Small s;
+  TruncBatch tb;
+  void* tcs = nullptr;
+};
+
+bool plan_vtrunc(Arena& a, long long n, int R, bool tc, const mpc_tuning& tu, VTruncPlan& p) {
+  const long long tcs = trunc_batch_tcs(n, R, tc, tu);
+  if (tcs < 0) return false;
+  p.s = plan_small(a);
+  p.tcs = tc && tcs > 0 ? (void*)a.take<unsigned char>(tcs) : nullptr;
+  plan_trunc_batch(a, n, R, tc, tu, p.tb);
   return true;
 }
 
@@ -1306,6 +1337,39 @@ int verify_trunc_chunk(mpc_ctx* ctx, TruncPlan& p, const Small& s, void* tcs, co
   return rc;
 }
 
+// workspace of a standalone truncation (mpc_trunc)
+struct TruncCallPlan {
+  u64* rx;   // 6n: the pairs' r_x shares in the mask components
+  u64 *gp2, *gq2, *gp2i, *gq2i, *mp1, *mq1, *mpi1, *mqi1, *mpi2, *mqi2;   // pair messages
+  u64 *d1, *d2, *d1p0, *d2p0, *d1_at_p2, *d2_at_p1;                      // mask switch
+  u32* hs[4];
+  u32* dg;   // 4 x 8 digest words
+};
+
+TruncCallPlan plan_trunc_call(Arena& a, long long n) {
+  TruncCallPlan p;
+  p.rx = a.take<u64>(6 * n);
+  u64** bufs[] = {&p.gp2, &p.gq2, &p.gp2i, &p.gq2i, &p.mp1, &p.mq1, &p.mpi1, &p.mqi1, &p.mpi2,
+                  &p.mqi2, &p.d1, &p.d2, &p.d1p0, &p.d2p0, &p.d1_at_p2, &p.d2_at_p1};
+  for (u64** b : bufs) *b = a.take<u64>(n);
+  for (int i = 0; i < 4; ++i) p.hs[i] = a.take<u32>((long long)hash_scratch_words(n));
+  p.dg = a.take<u32>(32);
+  return p;
+}
+
+// Every chunk of a truncation batch (batches 1, 2, ... of verify_id); trace: chunk after chunk.
+int verify_trunc_batch(mpc_ctx* ctx, TruncBatch& b, const Small& s, void* tcs, const u64* pq,
+                       int trunc_bits, u64 verify_id, u64 call_id, u64* tr) {
+  for (long long i = 0; i < b.nchunks; ++i) {
+    TruncPlan& tp = b.tp[i == b.nchunks - 1 ? 1 : 0];
+    const int rc = verify_trunc_chunk(ctx, tp, s, tcs, pq, b.E, i * b.C, trunc_bits, verify_id,
+                                      (u32)(1 + i), call_id, tr);
+    if (rc) return rc;
+    if (tr) tr += (long long)(tp.R1 + 1) * TRACE_ROUND;
+  }
+  return MPC_OK;
+}
+
 }  // namespace
 
 // =================================================================================================
@@ -1449,6 +1513,19 @@ int64_t mpc_trace_words(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int64_
       }
       return w;
     }
+    case MPC_OP_VERIFY_TRUNC: {
+      if (a <= 0) return -1;
+      const mpc_tuning tu = ctx ? ctx->tune : default_tuning();
+      long long n = 0, C = 0;
+      trunc_chunks(a, tu, &n, &C);
+      if (n > MAX_TRUNC_CHUNKS) return -1;
+      int64_t w = 0;
+      for (long long i = 0; i < n; ++i) {
+        const long long Ei = i == n - 1 ? a - (n - 1) * C : C;
+        w += (int64_t)((R_trunc < 0 ? default_R(64 * Ei) : R_trunc) + 1) * TRACE_ROUND;
+      }
+      return w;
+    }
     default:
       return -1;
   }
@@ -1510,6 +1587,31 @@ int64_t mpc_workspace_size(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int
       if (a < 0) return -1;
       plan_rec(ar, a, true);
       break;
+    case MPC_OP_SHARE_FIXED:
+      if (a < 0) return -1;
+      ar.take<u64>(a);
+      ar.take<double>(a);
+      ar.take<u64>(a);
+      ar.take<u64>(a);
+      break;
+    case MPC_OP_RECONSTRUCT_FIXED:
+      if (a < 0) return -1;
+      ar.take<u64>(a);
+      ar.take<double>(a);
+      plan_rec(ar, a, false);
+      break;
+    case MPC_OP_TRUNC:
+      if (a <= 0) return -1;
+      plan_trunc_call(ar, a);
+      break;
+    case MPC_OP_VERIFY_TRUNC: {
+      if (a <= 0) return -1;
+      VTruncPlan vp;
+      if (!plan_vtrunc(ar, a, R_trunc, ctx && ctx->gemm_path == MPC_GEMM_LIMB_TC,
+                       ctx ? ctx->tune : default_tuning(), vp))
+        return -1;
+      break;
+    }
     default:
       return -1;
   }
@@ -1832,16 +1934,10 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
   delete phase;
   if (rc) return rc;
   // ---- batch 1: the truncation pairs, chunk by chunk ----
-  if (trunc) {
-    u64* tr = trace ? trace + (long long)(p.R0 + 1) * TRACE_ROUND : nullptr;
-    for (long long i = 0; i < p.nchunks; ++i) {
-      TruncPlan& tp = p.tp[i == p.nchunks - 1 ? 1 : 0];
-      if ((rc = verify_trunc_chunk(ctx, tp, s, p.tcs, pq, E, i * p.C, trunc_bits, verify_id,
-                                   (u32)(1 + i), matmul_call_id, tr)))
-        return rc;
-      if (tr) tr += (long long)(tp.R1 + 1) * TRACE_ROUND;
-    }
-  }
+  if (trunc &&
+      (rc = verify_trunc_batch(ctx, p.tb, s, p.tcs, pq, trunc_bits, verify_id, matmul_call_id,
+                               trace ? trace + (long long)(p.R0 + 1) * TRACE_ROUND : nullptr)))
+    return rc;
   return finish_verify(ctx, (matmul_call_id << 1) | 1);
 }
 
@@ -1940,6 +2036,161 @@ int mpc_profile_read(mpc_ctx* ctx, double* ms, uint64_t* count, double* work) {
 }
 
 uint64_t mpc_launch_count(void) { return g_launches; }
+
+
+// ---- layer-level calls -----------------------------------------------------------------------
+int mpc_share_fixed(mpc_ctx* ctx, uint64_t call_id, int owner, const double* x, int x_on_host,
+                    int64_t n, int frac_bits, uint64_t* xs, void* workspace,
+                    size_t workspace_bytes) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (n < 0) return fail(ctx, MPC_ERR_SHAPE, "share_fixed: n < 0");
+  if (frac_bits < 0 || frac_bits > 62) return fail(ctx, MPC_ERR_ARG, "share_fixed: frac_bits");
+  if (n == 0) return MPC_OK;
+  if (!x || !xs || !workspace) return fail(ctx, MPC_ERR_ARG, "share_fixed: bad argument");
+  Arena ar{(char*)workspace, workspace_bytes, 0, false};
+  u64* enc = ar.take<u64>(n);
+  double* stage = ar.take<double>(n);
+  if (!ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "share_fixed: workspace too small");
+  const double* xd = x;
+  if (x_on_host) {
+    CK(cudaMemcpyAsync(stage, x, (size_t)n * 8, cudaMemcpyHostToDevice, ctx->st));
+    xd = stage;
+  }
+  {
+    Phase phase(ctx, MPC_PROF_SHARE);
+    launch_encode_fixed(ctx->st, xd, n, frac_bits, enc);
+    g_launches += 1;
+  }
+  rc = mpc_share_input_from(ctx, call_id, owner, enc, 0, n, xs, (char*)workspace + ar.off,
+                            workspace_bytes > ar.off ? workspace_bytes - ar.off : 0);
+  if (rc == MPC_OK && x_on_host) CK(cudaStreamSynchronize(ctx->st));   // x may be reused
+  return rc;
+}
+
+int mpc_reconstruct_fixed(mpc_ctx* ctx, const uint64_t* xs, int64_t n, int frac_bits, double* out,
+                          int out_on_host, void* workspace, size_t workspace_bytes) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (n <= 0) return fail(ctx, MPC_ERR_SHAPE, "reconstruct_fixed: n <= 0");
+  if (frac_bits < 0 || frac_bits > 62 || !xs || !out || !workspace)
+    return fail(ctx, MPC_ERR_ARG, "reconstruct_fixed: bad argument");
+  Arena ar{(char*)workspace, workspace_bytes, 0, false};
+  u64* v = ar.take<u64>(n);
+  double* stage = ar.take<double>(n);
+  if (!ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "reconstruct_fixed: workspace too small");
+  rc = mpc_reconstruct(ctx, xs, n, v, 0, (char*)workspace + ar.off,
+                       workspace_bytes > ar.off ? workspace_bytes - ar.off : 0);
+  if (rc) {
+    if (out_on_host) std::memset(out, 0, (size_t)n * 8);
+    return rc;
+  }
+  {
+    Phase phase(ctx, MPC_PROF_REC);
+    launch_decode_fixed(ctx->st, v, n, frac_bits, out_on_host ? stage : out);
+    g_launches += 1;
+  }
+  if (out_on_host) {
+    CK(cudaMemcpyAsync(out, stage, (size_t)n * 8, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  return cuda_check(ctx, "reconstruct_fixed");
+}
+
+int mpc_conv2d(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_t* ws_,
+               const int32_t geom[8], int64_t C_out, int trunc_bits, uint64_t* cols,
+               uint64_t* zpre, uint64_t* zout, uint64_t* pq, void* workspace,
+               size_t workspace_bytes) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (!geom || !xs || !cols) return fail(ctx, MPC_ERR_ARG, "conv2d: bad argument");
+  ConvGeom g;
+  g.B = geom[0]; g.C = geom[1]; g.H = geom[2]; g.W = geom[3];
+  g.kh = geom[4]; g.kw = geom[5]; g.stride = geom[6]; g.pad = geom[7];
+  if (g.B <= 0 || g.C <= 0 || g.H <= 0 || g.W <= 0 || g.kh <= 0 || g.kw <= 0 || g.stride <= 0 ||
+      g.pad < 0 || C_out <= 0)
+    return fail(ctx, MPC_ERR_SHAPE, "conv2d: bad geometry");
+  if (g.H + 2 * g.pad < g.kh || g.W + 2 * g.pad < g.kw)
+    return fail(ctx, MPC_ERR_SHAPE, "conv2d: kernel larger than the padded image");
+  g.Ho = (g.H + 2 * g.pad - g.kh) / g.stride + 1;
+  g.Wo = (g.W + 2 * g.pad - g.kw) / g.stride + 1;
+  launch_im2col(ctx->st, xs, g, cols);
+  g_launches += 1;
+  if ((rc = cuda_check(ctx, "conv2d: im2col"))) return rc;
+  return mpc_matmul(ctx, call_id, cols, ws_, g.B * g.Ho * g.Wo, C_out, g.C * g.kh * g.kw,
+                    trunc_bits, zpre, zout, pq, workspace, workspace_bytes);
+}
+
+int mpc_trunc(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, int64_t n, int t, uint64_t* out,
+              uint64_t* pq, void* workspace, size_t workspace_bytes) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (n <= 0) return fail(ctx, MPC_ERR_SHAPE, "trunc: n <= 0");
+  if (t < 0 || t > 63 || !xs || !out || !pq || out == xs || !id_ok(call_id))
+    return fail(ctx, MPC_ERR_ARG, "trunc: bad argument");
+  Arena ar{(char*)workspace, workspace_bytes, 0, false};
+  TruncCallPlan p = plan_trunc_call(ar, n);
+  if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "trunc: workspace too small");
+  cudaStream_t st = ctx->st;
+  const u64 obj = make_obj(call_id, 0, 0);
+  {  // preprocessing (Fig. trunc): the pairs, as for a truncated product
+    Phase phase(ctx, MPC_PROF_TRUNC_PAIRS);
+    launch_trunc_p0(st, n, ctx->k01, ctx->k02, obj, t, p.rx, out, pq, p.gp2, p.gq2, p.mp1, p.mq1);
+    const int ph = MPC_PHASE_OFFLINE, pr = MPC_PROTO_TRUNC;
+    if ((rc = deliver(ctx, ph, pr, p.gp2, p.gp2i, n, MPC_SITE_GAMMA2))) return rc;
+    if ((rc = deliver(ctx, ph, pr, p.mp1, p.mpi2, n, MPC_SITE_MZ1))) return rc;
+    if ((rc = deliver(ctx, ph, pr, p.gp2i, p.mpi1, n, MPC_SITE_MZ2))) return rc;
+    if ((rc = deliver(ctx, ph, pr, p.gq2, p.gq2i, n, MPC_SITE_GAMMA2))) return rc;
+    if ((rc = deliver(ctx, ph, pr, p.mq1, p.mqi2, n, MPC_SITE_MZ1))) return rc;
+    if ((rc = deliver(ctx, ph, pr, p.gq2i, p.mqi1, n, MPC_SITE_MZ2))) return rc;
+    launch_trunc_finish(st, n, ctx->k01, ctx->k02, obj, t, p.mpi1, p.mqi1, p.mpi2, p.mqi2,
+                        p.gp2i, p.gq2i, p.mp1, p.mq1, p.rx, out, pq);
+  }
+  {  // online: the wire's mask switched to the pairs' r_x (checked by P0's hashes), then m >> t
+    Phase phase(ctx, MPC_PROF_EXCHANGE);
+    launch_trunc_remask(st, xs, p.rx, n, p.d1, p.d2, p.d1p0, p.d2p0);
+    g_launches += 1;
+    const int ph = MPC_PHASE_ONLINE, pr = MPC_PROTO_TRUNC;
+    if ((rc = deliver(ctx, ph, pr, p.d1, p.d1_at_p2, n, MPC_SITE_TRUNC_D1))) return rc;   // P1->P2
+    if ((rc = deliver(ctx, ph, pr, p.d2, p.d2_at_p1, n, -1))) return rc;                 // P2->P1
+    launch_hash_u64(st, p.d1p0, n, p.hs[0], p.dg);            // P0: H(d1) -> P2
+    launch_hash_u64(st, p.d2p0, n, p.hs[1], p.dg + 8);        // P0: H(d2) -> P1
+    count_msgs(ctx, ph, pr, 2, 32);
+    launch_hash_u64(st, p.d1_at_p2, n, p.hs[2], p.dg + 16);   // P2 hashes the d1 it received
+    launch_hash_u64(st, p.d2_at_p1, n, p.hs[3], p.dg + 24);   // P1 hashes the d2 it received
+    launch_digest_check(st, p.dg, p.dg + 16, p.dg + 8, p.dg + 24, p.dg, p.dg + 16, ctx->status,
+                        ST_ABORT);
+    launch_trunc_online(st, xs, n, p.d1, p.d2_at_p1, p.d1_at_p2, p.d2, t, out);
+    g_launches += 1;
+  }
+  if ((rc = cuda_check(ctx, "trunc"))) return rc;
+  ctx->pending.insert((call_id << 1) | 1);
+  u32 stv = 0;
+  if ((rc = read_status(ctx, &stv))) return rc;
+  if (stv & ST_ABORT) {
+    ctx->aborted = true;
+    return fail(ctx, MPC_ERR_ABORT, "Pi_Trunc: a mask-switch message disagrees with P0's hash");
+  }
+  return MPC_OK;
+}
+
+int mpc_verify_trunc(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* pq, int64_t n, int t,
+                     uint64_t trunc_call_id, int R, void* workspace, size_t workspace_bytes,
+                     uint64_t* trace) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (n <= 0) return fail(ctx, MPC_ERR_SHAPE, "verify_trunc: n <= 0");
+  if (!pq || t < 0 || t > 63 || !id_ok(verify_id) || !id_ok(trunc_call_id))
+    return fail(ctx, MPC_ERR_ARG, "verify_trunc: bad argument");
+  Arena ar{(char*)workspace, workspace_bytes, 0, false};
+  VTruncPlan p;
+  if (!plan_vtrunc(ar, n, R, ctx->gemm_path == MPC_GEMM_LIMB_TC, ctx->tune, p))
+    return fail(ctx, MPC_ERR_SHAPE, "verify_trunc: more than 15 chunks");
+  if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "verify_trunc: workspace too small");
+  if ((rc = verify_trunc_batch(ctx, p.tb, p.s, p.tcs, pq, t, verify_id, trunc_call_id, trace)))
+    return rc;
+  return finish_verify(ctx, (trunc_call_id << 1) | 1);
+}
 
 }  // extern "C"
 

@@ -267,4 +267,22 @@ void launch_mult_offline_p(cudaStream_t st, const u64* xs, const u64* ys, long l
 void launch_mult_online_p(cudaStream_t st, const u64* xs, const u64* ys, long long n, Key k01,
                           u32 purpose, u64 obj, const u64* p2_in_g2, u64* p1_out, u64* p2_out);
 
+// ---- layer-level calls (layer_kernels.cu) ----------------------------------------------------
+// Geometry of a convolution: NCHW input (B, C, H, W), kh x kw kernel, stride, zero padding; the
+// output is Ho x Wo per image.
+struct ConvGeom {
+  long long B, C, H, W, kh, kw, stride, pad, Ho, Wo;
+};
+// out[i] = floor(x[i] 2^k) (saturating, NaN -> 0) / out[i] = (signed) v[i] / 2^k
+void launch_encode_fixed(cudaStream_t st, const double* x, long long n, int k, u64* out);
+void launch_decode_fixed(cudaStream_t st, const u64* v, long long n, int k, double* out);
+// the im2col rows of all six components of x: cols holds 6 (B Ho Wo) (C kh kw) words
+void launch_im2col(cudaStream_t st, const u64* x, const ConvGeom& g, u64* cols);
+// the mask-switch differences of a standalone truncation and its online shift
+void launch_trunc_remask(cudaStream_t st, const u64* xs, const u64* rx, long long n, u64* d1_p1,
+                         u64* d2_p2, u64* d1_p0, u64* d2_p0);
+void launch_trunc_online(cudaStream_t st, const u64* xs, long long n, const u64* d1,
+                         const u64* d2_at_p1, const u64* d1_at_p2, const u64* d2, int t,
+                         u64* out);
+
 }  // namespace mpc3

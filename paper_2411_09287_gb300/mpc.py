@@ -21,9 +21,10 @@ MPC_ERR_TIMEOUT, MPC_ERR_VERIFY, MPC_ERR_ABORT, MPC_ERR_PENDING = 5, 6, 7, 8
 REDUCE_POINT_X, REDUCE_POINT_2 = 0, 1
 GEMM_U64, GEMM_LIMB_TC = 0, 1
 (OP_SHARE, OP_MULT, OP_MATMUL, OP_VERIFY_MULT, OP_VERIFY_MATMUL, OP_RECONSTRUCT, OP_RELU,
- OP_MAXPOOL2, OP_VERIFY_MULT_CALLS) = range(9)
+ OP_MAXPOOL2, OP_VERIFY_MULT_CALLS, OP_SHARE_FIXED, OP_RECONSTRUCT_FIXED, OP_TRUNC,
+ OP_VERIFY_TRUNC) = range(13)
 SITES = {"GAMMA2": 0, "MZ1": 1, "MZ2": 2, "MX_COPY_P1": 3, "REC_MSG": 4, "HIGH_BIT": 5,
-         "AND_GAMMA2": 6}
+         "AND_GAMMA2": 6, "TRUNC_D1": 7}
 TRACE_GF_ROUND = 13
 PHASES = ("offline", "online", "verify")
 PROTOS = ("share", "mult", "inner", "trunc", "rec", "verify")
@@ -181,6 +182,81 @@ class Context:
         if on_host:   # the host buffer must stay alive until the copy ran
             self.sync()
         return out
+
+    def share_fixed(self, call_id: int, x, frac_bits: int, out=None, owner: int = 0):
+        """mpc_share_fixed: the library encodes floor(x 2^k) and shares it.  x: numpy float64
+        (host) or a CUDA float64 tensor (device)."""
+        if isinstance(x, np.ndarray):
+            xh = np.ascontiguousarray(x, dtype=np.float64)
+            n, ptr, on_host = xh.size, xh.ctypes.data, 1
+        else:
+            n, ptr, on_host = x.numel(), _ptr(x), 0
+        out = self.shares(n) if out is None else out
+        wsb = self.ws_size(OP_SHARE_FIXED, n)
+        ws = self.workspace(wsb)
+        self._check(self.lib.mpc_share_fixed(self.h, call_id, owner, C.c_void_p(ptr), on_host, n,
+                                             frac_bits, C.c_void_p(_ptr(out)),
+                                             C.c_void_p(_ptr(ws)), wsb))
+        return out
+
+    def reconstruct_fixed(self, xs, n: int, frac_bits: int) -> np.ndarray:
+        """mpc_reconstruct_fixed: Pi_Rec, then the signed value / 2^k (host float64 array)."""
+        out = np.empty(n, dtype=np.float64)
+        wsb = self.ws_size(OP_RECONSTRUCT_FIXED, n)
+        ws = self.workspace(wsb)
+        self._check(self.lib.mpc_reconstruct_fixed(self.h, C.c_void_p(_ptr(xs)), n, frac_bits,
+                                                   C.c_void_p(out.ctypes.data), 1,
+                                                   C.c_void_p(_ptr(ws)), wsb))
+        return out
+
+    @staticmethod
+    def conv_out(geom):
+        """(Ho, Wo) of a convolution, (0, 0) for a geometry the library rejects."""
+        B, Cc, H, W, kh, kw, stride, pad = geom
+        if stride <= 0 or pad < 0 or H + 2 * pad < kh or W + 2 * pad < kw:
+            return 0, 0
+        return (H + 2 * pad - kh) // stride + 1, (W + 2 * pad - kw) // stride + 1
+
+    def conv2d(self, call_id: int, xs, ws_, geom, C_out: int, trunc_bits: int = -1):
+        """mpc_conv2d.  geom = (B, C, H, W, kh, kw, stride, pad).  Returns (cols, zpre, zout, pq,
+        (M, N, K)) with M = B Ho Wo, N = C_out, K = C kh kw (output rows (b, i, j))."""
+        B, Cc, H, W, kh, kw, stride, pad = geom
+        Ho, Wo = self.conv_out(geom)
+        Mr, K = B * Ho * Wo, Cc * kh * kw
+        E = Mr * C_out
+        cols = self.shares(Mr * K)
+        zpre = self.shares(E)
+        zout = self.shares(E) if trunc_bits >= 0 else None
+        pq = self.empty(12 * E) if trunc_bits >= 0 else None
+        wsb = self.ws_size(OP_MATMUL, Mr, C_out, K, trunc_bits)
+        ws = self.workspace(wsb)
+        g = (C.c_int32 * 8)(*geom)
+        self._check(self.lib.mpc_conv2d(self.h, call_id, C.c_void_p(_ptr(xs)), C.c_void_p(_ptr(ws_)),
+                                        g, C_out, trunc_bits, C.c_void_p(_ptr(cols)),
+                                        C.c_void_p(_ptr(zpre)), C.c_void_p(_ptr(zout)),
+                                        C.c_void_p(_ptr(pq)), C.c_void_p(_ptr(ws)), wsb))
+        return cols, zpre, (zout if trunc_bits >= 0 else zpre), pq, (Mr, C_out, K)
+
+    def trunc(self, call_id: int, xs, n: int, t: int):
+        """mpc_trunc: Pi_Trunc^t of a sharing.  Returns (out sharing, pq)."""
+        out, pq = self.shares(n), self.empty(12 * n)
+        wsb = self.ws_size(OP_TRUNC, n)
+        ws = self.workspace(wsb)
+        self._check(self.lib.mpc_trunc(self.h, call_id, C.c_void_p(_ptr(xs)), n, t,
+                                       C.c_void_p(_ptr(out)), C.c_void_p(_ptr(pq)),
+                                       C.c_void_p(_ptr(ws)), wsb))
+        return out, pq
+
+    def verify_trunc(self, verify_id: int, pq, n: int, t: int, trunc_call_id: int, R: int = -1,
+                     trace: bool = False):
+        tr = self.zeros(self.trace_words(OP_VERIFY_TRUNC, n, 0, 0, t, -1, R)) if trace else None
+        wsb = self.ws_size(OP_VERIFY_TRUNC, n, R_trunc=R)
+        ws = self.workspace(wsb)
+        rc = self.lib.mpc_verify_trunc(self.h, verify_id, C.c_void_p(_ptr(pq)), n, t, trunc_call_id,
+                                       R, C.c_void_p(_ptr(ws)), wsb, C.c_void_p(_ptr(tr)))
+        if rc not in (MPC_OK, MPC_ERR_VERIFY, MPC_ERR_ABORT):
+            self._check(rc)
+        return rc, tr
 
     def mult(self, call_id: int, xs, ys, n: int, out=None):
         out = self.shares(n) if out is None else out
@@ -382,11 +458,3 @@ def from_u64(ctx: Context, a: np.ndarray):
     t = ctx.torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64))
     return t.to(ctx.device)
 
-
-def encode_fixed(x, k: int) -> np.ndarray:
-    """Sec. 2 fixed-point encoding: floor(x 2^k) mod 2^64 (two's complement for x < 0)."""
-    return np.floor(np.asarray(x, dtype=np.float64) * float(1 << k)).astype(np.int64).astype(np.uint64)
-
-
-def decode_fixed(v, k: int) -> np.ndarray:
-    return np.asarray(v, dtype=np.uint64).astype(np.int64).astype(np.float64) / float(1 << k)

@@ -1,9 +1,9 @@
-"""Secure CNN inference through libmpc3: convolutions as im2col share GEMMs (config C4, Net A:
-28x28x1 input, conv 5x5x16, 2x2 max-pool, conv 5x5x16, 2x2 max-pool, FC 256-100-10; reading A17).
+"""Secure CNN inference through libmpc3 (config C4, Net A: 28x28x1 input, conv 5x5x16, 2x2
+max-pool, conv 5x5x16, 2x2 max-pool, FC 256-100-10; reading A17).
 
-A convolution is a local im2col rearrangement of the shares (mpc_gather: every party applies the
-same index map to its components), one Pi_Inner matrix product with Pi_Trunc^k (Sec. 4.1: each
-output is one inner product) and its verification, and a local rearrangement back to NCHW.
+A convolution is mpc_conv2d (the library lowers the shares to the im2col rows of the outputs'
+inner products and runs Pi_Inner with Pi_Trunc^k on them, Sec. 4.1) with its verification, then a
+local rearrangement of the output rows (b, i, j) x c_out back to NCHW (mpc_gather).
 Max-pool and ReLU are the Sec. 4.3 layers; they commute (max of ReLUs = ReLU of the max), so
 every conv block pools first and applies ReLU to the 4x smaller result.  Non-linear layers are
 called per chunk of at most `nl_chunk` elements, each chunk with its own verification.  The index
@@ -130,35 +130,54 @@ def _pool_chunked(ctx, ids, h, shape, chunk_images):
     return _concat(ctx, parts)
 
 
-def _conv_block(ctx, ids, h, shape, w_fixed, k, pool_chunk, relu_chunk):
+def _conv_block(ctx, ids, h, shape, gw, wshape, k, pool_chunk, relu_chunk):
     B, C, H, W = shape
-    Co, _, kh, kw = w_fixed.shape
-    idx, Ho, Wo = im2col_index(B, C, H, W, kh, kw)
-    cols = ctx.gather(h, B * C * H * W, idx)
-    gw = ctx.share_input(ids.take(), conv_weight_matrix(w_fixed).reshape(-1))
-    Mr, K = B * Ho * Wo, C * kh * kw
-    z = _matmul_verified(ctx, ids, cols, gw, Mr, Co, K, k)
-    z = ctx.gather(z, Mr * Co, rows_to_nchw_index(B, Co, Ho, Wo))
+    Co, _, kh, kw = wshape
+    c = ids.take(2)
+    geom = (B, C, H, W, kh, kw, 1, 0)
+    cols, zpre, zout, pq, (Mr, N, K) = ctx.conv2d(c, h, gw, geom, Co, k)
+    rc, _ = ctx.verify_matmul(c + 1, cols, gw, zpre, pq, Mr, N, K, k, c)
+    if rc != M.MPC_OK:
+        raise M.MpcError(rc, "convolution rejected")
+    Ho, Wo = ctx.conv_out(geom)
+    z = ctx.gather(zout, Mr * Co, rows_to_nchw_index(B, Co, Ho, Wo))
     z = _pool_chunked(ctx, ids, z, (B, Co, Ho, Wo), pool_chunk)
     n = B * Co * (Ho // 2) * (Wo // 2)
     return _relu_chunked(ctx, ids, z, n, relu_chunk), (B, Co, Ho // 2, Wo // 2)
 
 
-def net_a_secure(ctx: "M.Context", x_fixed, p_fixed, k: int = 13, call_base: int = 5000,
-                 pool_chunk: int = 4, relu_chunk: int = 1 << 15):
-    """Secure Net A forward.  x_fixed: (B, 1, 28, 28) u64; p_fixed: the fixed-point parameters.
-    Returns the opened logits (B, 10), fixed-point with k bits."""
+def share_params(ctx: "M.Context", params, k: int = 13, call_base: int = 4000):
+    """P0 shares Net A's weights once (mpc_share_fixed): the conv kernels as (C kh kw) x C_out
+    matrices (a public layout of P0's plaintext), the FC matrices as they are.  The sharings can
+    serve any number of forward passes."""
+    out = {}
+    for i, name in enumerate(("c1", "c2", "f1", "f2")):
+        w = params[name]
+        m = conv_weight_matrix(w) if name.startswith("c") else w
+        out[name] = ctx.share_fixed(call_base + i, np.ascontiguousarray(m, dtype=np.float64).reshape(-1), k)
+    return out
+
+
+def net_a_secure(ctx: "M.Context", x, params, k: int = 13, call_base: int = 5000,
+                 pool_chunk: int = 4, relu_chunk: int = 1 << 15, shared=None):
+    """Secure Net A forward.  x: (B, 1, 28, 28) float inputs; params: the float parameters (shared
+    by P0 here unless `shared` holds share_params' sharings).  Returns the opened logits (B, 10)
+    as float64."""
     ids = _Ids(call_base)
-    B = x_fixed.shape[0]
-    h = ctx.share_input(ids.take(), np.ascontiguousarray(x_fixed).reshape(-1))
-    h, shape = _conv_block(ctx, ids, h, x_fixed.shape, p_fixed["c1"], k, pool_chunk, relu_chunk)
-    h, shape = _conv_block(ctx, ids, h, shape, p_fixed["c2"], k, pool_chunk, relu_chunk)
+    if shared is None:
+        shared = share_params(ctx, params, k, ids.take(4))
+    B = x.shape[0]
+    h = ctx.share_fixed(ids.take(), np.ascontiguousarray(x, dtype=np.float64).reshape(-1), k)
+    shape = x.shape
+    h, shape = _conv_block(ctx, ids, h, shape, shared["c1"], params["c1"].shape, k, pool_chunk,
+                           relu_chunk)
+    h, shape = _conv_block(ctx, ids, h, shape, shared["c2"], params["c2"].shape, k, pool_chunk,
+                           relu_chunk)
     flat = int(np.prod(shape[1:]))
     for name, last in (("f1", False), ("f2", True)):
-        w = p_fixed[name]
-        gw = ctx.share_input(ids.take(), np.ascontiguousarray(w).reshape(-1))
-        h = _matmul_verified(ctx, ids, h, gw, B, w.shape[1], flat, k)
+        w = params[name]
+        h = _matmul_verified(ctx, ids, h, shared[name], B, w.shape[1], flat, k)
         flat = w.shape[1]
         if not last:
             h = _relu_chunked(ctx, ids, h, B * flat, relu_chunk)
-    return ctx.reconstruct(h, B * flat).reshape(B, flat)
+    return ctx.reconstruct_fixed(h, B * flat, k).reshape(B, flat)

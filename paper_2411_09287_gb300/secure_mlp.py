@@ -31,27 +31,35 @@ def fp64_forward(x, weights):
     return h
 
 
-def secure_forward(ctx: "M.Context", x_fixed, w_fixed, k: int = 13, call_base: int = 1000,
-                   profile_phases=None):
-    """Secure forward pass.  x_fixed: (B, n0) u64 fixed-point; w_fixed: list of (n_i, n_{i+1}) u64
-    fixed-point matrices.  Returns the opened logits (u64, fixed-point with k bits)."""
-    B = x_fixed.shape[0]
+def quantized(x, k: int):
+    """The values the fixed-point encoding of Sec. 2 represents (floor(x 2^k) / 2^k), for the
+    float64 reference model."""
+    return np.floor(np.asarray(x, dtype=np.float64) * float(1 << k)) / float(1 << k)
+
+
+def secure_forward(ctx: "M.Context", x, weights, k: int = 13, call_base: int = 1000,
+                   shared_weights=None):
+    """Secure forward pass.  x: (B, n0) float inputs; weights: list of (n_i, n_{i+1}) float
+    matrices, shared by P0 (mpc_share_fixed) unless shared_weights already holds their sharings.
+    Returns the opened logits (B, n_last) as float64 (mpc_reconstruct_fixed)."""
+    B = x.shape[0]
     cid = call_base
-    h = ctx.share_input(cid, np.ascontiguousarray(x_fixed).reshape(-1))
+    h = ctx.share_fixed(cid, np.ascontiguousarray(x, dtype=np.float64).reshape(-1), k)
     cid += 1
-    for i, w in enumerate(w_fixed):
+    for i, w in enumerate(weights):
         n_in, n_out = w.shape
-        gw = ctx.share_input(cid, np.ascontiguousarray(w).reshape(-1))
+        gw = (shared_weights[i] if shared_weights is not None
+              else ctx.share_fixed(cid, np.ascontiguousarray(w, dtype=np.float64).reshape(-1), k))
         zpre, zout, pq = ctx.matmul(cid + 1, h, gw, B, n_out, n_in, k)
         rc, _ = ctx.verify_matmul(cid + 2, h, gw, zpre, pq, B, n_out, n_in, k, cid + 1)
         if rc != M.MPC_OK:
             raise M.MpcError(rc, f"layer {i}: verification rejected")
         h = zout
         cid += 3
-        if i + 1 < len(w_fixed):
+        if i + 1 < len(weights):
             rc, h, _ = ctx.relu(cid, cid + 1, h, B * n_out)
             if rc != M.MPC_OK:
                 raise M.MpcError(rc, f"layer {i}: ReLU verification rejected")
             cid += 2
-    n_last = w_fixed[-1].shape[1]
-    return ctx.reconstruct(h, B * n_last).reshape(B, n_last)
+    n_last = weights[-1].shape[1]
+    return ctx.reconstruct_fixed(h, B * n_last, k).reshape(B, n_last)

@@ -43,29 +43,25 @@ class Model:
     def __init__(self, kind: str, k: int = 13):
         self.kind, self.k = kind, k
         if kind == "mlp":
-            w = SM.mlp_weights([784, 128, 128, 10], "C2-weights")
-            self.wf = [M.encode_fixed(a, k) for a in w]
+            self.w = SM.mlp_weights([784, 128, 128, 10], "C2-weights")
             self.in_shape = (784,)
         elif kind == "neta":
-            p = SC.net_a_params("C4-netA-weights")
-            self.pf = {n: M.encode_fixed(a, k) for n, a in p.items()}
+            self.p = SC.net_a_params("C4-netA-weights")
             self.in_shape = (1, 28, 28)
         else:
             raise ValueError(kind)
 
     def secure(self, ctx, x, call_base):
-        xf = M.encode_fixed(x, self.k)
+        """Opened logits (float64) of one secure forward pass over the packed inputs x."""
         if self.kind == "mlp":
-            out = SM.secure_forward(ctx, xf, self.wf, self.k, call_base)
-        else:
-            out = SC.net_a_secure(ctx, xf, self.pf, self.k, call_base)
-        return M.decode_fixed(out, self.k)
+            return SM.secure_forward(ctx, x, self.w, self.k, call_base)
+        return SC.net_a_secure(ctx, x, self.p, self.k, call_base)
 
     def fp64(self, x):
-        xd = M.decode_fixed(M.encode_fixed(x, self.k), self.k)
+        q = lambda a: SM.quantized(a, self.k)
         if self.kind == "mlp":
-            return SM.fp64_forward(xd, [M.decode_fixed(a, self.k) for a in self.wf])
-        return SC.net_a_fp64(xd, {n: M.decode_fixed(a, self.k) for n, a in self.pf.items()})
+            return SM.fp64_forward(q(x), [q(w) for w in self.w])
+        return SC.net_a_fp64(q(x), {n: q(w) for n, w in self.p.items()})
 
     def bytes_per_image(self, ctx, b: int) -> float:
         """Peak workspace of one packed batch of b images (the largest single call) / b."""

@@ -27,12 +27,9 @@ def test_secure_mlp_logits_within_bound(mpc, path):
     sizes = [784, 128, 128, 10]
     weights = SM.mlp_weights(sizes, "C2-weights")
     x = workloads.rng("C2-inputs").uniform(0.0, 1.0, (128, 784))
-    xf = mpc.encode_fixed(x, k)
-    wf = [mpc.encode_fixed(w, k) for w in weights]
     ctx = mpc.Context(hashlib.sha256(b"mpc3-config-C2").digest(), gemm_path=path)
-    logits = SM.secure_forward(ctx, xf, wf, k)
-    got = mpc.decode_fixed(logits, k)
-    ref = SM.fp64_forward(mpc.decode_fixed(xf, k), [mpc.decode_fixed(w, k) for w in wf])
+    got = SM.secure_forward(ctx, x, weights, k)
+    ref = SM.fp64_forward(SM.quantized(x, k), [SM.quantized(w, k) for w in weights])
     err = np.abs(got - ref)
     assert err.max() <= 2.0 ** -8, err.max()
     # the secure network computes the same classification as the float64 model
@@ -44,15 +41,14 @@ def test_secure_cnn_net_a_within_bound(mpc, path):
     """Config C4, Net A (reading A17): conv 5x5x16, pool, conv 5x5x16, pool, FC 256-100-10 over
     im2col share GEMMs, batch 8; He-normal weights, inputs U[0, 1)."""
     from paper_2411_09287_gb300 import secure_cnn as SC
+    from paper_2411_09287_gb300 import secure_mlp as SM
     from paper_2411_09287_gb300 import workloads
     k = 13
     p = SC.net_a_params("C4-netA-weights")
     x = workloads.rng("C4-netA-inputs").uniform(0.0, 1.0, (8, 1, 28, 28))
-    xf = mpc.encode_fixed(x, k)
-    pf = {n: mpc.encode_fixed(w, k) for n, w in p.items()}
     ctx = mpc.Context(hashlib.sha256(b"mpc3-config-C4").digest(), gemm_path=path)
-    logits = SC.net_a_secure(ctx, xf, pf, k)
-    got = mpc.decode_fixed(logits, k)
-    ref = SC.net_a_fp64(mpc.decode_fixed(xf, k), {n: mpc.decode_fixed(w, k) for n, w in pf.items()})
+    got = SC.net_a_secure(ctx, x, p, k)
+    q = lambda a: SM.quantized(a, k)
+    ref = SC.net_a_fp64(q(x), {n: q(w) for n, w in p.items()})
     err = np.abs(got - ref)
     assert err.max() <= 2.0 ** -8, err.max()

@@ -109,7 +109,7 @@ def test_plain_small_mult_and_verify(mpc, mode):
     """Config 'plain protocol, small': Pi_Mult of two 4096-vectors, Pi_MultVerify, Pi_Rec."""
     seed = workloads.master_seed("C1")
     _, _, a, b = workloads.plain_small()
-    xa, xb = mpc.encode_fixed(a, 13), mpc.encode_fixed(b, 13)
+    xa, xb = OP.encode_fixed(a, 13), OP.encode_fixed(b, 13)
     ctx = mpc.Context(seed, reduce_mode=mode)
     sess = Session(seed, reduce_mode="x" if mode == 0 else "zeta2")
     n = a.size
@@ -137,8 +137,8 @@ def test_matmul_matches_oracle(mpc, M, N, K, t, path):
     X, W = workloads.gemm_shape(M, N, K)
     if t >= 0:
         g = workloads.rng(f"fx-{M}-{N}-{K}")
-        X = mpc.encode_fixed(g.uniform(-4, 4, (M, K)), 13)
-        W = mpc.encode_fixed(g.uniform(-4, 4, (K, N)), 13)
+        X = OP.encode_fixed(g.uniform(-4, 4, (M, K)), 13)
+        W = OP.encode_fixed(g.uniform(-4, 4, (K, N)), 13)
     ctx = mpc.Context(seed, gemm_path=path)
     sess = Session(seed)
     gx, gw = ctx.share_input(1, X), ctx.share_input(2, W)
@@ -162,8 +162,8 @@ def test_matmul_matches_oracle(mpc, M, N, K, t, path):
 def test_matmul_verify_transcript_matches_oracle(mpc, M, N, K, t, mode, path):
     seed = seed_of(f"vmat-{M}-{N}-{K}-{t}-{mode}")
     g = workloads.rng(f"vmat-{M}-{N}-{K}")
-    X = mpc.encode_fixed(g.uniform(-4, 4, (M, K)), 13)
-    W = mpc.encode_fixed(g.uniform(-4, 4, (K, N)), 13)
+    X = OP.encode_fixed(g.uniform(-4, 4, (M, K)), 13)
+    W = OP.encode_fixed(g.uniform(-4, 4, (K, N)), 13)
     ctx = mpc.Context(seed, reduce_mode=mode, gemm_path=path)
     sess = Session(seed, reduce_mode="x" if mode == 0 else "zeta2")
     gx, gw = ctx.share_input(1, X), ctx.share_input(2, W)
@@ -212,8 +212,8 @@ def test_tc_and_u64_paths_give_identical_verification(mpc, M, N, K):
     shapes above."""
     seed = seed_of(f"paths-{M}-{N}-{K}")
     g = workloads.rng(f"paths-{M}-{N}-{K}")
-    X = mpc.encode_fixed(g.uniform(-4, 4, (M, K)), 13)
-    W = mpc.encode_fixed(g.uniform(-4, 4, (K, N)), 13)
+    X = OP.encode_fixed(g.uniform(-4, 4, (M, K)), 13)
+    W = OP.encode_fixed(g.uniform(-4, 4, (K, N)), 13)
     res = []
     for path in (0, 1):
         ctx = mpc.Context(seed, gemm_path=path)
