@@ -117,7 +117,11 @@ typedef struct {
  *                  default 8.
  *   gram_split     split-K slices of a tensor-core Gram sum (dense rounds); default 76.
  *   fold_batch_max the folds of one Pi_Reduce round share one launch when the folded vectors
- *                  have at most this many elements; default 65536. */
+ *                  have at most this many elements; default 65536.
+ *   gr_producers   how the GR-matrix products (folds, tables) load their A rows: 1 producer
+ *                  warps' global loads into registers (two digit-plane stages), 2 TMA loads into
+ *                  shared memory (one digit-plane stage); default 1.
+ *   gr_drain_warps warps that drain the GR-matrix products' accumulators: 8 or 16; default 8. */
 typedef struct {
   int64_t trunc_block;
   int64_t trunc_chunk;
@@ -126,6 +130,8 @@ typedef struct {
   int32_t gemm_split_min;
   int32_t gram_split;
   int32_t fold_batch_max;
+  int32_t gr_producers;
+  int32_t gr_drain_warps;
 } mpc_tuning;
 
 /* Create a context (keys, stream, device constants, ledger).  *out is NULL on failure. */

@@ -19,7 +19,8 @@ class MpcConfig(C.Structure):
 class MpcTuning(C.Structure):
     _fields_ = [("trunc_block", C.c_int64), ("trunc_chunk", C.c_int64), ("row_split", C.c_int64),
                 ("tc_combine_min", C.c_int32), ("gemm_split_min", C.c_int32),
-                ("gram_split", C.c_int32), ("fold_batch_max", C.c_int32)]
+                ("gram_split", C.c_int32), ("fold_batch_max", C.c_int32),
+                ("gr_producers", C.c_int32), ("gr_drain_warps", C.c_int32)]
 
 
 _SIGS = {

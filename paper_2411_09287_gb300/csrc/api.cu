@@ -145,6 +145,8 @@ mpc_tuning default_tuning() {
   t.gemm_split_min = 8;
   t.gram_split = 76;
   t.fold_batch_max = 65536;
+  t.gr_producers = 1;
+  t.gr_drain_warps = 8;
   return t;
 }
 }  // namespace
@@ -311,6 +313,14 @@ void gram(mpc_ctx* ctx, u64* P, const u64* U0, const u64* U1, u64 su, long long 
   gemm_u64(ctx->st, 64, 64, count, 1, &T, epi_atomic(P, 64, sign), nsplit_for(count));
 }
 
+// GR-product arguments with this context's choice of producer and drain variant
+GrMMArgs grargs(const mpc_ctx* ctx) {
+  GrMMArgs g{};
+  g.tma = ctx->tune.gr_producers == 2;
+  g.drain_warps = ctx->tune.gr_drain_warps;
+  return g;
+}
+
 // out[i] = add0[i] + (p0[i] + s1 p1[i]) . M for i < R (rows of 64 words, M a 64 x 64 GR
 // multiplication matrix): the folds of Pi_Reduce and the products by a fixed GR element.  Tensor
 // cores on the limb path, the u64 CUDA-core GEMM otherwise.
@@ -320,9 +330,18 @@ int gr_matmul(mpc_ctx* ctx, long long R, const u64* p0, const u64* p1, u64 s1, l
   if (ctx->gemm_path == MPC_GEMM_LIMB_TC) {
     g_launches += 1;
     Phase kp(ctx, MPC_PROF_K_GR_MATMUL, (double)R * 4096);
-    if (gr_matmul_tc(ctx->st, R, p0, p1, s1, lda, 0, Mmat, add0, ld_add0, out, ldc, ctx->status,
-                     ST_TIMEOUT) == 0)
-      return MPC_OK;
+    GrMMArgs g = grargs(ctx);
+    g.R = R;
+    g.p0 = p0;
+    g.p1 = p1;
+    g.s1 = s1;
+    g.in = GrRowMap{0, lda, 0};
+    g.Mmat = Mmat;
+    g.add0 = add0;
+    g.ld_add0 = ld_add0 ? ld_add0 : ldc;
+    g.out = out;
+    g.om = GrRowMap{0, ldc, 0};
+    if (gr_matmul_tc_ex(ctx->st, g, ctx->status, ST_TIMEOUT) == 0)
     g_launches -= 1;   // misaligned view: fall through to the CUDA-core GEMM
   }
   GemmTerm T;
@@ -623,7 +642,7 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
       even = ins[i] - ins[0] == i * sin && outs[i] - outs[0] == i * sout;
     if (even && sin > 0 && sout > 0) {
       const long long Rp = (Dh + 127) / 128 * 128;
-      GrMMArgs g{};
+      GrMMArgs g = grargs(ctx);
       g.R = n * Rp;
       g.p0 = ins[0] + 64;
       g.p1 = ins[0];
@@ -1148,7 +1167,7 @@ int verify_trunc_chunk(mpc_ctx* ctx, TruncPlan& p, const Small& s, void* tcs, co
     launch_gr_mulmat_batch(st, p.nhi - 1, p.Thi + 64, 64, p.Mhi);
     bool done = false;
     if (ctx->gemm_path == MPC_GEMM_LIMB_TC) {
-      GrMMArgs g{};
+      GrMMArgs g = grargs(ctx);
       g.R = (p.nhi - 1) * p.L;
       g.p0 = p.Rtab;
       g.in = GrRowMap{p.L, 64, 0};
@@ -1266,7 +1285,7 @@ int verify_trunc_chunk(mpc_ctx* ctx, TruncPlan& p, const Small& s, void* tcs, co
         launch_gr_mulmat_batch(st, nB, p.Rtab, Lm * 64, p.Bm);
       }
       launch_word_transpose(st, nhm, Lm, E, p.b1, p.bT);
-      GrMMArgs g{};
+      GrMMArgs g = grargs(ctx);
       // Tm: rows sigma = j Lm + e_lo read r^(2 e_lo) and use matrix j; written at [e_lo][j]
       g.R = 64 * Lm;
       g.p0 = p.Rtab;
@@ -1278,7 +1297,7 @@ int verify_trunc_chunk(mpc_ctx* ctx, TruncPlan& p, const Small& s, void* tcs, co
       if (grmm(g, 64.0 * Lm * 4096)) return fail(ctx, MPC_ERR_CUDA, "verify_matmul: r^(2e) V table");
       for (int v = 0; v < 2; ++v) {
         // rows rho = e_lo nhm + e_hi (bits b_e), matrix Tm[e_lo], result at row e
-        GrMMArgs ga{};
+        GrMMArgs ga = grargs(ctx);
         ga.R = nhm * Lm;
         ga.p0 = p.bT;
         ga.in = GrRowMap{0, 1, 0};
@@ -1291,7 +1310,7 @@ int verify_trunc_chunk(mpc_ctx* ctx, TruncPlan& p, const Small& s, void* tcs, co
         if (grmm(ga, (double)nhm * Lm * 4096 * 8.0 / 36.0))
           return fail(ctx, MPC_ERR_CUDA, "verify_matmul: folded-vector product");
         // in place: rows e, matrix M(r^(2 Lm e_hi)) for e_hi = e / Lm
-        GrMMArgs gb{};
+        GrMMArgs gb = grargs(ctx);
         gb.R = E;
         gb.p0 = outs[v];
         gb.in = GrRowMap{0, 64, 0};
@@ -1304,7 +1323,7 @@ int verify_trunc_chunk(mpc_ctx* ctx, TruncPlan& p, const Small& s, void* tcs, co
       }
     }
     for (int v = p.Lm ? 2 : 0; v < 4; ++v) {
-      GrMMArgs g{};
+      GrMMArgs g = grargs(ctx);
       g.R = E;
       g.p0 = bits[v];
       g.in = GrRowMap{0, 1, 0};
@@ -1471,7 +1490,9 @@ int mpc_set_tuning(mpc_ctx* ctx, const mpc_tuning* tune) {
     if (tune->trunc_block < 0 || tune->trunc_chunk < 0 || tune->row_split < 0 ||
         tune->tc_combine_min < 0 || tune->gemm_split_min < 0 || tune->gram_split < 0 ||
         tune->fold_batch_max < 0 || tune->trunc_block % 128 || tune->row_split % 128 ||
-        tune->trunc_block > 65536 || tune->gram_split > 65535)
+        tune->trunc_block > 65536 || tune->gram_split > 65535 || tune->gr_producers < 0 ||
+        tune->gr_producers > 2 || (tune->gr_drain_warps != 0 && tune->gr_drain_warps != 8 &&
+                                   tune->gr_drain_warps != 16))
       return fail(ctx, MPC_ERR_ARG, "set_tuning: value out of range");
     if (tune->trunc_block) t.trunc_block = tune->trunc_block;
     if (tune->trunc_chunk) t.trunc_chunk = tune->trunc_chunk;
@@ -1480,6 +1501,8 @@ int mpc_set_tuning(mpc_ctx* ctx, const mpc_tuning* tune) {
     if (tune->gemm_split_min) t.gemm_split_min = tune->gemm_split_min;
     if (tune->gram_split) t.gram_split = tune->gram_split;
     if (tune->fold_batch_max) t.fold_batch_max = tune->fold_batch_max;
+    if (tune->gr_producers) t.gr_producers = tune->gr_producers;
+    if (tune->gr_drain_warps) t.gr_drain_warps = tune->gr_drain_warps;
   }
   ctx->tune = t;
   return MPC_OK;

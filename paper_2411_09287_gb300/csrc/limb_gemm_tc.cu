@@ -30,6 +30,8 @@
 #include <climits>
 #include <type_traits>
 
+#include <cstring>
+
 #include "kernels.h"
 #include "tcgen05.cuh"
 
@@ -545,16 +547,34 @@ __device__ __forceinline__ long long rowmap(const GrRowMap& m, long long rho) {
 
 // MODE 0: plain product, 1: fold (p0 - p1), 2: bit operand.  One instantiation per mode keeps
 // each kernel's code (and instruction-cache footprint) to the paths it runs.
-template <int MODE>
-__global__ void __launch_bounds__(GM_THREADS, 1)
-k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) {
+// TMA (MODE 0 and 1): one A stage; the other stage's 64 KB holds the raw A rows of the next K
+// chunk(s), loaded by TMA from the row-mapped input (tensor maps tm0 for p0, tm1 for p1: boxes of
+// 16 words x 128 rows, 128-byte swizzle, rows past the valid ones read as zero), so that the
+// producers split shared memory into digit planes without waiting on global loads, while the
+// loads of the next chunk overlap the MMAs of the current one.
+constexpr int GM_RAW_HALF = TC_BM * 128;        // 16 KB: 128 rows x 16 words
+constexpr int GM_RAW_ARR = 2 * GM_RAW_HALF;     // one operand's K chunk (32 words)
+
+template <int MODE, bool TMA, int ND>
+__global__ void __launch_bounds__((ND + GM_PROD + 1) * 32, 1)
+k_gr_matmul_tc(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1,
+               const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) {
+  static_assert(!TMA || MODE != 2, "bit operands take the register path");
+  constexpr int DC = 256 / ND;                              // columns per drain warp
+  static_assert(ND == 8 || ND == 16, "drain warps");
+  constexpr int NST = TMA ? 1 : NSTAGE;                     // A digit-plane stages
+  constexpr int NRAW = MODE == 1 ? 1 : 2;                   // raw stages (TMA)
+  constexpr int RAW_UNIT = (MODE == 1 ? 2 : 1) * GM_RAW_ARR;
+  static_assert(!TMA || NRAW * RAW_UNIT <= (NSTAGE - NST) * 8 * A_TILE, "raw stages");
   extern __shared__ unsigned char dsm[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
   unsigned char* Bsm = base;                       // [2 chunks][8 planes][64 rows][64 B]
-  unsigned char* Asm = base + 2 * GM_BCHUNK;       // [NSTAGE][8 planes][128 rows][64 B]
+  unsigned char* Asm = base + 2 * GM_BCHUNK;       // [NST][8 planes][128 rows][64 B]
+  unsigned char* Raw = Asm + NST * 8 * A_TILE;     // TMA: [NRAW][RAW_UNIT]
   unsigned char* Osm = Asm + NSTAGE * 8 * A_TILE;  // [drain warp][32 rows][48 B]
   __shared__ __align__(8) u64 full_bar[NSTAGE], empty_bar[NSTAGE];
+  __shared__ __align__(8) u64 raw_full[2], raw_empty[2];
   __shared__ __align__(8) u64 accf_bar[2], acce_bar[2], done_bar;
   __shared__ unsigned tmem_slot;
   __shared__ int abort_flag;
@@ -583,9 +603,13 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
       mbar_init(&full_bar[i], GM_PROD);
       mbar_init(&empty_bar[i], 1);
     }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&raw_full[i], 1);
+      mbar_init(&raw_empty[i], GM_PROD);
+    }
     for (int g = 0; g < 2; ++g) {
       mbar_init(&accf_bar[g], 1);
-      mbar_init(&acce_bar[g], GM_NDRAIN);
+      mbar_init(&acce_bar[g], ND);
     }
     mbar_init(&done_bar, 1);
     abort_flag = 0;
@@ -602,9 +626,9 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
     atomicOr(err, err_flag);
   };
 
-  if (warp >= GM_NDRAIN && warp < GM_NDRAIN + GM_PROD) {
+  if (warp >= ND && warp < ND + GM_PROD) {
     // ---- producers: B planes per matrix group, the A planes of every (tile, chunk) ----
-    const int pt = tid - GM_NDRAIN * 32;   // 0 .. 32 GM_PROD - 1
+    const int pt = tid - ND * 32;   // 0 .. 32 GM_PROD - 1
     const long long lda = a.in.s1;           // A row (bit word) stride inside a tile
     bool ok = true;
     long long cur_m = -1;
@@ -612,17 +636,17 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
     // at a tile's first chunk, B is rebuilt when the matrix group changes (after the previous
     // tile's MMAs) and the next tile's rows are prefetched into L2.
     auto begin_unit = [&](long long u) -> bool {
-      const int st = (int)(u % NSTAGE);
-      if (u >= NSTAGE &&
-          !__all_sync(0xffffffffu, mbar_wait(&empty_bar[st], (unsigned)(((u / NSTAGE) + 1) & 1), abort)))
+      const int st = (int)(u % NST);
+      if (u >= NST &&
+          !__all_sync(0xffffffffu, mbar_wait(&empty_bar[st], (unsigned)(((u / NST) + 1) & 1), abort)))
         return false;
       if (u & 1) return true;
       const long long tile = t0 + (u >> 1) * tstep;
       const long long rho0 = tile * TC_BM;
       const long long mi = a.mrows ? rho0 / a.mrows : 0;
       if (mi != cur_m) {
-        if (u > 0 && !__all_sync(0xffffffffu, mbar_wait(&empty_bar[(u - 1) % NSTAGE],
-                                                         (unsigned)(((u - 1) / NSTAGE) & 1), abort)))
+        if (u > 0 && !__all_sync(0xffffffffu, mbar_wait(&empty_bar[(u - 1) % NST],
+                                                         (unsigned)(((u - 1) / NST) & 1), abort)))
           return false;
         const u64* Mm = a.Mmat + mi * 4096;
         for (int it = pt; it < 64 * 8; it += GM_PROD * 32) {   // (row c of M^T, unit of 8 k)
@@ -636,7 +660,7 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
         // the next group's matrix into L2 (this CTA's tiles are contiguous, so it comes next)
         if (pt == 0 && a.mrows && (mi + 1) * a.mrows < R) prefetch_l2(Mm + 4096, 4096 * 8);
       }
-      if (pt == 0 && (u >> 1) + 1 < count && lda <= 128) {   // next tile's rows into L2
+      if (!TMA && pt == 0 && (u >> 1) + 1 < count && lda <= 128) {   // next tile's rows into L2
         const long long r0 = (tile + tstep) * TC_BM;
         long long nr = (R - r0 < TC_BM) ? R - r0 : TC_BM;
         if (a.qvalid && a.qvalid - r0 % a.in.q < nr) nr = a.qvalid - r0 % a.in.q;
@@ -663,9 +687,77 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
     auto end_unit = [&](long long u) {
       fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&full_bar[u % NSTAGE]);
+      if (lane == 0) mbar_arrive(&full_bar[u % NST]);
     };
-    if (a_bits) {
+    if constexpr (TMA) {
+      // one thread keeps NRAW units of raw rows in flight; a unit's buffer is refilled once every
+      // producer warp has split it
+      const bool tma_thr = pt == 0;
+      long long issued = 0, consumed = 0;
+      auto issue_raw = [&](long long u) {
+        const int rb = (int)(u % NRAW);
+        const long long rho0 = (t0 + (u >> 1) * tstep) * TC_BM;
+        const int kx = (int)(u & 1) * 32;
+        const int y = (int)(a.in.q ? rho0 % a.in.q : rho0);
+        const int z = (int)(a.in.q && a.in.s2 ? rho0 / a.in.q : 0);
+        unsigned char* dst = Raw + rb * RAW_UNIT;
+        mbar_expect_tx(&raw_full[rb], (unsigned)RAW_UNIT);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          tma_load_3d(dst + h * GM_RAW_HALF, &tm0, &raw_full[rb], kx + 16 * h, y, z);
+          if (MODE == 1)
+            tma_load_3d(dst + GM_RAW_ARR + h * GM_RAW_HALF, &tm1, &raw_full[rb], kx + 16 * h, y, z);
+        }
+      };
+      if (tma_thr)
+        for (; issued < nunits && issued < NRAW; ++issued) issue_raw(issued);
+      constexpr int NIT = (512 + GM_PROD * 32 - 1) / (GM_PROD * 32);   // items per thread
+      for (long long u = 0; u < nunits && ok; ++u) {
+        const int rb = (int)(u % NRAW);
+        if (!(ok = __all_sync(0xffffffffu,
+                              mbar_wait(&raw_full[rb], (unsigned)((u / NRAW) & 1), abort))))
+          break;
+        if (!(ok = begin_unit(u))) break;
+        const unsigned char* r0 = Raw + rb * RAW_UNIT;
+#pragma unroll
+        for (int q = 0; q < NIT; ++q) {
+          // item = (unit of 8 k, row): the 8 lanes of a shared-memory phase take 8 consecutive
+          // rows of one unit, conflict-free in the swizzled raw rows and in the digit planes
+          const int item = pt + q * GM_PROD * 32;
+          if (item < 512) {
+            const int row = item & (TC_BM - 1), u4 = item >> 7;
+            const unsigned char* src = r0 + (u4 >> 1) * GM_RAW_HALF + row * 128;
+            u64 v[8];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int c = (((u4 & 1) * 4 + j) ^ (row & 7)) * 16;   // 128-byte swizzle
+              const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(src + c);
+              v[2 * j] = x.x;
+              v[2 * j + 1] = x.y;
+              if (MODE == 1) {
+                const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(src + GM_RAW_ARR + c);
+                v[2 * j] -= w.x;
+                v[2 * j + 1] -= w.y;
+              }
+            }
+            split8_store(v, Asm, A_TILE, sw64_off(row, u4));
+          }
+        }
+        end_unit(u);
+        if (lane == 0) mbar_arrive(&raw_empty[rb]);
+        ++consumed;
+        bool iok = true;
+        if (tma_thr && issued < nunits) {
+          iok = mbar_wait(&raw_empty[rb], (unsigned)((u / NRAW) & 1), abort);
+          if (iok) issue_raw(issued++);
+        }
+        ok = __all_sync(0xffffffffu, iok);
+      }
+      // loads still in flight land before the CTA leaves
+      if (tma_thr)
+        for (long long u = consumed; u < issued; ++u)
+          mbar_wait_plain(&raw_full[u % NRAW], (unsigned)((u / NRAW) & 1));
+    } else if (a_bits) {
       constexpr int NIT = (512 + GM_PROD * 32 - 1) / (GM_PROD * 32);   // items per thread
       // One bit word per row serves both K chunks of its tile (bytes 0..3, then 4..7); the
       // words of tile t + 1 are in flight while tile t's two chunks are written.
@@ -767,14 +859,14 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
       else stream(std::integral_constant<int, 3>(), std::false_type());
     }
     if (!ok && lane == 0) fail();
-  } else if (warp == GM_NDRAIN + GM_PROD) {
+  } else if (warp == ND + GM_PROD) {
     // ---- MMA issuer ----
     if (lane == 0) {
       const u64 da0 = smem_desc(Asm, 64);
       const u64 db0 = smem_desc(Bsm, 64);
       for (long long u = 0; u < nunits; ++u) {
-        const int st = (int)(u % NSTAGE);
-        if (!mbar_wait(&full_bar[st], (unsigned)((u / NSTAGE) & 1), abort)) { fail(); break; }
+        const int st = (int)(u % NST);
+        if (!mbar_wait(&full_bar[st], (unsigned)((u / NST) & 1), abort)) { fail(); break; }
         tc_fence_after();
         const u64 ad = da0 + (u64)((st * 8 * A_TILE) >> 4);
         const u64 bd = db0 + (u64)(((int)(u & 1) * GM_BCHUNK) >> 4);
@@ -797,13 +889,13 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
       mma_commit(&done_bar);
       mbar_wait_plain(&done_bar, 0u);
     }
-  } else if (warp < GM_NDRAIN) {
-    // ---- drain warps: rows 32 (w % 4) + lane, columns GM_DC (w / 4) .. +GM_DC-1 ----
+  } else if (warp < ND) {
+    // ---- drain warps: rows 32 (w % 4) + lane, columns DC (w / 4) .. +DC-1 ----
     const int q4 = warp & 3, h = warp >> 2;
-    const unsigned tl = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)(h * GM_DC);
-    u64 acc[GM_DC];
+    const unsigned tl = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)(h * DC);
+    u64 acc[DC];
 #pragma unroll
-    for (int c = 0; c < GM_DC; ++c) acc[c] = 0;
+    for (int c = 0; c < DC; ++c) acc[c] = 0;
     bool ok = true;
     const long long nacc = nunits / 2;   // one accumulation per tile
     for (long long v = 0; v < nacc && ok; ++v) {
@@ -827,13 +919,13 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
       };
       // add0 words of the stored 16-byte chunks: a fold has the first EARLY columns in flight
       // during the drains; the rows come before the drains except for bit operands
-      constexpr int EARLY = MODE == 1 ? GM_DC / 2 : 0;
+      constexpr int EARLY = MODE == 1 ? DC / 2 : 0;
       if (MODE != 2) tile_rows_out();
-      ulonglong2 ad[GM_DC / 4][2];
+      ulonglong2 ad[DC / 4][2];
       auto load_add0 = [&](int c0) {
 #pragma unroll
         for (int pass = 0; pass < 2; ++pass) {
-          const long long col = h * GM_DC + c0 + 2 * (lane & 1);
+          const long long col = h * DC + c0 + 2 * (lane & 1);
           ad[c0 / 4][pass] = (a.add0 && obr[pass] >= 0)
                                  ? *reinterpret_cast<const ulonglong2*>(a.add0 + rg[pass] + col)
                                  : make_ulonglong2(0, 0);
@@ -847,7 +939,7 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
         if (!ok) break;
         tc_fence_after();
 #pragma unroll
-        for (int c16 = 0; c16 < GM_DC / 16; ++c16) {
+        for (int c16 = 0; c16 < DC / 16; ++c16) {
           if (a_bits) {
             if (g == 0) drain16_pairs<0>(tl, c16 * 16, acc + c16 * 16);
             else drain16_pairs<1>(tl, c16 * 16, acc + c16 * 16);
@@ -864,9 +956,9 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
         unsigned char* os = Osm + warp * GM_OSTAGE;
         if (MODE == 2) tile_rows_out();
 #pragma unroll
-        for (int c0 = EARLY; c0 < GM_DC; c0 += 4) load_add0(c0);
+        for (int c0 = EARLY; c0 < DC; c0 += 4) load_add0(c0);
 #pragma unroll
-        for (int c0 = 0; c0 < GM_DC; c0 += 4) {
+        for (int c0 = 0; c0 < DC; c0 += 4) {
 #pragma unroll
           for (int q = 0; q < 2; ++q)
             *reinterpret_cast<ulonglong2*>(os + lane * GM_OROW + q * 16) =
@@ -877,7 +969,7 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
             const int rr = pass * 16 + (lane >> 1), ch = lane & 1;
             ulonglong2 w = *reinterpret_cast<const ulonglong2*>(os + rr * GM_OROW + ch * 16);
             if (obr[pass] >= 0) {
-              const long long col = h * GM_DC + c0 + 2 * ch;
+              const long long col = h * DC + c0 + 2 * ch;
               w.x += ad[c0 / 4][pass].x;
               w.y += ad[c0 / 4][pass].y;
               *reinterpret_cast<ulonglong2*>(a.out + obr[pass] + col) = w;
@@ -886,7 +978,7 @@ k_gr_matmul_tc(const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) 
           __syncwarp();
         }
 #pragma unroll
-        for (int c = 0; c < GM_DC; ++c) acc[c] = 0;
+        for (int c = 0; c < DC; ++c) acc[c] = 0;
       }
     }
     if (!ok && lane == 0) fail();
@@ -1156,6 +1248,38 @@ int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nte
   return 0;
 }
 
+// Tensor map of the A rows of a GR-matrix product for the TMA producers: element (k, y, z) is
+// word k of row y of block z, at base + y s1 + z s2 words (rows y < the valid ones; the rest read
+// as zero).  Row maps with q = 0 are one block of R rows; with q > 0 a block of q rows (only the
+// first qvalid exist when qvalid > 0), blocks s2 words apart (one block when s2 = 0: the rows
+// repeat).  Boxes of 16 words x 128 rows, 128-byte swizzle.  false: not expressible (the caller
+// takes the register path).
+bool make_rows_map(CUtensorMap* map, const u64* base, const GrRowMap& in, long long R,
+                   long long qvalid) {
+  auto enc = encode_fn();
+  if (!enc || !base || in.s1 <= 0 || (in.s1 & 1) || (in.s2 & 1) || in.s2 < 0 ||
+      (reinterpret_cast<uintptr_t>(base) & 15))
+    return false;
+  cuuint64_t dims[3], strides[2];
+  dims[0] = 64;
+  if (in.q == 0) {
+    dims[1] = (cuuint64_t)R;
+    dims[2] = 1;
+  } else {
+    if (in.s2 && R % in.q) return false;   // a ragged last block would read past its rows
+    dims[1] = (cuuint64_t)(qvalid > 0 ? qvalid : in.q);
+    dims[2] = in.s2 ? (cuuint64_t)(R / in.q) : 1;
+  }
+  strides[0] = (cuuint64_t)in.s1 * 8;
+  strides[1] = in.s2 ? (cuuint64_t)in.s2 * 8 : dims[1] * strides[0];
+  if (dims[1] == 0 || dims[1] >= (1ull << 31) || dims[2] >= (1ull << 31)) return false;
+  cuuint32_t box[3] = {16, (cuuint32_t)TC_BM, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<u64*>(base), dims, strides, box,
+             es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int gr_matmul_tc_ex(cudaStream_t st, const GrMMArgs& args, unsigned* err, unsigned err_flag) {
   GrMMArgs a = args;
   if (a.R <= 0) return 0;
@@ -1183,13 +1307,31 @@ int gr_matmul_tc_ex(cudaStream_t st, const GrMMArgs& args, unsigned* err, unsign
   const long long ntiles = (a.R + TC_BM - 1) / TC_BM;
   const unsigned grid = (unsigned)(ntiles < nsm ? ntiles : nsm);
   const int mode = a.a_bits ? 2 : (a.p1 ? 1 : 0);
-  const void* fn = mode == 2 ? reinterpret_cast<const void*>(k_gr_matmul_tc<2>)
-                 : mode == 1 ? reinterpret_cast<const void*>(k_gr_matmul_tc<1>)
-                             : reinterpret_cast<const void*>(k_gr_matmul_tc<0>);
-  set_max_dynamic_smem(fn, (int)GM_SMEM);
-  if (mode == 2) k_gr_matmul_tc<2><<<grid, GM_THREADS, GM_SMEM, st>>>(a, err, err_flag);
-  else if (mode == 1) k_gr_matmul_tc<1><<<grid, GM_THREADS, GM_SMEM, st>>>(a, err, err_flag);
-  else k_gr_matmul_tc<0><<<grid, GM_THREADS, GM_SMEM, st>>>(a, err, err_flag);
+  CUtensorMap m0, m1;
+  std::memset(&m0, 0, sizeof(m0));
+  std::memset(&m1, 0, sizeof(m1));
+  const bool tma = a.tma && mode != 2 && make_rows_map(&m0, a.p0, a.in, a.R, a.qvalid) &&
+                   (mode == 0 || make_rows_map(&m1, a.p1, a.in, a.R, a.qvalid));
+  const int nd = a.drain_warps == 16 ? 16 : 8;
+  const size_t smem = (size_t)2 * GM_BCHUNK + (size_t)NSTAGE * 8 * A_TILE +
+                      (size_t)nd * GM_OSTAGE + 1024;
+  auto launch = [&](auto kern) {
+    set_max_dynamic_smem(reinterpret_cast<const void*>(kern), (int)smem);
+    kern<<<grid, (nd + GM_PROD + 1) * 32, smem, st>>>(m0, m1, a, err, err_flag);
+  };
+  if (nd == 16) {
+    if (mode == 2) launch(k_gr_matmul_tc<2, false, 16>);
+    else if (mode == 1 && tma) launch(k_gr_matmul_tc<1, true, 16>);
+    else if (mode == 1) launch(k_gr_matmul_tc<1, false, 16>);
+    else if (tma) launch(k_gr_matmul_tc<0, true, 16>);
+    else launch(k_gr_matmul_tc<0, false, 16>);
+  } else {
+    if (mode == 2) launch(k_gr_matmul_tc<2, false, 8>);
+    else if (mode == 1 && tma) launch(k_gr_matmul_tc<1, true, 8>);
+    else if (mode == 1) launch(k_gr_matmul_tc<1, false, 8>);
+    else if (tma) launch(k_gr_matmul_tc<0, true, 8>);
+    else launch(k_gr_matmul_tc<0, false, 8>);
+  }
   return 0;
 }
 
