@@ -120,7 +120,8 @@ typedef struct {
  *                  have at most this many elements; default 65536.
  *   gr_producers   how the GR-matrix products (folds, tables) load their A rows: 1 producer
  *                  warps' global loads into registers (two digit-plane stages), 2 TMA loads into
- *                  shared memory (one digit-plane stage); default 1.
+ *                  shared memory (one digit-plane stage), 3 TMA loads with the A digit planes in
+ *                  tensor memory (output in two halves of 32 columns); default 1.
  *   gr_drain_warps warps that drain the GR-matrix products' accumulators: 8 or 16; default 8. */
 typedef struct {
   int64_t trunc_block;

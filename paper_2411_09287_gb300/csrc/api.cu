@@ -316,7 +316,7 @@ void gram(mpc_ctx* ctx, u64* P, const u64* U0, const u64* U1, u64 su, long long 
 // GR-product arguments with this context's choice of producer and drain variant
 GrMMArgs grargs(const mpc_ctx* ctx) {
   GrMMArgs g{};
-  g.tma = ctx->tune.gr_producers == 2;
+  g.tma = ctx->tune.gr_producers >= 2 ? ctx->tune.gr_producers - 1 : 0;
   g.drain_warps = ctx->tune.gr_drain_warps;
   return g;
 }
@@ -1491,7 +1491,7 @@ int mpc_set_tuning(mpc_ctx* ctx, const mpc_tuning* tune) {
         tune->tc_combine_min < 0 || tune->gemm_split_min < 0 || tune->gram_split < 0 ||
         tune->fold_batch_max < 0 || tune->trunc_block % 128 || tune->row_split % 128 ||
         tune->trunc_block > 65536 || tune->gram_split > 65535 || tune->gr_producers < 0 ||
-        tune->gr_producers > 2 || (tune->gr_drain_warps != 0 && tune->gr_drain_warps != 8 &&
+        tune->gr_producers > 3 || (tune->gr_drain_warps != 0 && tune->gr_drain_warps != 8 &&
                                    tune->gr_drain_warps != 16))
       return fail(ctx, MPC_ERR_ARG, "set_tuning: value out of range");
     if (tune->trunc_block) t.trunc_block = tune->trunc_block;

@@ -95,7 +95,8 @@ struct GrMMArgs {
   long long out_lim;
   long long qvalid;   // > 0: only rows with rho % in.q < qvalid exist (padded segments)
   int add0_in;        // add0 row rho at add0 + in(rho) (the input map) instead of rho ld_add0
-  int tma;            // 1: the A rows of the plain and fold modes are loaded by TMA
+  int tma;            // 1: the A rows of the plain and fold modes are loaded by TMA; 2: and the
+                      // A operand sits in tensor memory
   int drain_warps;    // 8 (default) or 16 drain warps
 };
 int gr_matmul_tc_ex(cudaStream_t st, const GrMMArgs& a, unsigned* err, unsigned err_flag);

@@ -529,8 +529,6 @@ constexpr int GM_BCHUNK = 8 * B_TILE;                     // 32 KB: B planes of 
 // bytes apart so that both the row-wise writes and the 16-byte-chunk reads are conflict-free
 constexpr int GM_OROW = 48;
 constexpr int GM_OSTAGE = 32 * GM_OROW;
-constexpr size_t GM_SMEM = (size_t)2 * GM_BCHUNK + (size_t)NSTAGE * 8 * A_TILE +
-                           (size_t)GM_NDRAIN * GM_OSTAGE + 1024;
 
 // byte offset of 16-byte unit u (8 f16 along K) of row r inside a K-major 64-byte-swizzled tile
 __device__ __forceinline__ int sw64_off(int r, int u) {
@@ -989,6 +987,370 @@ k_gr_matmul_tc(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ 
   if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
+// ---- GR-matrix products with the A operand in tensor memory ------------------------------------
+// The same product as k_gr_matmul_tc (plain and fold modes), laid out so that an MMA reads only B
+// from shared memory.  With N = 64 fixed by the ring degree, an MMA whose A (4 KB) and B (2 KB)
+// both come from shared memory is bound by shared-memory reads (48 cycles for 128 x 64 x 16);
+// here A's eight digit planes (K = 64: 8 x 32 columns) sit in tensor memory next to the eight
+// accumulators of one output half (8 x 32 columns), and the output is computed in two halves of
+// 32 columns, each MMA 128 x 32 x 16 reading 1 KB of B.
+//   - TMA loads a tile's raw A rows (and p1's in a fold) into shared memory (boxes of 16 words x
+//     128 rows, 128-byte swizzle, rows past the valid ones as zero);
+//   - four producer warps, one per tensor-memory lane quarter, take one row per thread: the
+//     8-word units are split into digit planes and written with tcgen05.st into the A columns;
+//   - the MMA thread issues, per tile, the four units (half h, accumulator group G) into the
+//     group's columns once the drain of its previous use is done;
+//   - eight drain warps (rows 32 (w % 4) + lane, 16 columns each) drain a unit, add add0 and
+//     store the half through shared memory as in k_gr_matmul_tc.
+// A tile's A columns are rewritten only after all of its MMAs have completed.
+constexpr int TM_NDRAIN = 8, TM_NPROD = 4;
+constexpr int TM_THREADS = (TM_NDRAIN + TM_NPROD + 1) * 32;   // 416
+constexpr int TM_DC = 16;                                      // columns per drain warp and half
+constexpr int TM_RAW_ARR = TC_BM * 64 * 8;                     // 64 KB: one operand's tile
+constexpr unsigned TM_A_COL = 256;                             // A planes at columns 256 .. 511
+// Instruction descriptor, kind::f16: f32 accumulator, f16 A and B, K-major, M = 128, N = 32.
+constexpr unsigned IDESC_N32 = (1u << 4) | ((unsigned)(32 >> 3) << 17) | ((unsigned)(TC_BM >> 4) << 24);
+
+__host__ __device__ constexpr int tm_acc_col(int s) {   // group A {0,1,6,7} then B {2,3,4,5}
+  return s == 0 ? 0 : s == 1 ? 32 : s == 6 ? 64 : s == 7 ? 96 : 128 + (s - 2) * 32;
+}
+constexpr size_t tm_smem(int mode) {
+  return (size_t)2 * GM_BCHUNK + (size_t)2 * TM_RAW_ARR + (size_t)TM_NDRAIN * GM_OSTAGE + 1024;
+  (void)mode;
+}
+
+// D (+)= A B with A in tensor memory
+__device__ __forceinline__ void mma_f16_ta(unsigned d_tmem, unsigned a_tmem, u64 bdesc,
+                                           unsigned acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(IDESC_N32), "r"(acc));
+}
+__device__ __forceinline__ void tmem_st4(unsigned taddr, const unsigned v[4]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+}
+
+// 8 consecutive u64 values -> their 8 digit planes, 4 f16 pairs each (the split of split8_store)
+__device__ __forceinline__ void split8_regs(const u64 v[8], unsigned pk[8][4]) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const u64 a = v[2 * m] + 0x8080808080808080ull, b = v[2 * m + 1] + 0x8080808080808080ull;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const unsigned xa = (unsigned)(a >> (32 * h)), xb = (unsigned)(b >> (32 * h));
+      const unsigned a02 = __byte_perm(xa, 0x64u, 0x4240), a13 = __byte_perm(xa, 0x64u, 0x4341);
+      const unsigned b02 = __byte_perm(xb, 0x64u, 0x4240), b13 = __byte_perm(xb, 0x64u, 0x4341);
+      pk[4 * h + 0][m] = f16x2_minus_1152(__byte_perm(a02, b02, 0x5410));
+      pk[4 * h + 2][m] = f16x2_minus_1152(__byte_perm(a02, b02, 0x7632));
+      pk[4 * h + 1][m] = f16x2_minus_1152(__byte_perm(a13, b13, 0x5410));
+      pk[4 * h + 3][m] = f16x2_minus_1152(__byte_perm(a13, b13, 0x7632));
+    }
+  }
+}
+
+// The MMAs of accumulator group G for output half h: A from tensor memory (plane i at column
+// TM_A_COL + 32 i, k at + k / 2), B plane j of K chunk kc at bd0 + kc GM_BCHUNK + j B_TILE, its
+// rows 32 h .. 32 h + 31 (2 KB further per half), 16 of K per MMA.
+template <int G>
+__device__ __forceinline__ void tm_issue_group(unsigned tmem, u64 bd0, int h) {
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const int s = group_s(G, g);
+#pragma unroll
+    for (int kc = 0; kc < 2; ++kc)
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 16; ++kk)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          if (i <= s) {
+            const unsigned at = tmem + TM_A_COL + (unsigned)(32 * i + 16 * kc + 8 * kk);
+            const u64 bd = bd0 + (u64)((kc * GM_BCHUNK + (s - i) * B_TILE + h * 32 * 64) >> 4) +
+                           (u64)(kk * 2);
+            const bool first = kc == 0 && kk == 0 && i == 0;
+            mma_f16_ta(tmem + (unsigned)tm_acc_col(s), at, bd, first ? 0u : 1u);
+          }
+        }
+  }
+}
+
+// drain of group G for the 16 columns at tl (+ the group's accumulator columns): as drain16
+template <int G>
+__device__ __forceinline__ void tm_drain16(unsigned tl, u64* acc) {
+  constexpr int s0 = G == 0 ? 0 : 2, s1 = G == 0 ? 6 : 4;
+#pragma unroll
+  for (int h8 = 0; h8 < 16; h8 += 8) {
+    unsigned x0[8], x1[8], y0[8], y1[8];
+    tmem_ld8(tl + (unsigned)(tm_acc_col(s0) + h8), x0);
+    tmem_ld8(tl + (unsigned)(tm_acc_col(s0 + 1) + h8), x1);
+    tmem_ld8(tl + (unsigned)(tm_acc_col(s1) + h8), y0);
+    tmem_ld8(tl + (unsigned)(tm_acc_col(s1 + 1) + h8), y1);
+    tmem_ld_wait();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const unsigned ws =
+          (unsigned)f2i_biased(x0[j]) + (unsigned)f2i_biased(x1[j]) * 256u - PAIR_BIAS;
+      const unsigned whi = f32_int(y0[j]) + f32_int(y1[j]) * 256u;
+      acc[h8 + j] += (G == 0 ? (u64)(long long)(int)ws : (u64)(long long)(int)ws << 16) +
+                     ((u64)(G == 0 ? (whi << 16) : whi) << 32);
+    }
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(TM_THREADS, 1)
+k_gr_matmul_tm(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ CUtensorMap tm1,
+               const GrMMArgs a, unsigned* __restrict__ err, unsigned err_flag) {
+  static_assert(MODE == 0 || MODE == 1, "plain and fold modes");
+  constexpr int NRAW = MODE == 1 ? 1 : 2;                    // raw tile buffers
+  constexpr int RAW_TILE = (MODE == 1 ? 2 : 1) * TM_RAW_ARR;
+  extern __shared__ unsigned char dsm[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
+  unsigned char* Bsm = base;                               // [2 chunks][8 planes][64 rows][64 B]
+  unsigned char* Raw = base + 2 * GM_BCHUNK;               // [NRAW][RAW_TILE]
+  unsigned char* Osm = Raw + 2 * TM_RAW_ARR;               // [drain warp][32 rows][48 B]
+  __shared__ __align__(8) u64 raw_full[2], raw_empty[2], a_full, a_empty;
+  __shared__ __align__(8) u64 accf_bar[2], acce_bar[2], done_bar;
+  __shared__ unsigned tmem_slot;
+  __shared__ int abort_flag;
+  volatile int* abort = &abort_flag;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const long long R = a.R;
+  const long long ntiles = (R + TC_BM - 1) / TC_BM;
+  const long long G = gridDim.x;
+  const bool contig = a.mrows != 0;
+  const long long t0 = contig ? ntiles * blockIdx.x / G : blockIdx.x;
+  const long long tstep = contig ? 1 : G;
+  const long long count = contig ? ntiles * (blockIdx.x + 1) / G - t0
+                                 : (ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / G + 1 : 0);
+
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&raw_full[i], 1);
+      mbar_init(&raw_empty[i], TM_NPROD);
+    }
+    mbar_init(&a_full, TM_NPROD);
+    mbar_init(&a_empty, 1);
+    for (int g = 0; g < 2; ++g) {
+      mbar_init(&accf_bar[g], 1);
+      mbar_init(&acce_bar[g], TM_NDRAIN);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = tmem_slot;
+
+  auto fail = [&]() {
+    *abort = 1;
+    atomicOr(err, err_flag);
+  };
+
+  if (warp >= TM_NDRAIN && warp < TM_NDRAIN + TM_NPROD) {
+    // ---- producers: row = 32 (warp % 4) + lane of every tile; B planes per matrix group ----
+    const int pw = warp - TM_NDRAIN;                // 0 .. 3 = the warp's lane quarter
+    const int pt = pw * 32 + lane;                  // 0 .. 127
+    const int row = (warp & 3) * 32 + lane;         // tensor-memory lane of this thread
+    const unsigned trow = tmem + ((unsigned)((warp & 3) * 32) << 16);
+    const bool tma_thr = pt == 0;
+    long long issued = 0, consumed = 0, cur_m = -1;
+    bool ok = true;
+    auto issue_raw = [&](long long v) {
+      const int rb = (int)(v % NRAW);
+      const long long rho0 = (t0 + v * tstep) * TC_BM;
+      const int y = (int)(a.in.q ? rho0 % a.in.q : rho0);
+      const int z = (int)(a.in.q && a.in.s2 ? rho0 / a.in.q : 0);
+      unsigned char* dst = Raw + rb * RAW_TILE;
+      mbar_expect_tx(&raw_full[rb], (unsigned)RAW_TILE);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        tma_load_3d(dst + b * GM_RAW_HALF, &tm0, &raw_full[rb], 16 * b, y, z);
+        if (MODE == 1) tma_load_3d(dst + TM_RAW_ARR + b * GM_RAW_HALF, &tm1, &raw_full[rb], 16 * b, y, z);
+      }
+    };
+    if (tma_thr)
+      for (; issued < count && issued < NRAW; ++issued) issue_raw(issued);
+    for (long long v = 0; v < count && ok; ++v) {
+      const int rb = (int)(v % NRAW);
+      if (!(ok = __all_sync(0xffffffffu, mbar_wait(&raw_full[rb], (unsigned)((v / NRAW) & 1), abort))))
+        break;
+      // every MMA of tile v - 1 has read A (and B)
+      if (v > 0 && !(ok = __all_sync(0xffffffffu, mbar_wait(&a_empty, (unsigned)((v - 1) & 1), abort))))
+        break;
+      tc_fence_after();
+      const long long rho0 = (t0 + v * tstep) * TC_BM;
+      const long long mi = a.mrows ? rho0 / a.mrows : 0;
+      if (mi != cur_m) {   // B = M^T of this row group, split into its digit planes
+        const u64* Mm = a.Mmat + mi * 4096;
+        for (int it = pt; it < 64 * 8; it += TM_NPROD * 32) {   // (row c of M^T, unit of 8 k)
+          const int c = it >> 3, k8 = it & 7;
+          u64 w[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) w[q] = Mm[(k8 * 8 + q) * 64 + c];
+          split8_store(w, Bsm + (k8 >> 2) * GM_BCHUNK, B_TILE, sw64_off(c, k8 & 3));
+        }
+        fence_proxy_async_smem();
+        cur_m = mi;
+      }
+      const unsigned char* src = Raw + rb * RAW_TILE + row * 128;
+#pragma unroll 2
+      for (int u4 = 0; u4 < 8; ++u4) {   // words 8 u4 .. 8 u4 + 7 of the row
+        const unsigned char* s0 = src + (u4 >> 1) * GM_RAW_HALF;
+        u64 x[8];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = (((u4 & 1) * 4 + j) ^ (row & 7)) * 16;   // 128-byte swizzle
+          const ulonglong2 p = *reinterpret_cast<const ulonglong2*>(s0 + c);
+          x[2 * j] = p.x;
+          x[2 * j + 1] = p.y;
+          if (MODE == 1) {
+            const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(s0 + TM_RAW_ARR + c);
+            x[2 * j] -= w.x;
+            x[2 * j + 1] -= w.y;
+          }
+        }
+        unsigned pk[8][4];
+        split8_regs(x, pk);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) tmem_st4(trow + TM_A_COL + (unsigned)(32 * p + 4 * u4), pk[p]);
+      }
+      tmem_st_wait();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&a_full);
+        mbar_arrive(&raw_empty[rb]);
+      }
+      ++consumed;
+      bool iok = true;
+      if (tma_thr && issued < count) {
+        iok = mbar_wait(&raw_empty[rb], (unsigned)((v / NRAW) & 1), abort);
+        if (iok) issue_raw(issued++);
+      }
+      ok = __all_sync(0xffffffffu, iok);
+    }
+    if (tma_thr)
+      for (long long v = consumed; v < issued; ++v)
+        mbar_wait_plain(&raw_full[v % NRAW], (unsigned)((v / NRAW) & 1));
+    if (!ok && lane == 0) fail();
+  } else if (warp == TM_NDRAIN + TM_NPROD) {
+    // ---- MMA issuer: per tile, units (h, G) in the order (0,0) (0,1) (1,0) (1,1) ----
+    if (lane == 0) {
+      const u64 db0 = smem_desc(Bsm, 64);
+      bool ok = true;
+      for (long long v = 0; v < count && ok; ++v) {
+        if (!(ok = mbar_wait(&a_full, (unsigned)(v & 1), abort))) break;
+        tc_fence_after();
+        for (int h = 0; h < 2 && ok; ++h) {
+          const long long q = 2 * v + h;   // use of each accumulator group
+          for (int g = 0; g < 2; ++g) {
+            if (q > 0 && !(ok = mbar_wait(&acce_bar[g], (unsigned)((q - 1) & 1), abort))) break;
+            tc_fence_after();
+            if (g == 0) tm_issue_group<0>(tmem, db0, h);
+            else tm_issue_group<1>(tmem, db0, h);
+            mma_commit(&accf_bar[g]);
+          }
+        }
+        if (ok) mma_commit(&a_empty);
+      }
+      if (!ok) fail();
+      mma_commit(&done_bar);
+      mbar_wait_plain(&done_bar, 0u);
+    }
+  } else if (warp < TM_NDRAIN) {
+    // ---- drain warps: rows 32 (w % 4) + lane, columns 16 (w / 4) of each half ----
+    const int q4 = warp & 3, hw = warp >> 2;
+    const unsigned tl = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)(hw * TM_DC);
+    u64 acc[TM_DC];
+    bool ok = true;
+    for (long long v = 0; v < count && ok; ++v) {
+      // the rows this lane stores in the two passes (16 rows per pass, 2 lanes per row) as word
+      // offsets (-1: none) and their add0 offsets
+      long long obr[2], rg[2];
+      {
+        const long long r = (t0 + v * tstep) * TC_BM + q4 * 32 + lane;
+        const bool exists = r < R && (!a.qvalid || r % a.in.q < a.qvalid);
+        const long long ob = exists ? rowmap(a.om, r) : -1;
+        const bool live = ob >= 0 && ob < a.out_lim;
+        const long long ao =
+            !a.add0 ? 0 : (a.add0_in ? (exists ? rowmap(a.in, r) : 0) : r * a.ld_add0);
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+          const int rr = pass * 16 + (lane >> 1);
+          obr[pass] = __shfl_sync(0xffffffffu, live ? ob : -1, rr);
+          rg[pass] = __shfl_sync(0xffffffffu, ao, rr);
+        }
+      }
+      for (int h = 0; h < 2 && ok; ++h) {
+        const long long q = 2 * v + h;
+        const int col0 = h * 32 + hw * TM_DC;   // first output column of this warp's slice
+        ulonglong2 ad[TM_DC / 4][2];
+#pragma unroll
+        for (int c0 = 0; c0 < TM_DC; c0 += 4)
+#pragma unroll
+          for (int pass = 0; pass < 2; ++pass) {
+            const long long col = col0 + c0 + 2 * (lane & 1);
+            ad[c0 / 4][pass] = (a.add0 && obr[pass] >= 0)
+                                   ? *reinterpret_cast<const ulonglong2*>(a.add0 + rg[pass] + col)
+                                   : make_ulonglong2(0, 0);
+          }
+#pragma unroll
+        for (int c = 0; c < TM_DC; ++c) acc[c] = 0;
+#pragma unroll 1
+        for (int g = 0; g < 2; ++g) {
+          ok = __all_sync(0xffffffffu, mbar_wait(&accf_bar[g], (unsigned)(q & 1), abort));
+          if (!ok) break;
+          tc_fence_after();
+          if (g == 0) tm_drain16<0>(tl, acc);
+          else tm_drain16<1>(tl, acc);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acce_bar[g]);
+        }
+        if (!ok) break;
+        unsigned char* os = Osm + warp * GM_OSTAGE;
+#pragma unroll
+        for (int c0 = 0; c0 < TM_DC; c0 += 4) {
+#pragma unroll
+          for (int qq = 0; qq < 2; ++qq)
+            *reinterpret_cast<ulonglong2*>(os + lane * GM_OROW + qq * 16) =
+                make_ulonglong2(acc[c0 + 2 * qq], acc[c0 + 2 * qq + 1]);
+          __syncwarp();
+#pragma unroll
+          for (int pass = 0; pass < 2; ++pass) {
+            const int rr = pass * 16 + (lane >> 1), ch = lane & 1;
+            ulonglong2 w = *reinterpret_cast<const ulonglong2*>(os + rr * GM_OROW + ch * 16);
+            if (obr[pass] >= 0) {
+              const long long col = col0 + c0 + 2 * ch;
+              w.x += ad[c0 / 4][pass].x;
+              w.y += ad[c0 / 4][pass].y;
+              *reinterpret_cast<ulonglong2*>(a.out + obr[pass] + col) = w;
+            }
+          }
+          __syncwarp();
+        }
+      }
+    }
+    if (!ok && lane == 0) fail();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
 // ---- Gram sums of the dense Pi_Reduce rounds -------------------------------------------------
 // For vectors x, y of n = 2 Dh GR elements (rows of 64 words, element i at row i), the three P0
 // sums of a round in the truncation batch's form:
@@ -1312,6 +1674,16 @@ int gr_matmul_tc_ex(cudaStream_t st, const GrMMArgs& args, unsigned* err, unsign
   std::memset(&m1, 0, sizeof(m1));
   const bool tma = a.tma && mode != 2 && make_rows_map(&m0, a.p0, a.in, a.R, a.qvalid) &&
                    (mode == 0 || make_rows_map(&m1, a.p1, a.in, a.R, a.qvalid));
+  if (a.tma == 2 && mode != 2 && tma) {   // A operand in tensor memory
+    const size_t smem = tm_smem(mode);
+    auto launch_tm = [&](auto kern) {
+      set_max_dynamic_smem(reinterpret_cast<const void*>(kern), (int)smem);
+      kern<<<grid, TM_THREADS, smem, st>>>(m0, m1, a, err, err_flag);
+    };
+    if (mode == 1) launch_tm(k_gr_matmul_tm<1>);
+    else launch_tm(k_gr_matmul_tm<0>);
+    return 0;
+  }
   const int nd = a.drain_warps == 16 ? 16 : 8;
   const size_t smem = (size_t)2 * GM_BCHUNK + (size_t)NSTAGE * 8 * A_TILE +
                       (size_t)nd * GM_OSTAGE + 1024;

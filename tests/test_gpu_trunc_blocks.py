@@ -135,3 +135,24 @@ def test_tuning_round_trip_and_range(mpc):
     ctx.set_tuning(trunc_chunk=10)
     with pytest.raises(mpc.MpcError):
         ctx.ws_size(mpc.OP_VERIFY_MATMUL, 16, 16, 8, 13)
+
+
+# every variant of the GR-matrix product kernel (the autotuner's candidates) on a blocked, compact
+# and a chunked batch: register producers with 16 drain warps, TMA producers, A in tensor memory
+GR_VARIANTS = [dict(gr_producers=1, gr_drain_warps=16), dict(gr_producers=2),
+               dict(gr_producers=2, gr_drain_warps=16), dict(gr_producers=3)]
+
+
+@pytest.mark.parametrize("variant", range(len(GR_VARIANTS)))
+@pytest.mark.parametrize("name", ["compact-2blocks-tccombine", "chunks-ragged"])
+def test_gr_product_variants_match_oracle(mpc, name, variant):
+    M, N, K, tune = CASES[name]
+    saved = dict(tune)
+    try:
+        tune.update(GR_VARIANTS[variant])
+        ctx, rc, ok, zout, oout = _run(mpc, name, 1)
+    finally:
+        tune.clear()
+        tune.update(saved)
+    assert ok and rc == mpc.MPC_OK
+    assert np.array_equal(ctx.reconstruct(zout, M * N), oout)
