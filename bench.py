@@ -69,6 +69,8 @@ def parse(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default tuning instead of the autotuner's picks")
     return ap.parse_args(argv)
 
 
@@ -303,10 +305,7 @@ class Layer:
         self.zpre, self.zout, self.pq = ctx.shares(E), ctx.shares(E), ctx.empty(12 * E)
         self.out_dev = ctx.empty(E)
         # one workspace for every call of the step
-        self.wsb = max(ctx.ws_size(mpc.OP_SHARE, max(M * K, K * N)),
-                       ctx.ws_size(mpc.OP_MATMUL, M, N, K, t),
-                       ctx.ws_size(mpc.OP_VERIFY_MATMUL, M, N, K, t),
-                       ctx.ws_size(mpc.OP_RECONSTRUCT, E))
+        self.wsb = self.ws_bytes(ctx)
         self.ws = ctx.workspace(self.wsb)
         self.lib, self.h = ctx.lib, ctx.h
         self.call = 1
@@ -319,20 +318,51 @@ class Layer:
         if rc != self.mpc.MPC_OK:
             raise self.mpc.MpcError(rc, f"{what}: {self.lib.mpc_last_error(self.h).decode()}")
 
-    def step(self, x_ptr, w_ptr, on_host, out_ptr, out_host):
-        lib, h, P, M, N, K, t = self.lib, self.h, self.P, self.M, self.N, self.K, self.t
-        ws, wsb, c = self.ws, self.wsb, self.call
-        self.call += 8
+    def ws_bytes(self, ctx):
+        mpc, M, N, K, t = self.mpc, self.M, self.N, self.K, self.t
+        return max(ctx.ws_size(mpc.OP_SHARE, max(M * K, K * N)), ctx.ws_size(mpc.OP_MATMUL, M, N, K, t),
+                   ctx.ws_size(mpc.OP_VERIFY_MATMUL, M, N, K, t), ctx.ws_size(mpc.OP_RECONSTRUCT, self.E))
+
+    def retune(self, picks):
+        """The tuning the autotuner picked, on this layer's context (workspace re-sized)."""
+        self.ctx.set_tuning(**picks)
+        self.wsb = self.ws_bytes(self.ctx)
+        self.ws = None
+        self.ws = self.ctx.workspace(self.wsb)
+
+    def tune_step(self, ctx, trace):
+        """One step on another context (same seed, fixed call ids) with this layer's buffers and a
+        verification trace; returns the host copy of the trace (the autotuner's runs)."""
+        wsb = self.ws_bytes(ctx)
+        if self.ws.numel() * 8 < wsb + 256:
+            self.ws = None
+            self.ws = self.ctx.workspace(wsb)
+        return self.step(*self.dev_args, ctx=ctx, call=1, trace=trace, wsb=wsb)
+
+    def step(self, x_ptr, w_ptr, on_host, out_ptr, out_host, ctx=None, call=None, trace=None,
+             wsb=None):
+        lib, P, M, N, K, t = self.lib, self.P, self.M, self.N, self.K, self.t
+        h = ctx.h if ctx is not None else self.h
+        ws = self.ws
+        wsb = self.wsb if wsb is None else wsb
+        if call is None:
+            c = self.call
+            self.call += 8
+        else:
+            c = call
         self.check(lib.mpc_share_input(h, c, x_ptr, on_host, M * K, P(self.xs), P(ws), wsb), "share X")
         self.check(lib.mpc_share_input(h, c + 1, w_ptr, on_host, K * N, P(self.wsh), P(ws), wsb),
                    "share W")
         self.check(lib.mpc_matmul(h, c + 2, P(self.xs), P(self.wsh), M, N, K, t, P(self.zpre),
                                   P(self.zout), P(self.pq), P(ws), wsb), "matmul")
         self.check(lib.mpc_verify_matmul(h, c + 3, P(self.xs), P(self.wsh), P(self.zpre),
-                                         P(self.pq), M, N, K, t, c + 2, -1, -1, P(ws), wsb, None),
+                                         P(self.pq), M, N, K, t, c + 2, -1, -1, P(ws), wsb,
+                                         P(trace) if trace is not None else None),
                    "verify")
         self.check(lib.mpc_reconstruct(h, P(self.zout), self.E, out_ptr, out_host, P(ws), wsb),
                    "reconstruct")
+        if trace is not None:
+            return self.mpc.to_u64(trace).copy()
 
     def sampled_check(self, nsamples: int = 16):
         """On sampled outputs (a, b): the pre-truncation product reconstructs to (X W)_ab mod 2^64
@@ -385,6 +415,26 @@ class Layer:
         self.ctx.close()
 
 
+def run_autotune(mpc, torch, L, seed, device, path, M, N, K, t):
+    """The autotuner's picks for this layer (cached per device, shape and path): each candidate
+    runs one whole step on a fresh context of the same seed and call ids, and must reproduce the
+    default's verification transcript."""
+    from paper_2411_09287_gb300 import autotune as AT
+    key = AT._key(torch.cuda.get_device_name(device), M, N, K, t, path)
+    hit = AT.load_cached(key)
+    if hit is not None:
+        return {**hit, "cached": True}
+    trace = L.ctx.zeros(L.ctx.trace_words(mpc.OP_VERIFY_MATMUL, M, N, K, t))
+
+    def make_ctx(tuning):
+        return mpc.Context(seed, device=device, gemm_path=path, tuning=tuning or None,
+                           stream=L.ctx.stream)
+
+    rec = AT.autotune(make_ctx, lambda ctx: L.tune_step(ctx, trace), AT.search_space(M, N, K))
+    AT.store_cached(key, rec)
+    return {**rec, "cached": False}
+
+
 def parse_shape(args):
     if args.shape:
         M, N, K = (int(v) for v in args.shape.lower().split("x"))
@@ -419,6 +469,10 @@ def main():
     main_path = mpc.GEMM_U64 if args.gemm_path == "u64" else mpc.GEMM_LIMB_TC
     Xd, Wd = (torch.from_numpy(a.reshape(-1).view(np.int64)).to(f"cuda:{local}") for a in (X, W))
     L = Layer(mpc, torch, M, N, K, t, seed, local, main_path, X, W, Xd, Wd)
+    tuned = None
+    if not args.no_autotune:
+        tuned = run_autotune(mpc, torch, L, seed, local, main_path, M, N, K, t)
+        L.retune(tuned["picks"])
     for _ in range(args.warmup):
         L.step(*L.dev_args)
     torch.cuda.synchronize()
@@ -523,6 +577,8 @@ def main():
         "clocks": clk,
         "trunc_wraps_sampled": wraps,
     }
+    if tuned is not None:
+        line["autotune"] = tuned
     if other is not None:
         line["other_path"] = other
     if e2e:

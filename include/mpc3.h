@@ -423,6 +423,14 @@ int mpc_profile(mpc_ctx* ctx, int enable);
 int mpc_profile_read(mpc_ctx* ctx, double* ms /* MPC_NPROF */, uint64_t* count /* MPC_NPROF */,
                      double* work /* MPC_NPROF */);
 
+/* Test hook for failure detection (no counterpart in the paper): one thread waits, with the
+ * bounded-wait helper of the tensor-core kernels and a limit of `cycles` (1 .. 1e8) clock cycles,
+ * on an mbarrier that nothing arrives at.  The wait runs out, the kernel records the expiry in
+ * the context's status word and returns, and the call reports it as any expired wait is
+ * reported: MPC_ERR_TIMEOUT, with the context aborted (every later call returns
+ * MPC_ERR_ABORT).  The device stays usable.  For tests only. */
+int mpc_test_wait_expires(mpc_ctx* ctx, int64_t cycles);
+
 /* Number of kernel launches the library has issued in this process (all contexts). */
 uint64_t mpc_launch_count(void);
 

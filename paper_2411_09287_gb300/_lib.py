@@ -72,6 +72,7 @@ _SIGS = {
     "mpc_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), c_u64p,
                                    C.POINTER(C.c_double)]),
     "mpc_launch_count": (C.c_uint64, []),
+    "mpc_test_wait_expires": (C.c_int, [C.c_void_p, C.c_int64]),
     "mpc_share_fixed": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_int, C.c_int64,
                                   C.c_int, C.c_void_p, C.c_void_p, C.c_size_t]),
     "mpc_reconstruct_fixed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,

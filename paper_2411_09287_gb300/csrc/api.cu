@@ -341,7 +341,7 @@ int gr_matmul(mpc_ctx* ctx, long long R, const u64* p0, const u64* p1, u64 s1, l
     g.ld_add0 = ld_add0 ? ld_add0 : ldc;
     g.out = out;
     g.om = GrRowMap{0, ldc, 0};
-    if (gr_matmul_tc_ex(ctx->st, g, ctx->status, ST_TIMEOUT) == 0)
+    if (gr_matmul_tc_ex(ctx->st, g, ctx->status, ST_TIMEOUT) == 0) return MPC_OK;
     g_launches -= 1;   // misaligned view: fall through to the CUDA-core GEMM
   }
   GemmTerm T;
@@ -2215,6 +2215,17 @@ int mpc_verify_trunc(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* pq, int64
   return finish_verify(ctx, (trunc_call_id << 1) | 1);
 }
 
+
+int mpc_test_wait_expires(mpc_ctx* ctx, int64_t cycles) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (cycles < 1 || cycles > 100000000) return fail(ctx, MPC_ERR_ARG, "test_wait_expires: cycles");
+  launch_wait_expires(ctx->st, cycles, ctx->status, ST_TIMEOUT);
+  g_launches += 1;
+  if ((rc = cuda_check(ctx, "test_wait_expires"))) return rc;
+  u32 stv = 0;
+  return read_status(ctx, &stv);   // MPC_ERR_TIMEOUT, and the context is aborted
+}
 }  // extern "C"
 
 // ---- accessors for other translation units of the library (not part of the C-ABI) ----------

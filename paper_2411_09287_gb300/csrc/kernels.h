@@ -288,4 +288,7 @@ void launch_trunc_online(cudaStream_t st, const u64* xs, long long n, const u64*
                          const u64* d2_at_p1, const u64* d1_at_p2, const u64* d2, int t,
                          u64* out);
 
+// test hook: one thread's bounded wait (limit `cycles`) on an mbarrier nothing arrives at
+void launch_wait_expires(cudaStream_t st, long long cycles, unsigned* err, unsigned err_flag);
+
 }  // namespace mpc3

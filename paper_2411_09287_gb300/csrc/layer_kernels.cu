@@ -125,3 +125,30 @@ void launch_trunc_online(cudaStream_t st, const u64* xs, long long n, const u64*
 }
 
 }  // namespace mpc3
+
+// ---- test hook: a bounded wait that runs out -------------------------------------------------
+#include "tcgen05.cuh"
+
+namespace mpc3 {
+namespace {
+
+// One thread waits, with the tensor-core kernels' bounded-wait helper and a limit of `cycles`,
+// on an mbarrier that nothing arrives at; on expiry it records err_flag in the status word and
+// returns, exactly as a tensor-core kernel's waiting role does.
+__global__ void k_wait_expires(long long cycles, unsigned* __restrict__ err, unsigned err_flag) {
+  __shared__ __align__(8) u64 bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x != 0) return;
+  tc::mbar_init(&bar, 1);
+  abort_flag = 0;
+  tc::mbar_init_fence();
+  if (!tc::mbar_wait(&bar, 0u, &abort_flag, cycles)) atomicOr(err, err_flag);
+}
+
+}  // namespace
+
+void launch_wait_expires(cudaStream_t st, long long cycles, unsigned* err, unsigned err_flag) {
+  k_wait_expires<<<1, 32, 0, st>>>(cycles, err, err_flag);
+}
+
+}  // namespace mpc3

@@ -49,11 +49,12 @@ __device__ __forceinline__ bool mbar_try_wait(u64* bar, unsigned parity) {
   return ok != 0;
 }
 // Bounded wait for the completion of the phase with the given parity; gives up (false) after
-// WAIT_CYCLES or once *abort is set by another warp of the CTA.
-__device__ __forceinline__ bool mbar_wait(u64* bar, unsigned parity, volatile int* abort) {
+// `limit` cycles (WAIT_CYCLES by default) or once *abort is set by another warp of the CTA.
+__device__ __forceinline__ bool mbar_wait(u64* bar, unsigned parity, volatile int* abort,
+                                          long long limit = WAIT_CYCLES) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (*abort || clock64() - t0 > WAIT_CYCLES) return false;
+    if (*abort || clock64() - t0 > limit) return false;
   }
   return true;
 }
