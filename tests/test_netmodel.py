@@ -53,3 +53,14 @@ def test_time_at_the_best_R_is_the_minimum():
     R = NM.best_R(1 << 18, net)
     t = [NM.verify_time(1 << 18, r, net) for r in range(25)]
     assert t[R] == min(t)
+
+
+def test_best_by_total_adds_measured_computation():
+    """With computation that grows with R, the optimum moves to fewer rounds than the
+    communication-only optimum; with none it is the communication-only optimum."""
+    from paper_2411_09287_gb300 import netrun as NR
+    D, net = 1 << 18, NM.NETWORKS["MAN"]
+    free = {R: 0.0 for R in range(17)}
+    assert NR.best_by_total(free, D, net)[0] == NM.best_R(D, net, 16)
+    costly = {R: 0.004 * R for R in range(17)}
+    assert NR.best_by_total(costly, D, net)[0] < NM.best_R(D, net, 16)
