@@ -9,7 +9,8 @@ three parties' views.  Every random value comes from the pairwise PRG streams of
 * ``inner_rows``    Pi_Inner offline + online for a batch of inner products (Fig. DPP).
 * ``matmul``        Pi_Inner for every output of X.W (Sec. 4.1: a matrix product is m inner
                     products), optionally with Pi_Trunc^t (Fig. trunc).
-* ``trunc_pair``    Pi_Trunc^t preprocessing (Fig. trunc).
+* ``trunc_pair``    Pi_Trunc^t preprocessing (Fig. trunc); its bits keyed by the call or, for
+                    packed serving batches, by output row (``trunc_bit_words``, reading A12).
 * ``trunc``         Pi_Trunc^t of an existing sharing (Fig. trunc, reading T5).
 * ``conv2d``        a convolution as one Pi_Inner per output (Sec. 4.1), on the im2col rows of the
                     input written out from the definition of a convolution.
@@ -254,15 +255,26 @@ def bit_sharings(sess: Session, b1, b2):
     return sb1, sb2
 
 
-def trunc_pair(sess: Session, call_id: int, E: int, t: int) -> TruncPair:
+def trunc_bit_words(sess: Session, comp: int, call_id: int, E: int, row_keys=None, N: int = None):
+    """The E words of a truncation-bit stream: word e of the call's stream, or, keyed by rows
+    (reading A12: randomness keyed by request, layer and row, never by batch slot), word e mod N
+    of the stream of object row_keys[e // N]."""
+    if row_keys is None:
+        return sess.prf(comp, P_TRUNC_BITS, obj_id(call_id), E)
+    rows = [sess.prf(comp, P_TRUNC_BITS, int(k), N) for k in row_keys]
+    return np.concatenate(rows)[:E] if rows else np.zeros(0, dtype=U64)
+
+
+def trunc_pair(sess: Session, call_id: int, E: int, t: int, row_keys=None, N: int = None
+               ) -> TruncPair:
     """Fig. trunc, preprocessing: P0,P1 pick bits b1 (eta01); P0,P2 pick bits b2 (eta02);
     <r_x> and <r_z> are obtained with two Pi_Inner of dimension l over the bit sharings; then the
-    additive shares [r_x], [r_z] are formed as in reading T3."""
+    additive shares [r_x], [r_z] are formed as in reading T3.  row_keys: see ``trunc_bit_words``."""
     mask = sess.mask
     ell = sess.gr.ell
     obj = obj_id(call_id)
-    b1 = sess.prf(C_TB1, P_TRUNC_BITS, obj, E)
-    b2 = sess.prf(C_TB2, P_TRUNC_BITS, obj, E)
+    b1 = trunc_bit_words(sess, C_TB1, call_id, E, row_keys, N)
+    b2 = trunc_bit_words(sess, C_TB2, call_id, E, row_keys, N)
     c, cp = trunc_coeffs(t, ell)
     sb1, sb2 = bit_sharings(sess, b1, b2)
     xs_p = sb1.map(lambda a: (a * c[None, :]) & mask)
@@ -298,8 +310,8 @@ class MatmulResult:
     tp: TruncPair | None
 
 
-def matmul(sess: Session, X: Shared, W: Shared, call_id: int, trunc_bits: int | None = None
-           ) -> MatmulResult:
+def matmul(sess: Session, X: Shared, W: Shared, call_id: int, trunc_bits: int | None = None,
+           row_keys=None) -> MatmulResult:
     """Sec. 4.1 views the M x N product as M*N inner products of dimension K, each by Fig. DPP:
     offline P0 computes Gamma = R_X R_W + R_Z and shares it; online P1 computes
     [m_Z]_1 = -M_X [R_W]_1 - [R_X]_1 M_W + [Gamma]_1, P2 computes
@@ -318,7 +330,7 @@ def matmul(sess: Session, X: Shared, W: Shared, call_id: int, trunc_bits: int | 
         r2 = sess.prf(C_R2, P_INNER, obj, E).reshape(M, N)
         m1_p0, m2_p0, m1_p1, m2_p2 = r1, r2, r1, r2
     else:
-        tp = trunc_pair(sess, call_id, E, trunc_bits)
+        tp = trunc_pair(sess, call_id, E, trunc_bits, row_keys, N)
         m1_p0, m2_p0 = tp.rx1_p0.reshape(M, N), tp.rx2_p0.reshape(M, N)
         m1_p1, m2_p2 = tp.rx1_p1.reshape(M, N), tp.rx2_p2.reshape(M, N)
     # offline, P0

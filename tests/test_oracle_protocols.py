@@ -283,3 +283,51 @@ def test_conv2d_opens_the_convolution(geom):
     Ho, Wo = conv_out_size(H, W, kh, kw, stride, pad)
     got = reconstruct(s, res.z_pre).reshape(B, Ho, Wo, O).transpose(0, 3, 1, 2)
     assert np.array_equal(got, _conv_by_definition(x, w, stride, pad))
+
+
+# ---------------------------------------------------------------------------------------------
+# truncation bits keyed by output row (reading A12): a row opens to the same truncated value in
+# any batch
+# ---------------------------------------------------------------------------------------------
+def _row_key(req: int, layer: int, row: int) -> int:
+    from oracle.shares import obj_id
+    return obj_id(req * 64 + layer, (row >> 16) & 15, row & 0xFFFF)
+
+
+def test_keyed_trunc_bits_are_the_rows_streams():
+    from oracle.protocols import trunc_bit_words
+    from oracle.shares import C_TB1, P_TRUNC_BITS
+    s = Session(SEED)
+    keys = [_row_key(7, 1, i) for i in range(3)]
+    w = trunc_bit_words(s, C_TB1, 99, 3 * 5, keys, 5)
+    for i, k in enumerate(keys):
+        assert np.array_equal(w[5 * i:5 * i + 5], s.prf(C_TB1, P_TRUNC_BITS, k, 5))
+
+
+def test_a_request_opens_the_same_truncated_rows_alone_and_packed():
+    """Request A (2 rows) alone and packed behind request B (3 rows): with row-keyed truncation
+    bits, A's opened truncated outputs are bit-identical; with call-keyed bits they differ in
+    some carry."""
+    rng = np.random.default_rng(31)
+    K, N = 40, 6
+    W = encode_fixed(rng.uniform(-1, 1, (K, N)), 13)
+    XA = encode_fixed(rng.uniform(-1, 1, (2, K)), 13)
+    XB = encode_fixed(rng.uniform(-1, 1, (3, K)), 13)
+    keysA = [_row_key(1, 0, i) for i in range(2)]
+    keysB = [_row_key(2, 0, i) for i in range(3)]
+
+    def run(X, keys, call):
+        s = Session(SEED)
+        SX, SW = share_input(s, X, call), share_input(s, W, call + 1)
+        res = matmul(s, SX, SW, call + 2, trunc_bits=13, row_keys=keys)
+        return reconstruct(s, res.out)
+
+    alone = run(XA, keysA, 10)
+    packed = run(np.concatenate([XB, XA]), keysB + keysA, 20)
+    assert np.array_equal(packed[3:], alone)
+    unkeyed_alone = run(XA, None, 10)
+    unkeyed_packed = run(np.concatenate([XB, XA]), None, 20)
+    exact = (XA.astype(np.int64) @ W.astype(np.int64)) >> 13
+    for out in (alone, unkeyed_alone, unkeyed_packed[3:]):
+        assert np.all(np.abs(out.astype(np.int64) - exact) <= 1)
+    assert not np.array_equal(unkeyed_packed[3:], unkeyed_alone)
