@@ -200,6 +200,20 @@ int mpc_matmul(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_
                int64_t M, int64_t N, int64_t K, int trunc_bits, uint64_t* zpre, uint64_t* zout,
                uint64_t* pq, void* workspace, size_t workspace_bytes);
 
+/* mpc_matmul with the truncation pairs' random bits keyed by output row: the bits b1, b2 of output
+ * (a, b) are word b of the bit streams of object row_keys[a] (instead of word a N + b of the
+ * call's streams).  Every other random value stays the call's.  A truncated output's opened value
+ * depends on the other party-random values only through its pair mask r_x = b1 xor b2 (the carry
+ * of Fig. trunc), so rows keyed by (request, layer, row of the request) open to the same values
+ * whichever batch they are packed into; serving uses this to return a request the same logits
+ * alone and packed.  row_keys: M device words (borrowed), object ids as call_id << 20 | batch << 16
+ * | sub with call_id < 2^44; NULL is mpc_matmul.  Verify with mpc_verify_matmul_keyed and the
+ * same keys. */
+int mpc_matmul_keyed(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_t* ws_,
+                     int64_t M, int64_t N, int64_t K, int trunc_bits, const uint64_t* row_keys,
+                     uint64_t* zpre, uint64_t* zout, uint64_t* pq, void* workspace,
+                     size_t workspace_bytes);
+
 /* Pi_MultVerify^R (Fig. PPEV) of the n triples (x_i, y_i, z_i) produced by
  * mpc_mult(call_id = mult_call_id): Pi_Tran with a revealed challenge r, R rounds of Pi_Reduce,
  * then Pi_InnerVerify.  R < 0 selects max(0, ceil(log2 n) - 6).  Returns MPC_OK if the check
@@ -245,6 +259,15 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
                       const uint64_t* zpre, const uint64_t* pq, int64_t M, int64_t N, int64_t K,
                       int trunc_bits, uint64_t matmul_call_id, int R_main, int R_trunc,
                       void* workspace, size_t workspace_bytes, uint64_t* trace);
+
+/* mpc_verify_matmul of a layer made by mpc_matmul_keyed: the truncation batch regenerates the
+ * pairs' bits from the same row keys (M device words; NULL is mpc_verify_matmul). */
+int mpc_verify_matmul_keyed(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs,
+                            const uint64_t* ws_, const uint64_t* zpre, const uint64_t* pq,
+                            int64_t M, int64_t N, int64_t K, int trunc_bits,
+                            const uint64_t* row_keys, uint64_t matmul_call_id, int R_main,
+                            int R_trunc, void* workspace, size_t workspace_bytes,
+                            uint64_t* trace);
 
 /* Words of the optional verification trace of op = MPC_OP_VERIFY_MULT, MPC_OP_VERIFY_MULT_CALLS,
  * MPC_OP_VERIFY_MATMUL or MPC_OP_VERIFY_TRUNC, arguments as mpc_workspace_size; -1 for invalid
@@ -304,11 +327,13 @@ int mpc_reconstruct_fixed(mpc_ctx* ctx, const uint64_t* xs, int64_t n, int frac_
  *   the padding); keep it for the verification, which is mpc_verify_matmul(xs = cols, ws_, zpre,
  *   pq, B Ho Wo, C_out, C kh kw, trunc_bits, call_id, ...);
  *   zpre, zout, pq as mpc_matmul with M = B Ho Wo, N = C_out, K = C kh kw: output row (b, i, j),
- *   column c_out (NHWC order).
+ *   column c_out (NHWC order);
+ *   row_keys: NULL, or M device words keying the truncation bits by output row as
+ *   mpc_matmul_keyed does (verify with mpc_verify_matmul_keyed and the same keys).
  * Workspace: MPC_OP_MATMUL with (M, N, K) above.  MPC_ERR_SHAPE for a bad geometry. */
 int mpc_conv2d(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_t* ws_,
-               const int32_t geom[8], int64_t C_out, int trunc_bits, uint64_t* cols,
-               uint64_t* zpre, uint64_t* zout, uint64_t* pq, void* workspace,
+               const int32_t geom[8], int64_t C_out, int trunc_bits, const uint64_t* row_keys,
+               uint64_t* cols, uint64_t* zpre, uint64_t* zout, uint64_t* pq, void* workspace,
                size_t workspace_bytes);
 
 /* Pi_Trunc^t (Fig. trunc) of a sharing <x> of n elements: <z> with z = x >>_arith t, up to the

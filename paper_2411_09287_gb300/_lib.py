@@ -73,13 +73,20 @@ _SIGS = {
                                    C.POINTER(C.c_double)]),
     "mpc_launch_count": (C.c_uint64, []),
     "mpc_test_wait_expires": (C.c_int, [C.c_void_p, C.c_int64]),
+    "mpc_matmul_keyed": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_int64,
+                                   C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t]),
+    "mpc_verify_matmul_keyed": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64,
+                                          C.c_int, C.c_void_p, C.c_uint64, C.c_int, C.c_int,
+                                          C.c_void_p, C.c_size_t, C.c_void_p]),
     "mpc_share_fixed": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_int, C.c_int64,
                                   C.c_int, C.c_void_p, C.c_void_p, C.c_size_t]),
     "mpc_reconstruct_fixed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
                                         C.c_int, C.c_void_p, C.c_size_t]),
     "mpc_conv2d": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p,
                              C.POINTER(C.c_int32), C.c_int64, C.c_int, C.c_void_p, C.c_void_p,
-                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t]),
+                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t]),
     "mpc_trunc": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
                             C.c_void_p, C.c_void_p, C.c_size_t]),
     "mpc_verify_trunc": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int64, C.c_int,

@@ -70,6 +70,7 @@ inline void counted(int k, F f, A... a) {
 #define launch_gr_quad_combine(...) counted(1, mpc3::launch_gr_quad_combine, __VA_ARGS__)
 #define launch_mode_consts(...) counted(1, mpc3::launch_mode_consts, __VA_ARGS__)
 #define launch_prf_words(...) counted(1, mpc3::launch_prf_words, __VA_ARGS__)
+#define launch_prf_words_keyed(...) counted(1, mpc3::launch_prf_words_keyed, __VA_ARGS__)
 #define launch_trunc_limb_table(...) counted(1, mpc3::launch_trunc_limb_table, __VA_ARGS__)
 #define launch_trunc_bit_transpose(...) counted(1, mpc3::launch_trunc_bit_transpose, __VA_ARGS__)
 #define launch_fold_reduce_strided(...) counted(1, mpc3::launch_fold_reduce_strided, __VA_ARGS__)
@@ -1132,7 +1133,7 @@ bool plan_vtrunc(Arena& a, long long n, int R, bool tc, const mpc_tuning& tu, VT
 // streams of batch `batch`.  pq_all: the layer's 12 rows of <p>, <q> (stride E_all).
 int verify_trunc_chunk(mpc_ctx* ctx, TruncPlan& p, const Small& s, void* tcs, const u64* pq_all,
                        long long E_all, long long e0, int trunc_bits, u64 verify_id, u32 batch,
-                       u64 matmul_call_id, u64* tr) {
+                       u64 matmul_call_id, u64* tr, const u64* row_keys, long long N) {
   cudaStream_t st = ctx->st;
   Phase* phase = new Phase(ctx, MPC_PROF_TRUNC_SETUP);
   const u64 mobj = make_obj(matmul_call_id, 0, 0);
@@ -1150,8 +1151,13 @@ int verify_trunc_chunk(mpc_ctx* ctx, TruncPlan& p, const Small& s, void* tcs, co
     CK(cudaMemsetAsync(p.b1 + E, 0, (size_t)(p.Epad - E) * 8, st));
     CK(cudaMemsetAsync(p.b2 + E, 0, (size_t)(p.Epad - E) * 8, st));
   }
-  launch_prf_words(st, E, ctx->k01, make_tag(P_TRUNC_BITS, C_TB1), mobj, p.b1, e0);
-  launch_prf_words(st, E, ctx->k02, make_tag(P_TRUNC_BITS, C_TB2), mobj, p.b2, e0);
+  if (row_keys) {
+    launch_prf_words_keyed(st, E, ctx->k01, make_tag(P_TRUNC_BITS, C_TB1), row_keys, N, p.b1, e0);
+    launch_prf_words_keyed(st, E, ctx->k02, make_tag(P_TRUNC_BITS, C_TB2), row_keys, N, p.b2, e0);
+  } else {
+    launch_prf_words(st, E, ctx->k01, make_tag(P_TRUNC_BITS, C_TB1), mobj, p.b1, e0);
+    launch_prf_words(st, E, ctx->k02, make_tag(P_TRUNC_BITS, C_TB2), mobj, p.b2, e0);
+  }
   launch_gr_mul1(st, s.r, s.r, s.aux + 64);                          // r^2
   // r^(2e) for e < Epad: r^(2 e_lo) for e_lo < L by repeated multiplication, then every further
   // block of L rows is that block times the constant r^(2 L e_hi) (a 64 x 64 matrix product)
@@ -1378,11 +1384,12 @@ TruncCallPlan plan_trunc_call(Arena& a, long long n) {
 
 // Every chunk of a truncation batch (batches 1, 2, ... of verify_id); trace: chunk after chunk.
 int verify_trunc_batch(mpc_ctx* ctx, TruncBatch& b, const Small& s, void* tcs, const u64* pq,
-                       int trunc_bits, u64 verify_id, u64 call_id, u64* tr) {
+                       int trunc_bits, u64 verify_id, u64 call_id, u64* tr, const u64* row_keys,
+                       long long N) {
   for (long long i = 0; i < b.nchunks; ++i) {
     TruncPlan& tp = b.tp[i == b.nchunks - 1 ? 1 : 0];
     const int rc = verify_trunc_chunk(ctx, tp, s, tcs, pq, b.E, i * b.C, trunc_bits, verify_id,
-                                      (u32)(1 + i), call_id, tr);
+                                      (u32)(1 + i), call_id, tr, row_keys, N);
     if (rc) return rc;
     if (tr) tr += (long long)(tp.R1 + 1) * TRACE_ROUND;
   }
@@ -1710,6 +1717,14 @@ int mpc_mult(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_t*
 int mpc_matmul(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_t* ws_,
                int64_t M, int64_t N, int64_t K, int trunc_bits, uint64_t* zpre, uint64_t* zout,
                uint64_t* pq, void* workspace, size_t workspace_bytes) {
+  return mpc_matmul_keyed(ctx, call_id, xs, ws_, M, N, K, trunc_bits, nullptr, zpre, zout, pq,
+                          workspace, workspace_bytes);
+}
+
+int mpc_matmul_keyed(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_t* ws_,
+                     int64_t M, int64_t N, int64_t K, int trunc_bits, const uint64_t* row_keys,
+                     uint64_t* zpre, uint64_t* zout, uint64_t* pq, void* workspace,
+                     size_t workspace_bytes) {
   int rc = guard(ctx);
   if (rc) return rc;
   if (M <= 0 || N <= 0 || K <= 0) return fail(ctx, MPC_ERR_SHAPE, "matmul: bad shape");
@@ -1745,7 +1760,7 @@ int mpc_matmul(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_
   if (trunc) {   // Pi_Trunc preprocessing first: it assigns the product wire's mask
     Phase phase(ctx, MPC_PROF_TRUNC_PAIRS);
     launch_trunc_p0(st, E, ctx->k01, ctx->k02, obj, trunc_bits, zpre, zout, pq, p.gp2, p.gq2,
-                    p.mp1, p.mq1);
+                    p.mp1, p.mq1, (const u64*)row_keys, N);
     const int ph = MPC_PHASE_OFFLINE, pr = MPC_PROTO_TRUNC;
     if ((rc = deliver(ctx, ph, pr, p.gp2, p.gp2i, E, MPC_SITE_GAMMA2))) return rc;
     if ((rc = deliver(ctx, ph, pr, p.mp1, p.mpi2, E, MPC_SITE_MZ1))) return rc;
@@ -1754,7 +1769,7 @@ int mpc_matmul(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_
     if ((rc = deliver(ctx, ph, pr, p.mq1, p.mqi2, E, MPC_SITE_MZ1))) return rc;
     if ((rc = deliver(ctx, ph, pr, p.gq2i, p.mqi1, E, MPC_SITE_MZ2))) return rc;
     launch_trunc_finish(st, E, ctx->k01, ctx->k02, obj, trunc_bits, p.mpi1, p.mqi1, p.mpi2,
-                        p.mqi2, p.gp2i, p.gq2i, p.mp1, p.mq1, zpre, zout, pq);
+                        p.mqi2, p.gp2i, p.gq2i, p.mp1, p.mq1, zpre, zout, pq, (const u64*)row_keys, N);
   } else {
     launch_fill_masks(st, E, ctx->k01, ctx->k02, P_INNER, obj, zpre);
   }
@@ -1908,6 +1923,17 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
                       const uint64_t* zpre, const uint64_t* pq, int64_t M, int64_t N, int64_t K,
                       int trunc_bits, uint64_t matmul_call_id, int R_main, int R_trunc,
                       void* workspace, size_t workspace_bytes, uint64_t* trace) {
+  return mpc_verify_matmul_keyed(ctx, verify_id, xs, ws_, zpre, pq, M, N, K, trunc_bits, nullptr,
+                                 matmul_call_id, R_main, R_trunc, workspace, workspace_bytes,
+                                 trace);
+}
+
+int mpc_verify_matmul_keyed(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs,
+                            const uint64_t* ws_, const uint64_t* zpre, const uint64_t* pq,
+                            int64_t M, int64_t N, int64_t K, int trunc_bits,
+                            const uint64_t* row_keys, uint64_t matmul_call_id, int R_main,
+                            int R_trunc, void* workspace, size_t workspace_bytes,
+                            uint64_t* trace) {
   int rc = guard(ctx);
   if (rc) return rc;
   if (M <= 0 || N <= 0 || K <= 0) return fail(ctx, MPC_ERR_SHAPE, "verify_matmul: bad shape");
@@ -1959,7 +1985,8 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
   // ---- batch 1: the truncation pairs, chunk by chunk ----
   if (trunc &&
       (rc = verify_trunc_batch(ctx, p.tb, s, p.tcs, pq, trunc_bits, verify_id, matmul_call_id,
-                               trace ? trace + (long long)(p.R0 + 1) * TRACE_ROUND : nullptr)))
+                               trace ? trace + (long long)(p.R0 + 1) * TRACE_ROUND : nullptr,
+                               (const u64*)row_keys, N)))
     return rc;
   return finish_verify(ctx, (matmul_call_id << 1) | 1);
 }
@@ -2121,8 +2148,8 @@ int mpc_reconstruct_fixed(mpc_ctx* ctx, const uint64_t* xs, int64_t n, int frac_
 }
 
 int mpc_conv2d(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_t* ws_,
-               const int32_t geom[8], int64_t C_out, int trunc_bits, uint64_t* cols,
-               uint64_t* zpre, uint64_t* zout, uint64_t* pq, void* workspace,
+               const int32_t geom[8], int64_t C_out, int trunc_bits, const uint64_t* row_keys,
+               uint64_t* cols, uint64_t* zpre, uint64_t* zout, uint64_t* pq, void* workspace,
                size_t workspace_bytes) {
   int rc = guard(ctx);
   if (rc) return rc;
@@ -2140,8 +2167,8 @@ int mpc_conv2d(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, const uint64_
   launch_im2col(ctx->st, xs, g, cols);
   g_launches += 1;
   if ((rc = cuda_check(ctx, "conv2d: im2col"))) return rc;
-  return mpc_matmul(ctx, call_id, cols, ws_, g.B * g.Ho * g.Wo, C_out, g.C * g.kh * g.kw,
-                    trunc_bits, zpre, zout, pq, workspace, workspace_bytes);
+  return mpc_matmul_keyed(ctx, call_id, cols, ws_, g.B * g.Ho * g.Wo, C_out, g.C * g.kh * g.kw,
+                          trunc_bits, row_keys, zpre, zout, pq, workspace, workspace_bytes);
 }
 
 int mpc_trunc(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, int64_t n, int t, uint64_t* out,
@@ -2158,7 +2185,8 @@ int mpc_trunc(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, int64_t n, int
   const u64 obj = make_obj(call_id, 0, 0);
   {  // preprocessing (Fig. trunc): the pairs, as for a truncated product
     Phase phase(ctx, MPC_PROF_TRUNC_PAIRS);
-    launch_trunc_p0(st, n, ctx->k01, ctx->k02, obj, t, p.rx, out, pq, p.gp2, p.gq2, p.mp1, p.mq1);
+    launch_trunc_p0(st, n, ctx->k01, ctx->k02, obj, t, p.rx, out, pq, p.gp2, p.gq2, p.mp1, p.mq1,
+                    nullptr, n);
     const int ph = MPC_PHASE_OFFLINE, pr = MPC_PROTO_TRUNC;
     if ((rc = deliver(ctx, ph, pr, p.gp2, p.gp2i, n, MPC_SITE_GAMMA2))) return rc;
     if ((rc = deliver(ctx, ph, pr, p.mp1, p.mpi2, n, MPC_SITE_MZ1))) return rc;
@@ -2167,7 +2195,7 @@ int mpc_trunc(mpc_ctx* ctx, uint64_t call_id, const uint64_t* xs, int64_t n, int
     if ((rc = deliver(ctx, ph, pr, p.mq1, p.mqi2, n, MPC_SITE_MZ1))) return rc;
     if ((rc = deliver(ctx, ph, pr, p.gq2i, p.mqi1, n, MPC_SITE_MZ2))) return rc;
     launch_trunc_finish(st, n, ctx->k01, ctx->k02, obj, t, p.mpi1, p.mqi1, p.mpi2, p.mqi2,
-                        p.gp2i, p.gq2i, p.mp1, p.mq1, p.rx, out, pq);
+                        p.gp2i, p.gq2i, p.mp1, p.mq1, p.rx, out, pq, nullptr, n);
   }
   {  // online: the wire's mask switched to the pairs' r_x (checked by P0's hashes), then m >> t
     Phase phase(ctx, MPC_PROF_EXCHANGE);
@@ -2210,7 +2238,8 @@ int mpc_verify_trunc(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* pq, int64
   if (!plan_vtrunc(ar, n, R, ctx->gemm_path == MPC_GEMM_LIMB_TC, ctx->tune, p))
     return fail(ctx, MPC_ERR_SHAPE, "verify_trunc: more than 15 chunks");
   if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "verify_trunc: workspace too small");
-  if ((rc = verify_trunc_batch(ctx, p.tb, p.s, p.tcs, pq, t, verify_id, trunc_call_id, trace)))
+  if ((rc = verify_trunc_batch(ctx, p.tb, p.s, p.tcs, pq, t, verify_id, trunc_call_id, trace,
+                               nullptr, n)))
     return rc;
   return finish_verify(ctx, (trunc_call_id << 1) | 1);
 }

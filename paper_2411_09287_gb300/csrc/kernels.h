@@ -120,13 +120,16 @@ void launch_mult_online(cudaStream_t st, const u64* xs, const u64* ys, long long
 // out_s6 (P1.m, P2.m components) when out_s6 != null.
 void launch_exchange_finish(cudaStream_t st, long long n, const u64* p1_own, const u64* p1_in,
                             const u64* p2_own, const u64* p2_in, u64* zs, int t, u64* outs);
+// row_keys (device, one object id per output row of N outputs, or null): the truncation bits of
+// output e come from the streams of object row_keys[e / N] at word e mod N
 void launch_trunc_p0(cudaStream_t st, long long E, Key k01, Key k02, u64 obj, int t, u64* zpre,
                      u64* zout, u64* pq, u64* p0_out_gp2, u64* p0_out_gq2, u64* p1_out_mp,
-                     u64* p1_out_mq);
+                     u64* p1_out_mq, const u64* row_keys, long long N);
 void launch_trunc_finish(cudaStream_t st, long long E, Key k01, Key k02, u64 obj, int t,
                          const u64* p1_in_mp, const u64* p1_in_mq, const u64* p2_in_mp,
                          const u64* p2_in_mq, const u64* p2_gp2, const u64* p2_gq2,
-                         const u64* p1_mp1, const u64* p1_mq1, u64* zpre, u64* zout, u64* pq);
+                         const u64* p1_mp1, const u64* p1_mq1, u64* zpre, u64* zout, u64* pq,
+                         const u64* row_keys, long long N);
 void launch_xor_one(cudaStream_t st, u64* p, u64 mask);
 void launch_open_p1(cudaStream_t st, const u64* p1_m, const u64* p1_r1, const u64* p1_in_r2,
                     long long n, u64* out);
@@ -201,6 +204,9 @@ void launch_mode_consts(cudaStream_t st, int mode, u64* cst);
 // of the outputs of one verification chunk)
 void launch_prf_words(cudaStream_t st, long long n, Key key, u32 tag, u64 obj, u64* out,
                       long long off = 0);
+// the same for a row-keyed truncation-bit stream: word e = word e mod N of object row_keys[e / N]
+void launch_prf_words_keyed(cudaStream_t st, long long n, Key key, u32 tag, const u64* row_keys,
+                            long long N, u64* out, long long off);
 
 // ---- trunc-batch S matrix on the tensor cores (trunc_s.cu) ----------------------------------
 void launch_trunc_limb_table(cudaStream_t st, const u64* Tlo, long long L, unsigned char* TL8);

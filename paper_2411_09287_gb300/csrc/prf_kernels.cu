@@ -22,6 +22,32 @@ inline unsigned grid_for(long long n8) {
 
 __device__ __forceinline__ u64 asr64(u64 v, int t) { return (u64)(((long long)v) >> t); }
 
+// Words 8 blk .. 8 blk + 7 of a truncation-bit stream.  Unkeyed: words of the stream (tag, obj).
+// Keyed by rows (row_keys != null, outputs row-major with N per row): word e is word e mod N of
+// the stream (tag, row_keys[e / N]), so that a row draws the same bits whatever batch it is in;
+// words past E are 0.
+__device__ __forceinline__ void bits_block8(const Key& key, u32 tag, u64 obj, u64 blk,
+                                            const u64* __restrict__ row_keys, long long N,
+                                            long long E, u64 w[8]) {
+  if (!row_keys) {
+    prf_block8(key, tag, obj, blk, w);
+    return;
+  }
+#pragma unroll 1
+  for (int j = 0; j < 8; ++j) {
+    const long long e = (long long)blk * 8 + j;
+    w[j] = 0;
+    if (e < E) {
+      const long long row = e / N, col = e - row * N;
+      u64 b8[8];
+      prf_block8(key, tag, row_keys[row], (u64)(col >> 3), b8);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q == (int)(col & 7)) w[j] = b8[q];
+    }
+  }
+}
+
 // v, with a compiler scheduling fence: code that uses the result is not hoisted above the memory
 // operations before it (keeps one ChaCha20 block live at a time)
 __device__ __forceinline__ u64 seq_u64(u64 v) {
@@ -191,7 +217,8 @@ __global__ void k_exchange_finish(long long n, const u64* __restrict__ p1_own,
 // r_z with asr(b1, t), asr(b2, t), Gamma_q, r_q).
 // pq layout: <p> at pq[0..6E), <q> at pq[6E..12E).
 __global__ void __launch_bounds__(TPB, 1)
-k_trunc_p0(long long E, Key k01, Key k02, u64 obj, int t, u32 ttb1, u32 ttb2,
+k_trunc_p0(long long E, Key k01, Key k02, u64 obj, const u64* __restrict__ row_keys, long long N,
+           int t, u32 ttb1, u32 ttb2,
            u32 tp1, u32 tp2, u32 tpg, u32 tq1, u32 tq2, u32 tqg,
            u64* __restrict__ zpre, u64* __restrict__ zout, u64* __restrict__ pq,
            u64* __restrict__ gp2_out, u64* __restrict__ gq2_out,
@@ -209,8 +236,8 @@ k_trunc_p0(long long E, Key k01, Key k02, u64 obj, int t, u32 ttb1, u32 ttb2,
     const u64 b = (u64)(bw + lane);
     const long long e0 = bw * 8;
     u64 b1[8], b2[8], x[8], g[8];
-    prf_block8(k01, ttb1, obj, b, b1);
-    prf_block8(k02, ttb2, obj, b, b2);
+    bits_block8(k01, ttb1, obj, b, row_keys, N, E, b1);
+    bits_block8(k02, ttb2, obj, b, row_keys, N, E, b2);
     // <p>
     prf_block8(k01, tp1, obj, seq_u64(b), x);   // r_p1: P0 and P1 copies
     store8w(p, e0, E, x, st);
@@ -264,7 +291,8 @@ k_trunc_p0(long long E, Key k01, Key k02, u64 obj, int t, u32 ttb1, u32 ttb2,
 // Pi_Trunc^t preprocessing, P1's and P2's part after the messages: m_p = [m_p]_1 + [m_p]_2 at each
 // of P1, P2; [r_x]_1 := m_{r_x} - [r_{r_x}]_1 at P1, [r_x]_2 := -[r_{r_x}]_2 at P2 (same for r_z).
 __global__ void __launch_bounds__(TPB, 2)
-k_trunc_finish(long long E, Key k01, Key k02, u64 obj, int t, u32 ttb1,
+k_trunc_finish(long long E, Key k01, Key k02, u64 obj, const u64* __restrict__ row_keys,
+               long long N, int t, u32 ttb1,
                u32 ttb2, const u64* __restrict__ p1_in_mp,
                const u64* __restrict__ p1_in_mq, const u64* __restrict__ p2_in_mp,
                const u64* __restrict__ p2_in_mq, const u64* __restrict__ p2_gp2,
@@ -282,7 +310,7 @@ k_trunc_finish(long long E, Key k01, Key k02, u64 obj, int t, u32 ttb1,
     const u64 b = (u64)(bw + lane);
     const long long e0 = bw * 8;
     u64 bb[8], m[8], x[8];
-    prf_block8(k01, ttb1, obj, b, bb);   // b1 (P1)
+    bits_block8(k01, ttb1, obj, b, row_keys, N, E, bb);   // b1 (P1)
     // P1: m_p, m_q and its [r_x]_1, [r_z]_1
     load8w(p1_mp1, e0, E, m, st);
     load8w(p1_in_mp, e0, E, x, st);
@@ -303,7 +331,7 @@ k_trunc_finish(long long E, Key k01, Key k02, u64 obj, int t, u32 ttb1,
     for (int j = 0; j < 8; ++j) m[j] = m[j] + asr64(bb[j], t) - x[j];
     store8w(zout + 3 * E, e0, E, m, st);
     // P2
-    prf_block8(k02, ttb2, obj, b, bb);   // b2 (P2)
+    bits_block8(k02, ttb2, obj, b, row_keys, N, E, bb);   // b2 (P2)
     load8w(p2_in_mp, e0, E, m, st);
     load8w(p2_gp2, e0, E, x, st);
 #pragma unroll
@@ -326,6 +354,23 @@ k_trunc_finish(long long E, Key k01, Key k02, u64 obj, int t, u32 ttb1,
 }
 
 __global__ void k_xor_one(u64* p, u64 mask) { *p ^= mask; }
+
+// words off .. off + n - 1 of a row-keyed truncation-bit stream (see bits_block8) into out
+__global__ void k_prf_words_keyed(long long n, long long off, Key key, u32 tag,
+                                  const u64* __restrict__ row_keys, long long N,
+                                  u64* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long e = off + i, row = e / N, col = e - row * N;
+    u64 b8[8];
+    prf_block8(key, tag, row_keys[row], (u64)(col >> 3), b8);
+    u64 w = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q == (int)(col & 7)) w = b8[q];
+    out[i] = w;
+  }
+}
 
 // stream words off .. off + n - 1 (block b holds words 8b .. 8b + 7) into out[0 .. n)
 __global__ void k_prf_words(long long n, long long off, Key key, u32 tag, u64 obj,
@@ -406,10 +451,10 @@ void launch_exchange_finish(cudaStream_t st, long long n, const u64* p1_own, con
 
 void launch_trunc_p0(cudaStream_t st, long long E, Key k01, Key k02, u64 obj, int t, u64* zpre,
                      u64* zout, u64* pq, u64* p0_out_gp2, u64* p0_out_gq2, u64* p1_out_mp,
-                     u64* p1_out_mq) {
+                     u64* p1_out_mq, const u64* row_keys, long long N) {
   if (E <= 0) return;
   k_trunc_p0<<<grid_for((E + 7) / 8), TPB, 0, st>>>(
-      E, k01, k02, obj, t, make_tag(P_TRUNC_BITS, C_TB1), make_tag(P_TRUNC_BITS, C_TB2),
+      E, k01, k02, obj, row_keys, N, t, make_tag(P_TRUNC_BITS, C_TB1), make_tag(P_TRUNC_BITS, C_TB2),
       make_tag(P_TRUNC_P, C_R1), make_tag(P_TRUNC_P, C_R2), make_tag(P_TRUNC_P, C_G1),
       make_tag(P_TRUNC_Q, C_R1), make_tag(P_TRUNC_Q, C_R2), make_tag(P_TRUNC_Q, C_G1), zpre, zout,
       pq, p0_out_gp2, p0_out_gq2, p1_out_mp, p1_out_mq);
@@ -418,14 +463,21 @@ void launch_trunc_p0(cudaStream_t st, long long E, Key k01, Key k02, u64 obj, in
 void launch_trunc_finish(cudaStream_t st, long long E, Key k01, Key k02, u64 obj, int t,
                          const u64* p1_in_mp, const u64* p1_in_mq, const u64* p2_in_mp,
                          const u64* p2_in_mq, const u64* p2_gp2, const u64* p2_gq2,
-                         const u64* p1_mp1, const u64* p1_mq1, u64* zpre, u64* zout, u64* pq) {
+                         const u64* p1_mp1, const u64* p1_mq1, u64* zpre, u64* zout, u64* pq,
+                         const u64* row_keys, long long N) {
   if (E <= 0) return;
   k_trunc_finish<<<grid_for((E + 7) / 8), TPB, 0, st>>>(
-      E, k01, k02, obj, t, make_tag(P_TRUNC_BITS, C_TB1), make_tag(P_TRUNC_BITS, C_TB2), p1_in_mp,
+      E, k01, k02, obj, row_keys, N, t, make_tag(P_TRUNC_BITS, C_TB1), make_tag(P_TRUNC_BITS, C_TB2), p1_in_mp,
       p1_in_mq, p2_in_mp, p2_in_mq, p2_gp2, p2_gq2, p1_mp1, p1_mq1, zpre, zout, pq);
 }
 
 void launch_xor_one(cudaStream_t st, u64* p, u64 mask) { k_xor_one<<<1, 1, 0, st>>>(p, mask); }
+
+void launch_prf_words_keyed(cudaStream_t st, long long n, Key key, u32 tag, const u64* row_keys,
+                            long long N, u64* out, long long off) {
+  if (n <= 0 || off < 0) return;
+  k_prf_words_keyed<<<grid_for(n), TPB, 0, st>>>(n, off, key, tag, row_keys, N, out);
+}
 
 void launch_prf_words(cudaStream_t st, long long n, Key key, u32 tag, u64 obj, u64* out,
                       long long off) {

@@ -217,9 +217,11 @@ class Context:
             return 0, 0
         return (H + 2 * pad - kh) // stride + 1, (W + 2 * pad - kw) // stride + 1
 
-    def conv2d(self, call_id: int, xs, ws_, geom, C_out: int, trunc_bits: int = -1):
+    def conv2d(self, call_id: int, xs, ws_, geom, C_out: int, trunc_bits: int = -1,
+               row_keys=None):
         """mpc_conv2d.  geom = (B, C, H, W, kh, kw, stride, pad).  Returns (cols, zpre, zout, pq,
-        (M, N, K)) with M = B Ho Wo, N = C_out, K = C kh kw (output rows (b, i, j))."""
+        (M, N, K)) with M = B Ho Wo, N = C_out, K = C kh kw (output rows (b, i, j)); row_keys as
+        for matmul."""
         B, Cc, H, W, kh, kw, stride, pad = geom
         Ho, Wo = self.conv_out(geom)
         Mr, K = B * Ho * Wo, Cc * kh * kw
@@ -231,10 +233,14 @@ class Context:
         wsb = self.ws_size(OP_MATMUL, Mr, C_out, K, trunc_bits)
         ws = self.workspace(wsb)
         g = (C.c_int32 * 8)(*geom)
+        rk = self._row_keys(row_keys)
         self._check(self.lib.mpc_conv2d(self.h, call_id, C.c_void_p(_ptr(xs)), C.c_void_p(_ptr(ws_)),
-                                        g, C_out, trunc_bits, C.c_void_p(_ptr(cols)),
+                                        g, C_out, trunc_bits, C.c_void_p(_ptr(rk)),
+                                        C.c_void_p(_ptr(cols)),
                                         C.c_void_p(_ptr(zpre)), C.c_void_p(_ptr(zout)),
                                         C.c_void_p(_ptr(pq)), C.c_void_p(_ptr(ws)), wsb))
+        if rk is not None:
+            self.sync()   # the keys must outlive the enqueued work
         return cols, zpre, (zout if trunc_bits >= 0 else zpre), pq, (Mr, C_out, K)
 
     def trunc(self, call_id: int, xs, n: int, t: int):
@@ -266,8 +272,15 @@ class Context:
                                       n, C.c_void_p(_ptr(out)), C.c_void_p(_ptr(ws)), wsb))
         return out
 
+    def _row_keys(self, row_keys):
+        """numpy uint64 row keys -> a CUDA tensor (None stays None)."""
+        if row_keys is None or not isinstance(row_keys, np.ndarray):
+            return row_keys
+        return from_u64(self, np.ascontiguousarray(row_keys, dtype=np.uint64))
+
     def matmul(self, call_id: int, xs, ws_, M: int, N: int, K: int, trunc_bits: int = -1,
-               zpre=None, zout=None, pq=None):
+               zpre=None, zout=None, pq=None, row_keys=None):
+        """mpc_matmul, or mpc_matmul_keyed when row_keys (M object ids, numpy or CUDA) is given."""
         E = M * N
         zpre = self.shares(E) if zpre is None else zpre
         if trunc_bits >= 0:
@@ -275,10 +288,14 @@ class Context:
             pq = self.empty(12 * E) if pq is None else pq
         wsb = self.ws_size(OP_MATMUL, M, N, K, trunc_bits)
         ws = self.workspace(wsb)
-        self._check(self.lib.mpc_matmul(self.h, call_id, C.c_void_p(_ptr(xs)), C.c_void_p(_ptr(ws_)),
-                                        M, N, K, trunc_bits, C.c_void_p(_ptr(zpre)),
-                                        C.c_void_p(_ptr(zout)), C.c_void_p(_ptr(pq)),
-                                        C.c_void_p(_ptr(ws)), wsb))
+        rk = self._row_keys(row_keys)
+        self._check(self.lib.mpc_matmul_keyed(self.h, call_id, C.c_void_p(_ptr(xs)),
+                                              C.c_void_p(_ptr(ws_)), M, N, K, trunc_bits,
+                                              C.c_void_p(_ptr(rk)), C.c_void_p(_ptr(zpre)),
+                                              C.c_void_p(_ptr(zout)), C.c_void_p(_ptr(pq)),
+                                              C.c_void_p(_ptr(ws)), wsb))
+        if rk is not None:
+            self.sync()   # the keys must outlive the enqueued work
         return zpre, (zout if trunc_bits >= 0 else zpre), pq
 
     def verify_mult(self, verify_id: int, xs, ys, zs, n: int, mult_call_id: int, R: int = -1,
@@ -375,15 +392,17 @@ class Context:
 
     def verify_matmul(self, verify_id: int, xs, ws_, zpre, pq, M: int, N: int, K: int,
                       trunc_bits: int, matmul_call_id: int, R_main: int = -1, R_trunc: int = -1,
-                      trace: bool = False):
+                      trace: bool = False, row_keys=None):
         ntr = self.trace_words(OP_VERIFY_MATMUL, M, N, K, trunc_bits, R_main, R_trunc)
         tr = self.zeros(ntr) if trace else None
         wsb = self.ws_size(OP_VERIFY_MATMUL, M, N, K, trunc_bits, R_main, R_trunc)
         ws = self.workspace(wsb)
-        rc = self.lib.mpc_verify_matmul(self.h, verify_id, C.c_void_p(_ptr(xs)), C.c_void_p(_ptr(ws_)),
-                                        C.c_void_p(_ptr(zpre)), C.c_void_p(_ptr(pq)), M, N, K,
-                                        trunc_bits, matmul_call_id, R_main, R_trunc,
-                                        C.c_void_p(_ptr(ws)), wsb, C.c_void_p(_ptr(tr)))
+        rk = self._row_keys(row_keys)
+        rc = self.lib.mpc_verify_matmul_keyed(self.h, verify_id, C.c_void_p(_ptr(xs)),
+                                              C.c_void_p(_ptr(ws_)), C.c_void_p(_ptr(zpre)),
+                                              C.c_void_p(_ptr(pq)), M, N, K, trunc_bits,
+                                              C.c_void_p(_ptr(rk)), matmul_call_id, R_main, R_trunc,
+                                              C.c_void_p(_ptr(ws)), wsb, C.c_void_p(_ptr(tr)))
         if rc not in (MPC_OK, MPC_ERR_VERIFY, MPC_ERR_ABORT):
             self._check(rc)
         return rc, tr
@@ -446,6 +465,24 @@ class Context:
 
     def sync(self):
         self._check(self.lib.mpc_sync(self.h))
+
+
+def row_object_ids(call: int, rows: int, first: int = 0) -> np.ndarray:
+    """Object ids (call << 20 | batch << 16 | sub, the C-ABI layout) of rows first .. first + rows
+    - 1 of one call, the row number r split as batch = r >> 16, sub = r & 0xFFFF (r < 2^20)."""
+    r = np.arange(first, first + rows, dtype=np.uint64)
+    assert 0 <= call < (1 << 44) and first + rows <= (1 << 20)
+    return (np.uint64(call) << np.uint64(20)) | ((r >> np.uint64(16)) << np.uint64(16)) | (r & np.uint64(0xFFFF))
+
+
+def segment_row_keys(segments, layer: int, rows_per_image: int) -> np.ndarray:
+    """Row keys of one layer of a packed batch: segments = [(request id, images), ...] in packing
+    order; the rows of request q's images get the object ids of call 2^43 + q * 64 + layer (a
+    range apart from ordinary call ids), numbered from 0 within the request, so that a request
+    draws the same truncation bits packed or alone."""
+    assert 0 <= layer < 64
+    return np.concatenate([row_object_ids((1 << 43) + int(q) * 64 + layer, int(b) * rows_per_image)
+                           for q, b in segments])
 
 
 def to_u64(t) -> np.ndarray:

@@ -80,10 +80,10 @@ class _Ids:
         return v
 
 
-def _matmul_verified(ctx, ids, h, gw, Mr, N, K, k):
+def _matmul_verified(ctx, ids, h, gw, Mr, N, K, k, keys=None):
     c = ids.take(2)
-    zpre, zout, pq = ctx.matmul(c, h, gw, Mr, N, K, k)
-    rc, _ = ctx.verify_matmul(c + 1, h, gw, zpre, pq, Mr, N, K, k, c)
+    zpre, zout, pq = ctx.matmul(c, h, gw, Mr, N, K, k, row_keys=keys)
+    rc, _ = ctx.verify_matmul(c + 1, h, gw, zpre, pq, Mr, N, K, k, c, row_keys=keys)
     if rc != M.MPC_OK:
         raise M.MpcError(rc, "matrix-product layer rejected")
     return zout
@@ -130,16 +130,18 @@ def _pool_chunked(ctx, ids, h, shape, chunk_images):
     return _concat(ctx, parts)
 
 
-def _conv_block(ctx, ids, h, shape, gw, wshape, k, pool_chunk, relu_chunk):
+def _conv_block(ctx, ids, h, shape, gw, wshape, k, pool_chunk, relu_chunk, segments=None,
+                layer=0):
     B, C, H, W = shape
     Co, _, kh, kw = wshape
     c = ids.take(2)
     geom = (B, C, H, W, kh, kw, 1, 0)
-    cols, zpre, zout, pq, (Mr, N, K) = ctx.conv2d(c, h, gw, geom, Co, k)
-    rc, _ = ctx.verify_matmul(c + 1, cols, gw, zpre, pq, Mr, N, K, k, c)
+    Ho, Wo = ctx.conv_out(geom)
+    keys = M.segment_row_keys(segments, layer, Ho * Wo) if segments is not None else None
+    cols, zpre, zout, pq, (Mr, N, K) = ctx.conv2d(c, h, gw, geom, Co, k, row_keys=keys)
+    rc, _ = ctx.verify_matmul(c + 1, cols, gw, zpre, pq, Mr, N, K, k, c, row_keys=keys)
     if rc != M.MPC_OK:
         raise M.MpcError(rc, "convolution rejected")
-    Ho, Wo = ctx.conv_out(geom)
     z = ctx.gather(zout, Mr * Co, rows_to_nchw_index(B, Co, Ho, Wo))
     z = _pool_chunked(ctx, ids, z, (B, Co, Ho, Wo), pool_chunk)
     n = B * Co * (Ho // 2) * (Wo // 2)
@@ -159,10 +161,11 @@ def share_params(ctx: "M.Context", params, k: int = 13, call_base: int = 4000):
 
 
 def net_a_secure(ctx: "M.Context", x, params, k: int = 13, call_base: int = 5000,
-                 pool_chunk: int = 4, relu_chunk: int = 1 << 15, shared=None):
+                 pool_chunk: int = 4, relu_chunk: int = 1 << 15, shared=None, segments=None):
     """Secure Net A forward.  x: (B, 1, 28, 28) float inputs; params: the float parameters (shared
-    by P0 here unless `shared` holds share_params' sharings).  Returns the opened logits (B, 10)
-    as float64."""
+    by P0 here unless `shared` holds share_params' sharings); segments: as for
+    secure_mlp.secure_forward (truncation bits keyed by request, layer and row).  Returns the
+    opened logits (B, 10) as float64."""
     ids = _Ids(call_base)
     if shared is None:
         shared = share_params(ctx, params, k, ids.take(4))
@@ -170,13 +173,14 @@ def net_a_secure(ctx: "M.Context", x, params, k: int = 13, call_base: int = 5000
     h = ctx.share_fixed(ids.take(), np.ascontiguousarray(x, dtype=np.float64).reshape(-1), k)
     shape = x.shape
     h, shape = _conv_block(ctx, ids, h, shape, shared["c1"], params["c1"].shape, k, pool_chunk,
-                           relu_chunk)
+                           relu_chunk, segments, 0)
     h, shape = _conv_block(ctx, ids, h, shape, shared["c2"], params["c2"].shape, k, pool_chunk,
-                           relu_chunk)
+                           relu_chunk, segments, 1)
     flat = int(np.prod(shape[1:]))
-    for name, last in (("f1", False), ("f2", True)):
+    for layer, name, last in ((2, "f1", False), (3, "f2", True)):
         w = params[name]
-        h = _matmul_verified(ctx, ids, h, shared[name], B, w.shape[1], flat, k)
+        keys = M.segment_row_keys(segments, layer, 1) if segments is not None else None
+        h = _matmul_verified(ctx, ids, h, shared[name], B, w.shape[1], flat, k, keys)
         flat = w.shape[1]
         if not last:
             h = _relu_chunked(ctx, ids, h, B * flat, relu_chunk)

@@ -37,11 +37,20 @@ def quantized(x, k: int):
     return np.floor(np.asarray(x, dtype=np.float64) * float(1 << k)) / float(1 << k)
 
 
+def share_weights(ctx: "M.Context", weights, k: int = 13, call_base: int = 900):
+    """P0 shares the weight matrices once (mpc_share_fixed); the sharings serve any number of
+    forward passes."""
+    return [ctx.share_fixed(call_base + i, np.ascontiguousarray(w, dtype=np.float64).reshape(-1), k)
+            for i, w in enumerate(weights)]
+
+
 def secure_forward(ctx: "M.Context", x, weights, k: int = 13, call_base: int = 1000,
-                   shared_weights=None):
+                   shared_weights=None, segments=None):
     """Secure forward pass.  x: (B, n0) float inputs; weights: list of (n_i, n_{i+1}) float
     matrices, shared by P0 (mpc_share_fixed) unless shared_weights already holds their sharings.
-    Returns the opened logits (B, n_last) as float64 (mpc_reconstruct_fixed)."""
+    segments: [(request id, images), ...] of a packed batch; the truncation bits of every layer
+    are then keyed by (request, layer, row) so that each request opens to the logits it would
+    get alone.  Returns the opened logits (B, n_last) as float64 (mpc_reconstruct_fixed)."""
     B = x.shape[0]
     cid = call_base
     h = ctx.share_fixed(cid, np.ascontiguousarray(x, dtype=np.float64).reshape(-1), k)
@@ -50,8 +59,10 @@ def secure_forward(ctx: "M.Context", x, weights, k: int = 13, call_base: int = 1
         n_in, n_out = w.shape
         gw = (shared_weights[i] if shared_weights is not None
               else ctx.share_fixed(cid, np.ascontiguousarray(w, dtype=np.float64).reshape(-1), k))
-        zpre, zout, pq = ctx.matmul(cid + 1, h, gw, B, n_out, n_in, k)
-        rc, _ = ctx.verify_matmul(cid + 2, h, gw, zpre, pq, B, n_out, n_in, k, cid + 1)
+        keys = M.segment_row_keys(segments, i, 1) if segments is not None else None
+        zpre, zout, pq = ctx.matmul(cid + 1, h, gw, B, n_out, n_in, k, row_keys=keys)
+        rc, _ = ctx.verify_matmul(cid + 2, h, gw, zpre, pq, B, n_out, n_in, k, cid + 1,
+                                  row_keys=keys)
         if rc != M.MPC_OK:
             raise M.MpcError(rc, f"layer {i}: verification rejected")
         h = zout

@@ -7,9 +7,10 @@ worker.  Each worker owns a libmpc3 context on its own CUDA stream, so packed ba
 different workers run concurrently on the device (the library's calls release the GIL).  Logits
 are split back per request; latency is arrival -> opened logits.
 
-Every request's logits stay within the protocol's error bound of the float64 model whether the
-request runs alone or packed with others (the masks differ, the opened values agree within the
-truncation error).
+The weights are shared once per worker and stay resident.  Each request's truncation bits are
+keyed by (request, layer, row of the request), so a request's logits are bit-identical whether it
+runs alone or packed with others (the other random values differ, but an opened value depends on
+them only through the truncation carry).
 """
 from __future__ import annotations
 
@@ -51,11 +52,20 @@ class Model:
         else:
             raise ValueError(kind)
 
-    def secure(self, ctx, x, call_base):
-        """Opened logits (float64) of one secure forward pass over the packed inputs x."""
+    def share(self, ctx, call_base):
+        """P0 shares the weights once; the sharings stay resident for every later pass."""
         if self.kind == "mlp":
-            return SM.secure_forward(ctx, x, self.w, self.k, call_base)
-        return SC.net_a_secure(ctx, x, self.p, self.k, call_base)
+            return SM.share_weights(ctx, self.w, self.k, call_base)
+        return SC.share_params(ctx, self.p, self.k, call_base)
+
+    def secure(self, ctx, x, call_base, shared=None, segments=None):
+        """Opened logits (float64) of one secure forward pass over the packed inputs x.
+        segments = [(request id, images), ...]: truncation bits keyed per request, so that each
+        request gets exactly the logits it would get alone."""
+        if self.kind == "mlp":
+            return SM.secure_forward(ctx, x, self.w, self.k, call_base, shared_weights=shared,
+                                     segments=segments)
+        return SC.net_a_secure(ctx, x, self.p, self.k, call_base, shared=shared, segments=segments)
 
     def fp64(self, x):
         q = lambda a: SM.quantized(a, self.k)
@@ -84,11 +94,10 @@ class _Worker(threading.Thread):
     def __init__(self, wid, server, ctx=None, stream=None):
         super().__init__(daemon=True)
         self.wid, self.server = wid, server
-        if ctx is None:
+        if ctx is None:   # the same three parties (one seed) on every worker, own call ids
             import torch
             stream = torch.cuda.Stream()
-            seed = hashlib.sha256(f"serving-worker-{wid}".encode()).digest()
-            ctx = M.Context(seed, gemm_path=server.gemm_path, stream=stream)
+            ctx = M.Context(server.seed, gemm_path=server.gemm_path, stream=stream)
         self.ctx, self.stream = ctx, stream
         self.inbox = queue.Queue()
         self.calls = 1 + wid * (1 << 36)          # disjoint call-id spaces per worker
@@ -101,6 +110,7 @@ class _Worker(threading.Thread):
         return torch.cuda.stream(self.stream)
 
     def run(self):
+        shared = None
         while True:
             job = self.inbox.get()
             if job is None:
@@ -110,7 +120,11 @@ class _Worker(threading.Thread):
             try:
                 x = np.concatenate([r.x for r in reqs], axis=0)
                 with self._on_stream():
-                    logits = self.server.model.secure(self.ctx, x, self.calls)
+                    if shared is None:   # weights shared once, resident for the worker's life
+                        shared = self.server.model.share(self.ctx, self.calls)
+                        self.calls += 1 << 16
+                    logits = self.server.model.secure(self.ctx, x, self.calls, shared,
+                                                      [(r.rid, r.x.shape[0]) for r in reqs])
                 t = time.perf_counter() - self.server.t0
                 off = 0
                 for r in reqs:
@@ -154,12 +168,16 @@ def check_admissible(requests, max_batch: int, max_in_flight: int):
 
 
 class Server:
+    SEED = hashlib.sha256(b"mpc3-serving-parties").digest()
+
     def __init__(self, model: Model, n_workers: int = 2, max_batch: int = 256,
                  mem_budget_bytes: float = 64e9, gemm_path: int = M.GEMM_LIMB_TC,
-                 make_context=None):
+                 make_context=None, seed: bytes = None):
         """make_context(worker id) -> (context, CUDA stream or None) replaces the default context
-        per worker (one on a new stream)."""
+        per worker (one on a new stream, keyed by `seed`: every worker runs the same three
+        parties, in its own range of call ids)."""
         self.model, self.max_batch, self.gemm_path = model, max_batch, gemm_path
+        self.seed = seed or self.SEED
         self.lock = threading.Lock()
         self.wake = threading.Event()
         self.in_flight = 0
@@ -238,20 +256,21 @@ def main():
     import json
     ap = argparse.ArgumentParser(description="secure-inference serving run")
     ap.add_argument("--model", choices=["mlp", "neta"], default="mlp")
-    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--rate", type=float, nargs="+", default=[200.0])
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--max-b", type=int, default=256)
     ap.add_argument("--max-batch", type=int, default=256)
     ap.add_argument("--workers", type=int, default=2)
     a = ap.parse_args()
     model = Model(a.model)
-    reqs = poisson_requests(model, a.requests, a.rate, a.max_b, f"C5-{a.model}-{a.rate}")
-    srv = Server(model, a.workers, a.max_batch)
-    out = srv.serve(reqs)
-    st = Server.stats(out)
-    err = max(float(np.max(np.abs(r.logits - model.fp64(r.x)))) for r in out)
-    st.update({"model": a.model, "rate": a.rate, "max_abs_err_vs_fp64": err})
-    print(json.dumps(st))
+    for rate in a.rate:
+        reqs = poisson_requests(model, a.requests, rate, a.max_b, f"C5-{a.model}-{rate}")
+        srv = Server(model, a.workers, a.max_batch)
+        out = srv.serve(reqs)
+        st = Server.stats(out)
+        err = max(float(np.max(np.abs(r.logits - model.fp64(r.x)))) for r in out)
+        st.update({"model": a.model, "rate": rate, "max_abs_err_vs_fp64": err})
+        print(json.dumps(st), flush=True)
 
 
 if __name__ == "__main__":

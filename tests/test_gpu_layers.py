@@ -167,3 +167,60 @@ def test_a_corrupted_pair_mask_aborts_the_mask_switch(mpc):
     assert ei.value.code == mpc.MPC_ERR_ABORT
     with pytest.raises(OP.Abort):
         OP.trunc(sess, ox, 2, 13)
+
+
+def _row_keys(req, layer, rows):
+    from oracle.shares import obj_id
+    return np.array([obj_id(req * 64 + layer, (r >> 16) & 15, r & 0xFFFF) for r in range(rows)],
+                    dtype=np.uint64)
+
+
+@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("M,N,K,chunk", [(13, 10, 30, None), (20, 7, 16, 64)])
+def test_row_keyed_matmul_matches_oracle(mpc, M, N, K, chunk, path):
+    """mpc_matmul_keyed / mpc_verify_matmul_keyed: shares, pairs, transcript (chunked too), ledger
+    and opened output equal the oracle's with the same row keys (N not a multiple of 8, so a
+    ChaCha block of the call's layout would straddle rows)."""
+    t = 13
+    seed = seed_of(f"keyed-{M}-{N}-{K}-{chunk}")
+    g = workloads.rng(f"keyed-{M}-{N}-{K}")
+    X = OP.encode_fixed(g.uniform(-2, 2, (M, K)), 13)
+    W = OP.encode_fixed(g.uniform(-2, 2, (K, N)), 13)
+    keys = _row_keys(5, 2, M)
+    tune = dict(trunc_chunk=chunk, trunc_block=128) if chunk else None
+    ctx, sess = mpc.Context(seed, gemm_path=path, tuning=tune), Session(seed)
+    gx, gw = ctx.share_input(1, X), ctx.share_input(2, W)
+    zpre, zout, pq = ctx.matmul(3, gx, gw, M, N, K, t, row_keys=keys)
+    ox, ow = OP.share_input(sess, X, 1), OP.share_input(sess, W, 2)
+    res = OP.matmul(sess, ox, ow, 3, trunc_bits=t, row_keys=[int(k) for k in keys])
+    assert_shared_equal(gpu_shared(mpc, zpre, (M, N)), res.z_pre, "zpre")
+    assert_shared_equal(gpu_shared(mpc, zout, (M, N)), res.out, "zout")
+    rc, tr = ctx.verify_matmul(4, gx, gw, zpre, pq, M, N, K, t, 3, trace=True, row_keys=keys)
+    otr = []
+    ok = OV.matmul_verify(sess, ox, ow, res, 4, t, trace=otr, trunc_chunk=chunk)
+    assert ok and rc == mpc.MPC_OK
+    check_trace(mpc, tr, otr, [mpc.default_R(K)] + [mpc.default_R(64 * (e1 - e0))
+                                                    for e0, e1 in OV.trunc_chunks(M * N, chunk)])
+    assert_ledger(mpc, ctx, sess)
+    assert np.array_equal(ctx.reconstruct(zout, M * N), OP.reconstruct(sess, res.out).reshape(-1))
+
+
+def test_keyed_rows_open_the_same_alone_and_packed(mpc):
+    K, N, t = 64, 10, 13
+    g = workloads.rng("keyed-pack")
+    W = OP.encode_fixed(g.uniform(-1, 1, (K, N)), 13)
+    XA = OP.encode_fixed(g.uniform(-1, 1, (3, K)), 13)
+    XB = OP.encode_fixed(g.uniform(-1, 1, (5, K)), 13)
+
+    def run(X, keys, call):
+        ctx = mpc.Context(seed_of("keyed-pack"))
+        M = X.shape[0]
+        gx, gw = ctx.share_input(call, X), ctx.share_input(call + 1, W)
+        zpre, zout, pq = ctx.matmul(call + 2, gx, gw, M, N, K, t, row_keys=keys)
+        rc, _ = ctx.verify_matmul(call + 3, gx, gw, zpre, pq, M, N, K, t, call + 2, row_keys=keys)
+        assert rc == mpc.MPC_OK
+        return ctx.reconstruct(zout, M * N).reshape(M, N)
+
+    alone = run(XA, _row_keys(1, 0, 3), 10)
+    packed = run(np.concatenate([XB, XA]), np.concatenate([_row_keys(2, 0, 5), _row_keys(1, 0, 3)]), 50)
+    assert np.array_equal(packed[5:], alone)

@@ -57,7 +57,11 @@ class _StubModel:
     def bytes_per_image(self, ctx, b):
         return 1.0
 
-    def secure(self, ctx, x, call_base):
+    def share(self, ctx, call_base):
+        return "resident weights"
+
+    def secure(self, ctx, x, call_base, shared=None, segments=None):
+        assert shared == "resident weights" and sum(b for _, b in segments) == x.shape[0]
         self.calls += 1
         if self.calls == self.fail_on:
             raise RuntimeError("protocol aborted")
