@@ -49,6 +49,9 @@ class Model:
         elif kind == "neta":
             self.p = SC.net_a_params("C4-netA-weights")
             self.in_shape = (1, 28, 28)
+        elif kind == "netb":
+            self.p = SC.net_b_params("C4-netB-weights")
+            self.in_shape = (3, 32, 32)
         else:
             raise ValueError(kind)
 
@@ -56,6 +59,8 @@ class Model:
         """P0 shares the weights once; the sharings stay resident for every later pass."""
         if self.kind == "mlp":
             return SM.share_weights(ctx, self.w, self.k, call_base)
+        if self.kind == "netb":
+            return SC.share_params_b(ctx, self.p, self.k, call_base)
         return SC.share_params(ctx, self.p, self.k, call_base)
 
     def secure(self, ctx, x, call_base, shared=None, segments=None):
@@ -65,13 +70,17 @@ class Model:
         if self.kind == "mlp":
             return SM.secure_forward(ctx, x, self.w, self.k, call_base, shared_weights=shared,
                                      segments=segments)
+        if self.kind == "netb":
+            return SC.net_b_secure(ctx, x, self.p, self.k, call_base, shared=shared,
+                                   segments=segments)
         return SC.net_a_secure(ctx, x, self.p, self.k, call_base, shared=shared, segments=segments)
 
     def fp64(self, x):
         q = lambda a: SM.quantized(a, self.k)
         if self.kind == "mlp":
             return SM.fp64_forward(q(x), [q(w) for w in self.w])
-        return SC.net_a_fp64(q(x), {n: q(w) for n, w in self.p.items()})
+        ref = SC.net_b_fp64 if self.kind == "netb" else SC.net_a_fp64
+        return ref(q(x), {n: q(w) for n, w in self.p.items()})
 
     def bytes_per_image(self, ctx, b: int) -> float:
         """Peak workspace of one packed batch of b images (the largest single call) / b."""
@@ -83,10 +92,13 @@ class Model:
                 ws.append(ctx.ws_size(M.OP_VERIFY_MATMUL, b, sizes[i + 1], sizes[i], self.k))
                 if i < 2:
                     ws.append(ctx.ws_size(M.OP_RELU, b * sizes[i + 1]))
-        else:
+        elif self.kind == "neta":
             ws = [ctx.ws_size(M.OP_VERIFY_MATMUL, b * 576, 16, 25, self.k),
                   ctx.ws_size(M.OP_VERIFY_MATMUL, b * 64, 16, 400, self.k),
-                  ctx.ws_size(M.OP_MAXPOOL2, min(b, 4) * 16, 24, 24)]
+                  ctx.ws_size(M.OP_MAXPOOL2, 32, 24, 24), ctx.ws_size(M.OP_RELU, 1 << 15)]
+        else:
+            ws = [ctx.ws_size(M.OP_VERIFY_MATMUL, b * 1024, 64, 576, self.k),
+                  ctx.ws_size(M.OP_MAXPOOL2, 42, 32, 32), ctx.ws_size(M.OP_RELU, 1 << 15)]
         return max(ws) / b
 
 
@@ -255,7 +267,7 @@ def main():
     import argparse
     import json
     ap = argparse.ArgumentParser(description="secure-inference serving run")
-    ap.add_argument("--model", choices=["mlp", "neta"], default="mlp")
+    ap.add_argument("--model", choices=["mlp", "neta", "netb"], default="mlp")
     ap.add_argument("--rate", type=float, nargs="+", default=[200.0])
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--max-b", type=int, default=256)

@@ -22,3 +22,24 @@ def test_rows_to_nchw_is_the_transpose():
     z = np.arange(B * Ho * Wo * Co)
     got = z[SC.rows_to_nchw_index(B, Co, Ho, Wo)].reshape(B, Co, Ho, Wo)
     assert np.array_equal(got, z.reshape(B, Ho, Wo, Co).transpose(0, 3, 1, 2))
+
+
+def test_padded_conv_matches_direct_convolution():
+    g = np.random.default_rng(6)
+    x = g.normal(size=(2, 3, 5, 4))
+    w = g.normal(size=(2, 3, 3, 3))
+    xp = np.pad(x, ((0, 0), (0, 0), (1, 1), (1, 1)))
+    ref = np.zeros((2, 2, 5, 4))
+    for b in range(2):
+        for o in range(2):
+            for i in range(5):
+                for j in range(4):
+                    ref[b, o, i, j] = np.sum(xp[b, :, i:i + 3, j:j + 3] * w[o])
+    assert np.allclose(SC._conv_fp64(x, w, pad=1), ref)
+
+
+def test_net_b_geometry_reaches_the_4096_flatten():
+    p = SC.net_b_params("C4-netB-weights")
+    assert p["c5"].shape == (256, 128, 3, 3) and p["f1"].shape == (4096, 512)
+    x = np.random.default_rng(7).uniform(0, 1, (2, 3, 32, 32))
+    assert SC.net_b_fp64(x, p).shape == (2, 10)

@@ -52,3 +52,19 @@ def test_secure_cnn_net_a_within_bound(mpc, path):
     ref = SC.net_a_fp64(q(x), {n: q(w) for n, w in p.items()})
     err = np.abs(got - ref)
     assert err.max() <= 2.0 ** -8, err.max()
+
+
+def test_secure_cnn_net_b_within_bound(mpc):
+    """Config C4, Net B (reading A17): five 3x3 pad-1 convs with pools after the second, fourth
+    and fifth, FC 4096-512-10; one image, He-normal weights, inputs U[0, 1)."""
+    from paper_2411_09287_gb300 import secure_cnn as SC
+    from paper_2411_09287_gb300 import secure_mlp as SM
+    from paper_2411_09287_gb300 import workloads
+    k = 13
+    p = SC.net_b_params("C4-netB-weights")
+    x = workloads.rng("C4-netB-inputs").uniform(0.0, 1.0, (1, 3, 32, 32))
+    ctx = mpc.Context(hashlib.sha256(b"mpc3-config-C4-netB").digest())
+    got = SC.net_b_secure(ctx, x, p, k)
+    q = lambda a: SM.quantized(a, k)
+    ref = SC.net_b_fp64(q(x), {n: q(w) for n, w in p.items()})
+    assert np.max(np.abs(got - ref)) <= 2.0 ** -8
