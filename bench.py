@@ -204,6 +204,15 @@ def cpu_baseline(n: int, t: int, rows: int = 2, cols: int = 32):
                       f"per process"}
 
 
+def layer_config(M: int, N: int, K: int, t: int, gemm_path: str, world: int) -> dict:
+    """The workload both arms report (identical objects, so that their lines compare)."""
+    return {"workload": f"secure GEMM {M}x{N}x{K} (M x N x K) over Z_2^64 (uniform u64 shares) + "
+                        f"Pi_Trunc^{t} + Pi_BIVerify (2 batches, trunc batch in chunks of 2^24 "
+                        f"outputs) + Pi_Rec",
+            "M": M, "N": N, "K": K, "trunc_bits": t, "gemm_path": gemm_path,
+            "parallelism": f"replicas x{world}", "l2": "inputs larger than L2"}
+
+
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
@@ -222,11 +231,11 @@ def run_reference(args, rank: int, world: int):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": steps, "warmup": warm, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"secure GEMM {M}x{N}x{K} (M x N x K) + trunc + verify + rec",
-                       "sample_rows": rows, "sample_cols": cols},
+            "config": layer_config(M, N, K, args.trunc, args.gemm_path, world),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
                              "sample": f"per step, {pool.cores} x one {rows}x{cols} output slab "
-                                       f"of the layer, one per core at once"},
+                                       f"of the layer (K = {K}), one per core at once; the rate "
+                                       f"is the slabs' plaintext-equivalent MACs per second"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -564,12 +573,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"secure GEMM {name} (M x N x K) over Z_2^64 (uniform u64 shares) + "
-                               f"Pi_Trunc^{t} + Pi_BIVerify (2 batches, trunc batch in chunks of "
-                               f"2^24 outputs) + Pi_Rec",
-                   "M": M, "N": N, "K": K, "trunc_bits": t, "gemm_path": args.gemm_path,
-                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (working set "
-                                                            f"{(wsb + 8 * 6 * (M * K + K * N + 4 * E)) / 2**30:.1f} GiB)"},
+        "config": layer_config(M, N, K, t, args.gemm_path, world),
+        "working_set_gib": round((wsb + 8 * 6 * (M * K + K * N + 4 * E)) / 2**30, 1),
         "roofline": roof,
         "rooflines": roofs,
         "phases_ms": {k: round(v, 3) for k, v in per.items() if v > 0},

@@ -80,3 +80,14 @@ def test_reference_arm_line_keeps_the_contract():
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"].startswith("secure GEMM 64x64x64")
+
+
+def test_both_arms_report_the_same_config():
+    assert bench.layer_config(8192, 8192, 8192, 13, "tc", 1) == bench.layer_config(8192, 8192, 8192, 13, "tc", 1)
+    args = bench.parse(["--impl", "reference", "--n", "64", "--steps", "1", "--warmup", "0"])
+    import contextlib, io, json
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.run_reference(args, rank=0, world=1)
+    line = json.loads(buf.getvalue().strip().splitlines()[-1])
+    assert line["config"] == bench.layer_config(64, 64, 64, 13, "tc", 1)
