@@ -602,10 +602,49 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
       launch_gr_lincomb(st, ctx->cst + CST_ONE, s.aux + 192, ctx->cst + CST_MONE, s.aux + 64, S01);
     }
   } else {
-    if ((rc = party_sums(ctx, f[0], g[0], Dh, s.Pmat, S00))) return rc;
-    if ((rc = party_sums(ctx, f[0], g[1], Dh, s.Pmat + 3 * 4096, S01))) return rc;
-    if ((rc = party_sums(ctx, f[1], g[0], Dh, s.Pmat + 6 * 4096, S10))) return rc;
-    if ((rc = party_sums(ctx, f[1], g[1], Dh, s.Pmat + 9 * 4096, S11))) return rc;
+    bool done = false;
+    if (ctx->gemm_path == MPC_GEMM_LIMB_TC) {
+      // tensor cores: the party sums of S00, S11 and S01 + S10 as Gram blocks (in S01; S10 = 0),
+      // one job per Gram term.  P0: G(x0 + x1, y0 + y1); P1: -G(x2, y3) - G(y2, x3);
+      // P2: G(x4, y4 - y5) - G(y4, x5).  A term with an absent first source takes the second's
+      // scale into its sign; a term with an absent side is zero.
+      const u64 M1 = ~0ull;
+      GramJobs jobs{};
+      jobs.off_x = 3 * 4096;
+      jobs.off_oo = 9 * 4096;
+      auto add = [&](int party, const u64* a0, const u64* a1, u64 sa1, const u64* b0,
+                     const u64* b1, u64 sb1, u64 sign) {
+        if (!a0) { a0 = a1; a1 = nullptr; sign *= sa1; }
+        if (!b0) { b0 = b1; b1 = nullptr; sign *= sb1; }
+        if (!a0 || !b0) return;
+        jobs.j[jobs.n++] = GramJob{a0, a1, sa1, b0, b1, sb1, s.Pmat + party * 4096, sign};
+      };
+      add(0, x.c[0], x.c[1], 1, y.c[0], y.c[1], 1, 1);
+      add(1, x.c[2], nullptr, 0, y.c[3], nullptr, 0, M1);
+      add(1, y.c[2], nullptr, 0, x.c[3], nullptr, 0, M1);
+      add(2, x.c[4], nullptr, 0, y.c[4], y.c[5], M1, 1);
+      add(2, y.c[4], nullptr, 0, x.c[5], nullptr, 0, M1);
+      CK(cudaMemsetAsync(s.Pmat, 0, 12 * 4096 * 8, st));
+      int nl = 0;
+      for (int q = 0; q < jobs.n; ++q) nl |= (jobs.j[q].a1 || jobs.j[q].b1) ? 2 : 1;
+      nl = (nl & 1) + (nl >> 1);   // one launch for the single-source jobs, one for the others
+      g_launches += nl;
+      {
+        Phase kp(ctx, MPC_PROF_K_GRAM, 4.0 * Dh * 4096 * jobs.n);
+        done = gram_jobs_tc(st, Dh, jobs, ctx->status, ST_TIMEOUT, ctx->tune.gram_split) == 0;
+      }
+      if (done) {
+        launch_gr_fold_reduce(st, s.Pmat, 12, s.S);   // S00 | S01 + S10 | 0 | S11
+      } else {
+        g_launches -= nl;
+      }
+    }
+    if (!done) {
+      if ((rc = party_sums(ctx, f[0], g[0], Dh, s.Pmat, S00))) return rc;
+      if ((rc = party_sums(ctx, f[0], g[1], Dh, s.Pmat + 3 * 4096, S01))) return rc;
+      if ((rc = party_sums(ctx, f[1], g[0], Dh, s.Pmat + 6 * 4096, S10))) return rc;
+      if ((rc = party_sums(ctx, f[1], g[1], Dh, s.Pmat + 9 * 4096, S11))) return rc;
+    }
   }
   launch_gr_quad_combine(st, ctx->cst + CST_LAM, S00, S01, S10, S11, Sh2);
   const u64 obj = make_obj(vid, batch, (u32)k);
@@ -861,9 +900,59 @@ RecPlan plan_rec(Arena& a, long long n, bool need_out) {
   return p;
 }
 
+// A table of powers r^i, i < n (rows of 64 words): rows below L by repeated multiplication, row
+// h L + l (h >= 1) = r^(hL) r^l, all of them one grouped GR-matrix product (matrix h - 1 for the
+// rows L h .. L h + L - 1).  L is a multiple of 128 near sqrt(n).
+struct PowPlan {
+  long long n, L, nhi;
+  u64* Thi;   // r^(hL), h < nhi
+  u64* Mhi;   // multiplication matrices of r^(hL), h = 1 .. nhi - 1
+};
+
+PowPlan plan_pow(Arena& a, long long n) {
+  PowPlan p;
+  p.n = n;
+  long long L = 1024;
+  while (L * L < n) L += 128;
+  p.L = L;
+  p.nhi = (n + L - 1) / L;
+  p.Thi = a.take<u64>(p.nhi * 64);
+  p.Mhi = a.take<u64>(std::max<long long>(p.nhi - 1, 1) * 4096);
+  return p;
+}
+
+// table[i] = r^i for i < p.n; aux: 64 words of scratch
+int power_table(mpc_ctx* ctx, const u64* r, const PowPlan& p, u64* table, u64* aux) {
+  cudaStream_t st = ctx->st;
+  if (ctx->gemm_path != MPC_GEMM_LIMB_TC || p.nhi <= 1) {
+    launch_gr_powers(st, r, p.n, table);
+    return MPC_OK;
+  }
+  launch_gr_powers(st, r, p.L, table);
+  launch_gr_mul1(st, table + (p.L - 1) * 64, r, aux);                 // r^L
+  launch_gr_powers(st, aux, p.nhi, p.Thi);
+  launch_gr_mulmat_batch(st, p.nhi - 1, p.Thi + 64, 64, p.Mhi);
+  GrMMArgs g = grargs(ctx);
+  g.R = (p.nhi - 1) * p.L;
+  g.p0 = table;
+  g.in = GrRowMap{p.L, 64, 0};
+  g.Mmat = p.Mhi;
+  g.mrows = p.L;
+  g.out = table + p.L * 64;
+  g.om = GrRowMap{0, 64, 0};
+  g.out_lim = (p.n - p.L) * 64;
+  g_launches += 1;
+  Phase kp(ctx, MPC_PROF_K_GR_MATMUL, (double)(p.n - p.L) * 4096);
+  if (gr_matmul_tc_ex(st, g, ctx->status, ST_TIMEOUT) == 0) return MPC_OK;
+  g_launches -= 1;
+  launch_gr_powers(st, r, p.n, table);
+  return MPC_OK;
+}
+
 struct VMultPlan {
   Small s;
   u64* pw;
+  PowPlan pp;
   Dense dv;
   IVBuf iv;
   int R;
@@ -874,6 +963,7 @@ VMultPlan plan_vmult(Arena& a, long long n, int R) {
   p.R = R < 0 ? default_R(n) : R;
   p.s = plan_small(a);
   p.pw = a.take<u64>(n * 64);
+  p.pp = plan_pow(a, n);
   const bool all[6] = {true, true, true, true, true, true};
   p.dv = plan_dense(a, n, all, all);
   p.iv = plan_iv(a, dim_after(n, p.R));
@@ -1843,7 +1933,8 @@ int verify_mult_body(mpc_ctx* ctx, uint64_t verify_id, const u64* xs, const u64*
   const Small& s = p.s;
   // Pi_Tran (Fig. MTP): reveal r; x'_i = r^i x_i; y lifted; z = sum r^i z_i
   reveal(ctx, P_VER_R, make_obj(verify_id, 0, 0), s.tmp6, s.r);
-  launch_gr_powers(st, s.r, n, p.pw);
+  int rc;
+  if ((rc = power_table(ctx, s.r, p.pp, p.pw, s.aux))) return rc;
   Vec& x = p.dv.x[0];
   Vec& y = p.dv.y[0];
   for (int c = 0; c < 6; ++c) {
@@ -2745,7 +2836,7 @@ int verify_nl(mpc_ctx* ctx, u64 vid, NLPlan& p, u64* trace) {
     const Small& s = v.s;
     const long long n = p.nm;
     reveal(ctx, P_VER_R, make_obj(vid, 0, 0), s.tmp6, s.r);
-    launch_gr_powers(st, s.r, n, v.pw);
+    if ((rc = power_table(ctx, s.r, v.pp, v.pw, s.aux))) return rc;
     Vec& x = v.dv.x[0];
     Vec& y = v.dv.y[0];
     for (int c = 0; c < 6; ++c) {

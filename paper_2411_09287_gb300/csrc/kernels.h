@@ -101,6 +101,32 @@ struct GrMMArgs {
 };
 int gr_matmul_tc_ex(cudaStream_t st, const GrMMArgs& a, unsigned* err, unsigned err_flag);
 
+// One job of a batched tensor-core Gram launch.  u = a0 + sa1 a1 and v = b0 + sb1 b1 (a1, b1 may
+// be null; every pointer 16-byte aligned) are vectors of GR elements (rows of 64 words,
+// contiguous); over their Dh element pairs (2i, 2i + 1) the job adds, mod 2^64,
+//   P[0] += sign G(u_e, v_e),  P[off_oo] += sign G(u_o, v_o),  P[off_x] += sign (G(u_e, v_o) + G(u_o, v_e))
+// with G(u, v)[a][b] = sum_i u_i[a] v_i[b] a 64 x 64 block.
+struct GramJob {
+  const u64* a0;
+  const u64* a1;
+  u64 sa1;
+  const u64* b0;
+  const u64* b1;
+  u64 sb1;
+  u64* P;
+  u64 sign;
+};
+constexpr int GRAM_JOBS_MAX = 8;
+struct GramJobs {
+  GramJob j[GRAM_JOBS_MAX];
+  int n;
+  long long off_oo, off_x;   // word offsets of the odd-odd and cross blocks from a job's P
+};
+// Every job of `jobs`: one launch for the single-source jobs and one for those with a second
+// source (nsplit: CTAs per parity shared by a launch's jobs, 0 = half the SMs).  Returns -1 for a
+// bad job (null or misaligned pointers), 0 otherwise.
+int gram_jobs_tc(cudaStream_t st, long long Dh, const GramJobs& jobs, unsigned* err,
+                 unsigned err_flag, int nsplit = 0);
 // P[0..2] (3 x 4096 words, accumulated mod 2^64) += the Gram sums G(x_e, y_e), G(x_o, y_o),
 // G(x_e, y_o) + G(x_o, y_e) over the Dh element pairs (x_{2i}, x_{2i+1}) of x and y (rows of 64
 // words, contiguous).  Exact, on the tensor cores; returns -1 for misaligned inputs.

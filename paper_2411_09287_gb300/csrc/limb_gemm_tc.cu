@@ -1352,19 +1352,19 @@ k_gr_matmul_tm(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ 
 }
 
 // ---- Gram sums of the dense Pi_Reduce rounds -------------------------------------------------
-// For vectors x, y of n = 2 Dh GR elements (rows of 64 words, element i at row i), the three P0
-// sums of a round in the truncation batch's form:
-//   P[0] += G(x_even, y_even), P[1] += G(x_odd, y_odd), P[2] += G(x_even, y_odd) + G(x_odd, y_even)
-// with G(u, v)[a][b] = sum_i u_i[a] v_i[b] (each P[g] a 64 x 64 matrix, mod 2^64).  The MMA tile
-// is M = 128 (rows a: x_even coefficients, then x_odd) x N = 64 (y of one parity, blockIdx.y) with
-// K = the element pairs i, split across blockIdx.x; each CTA adds its partial tile atomically.
-// Producers split x and y rows into digit planes transposed to K-major; MMA issue and drains as in
-// k_limb_gemm_tc; the drain warps accumulate over all of the CTA's chunks.
+// For vectors u, v of n = 2 Dh GR elements (rows of 64 words, element i at row i) a job adds
+//   P[ee] += s G(u_even, v_even), P[oo] += s G(u_odd, v_odd), P[x] += s (G(u_even, v_odd) + G(u_odd, v_even))
+// with G(u, v)[a][b] = sum_i u_i[a] v_i[b] (each block a 64 x 64 matrix, mod 2^64) and s the job's
+// sign; u = a0 + sa1 a1 and v = b0 + sb1 b1 (a1, b1 may be absent).  The MMA tile is M = 128
+// (rows a: u_even coefficients, then u_odd) x N = 64 (v of one parity, blockIdx.y) with K = the
+// element pairs i, split across blockIdx.x; blockIdx.z is the job; each CTA adds its partial tile
+// atomically.  Producers combine and split the rows into digit planes transposed to K-major; MMA
+// issue and drains as in k_limb_gemm_tc; the drain warps accumulate over all of the CTA's chunks.
 constexpr size_t GR_SMEM = (size_t)NSTAGE * STAGE + 1024;   // 2 x (64 KB A + 32 KB B)
 
+template <bool GEN>
 __global__ void __launch_bounds__(GM_THREADS, 1)
-k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u64* __restrict__ P,
-          unsigned* __restrict__ err, unsigned err_flag) {
+k_gram_tc(long long Dh, const GramJobs jobs, unsigned* __restrict__ err, unsigned err_flag) {
   extern __shared__ unsigned char dsm[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
@@ -1374,6 +1374,9 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
   __shared__ int abort_flag;
   volatile int* abort = &abort_flag;
 
+  const GramJob& J = jobs.j[blockIdx.z];
+  const u64* __restrict__ x = J.a0;
+  const u64* __restrict__ y = J.b0;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int par = blockIdx.y;                      // parity of y in this CTA's tile
@@ -1413,12 +1416,17 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
     constexpr int NITEM = 768;
     // rounds of NQ items per thread, RPU rounds per unit; the loads of round k + 1 are in flight
     // while round k is split into the stage, across unit ends
-    constexpr int NQ = 2;
+    // (one item per round with a second source, whose words need registers of their own)
+    constexpr int NQ = GEN ? 1 : 2;
+    constexpr int NQ2 = GEN ? NQ : 1;
     constexpr int RPU = (NITEM + NQ * GM_PROD * 32 - 1) / (NQ * GM_PROD * 32);
     const long long nrounds = nunits * RPU;
     bool ok = true;
     u64 cv[NQ][8], nv[NQ][8];
-    auto issue = [&](long long k, u64 (&v)[NQ][8]) {
+    u64 cv2[NQ2][8], nv2[NQ2][8];
+    const u64* __restrict__ x1 = GEN ? J.a1 : nullptr;
+    const u64* __restrict__ y1 = GEN ? J.b1 : nullptr;
+    auto issue = [&](long long k, u64 (&v)[NQ][8], u64 (&v2)[NQ2][8]) {
       const long long u = k / RPU;
       const int r = (int)(k - u * RPU);
       const long long i0 = (c0 + u) * TC_BK;   // first element pair of the chunk
@@ -1430,20 +1438,29 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
         const int row = isA ? (it & 127) : (it & 63);
         const int k8 = isA ? (it >> 7) : (it >> 6);
         // A row a: coefficient a % 64 of x_{2i + a / 64}; B row b: coefficient b of y_{2i + par}
-        const u64* src = isA ? x + (row >> 6) * 64 + (row & 63) : y + par * 64 + row;
+        const long long roff = isA ? (row >> 6) * 64 + (row & 63) : par * 64 + row;
+        const u64* src = (isA ? x : y) + roff;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const long long i = i0 + k8 * 8 + j;
           v[q][j] = (item < NITEM && i < Dh) ? src[i * 128] : 0ull;
         }
+        if (GEN) {
+          const u64* s2 = isA ? x1 : y1;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const long long i = i0 + k8 * 8 + j;
+            v2[q][j] = (s2 && item < NITEM && i < Dh) ? s2[roff + i * 128] : 0ull;
+          }
+        }
       }
     };
-    if (nrounds > 0) issue(0, cv);
+    if (nrounds > 0) issue(0, cv, cv2);
     for (long long k = 0; k < nrounds; ++k) {
       const long long u = k / RPU;
       const int r = (int)(k - u * RPU);
       const int st = (int)(u % NSTAGE);
-      if (k + 1 < nrounds) issue(k + 1, nv);
+      if (k + 1 < nrounds) issue(k + 1, nv, nv2);
       if (r == 0) {
         if (u >= NSTAGE &&
             !(ok = __all_sync(0xffffffffu,
@@ -1467,6 +1484,11 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
           const int it = isA ? item : item - 512;
           unsigned char* dst = isA ? As : As + 8 * A_TILE;
           const int off = isA ? sw64_off(it & 127, it >> 7) : sw64_off(it & 63, it >> 6);
+          if (GEN) {
+            const u64 sc = isA ? J.sa1 : J.sb1;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) cv[q][j] += sc * cv2[q][j];
+          }
           split8_store(cv[q], dst, isA ? A_TILE : B_TILE, off);
         }
       }
@@ -1478,7 +1500,10 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
 #pragma unroll
       for (int q = 0; q < NQ; ++q)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) cv[q][j] = nv[q][j];
+        for (int j = 0; j < 8; ++j) {
+          cv[q][j] = nv[q][j];
+          if (GEN) cv2[q][j] = nv2[q][j];
+        }
     }
     if (!ok && lane == 0) fail();
   } else if (warp == GM_NDRAIN + GM_PROD) {
@@ -1536,11 +1561,13 @@ k_gram_tc(long long Dh, const u64* __restrict__ x, const u64* __restrict__ y, u6
     if (ok && !*abort && nunits > 0) {
       const int a = q4 * 32 + lane;                // tile row: x parity a / 64, coefficient a % 64
       const int xpar = a >> 6;
-      // (x parity, y parity) -> P block: (0,0) -> 0, (1,1) -> 1, mixed -> 2
-      u64* dst = P + (xpar == par ? xpar : 2) * 4096 + (a & 63) * 64 + h * GM_DC;
+      // (x parity, y parity) -> P block: (0,0) -> ee, (1,1) -> oo, mixed -> cross
+      const long long blk = xpar != par ? jobs.off_x : (xpar ? jobs.off_oo : 0);
+      u64* dst = J.P + blk + (a & 63) * 64 + h * GM_DC;
+      const u64 sg = J.sign;
 #pragma unroll
       for (int c = 0; c < GM_DC; ++c)
-        atomicAdd(reinterpret_cast<unsigned long long*>(dst + c), (unsigned long long)acc[c]);
+        atomicAdd(reinterpret_cast<unsigned long long*>(dst + c), (unsigned long long)(sg * acc[c]));
     } else if (!ok && lane == 0) {
       fail();
     }
@@ -1725,10 +1752,24 @@ int gr_matmul_tc(cudaStream_t st, long long R, const u64* p0, const u64* p1, u64
   return gr_matmul_tc_ex(st, a, err, err_flag);
 }
 
-int gram3_tc(cudaStream_t st, long long Dh, const u64* x, const u64* y, u64* P, unsigned* err,
-             unsigned err_flag, int nsplit) {
-  if (Dh <= 0) return 0;
-  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) return -1;
+int gram_jobs_tc(cudaStream_t st, long long Dh, const GramJobs& jobs, unsigned* err,
+                 unsigned err_flag, int nsplit) {
+  if (Dh <= 0 || jobs.n <= 0) return 0;
+  if (jobs.n > GRAM_JOBS_MAX) return -1;
+  // single-source jobs run in the kernel that keeps two items in flight per producer thread,
+  // jobs with a second source in the one that holds both sources' words
+  GramJobs one{}, two{};
+  one.off_oo = two.off_oo = jobs.off_oo;
+  one.off_x = two.off_x = jobs.off_x;
+  for (int q = 0; q < jobs.n; ++q) {
+    const GramJob& J = jobs.j[q];
+    if (!J.a0 || !J.b0 || !J.P) return -1;
+    if ((reinterpret_cast<uintptr_t>(J.a0) | reinterpret_cast<uintptr_t>(J.b0) |
+         reinterpret_cast<uintptr_t>(J.a1) | reinterpret_cast<uintptr_t>(J.b1)) & 15)
+      return -1;
+    GramJobs& dst = (J.a1 || J.b1) ? two : one;
+    dst.j[dst.n++] = J;
+  }
   static int nsm = 0;
   if (!nsm) {
     int dev = 0;
@@ -1737,12 +1778,33 @@ int gram3_tc(cudaStream_t st, long long Dh, const u64* x, const u64* y, u64* P, 
     if (nsm <= 0) nsm = 148;
   }
   const long long nch = (Dh + TC_BK - 1) / TC_BK;
-  long long split = nsplit > 0 ? nsplit : nsm / 2;
-  if (split > nch) split = nch;
-  if (split < 1) split = 1;
-  set_max_dynamic_smem(reinterpret_cast<const void*>(k_gram_tc), (int)GR_SMEM);
-  k_gram_tc<<<dim3((unsigned)split, 2), GM_THREADS, GR_SMEM, st>>>(Dh, x, y, P, err, err_flag);
+  // CTAs per job and parity: nsplit (nsm / 2 by default) shared by the jobs of a launch
+  auto grid_of = [&](int n) {
+    long long split = nsplit > 0 ? nsplit : nsm / 2;
+    split /= n;
+    if (split > nch) split = nch;
+    if (split < 1) split = 1;
+    return dim3((unsigned)split, 2, (unsigned)n);
+  };
+  if (one.n) {
+    set_max_dynamic_smem(reinterpret_cast<const void*>(k_gram_tc<false>), (int)GR_SMEM);
+    k_gram_tc<false><<<grid_of(one.n), GM_THREADS, GR_SMEM, st>>>(Dh, one, err, err_flag);
+  }
+  if (two.n) {
+    set_max_dynamic_smem(reinterpret_cast<const void*>(k_gram_tc<true>), (int)GR_SMEM);
+    k_gram_tc<true><<<grid_of(two.n), GM_THREADS, GR_SMEM, st>>>(Dh, two, err, err_flag);
+  }
   return 0;
+}
+
+int gram3_tc(cudaStream_t st, long long Dh, const u64* x, const u64* y, u64* P, unsigned* err,
+             unsigned err_flag, int nsplit) {
+  GramJobs jobs{};
+  jobs.n = 1;
+  jobs.off_oo = 4096;
+  jobs.off_x = 2 * 4096;
+  jobs.j[0] = GramJob{x, nullptr, 0ull, y, nullptr, 0ull, P, 1ull};
+  return gram_jobs_tc(st, Dh, jobs, err, err_flag, nsplit);
 }
 
 }  // namespace mpc3

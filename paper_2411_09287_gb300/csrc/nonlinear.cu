@@ -230,7 +230,7 @@ __global__ void k_b2a_apply(const u64* __restrict__ dbits, const u64* __restrict
 }
 
 // ---- GF(2^64) ------------------------------------------------------------------------------
-__device__ __forceinline__ u64 gf_mul(u64 a, u64 b) {
+__host__ __device__ __forceinline__ u64 gf_mul(u64 a, u64 b) {
   u64 lo = 0, hi = 0;
 #pragma unroll 8
   for (int i = 0; i < 64; ++i) {
@@ -245,7 +245,7 @@ __device__ __forceinline__ u64 gf_mul(u64 a, u64 b) {
   return lo;
 }
 
-__device__ u64 gf_pow(u64 a, unsigned long long e) {
+__host__ __device__ u64 gf_pow(u64 a, unsigned long long e) {
   u64 r = 1;
   while (e) {
     if (e & 1) r = gf_mul(r, a);
@@ -255,7 +255,7 @@ __device__ u64 gf_pow(u64 a, unsigned long long e) {
   return r;
 }
 
-__device__ __forceinline__ u64 gf_inv(u64 a) { return gf_pow(a, ~0ull - 1ull); }   // a^(2^64 - 2)
+__host__ __device__ __forceinline__ u64 gf_inv(u64 a) { return gf_pow(a, ~0ull - 1ull); }   // a^(2^64 - 2)
 
 // out[i] = r^i for i < n: each thread computes 64 consecutive powers
 __global__ void k_gf_powers(const u64* __restrict__ rp, long long n, u64* __restrict__ out) {
@@ -423,12 +423,16 @@ __global__ void k_gf_rec1(const u64* __restrict__ s6, u64 xor_mask, u64* __restr
 // Lagrange weights at the points 0, 1, x (reading A6/X) over GF(2^64):
 // L0 = (z - 1)(z - x) / x, L1 = z (z - x) / (1 - x), L2 = z (z - 1) / (x (x - 1)).
 // coef: [0] zeta, [1] L0, [2] L1, [3] L2, [4] 1 + x (the fold weight of f(0) at the point x).
-__global__ void k_gf_lagrange(const u64* __restrict__ zp, u64* __restrict__ coef) {
+// The three denominators are constants: their inverses (inv[0..2]) come from the host.
+struct GfLagInv {
+  u64 v[3];
+};
+__global__ void k_gf_lagrange(const u64* __restrict__ zp, u64* __restrict__ coef, GfLagInv inv) {
   const u64 z = *zp, x = 2ull, one = 1ull;
   coef[0] = z;
-  coef[1] = gf_mul(gf_mul(z ^ one, z ^ x), gf_inv(x));
-  coef[2] = gf_mul(gf_mul(z, z ^ x), gf_inv(one ^ x));
-  coef[3] = gf_mul(gf_mul(z, z ^ one), gf_inv(gf_mul(x, x ^ one)));
+  coef[1] = gf_mul(gf_mul(z ^ one, z ^ x), inv.v[0]);
+  coef[2] = gf_mul(gf_mul(z, z ^ x), inv.v[1]);
+  coef[3] = gf_mul(gf_mul(z, z ^ one), inv.v[2]);
   coef[4] = one ^ x;
 }
 
@@ -633,7 +637,11 @@ void launch_gf_rec1(cudaStream_t st, const u64* s6, u64 xor_mask, u64* out, u32*
   k_gf_rec1<<<1, 1, 0, st>>>(s6, xor_mask, out, status, flag);
 }
 void launch_gf_lagrange(cudaStream_t st, const u64* zeta, u64* coef) {
-  k_gf_lagrange<<<1, 1, 0, st>>>(zeta, coef);
+  static const GfLagInv inv = [] {
+    const u64 x = 2ull, one = 1ull;
+    return GfLagInv{{gf_inv(x), gf_inv(one ^ x), gf_inv(gf_mul(x, x ^ one))}};
+  }();
+  k_gf_lagrange<<<1, 1, 0, st>>>(zeta, coef, inv);
 }
 void launch_gf_combine_z(cudaStream_t st, const u64* coef, const u64* h0, const u64* h2, const u64* z,
                          u64* zo) {
