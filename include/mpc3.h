@@ -382,9 +382,11 @@ int mpc_gather(mpc_ctx* ctx, const uint64_t* xs, int64_t n_in, const int64_t* id
  *     element), Delta = x - r opened with Pi_Rec, msb(x) from a depth-6 parallel-prefix carry
  *     circuit of AND gates (Boolean Pi_Mult over Z_2, 125 per element), B2A of NOT msb with a
  *     daBit (two Pi_Mult), and one Pi_Mult (x - y) [x >= y];
- *   - then Pi_MultVerify of every arithmetic product (batch 0) and Pi_BIVerify of the edaBit
- *     inner products (batch 1) over GR(2^64, 64), and Pi_MultVerify of every AND gate over
- *     GF(2^64) = GR(2, 64) (batch 2).
+ *   - then Pi_MultVerify of the daBit and final products (batch 0, 3 per element) and
+ *     Pi_BIVerify of the edaBit inner products (batch 1) over GR(2^64, 64), Pi_MultVerify of
+ *     every AND gate over GF(2^64) = GR(2, 64) (batch 2), and Pi_MultVerify of the edaBit bit
+ *     products over GR(2^64, 64) (batch 3, 64 per element; a batch of its own, so that its
+ *     vectors keep the form in which only P0's Gram sum is non-zero).
  * Elements are processed in groups padded to n_pad = 64 ceil(n / 64); Boolean values are
  * bit-sliced.  Returns MPC_OK (verified), MPC_ERR_VERIFY, MPC_ERR_ABORT (a Pi_Rec mismatch).
  *   xs: device sharing of n elements (6 n words, read); out: 6 n words (written);
@@ -392,7 +394,7 @@ int mpc_gather(mpc_ctx* ctx, const uint64_t* xs, int64_t n_in, const int64_t* id
  *   trace (optional, device, zero-filled by the caller): per batch, R + 1 blocks as for
  *     mpc_verify_mult for batches 0 and 1 (R = max(0, ceil(log2 D) - 6), D = products / entries),
  *     then (R2 + 1) blocks of MPC_TRACE_GF_ROUND words for batch 2: zeta', h0 (6), h2 (6) per
- *     round and Delta. */
+ *     round and Delta, then R3 + 1 blocks as for mpc_verify_mult for batch 3. */
 #define MPC_TRACE_GF_ROUND 13
 int mpc_relu(mpc_ctx* ctx, uint64_t call_id, uint64_t verify_id, const uint64_t* xs, int64_t n,
              uint64_t* out, void* workspace, size_t workspace_bytes, uint64_t* trace);

@@ -13,6 +13,11 @@ Conventions (readings, also in the design notes):
     max-pool comparison, 1 for the second; sub = circuit level for the AND gates.
   - The Boolean AND gates are verified in GF(2^64) with verify batch 2, so that their challenges
     never share a stream with the arithmetic batches 0 (products) and 1 (edaBit inner products).
+  - Reading N8: the edaBit bit products b_{i,1} b_{i,2} (64 per element) are verified in a batch
+    of their own (verify batch 3) and batch 0 keeps the daBit and final products (3 per element).
+    Every product is still checked with a fresh challenge; splitting one Pi_MultVerify batch into
+    two adds their soundness errors (union bound).  The bit batch has the truncation pairs' form:
+    x carries only [r]_1 (P0, P1 copies) and y only [r]_2 (P0, P2 copies).
 """
 from __future__ import annotations
 
@@ -26,6 +31,7 @@ from .verify import BATCH_MAIN, bi_verify, challenge_r, lift_shared, tran_mult, 
 U64 = np.uint64
 BATCH_EDA_INNER = 1
 BATCH_BOOL = 2
+BATCH_EDA_MULT = 3
 
 
 def n_padded(n: int) -> int:
@@ -198,7 +204,7 @@ def compare_select(sess: Session, bsess: Session, a: Shared, b: Shared, call_id:
     ge_a = b2a(sess, bsess, ge, (da_ra, da_rb), call_id)
     prod = mult(sess, d, ge_a, call_id, P_NL_MULT, stage)
     out = s_add(b, prod)
-    return out, {"mults": eda_mults + da_mults + [(d, ge_a, prod)], "inner": eda_inner,
+    return out, {"mults": da_mults + [(d, ge_a, prod)], "eda": eda_mults, "inner": eda_inner,
                  "and": and_triples}
 
 
@@ -258,15 +264,17 @@ def tran_rows(sess: Session, X: Shared, Y: Shared, Z: Shared, r) -> tuple:
 
 
 def verify_layer(sess: Session, bsess: Session, triples, verify_id: int, R_mult=None,
-                 R_inner=None, R_and=None, trace=None) -> bool:
-    """Pi_MultVerify of every arithmetic product (batch 0), Pi_BIVerify of the edaBit inner
-    products (batch 1), both over GR(2^64, 64), and Pi_MultVerify of every AND gate over GF(2^64)
-    (batch 2) (Sec. 4.3: products over Z_2^l and Z_2 verified in their rings).  `trace`, if given,
-    is a dict of three lists."""
+                 R_inner=None, R_and=None, trace=None, R_eda=None) -> bool:
+    """Pi_MultVerify of the daBit and final products (batch 0), Pi_BIVerify of the edaBit inner
+    products (batch 1), both over GR(2^64, 64), Pi_MultVerify of every AND gate over GF(2^64)
+    (batch 2) (Sec. 4.3: products over Z_2^l and Z_2 verified in their rings), and Pi_MultVerify
+    of the edaBit bit products over GR(2^64, 64) (batch 3, reading N8).  `trace`, if given, is a
+    dict of four lists."""
     mults = [t for tr in triples for t in tr["mults"]]
+    edas = [t for tr in triples for t in tr["eda"]]
     inner = [t for tr in triples for t in tr["inner"]]
     ands = [t for tr in triples for t in tr["and"]]
-    tr = trace if trace is not None else {"mult": None, "inner": None, "and": None}
+    tr = trace if trace is not None else {"mult": None, "inner": None, "and": None, "eda": None}
     X, Y, Z = (_flat_concat(mults, k) for k in range(3))
     r = challenge_r(sess, verify_id, BATCH_MAIN)
     ok0 = bi_verify(sess, *tran_mult(sess, X, Y, Z, r), verify_id, BATCH_MAIN, R_mult, tr["mult"])
@@ -280,4 +288,8 @@ def verify_layer(sess: Session, bsess: Session, triples, verify_id: int, R_mult=
     r2 = challenge_r(bsess, verify_id, BATCH_BOOL)
     ok2 = bi_verify(bsess, *tran_mult(bsess, Xa, Ya, Za, r2), verify_id, BATCH_BOOL, R_and,
                     tr["and"])
-    return bool(ok0 and ok1 and ok2)
+    Xe, Ye, Ze = (_flat_concat(edas, k) for k in range(3))
+    r3 = challenge_r(sess, verify_id, BATCH_EDA_MULT)
+    ok3 = bi_verify(sess, *tran_mult(sess, Xe, Ye, Ze, r3), verify_id, BATCH_EDA_MULT, R_eda,
+                    tr["eda"])
+    return bool(ok0 and ok1 and ok2 and ok3)

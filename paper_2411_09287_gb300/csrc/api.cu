@@ -2772,6 +2772,14 @@ struct NLPlan {
   u64** ydev;                    // 6 device pointers (kernel argument)
   // batch 2: AND gates
   GfPlan gf;
+  // batch 3: edaBit bit products (nb = 64 sum np), x only [r]_1 and y only [r]_2 (reading N8)
+  long long nb;
+  int Rb;
+  Small sb;
+  PowPlan ppb;
+  u64* pwb;
+  Dense db;
+  IVBuf ivb;
 };
 
 NLPlan plan_nl(Arena& a, int nst, const long long np[2]) {
@@ -2785,7 +2793,7 @@ NLPlan plan_nl(Arena& a, int nst, const long long np[2]) {
     p.b[s] = a.take<u64>(6 * np[s]);
     p.o[s] = a.take<u64>(6 * np[s]);
     p.cs[s] = plan_cs(a, np[s]);
-    p.nm += 67 * np[s];
+    p.nm += 3 * np[s];
     p.ne += np[s];
     andw += p.cs[s].and_words;
   }
@@ -2801,6 +2809,15 @@ NLPlan plan_nl(Arena& a, int nst, const long long np[2]) {
   p.iv1 = plan_iv(a, dim_after(p.D1, p.R1));
   p.ydev = a.take<u64*>(6);
   p.gf = plan_gf(a, andw, -1);
+  p.nb = 64 * p.ne;
+  p.Rb = default_R(p.nb);
+  p.sb = plan_small(a);
+  p.pwb = a.take<u64>(p.nb * 64);
+  p.ppb = plan_pow(a, p.nb);
+  const bool bx[6] = {true, false, false, true, false, false};
+  const bool by[6] = {false, true, false, false, false, true};
+  p.db = plan_dense(a, p.nb, bx, by);
+  p.ivb = plan_iv(a, dim_after(p.nb, p.Rb));
   return p;
 }
 
@@ -2815,16 +2832,14 @@ int append_sharing(mpc_ctx* ctx, const u64* src, long long n, u64* dst, long lon
 int verify_nl(mpc_ctx* ctx, u64 vid, NLPlan& p, u64* trace) {
   int rc;
   cudaStream_t st = ctx->st;
-  // ---- batch 0: every arithmetic Pi_Mult, in the order edaBit products, daBit products (two),
-  // final product, stage by stage
+  // ---- batch 0: the daBit products (two) and the final product, stage by stage (the edaBit
+  // bit products are batch 3)
   long long off = 0;
   for (int s = 0; s < p.nst; ++s) {
     CSPlan& c = p.cs[s];
-    const long long N = 64 * c.np;
-    const u64* trip[4][3] = {{c.B1, c.B2, c.eprod}, {c.A1, c.A2, c.t}, {c.rpd, c.A3, c.u},
-                             {c.d, c.gea, c.prod}};
-    const long long len[4] = {N, c.np, c.np, c.np};
-    for (int q = 0; q < 4; ++q) {
+    const u64* trip[3][3] = {{c.A1, c.A2, c.t}, {c.rpd, c.A3, c.u}, {c.d, c.gea, c.prod}};
+    const long long len[3] = {c.np, c.np, c.np};
+    for (int q = 0; q < 3; ++q) {
       if ((rc = append_sharing(ctx, trip[q][0], len[q], p.MX, p.nm, off))) return rc;
       if ((rc = append_sharing(ctx, trip[q][1], len[q], p.MY, p.nm, off))) return rc;
       if ((rc = append_sharing(ctx, trip[q][2], len[q], p.MZ, p.nm, off))) return rc;
@@ -2886,6 +2901,30 @@ int verify_nl(mpc_ctx* ctx, u64 vid, NLPlan& p, u64* trace) {
       }
     }
     if ((rc = gf_verify(ctx, vid, g, tr2))) return rc;
+  }
+  u64* tr3 = tr2 ? tr2 + (long long)(p.gf.R + 1) * MPC_TRACE_GF_ROUND : nullptr;
+  // ---- batch 3: the edaBit bit products b_{i,1} b_{i,2}, stage by stage (plane-major); x has
+  // only the [r]_1 components and y only the [r]_2 ones, so the dense rounds take the
+  // single-Gram form
+  {
+    const Small& s = p.sb;
+    reveal(ctx, P_VER_R, make_obj(vid, 3, 0), s.tmp6, s.r);
+    if ((rc = power_table(ctx, s.r, p.ppb, p.pwb, s.aux))) return rc;
+    Vec& x = p.db.x[0];
+    Vec& y = p.db.y[0];
+    CK(cudaMemsetAsync(s.zinit, 0, 384 * 8, st));
+    long long e0 = 0;
+    for (int q = 0; q < p.nst; ++q) {
+      CSPlan& c = p.cs[q];
+      const long long N = 64 * c.np;
+      for (int comp : {0, 3})
+        launch_gr_scale_rows(st, p.pwb + e0 * 64, c.B1 + comp * N, N, x.c[comp] + e0 * 64);
+      for (int comp : {1, 5}) launch_gr_lift(st, c.B2 + comp * N, N, y.c[comp] + e0 * 64);
+      launch_scalar_gr_sum(st, N, c.eprod, N, 6, p.pwb + e0 * 64, s.zinit);
+      e0 += N;
+    }
+    p.db.cur = 0;
+    if ((rc = run_dense(ctx, vid, 3, p.db, p.nb, s.zinit, 1, p.Rb, s, p.ivb, tr3))) return rc;
   }
   return MPC_OK;
 }

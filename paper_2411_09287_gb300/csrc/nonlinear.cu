@@ -230,14 +230,34 @@ __global__ void k_b2a_apply(const u64* __restrict__ dbits, const u64* __restrict
 }
 
 // ---- GF(2^64) ------------------------------------------------------------------------------
+// 32 x 32 -> 64-bit carry-less product from integer multiplies on bits spaced 4 apart (the
+// "multiplication with holes" of T. Pornin's constant-time GHASH): with x_k = x & (0x11111111 << k),
+// the integer product x_i y_j has partial-product bits only in the columns p = i + j (mod 4),
+// at most 8 in a column, so each column count fits in the 4 bits p .. p + 3 and bit p is its
+// parity.  The XOR of the four products with i + j = k (mod 4), kept at those columns, gives the
+// carry-less product's bits there.
+__host__ __device__ __forceinline__ u64 clmul32(unsigned x, unsigned y) {
+  const unsigned m = 0x11111111u;
+  const unsigned x0 = x & m, x1 = x & (m << 1), x2 = x & (m << 2), x3 = x & (m << 3);
+  const unsigned y0 = y & m, y1 = y & (m << 1), y2 = y & (m << 2), y3 = y & (m << 3);
+  auto mw = [](unsigned a, unsigned b) { return (u64)a * (u64)b; };
+  const u64 z0 = mw(x0, y0) ^ mw(x1, y3) ^ mw(x2, y2) ^ mw(x3, y1);
+  const u64 z1 = mw(x0, y1) ^ mw(x1, y0) ^ mw(x2, y3) ^ mw(x3, y2);
+  const u64 z2 = mw(x0, y2) ^ mw(x1, y1) ^ mw(x2, y0) ^ mw(x3, y3);
+  const u64 z3 = mw(x0, y3) ^ mw(x1, y2) ^ mw(x2, y1) ^ mw(x3, y0);
+  const u64 M = 0x1111111111111111ull;
+  return (z0 & M) | (z1 & (M << 1)) | (z2 & (M << 2)) | (z3 & (M << 3));
+}
+
+// a b in GF(2^64) = GF(2)[x] / (x^64 + x^4 + x^3 + x + 1): the 128-bit carry-less product by one
+// Karatsuba step over 32-bit halves, then the reduction
 __host__ __device__ __forceinline__ u64 gf_mul(u64 a, u64 b) {
-  u64 lo = 0, hi = 0;
-#pragma unroll 8
-  for (int i = 0; i < 64; ++i) {
-    const u64 m = 0ull - ((b >> i) & 1ull);
-    lo ^= (a << i) & m;
-    hi ^= (i ? (a >> (64 - i)) : 0ull) & m;
-  }
+  const unsigned a0 = (unsigned)a, a1 = (unsigned)(a >> 32);
+  const unsigned b0 = (unsigned)b, b1 = (unsigned)(b >> 32);
+  const u64 l = clmul32(a0, b0), h = clmul32(a1, b1);
+  const u64 mid = clmul32(a0 ^ a1, b0 ^ b1) ^ l ^ h;
+  u64 lo = l ^ (mid << 32);
+  const u64 hi = h ^ (mid >> 32);
   // x^64 = x^4 + x^3 + x + 1: fold hi twice (the second fold has at most 4 bits)
   const u64 h2 = (hi >> 60) ^ (hi >> 61) ^ (hi >> 63);
   lo ^= hi ^ (hi << 1) ^ (hi << 3) ^ (hi << 4);
@@ -402,22 +422,23 @@ __global__ void k_gf_random_shared(Key k01, Key k02, Key k12, u32 t1, u32 t2, u3
 
 __global__ void k_gf_rec1(const u64* __restrict__ s6, u64 xor_mask, u64* __restrict__ out,
                           u32* status, u32 flag) {
-  const u64 in_p2_r1 = s6[0];
+  // 6 threads: one hash each (sent and received copies of the three messages)
+  __shared__ u32 dig[6][8];
+  const int t = threadIdx.x;
   const u64 in_p1_r2 = s6[1] ^ xor_mask;
-  const u64 in_p0_m = s6[2];
-  u32 a[8], b[8];
-  sha256_word(s6[3], a);   // P1: H([r]_1) -> P2
-  sha256_word(in_p2_r1, b);
-  bool bad = false;
-  for (int q = 0; q < 8; ++q) bad |= a[q] != b[q];
-  sha256_word(s6[4], a);   // P2: H(m) -> P0
-  sha256_word(in_p0_m, b);
-  for (int q = 0; q < 8; ++q) bad |= a[q] != b[q];
-  sha256_word(s6[5], a);   // P2: H([r]_2) -> P1
-  sha256_word(in_p1_r2, b);
-  for (int q = 0; q < 8; ++q) bad |= a[q] != b[q];
-  if (bad) atomicOr(status, flag);
-  *out = s6[2] ^ s6[3] ^ in_p1_r2;   // P1's opening
+  if (t < 6) {
+    const u64 v = t == 0 ? s6[3]      // P1: H([r]_1) -> P2
+                : t == 1 ? s6[4]      // P2: H(m) -> P0
+                : t == 2 ? s6[5]      // P2: H([r]_2) -> P1
+                : t == 3 ? s6[0]      // P2 hashes the [r]_1 it received
+                : t == 4 ? s6[2]      // P0 hashes the m it received
+                         : in_p1_r2;  // P1 hashes the [r]_2 it received
+    sha256_word(v, dig[t]);
+  }
+  __syncthreads();
+  if (t < 8 && (dig[0][t] != dig[3][t] || dig[1][t] != dig[4][t] || dig[2][t] != dig[5][t]))
+    atomicOr(status, flag);
+  if (t == 0) *out = s6[2] ^ s6[3] ^ in_p1_r2;   // P1's opening
 }
 
 // Lagrange weights at the points 0, 1, x (reading A6/X) over GF(2^64):
@@ -634,7 +655,7 @@ void launch_gf_random_shared(cudaStream_t st, Key k01, Key k02, Key k12, u32 pur
                                       make_tag(purpose, C_R2), make_tag(purpose, C_M12), obj, s6);
 }
 void launch_gf_rec1(cudaStream_t st, const u64* s6, u64 xor_mask, u64* out, u32* status, u32 flag) {
-  k_gf_rec1<<<1, 1, 0, st>>>(s6, xor_mask, out, status, flag);
+  k_gf_rec1<<<1, 32, 0, st>>>(s6, xor_mask, out, status, flag);
 }
 void launch_gf_lagrange(cudaStream_t st, const u64* zeta, u64* coef) {
   static const GfLagInv inv = [] {

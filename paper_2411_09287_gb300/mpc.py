@@ -348,18 +348,20 @@ class Context:
 
     @staticmethod
     def nonlinear_R(np_list):
-        """Default rounds (R0, R1, R2) of a non-linear layer's three verification batches for
-        stage widths np_list (padded): arithmetic products, edaBit inner products, AND gates."""
-        nm = sum(67 * n for n in np_list)
+        """Default rounds (R0, R1, R2, R3) of a non-linear layer's four verification batches for
+        stage widths np_list (padded): daBit and final products, edaBit inner products, AND
+        gates, edaBit bit products."""
+        nm = sum(3 * n for n in np_list)
         ne = sum(np_list)
         nand = sum(125 * n for n in np_list)
-        return default_R(nm), default_R(64 * ne), default_R(nand)
+        return default_R(nm), default_R(64 * ne), default_R(nand), default_R(64 * ne)
 
     def _nl_trace(self, np_list, trace):
         if not trace:
             return None
-        R0, R1, R2 = self.nonlinear_R(np_list)
-        return self.zeros((R0 + 1) * TRACE_ROUND + (R1 + 1) * TRACE_ROUND + (R2 + 1) * TRACE_GF_ROUND)
+        R0, R1, R2, R3 = self.nonlinear_R(np_list)
+        return self.zeros((R0 + 1) * TRACE_ROUND + (R1 + 1) * TRACE_ROUND + (R2 + 1) * TRACE_GF_ROUND
+                          + (R3 + 1) * TRACE_ROUND)
 
     def relu(self, call_id: int, verify_id: int, xs, n: int, trace: bool = False):
         """ReLU layer with its verification (Sec. 4.3).  Returns (code, out sharing, trace)."""

@@ -1,6 +1,7 @@
 """Non-linear layers on the GPU vs the oracle (Sec. 4.3), through the C-ABI: ReLU and 2x2
 max-pool outputs bit-exact in every share component, the three verification transcripts of the
-layer (arithmetic products and edaBit inner products over GR(2^64, 64), AND gates over GF(2^64)),
+layer (daBit and final products, edaBit inner products and edaBit bit products over GR(2^64, 64),
+AND gates over GF(2^64)),
 the ledger (the arithmetic and the Boolean oracle sessions together), rejection of corrupted
 messages, and plaintext correctness at a size the oracle does not reach."""
 import hashlib
@@ -81,10 +82,12 @@ def check_gf_batch(M, g, off, otr, R):
 
 def check_layer_trace(M, gtrace, otrace, nps):
     g = M.to_u64(gtrace)
-    R0, R1, R2 = M.Context.nonlinear_R(nps)
+    R0, R1, R2, R3 = M.Context.nonlinear_R(nps)
     off = check_gr_batch(M, g, 0, otrace["mult"], R0)
     off = check_gr_batch(M, g, off, otrace["inner"], R1)
     check_gf_batch(M, g, off, otrace["and"], R2)
+    off += (R2 + 1) * M.TRACE_GF_ROUND
+    check_gr_batch(M, g, off, otrace["eda"], R3)
 
 
 def signed(a):
@@ -106,7 +109,7 @@ def test_relu_matches_oracle(mpc):
     rc, out, tr = ctx.relu(2, 3, gx, n, trace=True)
     assert rc == mpc.MPC_OK
     oout, triples = NL.relu(s, bs, ox, 2)
-    otr = {"mult": [], "inner": [], "and": []}
+    otr = {"mult": [], "inner": [], "and": [], "eda": []}
     assert NL.verify_layer(s, bs, triples, 3, trace=otr)
     assert_shared_equal(gpu_shared(mpc, out, n), oout, "relu out")
     check_layer_trace(mpc, tr, otr, [64 * ((n + 63) // 64)])
@@ -130,7 +133,7 @@ def test_maxpool2_matches_oracle(mpc):
     rc, out, tr = ctx.maxpool2(2, 3, gx, shape, trace=True)
     assert rc == mpc.MPC_OK
     oout, triples = NL.maxpool2(s, bs, ox, shape, 2)
-    otr = {"mult": [], "inner": [], "and": []}
+    otr = {"mult": [], "inner": [], "and": [], "eda": []}
     assert NL.verify_layer(s, bs, triples, 3, trace=otr)
     nw = int(np.prod(shape)) // 4
     assert_shared_equal(gpu_shared(mpc, out, nw), oout, "maxpool out")

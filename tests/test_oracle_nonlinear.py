@@ -147,3 +147,38 @@ def test_layer_verification_rejects_a_corrupted_message(where):
     (bs if where == "and" else s).arm_fault("GAMMA2", 5, 1)
     out, triples = NL.relu(s, bs, x, 42)
     assert not NL.verify_layer(s, bs, triples, 43)
+
+
+@pytest.mark.parametrize("batch, comp", [("mults", "p1_m"), ("mults", "p0_r2"), ("eda", "p2_m"),
+                                         ("eda", "p0_r1")])
+def test_layer_verification_catches_a_wrong_product_in_each_batch(batch, comp):
+    """Reading N8 keeps every product under a check: a product triple made wrong after the fact
+    (one share word of z, in the general batch 0 or in the edaBit bit batch 3) is rejected, and
+    the untouched layer is accepted by the same call."""
+    s, bs = sessions(bytes(range(1, 33)))
+    vals = np.random.default_rng(9).integers(-2 ** 40, 2 ** 40, 64).view(U64)
+    x = OP.share_input(s, vals, 51)
+    _, triples = NL.relu(s, bs, x, 52)
+    assert len(triples[0]["mults"]) == 3 and len(triples[0]["eda"]) == 1
+    assert triples[0]["eda"][0][2].p1_m.shape == (64, 64)
+    s2, bs2 = sessions(bytes(range(1, 33)))
+    x2 = OP.share_input(s2, vals, 51)
+    _, triples2 = NL.relu(s2, bs2, x2, 52)
+    z = getattr(triples2[0][batch][-1][2], comp)
+    z.reshape(-1)[7] ^= U64(1 << 20)
+    assert NL.verify_layer(s, bs, triples, 53)
+    assert not NL.verify_layer(s2, bs2, triples2, 53)
+
+
+def test_edabit_bit_batch_has_the_truncation_pairs_form():
+    """The x side of batch 3 holds only [r]_1 (components p0_r1, p1_r1), the y side only [r]_2
+    (p0_r2, p2_r2): the form whose party sums reduce to P0's single Gram."""
+    s, bs = sessions()
+    vals = np.random.default_rng(10).integers(-2 ** 40, 2 ** 40, 64).view(U64)
+    _, triples = NL.relu(s, bs, OP.share_input(s, vals, 61), 62)
+    X, Y, _ = triples[0]["eda"][0]
+    for f in ("p0_r2", "p1_m", "p2_m", "p2_r2"):
+        assert not getattr(X, f).any(), f
+    for f in ("p0_r1", "p1_m", "p1_r1", "p2_m"):
+        assert not getattr(Y, f).any(), f
+    assert np.array_equal(X.p0_r1, X.p1_r1) and np.array_equal(Y.p0_r2, Y.p2_r2)
