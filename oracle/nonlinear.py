@@ -13,7 +13,7 @@ Conventions (readings, also in the design notes):
     max-pool comparison, 1 for the second; sub = circuit level for the AND gates.
   - The Boolean AND gates are verified in GF(2^64) with verify batch 2, so that their challenges
     never share a stream with the arithmetic batches 0 (products) and 1 (edaBit inner products).
-  - Reading N8: the edaBit bit products b_{i,1} b_{i,2} (64 per element) are verified in a batch
+  - Reading N9: the edaBit bit products b_{i,1} b_{i,2} (64 per element) are verified in a batch
     of their own (verify batch 3) and batch 0 keeps the daBit and final products (3 per element).
     Every product is still checked with a fresh challenge; splitting one Pi_MultVerify batch into
     two adds their soundness errors (union bound).  The bit batch has the truncation pairs' form:
@@ -268,7 +268,7 @@ def verify_layer(sess: Session, bsess: Session, triples, verify_id: int, R_mult=
     """Pi_MultVerify of the daBit and final products (batch 0), Pi_BIVerify of the edaBit inner
     products (batch 1), both over GR(2^64, 64), Pi_MultVerify of every AND gate over GF(2^64)
     (batch 2) (Sec. 4.3: products over Z_2^l and Z_2 verified in their rings), and Pi_MultVerify
-    of the edaBit bit products over GR(2^64, 64) (batch 3, reading N8).  `trace`, if given, is a
+    of the edaBit bit products over GR(2^64, 64) (batch 3, reading N9).  `trace`, if given, is a
     dict of four lists."""
     mults = [t for tr in triples for t in tr["mults"]]
     edas = [t for tr in triples for t in tr["eda"]]

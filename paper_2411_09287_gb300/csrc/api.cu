@@ -2772,7 +2772,7 @@ struct NLPlan {
   u64** ydev;                    // 6 device pointers (kernel argument)
   // batch 2: AND gates
   GfPlan gf;
-  // batch 3: edaBit bit products (nb = 64 sum np), x only [r]_1 and y only [r]_2 (reading N8)
+  // batch 3: edaBit bit products (nb = 64 sum np), x only [r]_1 and y only [r]_2 (reading N9)
   long long nb;
   int Rb;
   Small sb;

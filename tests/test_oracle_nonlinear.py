@@ -152,7 +152,7 @@ def test_layer_verification_rejects_a_corrupted_message(where):
 @pytest.mark.parametrize("batch, comp", [("mults", "p1_m"), ("mults", "p0_r2"), ("eda", "p2_m"),
                                          ("eda", "p0_r1")])
 def test_layer_verification_catches_a_wrong_product_in_each_batch(batch, comp):
-    """Reading N8 keeps every product under a check: a product triple made wrong after the fact
+    """Reading N9 keeps every product under a check: a product triple made wrong after the fact
     (one share word of z, in the general batch 0 or in the edaBit bit batch 3) is rejected, and
     the untouched layer is accepted by the same call."""
     s, bs = sessions(bytes(range(1, 33)))
