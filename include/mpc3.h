@@ -119,9 +119,10 @@ typedef struct {
  *   fold_batch_max the folds of one Pi_Reduce round share one launch when the folded vectors
  *                  have at most this many elements; default 65536.
  *   gr_producers   how the GR-matrix products (folds, tables) load their A rows: 1 producer
- *                  warps' global loads into registers (two digit-plane stages), 2 TMA loads into
- *                  shared memory (one digit-plane stage), 3 TMA loads with the A digit planes in
- *                  tensor memory (output in two halves of 32 columns); default 1.
+ *                  warps' global loads into registers (two digit-plane stages), 2 TMA loads of
+ *                  half-chunks into shared memory (one digit-plane stage, rewritten by K halves
+ *                  as the MMAs of each half finish), 3 TMA loads with the A digit planes in
+ *                  tensor memory (output in two halves of 32 columns); default 2.
  *   gr_drain_warps warps that drain the GR-matrix products' accumulators: 8 or 16; default 8. */
 typedef struct {
   int64_t trunc_block;

@@ -146,7 +146,7 @@ mpc_tuning default_tuning() {
   t.gemm_split_min = 8;
   t.gram_split = 76;
   t.fold_batch_max = 65536;
-  t.gr_producers = 1;
+  t.gr_producers = 2;
   t.gr_drain_warps = 8;
   return t;
 }

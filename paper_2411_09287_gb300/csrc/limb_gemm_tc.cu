@@ -134,7 +134,8 @@ __device__ __forceinline__ void drain16_pairs(unsigned tl, int col, u64* acc) {
 // (s, s + 1), s even, goes into the accumulator of s as C_s + 2^8 C_(s+1) (|.| <= 64 (128 +
 // 2^15) < 2^22 per 64 of K), four accumulators instead of eight.
 // fresh = 0 adds the chunk to what the accumulators hold instead of starting them anew.
-template <int G, bool A0 = false>
+// KK >= 0 issues only the MMAs of that k16 step (K words 16 KK .. 16 KK + 15 of the chunk).
+template <int G, bool A0 = false, int KK = -1>
 __device__ __forceinline__ void issue_group(unsigned tmem, u64 a_desc, u64 b_desc,
                                             unsigned fresh = 1) {
 #pragma unroll
@@ -142,7 +143,7 @@ __device__ __forceinline__ void issue_group(unsigned tmem, u64 a_desc, u64 b_des
     const int s = group_s(G, g);
     const int sa = A0 ? (s & ~1) : s;   // target accumulator
 #pragma unroll
-    for (int kk = 0; kk < TC_BK / 16; ++kk) {
+    for (int kk = (KK < 0 ? 0 : KK); kk < (KK < 0 ? TC_BK / 16 : KK + 1); ++kk) {
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         if (i <= s && (!A0 || i == 0)) {
@@ -545,11 +546,13 @@ __device__ __forceinline__ long long rowmap(const GrRowMap& m, long long rho) {
 
 // MODE 0: plain product, 1: fold (p0 - p1), 2: bit operand.  One instantiation per mode keeps
 // each kernel's code (and instruction-cache footprint) to the paths it runs.
-// TMA (MODE 0 and 1): one A stage; the other stage's 64 KB holds the raw A rows of the next K
-// chunk(s), loaded by TMA from the row-mapped input (tensor maps tm0 for p0, tm1 for p1: boxes of
-// 16 words x 128 rows, 128-byte swizzle, rows past the valid ones read as zero), so that the
-// producers split shared memory into digit planes without waiting on global loads, while the
-// loads of the next chunk overlap the MMAs of the current one.
+// TMA (MODE 0 and 1): one A stage, handled by K halves; the other stage's 64 KB holds slots of
+// raw A rows, one half-unit (16 words x 128 rows of p0, and of p1 in a fold) per slot, loaded by
+// TMA from the row-mapped input (tensor maps tm0 for p0, tm1 for p1: boxes of 16 words x 128 rows,
+// 128-byte swizzle, rows past the valid ones read as zero).  The issuer runs a unit's k16 step 0
+// (both accumulator groups) and commits, then step 1: the producers rewrite half h of the A stage
+// for the next unit as soon as the MMAs of step h are done, from a slot that TMA filled while
+// the previous MMAs ran.
 constexpr int GM_RAW_HALF = TC_BM * 128;        // 16 KB: 128 rows x 16 words
 constexpr int GM_RAW_ARR = 2 * GM_RAW_HALF;     // one operand's K chunk (32 words)
 
@@ -561,18 +564,18 @@ k_gr_matmul_tc(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ 
   constexpr int DC = 256 / ND;                              // columns per drain warp
   static_assert(ND == 8 || ND == 16, "drain warps");
   constexpr int NST = TMA ? 1 : NSTAGE;                     // A digit-plane stages
-  constexpr int NRAW = MODE == 1 ? 1 : 2;                   // raw stages (TMA)
-  constexpr int RAW_UNIT = (MODE == 1 ? 2 : 1) * GM_RAW_ARR;
-  static_assert(!TMA || NRAW * RAW_UNIT <= (NSTAGE - NST) * 8 * A_TILE, "raw stages");
+  constexpr int SLOT = (MODE == 1 ? 2 : 1) * GM_RAW_HALF;   // raw half-unit slot (TMA)
+  constexpr int NSLOT = MODE == 1 ? 2 : 4;
+  static_assert(!TMA || NSLOT * SLOT <= (NSTAGE - NST) * 8 * A_TILE, "raw slots");
   extern __shared__ unsigned char dsm[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsm) + 1023) & ~uintptr_t(1023));
   unsigned char* Bsm = base;                       // [2 chunks][8 planes][64 rows][64 B]
   unsigned char* Asm = base + 2 * GM_BCHUNK;       // [NST][8 planes][128 rows][64 B]
-  unsigned char* Raw = Asm + NST * 8 * A_TILE;     // TMA: [NRAW][RAW_UNIT]
+  unsigned char* Raw = Asm + NST * 8 * A_TILE;     // TMA: [NSLOT][SLOT]
   unsigned char* Osm = Asm + NSTAGE * 8 * A_TILE;  // [drain warp][32 rows][48 B]
   __shared__ __align__(8) u64 full_bar[NSTAGE], empty_bar[NSTAGE];
-  __shared__ __align__(8) u64 raw_full[2], raw_empty[2];
+  __shared__ __align__(8) u64 raw_full[4], raw_empty[4], hfull[2], hempty[2];
   __shared__ __align__(8) u64 accf_bar[2], acce_bar[2], done_bar;
   __shared__ unsigned tmem_slot;
   __shared__ int abort_flag;
@@ -601,9 +604,13 @@ k_gr_matmul_tc(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ 
       mbar_init(&full_bar[i], GM_PROD);
       mbar_init(&empty_bar[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 4; ++i) {
       mbar_init(&raw_full[i], 1);
       mbar_init(&raw_empty[i], GM_PROD);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&hfull[i], GM_PROD);
+      mbar_init(&hempty[i], 1);
     }
     for (int g = 0; g < 2; ++g) {
       mbar_init(&accf_bar[g], 1);
@@ -688,43 +695,68 @@ k_gr_matmul_tc(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ 
       if (lane == 0) mbar_arrive(&full_bar[u % NST]);
     };
     if constexpr (TMA) {
-      // one thread keeps NRAW units of raw rows in flight; a unit's buffer is refilled once every
-      // producer warp has split it
+      // half-unit hu = 2u + h: K words 16 h .. 16 h + 15 of unit u (the items with u4 = 2h, 2h + 1).
+      // One thread keeps NSLOT half-units of raw rows in flight; a slot is refilled once every
+      // producer warp has split it.
       const bool tma_thr = pt == 0;
+      const long long nhu = 2 * nunits;
       long long issued = 0, consumed = 0;
-      auto issue_raw = [&](long long u) {
-        const int rb = (int)(u % NRAW);
+      auto issue_raw = [&](long long hu) {
+        const int sl = (int)(hu % NSLOT);
+        const long long u = hu >> 1;
         const long long rho0 = (t0 + (u >> 1) * tstep) * TC_BM;
-        const int kx = (int)(u & 1) * 32;
+        const int kx = (int)(u & 1) * 32 + (int)(hu & 1) * 16;
         const int y = (int)(a.in.q ? rho0 % a.in.q : rho0);
         const int z = (int)(a.in.q && a.in.s2 ? rho0 / a.in.q : 0);
-        unsigned char* dst = Raw + rb * RAW_UNIT;
-        mbar_expect_tx(&raw_full[rb], (unsigned)RAW_UNIT);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          tma_load_3d(dst + h * GM_RAW_HALF, &tm0, &raw_full[rb], kx + 16 * h, y, z);
-          if (MODE == 1)
-            tma_load_3d(dst + GM_RAW_ARR + h * GM_RAW_HALF, &tm1, &raw_full[rb], kx + 16 * h, y, z);
-        }
+        unsigned char* dst = Raw + sl * SLOT;
+        mbar_expect_tx(&raw_full[sl], (unsigned)SLOT);
+        tma_load_3d(dst, &tm0, &raw_full[sl], kx, y, z);
+        if (MODE == 1) tma_load_3d(dst + GM_RAW_HALF, &tm1, &raw_full[sl], kx, y, z);
       };
       if (tma_thr)
-        for (; issued < nunits && issued < NRAW; ++issued) issue_raw(issued);
-      constexpr int NIT = (512 + GM_PROD * 32 - 1) / (GM_PROD * 32);   // items per thread
-      for (long long u = 0; u < nunits && ok; ++u) {
-        const int rb = (int)(u % NRAW);
+        for (; issued < nhu && issued < NSLOT; ++issued) issue_raw(issued);
+      constexpr int NIT = (256 + GM_PROD * 32 - 1) / (GM_PROD * 32);   // items per thread
+      for (long long hu = 0; hu < nhu && ok; ++hu) {
+        const long long u = hu >> 1;
+        const int h = (int)(hu & 1);
+        const int sl = (int)(hu % NSLOT);
         if (!(ok = __all_sync(0xffffffffu,
-                              mbar_wait(&raw_full[rb], (unsigned)((u / NRAW) & 1), abort))))
+                              mbar_wait(&raw_full[sl], (unsigned)((hu / NSLOT) & 1), abort))))
           break;
-        if (!(ok = begin_unit(u))) break;
-        const unsigned char* r0 = Raw + rb * RAW_UNIT;
+        if (h == 0 && !(u & 1)) {
+          // a tile's first half-unit: B is rebuilt when the matrix group changes, once every
+          // MMA of the previous unit is done
+          const long long tile = t0 + (u >> 1) * tstep;
+          const long long mi = a.mrows ? tile * TC_BM / a.mrows : 0;
+          if (mi != cur_m) {
+            if (u > 0 && !(ok = __all_sync(0xffffffffu,
+                                           mbar_wait(&hempty[1], (unsigned)((u - 1) & 1), abort))))
+              break;
+            const u64* Mm = a.Mmat + mi * 4096;
+            for (int it = pt; it < 64 * 8; it += GM_PROD * 32) {   // (row c of M^T, unit of 8 k)
+              const int c = it >> 3, k8 = it & 7;
+              u64 v[8];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) v[q] = Mm[(k8 * 8 + q) * 64 + c];
+              split8_store(v, Bsm + (k8 >> 2) * GM_BCHUNK, B_TILE, sw64_off(c, k8 & 3));
+            }
+            cur_m = mi;
+            if (pt == 0 && a.mrows && (mi + 1) * a.mrows < R) prefetch_l2(Mm + 4096, 4096 * 8);
+          }
+        }
+        // half h of the A stage is free once the MMAs of step h of unit u - 1 are done
+        if (u > 0 && !(ok = __all_sync(0xffffffffu,
+                                       mbar_wait(&hempty[h], (unsigned)((u - 1) & 1), abort))))
+          break;
+        const unsigned char* r0 = Raw + sl * SLOT;
 #pragma unroll
         for (int q = 0; q < NIT; ++q) {
-          // item = (unit of 8 k, row): the 8 lanes of a shared-memory phase take 8 consecutive
+          // item = (row, unit of 8 k): the 8 lanes of a shared-memory phase take 8 consecutive
           // rows of one unit, conflict-free in the swizzled raw rows and in the digit planes
           const int item = pt + q * GM_PROD * 32;
-          if (item < 512) {
-            const int row = item & (TC_BM - 1), u4 = item >> 7;
-            const unsigned char* src = r0 + (u4 >> 1) * GM_RAW_HALF + row * 128;
+          if (item < 256) {
+            const int row = item & (TC_BM - 1), u4 = 2 * h + (item >> 7);
+            const unsigned char* src = r0 + row * 128;
             u64 v[8];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -733,7 +765,7 @@ k_gr_matmul_tc(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ 
               v[2 * j] = x.x;
               v[2 * j + 1] = x.y;
               if (MODE == 1) {
-                const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(src + GM_RAW_ARR + c);
+                const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(src + GM_RAW_HALF + c);
                 v[2 * j] -= w.x;
                 v[2 * j + 1] -= w.y;
               }
@@ -741,20 +773,24 @@ k_gr_matmul_tc(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ 
             split8_store(v, Asm, A_TILE, sw64_off(row, u4));
           }
         }
-        end_unit(u);
-        if (lane == 0) mbar_arrive(&raw_empty[rb]);
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&hfull[h]);
+          mbar_arrive(&raw_empty[sl]);
+        }
         ++consumed;
         bool iok = true;
-        if (tma_thr && issued < nunits) {
-          iok = mbar_wait(&raw_empty[rb], (unsigned)((u / NRAW) & 1), abort);
+        if (tma_thr && issued < nhu) {
+          iok = mbar_wait(&raw_empty[sl], (unsigned)((hu / NSLOT) & 1), abort);
           if (iok) issue_raw(issued++);
         }
         ok = __all_sync(0xffffffffu, iok);
       }
       // loads still in flight land before the CTA leaves
       if (tma_thr)
-        for (long long u = consumed; u < issued; ++u)
-          mbar_wait_plain(&raw_full[u % NRAW], (unsigned)((u / NRAW) & 1));
+        for (long long hu = consumed; hu < issued; ++hu)
+          mbar_wait_plain(&raw_full[hu % NSLOT], (unsigned)((hu / NSLOT) & 1));
     } else if (a_bits) {
       constexpr int NIT = (512 + GM_PROD * 32 - 1) / (GM_PROD * 32);   // items per thread
       // One bit word per row serves both K chunks of its tile (bytes 0..3, then 4..7); the
@@ -859,7 +895,35 @@ k_gr_matmul_tc(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ 
     if (!ok && lane == 0) fail();
   } else if (warp == ND + GM_PROD) {
     // ---- MMA issuer ----
-    if (lane == 0) {
+    if (lane == 0 && TMA) {
+      // per unit: k16 step 0 of both groups, commit (half 0 free), step 1, commit (half 1 free)
+      const u64 ad = smem_desc(Asm, 64);
+      const u64 db0 = smem_desc(Bsm, 64);
+      for (long long u = 0; u < nunits; ++u) {
+        const u64 bd = db0 + (u64)(((int)(u & 1) * GM_BCHUNK) >> 4);
+        const bool first = !(u & 1), last = (u & 1) != 0;
+        const long long v = u >> 1;
+        const unsigned ph = (unsigned)(u & 1);
+        if (!mbar_wait(&hfull[0], ph, abort)) { fail(); break; }
+        tc_fence_after();
+        if (first && v > 0 && !mbar_wait(&acce_bar[0], (unsigned)((v - 1) & 1), abort)) { fail(); break; }
+        tc_fence_after();
+        issue_group<0, false, 0>(tmem, ad, bd, first ? 1u : 0u);
+        if (first && v > 0 && !mbar_wait(&acce_bar[1], (unsigned)((v - 1) & 1), abort)) { fail(); break; }
+        tc_fence_after();
+        issue_group<1, false, 0>(tmem, ad, bd, first ? 1u : 0u);
+        mma_commit(&hempty[0]);
+        if (!mbar_wait(&hfull[1], ph, abort)) { fail(); break; }
+        tc_fence_after();
+        issue_group<0, false, 1>(tmem, ad, bd, 0u);
+        if (last) mma_commit(&accf_bar[0]);
+        issue_group<1, false, 1>(tmem, ad, bd, 0u);
+        if (last) mma_commit(&accf_bar[1]);
+        mma_commit(&hempty[1]);
+      }
+      mma_commit(&done_bar);
+      mbar_wait_plain(&done_bar, 0u);
+    } else if (lane == 0) {
       const u64 da0 = smem_desc(Asm, 64);
       const u64 db0 = smem_desc(Bsm, 64);
       for (long long u = 0; u < nunits; ++u) {

@@ -138,8 +138,9 @@ def test_tuning_round_trip_and_range(mpc):
 
 
 # every variant of the GR-matrix product kernel (the autotuner's candidates) on a blocked, compact
-# and a chunked batch: register producers with 16 drain warps, TMA producers, A in tensor memory
-GR_VARIANTS = [dict(gr_producers=1, gr_drain_warps=16), dict(gr_producers=2),
+# and a chunked batch: register producers (8 and 16 drain warps), TMA producers with 16 drain
+# warps, A in tensor memory
+GR_VARIANTS = [dict(gr_producers=1), dict(gr_producers=1, gr_drain_warps=16),
                dict(gr_producers=2, gr_drain_warps=16), dict(gr_producers=3),
                # the autotuner's other knobs, away from their defaults
                dict(gemm_split_min=2, gram_split=19, fold_batch_max=1 << 20)]
