@@ -98,6 +98,8 @@ struct GrMMArgs {
   int tma;            // 1: the A rows of the plain and fold modes are loaded by TMA; 2: and the
                       // A operand sits in tensor memory
   int drain_warps;    // 8 (default) or 16 drain warps
+  int out_tma;        // set by the launcher: bit-operand tiles leave by TMA stores (tensor map of
+                      // out and om in place of p1's)
 };
 int gr_matmul_tc_ex(cudaStream_t st, const GrMMArgs& a, unsigned* err, unsigned err_flag);
 

@@ -520,7 +520,10 @@ bool make_map(CUtensorMap* map, void* planes, long long rows, long long Kp, int 
 //     columns) add add0 and store the tile;
 //   - a_bits mode (A = the bits of one word per row): A has digit plane 0 only, so the producers
 //     write that plane alone and the issuer runs the 8 pairs (0, s) instead of 36, merged two by
-//     two into four accumulators (odd B planes stored times 2^8), which halves the drain.
+//     two into four accumulators (odd B planes stored times 2^8), which halves the drain.  Its
+//     tiles can leave by TMA tensor stores: the drain warps write the tile into four 128-byte
+//     swizzled boxes (16 words x 128 rows) in the A stages' unused planes, and one thread stores
+//     them while the next tile is drained.
 constexpr int GM_NDRAIN = 8;                              // drain warps: 32 rows x GM_DC columns
 constexpr int GM_DC = 256 / GM_NDRAIN;                    // columns per drain warp (32)
 constexpr int GM_PROD = 3;                                // producer warps
@@ -577,9 +580,15 @@ k_gr_matmul_tc(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ 
   __shared__ __align__(8) u64 full_bar[NSTAGE], empty_bar[NSTAGE];
   __shared__ __align__(8) u64 raw_full[4], raw_empty[4], hfull[2], hempty[2];
   __shared__ __align__(8) u64 accf_bar[2], acce_bar[2], done_bar;
+  __shared__ __align__(8) u64 stg_full, stg_free;
   __shared__ unsigned tmem_slot;
   __shared__ int abort_flag;
   volatile int* abort = &abort_flag;
+  // bit-operand staging boxes (16 KB each, 1024-byte aligned) in the planes 1..7 of the A stages
+  auto stg_box = [&](int b) -> unsigned char* {
+    return Asm + (b < 3 ? (b + 1) * 16384 : 8 * A_TILE + 16384);
+  };
+  const bool out_tma = MODE == 2 && a.out_tma;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -616,6 +625,8 @@ k_gr_matmul_tc(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ 
       mbar_init(&accf_bar[g], 1);
       mbar_init(&acce_bar[g], ND);
     }
+    mbar_init(&stg_full, ND);
+    mbar_init(&stg_free, 1);
     mbar_init(&done_bar, 1);
     abort_flag = 0;
     mbar_init_fence();
@@ -959,6 +970,7 @@ k_gr_matmul_tc(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ 
 #pragma unroll
     for (int c = 0; c < DC; ++c) acc[c] = 0;
     bool ok = true;
+    long long nst = 0;                   // tiles stored by TMA so far
     const long long nacc = nunits / 2;   // one accumulation per tile
     for (long long v = 0; v < nacc && ok; ++v) {
       const unsigned par = (unsigned)(v & 1);
@@ -1014,7 +1026,54 @@ k_gr_matmul_tc(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ 
         __syncwarp();
         if (lane == 0) mbar_arrive(&acce_bar[g]);
       }
-      if (ok) {   // tile complete: add add0, store (4 columns at a time through shared memory)
+      // a bit-operand tile leaves by TMA stores when all its rows lie below the row limit
+      // (uniform over the drain warps); the others take the register epilogue
+      bool tile_tma = false;
+      long long rho0 = 0;
+      int ty = 0, tz = 0;
+      if (out_tma) {
+        rho0 = (t0 + v * tstep) * TC_BM;
+        ty = (int)(a.om.q ? rho0 % a.om.q : rho0);
+        tz = (int)(a.om.q ? rho0 / a.om.q : 0);
+        const long long last = a.om.q ? ty + TC_BM - 1 : (rho0 + TC_BM - 1 < R ? rho0 + TC_BM - 1 : R - 1);
+        const long long off = last * a.om.s1 + (long long)tz * a.om.s2;
+        tile_tma = off + 64 <= a.out_lim;
+      }
+      if (ok && tile_tma) {   // tile complete: into the staging boxes, out by TMA stores
+        const bool st_thr = warp == 0 && lane == 0;
+        const unsigned spar = (unsigned)(nst & 1);
+        if (st_thr) {
+          if (nst > 0) bulk_wait_read0();   // the previous stores have read the boxes
+          mbar_arrive(&stg_free);
+        }
+        ok = __all_sync(0xffffffffu, mbar_wait(&stg_free, spar, abort));
+        if (ok) {
+          const int r = q4 * 32 + lane;   // tile row
+#pragma unroll
+          for (int c = 0; c < DC; c += 2) {
+            const int col = h * DC + c;   // word column
+            const int k = (col & 15) >> 1;
+            *reinterpret_cast<ulonglong2*>(stg_box(col >> 4) + r * 128 + ((k ^ (r & 7)) << 4)) =
+                make_ulonglong2(acc[c], acc[c + 1]);
+          }
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&stg_full);
+          bool sok = true;
+          if (st_thr) {
+            sok = mbar_wait(&stg_full, spar, abort);
+            if (sok) {
+#pragma unroll
+              for (int b = 0; b < 4; ++b) tma_store_3d(&tm1, stg_box(b), 16 * b, ty, tz);
+              bulk_commit();
+            }
+          }
+          ok = __all_sync(0xffffffffu, sok);
+        }
+        ++nst;
+#pragma unroll
+        for (int c = 0; c < DC; ++c) acc[c] = 0;
+      } else if (ok) {   // tile complete: add add0, store (4 columns at a time through shared memory)
         unsigned char* os = Osm + warp * GM_OSTAGE;
         if (MODE == 2) tile_rows_out();
 #pragma unroll
@@ -1043,6 +1102,8 @@ k_gr_matmul_tc(const __grid_constant__ CUtensorMap tm0, const __grid_constant__ 
         for (int c = 0; c < DC; ++c) acc[c] = 0;
       }
     }
+    // the stores still in flight complete before the CTA leaves
+    if (out_tma && warp == 0 && lane == 0) bulk_wait0();
     if (!ok && lane == 0) fail();
   }
   tc_fence_before();
@@ -1765,6 +1826,12 @@ int gr_matmul_tc_ex(cudaStream_t st, const GrMMArgs& args, unsigned* err, unsign
   std::memset(&m1, 0, sizeof(m1));
   const bool tma = a.tma && mode != 2 && make_rows_map(&m0, a.p0, a.in, a.R, a.qvalid) &&
                    (mode == 0 || make_rows_map(&m1, a.p1, a.in, a.R, a.qvalid));
+  // bit-operand tiles can leave by TMA stores when the output map covers exactly the rows that
+  // exist: no padded segments, whole periods (the map then clips only rows past R); tiles with
+  // rows at or past out_lim keep the register epilogue
+  a.out_tma = 0;
+  if (mode == 2 && a.tma && !a.qvalid && (a.om.q == 0 || (a.om.s2 != 0 && a.R % a.om.q == 0)))
+    a.out_tma = make_rows_map(&m1, a.out, a.om, a.R, 0) ? 1 : 0;
   if (a.tma == 2 && mode != 2 && tma) {   // A operand in tensor memory
     const size_t smem = tm_smem(mode);
     auto launch_tm = [&](auto kern) {

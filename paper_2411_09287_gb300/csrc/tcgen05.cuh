@@ -89,6 +89,27 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// Tensor store shared -> global of one box (bulk-group completion), and the group operations:
+// commit the stores issued so far, wait until every committed store has read shared memory, wait
+// until they have completed.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int x, int y,
+                                             int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];\n" ::"l"(
+          reinterpret_cast<u64>(map)),
+      "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read0() {
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait0() {
+  asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+}
+
 // Shared-memory matrix descriptor of a K-major operand tile whose rows are `row_bytes` long
 // (64 or 128) with the matching swizzle; 8-row groups are 8 * row_bytes apart.  The tile must
 // start on a 1024-byte boundary.  Adding 2 advances the start by 32 bytes (one K step of 16
