@@ -142,6 +142,18 @@ int mpc_create(const mpc_config* cfg, mpc_ctx** out);
 void mpc_destroy(mpc_ctx* ctx);
 /* Description of the last failure of this context ("" if none).  Owned by the context. */
 const char* mpc_last_error(const mpc_ctx* ctx);
+/* ---- asynchronous uploads --------------------------------------------------------------------
+ * A pipelined caller uploads the next step's inputs while the current step runs:
+ * mpc_h2d_async copies `bytes` from host `src` (pinned memory, for the copy to overlap) to device
+ * `dst` on the context's copy stream (created on first use) and records the copy under `slot`
+ * (0 .. MPC_H2D_SLOTS - 1); mpc_h2d_wait makes the context's stream wait, on the device, for the
+ * copies last recorded under `slot` (no host synchronisation; a slot never used is a no-op).  The
+ * caller owns both buffers and must not reuse `dst` before the work that reads it has run.
+ * Returns MPC_OK, MPC_ERR_ARG (null pointer, zero bytes, bad slot) or MPC_ERR_CUDA. */
+#define MPC_H2D_SLOTS 4
+int mpc_h2d_async(mpc_ctx* ctx, void* dst, const void* src, size_t bytes, int slot);
+int mpc_h2d_wait(mpc_ctx* ctx, int slot);
+
 /* Run subsequent work on `stream` (cudaStream_t). */
 int mpc_set_stream(mpc_ctx* ctx, void* stream);
 /* Replace the context's tuning (NULL: all defaults).  MPC_ERR_ARG for a value out of range

@@ -178,6 +178,9 @@ struct mpc_ctx {
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
+  // asynchronous uploads (mpc_h2d_async): a copy stream and one event per slot
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t copy_ev[MPC_H2D_SLOTS] = {};
 };
 
 namespace {
@@ -1549,6 +1552,12 @@ void mpc_destroy(mpc_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->st) cudaStreamSynchronize(ctx->st);
+  if (ctx->copy_st) {
+    cudaStreamSynchronize(ctx->copy_st);
+    cudaStreamDestroy(ctx->copy_st);
+  }
+  for (cudaEvent_t e : ctx->copy_ev)
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
   if (ctx->cst) cudaFree(ctx->cst);
   if (ctx->own_stream && ctx->st) cudaStreamDestroy(ctx->st);
@@ -1556,6 +1565,27 @@ void mpc_destroy(mpc_ctx* ctx) {
 }
 
 const char* mpc_last_error(const mpc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int mpc_h2d_async(mpc_ctx* ctx, void* dst, const void* src, size_t bytes, int slot) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (!dst || !src || bytes == 0 || slot < 0 || slot >= MPC_H2D_SLOTS)
+    return fail(ctx, MPC_ERR_ARG, "h2d_async: bad argument");
+  if (!ctx->copy_st) CK(cudaStreamCreateWithFlags(&ctx->copy_st, cudaStreamNonBlocking));
+  if (!ctx->copy_ev[slot]) CK(cudaEventCreateWithFlags(&ctx->copy_ev[slot], cudaEventDisableTiming));
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->copy_st));
+  CK(cudaEventRecord(ctx->copy_ev[slot], ctx->copy_st));
+  return MPC_OK;
+}
+
+int mpc_h2d_wait(mpc_ctx* ctx, int slot) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (slot < 0 || slot >= MPC_H2D_SLOTS) return fail(ctx, MPC_ERR_ARG, "h2d_wait: bad slot");
+  if (!ctx->copy_ev[slot]) return MPC_OK;   // nothing was issued under this slot
+  CK(cudaStreamWaitEvent(ctx->st, ctx->copy_ev[slot], 0));
+  return MPC_OK;
+}
 
 int mpc_set_stream(mpc_ctx* ctx, void* stream) {
   if (!ctx || !stream) return MPC_ERR_ARG;

@@ -50,6 +50,9 @@ def _torch():
     return torch
 
 
+H2D_SLOTS = 4   # MPC_H2D_SLOTS: the upload slots of mpc_h2d_async
+
+
 def _ptr(t) -> int:
     return 0 if t is None else int(t.data_ptr())
 
@@ -116,6 +119,18 @@ class Context:
         """Enqueue subsequent work on `stream` (a torch.cuda.Stream), e.g. a graph-capture stream."""
         self._check(self.lib.mpc_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
         self.stream = stream
+
+    def h2d_async(self, dst, src, slot: int = 0):
+        """mpc_h2d_async: copy the host tensor `src` (pinned, for overlap) into the device tensor
+        `dst` on the context's copy stream, recorded under `slot`."""
+        nbytes = src.numel() * src.element_size()
+        assert dst.numel() * dst.element_size() >= nbytes
+        self._check(self.lib.mpc_h2d_async(self.h, C.c_void_p(_ptr(dst)), C.c_void_p(_ptr(src)),
+                                           nbytes, slot))
+
+    def h2d_wait(self, slot: int = 0):
+        """mpc_h2d_wait: the context's stream waits (on the device) for the copies of `slot`."""
+        self._check(self.lib.mpc_h2d_wait(self.h, slot))
 
     def close(self):
         if getattr(self, "h", None):
