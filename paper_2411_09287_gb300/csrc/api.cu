@@ -53,6 +53,8 @@ inline void counted(int k, F f, A... a) {
 #define launch_gr_combine_z(...) counted(1, mpc3::launch_gr_combine_z, __VA_ARGS__)
 #define launch_gr_scale_rows(...) counted(1, mpc3::launch_gr_scale_rows, __VA_ARGS__)
 #define launch_gr_lift(...) counted(1, mpc3::launch_gr_lift, __VA_ARGS__)
+#define launch_gram_lifted(...) counted(1, mpc3::launch_gram_lifted, __VA_ARGS__)
+#define launch_fold_lifted(...) counted(1, mpc3::launch_fold_lifted, __VA_ARGS__)
 #define launch_neg_copy(...) counted(1, mpc3::launch_neg_copy, __VA_ARGS__)
 #define launch_gr_check_zero(...) counted(1, mpc3::launch_gr_check_zero, __VA_ARGS__)
 #define launch_trunc_u(...) counted(1, mpc3::launch_trunc_u, __VA_ARGS__)
@@ -542,15 +544,18 @@ void trace_round(mpc_ctx* ctx, u64* trace, int k, const Small& s) {
 
 // One Pi_Reduce round on a dense claim (Fig. Reduce).  x, y: current vectors (D elements, with
 // capacity for D+1), z: current claim; writes the folded vectors into xo, yo and z into zo.
+// ys (optional): the y vectors are lifted ring words, one word per element (Fig. MTP's y side
+// before any fold); y is then not read, the party sums are scalar-weighted row sums and the y
+// folds scalar times GR element.
 int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, const Vec& y,
                        long long D, const u64* z, Vec& xo, Vec& yo, u64* zo, const Small& s,
-                       u64* trace) {
+                       u64* trace, const Vec* ys = nullptr) {
   cudaStream_t st = ctx->st;
   const long long Dh = (D + 1) / 2;
   if (D & 1) {
     for (int c = 0; c < 6; ++c) {
       if (x.c[c]) CK(cudaMemsetAsync(x.c[c] + D * 64, 0, 512, st));
-      if (y.c[c]) CK(cudaMemsetAsync(y.c[c] + D * 64, 0, 512, st));
+      if (y.c[c] && !ys) CK(cudaMemsetAsync(y.c[c] + D * 64, 0, 512, st));
     }
   }
   View f[2], g[2];
@@ -570,9 +575,12 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
   int rc;
   // Shape of the truncation batch's dense rounds: x holds only [r]_1 (P0, P1 copies), y only
   // [r]_2 (P0, P2 copies), so P1's and P2's cross terms vanish and P0's sums are single Grams.
-  const bool bit_form = x.c[0] && !x.c[1] && !x.c[2] && x.c[3] && !x.c[4] && !x.c[5] &&
+  const bool bit_form = !ys && x.c[0] && !x.c[1] && !x.c[2] && x.c[3] && !x.c[4] && !x.c[5] &&
                         !y.c[0] && y.c[1] && !y.c[2] && !y.c[3] && !y.c[4] && y.c[5];
-  if (bit_form) {
+  if (ys) {
+    CK(cudaMemsetAsync(s.S, 0, 4 * 192 * 8, st));
+    launch_gram_lifted(st, x.c, ys->c, Dh, D, s.S);   // S00 | S01 + S10 | 0 | S11
+  } else if (bit_form) {
     // G00, G11 and G(x0 + x1, y0 + y1); G01 + G10 = G(x0 + x1, y0 + y1) - G00 - G11
     CK(cudaMemsetAsync(s.Pmat, 0, 3 * 4096 * 8, st));
     CK(cudaMemsetAsync(s.S, 0, 4 * 192 * 8, st));
@@ -670,7 +678,7 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
     int n = 0;
     bool even = true;
     for (int c = 0; c < 6; ++c)
-      for (int side = 0; side < 2; ++side) {
+      for (int side = 0; side < (ys ? 1 : 2); ++side) {
         const u64* in = side ? y.c[c] : x.c[c];
         u64* out = side ? yo.c[c] : xo.c[c];
         if (!in) continue;
@@ -704,13 +712,16 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
     }
   }
   for (int c = 0; c < 6 && !batched; ++c) {
-    for (int side = 0; side < 2; ++side) {
+    for (int side = 0; side < (ys ? 1 : 2); ++side) {
       const u64* in = side ? y.c[c] : x.c[c];
       u64* out = side ? yo.c[c] : xo.c[c];
       if (!in) continue;
       if ((rc = gr_matmul(ctx, Dh, in + 64, in, ~0ull, 128, s.MM, in, 128, out, 64))) return rc;
     }
   }
+  if (ys)   // the fold element is the first GR element of the Lagrange coefficients
+    for (int c = 0; c < 6; ++c)
+      if (ys->c[c]) launch_fold_lifted(st, ys->c[c], Dh, D, s.coef, yo.c[c]);
   trace_round(ctx, trace, k, s);
   return cuda_check(ctx, "reduce_round");
 }
@@ -806,8 +817,11 @@ int inner_verify_dense(mpc_ctx* ctx, u64 vid, u32 batch, const Vec& x, const Vec
 }
 
 // Dense rounds k = k0..R followed by Pi_InnerVerify.
+// ylift (optional): the y vectors entering round k0 are lifted ring words (one word per element
+// and present component); they are folded into dv.y's GR rows by the first round, or lifted there
+// when no round is left.
 int run_dense(mpc_ctx* ctx, u64 vid, u32 batch, Dense& dv, long long D, const u64* z0, int k0,
-              int R, const Small& s, const IVBuf& ivb, u64* trace) {
+              int R, const Small& s, const IVBuf& ivb, u64* trace, const Vec* ylift = nullptr) {
   int rc;
   const u64* z = z0;
   int zi = 0;
@@ -817,12 +831,17 @@ int run_dense(mpc_ctx* ctx, u64 vid, u32 batch, Dense& dv, long long D, const u6
     Vec& xo = dv.x[dv.cur ^ 1];
     Vec& yo = dv.y[dv.cur ^ 1];
     u64* zo = s.z[zi];
-    if ((rc = reduce_round_dense(ctx, vid, batch, k, x, y, D, z, xo, yo, zo, s, trace))) return rc;
+    if ((rc = reduce_round_dense(ctx, vid, batch, k, x, y, D, z, xo, yo, zo, s, trace,
+                                 k == k0 ? ylift : nullptr)))
+      return rc;
     z = zo;
     zi ^= 1;
     dv.cur ^= 1;
     D = (D + 1) / 2;
   }
+  if (ylift && k0 > R)
+    for (int c = 0; c < 6; ++c)
+      if (ylift->c[c]) launch_gr_lift(ctx->st, ylift->c[c], D, dv.y[dv.cur].c[c]);
   return inner_verify_dense(ctx, vid, batch, dv.x[dv.cur], dv.y[dv.cur], D, z, s, ivb, trace, R);
 }
 
@@ -1966,10 +1985,10 @@ int verify_mult_body(mpc_ctx* ctx, uint64_t verify_id, const u64* xs, const u64*
   int rc;
   if ((rc = power_table(ctx, s.r, p.pp, p.pw, s.aux))) return rc;
   Vec& x = p.dv.x[0];
-  Vec& y = p.dv.y[0];
+  Vec ylift;   // y stays in ring words until the first round folds it
   for (int c = 0; c < 6; ++c) {
     launch_gr_scale_rows(st, p.pw, xs + c * n, n, x.c[c]);
-    launch_gr_lift(st, ys + c * n, n, y.c[c]);
+    ylift.c[c] = const_cast<u64*>(ys + c * n);
   }
   CK(cudaMemsetAsync(s.zinit, 0, 384 * 8, st));
   {  // z_c = sum_i z_c[i] r^i for the 6 components at once: (6 x n) . (n x 64)
@@ -1979,7 +1998,7 @@ int verify_mult_body(mpc_ctx* ctx, uint64_t verify_id, const u64* xs, const u64*
     gemm_u64(st, 6, 64, n, 1, &T, epi_atomic(s.zinit, 64), nsplit_for(n));
   }
   p.dv.cur = 0;
-  return run_dense(ctx, verify_id, 0, p.dv, n, s.zinit, 1, p.R, s, p.iv, trace);
+  return run_dense(ctx, verify_id, 0, p.dv, n, s.zinit, 1, p.R, s, p.iv, trace, &ylift);
 }
 }  // namespace
 
@@ -2799,6 +2818,7 @@ struct NLPlan {
   u64* pw1;
   Dense d1;
   IVBuf iv1;
+  u64* Ye;                       // 6 x D1 ring words: the y side before its first fold
   u64** ydev;                    // 6 device pointers (kernel argument)
   // batch 2: AND gates
   GfPlan gf;
@@ -2810,6 +2830,7 @@ struct NLPlan {
   u64* pwb;
   Dense db;
   IVBuf ivb;
+  u64* Yb;                       // 2 x nb ring words: components 1 and 5 of the b2 bits
 };
 
 NLPlan plan_nl(Arena& a, int nst, const long long np[2]) {
@@ -2837,6 +2858,7 @@ NLPlan plan_nl(Arena& a, int nst, const long long np[2]) {
   const bool yc[6] = {true, true, true, true, true, true};
   p.d1 = plan_dense(a, p.D1, xc, yc);
   p.iv1 = plan_iv(a, dim_after(p.D1, p.R1));
+  p.Ye = a.take<u64>(6 * p.D1);
   p.ydev = a.take<u64*>(6);
   p.gf = plan_gf(a, andw, -1);
   p.nb = 64 * p.ne;
@@ -2848,6 +2870,7 @@ NLPlan plan_nl(Arena& a, int nst, const long long np[2]) {
   const bool by[6] = {false, true, false, false, false, true};
   p.db = plan_dense(a, p.nb, bx, by);
   p.ivb = plan_iv(a, dim_after(p.nb, p.Rb));
+  p.Yb = a.take<u64>(2 * p.nb);
   return p;
 }
 
@@ -2883,15 +2906,15 @@ int verify_nl(mpc_ctx* ctx, u64 vid, NLPlan& p, u64* trace) {
     reveal(ctx, P_VER_R, make_obj(vid, 0, 0), s.tmp6, s.r);
     if ((rc = power_table(ctx, s.r, v.pp, v.pw, s.aux))) return rc;
     Vec& x = v.dv.x[0];
-    Vec& y = v.dv.y[0];
+    Vec ylift;
     for (int c = 0; c < 6; ++c) {
       launch_gr_scale_rows(st, v.pw, p.MX + c * n, n, x.c[c]);
-      launch_gr_lift(st, p.MY + c * n, n, y.c[c]);
+      ylift.c[c] = p.MY + c * n;
     }
     CK(cudaMemsetAsync(s.zinit, 0, 384 * 8, st));
     launch_scalar_gr_sum(st, n, p.MZ, n, 6, v.pw, s.zinit);
     v.dv.cur = 0;
-    if ((rc = run_dense(ctx, vid, 0, v.dv, n, s.zinit, 1, v.R, s, v.iv, trace))) return rc;
+    if ((rc = run_dense(ctx, vid, 0, v.dv, n, s.zinit, 1, v.R, s, v.iv, trace, &ylift))) return rc;
   }
   u64* tr1 = trace ? trace + (long long)(p.vm.R + 1) * TRACE_ROUND : nullptr;
   // ---- batch 1: the edaBit inner products, weight r^e on row e (e over all stages)
@@ -2900,8 +2923,9 @@ int verify_nl(mpc_ctx* ctx, u64 vid, NLPlan& p, u64* trace) {
     reveal(ctx, P_VER_R, make_obj(vid, 1, 0), s.tmp6, s.r);
     launch_gr_powers(st, s.r, p.ne, p.pw1);
     Vec& x = p.d1.x[0];
-    Vec& y = p.d1.y[0];
-    CK(cudaMemcpyAsync(p.ydev, y.c, 6 * sizeof(u64*), cudaMemcpyHostToDevice, st));
+    Vec ylift;
+    for (int c = 0; c < 6; ++c) ylift.c[c] = p.Ye + c * p.D1;
+    CK(cudaMemcpyAsync(p.ydev, ylift.c, 6 * sizeof(u64*), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(s.zinit, 0, 384 * 8, st));
     long long e0 = 0;
     for (int q = 0; q < p.nst; ++q) {
@@ -2912,7 +2936,8 @@ int verify_nl(mpc_ctx* ctx, u64 vid, NLPlan& p, u64* trace) {
       e0 += c.np;
     }
     p.d1.cur = 0;
-    if ((rc = run_dense(ctx, vid, 1, p.d1, p.D1, s.zinit, 1, p.R1, s, p.iv1, tr1))) return rc;
+    if ((rc = run_dense(ctx, vid, 1, p.d1, p.D1, s.zinit, 1, p.R1, s, p.iv1, tr1, &ylift)))
+      return rc;
   }
   u64* tr2 = tr1 ? tr1 + (long long)(p.R1 + 1) * TRACE_ROUND : nullptr;
   // ---- batch 2: every AND gate over GF(2^64), stage by stage, level by level
@@ -2941,7 +2966,9 @@ int verify_nl(mpc_ctx* ctx, u64 vid, NLPlan& p, u64* trace) {
     reveal(ctx, P_VER_R, make_obj(vid, 3, 0), s.tmp6, s.r);
     if ((rc = power_table(ctx, s.r, p.ppb, p.pwb, s.aux))) return rc;
     Vec& x = p.db.x[0];
-    Vec& y = p.db.y[0];
+    Vec ylift{};   // components 1 and 5 of the b2 bits, as ring words
+    ylift.c[1] = p.Yb;
+    ylift.c[5] = p.Yb + p.nb;
     CK(cudaMemsetAsync(s.zinit, 0, 384 * 8, st));
     long long e0 = 0;
     for (int q = 0; q < p.nst; ++q) {
@@ -2949,12 +2976,15 @@ int verify_nl(mpc_ctx* ctx, u64 vid, NLPlan& p, u64* trace) {
       const long long N = 64 * c.np;
       for (int comp : {0, 3})
         launch_gr_scale_rows(st, p.pwb + e0 * 64, c.B1 + comp * N, N, x.c[comp] + e0 * 64);
-      for (int comp : {1, 5}) launch_gr_lift(st, c.B2 + comp * N, N, y.c[comp] + e0 * 64);
+      for (int comp : {1, 5})
+        CK(cudaMemcpyAsync(ylift.c[comp] + e0, c.B2 + comp * N, (size_t)N * 8,
+                           cudaMemcpyDeviceToDevice, st));
       launch_scalar_gr_sum(st, N, c.eprod, N, 6, p.pwb + e0 * 64, s.zinit);
       e0 += N;
     }
     p.db.cur = 0;
-    if ((rc = run_dense(ctx, vid, 3, p.db, p.nb, s.zinit, 1, p.Rb, s, p.ivb, tr3))) return rc;
+    if ((rc = run_dense(ctx, vid, 3, p.db, p.nb, s.zinit, 1, p.Rb, s, p.ivb, tr3, &ylift)))
+      return rc;
   }
   return MPC_OK;
 }

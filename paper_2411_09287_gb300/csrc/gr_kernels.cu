@@ -345,6 +345,74 @@ __global__ void k_gr_lift(const u64* __restrict__ s, long long n, u64* __restric
     out[w] = ((w & 63) == 0) ? s[w >> 6] : 0ull;
 }
 
+// First Pi_Reduce round of a claim whose y vectors are lifted ring elements (Fig. MTP: y_i = lift
+// of a ring word Y_i): the Gram sum G(u, lift(V)) has one non-zero column, so a party sum of the
+// round is sum_i V_i u_i, a scalar-weighted sum of GR rows.  For the Dh element pairs of x (rows
+// of 64 words) and the words Y (one per element), with A = x0 + x1 and the party terms
+//   P0: A (Y0 + Y1),  P1: -(x2 Y3 + x3 Y2),  P2: x4 (Y4 - Y5) - x5 Y4
+// (absent components null), adds to S the sums over the pairs of the even elements (ee), the odd
+// ones (oo) and the cross terms V_{2i+1} A_{2i} + V_{2i} A_{2i+1} (xo): S[0..2] = ee of P0..P2,
+// S[3..5] = xo, S[9..11] = oo, 64 words each.  Element 2 Dh - 1 may be the zero padding: Y
+// words past D read as 0.
+struct LiftedIn {
+  const u64* x[6];
+  const u64* y[6];
+};
+__global__ void k_gram_lifted(LiftedIn in, long long Dh, long long D, u64* __restrict__ S) {
+  const int c = threadIdx.x & 63;       // GR coefficient
+  const int slot = threadIdx.x >> 6;    // pair slot of the block (4 per block)
+  u64 acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};   // [party][ee, xo, oo]
+  for (long long i = (long long)blockIdx.x * 4 + slot; i < Dh; i += (long long)gridDim.x * 4) {
+    const long long e0 = 2 * i, e1 = 2 * i + 1;
+    u64 xe[6], xo[6], ye[6], yo[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      xe[k] = in.x[k] ? in.x[k][e0 * 64 + c] : 0ull;
+      xo[k] = in.x[k] ? in.x[k][e1 * 64 + c] : 0ull;
+      ye[k] = in.y[k] ? in.y[k][e0] : 0ull;
+      yo[k] = (in.y[k] && e1 < D) ? in.y[k][e1] : 0ull;
+    }
+    const u64 ae = xe[0] + xe[1], ao = xo[0] + xo[1];
+    const u64 ve = ye[0] + ye[1], vo = yo[0] + yo[1];
+    acc[0][0] += ve * ae;
+    acc[0][1] += vo * ae + ve * ao;
+    acc[0][2] += vo * ao;
+    acc[1][0] -= ye[3] * xe[2] + ye[2] * xe[3];
+    acc[1][1] -= yo[3] * xe[2] + ye[3] * xo[2] + yo[2] * xe[3] + ye[2] * xo[3];
+    acc[1][2] -= yo[3] * xo[2] + yo[2] * xo[3];
+    const u64 we = ye[4] - ye[5], wo = yo[4] - yo[5];
+    acc[2][0] += we * xe[4] - ye[4] * xe[5];
+    acc[2][1] += wo * xe[4] + we * xo[4] - (yo[4] * xe[5] + ye[4] * xo[5]);
+    acc[2][2] += wo * xo[4] - yo[4] * xo[5];
+  }
+  // the block's 4 slots, then one atomic add per (party, block, coefficient)
+  __shared__ u64 red[3][3][4][64];
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) red[p][b][slot][c] = acc[p][b];
+  __syncthreads();
+  for (int t = threadIdx.x; t < 9 * 64; t += blockDim.x) {
+    const int p = t / 192, b = (t / 64) % 3, cc = t & 63;
+    const u64 v = red[p][b][0][cc] + red[p][b][1][cc] + red[p][b][2][cc] + red[p][b][3][cc];
+    const int blk = b == 0 ? 0 : (b == 1 ? 3 : 9);   // ee -> S00, xo -> S01, oo -> S11
+    atomicAdd(reinterpret_cast<unsigned long long*>(S + (blk + p) * 64 + cc), (unsigned long long)v);
+  }
+}
+
+// The fold of a lifted y vector: out_i = lift(Y_{2i}) + f (Y_{2i+1} - Y_{2i}) for i < Dh (f: the
+// fold's GR element, 64 words; Y words past D read as 0), out rows of 64 words.
+__global__ void k_fold_lifted(const u64* __restrict__ Y, long long Dh, long long D,
+                              const u64* __restrict__ f, u64* __restrict__ out) {
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < Dh * 64;
+       w += (long long)gridDim.x * blockDim.x) {
+    const long long i = w >> 6;
+    const int c = (int)(w & 63);
+    const u64 y0 = Y[2 * i], y1 = 2 * i + 1 < D ? Y[2 * i + 1] : 0ull;
+    out[w] = (c == 0 ? y0 : 0ull) + f[c] * (y1 - y0);
+  }
+}
+
 __global__ void k_fill(u64* __restrict__ p, long long n, u64 v) {
   for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < n;
        w += (long long)gridDim.x * blockDim.x)
@@ -807,6 +875,25 @@ void launch_gr_scale_rows(cudaStream_t st, const u64* pw, const u64* s, long lon
 void launch_gr_lift(cudaStream_t st, const u64* s, long long n, u64* out) {
   if (n <= 0) return;
   k_gr_lift<<<grid_for(n * 64), TPB, 0, st>>>(s, n, out);
+}
+
+void launch_gram_lifted(cudaStream_t st, const u64* const x[6], const u64* const y[6], long long Dh,
+                        long long D, u64* S) {
+  if (Dh <= 0) return;
+  LiftedIn in;
+  for (int k = 0; k < 6; ++k) {
+    in.x[k] = x[k];
+    in.y[k] = y[k];
+  }
+  long long g = (Dh + 3) / 4;
+  if (g > 152 * 8) g = 152 * 8;
+  k_gram_lifted<<<(unsigned)g, 256, 0, st>>>(in, Dh, D, S);
+}
+
+void launch_fold_lifted(cudaStream_t st, const u64* Y, long long Dh, long long D, const u64* f,
+                        u64* out) {
+  if (Dh <= 0) return;
+  k_fold_lifted<<<grid_for(Dh * 64), TPB, 0, st>>>(Y, Dh, D, f, out);
 }
 
 void launch_fill(cudaStream_t st, u64* p, long long n, u64 v) {

@@ -195,6 +195,14 @@ void launch_gr_combine_z(cudaStream_t st, const u64* coef, const u64* h0, const 
                          const u64* z, u64* znew);
 void launch_gr_scale_rows(cudaStream_t st, const u64* pw, const u64* s, long long n, u64* out);
 void launch_gr_lift(cudaStream_t st, const u64* s, long long n, u64* out);
+// First-round party sums and folds of a claim whose y vectors are lifted ring words (one word per
+// element, components null when absent): S (12 x 64 words, accumulated) receives the party sums
+// of the even pairs at S[0..2], of the cross terms at S[3..5] and of the odd pairs at S[9..11];
+// out_i = lift(Y_{2i}) + f (Y_{2i+1} - Y_{2i}).  Words at or past D read as 0.
+void launch_gram_lifted(cudaStream_t st, const u64* const x[6], const u64* const y[6], long long Dh,
+                        long long D, u64* S);
+void launch_fold_lifted(cudaStream_t st, const u64* Y, long long Dh, long long D, const u64* f,
+                        u64* out);
 void launch_fill(cudaStream_t st, u64* p, long long n, u64 v);
 void launch_neg_copy(cudaStream_t st, const u64* a, long long n, u64* out);
 void launch_gr_check_zero(cudaStream_t st, const u64* v, u32* status, u32 flag);

@@ -505,8 +505,9 @@ __global__ void k_open_xor(const u64* __restrict__ m, const u64* __restrict__ r1
 }
 
 // Pi_Tran of the edaBit inner products (rows e of dimension 64, weight r^(e0 + e) on row e):
-// x'_{(e0+e) 64 + i} = r^(e0+e) <m_i> (components 2 and 4 only: <m_i> has no mask) and
-// y'_{(e0+e) 64 + i} = lift(2^(i+1) <r'_i>) (all components), as GR vectors (64 words per entry).
+// x'_{(e0+e) 64 + i} = r^(e0+e) <m_i> (components 2 and 4 only: <m_i> has no mask) as GR vectors
+// (64 words per entry), and y_{(e0+e) 64 + i} = 2^(i+1) <r'_i> (all components) as ring words, one
+// per entry (the lifted vectors' first round reads them as such).
 __global__ void k_eda_tran(const u64* __restrict__ mbits, const u64* __restrict__ rp, long long np,
                            const u64* __restrict__ pw, long long e0, u64* __restrict__ x2,
                            u64* __restrict__ x4, u64* const* __restrict__ y) {
@@ -522,7 +523,7 @@ __global__ void k_eda_tran(const u64* __restrict__ mbits, const u64* __restrict_
     const u64 xv = m ? pw[(e0 + e) * 64 + k] : 0ull;
     x2[row * 64 + k] = xv;
     x4[row * 64 + k] = xv;
-    for (int c = 0; c < 6; ++c) y[c][row * 64 + k] = k == 0 ? shl_mod(rp[c * N + j], i + 1) : 0ull;
+    if (k < 6) y[k][row] = shl_mod(rp[k * N + j], i + 1);   // component k of the ring word
   }
 }
 
