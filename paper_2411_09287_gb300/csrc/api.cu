@@ -666,57 +666,55 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
   launch_gr_combine_z(st, s.coef, s.h0, s.h2, z, zo);
   launch_gr_mulmat2(st, s.coef, nullptr, s.MM);   // M_zeta
   // f(zeta) = f(0) + zeta (f(1) - f(0)): rows [x_{2i+1} - x_{2i}] times M_zeta, plus x_{2i}.
-  // When the vectors present sit at one stride (x_0, y_0, x_1, y_1, ... as the dense plans
-  // allocate them, skipping absent components), all of them go through one launch: segment s of
-  // Dh rows (padded to whole tiles).  Only short vectors are batched: there one launch replaces
-  // several latency-bound ones, while on long ones the segment arithmetic of the batched row map
-  // costs more than the launches it saves.
-  bool batched = false;
-  if (ctx->gemm_path == MPC_GEMM_LIMB_TC && Dh <= ctx->tune.fold_batch_max) {
-    const u64* ins[12];
-    u64* outs[12];
-    int n = 0;
-    bool even = true;
-    for (int c = 0; c < 6; ++c)
-      for (int side = 0; side < (ys ? 1 : 2); ++side) {
-        const u64* in = side ? y.c[c] : x.c[c];
-        u64* out = side ? yo.c[c] : xo.c[c];
-        if (!in) continue;
-        even = even && out;
-        ins[n] = in;
-        outs[n] = out;
+  // When the vectors present on one side sit at one stride (as the dense plans allocate them),
+  // all of that side's go through one launch: segment s of Dh rows (padded to whole tiles).  Only
+  // short vectors are batched: there one launch replaces several latency-bound ones, while on long
+  // ones the segment arithmetic of the batched row map costs more than the launches it saves.
+  for (int side = 0; side < (ys ? 1 : 2); ++side) {
+    const Vec& vin = side ? y : x;
+    Vec& vout = side ? yo : xo;
+    bool batched = false;
+    if (ctx->gemm_path == MPC_GEMM_LIMB_TC && Dh <= ctx->tune.fold_batch_max) {
+      const u64* ins[6];
+      u64* outs[6];
+      int n = 0;
+      bool even = true;
+      for (int c = 0; c < 6; ++c) {
+        if (!vin.c[c]) continue;
+        even = even && vout.c[c];
+        ins[n] = vin.c[c];
+        outs[n] = vout.c[c];
         ++n;
       }
-    even = even && n >= 2;
-    const long long sin = even ? ins[1] - ins[0] : 0, sout = even ? outs[1] - outs[0] : 0;
-    for (int i = 1; i < n && even; ++i)
-      even = ins[i] - ins[0] == i * sin && outs[i] - outs[0] == i * sout;
-    if (even && sin > 0 && sout > 0) {
-      const long long Rp = (Dh + 127) / 128 * 128;
-      GrMMArgs g = grargs(ctx);
-      g.R = n * Rp;
-      g.p0 = ins[0] + 64;
-      g.p1 = ins[0];
-      g.s1 = ~0ull;
-      g.in = GrRowMap{Rp, 128, sin};
-      g.qvalid = Dh;
-      g.Mmat = s.MM;
-      g.add0 = ins[0];
-      g.add0_in = 1;
-      g.out = outs[0];
-      g.om = GrRowMap{Rp, 64, sout};
-      g_launches += 1;
-      Phase kp(ctx, MPC_PROF_K_GR_MATMUL, (double)n * Dh * 4096);
-      batched = gr_matmul_tc_ex(st, g, ctx->status, ST_TIMEOUT) == 0;
-      if (!batched) g_launches -= 1;
+      even = even && n >= 2;
+      const long long sin = even ? ins[1] - ins[0] : 0, sout = even ? outs[1] - outs[0] : 0;
+      for (int i = 1; i < n && even; ++i)
+        even = ins[i] - ins[0] == i * sin && outs[i] - outs[0] == i * sout;
+      if (even && sin > 0 && sout > 0) {
+        const long long Rp = (Dh + 127) / 128 * 128;
+        GrMMArgs g = grargs(ctx);
+        g.R = n * Rp;
+        g.p0 = ins[0] + 64;
+        g.p1 = ins[0];
+        g.s1 = ~0ull;
+        g.in = GrRowMap{Rp, 128, sin};
+        g.qvalid = Dh;
+        g.Mmat = s.MM;
+        g.add0 = ins[0];
+        g.add0_in = 1;
+        g.out = outs[0];
+        g.om = GrRowMap{Rp, 64, sout};
+        g_launches += 1;
+        Phase kp(ctx, MPC_PROF_K_GR_MATMUL, (double)n * Dh * 4096);
+        batched = gr_matmul_tc_ex(st, g, ctx->status, ST_TIMEOUT) == 0;
+        if (!batched) g_launches -= 1;
+      }
     }
-  }
-  for (int c = 0; c < 6 && !batched; ++c) {
-    for (int side = 0; side < (ys ? 1 : 2); ++side) {
-      const u64* in = side ? y.c[c] : x.c[c];
-      u64* out = side ? yo.c[c] : xo.c[c];
+    for (int c = 0; c < 6 && !batched; ++c) {
+      const u64* in = vin.c[c];
       if (!in) continue;
-      if ((rc = gr_matmul(ctx, Dh, in + 64, in, ~0ull, 128, s.MM, in, 128, out, 64))) return rc;
+      if ((rc = gr_matmul(ctx, Dh, in + 64, in, ~0ull, 128, s.MM, in, 128, vout.c[c], 64)))
+        return rc;
     }
   }
   if (ys)   // the fold element is the first GR element of the Lagrange coefficients
@@ -850,16 +848,21 @@ long long dim_after(long long D, int R) {
   return D;
 }
 
-// Allocate ping-pong vectors for a dense claim of dimension D over the present components.
-Dense plan_dense(Arena& a, long long D, const bool xc[6], const bool yc[6]) {
+// Allocate ping-pong vectors for a dense claim of dimension D over the present components.  With
+// ylifted_R >= 1 the y side enters in ring words (run_dense's ylift) and the first round writes
+// slot 1, so slot 0 of y only ever holds the outputs of round 2 and later (at most cap[1] rows).
+Dense plan_dense(Arena& a, long long D, const bool xc[6], const bool yc[6], int ylifted_R = 0) {
   Dense d;
   d.cap[0] = D + 1;
   d.cap[1] = (D + 1) / 2 + 1;
-  for (int i = 0; i < 2; ++i)
-    for (int c = 0; c < 6; ++c) {
-      d.x[i].c[c] = xc[c] ? a.take<u64>(d.cap[i] * 64) : nullptr;
-      d.y[i].c[c] = yc[c] ? a.take<u64>(d.cap[i] * 64) : nullptr;
-    }
+  const long long ycap0 = ylifted_R >= 1 ? d.cap[1] : d.cap[0];
+  // a slot's x vectors, then its y vectors: each side's present vectors sit at one stride (the
+  // batched folds use that)
+  for (int i = 0; i < 2; ++i) {
+    for (int c = 0; c < 6; ++c) d.x[i].c[c] = xc[c] ? a.take<u64>(d.cap[i] * 64) : nullptr;
+    for (int c = 0; c < 6; ++c)
+      d.y[i].c[c] = yc[c] ? a.take<u64>((i ? d.cap[1] : ycap0) * 64) : nullptr;
+  }
   return d;
 }
 
@@ -987,7 +990,7 @@ VMultPlan plan_vmult(Arena& a, long long n, int R) {
   p.pw = a.take<u64>(n * 64);
   p.pp = plan_pow(a, n);
   const bool all[6] = {true, true, true, true, true, true};
-  p.dv = plan_dense(a, n, all, all);
+  p.dv = plan_dense(a, n, all, all, p.R);
   p.iv = plan_iv(a, dim_after(n, p.R));
   return p;
 }
@@ -2856,7 +2859,7 @@ NLPlan plan_nl(Arena& a, int nst, const long long np[2]) {
   p.pw1 = a.take<u64>(p.ne * 64);
   const bool xc[6] = {false, false, true, false, true, false};
   const bool yc[6] = {true, true, true, true, true, true};
-  p.d1 = plan_dense(a, p.D1, xc, yc);
+  p.d1 = plan_dense(a, p.D1, xc, yc, p.R1);
   p.iv1 = plan_iv(a, dim_after(p.D1, p.R1));
   p.Ye = a.take<u64>(6 * p.D1);
   p.ydev = a.take<u64*>(6);
@@ -2868,7 +2871,7 @@ NLPlan plan_nl(Arena& a, int nst, const long long np[2]) {
   p.ppb = plan_pow(a, p.nb);
   const bool bx[6] = {true, false, false, true, false, false};
   const bool by[6] = {false, true, false, false, false, true};
-  p.db = plan_dense(a, p.nb, bx, by);
+  p.db = plan_dense(a, p.nb, bx, by, p.Rb);
   p.ivb = plan_iv(a, dim_after(p.nb, p.Rb));
   p.Yb = a.take<u64>(2 * p.nb);
   return p;
