@@ -512,12 +512,12 @@ def main():
         # pipelined uploads: step k + 1's inputs go up on the context's copy stream
         # (mpc_h2d_async) while step k runs; step k's stream waits for its own slot
         # (mpc_h2d_wait); every step's output comes back to pinned host memory in its Pi_Rec
-        Xd = [L.ctx.empty(M * K) for _ in range(2)]
-        Wd = [L.ctx.empty(K * N) for _ in range(2)]
+        Xu = [L.ctx.empty(M * K) for _ in range(2)]
+        Wu = [L.ctx.empty(K * N) for _ in range(2)]
 
         def upload(k):
-            L.ctx.h2d_async(Xd[k % 2], Xh, k % 2)
-            L.ctx.h2d_async(Wd[k % 2], Wh, k % 2)
+            L.ctx.h2d_async(Xu[k % 2], Xh, k % 2)
+            L.ctx.h2d_async(Wu[k % 2], Wh, k % 2)
 
         if world > 1:
             dist.barrier()
@@ -527,7 +527,7 @@ def main():
             L.ctx.h2d_wait(k % 2)
             if k + 1 < e_steps:
                 upload(k + 1)
-            L.step(L.P(Xd[k % 2]), L.P(Wd[k % 2]), 0, L.P(Oh), 1)
+            L.step(L.P(Xu[k % 2]), L.P(Wu[k % 2]), 0, L.P(Oh), 1)
         torch.cuda.synchronize()
         dt = max_over_ranks((time.perf_counter() - t0) / e_steps, world)
         L.sampled_check()
@@ -535,7 +535,7 @@ def main():
                "h2d_bytes_per_step": (M * K + K * N) * 8, "d2h_bytes_per_step": E * 8,
                "steps": e_steps, "upload": "pinned host inputs, mpc_h2d_async one step ahead on "
                                            "the context's copy stream"}
-        del Xh, Wh, Oh, Xd, Wd
+        del Xh, Wh, Oh, Xu, Wu
 
     ms = max_over_ranks(ms, world)
     value = job_value(0, world, ms * 1e-3, (M, N, K))
