@@ -8,9 +8,9 @@ Step = the whole hot path on one batch of synthetic input (default n = M = N = K
   Pi_Rec of the M x N output
 Metric: secure ring-MAC/s = M N K / step time (plaintext-equivalent multiply-accumulates of the
 secure product, verification included).  Inputs are resident in HBM when timing starts ("value");
-"e2e" repeats the step through the same C-ABI with the inputs in pinned host memory (each step's
-inputs uploaded by mpc_h2d_async one step ahead, on the context's copy stream) and the output read
-back to pinned host memory by each step's Pi_Rec.
+"e2e" repeats the step through the same C-ABI with the inputs and the output in pinned host
+memory: each step's inputs are uploaded by mpc_h2d_async one step ahead and its output downloaded
+by mpc_d2h_async one step behind, on the context's copy stream.
 
 The same step also runs on the other GEMM path (the u64 CUDA-core products when the main path is
 the limb-split tensor-core one) on the same layer and inputs, reported under "other_path".
@@ -508,12 +508,15 @@ def main():
         host_args = (L.P(Xh), L.P(Wh), 1, L.P(Oh), 1)
         L.step(*host_args)
         torch.cuda.synchronize()
-        e_steps = max(1, min(args.steps, 3))
-        # pipelined uploads: step k + 1's inputs go up on the context's copy stream
-        # (mpc_h2d_async) while step k runs; step k's stream waits for its own slot
-        # (mpc_h2d_wait); every step's output comes back to pinned host memory in its Pi_Rec
+        e_steps = max(1, args.steps)
+        # pipelined copies: step k + 1's inputs go up on the context's copy stream
+        # (mpc_h2d_async) while step k runs, and step k's output comes down on it
+        # (mpc_d2h_async) while step k + 1 runs; mpc_h2d_wait orders each step after its
+        # upload, and the reuse of an output buffer after its download
         Xu = [L.ctx.empty(M * K) for _ in range(2)]
         Wu = [L.ctx.empty(K * N) for _ in range(2)]
+        Od = [L.ctx.empty(E) for _ in range(2)]
+        Ohs = [Oh, torch.empty(E, dtype=torch.int64).pin_memory()]
 
         def upload(k):
             L.ctx.h2d_async(Xu[k % 2], Xh, k % 2)
@@ -527,15 +530,27 @@ def main():
             L.ctx.h2d_wait(k % 2)
             if k + 1 < e_steps:
                 upload(k + 1)
-            L.step(L.P(Xu[k % 2]), L.P(Wu[k % 2]), 0, L.P(Oh), 1)
-        torch.cuda.synchronize()
+            if k >= 2:
+                L.ctx.h2d_wait(2 + k % 2)
+            L.step(L.P(Xu[k % 2]), L.P(Wu[k % 2]), 0, L.P(Od[k % 2]), 0)
+            L.ctx.d2h_async(Ohs[k % 2], Od[k % 2], 2 + k % 2)
+        torch.cuda.synchronize()   # the device, copy stream included
         dt = max_over_ranks((time.perf_counter() - t0) / e_steps, world)
         L.sampled_check()
+        # the last download equals the last step's output opened again on the device
+        od = torch.empty(E, dtype=torch.int64, device=L.out_dev.device)
+        L.check(L.lib.mpc_reconstruct(L.h, L.P(L.zout), E, L.P(od), 0, L.P(L.ws), L.wsb),
+                "reconstruct e2e output")
+        if not torch.equal(od.cpu(), Ohs[(e_steps - 1) % 2]):
+            raise SystemExit("e2e: the downloaded output differs from the device-side opening")
+        del od
         e2e = {"value": job_value(0, world, dt, (M, N, K)), "unit": UNIT, "ms_per_step": dt * 1e3,
                "h2d_bytes_per_step": (M * K + K * N) * 8, "d2h_bytes_per_step": E * 8,
-               "steps": e_steps, "upload": "pinned host inputs, mpc_h2d_async one step ahead on "
-                                           "the context's copy stream"}
-        del Xh, Wh, Oh, Xu, Wu
+               "steps": e_steps, "copies": "pinned host buffers; each step's inputs uploaded by "
+                                           "mpc_h2d_async one step ahead and its output "
+                                           "downloaded by mpc_d2h_async one step behind, on the "
+                                           "context's copy stream"}
+        del Xh, Wh, Oh, Ohs, Xu, Wu, Od
 
     ms = max_over_ranks(ms, world)
     value = job_value(0, world, ms * 1e-3, (M, N, K))

@@ -142,16 +142,22 @@ int mpc_create(const mpc_config* cfg, mpc_ctx** out);
 void mpc_destroy(mpc_ctx* ctx);
 /* Description of the last failure of this context ("" if none).  Owned by the context. */
 const char* mpc_last_error(const mpc_ctx* ctx);
-/* ---- asynchronous uploads --------------------------------------------------------------------
- * A pipelined caller uploads the next step's inputs while the current step runs:
- * mpc_h2d_async copies `bytes` from host `src` (pinned memory, for the copy to overlap) to device
- * `dst` on the context's copy stream (created on first use) and records the copy under `slot`
- * (0 .. MPC_H2D_SLOTS - 1); mpc_h2d_wait makes the context's stream wait, on the device, for the
- * copies last recorded under `slot` (no host synchronisation; a slot never used is a no-op).  The
- * caller owns both buffers and must not reuse `dst` before the work that reads it has run.
+/* ---- asynchronous copies ---------------------------------------------------------------------
+ * A pipelined caller uploads the next step's inputs and downloads the last step's result while
+ * the current step runs:
+ *   mpc_h2d_async copies `bytes` from host `src` (pinned memory, for the copy to overlap) to
+ *     device `dst` on the context's copy stream (created on first use);
+ *   mpc_d2h_async copies `bytes` from device `src` to host `dst` (pinned) on the copy stream,
+ *     after the work enqueued so far on the context's stream (which writes `src`);
+ * each records the copy under `slot` (0 .. MPC_H2D_SLOTS - 1).  mpc_h2d_wait makes the context's
+ * stream wait, on the device, for the copy last recorded under `slot` (no host synchronisation; a
+ * slot never used is a no-op): before work that reads an uploaded buffer, or that rewrites a
+ * buffer still being downloaded.  A download is complete on the host after a device
+ * synchronisation.  The caller owns all buffers.
  * Returns MPC_OK, MPC_ERR_ARG (null pointer, zero bytes, bad slot) or MPC_ERR_CUDA. */
 #define MPC_H2D_SLOTS 4
 int mpc_h2d_async(mpc_ctx* ctx, void* dst, const void* src, size_t bytes, int slot);
+int mpc_d2h_async(mpc_ctx* ctx, void* dst, const void* src, size_t bytes, int slot);
 int mpc_h2d_wait(mpc_ctx* ctx, int slot);
 
 /* Run subsequent work on `stream` (cudaStream_t). */

@@ -30,6 +30,7 @@ _SIGS = {
     "mpc_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mpc_h2d_async": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]),
     "mpc_h2d_wait": (C.c_int, [C.c_void_p, C.c_int]),
+    "mpc_d2h_async": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]),
     "mpc_sync": (C.c_int, [C.c_void_p]),
     "mpc_set_tuning": (C.c_int, [C.c_void_p, C.POINTER(MpcTuning)]),
     "mpc_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(MpcTuning)]),

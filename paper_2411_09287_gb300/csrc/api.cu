@@ -183,6 +183,7 @@ struct mpc_ctx {
   // asynchronous uploads (mpc_h2d_async): a copy stream and one event per slot
   cudaStream_t copy_st = nullptr;
   cudaEvent_t copy_ev[MPC_H2D_SLOTS] = {};
+  cudaEvent_t order_ev = nullptr;   // the context stream's work before a download
 };
 
 namespace {
@@ -666,56 +667,55 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
   launch_gr_combine_z(st, s.coef, s.h0, s.h2, z, zo);
   launch_gr_mulmat2(st, s.coef, nullptr, s.MM);   // M_zeta
   // f(zeta) = f(0) + zeta (f(1) - f(0)): rows [x_{2i+1} - x_{2i}] times M_zeta, plus x_{2i}.
-  // When the vectors present on one side sit at one stride (as the dense plans allocate them),
-  // all of that side's go through one launch: segment s of Dh rows (padded to whole tiles).  Only
-  // short vectors are batched: there one launch replaces several latency-bound ones, while on long
-  // ones the segment arithmetic of the batched row map costs more than the launches it saves.
-  for (int side = 0; side < (ys ? 1 : 2); ++side) {
-    const Vec& vin = side ? y : x;
-    Vec& vout = side ? yo : xo;
-    bool batched = false;
-    if (ctx->gemm_path == MPC_GEMM_LIMB_TC && Dh <= ctx->tune.fold_batch_max) {
-      const u64* ins[6];
-      u64* outs[6];
-      int n = 0;
-      bool even = true;
-      for (int c = 0; c < 6; ++c) {
-        if (!vin.c[c]) continue;
-        even = even && vout.c[c];
-        ins[n] = vin.c[c];
-        outs[n] = vout.c[c];
-        ++n;
-      }
-      even = even && n >= 2;
-      const long long sin = even ? ins[1] - ins[0] : 0, sout = even ? outs[1] - outs[0] : 0;
-      for (int i = 1; i < n && even; ++i)
-        even = ins[i] - ins[0] == i * sin && outs[i] - outs[0] == i * sout;
-      if (even && sin > 0 && sout > 0) {
-        const long long Rp = (Dh + 127) / 128 * 128;
-        GrMMArgs g = grargs(ctx);
-        g.R = n * Rp;
-        g.p0 = ins[0] + 64;
-        g.p1 = ins[0];
-        g.s1 = ~0ull;
-        g.in = GrRowMap{Rp, 128, sin};
-        g.qvalid = Dh;
-        g.Mmat = s.MM;
-        g.add0 = ins[0];
-        g.add0_in = 1;
-        g.out = outs[0];
-        g.om = GrRowMap{Rp, 64, sout};
-        g_launches += 1;
-        Phase kp(ctx, MPC_PROF_K_GR_MATMUL, (double)n * Dh * 4096);
-        batched = gr_matmul_tc_ex(st, g, ctx->status, ST_TIMEOUT) == 0;
-        if (!batched) g_launches -= 1;
-      }
-    }
-    for (int c = 0; c < 6 && !batched; ++c) {
-      const u64* in = vin.c[c];
+  // Vectors that sit at one stride (the dense plans put a slot's x vectors, then its y vectors,
+  // one after another) go through one launch: segment s of Dh rows (padded to whole tiles); all
+  // of them when x's and y's rows have the same capacity, else each side's.  Only short vectors
+  // are batched: there one launch replaces several latency-bound ones, while on long ones the
+  // segment arithmetic of the batched row map costs more than the launches it saves.
+  auto fold_batched = [&](const u64* const* ins, u64* const* outs, int n) -> bool {
+    if (ctx->gemm_path != MPC_GEMM_LIMB_TC || Dh > ctx->tune.fold_batch_max || n < 2) return false;
+    const long long sin = ins[1] - ins[0], sout = outs[1] - outs[0];
+    for (int i = 1; i < n; ++i)
+      if (ins[i] - ins[0] != i * sin || outs[i] - outs[0] != i * sout) return false;
+    if (sin <= 0 || sout <= 0) return false;
+    const long long Rp = (Dh + 127) / 128 * 128;
+    GrMMArgs g = grargs(ctx);
+    g.R = n * Rp;
+    g.p0 = ins[0] + 64;
+    g.p1 = ins[0];
+    g.s1 = ~0ull;
+    g.in = GrRowMap{Rp, 128, sin};
+    g.qvalid = Dh;
+    g.Mmat = s.MM;
+    g.add0 = ins[0];
+    g.add0_in = 1;
+    g.out = outs[0];
+    g.om = GrRowMap{Rp, 64, sout};
+    g_launches += 1;
+    Phase kp(ctx, MPC_PROF_K_GR_MATMUL, (double)n * Dh * 4096);
+    if (gr_matmul_tc_ex(st, g, ctx->status, ST_TIMEOUT) == 0) return true;
+    g_launches -= 1;
+    return false;
+  };
+  const u64* ins[12];
+  u64* outs[12];
+  int nx = 0, n = 0;
+  for (int side = 0; side < (ys ? 1 : 2); ++side)
+    for (int c = 0; c < 6; ++c) {
+      const u64* in = side ? y.c[c] : x.c[c];
       if (!in) continue;
-      if ((rc = gr_matmul(ctx, Dh, in + 64, in, ~0ull, 128, s.MM, in, 128, vout.c[c], 64)))
-        return rc;
+      ins[n] = in;
+      outs[n] = side ? yo.c[c] : xo.c[c];
+      ++n;
+      if (!side) ++nx;
     }
+  bool done_all = fold_batched(ins, outs, n);
+  for (int side = 0; side < (ys ? 1 : 2) && !done_all; ++side) {
+    const int i0 = side ? nx : 0, i1 = side ? n : nx;
+    if (fold_batched(ins + i0, outs + i0, i1 - i0)) continue;
+    for (int i = i0; i < i1; ++i)
+      if ((rc = gr_matmul(ctx, Dh, ins[i] + 64, ins[i], ~0ull, 128, s.MM, ins[i], 128, outs[i], 64)))
+        return rc;
   }
   if (ys)   // the fold element is the first GR element of the Lagrange coefficients
     for (int c = 0; c < 6; ++c)
@@ -1580,6 +1580,7 @@ void mpc_destroy(mpc_ctx* ctx) {
   }
   for (cudaEvent_t e : ctx->copy_ev)
     if (e) cudaEventDestroy(e);
+  if (ctx->order_ev) cudaEventDestroy(ctx->order_ev);
   for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
   if (ctx->cst) cudaFree(ctx->cst);
   if (ctx->own_stream && ctx->st) cudaStreamDestroy(ctx->st);
@@ -1596,6 +1597,21 @@ int mpc_h2d_async(mpc_ctx* ctx, void* dst, const void* src, size_t bytes, int sl
   if (!ctx->copy_st) CK(cudaStreamCreateWithFlags(&ctx->copy_st, cudaStreamNonBlocking));
   if (!ctx->copy_ev[slot]) CK(cudaEventCreateWithFlags(&ctx->copy_ev[slot], cudaEventDisableTiming));
   CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->copy_st));
+  CK(cudaEventRecord(ctx->copy_ev[slot], ctx->copy_st));
+  return MPC_OK;
+}
+
+int mpc_d2h_async(mpc_ctx* ctx, void* dst, const void* src, size_t bytes, int slot) {
+  int rc = guard(ctx);
+  if (rc) return rc;
+  if (!dst || !src || bytes == 0 || slot < 0 || slot >= MPC_H2D_SLOTS)
+    return fail(ctx, MPC_ERR_ARG, "d2h_async: bad argument");
+  if (!ctx->copy_st) CK(cudaStreamCreateWithFlags(&ctx->copy_st, cudaStreamNonBlocking));
+  if (!ctx->copy_ev[slot]) CK(cudaEventCreateWithFlags(&ctx->copy_ev[slot], cudaEventDisableTiming));
+  if (!ctx->order_ev) CK(cudaEventCreateWithFlags(&ctx->order_ev, cudaEventDisableTiming));
+  CK(cudaEventRecord(ctx->order_ev, ctx->st));   // after the work that writes src
+  CK(cudaStreamWaitEvent(ctx->copy_st, ctx->order_ev, 0));
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->copy_st));
   CK(cudaEventRecord(ctx->copy_ev[slot], ctx->copy_st));
   return MPC_OK;
 }

@@ -128,8 +128,16 @@ class Context:
         self._check(self.lib.mpc_h2d_async(self.h, C.c_void_p(_ptr(dst)), C.c_void_p(_ptr(src)),
                                            nbytes, slot))
 
+    def d2h_async(self, dst, src, slot: int = 0):
+        """mpc_d2h_async: copy the device tensor `src` into the host tensor `dst` (pinned) on the
+        copy stream, after the work enqueued so far; recorded under `slot`."""
+        nbytes = src.numel() * src.element_size()
+        assert dst.numel() * dst.element_size() >= nbytes
+        self._check(self.lib.mpc_d2h_async(self.h, C.c_void_p(_ptr(dst)), C.c_void_p(_ptr(src)),
+                                           nbytes, slot))
+
     def h2d_wait(self, slot: int = 0):
-        """mpc_h2d_wait: the context's stream waits (on the device) for the copies of `slot`."""
+        """mpc_h2d_wait: the context's stream waits (on the device) for the copy of `slot`."""
         self._check(self.lib.mpc_h2d_wait(self.h, slot))
 
     def close(self):

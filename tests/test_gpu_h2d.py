@@ -1,6 +1,7 @@
-"""Asynchronous uploads (mpc_h2d_async / mpc_h2d_wait): a sharing of inputs uploaded on the copy
-stream equals the sharing of the same inputs passed as host memory, word for word, with the
-uploads of the next step in flight while the current one runs; bad arguments are refused."""
+"""Asynchronous copies (mpc_h2d_async / mpc_d2h_async / mpc_h2d_wait): a sharing of inputs
+uploaded on the copy stream equals the sharing of the same inputs passed as host memory, word for
+word, with the uploads of the next step in flight while the current one runs; an opened result
+downloaded on the copy stream equals the one read back by Pi_Rec; bad arguments are refused."""
 import hashlib
 
 import numpy as np
@@ -52,3 +53,17 @@ def test_upload_arguments_are_checked(mpc):
         with pytest.raises(mpc.MpcError):
             ctx.h2d_wait(bad)
     ctx.h2d_wait(3)   # a slot never used: nothing to wait for
+
+
+def test_downloaded_result_equals_host_read(mpc):
+    import torch
+    ctx = mpc.Context(hashlib.sha256(b"d2h").digest())
+    n = 1 << 18
+    x = np.random.default_rng(6).integers(0, 2 ** 63, n, dtype=np.uint64)
+    xs = ctx.share_input(1, x)
+    dev = ctx.reconstruct(xs, n, to_host=False)      # Pi_Rec into device memory
+    host = torch.empty(n, dtype=torch.int64).pin_memory()
+    ctx.d2h_async(host, dev[:n], 2)                  # ordered after Pi_Rec on the context stream
+    torch.cuda.synchronize()
+    assert np.array_equal(host.numpy().view(np.uint64), ctx.reconstruct(xs, n))
+    assert np.array_equal(host.numpy().view(np.uint64), x)
