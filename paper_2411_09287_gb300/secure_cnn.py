@@ -145,12 +145,22 @@ def _concat(ctx, parts):
     return out
 
 
+# Comparisons per non-linear call: each call (a ReLU chunk, or whole channel planes of a max-pool)
+# is verified on its own; 2^16 comparisons take about 37 GB of workspace.
+NL_CHUNK = 1 << 16
+
+
+def pool_planes(nl_budget: int, H: int, W: int, planes: int) -> int:
+    """Channel planes per max-pool call: about nl_budget comparisons (3/4 of the elements)."""
+    return max(1, min(planes, (4 * nl_budget) // (3 * H * W)))
+
+
 def _pool_chunked(ctx, ids, h, shape, nl_budget):
     """2x2 max-pool of a (B, C, H, W) sharing in calls of whole channel planes, each call at most
     about nl_budget comparisons (3/4 of its elements), each verified on its own."""
     B, C, H, W = shape
     planes, per = B * C, H * W
-    step = max(1, min(planes, (4 * nl_budget) // (3 * per)))
+    step = pool_planes(nl_budget, H, W, planes)
     parts = []
     for p0 in range(0, planes, step):
         p1 = min(planes, p0 + step)
@@ -196,7 +206,7 @@ def share_params(ctx: "M.Context", params, k: int = 13, call_base: int = 4000):
 
 
 def net_a_secure(ctx: "M.Context", x, params, k: int = 13, call_base: int = 5000,
-                 nl_budget: int = 1 << 15, relu_chunk: int = 1 << 15, shared=None, segments=None):
+                 nl_budget: int = NL_CHUNK, relu_chunk: int = NL_CHUNK, shared=None, segments=None):
     """Secure Net A forward.  x: (B, 1, 28, 28) float inputs; params: the float parameters (shared
     by P0 here unless `shared` holds share_params' sharings); segments: as for
     secure_mlp.secure_forward (truncation bits keyed by request, layer and row).  Returns the
@@ -233,7 +243,7 @@ def share_params_b(ctx: "M.Context", params, k: int = 13, call_base: int = 4000)
 
 
 def net_b_secure(ctx: "M.Context", x, params, k: int = 13, call_base: int = 7000,
-                 nl_budget: int = 1 << 15, relu_chunk: int = 1 << 15, shared=None, segments=None):
+                 nl_budget: int = NL_CHUNK, relu_chunk: int = NL_CHUNK, shared=None, segments=None):
     """Secure Net B forward.  x: (B, 3, 32, 32) float inputs; params: the float parameters;
     shared / segments as for net_a_secure.  Returns the opened logits (B, 10) as float64."""
     ids = _Ids(call_base)

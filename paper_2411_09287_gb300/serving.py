@@ -95,10 +95,12 @@ class Model:
         elif self.kind == "neta":
             ws = [ctx.ws_size(M.OP_VERIFY_MATMUL, b * 576, 16, 25, self.k),
                   ctx.ws_size(M.OP_VERIFY_MATMUL, b * 64, 16, 400, self.k),
-                  ctx.ws_size(M.OP_MAXPOOL2, 32, 24, 24), ctx.ws_size(M.OP_RELU, 1 << 15)]
+                  ctx.ws_size(M.OP_MAXPOOL2, SC.pool_planes(SC.NL_CHUNK, 24, 24, b * 16), 24, 24),
+                  ctx.ws_size(M.OP_RELU, min(SC.NL_CHUNK, b * 16 * 12 * 12))]
         else:
             ws = [ctx.ws_size(M.OP_VERIFY_MATMUL, b * 1024, 64, 576, self.k),
-                  ctx.ws_size(M.OP_MAXPOOL2, 42, 32, 32), ctx.ws_size(M.OP_RELU, 1 << 15)]
+                  ctx.ws_size(M.OP_MAXPOOL2, SC.pool_planes(SC.NL_CHUNK, 32, 32, b * 64), 32, 32),
+                  ctx.ws_size(M.OP_RELU, min(SC.NL_CHUNK, b * 64 * 32 * 32))]
         return max(ws) / b
 
 
