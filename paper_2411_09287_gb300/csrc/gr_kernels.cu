@@ -358,19 +358,25 @@ struct LiftedIn {
   const u64* x[6];
   const u64* y[6];
 };
-__global__ void k_gram_lifted(LiftedIn in, long long Dh, long long D, u64* __restrict__ S) {
+// XM / YM: bit masks of the x and y components that are present (compile-time, so that absent
+// components cost neither loads nor registers); XM = YM = 0 reads the masks from the pointers.
+template <int XM, int YM>
+__global__ void __launch_bounds__(256)
+k_gram_lifted(LiftedIn in, long long Dh, long long D, u64* __restrict__ S) {
   const int c = threadIdx.x & 63;       // GR coefficient
   const int slot = threadIdx.x >> 6;    // pair slot of the block (4 per block)
+  auto hx = [&](int k) { return XM ? ((XM >> k) & 1) != 0 : in.x[k] != nullptr; };
+  auto hy = [&](int k) { return YM ? ((YM >> k) & 1) != 0 : in.y[k] != nullptr; };
   u64 acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};   // [party][ee, xo, oo]
   for (long long i = (long long)blockIdx.x * 4 + slot; i < Dh; i += (long long)gridDim.x * 4) {
     const long long e0 = 2 * i, e1 = 2 * i + 1;
     u64 xe[6], xo[6], ye[6], yo[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      xe[k] = in.x[k] ? in.x[k][e0 * 64 + c] : 0ull;
-      xo[k] = in.x[k] ? in.x[k][e1 * 64 + c] : 0ull;
-      ye[k] = in.y[k] ? in.y[k][e0] : 0ull;
-      yo[k] = (in.y[k] && e1 < D) ? in.y[k][e1] : 0ull;
+      xe[k] = hx(k) ? in.x[k][e0 * 64 + c] : 0ull;
+      xo[k] = hx(k) ? in.x[k][e1 * 64 + c] : 0ull;
+      ye[k] = hy(k) ? in.y[k][e0] : 0ull;
+      yo[k] = (hy(k) && e1 < D) ? in.y[k][e1] : 0ull;
     }
     const u64 ae = xe[0] + xe[1], ao = xo[0] + xo[1];
     const u64 ve = ye[0] + ye[1], vo = yo[0] + yo[1];
@@ -401,15 +407,21 @@ __global__ void k_gram_lifted(LiftedIn in, long long Dh, long long D, u64* __res
 }
 
 // The fold of a lifted y vector: out_i = lift(Y_{2i}) + f (Y_{2i+1} - Y_{2i}) for i < Dh (f: the
-// fold's GR element, 64 words; Y words past D read as 0), out rows of 64 words.
+// fold's GR element, 64 words; Y words past D read as 0), out rows of 64 words; 16 threads per
+// row, 4 coefficients each (16-byte stores).
 __global__ void k_fold_lifted(const u64* __restrict__ Y, long long Dh, long long D,
                               const u64* __restrict__ f, u64* __restrict__ out) {
-  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < Dh * 64;
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < Dh * 16;
        w += (long long)gridDim.x * blockDim.x) {
-    const long long i = w >> 6;
-    const int c = (int)(w & 63);
+    const long long i = w >> 4;
+    const int c = (int)(w & 15) * 4;
     const u64 y0 = Y[2 * i], y1 = 2 * i + 1 < D ? Y[2 * i + 1] : 0ull;
-    out[w] = (c == 0 ? y0 : 0ull) + f[c] * (y1 - y0);
+    const u64 d = y1 - y0;
+    const ulonglong2 f0 = *reinterpret_cast<const ulonglong2*>(f + c);
+    const ulonglong2 f1 = *reinterpret_cast<const ulonglong2*>(f + c + 2);
+    ulonglong2* o = reinterpret_cast<ulonglong2*>(out + i * 64 + c);
+    o[0] = make_ulonglong2((c == 0 ? y0 : 0ull) + f0.x * d, f0.y * d);
+    o[1] = make_ulonglong2(f1.x * d, f1.y * d);
   }
 }
 
@@ -887,13 +899,23 @@ void launch_gram_lifted(cudaStream_t st, const u64* const x[6], const u64* const
   }
   long long g = (Dh + 3) / 4;
   if (g > 152 * 8) g = 152 * 8;
-  k_gram_lifted<<<(unsigned)g, 256, 0, st>>>(in, Dh, D, S);
+  int xm = 0, ym = 0;
+  for (int k = 0; k < 6; ++k) {
+    xm |= x[k] ? 1 << k : 0;
+    ym |= y[k] ? 1 << k : 0;
+  }
+  // the component patterns of Pi_MultVerify (all), the edaBit inner products (x: the m
+  // components) and the edaBit bit products (x: [r]_1, y: [r]_2); any other takes the general form
+  if (xm == 63 && ym == 63) k_gram_lifted<63, 63><<<(unsigned)g, 256, 0, st>>>(in, Dh, D, S);
+  else if (xm == 0x14 && ym == 63) k_gram_lifted<0x14, 63><<<(unsigned)g, 256, 0, st>>>(in, Dh, D, S);
+  else if (xm == 0x09 && ym == 0x22) k_gram_lifted<0x09, 0x22><<<(unsigned)g, 256, 0, st>>>(in, Dh, D, S);
+  else k_gram_lifted<0, 0><<<(unsigned)g, 256, 0, st>>>(in, Dh, D, S);
 }
 
 void launch_fold_lifted(cudaStream_t st, const u64* Y, long long Dh, long long D, const u64* f,
                         u64* out) {
   if (Dh <= 0) return;
-  k_fold_lifted<<<grid_for(Dh * 64), TPB, 0, st>>>(Y, Dh, D, f, out);
+  k_fold_lifted<<<grid_for(Dh * 16), TPB, 0, st>>>(Y, Dh, D, f, out);
 }
 
 void launch_fill(cudaStream_t st, u64* p, long long n, u64 v) {
