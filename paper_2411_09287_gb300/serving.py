@@ -244,6 +244,23 @@ class Server:
             raise RuntimeError(f"a packed secure pass failed: {self.errors[0]!r}") from self.errors[0]
         return reqs
 
+    def close(self):
+        """Release the workers' contexts and their workspaces (after serve)."""
+        for w in self.workers:
+            ctx = getattr(w, "ctx", None)
+            if ctx is None:
+                continue
+            if hasattr(ctx, "_ws"):
+                ctx._ws = None
+            if hasattr(ctx, "close"):
+                ctx.close()
+        try:
+            import torch
+            if torch.cuda.is_available():
+                torch.cuda.empty_cache()
+        except ImportError:
+            pass
+
     @staticmethod
     def stats(reqs):
         lat = np.array([r.done - r.arrival for r in reqs])
@@ -280,7 +297,10 @@ def main():
     for rate in a.rate:
         reqs = poisson_requests(model, a.requests, rate, a.max_b, f"C5-{a.model}-{rate}")
         srv = Server(model, a.workers, a.max_batch)
-        out = srv.serve(reqs)
+        try:
+            out = srv.serve(reqs)
+        finally:
+            srv.close()   # each rate's workers hold workspaces sized for the largest call
         st = Server.stats(out)
         err = max(float(np.max(np.abs(r.logits - model.fp64(r.x)))) for r in out)
         st.update({"model": a.model, "rate": rate, "max_abs_err_vs_fp64": err})
