@@ -987,9 +987,7 @@ void launch_scalar_gr_sum(cudaStream_t st, long long n, const u64* A, long long 
   if (n <= 0 || nrows <= 0) return;
   long long g = (n + 4095) / 4096;
   if (g > 152 * 8) g = 152 * 8;
-  if (nrows <= 6)   // the six share components of one vector
-    k_scalar_gr_sum<6><<<(unsigned)g, 256, 0, st>>>(n, A, lda, nrows, R, out);
-  else if (nrows <= 12)
+  if (nrows <= 12)
     k_scalar_gr_sum<12><<<(unsigned)g, 256, 0, st>>>(n, A, lda, nrows, R, out);
   else
     k_scalar_gr_sum<16><<<(unsigned)g, 256, 0, st>>>(n, A, lda, nrows, R, out);
