@@ -250,10 +250,10 @@ def run_reference(args, rank: int, world: int):
 # the figure by E / 2^20.  The summaries, with the commands that produced them: profiles/.
 NCU_TRAFFIC_E = 2 ** 20
 NCU_TRAFFIC = {   # bytes per step at E = 2^20 (profiles/traffic_gr_kernels_n1024.md)
-    "k_trunc_s": 0.3948e9,
-    "k_limb_gemm": 0.7627e9,
-    "k_gr_matmul": 10.09e9,
-    "k_gram": 2.166e9,
+    "k_trunc_s": 0.3965e9,
+    "k_limb_gemm": 0.7628e9,
+    "k_gr_matmul": 10.066e9,
+    "k_gram": 2.165e9,
     "k_gr_mul_rows": None,   # not launched at these sizes (the tensor-core form replaces it)
 }
 ALU_NOTE = "peak derived: 152 SMs x 64 IMAD/clk x max SM clock; a u64 MAC is 3 IMAD"
