@@ -543,6 +543,21 @@ void trace_round(mpc_ctx* ctx, u64* trace, int k, const Small& s) {
   cudaMemcpyAsync(t + 448, s.h2, 384 * 8, cudaMemcpyDeviceToDevice, ctx->st);
 }
 
+// The part of a Pi_Reduce round after its party sums (in s.S: S00, S01 + S10 (with S10), S11):
+// h(0) and h(p2) by secure GR inner products, zeta revealed, the Lagrange weights, the next claim
+// zo, and M_zeta (s.MM) for the folds; the fold element is s.coef[0..63].
+void round_tail(mpc_ctx* ctx, u64 vid, u32 batch, int k, const u64* z, u64* zo, const Small& s) {
+  cudaStream_t st = ctx->st;
+  launch_gr_quad_combine(st, ctx->cst + CST_LAM, s.S, s.S + 192, s.S + 384, s.S + 576, s.S + 768);
+  const u64 obj = make_obj(vid, batch, (u32)k);
+  inner_finish(ctx, s.S, P_VER_H0, obj, s.h0);
+  inner_finish(ctx, s.S + 768, P_VER_H2, obj, s.h2);
+  reveal(ctx, P_VER_ZETA, obj, s.tmp6, s.zp);
+  launch_gr_lagrange(st, s.zp, ctx->reduce_mode, ctx->cst + CST_INV, s.coef);
+  launch_gr_combine_z(st, s.coef, s.h0, s.h2, z, zo);
+  launch_gr_mulmat2(st, s.coef, nullptr, s.MM);   // M_zeta
+}
+
 // One Pi_Reduce round on a dense claim (Fig. Reduce).  x, y: current vectors (D elements, with
 // capacity for D+1), z: current claim; writes the folded vectors into xo, yo and z into zo.
 // ys (optional): the y vectors are lifted ring words, one word per element (Fig. MTP's y side
@@ -572,7 +587,6 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
   u64* S01 = s.S + 192;
   u64* S10 = s.S + 384;
   u64* S11 = s.S + 576;
-  u64* Sh2 = s.S + 768;
   int rc;
   // Shape of the truncation batch's dense rounds: x holds only [r]_1 (P0, P1 copies), y only
   // [r]_2 (P0, P2 copies), so P1's and P2's cross terms vanish and P0's sums are single Grams.
@@ -658,14 +672,7 @@ int reduce_round_dense(mpc_ctx* ctx, u64 vid, u32 batch, int k, const Vec& x, co
       if ((rc = party_sums(ctx, f[1], g[1], Dh, s.Pmat + 9 * 4096, S11))) return rc;
     }
   }
-  launch_gr_quad_combine(st, ctx->cst + CST_LAM, S00, S01, S10, S11, Sh2);
-  const u64 obj = make_obj(vid, batch, (u32)k);
-  inner_finish(ctx, S00, P_VER_H0, obj, s.h0);
-  inner_finish(ctx, Sh2, P_VER_H2, obj, s.h2);
-  reveal(ctx, P_VER_ZETA, obj, s.tmp6, s.zp);
-  launch_gr_lagrange(st, s.zp, ctx->reduce_mode, ctx->cst + CST_INV, s.coef);
-  launch_gr_combine_z(st, s.coef, s.h0, s.h2, z, zo);
-  launch_gr_mulmat2(st, s.coef, nullptr, s.MM);   // M_zeta
+  round_tail(ctx, vid, batch, k, z, zo, s);
   // f(zeta) = f(0) + zeta (f(1) - f(0)): rows [x_{2i+1} - x_{2i}] times M_zeta, plus x_{2i}.
   // Vectors that sit at one stride (the dense plans put a slot's x vectors, then its y vectors,
   // one after another) go through one launch: segment s of Dh rows (padded to whole tiles); all
@@ -851,15 +858,19 @@ long long dim_after(long long D, int R) {
 // Allocate ping-pong vectors for a dense claim of dimension D over the present components.  With
 // ylifted_R >= 1 the y side enters in ring words (run_dense's ylift) and the first round writes
 // slot 1, so slot 0 of y only ever holds the outputs of round 2 and later (at most cap[1] rows).
-Dense plan_dense(Arena& a, long long D, const bool xc[6], const bool yc[6], int ylifted_R = 0) {
+// With x_from_bits the first round writes x's slot 1 without reading slot 0 (the edaBit
+// inner-product batch), so x's slot 0 is half size as well.
+Dense plan_dense(Arena& a, long long D, const bool xc[6], const bool yc[6], int ylifted_R = 0,
+                 bool x_from_bits = false) {
   Dense d;
   d.cap[0] = D + 1;
   d.cap[1] = (D + 1) / 2 + 1;
   const long long ycap0 = ylifted_R >= 1 ? d.cap[1] : d.cap[0];
+  const long long xcap0 = x_from_bits && ylifted_R >= 1 ? d.cap[1] : d.cap[0];
   // a slot's x vectors, then its y vectors: each side's present vectors sit at one stride (the
   // batched folds use that)
   for (int i = 0; i < 2; ++i) {
-    for (int c = 0; c < 6; ++c) d.x[i].c[c] = xc[c] ? a.take<u64>(d.cap[i] * 64) : nullptr;
+    for (int c = 0; c < 6; ++c) d.x[i].c[c] = xc[c] ? a.take<u64>((i ? d.cap[1] : xcap0) * 64) : nullptr;
     for (int c = 0; c < 6; ++c)
       d.y[i].c[c] = yc[c] ? a.take<u64>((i ? d.cap[1] : ycap0) * 64) : nullptr;
   }
@@ -2108,7 +2119,7 @@ int mpc_verify_matmul_keyed(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs
   if (!workspace || !ar.ok()) return fail(ctx, MPC_ERR_WORKSPACE, "verify_matmul: workspace too small");
   cudaStream_t st = ctx->st;
   const Small& s = p.s;
-  const long long MK = M * K, KN = K * N, E = M * N;
+  const long long MK = M * K, KN = K * N;
   // ---- batch 0: the M N inner products of Z = X W, rank-1 consolidation ----
   Phase* phase = new Phase(ctx, MPC_PROF_VERIFY_GEMM);
   reveal(ctx, P_VER_R, make_obj(verify_id, 0, 0), s.tmp6, s.r);
@@ -2838,6 +2849,8 @@ struct NLPlan {
   Dense d1;
   IVBuf iv1;
   u64* Ye;                       // 6 x D1 ring words: the y side before its first fold
+  u64* S6;                       // 6 x ne: the first round's per-element party-sum words
+  u64* A1;                       // ne x 64: r^g f, the first round's x fold
   u64** ydev;                    // 6 device pointers (kernel argument)
   // batch 2: AND gates
   GfPlan gf;
@@ -2875,9 +2888,11 @@ NLPlan plan_nl(Arena& a, int nst, const long long np[2]) {
   p.pw1 = a.take<u64>(p.ne * 64);
   const bool xc[6] = {false, false, true, false, true, false};
   const bool yc[6] = {true, true, true, true, true, true};
-  p.d1 = plan_dense(a, p.D1, xc, yc, p.R1);
+  p.d1 = plan_dense(a, p.D1, xc, yc, p.R1, true);
   p.iv1 = plan_iv(a, dim_after(p.D1, p.R1));
   p.Ye = a.take<u64>(6 * p.D1);
+  p.S6 = a.take<u64>(6 * p.ne);
+  p.A1 = a.take<u64>(p.ne * 64);
   p.ydev = a.take<u64*>(6);
   p.gf = plan_gf(a, andw, -1);
   p.nb = 64 * p.ne;
@@ -2941,22 +2956,49 @@ int verify_nl(mpc_ctx* ctx, u64 vid, NLPlan& p, u64* trace) {
     const Small& s = p.s1;
     reveal(ctx, P_VER_R, make_obj(vid, 1, 0), s.tmp6, s.r);
     launch_gr_powers(st, s.r, p.ne, p.pw1);
-    Vec& x = p.d1.x[0];
     Vec ylift;
     for (int c = 0; c < 6; ++c) ylift.c[c] = p.Ye + c * p.D1;
     CK(cudaMemcpyAsync(p.ydev, ylift.c, 6 * sizeof(u64*), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(s.zinit, 0, 384 * 8, st));
     long long e0 = 0;
-    for (int q = 0; q < p.nst; ++q) {
+    for (int q = 0; q < p.nst; ++q) {   // the y words and the claim (x is never materialised)
       CSPlan& c = p.cs[q];
-      launch_eda_tran(st, c.mbw, c.rp, c.np, p.pw1, e0, x.c[2], x.c[4], p.ydev);
+      launch_eda_tran(st, c.mbw, c.rp, c.np, p.pw1, e0, nullptr, nullptr, p.ydev);
       launch_scalar_gr_sum(st, c.np, c.ez, c.np, 6, p.pw1 + e0 * 64, s.zinit);
       g_launches += 1;
       e0 += c.np;
     }
-    p.d1.cur = 0;
-    if ((rc = run_dense(ctx, vid, 1, p.d1, p.D1, s.zinit, 1, p.R1, s, p.iv1, tr1, &ylift)))
-      return rc;
+    // Round 1 from the bits: x = r^g <m_i> pairs the bits 2k, 2k + 1 of one element, so the
+    // party sums are sum_g r^g s(g) over per-element words (rows P1, P2 of each block; P0's are
+    // zero) and the folded x is a selection among 0, r^g - r^g f, r^g f and r^g.
+    CK(cudaMemsetAsync(s.S, 0, 4 * 192 * 8, st));
+    e0 = 0;
+    for (int q = 0; q < p.nst; ++q) {
+      CSPlan& c = p.cs[q];
+      launch_eda_r1_sums(st, c.mbw, c.rp, c.np, e0, p.ne, p.S6);
+      g_launches += 1;
+      e0 += c.np;
+    }
+    launch_scalar_gr_sum(st, p.ne, p.S6, p.ne, 2, p.pw1, s.S + 64);                   // S00
+    launch_scalar_gr_sum(st, p.ne, p.S6 + 2 * p.ne, p.ne, 2, p.pw1, s.S + 192 + 64);  // S01 + S10
+    launch_scalar_gr_sum(st, p.ne, p.S6 + 4 * p.ne, p.ne, 2, p.pw1, s.S + 576 + 64);  // S11
+    round_tail(ctx, vid, 1, 1, s.zinit, s.z[1], s);
+    Vec& xo = p.d1.x[1];
+    Vec& yo = p.d1.y[1];
+    if ((rc = gr_matmul(ctx, p.ne, p.pw1, nullptr, 1, 64, s.MM, nullptr, 0, p.A1, 64))) return rc;
+    e0 = 0;
+    for (int q = 0; q < p.nst; ++q) {
+      CSPlan& c = p.cs[q];
+      launch_eda_x_fold(st, c.mbw, c.np, e0, p.pw1, p.A1, xo.c[2], xo.c[4]);
+      g_launches += 1;
+      e0 += c.np;
+    }
+    const long long Dh = p.D1 / 2;
+    for (int c = 0; c < 6; ++c) launch_fold_lifted(st, ylift.c[c], Dh, p.D1, s.coef, yo.c[c]);
+    trace_round(ctx, tr1, 1, s);
+    if ((rc = cuda_check(ctx, "edaBit first round"))) return rc;
+    p.d1.cur = 1;
+    if ((rc = run_dense(ctx, vid, 1, p.d1, Dh, s.z[1], 2, p.R1, s, p.iv1, tr1))) return rc;
   }
   u64* tr2 = tr1 ? tr1 + (long long)(p.R1 + 1) * TRACE_ROUND : nullptr;
   // ---- batch 2: every AND gate over GF(2^64), stage by stage, level by level

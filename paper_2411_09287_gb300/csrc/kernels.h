@@ -283,6 +283,12 @@ void launch_b2a_apply(cudaStream_t st, const u64* dbits, const u64* ra, long lon
 void launch_addsub(cudaStream_t st, long long n, const u64* a, const u64* b, int sub, u64* out);
 void launch_open_xor(cudaStream_t st, const u64* m, const u64* r1, const u64* r2_in, long long n,
                      u64* out);
+// First round of the edaBit inner-product batch from the bits (see nonlinear.cu): per-element
+// party-sum words (6 rows of ld words) and the x fold (A: r^g f per element g).
+void launch_eda_r1_sums(cudaStream_t st, const u64* mbits, const u64* rp, long long np, long long e0,
+                        long long ld, u64* out);
+void launch_eda_x_fold(cudaStream_t st, const u64* mbits, long long np, long long e0, const u64* pw,
+                       const u64* A, u64* x2, u64* x4);
 void launch_eda_tran(cudaStream_t st, const u64* mbits, const u64* rp, long long np, const u64* pw,
                      long long e0, u64* x2, u64* x4, u64* const* y_dev);
 void launch_gf_powers(cudaStream_t st, const u64* r, long long n, u64* out);

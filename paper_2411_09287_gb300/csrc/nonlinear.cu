@@ -519,11 +519,69 @@ __global__ void k_eda_tran(const u64* __restrict__ mbits, const u64* __restrict_
     const int i = (int)(q & 63);
     const long long j = (long long)i * np + e;
     const long long row = (e0 + e) * 64 + i;
-    const u64 m = (mbits[j >> 6] >> (j & 63)) & 1ull;
-    const u64 xv = m ? pw[(e0 + e) * 64 + k] : 0ull;
-    x2[row * 64 + k] = xv;
-    x4[row * 64 + k] = xv;
+    if (x2) {   // the x vectors (absent when the first round takes them from the bits)
+      const u64 m = (mbits[j >> 6] >> (j & 63)) & 1ull;
+      const u64 xv = m ? pw[(e0 + e) * 64 + k] : 0ull;
+      x2[row * 64 + k] = xv;
+      x4[row * 64 + k] = xv;
+    }
     if (k < 6) y[k][row] = shl_mod(rp[k * N + j], i + 1);   // component k of the ring word
+  }
+}
+
+// First Pi_Reduce round of the edaBit inner-product batch without its x vectors: x = r^g <m_i>
+// (g = e0 + e the element, i the bit, components 2 and 4, no mask) pairs bits 2k and 2k + 1 of one
+// element, so the round's party sums are sum_g r^g s(g) with per-element words s(g) (P0 has none:
+// x has no mask), here written to out (6 rows of ld words, element g at column g):
+//   rows 0, 1: the even pairs' sums of P1 (-m Y3) and P2 (m (Y4 - Y5)); rows 2, 3: the cross
+//   terms; rows 4, 5: the odd pairs'; Y_c = 2^(i+1) <r'_i>_c (the batch's y words).
+__global__ void k_eda_r1_sums(const u64* __restrict__ mbits, const u64* __restrict__ rp, long long np,
+                              long long e0, long long ld, u64* __restrict__ out) {
+  const long long N = 64 * np;
+  GRID_STRIDE(e, np) {
+    u64 p1[3] = {0, 0, 0}, p2[3] = {0, 0, 0};   // [ee, cross, oo]
+#pragma unroll 4
+    for (int k = 0; k < 32; ++k) {
+      const long long ja = (long long)(2 * k) * np + e, jb = ja + np;
+      const u64 ma = (mbits[ja >> 6] >> (ja & 63)) & 1ull, mb = (mbits[jb >> 6] >> (jb & 63)) & 1ull;
+      const u64 y3a = shl_mod(rp[3 * N + ja], 2 * k + 1), y3b = shl_mod(rp[3 * N + jb], 2 * k + 2);
+      const u64 wa = shl_mod(rp[4 * N + ja], 2 * k + 1) - shl_mod(rp[5 * N + ja], 2 * k + 1);
+      const u64 wb = shl_mod(rp[4 * N + jb], 2 * k + 2) - shl_mod(rp[5 * N + jb], 2 * k + 2);
+      p1[0] += ma * y3a;
+      p1[1] += ma * y3b + mb * y3a;
+      p1[2] += mb * y3b;
+      p2[0] += ma * wa;
+      p2[1] += ma * wb + mb * wa;
+      p2[2] += mb * wb;
+    }
+    const long long g = e0 + e;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      out[(2 * b) * ld + g] = 0ull - p1[b];
+      out[(2 * b + 1) * ld + g] = p2[b];
+    }
+  }
+}
+
+// The round's x fold without the x vectors: row g 32 + k of the folded vector is
+// r^g (m_2k + f (m_2k+1 - m_2k)) = 0, r^g - A_g, A_g or r^g (A_g = r^g f, f the fold element),
+// for components 2 and 4.
+__global__ void k_eda_x_fold(const u64* __restrict__ mbits, long long np, long long e0,
+                             const u64* __restrict__ pw, const u64* __restrict__ A,
+                             u64* __restrict__ x2, u64* __restrict__ x4) {
+  GRID_STRIDE(t, np * 32 * 64) {
+    const int c = (int)(t & 63);
+    const long long q = t >> 6;              // local folded row: e * 32 + k
+    const long long e = q >> 5;
+    const int k = (int)(q & 31);
+    const long long ja = (long long)(2 * k) * np + e, jb = ja + np;
+    const u64 ma = (mbits[ja >> 6] >> (ja & 63)) & 1ull, mb = (mbits[jb >> 6] >> (jb & 63)) & 1ull;
+    const long long g = e0 + e;
+    const u64 pv = pw[g * 64 + c], av = A[g * 64 + c];
+    const u64 v = ma ? (mb ? pv : pv - av) : (mb ? av : 0ull);
+    const long long row = g * 32 + k;
+    x2[row * 64 + c] = v;
+    x4[row * 64 + c] = v;
   }
 }
 
@@ -694,6 +752,15 @@ void launch_open_xor(cudaStream_t st, const u64* m, const u64* r1, const u64* r2
 void launch_eda_tran(cudaStream_t st, const u64* mbits, const u64* rp, long long np, const u64* pw,
                      long long e0, u64* x2, u64* x4, u64* const* y_dev) {
   k_eda_tran<<<grid_for(64 * np * 64), TPB, 0, st>>>(mbits, rp, np, pw, e0, x2, x4, y_dev);
+}
+
+void launch_eda_r1_sums(cudaStream_t st, const u64* mbits, const u64* rp, long long np, long long e0,
+                        long long ld, u64* out) {
+  k_eda_r1_sums<<<grid_for(np), TPB, 0, st>>>(mbits, rp, np, e0, ld, out);
+}
+void launch_eda_x_fold(cudaStream_t st, const u64* mbits, long long np, long long e0, const u64* pw,
+                       const u64* A, u64* x2, u64* x4) {
+  k_eda_x_fold<<<grid_for(np * 32 * 64), TPB, 0, st>>>(mbits, np, e0, pw, A, x2, x4);
 }
 
 void launch_window_gather(cudaStream_t st, const u64* x, long long BC, long long H, long long W,
