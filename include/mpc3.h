@@ -146,7 +146,9 @@ const char* mpc_last_error(const mpc_ctx* ctx);
  * A pipelined caller uploads the next step's inputs and downloads the last step's result while
  * the current step runs:
  *   mpc_h2d_async copies `bytes` from host `src` (pinned memory, for the copy to overlap) to
- *     device `dst` on the context's copy stream (created on first use);
+ *     device `dst` on the context's copy stream (created on first use), after the work enqueued
+ *     so far on the context's stream (which may still read `dst`); it overlaps the work enqueued
+ *     after it, so step k + 1's upload is issued before step k is enqueued;
  *   mpc_d2h_async copies `bytes` from device `src` to host `dst` (pinned) on the copy stream,
  *     after the work enqueued so far on the context's stream (which writes `src`);
  * each records the copy under `slot` (0 .. MPC_H2D_SLOTS - 1).  mpc_h2d_wait makes the context's

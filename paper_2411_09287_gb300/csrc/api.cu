@@ -1607,6 +1607,9 @@ int mpc_h2d_async(mpc_ctx* ctx, void* dst, const void* src, size_t bytes, int sl
     return fail(ctx, MPC_ERR_ARG, "h2d_async: bad argument");
   if (!ctx->copy_st) CK(cudaStreamCreateWithFlags(&ctx->copy_st, cudaStreamNonBlocking));
   if (!ctx->copy_ev[slot]) CK(cudaEventCreateWithFlags(&ctx->copy_ev[slot], cudaEventDisableTiming));
+  if (!ctx->order_ev) CK(cudaEventCreateWithFlags(&ctx->order_ev, cudaEventDisableTiming));
+  CK(cudaEventRecord(ctx->order_ev, ctx->st));   // after the work that may still read dst
+  CK(cudaStreamWaitEvent(ctx->copy_st, ctx->order_ev, 0));
   CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->copy_st));
   CK(cudaEventRecord(ctx->copy_ev[slot], ctx->copy_st));
   return MPC_OK;

@@ -122,7 +122,7 @@ class Context:
 
     def h2d_async(self, dst, src, slot: int = 0):
         """mpc_h2d_async: copy the host tensor `src` (pinned, for overlap) into the device tensor
-        `dst` on the context's copy stream, recorded under `slot`."""
+        `dst` on the copy stream, after the work enqueued so far; recorded under `slot`."""
         nbytes = src.numel() * src.element_size()
         assert dst.numel() * dst.element_size() >= nbytes
         self._check(self.lib.mpc_h2d_async(self.h, C.c_void_p(_ptr(dst)), C.c_void_p(_ptr(src)),

@@ -1,7 +1,8 @@
 """Asynchronous copies (mpc_h2d_async / mpc_d2h_async / mpc_h2d_wait): a sharing of inputs
 uploaded on the copy stream equals the sharing of the same inputs passed as host memory, word for
 word, with the uploads of the next step in flight while the current one runs; an opened result
-downloaded on the copy stream equals the one read back by Pi_Rec; bad arguments are refused."""
+downloaded on the copy stream equals the one read back by Pi_Rec; an upload waits for the work
+enqueued before it that reads its buffer; bad arguments are refused."""
 import hashlib
 
 import numpy as np
@@ -67,3 +68,29 @@ def test_downloaded_result_equals_host_read(mpc):
     torch.cuda.synchronize()
     assert np.array_equal(host.numpy().view(np.uint64), ctx.reconstruct(xs, n))
     assert np.array_equal(host.numpy().view(np.uint64), x)
+
+
+def test_upload_waits_for_earlier_readers(mpc):
+    # a buffer still read by work on the context stream is overwritten only after that work:
+    # the sharing enqueued before the upload sees the old words, the one after sees the new
+    import torch
+    seed = hashlib.sha256(b"h2d-war").digest()
+    n = 1 << 24
+    g = np.random.default_rng(7)
+    old, new = (g.integers(0, 2 ** 63, n, dtype=np.uint64) for _ in range(2))
+    ref = mpc.Context(seed)
+    want_old = mpc.to_u64(ref.share_input(20, old))
+    want_new = mpc.to_u64(ref.share_input(21, new))
+    del ref
+    ctx = mpc.Context(seed)
+    dev = ctx.empty(n)
+    dev.copy_(torch.from_numpy(old.view(np.int64)))
+    torch.cuda.synchronize()
+    s_old = ctx.share_input(20, dev[:n])              # reads dev on the context stream
+    hnew = torch.from_numpy(new.view(np.int64)).pin_memory()
+    ctx.h2d_async(dev, hnew, 1)
+    ctx.h2d_wait(1)
+    s_new = ctx.share_input(21, dev[:n])
+    torch.cuda.synchronize()
+    assert np.array_equal(mpc.to_u64(s_old), want_old)
+    assert np.array_equal(mpc.to_u64(s_new), want_new)
