@@ -31,6 +31,7 @@ inline void counted(int k, F f, A... a) {
 }
 }  // namespace
 #define gemm_u64(...) counted(1, mpc3::gemm_u64, __VA_ARGS__)
+#define gemm_u64_small(...) counted(1, mpc3::gemm_u64_small, __VA_ARGS__)
 #define launch_share_input(...) counted(1, mpc3::launch_share_input, __VA_ARGS__)
 #define launch_fill_masks(...) counted(1, mpc3::launch_fill_masks, __VA_ARGS__)
 #define launch_mult_offline(...) counted(1, mpc3::launch_mult_offline, __VA_ARGS__)
@@ -765,7 +766,7 @@ int inner_verify_dense(mpc_ctx* ctx, u64 vid, u32 batch, const Vec& x, const Vec
     e.key = ctx->k01;
     e.tag = make_tag(P_VER_XA, C_G1);
     e.obj = obj;
-    gemm_u64(st, D, 64, 64, 1, &T, e, 1);
+    gemm_u64_small(st, D, 64, 64, 1, &T, e);
   }
   int rc;
   if ((rc = deliver(ctx, MPC_PHASE_VERIFY, MPC_PROTO_VERIFY, b.g2o, b.g2i, D * 64, -1))) return rc;
@@ -781,7 +782,7 @@ int inner_verify_dense(mpc_ctx* ctx, u64 vid, u32 batch, const Vec& x, const Vec
     e.key = ctx->k01;
     e.tag = make_tag(P_VER_XA, C_G1);
     e.obj = obj;
-    gemm_u64(st, D, 64, 64, 2, T, e, 1);
+    gemm_u64_small(st, D, 64, 64, 2, T, e);
   }
   {  // P2: [m]_2 = m_x (m_a - [r_a]_2) - [r_x]_2 m_a + [Gamma]_2
     GemmTerm T[2];
@@ -791,7 +792,7 @@ int inner_verify_dense(mpc_ctx* ctx, u64 vid, u32 batch, const Vec& x, const Vec
     T[1].B = op(s.MA + 16384, 64);
     Epi e = epi_store(b.p2o, 64);
     e.add0 = b.g2i;
-    gemm_u64(st, D, 64, 64, 2, T, e, 1);
+    gemm_u64_small(st, D, 64, 64, 2, T, e);
   }
   if ((rc = deliver(ctx, MPC_PHASE_VERIFY, MPC_PROTO_VERIFY, b.p1o, b.p2i, D * 64, -1))) return rc;
   if ((rc = deliver(ctx, MPC_PHASE_VERIFY, MPC_PROTO_VERIFY, b.p2o, b.p1i, D * 64, -1))) return rc;

@@ -232,4 +232,14 @@ void gemm_u64(cudaStream_t st, long long M, long long N, long long K, int nterms
   }
 }
 
+void gemm_u64_small(cudaStream_t st, long long M, long long N, long long K, int nterms,
+                    const GemmTerm* terms, const Epi& epi) {
+  if (M <= 0 || N <= 0) return;
+  constexpr int BM = 16, BN = 16, BK = 16, TM = 1, TN = 1;
+  GemmTerm t1 = (nterms > 1) ? terms[1] : terms[0];
+  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), 1);
+  gemm_u64_kernel<BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, st>>>(
+      M, N, K, nterms, terms[0], t1, epi, K);
+}
+
 }  // namespace mpc3

@@ -49,6 +49,10 @@ void gemm_u64_gram_batch(cudaStream_t st, long long K, int n, const GemmTerm* te
 // K across grid.z and requires epi.atomic = 1.
 void gemm_u64(cudaStream_t st, long long M, long long N, long long K, int nterms,
               const GemmTerm* terms, const Epi& epi, int nsplit);
+// The same product in 16 x 16 output tiles, one output per thread and no split: for small
+// products (a few thousand outputs, short K) that one 64 x 64 tile would leave on one SM.
+void gemm_u64_small(cudaStream_t st, long long M, long long N, long long K, int nterms,
+                    const GemmTerm* terms, const Epi& epi);
 
 // ---- exact u64 GEMM on the tcgen05 tensor cores (limb_gemm_tc.cu) ---------------------------
 // Same contract as gemm_u64 without split-K (epi.atomic must be 0; returns -1 otherwise, -2 if
