@@ -2784,11 +2784,8 @@ int gf_verify(mpc_ctx* ctx, u64 vid, GfPlan& g, u64* trace) {
       yo = g.y[0];
     }
     const long long ocap2 = cur == 1 ? g.D + 1 : ocap;
-    for (int c = 0; c < 6; ++c) {
-      launch_gf_fold(st, xv + c * cap, D, coef, xo + c * ocap2);
-      launch_gf_fold(st, yv + c * cap, D, coef, yo + c * ocap2);
-    }
-    g_launches += 12;
+    launch_gf_fold6x2(st, xv, yv, cap, D, coef, xo, yo, ocap2);
+    g_launches += 1;
     if (trace) {
       u64* t = trace + (long long)(k - 1) * MPC_TRACE_GF_ROUND;
       CK(cudaMemcpyAsync(t, zp, 8, cudaMemcpyDeviceToDevice, st));

@@ -300,7 +300,9 @@ void launch_gf_tran(cudaStream_t st, const u64* X, const u64* Y, const u64* Z, l
                     const u64* pw, long long ld, u64* xo, u64* yo, u64* zsum);
 void launch_gf_party_sums(cudaStream_t st, const u64* const u[6], const u64* const v[6], long long D,
                           long long stride, long long off, int fold, u64 fa, u64 fb, u64* S);
-void launch_gf_fold(cudaStream_t st, const u64* v, long long D, const u64* zeta, u64* out);
+// The GF fold of the six components of x and of y (component c at c * cap in, c * ocap out).
+void launch_gf_fold6x2(cudaStream_t st, const u64* xv, const u64* yv, long long cap, long long D,
+                       const u64* zeta, u64* xo, u64* yo, long long ocap);
 void launch_gf_inner_finish(cudaStream_t st, const u64* S, Key k01, Key k02, u32 purpose, u64 obj,
                             u64* h6);
 void launch_gf_random_shared(cudaStream_t st, Key k01, Key k02, Key k12, u32 purpose, u64 obj,

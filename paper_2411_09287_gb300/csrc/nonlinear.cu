@@ -330,10 +330,16 @@ struct GfVec {
   const u64* c[6];
 };
 __device__ __forceinline__ u64 gv(const GfVec& v, int c, long long i) { return v.c[c] ? v.c[c][i] : 0ull; }
+// a x in GF(2^64): a shift, and x^4 + x^3 + x + 1 for the x^64 that it carries out
+__device__ __forceinline__ u64 gf_mulx(u64 a) { return (a << 1) ^ ((0ull - (a >> 63)) & 0x1Bull); }
+// fold = 1: fa a_{2i} + fb a_{2i+1}; fold = 2: the same at fa = 1 + x, fb = x, which is
+// a_{2i} + x (a_{2i} + a_{2i+1})
 __device__ __forceinline__ u64 gvf(const GfVec& v, int c, long long i, int fold, u64 fa, u64 fb) {
   if (!v.c[c]) return 0ull;
   if (!fold) return v.c[c][i];
-  return gf_mul(fa, v.c[c][2 * i]) ^ gf_mul(fb, v.c[c][2 * i + 1]);
+  const u64 a = v.c[c][2 * i], b = v.c[c][2 * i + 1];
+  if (fold == 2) return a ^ gf_mulx(a ^ b);
+  return gf_mul(fa, a) ^ gf_mul(fb, b);
 }
 
 __global__ void k_gf_party_sums(GfVec u, GfVec v, long long D, long long stride, long long off,
@@ -364,9 +370,15 @@ __global__ void k_gf_party_sums(GfVec u, GfVec v, long long D, long long stride,
 }
 
 // out_i = (1 + zeta) v_{2i} + zeta v_{2i+1} (the fold f(zeta) = (1 - zeta) f(0) + zeta f(1)),
-// i < Dh; v has D elements (v_D = 0 when D is odd)
-__global__ void k_gf_fold(const u64* __restrict__ v, long long D, const u64* __restrict__ zp,
-                          u64* __restrict__ out) {
+// i < Dh; v has D elements (v_D = 0 when D is odd).  grid.y = 12 folds the six components of
+// two vectors: q = blockIdx.y takes component q / 2 of x (q even) or y (q odd), component c at
+// c * cap of the input and c * ocap of the output.
+__global__ void k_gf_fold(const u64* __restrict__ xv, const u64* __restrict__ yv, long long cap,
+                          long long D, const u64* __restrict__ zp, u64* __restrict__ xo,
+                          u64* __restrict__ yo, long long ocap) {
+  const int q = blockIdx.y;
+  const u64* __restrict__ v = ((q & 1) ? yv : xv) + (q >> 1) * cap;
+  u64* __restrict__ out = ((q & 1) ? yo : xo) + (q >> 1) * ocap;
   const u64 z = *zp, z1 = z ^ 1ull;
   const long long Dh = (D + 1) / 2;
   GRID_STRIDE(i, Dh) {
@@ -698,10 +710,13 @@ void launch_gf_party_sums(cudaStream_t st, const u64* const u[6], const u64* con
     U.c[c] = u[c];
     V.c[c] = v[c];
   }
+  if (fold && fa == 3ull && fb == 2ull) fold = 2;   // the third point x: no general products
   k_gf_party_sums<<<grid_for(D), TPB, 0, st>>>(U, V, D, stride, off, fold, fa, fb, S);
 }
-void launch_gf_fold(cudaStream_t st, const u64* v, long long D, const u64* zeta, u64* out) {
-  k_gf_fold<<<grid_for((D + 1) / 2), TPB, 0, st>>>(v, D, zeta, out);
+void launch_gf_fold6x2(cudaStream_t st, const u64* xv, const u64* yv, long long cap, long long D,
+                       const u64* zeta, u64* xo, u64* yo, long long ocap) {
+  if (D <= 0) return;
+  k_gf_fold<<<dim3(grid_for((D + 1) / 2), 12), TPB, 0, st>>>(xv, yv, cap, D, zeta, xo, yo, ocap);
 }
 void launch_gf_inner_finish(cudaStream_t st, const u64* S, Key k01, Key k02, u32 purpose, u64 obj,
                             u64* h6) {
