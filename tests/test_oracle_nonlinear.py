@@ -179,3 +179,67 @@ def test_edabit_bit_batch_has_the_truncation_pairs_form():
     for f in ("p0_r1", "p1_m", "p1_r1", "p2_m"):
         assert not getattr(Y, f).any(), f
     assert np.array_equal(X.p0_r1, X.p1_r1) and np.array_equal(Y.p0_r2, Y.p2_r2)
+
+
+def _weighted_error(gr, r, errs):
+    """sum_j r^j err_j in GR(2^64, 64) for ring scalars err_j, with r^j by repeated products and
+    the scalar products coefficient by coefficient in Python integers."""
+    acc = [0] * gr.d
+    p = gr.const(1)
+    for e in errs:
+        e = int(e) % (1 << 64)
+        for c in range(gr.d):
+            acc[c] = (acc[c] + e * int(p[c])) % (1 << 64)
+        p = gr.mul(p, r)
+    return np.array(acc, dtype=U64)
+
+
+def _relation(gr, xs, ys, zs):
+    x, y, z = xs.open(gr.mask), ys.open(gr.mask), zs.open(gr.mask)
+    return gr.sub(gr.inner(x, y), z)
+
+
+@pytest.mark.parametrize("bad", [(), (3,), (0, 6)])
+def test_multiplication_transform_is_the_weighted_product_error(bad):
+    """Fig. MTP as batches 0, 2 and 3 use it: after the transform the claim's relation error
+    sum_j x'_j y_j - z' equals sum_j r^j (x_j y_j - z_j), the per-gate errors of the opened
+    triples weighted by the powers of r in gate order (zero for honest triples)."""
+    from oracle.verify import challenge_r, tran_mult
+    s = Session(bytes(range(2, 34)))
+    gr = s.gr
+    g = np.random.default_rng(12)
+    x = g.integers(0, 2 ** 64, 7, dtype=U64)
+    y = g.integers(0, 2 ** 64, 7, dtype=U64)
+    z = np.array([(int(a) * int(b)) % (1 << 64) for a, b in zip(x, y)], dtype=U64)
+    for j in bad:
+        z[j] ^= U64(1 << (13 + j))
+    X, Y, Z = (OP.share_input(s, v, 70 + k) for k, v in enumerate((x, y, z)))
+    r = challenge_r(s, 73, 0)
+    errs = [(int(a) * int(b) - int(c)) % (1 << 64) for a, b, c in zip(x, y, z)]
+    assert np.array_equal(_relation(gr, *tran_mult(s, X, Y, Z, r)), _weighted_error(gr, r, errs))
+    assert _relation(gr, *tran_mult(s, X, Y, Z, r)).any() == bool(bad)
+
+
+@pytest.mark.parametrize("bad", [(), (1,), (0, 4)])
+def test_row_transform_is_the_weighted_inner_product_error(bad):
+    """Fig. PBDP as the edaBit inner-product batch (batch 1) uses it: n inner products of
+    dimension k, row e weighted by r^e; the relation error equals
+    sum_e r^e (sum_i X_ei Y_ei - Z_e) with Python integers."""
+    s = Session(bytes(range(3, 35)))
+    gr = s.gr
+    g = np.random.default_rng(13)
+    n, k = 5, 4
+    Xv = g.integers(0, 2 ** 64, (n, k), dtype=U64)
+    Yv = g.integers(0, 2 ** 64, (n, k), dtype=U64)
+    Zv = np.array([sum(int(a) * int(b) for a, b in zip(Xv[e], Yv[e])) % (1 << 64)
+                   for e in range(n)], dtype=U64)
+    for e in bad:
+        Zv[e] += U64(1 << (20 + e))
+    X, Y, Z = (OP.share_input(s, v, 80 + q) for q, v in enumerate((Xv, Yv, Zv)))
+    from oracle.verify import challenge_r
+    r = challenge_r(s, 83, 1)
+    errs = [(sum(int(a) * int(b) for a, b in zip(Xv[e], Yv[e])) - int(Zv[e])) % (1 << 64)
+            for e in range(n)]
+    rel = _relation(gr, *NL.tran_rows(s, X, Y, Z, r))
+    assert np.array_equal(rel, _weighted_error(gr, r, errs))
+    assert rel.any() == bool(bad)
