@@ -1,5 +1,6 @@
 """The im2col / layout index maps of the secure CNN against a direct convolution (CPU)."""
 import numpy as np
+import pytest
 
 from paper_2411_09287_gb300 import secure_cnn as SC
 
@@ -43,3 +44,15 @@ def test_net_b_geometry_reaches_the_4096_flatten():
     assert p["c5"].shape == (256, 128, 3, 3) and p["f1"].shape == (4096, 512)
     x = np.random.default_rng(7).uniform(0, 1, (2, 3, 32, 32))
     assert SC.net_b_fp64(x, p).shape == (2, 10)
+
+
+@pytest.mark.parametrize("H,W", [(24, 24), (32, 32), (8, 8), (2, 2)])
+@pytest.mark.parametrize("budget", [SC.NL_CHUNK, 1000, 1])
+def test_pool_chunks_are_the_most_whole_planes_within_the_budget(H, W, budget):
+    """A max-pool call takes whole channel planes, 3 H W / 4 comparisons each (three per 2x2
+    window): as many as fit in the comparison budget, at least one, at most all."""
+    for planes in (1, 7, 1024, 16384):
+        step = SC.pool_planes(budget, H, W, planes)
+        assert 1 <= step <= planes
+        assert step == 1 or 3 * H * W * step <= 4 * budget
+        assert step == planes or 3 * H * W * (step + 1) > 4 * budget
