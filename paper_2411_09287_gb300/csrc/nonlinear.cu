@@ -324,8 +324,8 @@ __global__ void k_gf_tran(const u64* __restrict__ X, const u64* __restrict__ Y, 
 // Party sums of a secure GF inner product sum_i u_i v_i over the first D elements (components
 // may be absent: null):  S[0] = sum r_u r_v (P0), S[1] = sum (m_u [r_v]_1 + m_v [r_u]_1) (P1),
 // S[2] = sum (m_u m_v + m_u [r_v]_2 + m_v [r_u]_2) (P2) (over Z_2 the signs vanish).  XOR-added
-// into S; u (and v) may be given as a fold of two halves: u_i = a u_{2i} + b u_{2i+1} when
-// (fa, fb) != (1, 0), i < D (stride 2).
+// into S; with fold set, u (and v) are given as a fold of two halves: u_i = fa u_{2i} +
+// fb u_{2i+1}, i < D (fold = 2: fa = 1 + x, fb = x, taken as a shift and an XOR).
 struct GfVec {
   const u64* c[6];
 };
