@@ -281,8 +281,9 @@ int mpc_verify_matmul(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs, cons
                       int trunc_bits, uint64_t matmul_call_id, int R_main, int R_trunc,
                       void* workspace, size_t workspace_bytes, uint64_t* trace);
 
-/* mpc_verify_matmul of a layer made by mpc_matmul_keyed: the truncation batch regenerates the
- * pairs' bits from the same row keys (M device words; NULL is mpc_verify_matmul). */
+/* mpc_verify_matmul (Fig. PBDP, Fig. trunc) of a layer made by mpc_matmul_keyed (reading A12):
+ * the truncation batch regenerates the pairs' bits from the same row keys (M device words; NULL
+ * is mpc_verify_matmul). */
 int mpc_verify_matmul_keyed(mpc_ctx* ctx, uint64_t verify_id, const uint64_t* xs,
                             const uint64_t* ws_, const uint64_t* zpre, const uint64_t* pq,
                             int64_t M, int64_t N, int64_t K, int trunc_bits,
@@ -303,7 +304,7 @@ int64_t mpc_trace_words(const mpc_ctx* ctx, int op, int64_t a, int64_t b, int64_
 int mpc_reconstruct(mpc_ctx* ctx, const uint64_t* xs, int64_t n, uint64_t* out, int out_on_host,
                     void* workspace, size_t workspace_bytes);
 
-/* Pi_Rec without any device allocation: the same protocol, messages, checks and result as
+/* Pi_Rec (Sec. 2) without any device allocation: the same protocol, messages, checks and result as
  * mpc_reconstruct with a device output, but the received shares and the hash scratch live in
  * one fixed device array compiled into the library instead of a caller-provided workspace.  The
  * paper has no counterpart; this serves callers that cannot allocate device memory when they
@@ -419,21 +420,24 @@ int mpc_gather(mpc_ctx* ctx, const uint64_t* xs, int64_t n_in, const int64_t* id
 #define MPC_TRACE_GF_ROUND 13
 int mpc_relu(mpc_ctx* ctx, uint64_t call_id, uint64_t verify_id, const uint64_t* xs, int64_t n,
              uint64_t* out, void* workspace, size_t workspace_bytes, uint64_t* trace);
-/* 2x2 / stride-2 max-pool of a (B, C, H, W) tensor, H and W even; out has B C (H/2) (W/2)
- * elements.  Stage 0 compares the window pairs ([2i][2j], [2i][2j+1]) and ([2i+1][2j],
- * [2i+1][2j+1]) in one batch, stage 1 the two winners. */
+/* 2x2 / stride-2 max-pool (Sec. 4.3: max(a, b) = b + (a - b)[a >= b], reading N6) of a
+ * (B, C, H, W) tensor, H and W even; out has B C (H/2) (W/2) elements.  Stage 0 compares the
+ * window pairs ([2i][2j], [2i][2j+1]) and ([2i+1][2j], [2i+1][2j+1]) in one batch, stage 1 the
+ * two winners; the comparisons and their verification are mpc_relu's.  Arguments, trace and
+ * return codes as mpc_relu. */
 int mpc_maxpool2(mpc_ctx* ctx, uint64_t call_id, uint64_t verify_id, const uint64_t* xs, int64_t B,
                  int64_t C, int64_t H, int64_t W, uint64_t* out, void* workspace,
                  size_t workspace_bytes, uint64_t* trace);
 
-/* Ledger: bytes[phase * MPC_NPROTO + proto] of every message sent so far, and the message
- * count.  Hash messages count 32 bytes. */
+/* Ledger (the communication that Table 1 and Sec. 4.2 count): bytes[phase * MPC_NPROTO + proto]
+ * of every message sent so far, and the message count.  Hash messages count 32 bytes. */
 int mpc_ledger(const mpc_ctx* ctx, uint64_t* bytes, uint64_t* messages);
 void mpc_ledger_reset(mpc_ctx* ctx);
 
-/* Arm a one-shot fault: the next message delivered at `site` has element (index mod length)
- * XORed with xor_mask (MPC_SITE_HIGH_BIT ignores xor_mask and uses 2^63).  Host side only; it
- * models a cheating party and never faults the device. */
+/* Arm a one-shot fault (the actively corrupted party of Sec. 2's security model, whose cheating
+ * the checks must catch, with abort): the next message delivered at `site` has element
+ * (index mod length) XORed with xor_mask (MPC_SITE_HIGH_BIT ignores xor_mask and uses 2^63).
+ * Host side only; it never faults the device. */
 int mpc_inject_fault(mpc_ctx* ctx, int site, uint64_t index, uint64_t xor_mask);
 
 /* Phase timers: with profiling on, the library brackets each phase of its work with CUDA events
