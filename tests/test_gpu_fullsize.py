@@ -1,9 +1,11 @@
-"""The full-size layer that bench.py times (config C3: 4096 x 4096 x 4096 over Z_2^64, uniform
-64-bit words, Pi_Trunc^13, both verification batches, Pi_Rec) on the tensor-core path, in the
-bench's launch configuration.  The oracle cannot run it whole, so the test checks what holds at
-any size: the verification accepts, and on sampled outputs the reconstructed pre-truncation
-product equals X W mod 2^64 (each computed one by one with Python integers); a product with one
-flipped bit is rejected by the same verification."""
+"""A full-size layer of config C3 (4096 x 4096 x 4096 over Z_2^64, uniform 64-bit words,
+Pi_Trunc^13, both verification batches, Pi_Rec) on the tensor-core path with the default tuning:
+one truncation chunk of 2^24 outputs.  bench.py's default layer, 8192^3, runs the same code in
+four chunks and checks 16 sampled outputs the same way on every run; the chunked paths are
+compared with the oracle at small sizes in test_gpu_trunc_blocks.py.  The oracle cannot run this
+layer whole, so the test checks what holds at any size: the verification accepts, and on sampled
+outputs the reconstructed pre-truncation product equals X W mod 2^64 (each computed one by one
+with Python integers); a product with one flipped bit is rejected by the same verification."""
 import hashlib
 
 import numpy as np
