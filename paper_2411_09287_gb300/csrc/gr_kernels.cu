@@ -425,12 +425,6 @@ __global__ void k_fold_lifted(const u64* __restrict__ Y, long long Dh, long long
   }
 }
 
-__global__ void k_fill(u64* __restrict__ p, long long n, u64 v) {
-  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < n;
-       w += (long long)gridDim.x * blockDim.x)
-    p[w] = v;
-}
-
 __global__ void k_neg_copy(const u64* __restrict__ a, long long n, u64* __restrict__ out) {
   for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < n;
        w += (long long)gridDim.x * blockDim.x)
@@ -916,11 +910,6 @@ void launch_fold_lifted(cudaStream_t st, const u64* Y, long long Dh, long long D
                         u64* out) {
   if (Dh <= 0) return;
   k_fold_lifted<<<grid_for(Dh * 16), TPB, 0, st>>>(Y, Dh, D, f, out);
-}
-
-void launch_fill(cudaStream_t st, u64* p, long long n, u64 v) {
-  if (n <= 0) return;
-  k_fill<<<grid_for(n), TPB, 0, st>>>(p, n, v);
 }
 
 void launch_neg_copy(cudaStream_t st, const u64* a, long long n, u64* out) {

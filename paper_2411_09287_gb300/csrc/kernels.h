@@ -65,24 +65,18 @@ int limb_gemm_tc(cudaStream_t st, long long M, long long N, long long K, int nte
                  const GemmTerm* terms, const Epi& epi, void* scratch, unsigned* err,
                  unsigned err_flag, cudaEvent_t ev0, cudaEvent_t ev1, int split_min = 0);
 
-// out[i][c] = add0[i][c] + sum_k A[i][k] M[k][c], i < R, k, c < 64 (M row-major 64 x 64) with
-// A[i][k] = p0[i][k] + s1 p1[i][k] (p1 may be null), or, with a_bits, A[i][k] = bit k of the word
-// p0[i].  add0 may be null; ld_add0 = 0 means ldc.  Exact, on the tensor cores.  Needs 16-byte
-// aligned bases and even row strides (returns -1 otherwise).
-int gr_matmul_tc(cudaStream_t st, long long R, const u64* p0, const u64* p1, u64 s1, long long lda,
-                 int a_bits, const u64* Mmat, const u64* add0, long long ld_add0, u64* out,
-                 long long ldc, unsigned* err, unsigned err_flag);
-
 // Row map of a GR matrix product: logical row rho sits at word offset (rho % q) s1 + (rho / q) s2
 // (q = 0: rho s1).  q must be a multiple of 128.
 struct GrRowMap {
   long long q, s1, s2;
 };
-// The general form: rows rho < R, A row rho at p0 + in(rho) (minus p1 + in(rho): s1 must be -1
-// when p1 is given; returns -1 otherwise), or with a_bits
-// the word p0[in(rho)]; matrix rho / mrows at Mmat + 4096 (rho / mrows) (mrows = 0: one matrix,
-// else a multiple of 128); out row rho at out + om(rho), written only when om(rho) < out_lim
-// (0: no limit); add0 row rho at add0 + rho ld_add0 (0: 64).
+// GR-matrix product on the tensor cores, exact: out[rho][c] = add0[rho][c] +
+// sum_k A[rho][k] M[k][c] (k, c < 64, M row-major 64 x 64) for rows rho < R.  A row rho at
+// p0 + in(rho) (minus p1 + in(rho): s1 must be -1 when p1 is given; returns -1 otherwise), or
+// with a_bits the bits of the word p0[in(rho)]; matrix rho / mrows at Mmat + 4096 (rho / mrows)
+// (mrows = 0: one matrix, else a multiple of 128); out row rho at out + om(rho), written only
+// when om(rho) < out_lim (0: no limit); add0 (may be null) row rho at add0 + rho ld_add0
+// (0: 64).  Needs 16-byte aligned bases and even row strides (returns -1 otherwise).
 struct GrMMArgs {
   long long R;
   const u64* p0;
@@ -207,7 +201,6 @@ void launch_gram_lifted(cudaStream_t st, const u64* const x[6], const u64* const
                         long long D, u64* S);
 void launch_fold_lifted(cudaStream_t st, const u64* Y, long long Dh, long long D, const u64* f,
                         u64* out);
-void launch_fill(cudaStream_t st, u64* p, long long n, u64 v);
 void launch_neg_copy(cudaStream_t st, const u64* a, long long n, u64* out);
 void launch_gr_check_zero(cudaStream_t st, const u64* v, u32* status, u32 flag);
 void launch_trunc_u(cudaStream_t st, const u64* r, int t, u64* u);

@@ -1865,24 +1865,6 @@ int gr_matmul_tc_ex(cudaStream_t st, const GrMMArgs& args, unsigned* err, unsign
   return 0;
 }
 
-int gr_matmul_tc(cudaStream_t st, long long R, const u64* p0, const u64* p1, u64 s1, long long lda,
-                 int a_bits, const u64* Mmat, const u64* add0, long long ld_add0, u64* out,
-                 long long ldc, unsigned* err, unsigned err_flag) {
-  GrMMArgs a{};
-  a.R = R;
-  a.p0 = p0;
-  a.p1 = p1;
-  a.s1 = s1;
-  a.in = GrRowMap{0, a_bits ? 1 : lda, 0};
-  a.a_bits = a_bits;
-  a.Mmat = Mmat;
-  a.add0 = add0;
-  a.ld_add0 = ld_add0 ? ld_add0 : ldc;
-  a.out = out;
-  a.om = GrRowMap{0, ldc, 0};
-  return gr_matmul_tc_ex(st, a, err, err_flag);
-}
-
 int gram_jobs_tc(cudaStream_t st, long long Dh, const GramJobs& jobs, unsigned* err,
                  unsigned err_flag, int nsplit) {
   if (Dh <= 0 || jobs.n <= 0) return 0;
